@@ -1,0 +1,176 @@
+/*
+ * llama.h -- C ABI of the B300-native scheduling step of Llama
+ * (arXiv 2102.01887): per-invocation slack (Section 4.1, Algorithm 1) and
+ * cost-based configuration selection (Section 4.2, Eq. 1).
+ *
+ * Units and types.  Latencies are int32 microseconds, costs int64
+ * nano-dollars per invocation (the C(x)/B(x) term of Eq. 1), times int64
+ * microseconds.  All integer arithmetic is exact: decisions are bit-exact
+ * against a plain CPU evaluation of the same definitions.
+ *
+ * Ownership.  Every llama_set_* call copies its (host) arrays into
+ * library-owned device memory; the caller may free them on return.  The
+ * scheduling calls read caller buffers and write the caller-owned output;
+ * nothing the caller passes is retained after the call (blocking form) or
+ * after the stream reaches the call (asynchronous form).
+ *
+ * Errors.  Every call returns an int status (LLAMA_OK or a negative
+ * LLAMA_E* code); llama_last_error() gives a one-line description of the
+ * last failure on that context.  A context is not thread-safe: use one
+ * context per host thread, or serialise calls.
+ */
+#ifndef LLAMA_H
+#define LLAMA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LLAMA_OK 0
+#define LLAMA_EINVAL (-1)    /* invalid argument, table, DAG or invocation */
+#define LLAMA_ENOMEM (-2)    /* device or host allocation failed */
+#define LLAMA_ECUDA (-3)     /* a CUDA runtime call or kernel launch failed */
+#define LLAMA_ENOTREADY (-4) /* scheduling before both DAGs and profiles are set */
+#define LLAMA_ETIMEOUT (-5)  /* a bounded device-side wait gave up */
+
+/* Objective (Section 4.2).  COST_FIRST: feasible (L < slack) beats
+ * infeasible; among feasible configurations the lowest C/B wins, among
+ * infeasible ones the lowest latency; ties go to the lowest configuration
+ * index.  ALPHA: Eq. 1 in integers, obj = C/B if L < slack, otherwise
+ * C/B + floor(alpha_num*L*R(x) / (alpha_den*B(x)*R_total(lambda(x)))),
+ * saturating at INT64_MAX; argmin over (obj, index). */
+#define LLAMA_MODE_COST_FIRST 0
+#define LLAMA_MODE_ALPHA 1
+
+/* llama_decision.flags */
+#define LLAMA_FLAG_FEASIBLE 1 /* the chosen configuration meets its slack */
+#define LLAMA_FLAG_INVALID 2  /* the invocation was rejected; cfg = -1 */
+
+/* Limits enforced by validation. */
+#define LLAMA_MAX_HW 8          /* backends lambda */
+#define LLAMA_MAX_CFG 8192      /* configurations of one operation */
+#define LLAMA_MAX_INV (1 << 30) /* invocations in one call */
+#define LLAMA_MAX_ALPHA 65535   /* alpha_num, alpha_den, B(x), R(x) upper bound */
+
+typedef struct llama_ctx llama_ctx;
+
+typedef struct llama_opts {
+    int32_t mode;      /* LLAMA_MODE_* */
+    int32_t n_hw;      /* number of backends, 1..LLAMA_MAX_HW */
+    int64_t alpha_num; /* alpha = alpha_num / alpha_den, each in 1..LLAMA_MAX_ALPHA (ALPHA mode) */
+    int64_t alpha_den;
+    int32_t device;    /* CUDA device ordinal the context lives on */
+    int32_t use_graph; /* nonzero: replay each scheduling call as one CUDA graph */
+} llama_opts;
+
+/* One scheduling decision; 24 bytes, naturally aligned. */
+typedef struct llama_decision {
+    int32_t cfg;   /* op-local index of the chosen configuration, -1 if invalid */
+    int32_t lat;   /* L(cfg), us */
+    int64_t cost;  /* C(cfg)/B(cfg), nano-dollars */
+    int32_t slack; /* slack(op, lambda(cfg)), us (Algorithm 1) */
+    int32_t flags; /* LLAMA_FLAG_* */
+} llama_decision;
+
+/* Create a context on opts->device.  *out is set on success.
+ * Errors: EINVAL (bad opts), ENOMEM, ECUDA. */
+int llama_create(llama_ctx **out, const llama_opts *opts);
+
+/* Release every device and host resource of the context (NULL is a no-op). */
+void llama_destroy(llama_ctx *ctx);
+
+/* Pipelines (Section 3.2, Fig. 1): n_dags DAGs over global operation ids.
+ *   dag_op_off[n_dags+1]  DAG d owns global ops [dag_op_off[d], dag_op_off[d+1]);
+ *                         dag_op_off[0] = 0, every DAG has at least one op.
+ *   row_ptr[n_ops+1]      successor CSR, n_ops = dag_op_off[n_dags];
+ *   col[row_ptr[n_ops]]   successor global ids, inside the op's own DAG;
+ *   slo_us[n_dags]        pipeline latency target, 1..INT32_MAX.
+ * Host memory.  Rejects (EINVAL) a malformed CSR, a cross-DAG edge, a
+ * self-loop or a cycle.  Replaces any previous DAGs. */
+int llama_set_dags(llama_ctx *ctx, int32_t n_dags, const int32_t *dag_op_off,
+                   const int32_t *row_ptr, const int32_t *col, const int64_t *slo_us);
+
+/* Profiles (Section 3.2, "configuration specification"; Section 4.2).
+ *   cfg_off[n_ops+1]          configurations of op v are [cfg_off[v], cfg_off[v+1]),
+ *                             1..LLAMA_MAX_CFG per op;
+ *   hw_off[n_ops*(n_hw+1)]    op-local start of each backend's segment: configurations
+ *                             are grouped hardware-major, hw_off[v][0] = 0,
+ *                             non-decreasing, hw_off[v][n_hw] = size of op v;
+ *   lat_us[n_cfg]             L(x), 1..INT32_MAX-1;
+ *   cost_nd[n_cfg]            C(x)/B(x), >= 0;
+ *   ref_cfg[n_ops]            op-local reference configuration (Section 3.2:
+ *                             smallest CPU configuration, 1 core, batch 1);
+ *   batch, res [n_cfg]        B(x), R(x) in 1..LLAMA_MAX_ALPHA   (ALPHA mode; else NULL ok);
+ *   res_total[n_hw]           R_total(lambda) in 1..INT32_MAX     (ALPHA mode; else NULL ok).
+ * Host memory.  Copies the tables to the device and builds the scan
+ * encoding there.  Errors: EINVAL, ENOMEM, ECUDA. */
+int llama_set_profiles(llama_ctx *ctx, int32_t n_ops, const int64_t *cfg_off,
+                       const int32_t *hw_off, const int32_t *lat_us, const int64_t *cost_nd,
+                       const int32_t *ref_cfg, const int32_t *batch, const int32_t *res,
+                       const int32_t *res_total);
+
+/* Queueing time per backend, queueingTime(lambda) of Algorithm 1 (Eq. 2's
+ * value, supplied by the caller), q_us[n_hw] in 0..INT32_MAX; host memory;
+ * default all zero. */
+int llama_set_queue(llama_ctx *ctx, const int64_t *q_us);
+
+/* Schedule n_inv pending invocations at time now_us (blocking).
+ *   dag[n_inv], op_local[n_inv]  the invocation's DAG and op-local operation;
+ *   start_us[n_inv]              start time of its pipeline instance, 0..now_us;
+ *   out[n_inv]                   decisions, written in invocation order.
+ * Each pointer may be host or device memory (detected per pointer).  An
+ * invalid invocation (bad DAG or op index, start outside 0..now) gets
+ * cfg = -1 and LLAMA_FLAG_INVALID, every valid one is still decided, and the
+ * call returns EINVAL.  n_inv = 0 is a no-op.  Errors: EINVAL, ENOTREADY,
+ * ENOMEM, ECUDA. */
+int llama_schedule(llama_ctx *ctx, int64_t n_inv, const int32_t *dag, const int32_t *op_local,
+                   const int64_t *start_us, int64_t now_us, llama_decision *out);
+
+/* Same as llama_schedule, enqueued on `stream` (a cudaStream_t; NULL = the
+ * legacy default stream) and returning without waiting.  Every pointer must
+ * be device memory that stays valid until the stream passes the call.
+ * Invalid invocations are flagged in `out` but the return value does not
+ * report them.  Scratch space is library-owned and grows on demand; call
+ * llama_reserve first to keep allocations out of the call (for instance
+ * before a stream capture).  Errors: EINVAL (bad arguments), ENOTREADY,
+ * ENOMEM, ECUDA. */
+int llama_schedule_async(llama_ctx *ctx, int64_t n_inv, const int32_t *dag,
+                         const int32_t *op_local, const int64_t *start_us, int64_t now_us,
+                         llama_decision *out, void *stream);
+
+/* Pre-allocate scratch for calls of up to max_inv invocations. */
+int llama_reserve(llama_ctx *ctx, int64_t max_inv);
+
+/* Longest remaining reference-latency path of every operation, op included
+ * (the RemainingPathLatency maximised over the paths of Algorithm 1):
+ * cp_us[n_ops], host memory.  Runs the device critical-path pass. */
+int llama_critical_path(llama_ctx *ctx, int64_t *cp_us);
+
+/* Slack of every invocation for every backend (Algorithm 1; 0 once the
+ * target has passed), slack_us[n_inv*n_hw] int32, row-major by invocation,
+ * -1 for an invalid invocation.  Host or device pointers, blocking. */
+int llama_slack(llama_ctx *ctx, int64_t n_inv, const int32_t *dag, const int32_t *op_local,
+                const int64_t *start_us, int64_t now_us, int32_t *slack_us);
+
+/* Tracing.  events[0..LLAMA_TRACE_EVENTS-1] are caller-owned cudaEvent_t
+ * handles; once set, every scheduling call records them on its stream at
+ * the phase boundaries: [0] call start, [1] after the critical path, [2]
+ * after counting, [3] after the prefix scan, [4] after the scatter (slack),
+ * [5] after scoring.  n_events = 0 turns tracing off.  The events must stay
+ * valid while tracing is on.  Errors: EINVAL. */
+#define LLAMA_TRACE_EVENTS 6
+int llama_set_trace_events(llama_ctx *ctx, void *const *events, int32_t n_events);
+
+/* Kernel launches issued by the last scheduling call (for accounting). */
+int llama_last_launch_count(llama_ctx *ctx);
+
+/* One-line description of the last error on ctx (never NULL). */
+const char *llama_last_error(llama_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LLAMA_H */

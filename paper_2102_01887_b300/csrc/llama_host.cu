@@ -1,0 +1,627 @@
+// llama_host.cu -- C ABI of the scheduling step (include/llama.h): argument
+// validation, DAG levelling, padded table layout, device memory, launches.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "llama_internal.cuh"
+
+using namespace llama;
+
+namespace {
+
+// Owning device buffer.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    cudaError_t alloc(size_t n) {
+        release();
+        if (n == 0) n = 16;
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e == cudaSuccess) bytes = n; else p = nullptr;
+        return e;
+    }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// Makes the context's device current for the duration of an API call.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+struct llama_ctx {
+    llama_opts opts{};
+    int num_sms = 0;
+    int max_smem_optin = 0;
+    cudaStream_t stream = nullptr;
+    std::string err = "no error";
+
+    // DAGs
+    bool dags_set = false;
+    int32_t n_dags = 0, n_ops_dag = 0;
+    DevBuf dag_op_off, row_ptr, col, slo, topo, lvl_off, dag_lvl;
+
+    // profiles
+    bool prof_set = false;
+    int32_t n_ops = 0, max_npad = 0;
+    int64_t n_cfg = 0, n_pad = 0;
+    DevBuf cfg_off, hw_off, lat, cost, ref_cfg, batch, res, res_total;
+    DevBuf pad_off, seg_pad, lat_pad, rf, df, inv, fast;
+    DevBuf ref, cp;
+    int64_t q[LLAMA_MAX_HW] = {0};
+
+    // bucketing scratch
+    int64_t cap_inv = 0;
+    int32_t cap_ops = 0;
+    DevBuf cnt, op_start, wprefix, gop, slot, b_inv, b_slack, n_invalid;
+
+    // staging for host-memory arguments of the blocking calls
+    int64_t cap_stage = 0;
+    DevBuf s_dag, s_opl, s_start, s_out, s_slack;
+    unsigned long long *h_invalid = nullptr;  // pinned
+
+    int score_blocks_per_sm = 0;
+    int last_launches = 0;
+    cudaEvent_t trace[LLAMA_TRACE_EVENTS] = {};
+    bool tracing = false;
+
+    int fail(int code, const std::string &msg) {
+        err = msg;
+        return code;
+    }
+    int cuda_fail(cudaError_t e, const char *what) {
+        err = std::string(what) + ": " + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? LLAMA_ENOMEM : LLAMA_ECUDA;
+    }
+};
+
+#define LL_CUDA(ctx, call)                                   \
+    do {                                                     \
+        cudaError_t e__ = (call);                            \
+        if (e__ != cudaSuccess) return (ctx)->cuda_fail(e__, #call); \
+    } while (0)
+
+namespace {
+
+DevProblem make_problem(const llama_ctx *c) {
+    DevProblem P{};
+    P.n_dags = c->n_dags;
+    P.n_ops = c->n_ops;
+    P.n_hw = c->opts.n_hw;
+    P.mode = c->opts.mode;
+    P.dag_op_off = c->dag_op_off.as<int32_t>();
+    P.row_ptr = c->row_ptr.as<int32_t>();
+    P.col = c->col.as<int32_t>();
+    P.slo = c->slo.as<int64_t>();
+    P.cfg_off = c->cfg_off.as<int64_t>();
+    P.hw_off = c->hw_off.as<int32_t>();
+    P.lat = c->lat.as<int32_t>();
+    P.cost = c->cost.as<int64_t>();
+    P.ref_cfg = c->ref_cfg.as<int32_t>();
+    P.batch = c->batch.as<int32_t>();
+    P.res = c->res.as<int32_t>();
+    P.res_total = c->res_total.as<int32_t>();
+    P.pad_off = c->pad_off.as<int64_t>();
+    P.seg_pad = c->seg_pad.as<int32_t>();
+    P.lat_pad = c->lat_pad.as<int32_t>();
+    P.rf = c->rf.as<uint16_t>();
+    P.df = c->df.as<uint16_t>();
+    P.inv = c->inv.as<uint16_t>();
+    P.fast = c->fast.as<int32_t>();
+    P.max_npad = c->max_npad;
+    P.ref = c->ref.as<int64_t>();
+    P.cp = c->cp.as<int64_t>();
+    for (int h = 0; h < LLAMA_MAX_HW; ++h) P.q[h] = c->q[h];
+    P.alpha_num = c->opts.alpha_num;
+    P.alpha_den = c->opts.alpha_den;
+    return P;
+}
+
+BucketScratch make_scratch(const llama_ctx *c) {
+    BucketScratch S{};
+    S.cnt = c->cnt.as<int32_t>();
+    S.op_start = c->op_start.as<int32_t>();
+    S.wprefix = c->wprefix.as<int64_t>();
+    S.gop = c->gop.as<int32_t>();
+    S.slot = c->slot.as<int32_t>();
+    S.b_inv = c->b_inv.as<int32_t>();
+    S.b_slack = c->b_slack.as<int32_t>();
+    S.n_invalid = c->n_invalid.as<unsigned long long>();
+    return S;
+}
+
+size_t score_smem_bytes(const llama_ctx *c) {
+    const size_t per = 4 + 2 + (c->opts.mode == LLAMA_MODE_ALPHA ? 2 : 0);
+    return per * (size_t)c->max_npad;
+}
+
+int check_ready(llama_ctx *c) {
+    if (!c->dags_set || !c->prof_set)
+        return c->fail(LLAMA_ENOTREADY, "schedule called before llama_set_dags and llama_set_profiles");
+    if (c->n_ops_dag != c->n_ops)
+        return c->fail(LLAMA_EINVAL, "DAGs and profiles describe different numbers of operations");
+    return LLAMA_OK;
+}
+
+int ensure_scratch(llama_ctx *c, int64_t n_inv) {
+    const int H = c->opts.n_hw;
+    if (c->cap_ops < c->n_ops + 1) {
+        const int32_t n = c->n_ops + 1;
+        LL_CUDA(c, c->cnt.alloc(sizeof(int32_t) * n));
+        LL_CUDA(c, c->op_start.alloc(sizeof(int32_t) * n));
+        LL_CUDA(c, c->wprefix.alloc(sizeof(int64_t) * n));
+        LL_CUDA(c, c->n_invalid.alloc(sizeof(unsigned long long)));
+        c->cap_ops = n;
+    }
+    if (c->cap_inv < n_inv) {
+        const int64_t n = std::max<int64_t>(n_inv, 1024);
+        LL_CUDA(c, c->gop.alloc(sizeof(int32_t) * n));
+        LL_CUDA(c, c->slot.alloc(sizeof(int32_t) * n));
+        LL_CUDA(c, c->b_inv.alloc(sizeof(int32_t) * n));
+        LL_CUDA(c, c->b_slack.alloc(sizeof(int32_t) * n * H));
+        c->cap_inv = n;
+    }
+    return LLAMA_OK;
+}
+
+int ensure_stage(llama_ctx *c, int64_t n_inv) {
+    if (c->cap_stage >= n_inv) return LLAMA_OK;
+    const int64_t n = std::max<int64_t>(n_inv, 1024);
+    LL_CUDA(c, c->s_dag.alloc(sizeof(int32_t) * n));
+    LL_CUDA(c, c->s_opl.alloc(sizeof(int32_t) * n));
+    LL_CUDA(c, c->s_start.alloc(sizeof(int64_t) * n));
+    LL_CUDA(c, c->s_out.alloc(sizeof(llama_decision) * n));
+    LL_CUDA(c, c->s_slack.alloc(sizeof(int32_t) * n * c->opts.n_hw));
+    c->cap_stage = n;
+    return LLAMA_OK;
+}
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int grid_for(const llama_ctx *c, int64_t n, int threads) {
+    const int64_t want = (n + threads - 1) / threads;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)c->num_sms * 16));
+}
+
+// The launch sequence of one scheduling call (all device pointers).
+int launch_schedule(llama_ctx *c, int64_t n_inv, const int32_t *dag, const int32_t *op_local,
+                    const int64_t *start, int64_t now, llama_decision *out, cudaStream_t s) {
+    const DevProblem P = make_problem(c);
+    const BucketScratch S = make_scratch(c);
+    auto mark = [&](int k) { if (c->tracing) cudaEventRecord(c->trace[k], s); };
+    mark(0);
+    LL_CUDA(c, cudaMemsetAsync(S.cnt, 0, sizeof(int32_t) * c->n_ops, s));
+    LL_CUDA(c, cudaMemsetAsync(S.n_invalid, 0, sizeof(unsigned long long), s));
+    k_critical_path<<<c->n_dags, 64, 0, s>>>(P, c->topo.as<int32_t>(), c->lvl_off.as<int32_t>(),
+                                             c->dag_lvl.as<int32_t>());
+    mark(1);
+    const int gi = grid_for(c, n_inv, 256);
+    k_bucket_count<<<gi, 256, 0, s>>>(P, n_inv, dag, op_local, start, now, S, out);
+    mark(2);
+    k_bucket_scan<<<1, 1024, 0, s>>>(P, S);
+    mark(3);
+    k_bucket_scatter<<<gi, 256, 0, s>>>(P, n_inv, dag, start, now, S);
+    mark(4);
+    const int grid = c->num_sms * c->score_blocks_per_sm;
+    const size_t smem = score_smem_bytes(c);
+    if (c->opts.mode == LLAMA_MODE_ALPHA)
+        k_score_alpha<<<grid, kScoreThreads, smem, s>>>(P, S, out);
+    else
+        k_score_cost_first<<<grid, kScoreThreads, smem, s>>>(P, S, out);
+    mark(5);
+    LL_CUDA(c, cudaGetLastError());
+    c->last_launches = 5;
+    return LLAMA_OK;
+}
+
+int check_inv_args(llama_ctx *c, int64_t n_inv, const void *a, const void *b, const void *d,
+                   const void *o) {
+    if (n_inv < 0 || n_inv > LLAMA_MAX_INV) return c->fail(LLAMA_EINVAL, "n_inv out of range");
+    if (n_inv > 0 && (!a || !b || !d || !o)) return c->fail(LLAMA_EINVAL, "null invocation or output pointer");
+    return LLAMA_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" int llama_create(llama_ctx **out, const llama_opts *opts) {
+    if (!out || !opts) return LLAMA_EINVAL;
+    *out = nullptr;
+    if (opts->mode != LLAMA_MODE_COST_FIRST && opts->mode != LLAMA_MODE_ALPHA) return LLAMA_EINVAL;
+    if (opts->n_hw < 1 || opts->n_hw > LLAMA_MAX_HW) return LLAMA_EINVAL;
+    if (opts->mode == LLAMA_MODE_ALPHA &&
+        (opts->alpha_num < 1 || opts->alpha_num > LLAMA_MAX_ALPHA || opts->alpha_den < 1 ||
+         opts->alpha_den > LLAMA_MAX_ALPHA))
+        return LLAMA_EINVAL;
+    int n_dev = 0;
+    if (cudaGetDeviceCount(&n_dev) != cudaSuccess) {
+        cudaGetLastError();
+        return LLAMA_ECUDA;
+    }
+    if (opts->device < 0 || opts->device >= n_dev) return LLAMA_EINVAL;
+    llama_ctx *c = new (std::nothrow) llama_ctx();
+    if (!c) return LLAMA_ENOMEM;
+    c->opts = *opts;
+    DeviceGuard g(opts->device);
+    if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, opts->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
+                               opts->device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMallocHost(&c->h_invalid, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return LLAMA_ECUDA;
+    }
+    *out = c;
+    return LLAMA_OK;
+}
+
+extern "C" void llama_destroy(llama_ctx *c) {
+    if (!c) return;
+    {
+        DeviceGuard g(c->opts.device);
+        if (c->stream) cudaStreamSynchronize(c->stream);
+        if (c->stream) cudaStreamDestroy(c->stream);
+        if (c->h_invalid) cudaFreeHost(c->h_invalid);
+        delete c;  // DevBuf destructors free device memory with the device current
+    }
+}
+
+extern "C" const char *llama_last_error(llama_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+extern "C" int llama_last_launch_count(llama_ctx *c) { return c ? c->last_launches : 0; }
+
+extern "C" int llama_set_trace_events(llama_ctx *c, void *const *events, int32_t n_events) {
+    if (!c) return LLAMA_EINVAL;
+    if (n_events == 0) {
+        c->tracing = false;
+        return LLAMA_OK;
+    }
+    if (n_events != LLAMA_TRACE_EVENTS || !events)
+        return c->fail(LLAMA_EINVAL, "set_trace_events: need LLAMA_TRACE_EVENTS event handles");
+    for (int k = 0; k < LLAMA_TRACE_EVENTS; ++k) {
+        if (!events[k]) return c->fail(LLAMA_EINVAL, "set_trace_events: null event");
+        c->trace[k] = (cudaEvent_t)events[k];
+    }
+    c->tracing = true;
+    return LLAMA_OK;
+}
+
+extern "C" int llama_set_dags(llama_ctx *c, int32_t n_dags, const int32_t *dag_op_off,
+                              const int32_t *row_ptr, const int32_t *col, const int64_t *slo_us) {
+    if (!c) return LLAMA_EINVAL;
+    if (n_dags < 1 || !dag_op_off || !row_ptr || !slo_us)
+        return c->fail(LLAMA_EINVAL, "set_dags: need n_dags >= 1 and non-null arrays");
+    if (dag_op_off[0] != 0) return c->fail(LLAMA_EINVAL, "set_dags: dag_op_off[0] must be 0");
+    for (int32_t d = 0; d < n_dags; ++d) {
+        if (dag_op_off[d + 1] <= dag_op_off[d])
+            return c->fail(LLAMA_EINVAL, "set_dags: every DAG needs at least one operation");
+        if (slo_us[d] < 1 || slo_us[d] > INT32_MAX)
+            return c->fail(LLAMA_EINVAL, "set_dags: slo_us out of 1..INT32_MAX");
+    }
+    const int32_t n_ops = dag_op_off[n_dags];
+    if (row_ptr[0] != 0) return c->fail(LLAMA_EINVAL, "set_dags: row_ptr[0] must be 0");
+    for (int32_t v = 0; v < n_ops; ++v)
+        if (row_ptr[v + 1] < row_ptr[v]) return c->fail(LLAMA_EINVAL, "set_dags: row_ptr decreasing");
+    const int32_t n_edges = row_ptr[n_ops];
+    if (n_edges > 0 && !col) return c->fail(LLAMA_EINVAL, "set_dags: null col");
+    std::vector<int32_t> owner(n_ops);
+    for (int32_t d = 0; d < n_dags; ++d)
+        for (int32_t v = dag_op_off[d]; v < dag_op_off[d + 1]; ++v) owner[v] = d;
+    std::vector<int32_t> indeg(n_ops, 0);
+    for (int32_t v = 0; v < n_ops; ++v)
+        for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+            const int32_t w = col[e];
+            if (w < 0 || w >= n_ops || owner[w] != owner[v])
+                return c->fail(LLAMA_EINVAL, "set_dags: edge leaves its DAG or is out of range");
+            if (w == v) return c->fail(LLAMA_EINVAL, "set_dags: self-loop");
+            ++indeg[w];
+        }
+    // Kahn order, then height above the sinks in reverse order
+    std::vector<int32_t> order;
+    order.reserve(n_ops);
+    for (int32_t v = 0; v < n_ops; ++v)
+        if (indeg[v] == 0) order.push_back(v);
+    for (size_t h = 0; h < order.size(); ++h) {
+        const int32_t v = order[h];
+        for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e)
+            if (--indeg[col[e]] == 0) order.push_back(col[e]);
+    }
+    if ((int32_t)order.size() != n_ops) return c->fail(LLAMA_EINVAL, "set_dags: the graph has a cycle");
+    std::vector<int32_t> height(n_ops, 0);
+    for (int32_t k = n_ops - 1; k >= 0; --k) {
+        const int32_t v = order[k];
+        int32_t hv = 0;
+        for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) hv = std::max(hv, height[col[e]] + 1);
+        height[v] = hv;
+    }
+    std::vector<int32_t> topo(n_ops), lvl_off, dag_lvl(n_dags + 1);
+    for (int32_t d = 0; d < n_dags; ++d) {
+        const int32_t lo = dag_op_off[d], hi = dag_op_off[d + 1];
+        for (int32_t v = lo; v < hi; ++v) topo[v] = v;
+        std::stable_sort(topo.begin() + lo, topo.begin() + hi,
+                         [&](int32_t a, int32_t b) { return height[a] < height[b]; });
+        dag_lvl[d] = (int32_t)lvl_off.size();
+        for (int32_t p = lo; p < hi; ++p)
+            if (p == lo || height[topo[p]] != height[topo[p - 1]]) lvl_off.push_back(p);
+    }
+    dag_lvl[n_dags] = (int32_t)lvl_off.size();
+    lvl_off.push_back(n_ops);
+
+    DeviceGuard g(c->opts.device);
+    c->dags_set = false;
+    auto up = [&](DevBuf &b, const void *h, size_t bytes) -> cudaError_t {
+        cudaError_t e = b.alloc(bytes);
+        if (e != cudaSuccess || bytes == 0) return e;
+        return cudaMemcpy(b.p, h, bytes, cudaMemcpyHostToDevice);
+    };
+    cudaError_t e;
+    if ((e = up(c->dag_op_off, dag_op_off, 4 * (size_t)(n_dags + 1))) != cudaSuccess ||
+        (e = up(c->row_ptr, row_ptr, 4 * (size_t)(n_ops + 1))) != cudaSuccess ||
+        (e = up(c->col, col, 4 * (size_t)n_edges)) != cudaSuccess ||
+        (e = up(c->slo, slo_us, 8 * (size_t)n_dags)) != cudaSuccess ||
+        (e = up(c->topo, topo.data(), 4 * (size_t)n_ops)) != cudaSuccess ||
+        (e = up(c->lvl_off, lvl_off.data(), 4 * lvl_off.size())) != cudaSuccess ||
+        (e = up(c->dag_lvl, dag_lvl.data(), 4 * dag_lvl.size())) != cudaSuccess)
+        return c->cuda_fail(e, "set_dags upload");
+    c->n_dags = n_dags;
+    c->n_ops_dag = n_ops;
+    c->dags_set = true;
+    return LLAMA_OK;
+}
+
+extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cfg_off,
+                                  const int32_t *hw_off, const int32_t *lat_us,
+                                  const int64_t *cost_nd, const int32_t *ref_cfg,
+                                  const int32_t *batch, const int32_t *res,
+                                  const int32_t *res_total) {
+    if (!c) return LLAMA_EINVAL;
+    const int H = c->opts.n_hw;
+    const bool alpha = c->opts.mode == LLAMA_MODE_ALPHA;
+    if (n_ops < 1 || !cfg_off || !hw_off || !lat_us || !cost_nd || !ref_cfg)
+        return c->fail(LLAMA_EINVAL, "set_profiles: need n_ops >= 1 and non-null arrays");
+    if (alpha && (!batch || !res || !res_total))
+        return c->fail(LLAMA_EINVAL, "set_profiles: alpha mode needs batch, res and res_total");
+    if (cfg_off[0] != 0) return c->fail(LLAMA_EINVAL, "set_profiles: cfg_off[0] must be 0");
+    std::vector<int64_t> pad_off(n_ops + 1);
+    std::vector<int32_t> seg_pad((size_t)n_ops * (H + 1));
+    int32_t max_n = 0, max_npad = 0;
+    pad_off[0] = 0;
+    for (int32_t v = 0; v < n_ops; ++v) {
+        const int64_t n = cfg_off[v + 1] - cfg_off[v];
+        if (n < 1 || n > LLAMA_MAX_CFG)
+            return c->fail(LLAMA_EINVAL, "set_profiles: configurations per op must be 1..8192");
+        const int32_t *hw = hw_off + (size_t)v * (H + 1);
+        if (hw[0] != 0 || hw[H] != n) return c->fail(LLAMA_EINVAL, "set_profiles: bad hw_off bounds");
+        int32_t *sp = seg_pad.data() + (size_t)v * (H + 1);
+        sp[0] = 0;
+        for (int h = 0; h < H; ++h) {
+            if (hw[h + 1] < hw[h]) return c->fail(LLAMA_EINVAL, "set_profiles: hw_off decreasing");
+            sp[h + 1] = sp[h] + (int32_t)round_up(hw[h + 1] - hw[h], kVec);
+        }
+        if (ref_cfg[v] < 0 || ref_cfg[v] >= n)
+            return c->fail(LLAMA_EINVAL, "set_profiles: ref_cfg out of range");
+        pad_off[v + 1] = pad_off[v] + sp[H];
+        max_n = std::max<int32_t>(max_n, (int32_t)n);
+        max_npad = std::max<int32_t>(max_npad, sp[H]);
+    }
+    const int64_t n_cfg = cfg_off[n_ops];
+    for (int64_t x = 0; x < n_cfg; ++x) {
+        if (lat_us[x] < 1 || lat_us[x] > INT32_MAX - 1)
+            return c->fail(LLAMA_EINVAL, "set_profiles: latency out of 1..INT32_MAX-1");
+        if (cost_nd[x] < 0) return c->fail(LLAMA_EINVAL, "set_profiles: negative cost");
+        if (alpha && (batch[x] < 1 || batch[x] > LLAMA_MAX_ALPHA || res[x] < 1 || res[x] > LLAMA_MAX_ALPHA))
+            return c->fail(LLAMA_EINVAL, "set_profiles: batch or res out of 1..65535");
+    }
+    if (alpha)
+        for (int h = 0; h < H; ++h)
+            if (res_total[h] < 1) return c->fail(LLAMA_EINVAL, "set_profiles: res_total must be >= 1");
+
+    DeviceGuard g(c->opts.device);
+    c->prof_set = false;
+    const int64_t n_pad = pad_off[n_ops];
+    auto up = [&](DevBuf &b, const void *h, size_t bytes) -> cudaError_t {
+        cudaError_t e = b.alloc(bytes);
+        if (e != cudaSuccess) return e;
+        return cudaMemcpy(b.p, h, bytes, cudaMemcpyHostToDevice);
+    };
+    cudaError_t e;
+    if ((e = up(c->cfg_off, cfg_off, 8 * (size_t)(n_ops + 1))) != cudaSuccess ||
+        (e = up(c->hw_off, hw_off, 4 * (size_t)n_ops * (H + 1))) != cudaSuccess ||
+        (e = up(c->lat, lat_us, 4 * (size_t)n_cfg)) != cudaSuccess ||
+        (e = up(c->cost, cost_nd, 8 * (size_t)n_cfg)) != cudaSuccess ||
+        (e = up(c->ref_cfg, ref_cfg, 4 * (size_t)n_ops)) != cudaSuccess ||
+        (e = up(c->pad_off, pad_off.data(), 8 * (size_t)(n_ops + 1))) != cudaSuccess ||
+        (e = up(c->seg_pad, seg_pad.data(), 4 * seg_pad.size())) != cudaSuccess ||
+        (e = c->lat_pad.alloc(4 * (size_t)n_pad)) != cudaSuccess ||
+        (e = c->rf.alloc(2 * (size_t)n_pad)) != cudaSuccess ||
+        (e = c->inv.alloc(2 * 2 * (size_t)n_cfg)) != cudaSuccess ||
+        (e = c->fast.alloc(4 * (size_t)n_ops)) != cudaSuccess ||
+        (e = c->ref.alloc(8 * (size_t)n_ops)) != cudaSuccess ||
+        (e = c->cp.alloc(8 * (size_t)n_ops)) != cudaSuccess)
+        return c->cuda_fail(e, "set_profiles upload");
+    if (alpha) {
+        if ((e = up(c->batch, batch, 4 * (size_t)n_cfg)) != cudaSuccess ||
+            (e = up(c->res, res, 4 * (size_t)n_cfg)) != cudaSuccess ||
+            (e = up(c->res_total, res_total, 4 * (size_t)H)) != cudaSuccess ||
+            (e = c->df.alloc(2 * (size_t)n_pad)) != cudaSuccess)
+            return c->cuda_fail(e, "set_profiles upload");
+    } else {
+        c->batch.release();
+        c->res.release();
+        c->res_total.release();
+        c->df.release();
+    }
+    c->n_ops = n_ops;
+    c->n_cfg = n_cfg;
+    c->n_pad = n_pad;
+    c->max_npad = max_npad;
+
+    const DevProblem P = make_problem(c);
+    k_encode_pad<<<n_ops, 256, 0, c->stream>>>(P, c->lat_pad.as<int32_t>(), c->rf.as<uint16_t>(),
+                                               alpha ? c->df.as<uint16_t>() : nullptr,
+                                               c->fast.as<int32_t>());
+    int32_t sort_cap = 1;
+    while (sort_cap < (alpha ? 2 * max_n : max_n)) sort_cap <<= 1;
+    const size_t sort_smem = (size_t)sort_cap * 12;
+    if (sort_smem > (size_t)c->max_smem_optin)
+        return c->fail(LLAMA_EINVAL, "set_profiles: configuration space too large for one CTA sort");
+    LL_CUDA(c, cudaFuncSetAttribute(k_encode_rank, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sort_smem));
+    k_encode_rank<<<n_ops, 1024, sort_smem, c->stream>>>(P, sort_cap, c->rf.as<uint16_t>(),
+                                                        alpha ? c->df.as<uint16_t>() : nullptr,
+                                                        c->inv.as<uint16_t>());
+    LL_CUDA(c, cudaGetLastError());
+    LL_CUDA(c, cudaStreamSynchronize(c->stream));
+
+    const size_t smem = score_smem_bytes(c);
+    if (smem > (size_t)c->max_smem_optin)
+        return c->fail(LLAMA_EINVAL, "set_profiles: table too large for shared memory");
+    auto fn = alpha ? (const void *)k_score_alpha : (const void *)k_score_cost_first;
+    LL_CUDA(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int nb = 0;
+    LL_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kScoreThreads, smem));
+    c->score_blocks_per_sm = std::max(1, nb);
+    c->prof_set = true;
+    return LLAMA_OK;
+}
+
+extern "C" int llama_set_queue(llama_ctx *c, const int64_t *q_us) {
+    if (!c) return LLAMA_EINVAL;
+    if (!q_us) return c->fail(LLAMA_EINVAL, "set_queue: null q_us");
+    for (int h = 0; h < c->opts.n_hw; ++h)
+        if (q_us[h] < 0 || q_us[h] > INT32_MAX) return c->fail(LLAMA_EINVAL, "set_queue: q out of 0..INT32_MAX");
+    for (int h = 0; h < c->opts.n_hw; ++h) c->q[h] = q_us[h];
+    return LLAMA_OK;
+}
+
+extern "C" int llama_reserve(llama_ctx *c, int64_t max_inv) {
+    if (!c) return LLAMA_EINVAL;
+    if (max_inv < 0 || max_inv > LLAMA_MAX_INV) return c->fail(LLAMA_EINVAL, "reserve: out of range");
+    int rc = check_ready(c);
+    if (rc) return rc;
+    DeviceGuard g(c->opts.device);
+    return ensure_scratch(c, max_inv);
+}
+
+extern "C" int llama_schedule_async(llama_ctx *c, int64_t n_inv, const int32_t *dag,
+                                    const int32_t *op_local, const int64_t *start_us, int64_t now_us,
+                                    llama_decision *out, void *stream) {
+    if (!c) return LLAMA_EINVAL;
+    int rc = check_inv_args(c, n_inv, dag, op_local, start_us, out);
+    if (rc) return rc;
+    if ((rc = check_ready(c))) return rc;
+    if (n_inv == 0) return LLAMA_OK;
+    DeviceGuard g(c->opts.device);
+    if ((rc = ensure_scratch(c, n_inv))) return rc;
+    return launch_schedule(c, n_inv, dag, op_local, start_us, now_us, out, (cudaStream_t)stream);
+}
+
+extern "C" int llama_schedule(llama_ctx *c, int64_t n_inv, const int32_t *dag, const int32_t *op_local,
+                              const int64_t *start_us, int64_t now_us, llama_decision *out) {
+    if (!c) return LLAMA_EINVAL;
+    int rc = check_inv_args(c, n_inv, dag, op_local, start_us, out);
+    if (rc) return rc;
+    if ((rc = check_ready(c))) return rc;
+    if (n_inv == 0) return LLAMA_OK;
+    DeviceGuard g(c->opts.device);
+    if ((rc = ensure_scratch(c, n_inv))) return rc;
+    const bool dd = is_device_ptr(dag), od = is_device_ptr(op_local), sd = is_device_ptr(start_us),
+               outd = is_device_ptr(out);
+    if (!(dd && od && sd && outd) && (rc = ensure_stage(c, n_inv))) return rc;
+    cudaStream_t s = c->stream;
+    const int32_t *d_dag = dd ? dag : c->s_dag.as<int32_t>();
+    const int32_t *d_opl = od ? op_local : c->s_opl.as<int32_t>();
+    const int64_t *d_start = sd ? start_us : c->s_start.as<int64_t>();
+    llama_decision *d_out = outd ? out : c->s_out.as<llama_decision>();
+    if (!dd) LL_CUDA(c, cudaMemcpyAsync((void *)d_dag, dag, 4 * n_inv, cudaMemcpyHostToDevice, s));
+    if (!od) LL_CUDA(c, cudaMemcpyAsync((void *)d_opl, op_local, 4 * n_inv, cudaMemcpyHostToDevice, s));
+    if (!sd) LL_CUDA(c, cudaMemcpyAsync((void *)d_start, start_us, 8 * n_inv, cudaMemcpyHostToDevice, s));
+    if ((rc = launch_schedule(c, n_inv, d_dag, d_opl, d_start, now_us, d_out, s))) return rc;
+    if (!outd) LL_CUDA(c, cudaMemcpyAsync(out, d_out, sizeof(llama_decision) * n_inv, cudaMemcpyDeviceToHost, s));
+    LL_CUDA(c, cudaMemcpyAsync(c->h_invalid, c->n_invalid.p, sizeof(unsigned long long),
+                               cudaMemcpyDeviceToHost, s));
+    LL_CUDA(c, cudaStreamSynchronize(s));
+    if (*c->h_invalid) return c->fail(LLAMA_EINVAL, "schedule: some invocations are invalid (flagged in out)");
+    return LLAMA_OK;
+}
+
+extern "C" int llama_critical_path(llama_ctx *c, int64_t *cp_us) {
+    if (!c) return LLAMA_EINVAL;
+    if (!cp_us) return c->fail(LLAMA_EINVAL, "critical_path: null output");
+    int rc = check_ready(c);
+    if (rc) return rc;
+    DeviceGuard g(c->opts.device);
+    const DevProblem P = make_problem(c);
+    k_critical_path<<<c->n_dags, 64, 0, c->stream>>>(P, c->topo.as<int32_t>(), c->lvl_off.as<int32_t>(),
+                                                     c->dag_lvl.as<int32_t>());
+    LL_CUDA(c, cudaGetLastError());
+    LL_CUDA(c, cudaMemcpyAsync(cp_us, c->cp.p, 8 * (size_t)c->n_ops, cudaMemcpyDeviceToHost, c->stream));
+    LL_CUDA(c, cudaStreamSynchronize(c->stream));
+    return LLAMA_OK;
+}
+
+extern "C" int llama_slack(llama_ctx *c, int64_t n_inv, const int32_t *dag, const int32_t *op_local,
+                           const int64_t *start_us, int64_t now_us, int32_t *slack_us) {
+    if (!c) return LLAMA_EINVAL;
+    int rc = check_inv_args(c, n_inv, dag, op_local, start_us, slack_us);
+    if (rc) return rc;
+    if ((rc = check_ready(c))) return rc;
+    if (n_inv == 0) return LLAMA_OK;
+    DeviceGuard g(c->opts.device);
+    const int H = c->opts.n_hw;
+    const bool dd = is_device_ptr(dag), od = is_device_ptr(op_local), sd = is_device_ptr(start_us),
+               outd = is_device_ptr(slack_us);
+    if (!(dd && od && sd && outd) && (rc = ensure_stage(c, n_inv))) return rc;
+    cudaStream_t s = c->stream;
+    const int32_t *d_dag = dd ? dag : c->s_dag.as<int32_t>();
+    const int32_t *d_opl = od ? op_local : c->s_opl.as<int32_t>();
+    const int64_t *d_start = sd ? start_us : c->s_start.as<int64_t>();
+    int32_t *d_out = outd ? slack_us : c->s_slack.as<int32_t>();
+    if (!dd) LL_CUDA(c, cudaMemcpyAsync((void *)d_dag, dag, 4 * n_inv, cudaMemcpyHostToDevice, s));
+    if (!od) LL_CUDA(c, cudaMemcpyAsync((void *)d_opl, op_local, 4 * n_inv, cudaMemcpyHostToDevice, s));
+    if (!sd) LL_CUDA(c, cudaMemcpyAsync((void *)d_start, start_us, 8 * n_inv, cudaMemcpyHostToDevice, s));
+    const DevProblem P = make_problem(c);
+    k_critical_path<<<c->n_dags, 64, 0, s>>>(P, c->topo.as<int32_t>(), c->lvl_off.as<int32_t>(),
+                                             c->dag_lvl.as<int32_t>());
+    k_slack<<<grid_for(c, n_inv, 256), 256, 0, s>>>(P, n_inv, d_dag, d_opl, d_start, now_us, d_out);
+    LL_CUDA(c, cudaGetLastError());
+    if (!outd) LL_CUDA(c, cudaMemcpyAsync(slack_us, d_out, 4 * n_inv * H, cudaMemcpyDeviceToHost, s));
+    LL_CUDA(c, cudaStreamSynchronize(s));
+    return LLAMA_OK;
+}

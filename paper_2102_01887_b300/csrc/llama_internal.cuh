@@ -1,0 +1,91 @@
+// llama_internal.cuh -- device-side data layout and kernel entry points of
+// the scheduling step (Section 4.1 Algorithm 1, Section 4.2 Eq. 1).
+//
+// Layout in HBM (all library-owned, written by llama_set_*):
+//   DAGs      dag_op_off[n_dags+1], row_ptr[n_ops+1], col[n_edges], slo[n_dags],
+//             topo[n_ops] (ops of each DAG ordered by height above the sinks),
+//             lvl_off[n_levels+1] (ranges of topo per height), dag_lvl[n_dags+1].
+//   Profiles  cfg_off[n_ops+1] int64, hw_off[n_ops*(H+1)], lat[n_cfg] int32,
+//             cost[n_cfg] int64, ref_cfg[n_ops] (+ batch, res, res_total).
+//   Scan encoding (built on the device by the encode kernels):
+//             pad_off[n_ops+1] int64   start of op v in the padded space, a multiple of 8;
+//             seg_pad[n_ops*(H+1)]     op-local padded start of each backend segment,
+//                                      every segment padded to a multiple of 8 entries;
+//             lat_pad[n_pad] int32     L(x) at its padded position, INT32_MAX at pads;
+//             rf[n_pad] u16            rank of x's feasible-branch objective;
+//             df[n_pad] u16            rf ^ rank of x's infeasible-branch objective (ALPHA);
+//             inv[2*n_cfg] u16         rank -> op-local index (op base 2*cfg_off[v]);
+//             fast[n_ops]              argmin (L, index), the cost-first fallback.
+//   Per call: ref[n_ops], cp[n_ops] int64; bucketing scratch (see llama_ctx).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/llama.h"
+
+namespace llama {
+
+constexpr int kVec = 8;            // configurations per 128-bit rank vector
+constexpr uint16_t kPadRank = 0xFFFF;
+constexpr int kScoreThreads = 256;
+
+struct DevProblem {
+    int32_t n_dags, n_ops, n_hw, mode;
+    const int32_t *dag_op_off, *row_ptr, *col;
+    const int64_t *slo;
+    const int64_t *cfg_off;
+    const int32_t *hw_off;
+    const int32_t *lat;
+    const int64_t *cost;
+    const int32_t *ref_cfg;
+    const int32_t *batch, *res, *res_total;
+    const int64_t *pad_off;
+    const int32_t *seg_pad;
+    const int32_t *lat_pad;
+    const uint16_t *rf, *df, *inv;
+    const int32_t *fast;
+    int32_t max_npad;  // largest padded op table (entries)
+    int64_t *ref;
+    int64_t *cp;
+    int64_t q[LLAMA_MAX_HW];
+    int64_t alpha_num, alpha_den;
+};
+
+struct BucketScratch {
+    int32_t *cnt;       // [n_ops]   invocations per op (zeroed before each call)
+    int32_t *op_start;  // [n_ops+1] exclusive prefix of cnt
+    int64_t *wprefix;   // [n_ops+1] exclusive prefix of cnt * padded table size (scores)
+    int32_t *gop;       // [n_inv]   global op of each invocation, -1 if invalid
+    int32_t *slot;      // [n_inv]   rank of the invocation inside its op's bucket
+    int32_t *b_inv;     // [n_inv]   bucketed invocation ids
+    int32_t *b_slack;   // [n_inv*H] slack per bucketed invocation and backend
+    unsigned long long *n_invalid;
+};
+
+// Slack of Algorithm 1 through the longest remaining path (Section 4.1):
+// floor(ref * R / cp), 0 once the target has passed.  ref*R < 2^62.
+__device__ __forceinline__ int32_t slack_of(int64_t ref, int64_t cp, int64_t R) {
+    if (R <= 0) return 0;
+    return (int32_t)((ref * R) / cp);
+}
+
+// Kernels (defined in kernels.cu).
+__global__ void k_critical_path(DevProblem P, const int32_t *topo, const int32_t *lvl_off,
+                                const int32_t *dag_lvl);
+__global__ void k_bucket_count(DevProblem P, int64_t n_inv, const int32_t *dag,
+                               const int32_t *op_local, const int64_t *start, int64_t now,
+                               BucketScratch S, llama_decision *out);
+__global__ void k_bucket_scan(DevProblem P, BucketScratch S);
+__global__ void k_bucket_scatter(DevProblem P, int64_t n_inv, const int32_t *dag,
+                                 const int64_t *start, int64_t now, BucketScratch S);
+__global__ void k_score_cost_first(DevProblem P, BucketScratch S, llama_decision *out);
+__global__ void k_score_alpha(DevProblem P, BucketScratch S, llama_decision *out);
+__global__ void k_slack(DevProblem P, int64_t n_inv, const int32_t *dag, const int32_t *op_local,
+                        const int64_t *start, int64_t now, int32_t *slack_out);
+__global__ void k_encode_pad(DevProblem P, int32_t *lat_pad, uint16_t *rf, uint16_t *df,
+                             int32_t *fast);
+__global__ void k_encode_rank(DevProblem P, int32_t sort_n, uint16_t *rf, uint16_t *df,
+                              uint16_t *inv);
+
+}  // namespace llama

@@ -1,0 +1,247 @@
+"""Thin Python binding of ``libllama.so`` (the C ABI in ``include/llama.h``).
+
+Argument marshalling only: every step of the scheduling path runs in the
+library's CUDA kernels.  Functions carry the C names.  Host arrays are numpy;
+device arrays are torch CUDA tensors (PyTorch supplies device memory and
+streams, nothing else).  There is no CPU fallback: loading fails loudly if
+the shared library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libllama.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ENOTREADY, ETIMEOUT = 0, -1, -2, -3, -4, -5
+MODE_COST_FIRST, MODE_ALPHA = 0, 1
+FLAG_FEASIBLE, FLAG_INVALID = 1, 2
+MAX_HW, MAX_CFG = 8, 8192
+
+DECISION_DTYPE = np.dtype([("cfg", "<i4"), ("lat", "<i4"), ("cost", "<i8"),
+                           ("slack", "<i4"), ("flags", "<i4")])
+assert DECISION_DTYPE.itemsize == 24
+
+EXPORTS = ("llama_create", "llama_destroy", "llama_set_dags", "llama_set_profiles",
+           "llama_set_queue", "llama_schedule", "llama_schedule_async", "llama_reserve",
+           "llama_critical_path", "llama_slack", "llama_set_trace_events", "llama_last_launch_count",
+           "llama_last_error")
+TRACE_EVENTS = 6
+TRACE_PHASES = ("critical_path", "bucket_count", "bucket_scan", "bucket_scatter_slack", "score")
+
+
+class LlamaError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"llama error {code}: {message}")
+        self.code = code
+
+
+class llama_opts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("n_hw", ctypes.c_int32),
+                ("alpha_num", ctypes.c_int64), ("alpha_den", ctypes.c_int64),
+                ("device", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing: build it with `python -m paper_2102_01887_b300.build`")
+        lib = ctypes.CDLL(path)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        sig = {
+            "llama_create": ([ctypes.POINTER(vp), ctypes.POINTER(llama_opts)], ctypes.c_int),
+            "llama_destroy": ([vp], None),
+            "llama_set_dags": ([vp, i32, vp, vp, vp, vp], ctypes.c_int),
+            "llama_set_profiles": ([vp, i32, vp, vp, vp, vp, vp, vp, vp, vp], ctypes.c_int),
+            "llama_set_queue": ([vp, vp], ctypes.c_int),
+            "llama_schedule": ([vp, i64, vp, vp, vp, i64, vp], ctypes.c_int),
+            "llama_schedule_async": ([vp, i64, vp, vp, vp, i64, vp, vp], ctypes.c_int),
+            "llama_reserve": ([vp, i64], ctypes.c_int),
+            "llama_critical_path": ([vp, vp], ctypes.c_int),
+            "llama_slack": ([vp, i64, vp, vp, vp, i64, vp], ctypes.c_int),
+            "llama_set_trace_events": ([vp, vp, i32], ctypes.c_int),
+            "llama_last_launch_count": ([vp], ctypes.c_int),
+            "llama_last_error": ([vp], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = lib
+        return lib
+
+
+def _ptr(a) -> Optional[int]:
+    """Address of a numpy array or torch tensor (None for None)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    assert a.is_contiguous()
+    return a.data_ptr()
+
+
+def _check(ctx, rc: int, allow=(OK,)) -> int:
+    if rc not in allow:
+        raise LlamaError(rc, llama_last_error(ctx))
+    return rc
+
+
+def llama_last_error(ctx) -> str:
+    return load().llama_last_error(ctx).decode()
+
+
+def llama_create(mode: int = MODE_COST_FIRST, n_hw: int = 3, alpha=(1, 1), device: int = 0,
+                 use_graph: bool = False) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    o = llama_opts(mode, n_hw, int(alpha[0]), int(alpha[1]), device, int(bool(use_graph)))
+    rc = load().llama_create(ctypes.byref(ctx), ctypes.byref(o))
+    if rc != OK:
+        raise LlamaError(rc, "llama_create failed")
+    return ctx
+
+
+def llama_destroy(ctx) -> None:
+    if ctx:
+        load().llama_destroy(ctx)
+
+
+def _c(a, dt):
+    return None if a is None else np.ascontiguousarray(a, dtype=dt)
+
+
+def llama_set_dags(ctx, dag_op_off, row_ptr, col, slo_us) -> None:
+    a = [_c(dag_op_off, np.int32), _c(row_ptr, np.int32), _c(col, np.int32), _c(slo_us, np.int64)]
+    if a[2].size == 0:
+        a[2] = np.zeros(1, np.int32)
+    _check(ctx, load().llama_set_dags(ctx, a[0].shape[0] - 1, *[_ptr(x) for x in a]))
+
+
+def llama_set_profiles(ctx, cfg_off, hw_off, lat_us, cost_nd, ref_cfg, batch=None, res=None,
+                       res_total=None) -> None:
+    a = [_c(cfg_off, np.int64), _c(hw_off, np.int32), _c(lat_us, np.int32), _c(cost_nd, np.int64),
+         _c(ref_cfg, np.int32), _c(batch, np.int32), _c(res, np.int32), _c(res_total, np.int32)]
+    _check(ctx, load().llama_set_profiles(ctx, a[0].shape[0] - 1, *[_ptr(x) for x in a]))
+
+
+def llama_set_queue(ctx, q_us) -> None:
+    q = _c(q_us, np.int64)
+    _check(ctx, load().llama_set_queue(ctx, _ptr(q)))
+
+
+def llama_reserve(ctx, max_inv: int) -> None:
+    _check(ctx, load().llama_reserve(ctx, int(max_inv)))
+
+
+def llama_schedule(ctx, dag, op_local, start_us, now_us: int, out=None):
+    """Blocking call.  Host (numpy) or device (torch) arrays.  Returns (out, rc) with
+    rc = OK or EINVAL (some invocations invalid, flagged in out); raises otherwise."""
+    n = int(dag.shape[0])
+    if out is None:
+        out = np.zeros(n, dtype=DECISION_DTYPE)
+    rc = load().llama_schedule(ctx, n, _ptr(dag), _ptr(op_local), _ptr(start_us), int(now_us), _ptr(out))
+    _check(ctx, rc, (OK, EINVAL) if n else (OK,))
+    if rc == EINVAL and "invalid" not in llama_last_error(ctx):
+        raise LlamaError(rc, llama_last_error(ctx))
+    return out, rc
+
+
+def llama_schedule_async(ctx, dag, op_local, start_us, now_us: int, out, stream=None) -> None:
+    """Enqueue on a torch CUDA stream (default: torch's current stream); device tensors only."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(ctx, load().llama_schedule_async(ctx, int(dag.shape[0]), _ptr(dag), _ptr(op_local),
+                                            _ptr(start_us), int(now_us), _ptr(out),
+                                            ctypes.c_void_p(stream.cuda_stream)))
+
+
+def llama_critical_path(ctx, n_ops: int) -> np.ndarray:
+    cp = np.zeros(n_ops, dtype=np.int64)
+    _check(ctx, load().llama_critical_path(ctx, _ptr(cp)))
+    return cp
+
+
+def llama_slack(ctx, dag, op_local, start_us, now_us: int, n_hw: int, out=None):
+    n = int(dag.shape[0])
+    if out is None:
+        out = np.zeros((n, n_hw), dtype=np.int32)
+    _check(ctx, load().llama_slack(ctx, n, _ptr(dag), _ptr(op_local), _ptr(start_us), int(now_us),
+                                   _ptr(out)))
+    return out
+
+
+def llama_set_trace_events(ctx, events) -> None:
+    """events: list of TRACE_EVENTS torch.cuda.Event(enable_timing=True), or [] to stop."""
+    if not events:
+        _check(ctx, load().llama_set_trace_events(ctx, None, 0))
+        return
+    for e in events:
+        if not e.cuda_event:  # torch creates the handle on first record
+            e.record()
+    arr = (ctypes.c_void_p * len(events))(*[e.cuda_event for e in events])
+    _check(ctx, load().llama_set_trace_events(ctx, arr, len(events)))
+
+
+def llama_last_launch_count(ctx) -> int:
+    return load().llama_last_launch_count(ctx)
+
+
+class Scheduler:
+    """A context loaded with one Problem (see ``workloads``)."""
+
+    def __init__(self, problem, mode: int = MODE_COST_FIRST, alpha=(1, 1), device: int = 0,
+                 use_graph: bool = False):
+        self.problem = problem
+        self.mode = mode
+        self.ctx = llama_create(mode, problem.n_hw, alpha, device, use_graph)
+        p = problem
+        llama_set_dags(self.ctx, p.dag_op_off, p.row_ptr, p.col, p.slo_us)
+        alpha_mode = mode == MODE_ALPHA
+        llama_set_profiles(self.ctx, p.cfg_off, p.hw_off, p.lat_us, p.cost_nd, p.ref_cfg,
+                           p.batch if alpha_mode else None, p.res if alpha_mode else None,
+                           p.res_total if alpha_mode else None)
+        if p.q_us is not None:
+            llama_set_queue(self.ctx, p.q_us)
+
+    def schedule(self, inv, out=None):
+        return llama_schedule(self.ctx, _c(inv.dag, np.int32), _c(inv.op_local, np.int32),
+                              _c(inv.start_us, np.int64), inv.now_us, out)
+
+    def slack(self, inv):
+        return llama_slack(self.ctx, _c(inv.dag, np.int32), _c(inv.op_local, np.int32),
+                           _c(inv.start_us, np.int64), inv.now_us, self.problem.n_hw)
+
+    def critical_path(self):
+        return llama_critical_path(self.ctx, self.problem.n_ops)
+
+    def close(self):
+        if self.ctx:
+            llama_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

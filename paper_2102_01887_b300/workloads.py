@@ -274,7 +274,7 @@ def tiny(seed: int = 0) -> tuple[Problem, Invocations]:
     return p, inv
 
 
-def medium(seed: int = 1, n_inv: int = 65_536) -> tuple[Problem, Invocations]:
+def medium(seed: int = 1, n_inv: int = 65_536, inv_seed: Optional[int] = None) -> tuple[Problem, Invocations]:
     """16 random DAGs of 10-20 ops, 1,024 configurations per op, 65,536 invocations.
 
     SLO of a DAG = U(0.5, 2) x half the sum of its operations' reference
@@ -289,7 +289,8 @@ def medium(seed: int = 1, n_inv: int = 65_536) -> tuple[Problem, Invocations]:
         return np.rint(rng.uniform(0.5, 2.0, off.shape[0] - 1) * 0.5 * sums)
 
     p = _assemble(rng, dags, np.full(n_ops, 1024), slo_fn, q_max=100_000)
-    return p, _invocations(rng, p, n_inv, 10**11)
+    inv_rng = rng if inv_seed is None else np.random.default_rng(inv_seed)
+    return p, _invocations(inv_rng, p, n_inv, 10**11)
 
 
 def _zipf_sizes(rng: np.random.Generator, n: int, s: float = 1.2) -> np.ndarray:
@@ -303,16 +304,19 @@ def _log_uniform_slo(rng: np.random.Generator):
     return slo_fn
 
 
-def batched(seed: int = 2, n_inv: int = 1_048_576, n_dags: int = 256) -> tuple[Problem, Invocations]:
+def batched(seed: int = 2, n_inv: int = 1_048_576, n_dags: int = 256,
+            inv_seed: Optional[int] = None) -> tuple[Problem, Invocations]:
     """256 DAGs of 5-60 ops, Zipf(1.2) config-space sizes 96..8,192, SLO log-uniform 0.5-60 s."""
     rng = np.random.default_rng(seed)
     dags = [_random_dag_edges(rng, int(rng.integers(5, 61))) for _ in range(n_dags)]
     n_ops = sum(len(d) for d in dags)
     p = _assemble(rng, dags, _zipf_sizes(rng, n_ops), _log_uniform_slo(rng), q_max=100_000)
-    return p, _invocations(rng, p, n_inv, 10**11)
+    inv_rng = rng if inv_seed is None else np.random.default_rng(inv_seed)
+    return p, _invocations(inv_rng, p, n_inv, 10**11)
 
 
-def batched_large(seed: int = 3, n_inv: int = 32_768, n_dags: int = 512) -> tuple[Problem, Invocations]:
+def batched_large(seed: int = 3, n_inv: int = 32_768, n_dags: int = 512,
+                  inv_seed: Optional[int] = None) -> tuple[Problem, Invocations]:
     """512 DAGs of 5-60 ops, every op with 8,192 configurations (tables >> L2).
 
     Few invocations per operation, so each table is streamed from HBM about
@@ -322,7 +326,8 @@ def batched_large(seed: int = 3, n_inv: int = 32_768, n_dags: int = 512) -> tupl
     dags = [_random_dag_edges(rng, int(rng.integers(5, 61))) for _ in range(n_dags)]
     n_ops = sum(len(d) for d in dags)
     p = _assemble(rng, dags, np.full(n_ops, 8192), _log_uniform_slo(rng), knobs=False, q_max=100_000)
-    return p, _invocations(rng, p, n_inv, 10**11)
+    inv_rng = rng if inv_seed is None else np.random.default_rng(inv_seed)
+    return p, _invocations(inv_rng, p, n_inv, 10**11)
 
 
 def random_small(seed: int, max_dags: int = 3, max_ops: int = 6, max_cfg: int = 8,

@@ -1,0 +1,265 @@
+"""CUDA path against the CPU oracle, element by element, through the C ABI.
+
+Integer work, so the bar is bit-exact on every field of every decision
+(chosen configuration, its latency, cost, slack and flags), on the critical
+path and on the slack of every backend.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2102_01887_b300 import workloads as W
+from tests.problems import load_golden, single_table_problem
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("cfg", "lat", "cost", "slack", "flags")
+
+
+@pytest.fixture(scope="module")
+def L(cuda_device):
+    from paper_2102_01887_b300 import build, llama
+    build.build()
+    llama.load()
+    return llama
+
+
+def assert_same(got, exp, what=""):
+    for k in FIELDS:
+        bad = np.flatnonzero(got[k] != exp[k])
+        assert bad.size == 0, f"{what} field {k}: {bad.size} mismatches, first at {bad[:5]}: " \
+                              f"got {got[bad[:5]]} expected {exp[bad[:5]]}"
+
+
+def run_both(L, p, inv, mode=0, alpha=(1, 1)):
+    with L.Scheduler(p, mode=mode, alpha=alpha) as s:
+        got, rc = s.schedule(inv)
+    exp, rc_o = oracle.schedule(p, inv, mode=mode, alpha=alpha)
+    assert rc == rc_o
+    return got, exp
+
+
+# ---------------------------------------------------------------- golden ---
+
+@pytest.mark.parametrize("mode", ["cost_first", "alpha"])
+def test_golden_worked_example(L, mode):
+    g, p, inv = load_golden("amber_worked_example.json")
+    m = L.MODE_ALPHA if mode == "alpha" else L.MODE_COST_FIRST
+    with L.Scheduler(p, mode=m, alpha=tuple(g["alpha"])) as s:
+        assert s.critical_path().tolist() == g["expected_critical_path"]
+        assert s.slack(inv).tolist() == g["expected_slack"]
+        d, rc = s.schedule(inv)
+    assert rc == L.OK
+    for k in FIELDS:
+        assert d[k].tolist() == g["expected_" + mode][k], k
+
+
+# --------------------------------------------------- a1, a2 in isolation ---
+
+@pytest.mark.parametrize("name", ["tiny", "medium", "batched"])
+def test_critical_path_and_slack(L, name):
+    p, inv = W.WORKLOADS[name]()
+    sub = inv.subset(np.arange(min(inv.n, 20000)))
+    with L.Scheduler(p) as s:
+        assert (s.critical_path() == oracle.critical_path(p)).all()
+        assert (s.slack(sub) == oracle.slacks(p, sub)).all()
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_slack_random_small(L, seed):
+    p, inv = W.random_small(seed)
+    with L.Scheduler(p) as s:
+        assert (s.critical_path() == oracle.critical_path(p)).all()
+        assert (s.slack(inv) == oracle.slacks(p, inv)).all()
+
+
+# ------------------------------------------------------------- full path ---
+
+@pytest.mark.parametrize("seed", range(40))
+@pytest.mark.parametrize("mode", [0, 1])
+def test_random_small(L, seed, mode):
+    p, inv = W.random_small(seed, max_cfg=24, n_inv=300)
+    got, exp = run_both(L, p, inv, mode, alpha=(1 + seed % 7, 1 + seed % 3))
+    assert_same(got, exp, f"seed {seed}")
+
+
+def test_tiny(L):
+    p, inv = W.tiny()
+    got, exp = run_both(L, p, inv)
+    assert_same(got, exp)
+
+
+def test_medium_full(L):
+    # the benchmark's workload, every invocation
+    p, inv = W.medium()
+    got, exp = run_both(L, p, inv)
+    assert_same(got, exp)
+    assert 0.5 < (got["flags"] & 1).mean() < 1.0  # both branches exercised
+
+
+def test_medium_alpha(L):
+    p, inv = W.medium()
+    sub = inv.subset(np.arange(0, inv.n, 3))
+    got, exp = run_both(L, p, sub, mode=1, alpha=(3, 2))
+    assert_same(got, exp)
+
+
+@pytest.mark.slow
+def test_batched_full(L):
+    p, inv = W.batched()
+    got, exp = run_both(L, p, inv)
+    assert_same(got, exp)
+
+
+# ------------------------------------------------------------ edge cases ---
+
+def test_empty_call(L):
+    p, inv = W.tiny()
+    with L.Scheduler(p) as s:
+        d, rc = s.schedule(inv.subset(np.arange(0)))
+    assert rc == L.OK and d.shape == (0,)
+
+
+def test_invalid_invocations_mixed_with_valid(L):
+    g, p, inv = load_golden("amber_worked_example.json")
+    bad = W.Invocations(np.asarray([0, 1, 0, 0, -1, 0], np.int32),
+                        np.asarray([1, 0, 4, 2, 0, -3], np.int32),
+                        np.asarray([9400, 9400, 9400, 10001, 0, 9400], np.int64), 10000)
+    with L.Scheduler(p) as s:
+        d, rc = s.schedule(bad)
+    exp, rc_o = oracle.schedule(p, bad)
+    assert rc == L.EINVAL == rc_o
+    assert_same(d, exp)
+    assert d["cfg"].tolist() == [5, -1, -1, -1, -1, -1]
+
+
+def test_all_targets_passed(L):
+    p, inv = W.medium()
+    late = W.Invocations(inv.dag, inv.op_local, np.zeros(inv.n, np.int64), inv.now_us)
+    got, exp = run_both(L, p, late.subset(np.arange(5000)))
+    assert_same(got, exp)
+    assert (got["flags"] == 0).all() and (got["slack"] == 0).all()
+
+
+def test_all_ties(L):
+    # identical latency and cost everywhere: the lowest index must win
+    p, inv = W.medium()
+    p.lat_us[:] = 1000
+    p.cost_nd[:] = 7
+    got, exp = run_both(L, p, inv.subset(np.arange(3000)))
+    assert_same(got, exp)
+
+
+def test_single_config_ops_and_single_backend_segments(L):
+    # ops with one configuration, ops whose configurations all sit on one backend
+    p = single_table_problem([[1, 2], [3], [3], []], [10, 20, 30, 40], slo=400,
+                             extra=[[], [(2, 5, 100), (2, 4, 100), (2, 4, 50)], [(1, 29, 1)],
+                                    [(0, 39, 2), (0, 41, 1)]])
+    rng = np.random.default_rng(5)
+    n = 500
+    inv = W.Invocations(np.zeros(n, np.int32), rng.integers(0, 4, n).astype(np.int32),
+                        (10**6 - rng.integers(0, 500, n)).astype(np.int64), 10**6)
+    for mode in (0, 1):
+        got, exp = run_both(L, p, inv, mode)
+        assert_same(got, exp)
+
+
+def test_largest_config_space_with_ties(L):
+    # 8,192 configurations per op (the limit), heavy ties, several tiles per op
+    p, inv = W.random_small(3, max_dags=1, max_ops=4, max_cfg=2, n_inv=2000, value_range=5000)
+    n = 8192
+    rng = np.random.default_rng(9)
+    k = p.n_ops
+    p.cfg_off = np.arange(0, (k + 1) * n, n, dtype=np.int64)
+    cuts = np.sort(rng.integers(0, n, size=(k, 2)), axis=1)
+    p.hw_off = np.concatenate([np.zeros((k, 1)), cuts, np.full((k, 1), n)], axis=1).astype(np.int32).ravel()
+    p.lat_us = rng.integers(1, 3000, size=k * n).astype(np.int32)
+    p.cost_nd = rng.integers(0, 50, size=k * n).astype(np.int64)
+    p.ref_cfg = rng.integers(0, n, size=k).astype(np.int32)
+    p.batch = rng.integers(1, 4, size=k * n).astype(np.int32)
+    p.res = rng.integers(1, 4, size=k * n).astype(np.int32)
+    p.slo_us[:] = 20000
+    for mode in (0, 1):
+        got, exp = run_both(L, p, inv, mode, alpha=(2, 3))
+        assert_same(got, exp)
+
+
+@pytest.mark.parametrize("n_hw", [1, 2, 8])
+def test_backend_counts(L, n_hw):
+    rng = np.random.default_rng(n_hw)
+    p, inv = W.random_small(100 + n_hw, max_cfg=40, n_inv=1000)
+    k = p.n_ops
+    sizes = np.diff(p.cfg_off)
+    hw = []
+    for n in sizes:
+        cuts = np.sort(rng.integers(0, n + 1, size=n_hw - 1))
+        hw.append(np.concatenate([[0], cuts, [n]]))
+    p.n_hw = n_hw
+    p.hw_off = np.concatenate(hw).astype(np.int32)
+    p.q_us = rng.integers(0, 20, size=n_hw).astype(np.int64)
+    p.res_total = rng.integers(1, 9, size=n_hw).astype(np.int32)
+    assert p.hw_off.shape[0] == k * (n_hw + 1)
+    for mode in (0, 1):
+        got, exp = run_both(L, p, inv, mode, alpha=(5, 2))
+        assert_same(got, exp)
+
+
+# ---------------------------------------------------- device-side calls ---
+
+def test_device_pointers_and_async_stream(L):
+    import torch
+    p, inv = W.medium()
+    exp, _ = oracle.schedule(p, inv)
+    dev = torch.device("cuda:0")
+    dag = torch.from_numpy(inv.dag).to(dev)
+    opl = torch.from_numpy(inv.op_local).to(dev)
+    st = torch.from_numpy(inv.start_us).to(dev)
+    with L.Scheduler(p) as s:
+        out = torch.zeros(inv.n * 24, dtype=torch.uint8, device=dev)
+        L.llama_schedule(s.ctx, dag, opl, st, inv.now_us, out)  # blocking, device pointers
+        got = out.cpu().numpy().view(L.DECISION_DTYPE)
+        assert_same(got, exp, "blocking device")
+        stream = torch.cuda.Stream()
+        out2 = torch.zeros_like(out)
+        L.llama_reserve(s.ctx, inv.n)
+        for _ in range(3):  # repeated calls reuse the scratch
+            L.llama_schedule_async(s.ctx, dag, opl, st, inv.now_us, out2, stream)
+        stream.synchronize()
+        assert_same(out2.cpu().numpy().view(L.DECISION_DTYPE), exp, "async")
+        assert L.llama_last_launch_count(s.ctx) >= 1
+
+
+def test_growing_and_shrinking_batches(L):
+    p, inv = W.medium()
+    exp, _ = oracle.schedule(p, inv)
+    with L.Scheduler(p) as s:
+        for n in (17, 65536, 1, 4096, 65535):
+            idx = np.arange(n)
+            got, rc = s.schedule(inv.subset(idx))
+            assert rc == L.OK
+            assert_same(got, exp[idx], f"n={n}")
+
+
+def test_errors(L):
+    p, inv = W.tiny()
+    ctx = L.llama_create(0, 3)
+    try:
+        with pytest.raises(L.LlamaError) as e:
+            L.llama_schedule(ctx, inv.dag, inv.op_local, inv.start_us, inv.now_us)
+        assert e.value.code == L.ENOTREADY
+        with pytest.raises(L.LlamaError) as e:  # cycle
+            L.llama_set_dags(ctx, [0, 2], [0, 1, 2], [1, 0], [100])
+        assert e.value.code == L.EINVAL
+        with pytest.raises(L.LlamaError):  # cross-DAG edge
+            L.llama_set_dags(ctx, [0, 1, 2], [0, 1, 1], [1], [100, 100])
+        with pytest.raises(L.LlamaError):  # latency 0
+            L.llama_set_profiles(ctx, [0, 1], [0, 1, 1, 1], [0], [1], [0])
+        with pytest.raises(L.LlamaError):  # ref_cfg out of range
+            L.llama_set_profiles(ctx, [0, 1], [0, 1, 1, 1], [5], [1], [1])
+        with pytest.raises(L.LlamaError):  # more than 8192 configurations
+            n = 8193
+            L.llama_set_profiles(ctx, [0, n], [0, n, n, n], np.ones(n), np.ones(n), [0])
+        with pytest.raises(L.LlamaError):  # negative queueing time
+            L.llama_set_queue(ctx, [0, -1, 0])
+    finally:
+        L.llama_destroy(ctx)
