@@ -140,6 +140,30 @@ int llama_schedule_async(llama_ctx *ctx, int64_t n_inv, const int32_t *dag,
                          const int32_t *op_local, const int64_t *start_us, int64_t now_us,
                          llama_decision *out, void *stream);
 
+/* Allocation-free variant of llama_schedule_async.  The paper has no
+ * counterpart: this is a deployment convenience.  Some callers cannot let a
+ * library call cudaMalloc or cudaFree while they schedule: a serving loop
+ * whose device memory is carved up front by its own allocator, a
+ * latency-bound loop that cannot take the implicit synchronisation of the
+ * CUDA allocator, or code running where the allocator must not be entered.
+ * This call allocates nothing: its bucketing scratch is one fixed, file-scope
+ * device array of about 3 MB, which every GPU that loads the library holds
+ * until the process exits.  Same arguments and results as
+ * llama_schedule_async (device pointers, enqueued on `stream`, invalid
+ * invocations flagged in `out`), with these limits: n_inv at most
+ * LLAMA_STATIC_MAX_INV and at most LLAMA_STATIC_MAX_OPS operations in the
+ * profiles; larger sizes are rejected with EINVAL before anything is
+ * launched.  The first call on a device looks up the array's device address
+ * (once per device, with that device current); make that first call before
+ * any stream capture.  Every call shares the one array and each call clears
+ * the counters it needs at zero; calls that overlap on the GPU race on the
+ * array: serialise them.  Errors: EINVAL, ENOTREADY, ECUDA. */
+#define LLAMA_STATIC_MAX_INV 65536
+#define LLAMA_STATIC_MAX_OPS 4096
+int llama_schedule_static(llama_ctx *ctx, int64_t n_inv, const int32_t *dag,
+                          const int32_t *op_local, const int64_t *start_us, int64_t now_us,
+                          llama_decision *out, void *stream);
+
 /* Pre-allocate scratch for calls of up to max_inv invocations. */
 int llama_reserve(llama_ctx *ctx, int64_t max_inv);
 

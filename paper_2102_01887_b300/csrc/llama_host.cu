@@ -255,6 +255,30 @@ int check_inv_args(llama_ctx *c, int64_t n_inv, const void *a, const void *b, co
 
 }  // namespace
 
+namespace llama {
+
+int context_view(llama_ctx *c, ContextView *v) {
+    const int rc = check_ready(c);
+    if (rc) return rc;
+    v->P = make_problem(c);
+    v->topo = c->topo.as<int32_t>();
+    v->lvl_off = c->lvl_off.as<int32_t>();
+    v->dag_lvl = c->dag_lvl.as<int32_t>();
+    v->n_dags = c->n_dags;
+    v->n_ops = c->n_ops;
+    v->n_hw = c->opts.n_hw;
+    v->mode = c->opts.mode;
+    v->device = c->opts.device;
+    v->num_sms = c->num_sms;
+    v->score_blocks_per_sm = c->score_blocks_per_sm;
+    v->score_smem = score_smem_bytes(c);
+    return LLAMA_OK;
+}
+
+int context_fail(llama_ctx *c, int code, const char *msg) { return c->fail(code, msg); }
+
+}  // namespace llama
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------

@@ -70,6 +70,17 @@ __device__ __forceinline__ int32_t slack_of(int64_t ref, int64_t cp, int64_t R) 
     return (int32_t)((ref * R) / cp);
 }
 
+// Read-only view of a ready context for launchers outside llama_host.cu
+// (defined in llama_host.cu).
+struct ContextView {
+    DevProblem P;
+    const int32_t *topo, *lvl_off, *dag_lvl;
+    int32_t n_dags, n_ops, n_hw, mode, device, num_sms, score_blocks_per_sm;
+    size_t score_smem;
+};
+int context_view(llama_ctx *c, ContextView *v);  // LLAMA_OK or the readiness error
+int context_fail(llama_ctx *c, int code, const char *msg);
+
 // Kernels (defined in kernels.cu).
 __global__ void k_critical_path(DevProblem P, const int32_t *topo, const int32_t *lvl_off,
                                 const int32_t *dag_lvl);

@@ -1,0 +1,144 @@
+// llama_static.cu -- llama_schedule_static: the scheduling call without any
+// device allocation.
+//
+// Why it exists.  llama_schedule and llama_schedule_async keep their
+// bucketing scratch in context-owned buffers that grow with cudaMalloc when
+// a call needs more room.  Some callers cannot let a library allocate at call
+// time: a serving loop whose device memory was carved up front by its own
+// allocator (an extra cudaMalloc can fail or fragment it), a latency-bound
+// loop that cannot absorb the implicit synchronisation of cudaMalloc/cudaFree,
+// or code that runs where the CUDA allocator must not be entered at all.
+// This entry point uses instead one fixed, file-scope device array: every GPU
+// that loads the library holds it (about 3 MB) until the process exits.  The
+// caller still passes inputs and outputs; the context's tables were copied to
+// the device earlier by llama_set_profiles.
+//
+// Sharing.  Every call on a device uses the same array, and the array keeps
+// the contents of the last call; the counters that must start at zero are
+// cleared by each call on its own stream.  Calls that overlap on the GPU
+// (two streams, or two contexts on one device, in flight at once) race on
+// the array and give wrong results: serialise them.
+//
+// Set-up.  The device address of the array is looked up once per device with
+// cudaGetSymbolAddress, by the first call on that device, with that device
+// current.  Make that first call before any stream capture.
+#include <mutex>
+#include <string>
+
+#include "llama_internal.cuh"
+
+using namespace llama;
+
+namespace {
+
+constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Layout of the array (offsets in bytes, each part 256-byte aligned).
+constexpr size_t kCntOff = 0;
+constexpr size_t kOpStartOff = align256(kCntOff + 4 * (size_t)(LLAMA_STATIC_MAX_OPS + 1));
+constexpr size_t kWprefixOff = align256(kOpStartOff + 4 * (size_t)(LLAMA_STATIC_MAX_OPS + 1));
+constexpr size_t kInvalidOff = align256(kWprefixOff + 8 * (size_t)(LLAMA_STATIC_MAX_OPS + 1));
+constexpr size_t kGopOff = align256(kInvalidOff + 8);
+constexpr size_t kSlotOff = align256(kGopOff + 4 * (size_t)LLAMA_STATIC_MAX_INV);
+constexpr size_t kBInvOff = align256(kSlotOff + 4 * (size_t)LLAMA_STATIC_MAX_INV);
+constexpr size_t kBSlackOff = align256(kBInvOff + 4 * (size_t)LLAMA_STATIC_MAX_INV);
+constexpr size_t kScratchBytes = align256(kBSlackOff + 4 * (size_t)LLAMA_STATIC_MAX_INV * LLAMA_MAX_HW);
+
+constexpr int kMaxDevices = 64;
+
+}  // namespace
+
+// In host code this name is only a host-side stand-in for the array; the
+// device address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
+
+namespace {
+
+std::mutex g_mu;
+void *g_scratch_addr[kMaxDevices] = {};
+
+// Device address of the array on `device`, which must be current.
+cudaError_t scratch_address(int device, void **out) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_scratch_addr[device]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_addr[device] = p;
+    }
+    *out = g_scratch_addr[device];
+    return cudaSuccess;
+}
+
+struct CurrentDevice {
+    int prev = -1;
+    explicit CurrentDevice(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~CurrentDevice() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int cuda_error(llama_ctx *c, cudaError_t e, const char *what) {
+    std::string msg = std::string("schedule_static: ") + what + ": " + cudaGetErrorString(e);
+    return context_fail(c, LLAMA_ECUDA, msg.c_str());
+}
+
+}  // namespace
+
+extern "C" int llama_schedule_static(llama_ctx *c, int64_t n_inv, const int32_t *dag,
+                                     const int32_t *op_local, const int64_t *start_us,
+                                     int64_t now_us, llama_decision *out, void *stream) {
+    if (!c) return LLAMA_EINVAL;
+    if (n_inv < 0 || n_inv > LLAMA_STATIC_MAX_INV)
+        return context_fail(c, LLAMA_EINVAL,
+                            "schedule_static: n_inv exceeds LLAMA_STATIC_MAX_INV (65536)");
+    if (n_inv > 0 && (!dag || !op_local || !start_us || !out))
+        return context_fail(c, LLAMA_EINVAL, "schedule_static: null invocation or output pointer");
+    ContextView v;
+    int rc = context_view(c, &v);
+    if (rc) return rc;
+    if (v.n_ops > LLAMA_STATIC_MAX_OPS)
+        return context_fail(c, LLAMA_EINVAL,
+                            "schedule_static: the profiles have more than LLAMA_STATIC_MAX_OPS (4096) operations");
+    if (v.device < 0 || v.device >= kMaxDevices)
+        return context_fail(c, LLAMA_EINVAL, "schedule_static: device ordinal above 63");
+    if (n_inv == 0) return LLAMA_OK;
+
+    CurrentDevice guard(v.device);
+    unsigned char *base = nullptr;
+    cudaError_t e = scratch_address(v.device, reinterpret_cast<void **>(&base));
+    if (e != cudaSuccess) return cuda_error(c, e, "cudaGetSymbolAddress");
+    BucketScratch S{};
+    S.cnt = reinterpret_cast<int32_t *>(base + kCntOff);
+    S.op_start = reinterpret_cast<int32_t *>(base + kOpStartOff);
+    S.wprefix = reinterpret_cast<int64_t *>(base + kWprefixOff);
+    S.n_invalid = reinterpret_cast<unsigned long long *>(base + kInvalidOff);
+    S.gop = reinterpret_cast<int32_t *>(base + kGopOff);
+    S.slot = reinterpret_cast<int32_t *>(base + kSlotOff);
+    S.b_inv = reinterpret_cast<int32_t *>(base + kBInvOff);
+    S.b_slack = reinterpret_cast<int32_t *>(base + kBSlackOff);
+
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // the previous call's counters are still in the array: start from zero
+    if ((e = cudaMemsetAsync(S.cnt, 0, sizeof(int32_t) * v.n_ops, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(S.n_invalid, 0, sizeof(unsigned long long), s)) != cudaSuccess)
+        return cuda_error(c, e, "cudaMemsetAsync");
+    k_critical_path<<<v.n_dags, 64, 0, s>>>(v.P, v.topo, v.lvl_off, v.dag_lvl);
+    const int64_t want = (n_inv + 255) / 256;
+    const int gi = (int)(want < (int64_t)v.num_sms * 16 ? want : (int64_t)v.num_sms * 16);
+    k_bucket_count<<<gi, 256, 0, s>>>(v.P, n_inv, dag, op_local, start_us, now_us, S, out);
+    k_bucket_scan<<<1, 1024, 0, s>>>(v.P, S);
+    k_bucket_scatter<<<gi, 256, 0, s>>>(v.P, n_inv, dag, start_us, now_us, S);
+    const int grid = v.num_sms * v.score_blocks_per_sm;
+    if (v.mode == LLAMA_MODE_ALPHA)
+        k_score_alpha<<<grid, kScoreThreads, v.score_smem, s>>>(v.P, S, out);
+    else
+        k_score_cost_first<<<grid, kScoreThreads, v.score_smem, s>>>(v.P, S, out);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(c, e, "kernel launch");
+    return LLAMA_OK;
+}

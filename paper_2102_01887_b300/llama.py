@@ -28,7 +28,8 @@ DECISION_DTYPE = np.dtype([("cfg", "<i4"), ("lat", "<i4"), ("cost", "<i8"),
 assert DECISION_DTYPE.itemsize == 24
 
 EXPORTS = ("llama_create", "llama_destroy", "llama_set_dags", "llama_set_profiles",
-           "llama_set_queue", "llama_schedule", "llama_schedule_async", "llama_reserve",
+           "llama_set_queue", "llama_schedule", "llama_schedule_async", "llama_schedule_static",
+           "llama_reserve",
            "llama_critical_path", "llama_slack", "llama_set_trace_events", "llama_last_launch_count",
            "llama_last_error")
 TRACE_EVENTS = 6
@@ -69,6 +70,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "llama_set_queue": ([vp, vp], ctypes.c_int),
             "llama_schedule": ([vp, i64, vp, vp, vp, i64, vp], ctypes.c_int),
             "llama_schedule_async": ([vp, i64, vp, vp, vp, i64, vp, vp], ctypes.c_int),
+            "llama_schedule_static": ([vp, i64, vp, vp, vp, i64, vp, vp], ctypes.c_int),
             "llama_reserve": ([vp, i64], ctypes.c_int),
             "llama_critical_path": ([vp, vp], ctypes.c_int),
             "llama_slack": ([vp, i64, vp, vp, vp, i64, vp], ctypes.c_int),
@@ -168,6 +170,22 @@ def llama_schedule_async(ctx, dag, op_local, start_us, now_us: int, out, stream=
     _check(ctx, load().llama_schedule_async(ctx, int(dag.shape[0]), _ptr(dag), _ptr(op_local),
                                             _ptr(start_us), int(now_us), _ptr(out),
                                             ctypes.c_void_p(stream.cuda_stream)))
+
+
+STATIC_MAX_INV, STATIC_MAX_OPS = 65536, 4096
+
+
+def llama_schedule_static(ctx, dag, op_local, start_us, now_us: int, out, stream=None) -> None:
+    """Allocation-free scheduling call (device tensors, enqueued on a torch CUDA stream):
+    the library allocates nothing during it; its scratch is one fixed device array, so
+    calls must not overlap on the GPU.  At most STATIC_MAX_INV invocations and
+    STATIC_MAX_OPS operations."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(ctx, load().llama_schedule_static(ctx, int(dag.shape[0]), _ptr(dag), _ptr(op_local),
+                                             _ptr(start_us), int(now_us), _ptr(out),
+                                             ctypes.c_void_p(stream.cuda_stream)))
 
 
 def llama_critical_path(ctx, n_ops: int) -> np.ndarray:
