@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="launch kernels directly, no CUDA graph")
     return ap.parse_args()
 
 
@@ -69,7 +70,7 @@ def workload_config(name, p, inv, mode, scores):
             "configs_per_op": (int(np.diff(p.cfg_off).min()), int(np.diff(p.cfg_off).max())),
             "invocations": inv.n, "backends": p.n_hw, "objective": mode,
             "scores_per_step": int(scores), "table_bytes": p.table_bytes(),
-            "l2": "flushed before every timed step (256 MiB write)"}
+            "l2": "flushed before every timed step (256 MiB write)", "cuda_graph": True}
 
 
 def scores_of(p, inv) -> int:
@@ -196,7 +197,7 @@ def main():
     B.build()
     p, inv = make_workload(args.workload, rank)
     mode = L.MODE_ALPHA if args.mode == "alpha" else L.MODE_COST_FIRST
-    sched = L.Scheduler(p, mode=mode, alpha=(3, 2), device=local)
+    sched = L.Scheduler(p, mode=mode, alpha=(3, 2), device=local, use_graph=not args.no_graph)
     ctx = sched.ctx
     scores = scores_of(p, inv)
 

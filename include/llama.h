@@ -147,7 +147,7 @@ int llama_schedule_async(llama_ctx *ctx, int64_t n_inv, const int32_t *dag,
  * latency-bound loop that cannot take the implicit synchronisation of the
  * CUDA allocator, or code running where the allocator must not be entered.
  * This call allocates nothing: its bucketing scratch is one fixed, file-scope
- * device array of about 3 MB, which every GPU that loads the library holds
+ * device array of about 4.5 MB, which every GPU that loads the library holds
  * until the process exits.  Same arguments and results as
  * llama_schedule_async (device pointers, enqueued on `stream`, invalid
  * invocations flagged in `out`), with these limits: n_inv at most
@@ -180,11 +180,12 @@ int llama_slack(llama_ctx *ctx, int64_t n_inv, const int32_t *dag, const int32_t
 
 /* Tracing.  events[0..LLAMA_TRACE_EVENTS-1] are caller-owned cudaEvent_t
  * handles; once set, every scheduling call records them on its stream at
- * the phase boundaries: [0] call start, [1] after the critical path, [2]
- * after counting, [3] after the prefix scan, [4] after the scatter (slack),
- * [5] after scoring.  n_events = 0 turns tracing off.  The events must stay
- * valid while tracing is on.  Errors: EINVAL. */
-#define LLAMA_TRACE_EVENTS 6
+ * the phase boundaries: [0] call start, [1] after the prepare kernel
+ * (critical path, counting per operation, bucket layout), [2] after the
+ * scatter kernel (slack, bucketing), [3] after the scoring kernel.
+ * n_events = 0 turns tracing off.  The events must stay valid while tracing
+ * is on.  Errors: EINVAL. */
+#define LLAMA_TRACE_EVENTS 4
 int llama_set_trace_events(llama_ctx *ctx, void *const *events, int32_t n_events);
 
 /* Kernel launches issued by the last scheduling call (for accounting). */

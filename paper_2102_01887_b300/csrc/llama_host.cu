@@ -58,6 +58,7 @@ struct llama_ctx {
     llama_opts opts{};
     int num_sms = 0;
     int max_smem_optin = 0;
+    int64_t l2_bytes = 0;
     cudaStream_t stream = nullptr;
     std::string err = "no error";
 
@@ -71,24 +72,49 @@ struct llama_ctx {
     int32_t n_ops = 0, max_npad = 0;
     int64_t n_cfg = 0, n_pad = 0;
     DevBuf cfg_off, hw_off, lat, cost, ref_cfg, batch, res, res_total;
-    DevBuf pad_off, seg_pad, lat_pad, rf, df, inv, fast;
+    DevBuf pad_off, seg_pad, lat_lo, lat_hi, rf, df, inv, fast, op_order;
+    int64_t mean_npad = 0;
     DevBuf ref, cp;
     int64_t q[LLAMA_MAX_HW] = {0};
 
     // bucketing scratch
-    int64_t cap_inv = 0;
+    int64_t cap_inv = 0, cap_tiles = 0;
     int32_t cap_ops = 0;
-    DevBuf cnt, op_start, wprefix, gop, slot, b_inv, b_slack, n_invalid;
+    DevBuf cnt, ctrl, op_start, gop, slot, b_inv, b_slack, tiles;
+    // scoring kernel geometry (set by llama_set_profiles)
+    int32_t min_vpl = 16, score_grid = 0, score_chunk = 0;
+    size_t score_smem = 0;
 
     // staging for host-memory arguments of the blocking calls
     int64_t cap_stage = 0;
     DevBuf s_dag, s_opl, s_start, s_out, s_slack;
-    unsigned long long *h_invalid = nullptr;  // pinned
+    unsigned long long *h_ctrl = nullptr;  // pinned copy of the control words
 
-    int score_blocks_per_sm = 0;
     int last_launches = 0;
     cudaEvent_t trace[LLAMA_TRACE_EVENTS] = {};
     bool tracing = false;
+
+    // CUDA graph of the last scheduling call (opts.use_graph): replayed while
+    // the call's arguments and the context's buffers stay the same; `now` is
+    // patched into the two kernels that take it, trace events are swapped.
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraphNode_t g_prepare = nullptr, g_scatter = nullptr;
+    cudaGraphNode_t g_events[LLAMA_TRACE_EVENTS] = {};
+    int64_t g_n_inv = -1, g_now = 0;
+    const void *g_args[4] = {};
+    bool g_traced = false;
+
+    void drop_graph() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (graph) cudaGraphDestroy(graph);
+        gexec = nullptr;
+        graph = nullptr;
+        g_prepare = g_scatter = nullptr;
+        for (auto &e : g_events) e = nullptr;
+        g_n_inv = -1;
+    }
 
     int fail(int code, const std::string &msg) {
         err = msg;
@@ -128,12 +154,18 @@ DevProblem make_problem(const llama_ctx *c) {
     P.res_total = c->res_total.as<int32_t>();
     P.pad_off = c->pad_off.as<int64_t>();
     P.seg_pad = c->seg_pad.as<int32_t>();
-    P.lat_pad = c->lat_pad.as<int32_t>();
+    P.lat_lo = c->lat_lo.as<int32_t>();
+    P.lat_hi = c->lat_hi.as<int32_t>();
     P.rf = c->rf.as<uint16_t>();
     P.df = c->df.as<uint16_t>();
     P.inv = c->inv.as<uint16_t>();
     P.fast = c->fast.as<int32_t>();
+    P.op_order = c->op_order.as<int32_t>();
     P.max_npad = c->max_npad;
+    // prefetch the encoded tables into L2 when they take at most half of it
+    const int64_t tbl_bytes = (int64_t)(c->opts.mode == LLAMA_MODE_ALPHA ? 8 : 6) * c->n_pad;
+    const bool pf = c->n_pad > 0 && tbl_bytes <= c->l2_bytes / 2;
+    P.prefetch_lines = pf ? (2 * c->n_pad + 127) / 128 : 0;
     P.ref = c->ref.as<int64_t>();
     P.cp = c->cp.as<int64_t>();
     for (int h = 0; h < LLAMA_MAX_HW; ++h) P.q[h] = c->q[h];
@@ -145,19 +177,33 @@ DevProblem make_problem(const llama_ctx *c) {
 BucketScratch make_scratch(const llama_ctx *c) {
     BucketScratch S{};
     S.cnt = c->cnt.as<int32_t>();
+    S.ctrl = c->ctrl.as<unsigned long long>();
     S.op_start = c->op_start.as<int32_t>();
-    S.wprefix = c->wprefix.as<int64_t>();
     S.gop = c->gop.as<int32_t>();
     S.slot = c->slot.as<int32_t>();
     S.b_inv = c->b_inv.as<int32_t>();
     S.b_slack = c->b_slack.as<int32_t>();
-    S.n_invalid = c->n_invalid.as<unsigned long long>();
+    S.tiles = c->tiles.as<int4>();
     return S;
 }
 
-size_t score_smem_bytes(const llama_ctx *c) {
-    const size_t per = 4 + 2 + (c->opts.mode == LLAMA_MODE_ALPHA ? 2 : 0);
-    return per * (size_t)c->max_npad;
+ContextView view_of(const llama_ctx *c) {
+    ContextView v{};
+    v.P = make_problem(c);
+    v.topo = c->topo.as<int32_t>();
+    v.lvl_off = c->lvl_off.as<int32_t>();
+    v.dag_lvl = c->dag_lvl.as<int32_t>();
+    v.n_dags = c->n_dags;
+    v.n_ops = c->n_ops;
+    v.n_hw = c->opts.n_hw;
+    v.mode = c->opts.mode;
+    v.device = c->opts.device;
+    v.num_sms = c->num_sms;
+    v.min_vpl = c->min_vpl;
+    v.score_grid = c->score_grid;
+    v.score_chunk = c->score_chunk;
+    v.score_smem = c->score_smem;
+    return v;
 }
 
 int check_ready(llama_ctx *c) {
@@ -170,13 +216,14 @@ int check_ready(llama_ctx *c) {
 
 int ensure_scratch(llama_ctx *c, int64_t n_inv) {
     const int H = c->opts.n_hw;
+    if (c->cap_ops < c->n_ops + 1 || c->cap_inv < n_inv) c->drop_graph();  // buffers move
     if (c->cap_ops < c->n_ops + 1) {
         const int32_t n = c->n_ops + 1;
-        LL_CUDA(c, c->cnt.alloc(sizeof(int32_t) * n));
+        LL_CUDA(c, c->cnt.alloc(sizeof(int32_t) * kCntStride * n));
+        LL_CUDA(c, c->ctrl.alloc(sizeof(unsigned long long) * kCtrlWords));
         LL_CUDA(c, c->op_start.alloc(sizeof(int32_t) * n));
-        LL_CUDA(c, c->wprefix.alloc(sizeof(int64_t) * n));
-        LL_CUDA(c, c->n_invalid.alloc(sizeof(unsigned long long)));
         c->cap_ops = n;
+        c->cap_tiles = 0;
     }
     if (c->cap_inv < n_inv) {
         const int64_t n = std::max<int64_t>(n_inv, 1024);
@@ -185,6 +232,12 @@ int ensure_scratch(llama_ctx *c, int64_t n_inv) {
         LL_CUDA(c, c->b_inv.alloc(sizeof(int32_t) * n));
         LL_CUDA(c, c->b_slack.alloc(sizeof(int32_t) * n * H));
         c->cap_inv = n;
+        c->cap_tiles = 0;
+    }
+    const int64_t nt = max_tiles(c->cap_inv, c->n_ops);
+    if (c->cap_tiles < nt) {
+        LL_CUDA(c, c->tiles.alloc(sizeof(int4) * nt));
+        c->cap_tiles = nt;
     }
     return LLAMA_OK;
 }
@@ -216,33 +269,95 @@ int grid_for(const llama_ctx *c, int64_t n, int threads) {
 }
 
 // The launch sequence of one scheduling call (all device pointers).
+// Replace argument `index` of a captured kernel node by *value (same type).
+template <class T>
+cudaError_t patch_arg(cudaGraphExec_t exec, cudaGraphNode_t node, int n_args, int index, const T *value) {
+    cudaKernelNodeParams p{};
+    cudaError_t e = cudaGraphKernelNodeGetParams(node, &p);
+    if (e != cudaSuccess) return e;
+    if (!p.kernelParams || n_args > 16) return cudaErrorInvalidValue;
+    void *args[16];
+    for (int k = 0; k < n_args; ++k) args[k] = p.kernelParams[k];
+    args[index] = const_cast<T *>(value);
+    p.kernelParams = args;
+    return cudaGraphExecKernelNodeSetParams(exec, node, &p);
+}
+
+int capture_graph(llama_ctx *c, int64_t n_inv, const int32_t *dag, const int32_t *op_local,
+                  const int64_t *start, int64_t now, llama_decision *out) {
+    c->drop_graph();
+    const ContextView v = view_of(c);
+    const BucketScratch S = make_scratch(c);
+    const cudaEvent_t *tr = c->tracing ? c->trace : nullptr;
+    LL_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const cudaError_t e = enqueue_schedule(v, S, n_inv, dag, op_local, start, now, out, c->cap_stream, tr);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return c->cuda_fail(e, "capture enqueue_schedule");
+    }
+    LL_CUDA(c, e2);
+    c->graph = g;
+    LL_CUDA(c, cudaGraphInstantiate(&c->gexec, g, 0));
+    size_t n = 0;
+    LL_CUDA(c, cudaGraphGetNodes(g, nullptr, &n));
+    std::vector<cudaGraphNode_t> nodes(n);
+    LL_CUDA(c, cudaGraphGetNodes(g, nodes.data(), &n));
+    for (cudaGraphNode_t node : nodes) {
+        cudaGraphNodeType t;
+        LL_CUDA(c, cudaGraphNodeGetType(node, &t));
+        if (t == cudaGraphNodeTypeKernel) {
+            cudaKernelNodeParams p{};
+            LL_CUDA(c, cudaGraphKernelNodeGetParams(node, &p));
+            if (p.func == (void *)k_prepare) c->g_prepare = node;
+            if (p.func == (void *)k_scatter) c->g_scatter = node;
+        } else if (t == cudaGraphNodeTypeEventRecord && tr) {
+            cudaEvent_t ev;
+            LL_CUDA(c, cudaGraphEventRecordNodeGetEvent(node, &ev));
+            for (int k = 0; k < LLAMA_TRACE_EVENTS; ++k)
+                if (ev == tr[k]) c->g_events[k] = node;
+        }
+    }
+    if (!c->g_prepare || !c->g_scatter) return c->fail(LLAMA_ECUDA, "graph capture: kernel nodes not found");
+    c->g_n_inv = n_inv;
+    c->g_now = now;
+    c->g_args[0] = dag;
+    c->g_args[1] = op_local;
+    c->g_args[2] = start;
+    c->g_args[3] = out;
+    c->g_traced = tr != nullptr;
+    return LLAMA_OK;
+}
+
 int launch_schedule(llama_ctx *c, int64_t n_inv, const int32_t *dag, const int32_t *op_local,
                     const int64_t *start, int64_t now, llama_decision *out, cudaStream_t s) {
-    const DevProblem P = make_problem(c);
-    const BucketScratch S = make_scratch(c);
-    auto mark = [&](int k) { if (c->tracing) cudaEventRecord(c->trace[k], s); };
-    mark(0);
-    LL_CUDA(c, cudaMemsetAsync(S.cnt, 0, sizeof(int32_t) * c->n_ops, s));
-    LL_CUDA(c, cudaMemsetAsync(S.n_invalid, 0, sizeof(unsigned long long), s));
-    k_critical_path<<<c->n_dags, 64, 0, s>>>(P, c->topo.as<int32_t>(), c->lvl_off.as<int32_t>(),
-                                             c->dag_lvl.as<int32_t>());
-    mark(1);
-    const int gi = grid_for(c, n_inv, 256);
-    k_bucket_count<<<gi, 256, 0, s>>>(P, n_inv, dag, op_local, start, now, S, out);
-    mark(2);
-    k_bucket_scan<<<1, 1024, 0, s>>>(P, S);
-    mark(3);
-    k_bucket_scatter<<<gi, 256, 0, s>>>(P, n_inv, dag, start, now, S);
-    mark(4);
-    const int grid = c->num_sms * c->score_blocks_per_sm;
-    const size_t smem = score_smem_bytes(c);
-    if (c->opts.mode == LLAMA_MODE_ALPHA)
-        k_score_alpha<<<grid, kScoreThreads, smem, s>>>(P, S, out);
-    else
-        k_score_cost_first<<<grid, kScoreThreads, smem, s>>>(P, S, out);
-    mark(5);
-    LL_CUDA(c, cudaGetLastError());
-    c->last_launches = 5;
+    if (!c->opts.use_graph) {
+        const ContextView v = view_of(c);
+        const BucketScratch S = make_scratch(c);
+        LL_CUDA(c, enqueue_schedule(v, S, n_inv, dag, op_local, start, now, out, s,
+                                    c->tracing ? c->trace : nullptr));
+        c->last_launches = 3;
+        return LLAMA_OK;
+    }
+    const bool same = c->gexec && c->g_n_inv == n_inv && c->g_args[0] == dag &&
+                      c->g_args[1] == op_local && c->g_args[2] == start && c->g_args[3] == out &&
+                      c->g_traced == c->tracing;
+    if (!same) {
+        const int rc = capture_graph(c, n_inv, dag, op_local, start, now, out);
+        if (rc) return rc;
+    }
+    if (now != c->g_now) {
+        // `now` is argument 5 of k_prepare's 12 and argument 4 of k_scatter's 6
+        LL_CUDA(c, patch_arg(c->gexec, c->g_prepare, 12, 5, &now));
+        LL_CUDA(c, patch_arg(c->gexec, c->g_scatter, 6, 4, &now));
+        c->g_now = now;
+    }
+    if (c->tracing)
+        for (int k = 0; k < LLAMA_TRACE_EVENTS; ++k)
+            if (c->g_events[k]) LL_CUDA(c, cudaGraphExecEventRecordNodeSetEvent(c->gexec, c->g_events[k], c->trace[k]));
+    LL_CUDA(c, cudaGraphLaunch(c->gexec, s));
+    c->last_launches = 3;
     return LLAMA_OK;
 }
 
@@ -260,18 +375,7 @@ namespace llama {
 int context_view(llama_ctx *c, ContextView *v) {
     const int rc = check_ready(c);
     if (rc) return rc;
-    v->P = make_problem(c);
-    v->topo = c->topo.as<int32_t>();
-    v->lvl_off = c->lvl_off.as<int32_t>();
-    v->dag_lvl = c->dag_lvl.as<int32_t>();
-    v->n_dags = c->n_dags;
-    v->n_ops = c->n_ops;
-    v->n_hw = c->opts.n_hw;
-    v->mode = c->opts.mode;
-    v->device = c->opts.device;
-    v->num_sms = c->num_sms;
-    v->score_blocks_per_sm = c->score_blocks_per_sm;
-    v->score_smem = score_smem_bytes(c);
+    *v = view_of(c);
     return LLAMA_OK;
 }
 
@@ -302,15 +406,19 @@ extern "C" int llama_create(llama_ctx **out, const llama_opts *opts) {
     if (!c) return LLAMA_ENOMEM;
     c->opts = *opts;
     DeviceGuard g(opts->device);
+    int l2 = 0;
     if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, opts->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&c->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
                                opts->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, opts->device) != cudaSuccess ||
         cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaMallocHost(&c->h_invalid, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMallocHost(&c->h_ctrl, sizeof(unsigned long long) * kCtrlWords) != cudaSuccess) {
         cudaGetLastError();
         delete c;
         return LLAMA_ECUDA;
     }
+    c->l2_bytes = l2;
     *out = c;
     return LLAMA_OK;
 }
@@ -320,8 +428,10 @@ extern "C" void llama_destroy(llama_ctx *c) {
     {
         DeviceGuard g(c->opts.device);
         if (c->stream) cudaStreamSynchronize(c->stream);
+        c->drop_graph();
         if (c->stream) cudaStreamDestroy(c->stream);
-        if (c->h_invalid) cudaFreeHost(c->h_invalid);
+        if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+        if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
         delete c;  // DevBuf destructors free device memory with the device current
     }
 }
@@ -408,6 +518,7 @@ extern "C" int llama_set_dags(llama_ctx *c, int32_t n_dags, const int32_t *dag_o
     lvl_off.push_back(n_ops);
 
     DeviceGuard g(c->opts.device);
+    c->drop_graph();
     c->dags_set = false;
     auto up = [&](DevBuf &b, const void *h, size_t bytes) -> cudaError_t {
         cudaError_t e = b.alloc(bytes);
@@ -464,6 +575,13 @@ extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cf
         max_n = std::max<int32_t>(max_n, (int32_t)n);
         max_npad = std::max<int32_t>(max_npad, sp[H]);
     }
+    // bucket order of the ops: largest padded table first (stable), so the
+    // scoring kernel's longest warps are launched first
+    std::vector<int32_t> op_order(n_ops);
+    for (int32_t v = 0; v < n_ops; ++v) op_order[v] = v;
+    std::stable_sort(op_order.begin(), op_order.end(), [&](int32_t a, int32_t b) {
+        return pad_off[a + 1] - pad_off[a] > pad_off[b + 1] - pad_off[b];
+    });
     const int64_t n_cfg = cfg_off[n_ops];
     for (int64_t x = 0; x < n_cfg; ++x) {
         if (lat_us[x] < 1 || lat_us[x] > INT32_MAX - 1)
@@ -477,6 +595,7 @@ extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cf
             if (res_total[h] < 1) return c->fail(LLAMA_EINVAL, "set_profiles: res_total must be >= 1");
 
     DeviceGuard g(c->opts.device);
+    c->drop_graph();
     c->prof_set = false;
     const int64_t n_pad = pad_off[n_ops];
     auto up = [&](DevBuf &b, const void *h, size_t bytes) -> cudaError_t {
@@ -492,7 +611,9 @@ extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cf
         (e = up(c->ref_cfg, ref_cfg, 4 * (size_t)n_ops)) != cudaSuccess ||
         (e = up(c->pad_off, pad_off.data(), 8 * (size_t)(n_ops + 1))) != cudaSuccess ||
         (e = up(c->seg_pad, seg_pad.data(), 4 * seg_pad.size())) != cudaSuccess ||
-        (e = c->lat_pad.alloc(4 * (size_t)n_pad)) != cudaSuccess ||
+        (e = up(c->op_order, op_order.data(), 4 * (size_t)n_ops)) != cudaSuccess ||
+        (e = c->lat_lo.alloc(2 * (size_t)n_pad)) != cudaSuccess ||
+        (e = c->lat_hi.alloc(2 * (size_t)n_pad)) != cudaSuccess ||
         (e = c->rf.alloc(2 * (size_t)n_pad)) != cudaSuccess ||
         (e = c->inv.alloc(2 * 2 * (size_t)n_cfg)) != cudaSuccess ||
         (e = c->fast.alloc(4 * (size_t)n_ops)) != cudaSuccess ||
@@ -515,9 +636,10 @@ extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cf
     c->n_cfg = n_cfg;
     c->n_pad = n_pad;
     c->max_npad = max_npad;
+    c->cap_ops = 0;  // op count may have changed: re-size the per-op scratch
 
     const DevProblem P = make_problem(c);
-    k_encode_pad<<<n_ops, 256, 0, c->stream>>>(P, c->lat_pad.as<int32_t>(), c->rf.as<uint16_t>(),
+    k_encode_pad<<<n_ops, 256, 0, c->stream>>>(P, c->lat_lo.as<int32_t>(), c->lat_hi.as<int32_t>(), c->rf.as<uint16_t>(),
                                                alpha ? c->df.as<uint16_t>() : nullptr,
                                                c->fast.as<int32_t>());
     int32_t sort_cap = 1;
@@ -533,14 +655,15 @@ extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cf
     LL_CUDA(c, cudaGetLastError());
     LL_CUDA(c, cudaStreamSynchronize(c->stream));
 
-    const size_t smem = score_smem_bytes(c);
-    if (smem > (size_t)c->max_smem_optin)
-        return c->fail(LLAMA_EINVAL, "set_profiles: table too large for shared memory");
+    // scoring kernel: stage tables in chunks of at most kMaxChunk entries, one
+    // persistent CTA per resident slot
+    c->score_chunk = std::min<int32_t>(max_npad, kMaxChunk);
+    c->score_smem = (size_t)c->score_chunk * (alpha ? 8 : 6);
     auto fn = alpha ? (const void *)k_score_alpha : (const void *)k_score_cost_first;
-    LL_CUDA(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LL_CUDA(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->score_smem));
     int nb = 0;
-    LL_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kScoreThreads, smem));
-    c->score_blocks_per_sm = std::max(1, nb);
+    LL_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kScoreThreads, c->score_smem));
+    c->score_grid = c->num_sms * std::max(1, nb);
     c->prof_set = true;
     return LLAMA_OK;
 }
@@ -551,6 +674,7 @@ extern "C" int llama_set_queue(llama_ctx *c, const int64_t *q_us) {
     for (int h = 0; h < c->opts.n_hw; ++h)
         if (q_us[h] < 0 || q_us[h] > INT32_MAX) return c->fail(LLAMA_EINVAL, "set_queue: q out of 0..INT32_MAX");
     for (int h = 0; h < c->opts.n_hw; ++h) c->q[h] = q_us[h];
+    c->drop_graph();  // the queueing times are kernel arguments
     return LLAMA_OK;
 }
 
@@ -598,10 +722,13 @@ extern "C" int llama_schedule(llama_ctx *c, int64_t n_inv, const int32_t *dag, c
     if (!sd) LL_CUDA(c, cudaMemcpyAsync((void *)d_start, start_us, 8 * n_inv, cudaMemcpyHostToDevice, s));
     if ((rc = launch_schedule(c, n_inv, d_dag, d_opl, d_start, now_us, d_out, s))) return rc;
     if (!outd) LL_CUDA(c, cudaMemcpyAsync(out, d_out, sizeof(llama_decision) * n_inv, cudaMemcpyDeviceToHost, s));
-    LL_CUDA(c, cudaMemcpyAsync(c->h_invalid, c->n_invalid.p, sizeof(unsigned long long),
+    LL_CUDA(c, cudaMemcpyAsync(c->h_ctrl, c->ctrl.p, sizeof(unsigned long long) * kCtrlWords,
                                cudaMemcpyDeviceToHost, s));
     LL_CUDA(c, cudaStreamSynchronize(s));
-    if (*c->h_invalid) return c->fail(LLAMA_EINVAL, "schedule: some invocations are invalid (flagged in out)");
+    if (c->h_ctrl[kCtrlTimeout])
+        return c->fail(LLAMA_ETIMEOUT, "schedule: a bounded device wait gave up (table staging)");
+    if (c->h_ctrl[kCtrlInvalid])
+        return c->fail(LLAMA_EINVAL, "schedule: some invocations are invalid (flagged in out)");
     return LLAMA_OK;
 }
 

@@ -11,7 +11,9 @@
 //             pad_off[n_ops+1] int64   start of op v in the padded space, a multiple of 8;
 //             seg_pad[n_ops*(H+1)]     op-local padded start of each backend segment,
 //                                      every segment padded to a multiple of 8 entries;
-//             lat_pad[n_pad] int32     L(x) at its padded position, INT32_MAX at pads;
+//             lat_lo, lat_hi [n_pad/2] int32  L(x) at its padded position, INT32_MAX at
+//                                      pads, split in two planes: entries 0-3 of each
+//                                      8-entry vector in lat_lo, entries 4-7 in lat_hi;
 //             rf[n_pad] u16            rank of x's feasible-branch objective;
 //             df[n_pad] u16            rf ^ rank of x's infeasible-branch objective (ALPHA);
 //             inv[2*n_cfg] u16         rank -> op-local index (op base 2*cfg_off[v]);
@@ -29,6 +31,20 @@ namespace llama {
 constexpr int kVec = 8;            // configurations per 128-bit rank vector
 constexpr uint16_t kPadRank = 0xFFFF;
 constexpr int kScoreThreads = 256;
+constexpr int kScoreThreadsLog2 = 8;
+constexpr int kMaxChunk = 4096;        // table entries staged at a time by the scoring kernel
+constexpr int kMaxWaitTries = 1 << 20; // bounded mbarrier waits
+constexpr int kCntStride = 32;     // int32 slots between per-op counters: one 128-byte line each
+// control words of a call (unsigned long long each)
+constexpr int kCtrlInvalid = 0;    // invalid invocations
+constexpr int kCtrlTicket = 1;     // blocks of k_prepare that have finished
+constexpr int kCtrlPositions = 2;  // bucket positions laid out
+constexpr int kCtrlTiles = 3;      // scoring tiles laid out
+constexpr int kCtrlTimeout = 4;    // nonzero: a bounded device wait gave up
+constexpr int kCtrlWords = 8;
+// DAGs up to this size are staged in shared memory for the critical path
+constexpr int kCpSmemOps = 512;
+constexpr int kCpSmemEdges = 2048;
 
 struct DevProblem {
     int32_t n_dags, n_ops, n_hw, mode;
@@ -42,10 +58,14 @@ struct DevProblem {
     const int32_t *batch, *res, *res_total;
     const int64_t *pad_off;
     const int32_t *seg_pad;
-    const int32_t *lat_pad;
+    const int32_t *lat_lo, *lat_hi;
     const uint16_t *rf, *df, *inv;
     const int32_t *fast;
+    const int32_t *op_order;  // ops by padded table size, largest first (bucket order)
     int32_t max_npad;  // largest padded op table (entries)
+    // 128-byte lines of each of lat_lo, lat_hi, rf (and df), all 2*n_pad bytes long,
+    // to pull into L2 before scoring (0: off)
+    int64_t prefetch_lines;
     int64_t *ref;
     int64_t *cp;
     int64_t q[LLAMA_MAX_HW];
@@ -53,14 +73,14 @@ struct DevProblem {
 };
 
 struct BucketScratch {
-    int32_t *cnt;       // [n_ops]   invocations per op (zeroed before each call)
-    int32_t *op_start;  // [n_ops+1] exclusive prefix of cnt
-    int64_t *wprefix;   // [n_ops+1] exclusive prefix of cnt * padded table size (scores)
-    int32_t *gop;       // [n_inv]   global op of each invocation, -1 if invalid
-    int32_t *slot;      // [n_inv]   rank of the invocation inside its op's bucket
-    int32_t *b_inv;     // [n_inv]   bucketed invocation ids
-    int32_t *b_slack;   // [n_inv*H] slack per bucketed invocation and backend
-    unsigned long long *n_invalid;
+    int32_t *cnt;             // [n_ops*kCntStride] invocations per op (zeroed before each call)
+    unsigned long long *ctrl; // [kCtrlWords] control words (zeroed before each call)
+    int32_t *op_start;        // [n_ops]     first bucket position of each op
+    int32_t *gop;             // [n_inv]     global op of each invocation, -1 if invalid
+    int32_t *slot;            // [n_inv]     rank of the invocation inside its op's bucket
+    int32_t *b_inv;           // [n_inv]     invocation at each bucket position
+    int32_t *b_slack;         // [n_inv*H]   slack per invocation and backend
+    int4 *tiles;              // [max_tiles] scoring tiles {op, j0, m, lanes_log2}
 };
 
 // Slack of Algorithm 1 through the longest remaining path (Section 4.1):
@@ -75,8 +95,11 @@ __device__ __forceinline__ int32_t slack_of(int64_t ref, int64_t cp, int64_t R) 
 struct ContextView {
     DevProblem P;
     const int32_t *topo, *lvl_off, *dag_lvl;
-    int32_t n_dags, n_ops, n_hw, mode, device, num_sms, score_blocks_per_sm;
-    size_t score_smem;
+    int32_t n_dags, n_ops, n_hw, mode, device, num_sms;
+    int32_t min_vpl;      // vectors a lane should scan at least (sets lanes per invocation)
+    int32_t score_grid;   // persistent CTAs of the scoring kernel
+    int32_t score_chunk;  // table entries staged per chunk
+    size_t score_smem;    // dynamic shared memory of the scoring kernel
 };
 int context_view(llama_ctx *c, ContextView *v);  // LLAMA_OK or the readiness error
 int context_fail(llama_ctx *c, int code, const char *msg);
@@ -84,18 +107,28 @@ int context_fail(llama_ctx *c, int code, const char *msg);
 // Kernels (defined in kernels.cu).
 __global__ void k_critical_path(DevProblem P, const int32_t *topo, const int32_t *lvl_off,
                                 const int32_t *dag_lvl);
-__global__ void k_bucket_count(DevProblem P, int64_t n_inv, const int32_t *dag,
-                               const int32_t *op_local, const int64_t *start, int64_t now,
-                               BucketScratch S, llama_decision *out);
-__global__ void k_bucket_scan(DevProblem P, BucketScratch S);
-__global__ void k_bucket_scatter(DevProblem P, int64_t n_inv, const int32_t *dag,
-                                 const int64_t *start, int64_t now, BucketScratch S);
-__global__ void k_score_cost_first(DevProblem P, BucketScratch S, llama_decision *out);
-__global__ void k_score_alpha(DevProblem P, BucketScratch S, llama_decision *out);
+__global__ void k_prepare(DevProblem P, int64_t n_inv, const int32_t *dag, const int32_t *op_local,
+                          const int64_t *start, int64_t now, BucketScratch S, llama_decision *out,
+                          const int32_t *topo, const int32_t *lvl_off, const int32_t *dag_lvl,
+                          int32_t min_vpl);
+__global__ void k_scatter(DevProblem P, int64_t n_inv, const int32_t *dag, const int64_t *start,
+                          int64_t now, BucketScratch S);
+__global__ void k_score_cost_first(DevProblem P, BucketScratch S, llama_decision *out, int32_t chunk);
+__global__ void k_score_alpha(DevProblem P, BucketScratch S, llama_decision *out, int32_t chunk);
+
+// Scoring tiles a call may lay out (each op: full tiles plus one tail).
+int64_t max_tiles(int64_t n_inv, int32_t n_ops);
+// Enqueue the whole scheduling call on stream s: counters cleared, then
+// k_prepare, k_scatter, k_score.  trace (nullable) = LLAMA_TRACE_EVENTS events
+// recorded at the phase boundaries.
+cudaError_t enqueue_schedule(const ContextView &v, const BucketScratch &S, int64_t n_inv,
+                             const int32_t *dag, const int32_t *op_local, const int64_t *start,
+                             int64_t now, llama_decision *out, cudaStream_t s,
+                             const cudaEvent_t *trace);
 __global__ void k_slack(DevProblem P, int64_t n_inv, const int32_t *dag, const int32_t *op_local,
                         const int64_t *start, int64_t now, int32_t *slack_out);
-__global__ void k_encode_pad(DevProblem P, int32_t *lat_pad, uint16_t *rf, uint16_t *df,
-                             int32_t *fast);
+__global__ void k_encode_pad(DevProblem P, int32_t *lat_lo, int32_t *lat_hi, uint16_t *rf,
+                             uint16_t *df, int32_t *fast);
 __global__ void k_encode_rank(DevProblem P, int32_t sort_n, uint16_t *rf, uint16_t *df,
                               uint16_t *inv);
 

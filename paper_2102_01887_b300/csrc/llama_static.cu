@@ -9,7 +9,7 @@
 // loop that cannot absorb the implicit synchronisation of cudaMalloc/cudaFree,
 // or code that runs where the CUDA allocator must not be entered at all.
 // This entry point uses instead one fixed, file-scope device array: every GPU
-// that loads the library holds it (about 3 MB) until the process exits.  The
+// that loads the library holds it (about 4.5 MB) until the process exits.  The
 // caller still passes inputs and outputs; the context's tables were copied to
 // the device earlier by llama_set_profiles.
 //
@@ -34,15 +34,16 @@ namespace {
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Layout of the array (offsets in bytes, each part 256-byte aligned).
+constexpr size_t kMaxTiles = (size_t)LLAMA_STATIC_MAX_INV + (size_t)LLAMA_STATIC_MAX_OPS;
 constexpr size_t kCntOff = 0;
-constexpr size_t kOpStartOff = align256(kCntOff + 4 * (size_t)(LLAMA_STATIC_MAX_OPS + 1));
-constexpr size_t kWprefixOff = align256(kOpStartOff + 4 * (size_t)(LLAMA_STATIC_MAX_OPS + 1));
-constexpr size_t kInvalidOff = align256(kWprefixOff + 8 * (size_t)(LLAMA_STATIC_MAX_OPS + 1));
-constexpr size_t kGopOff = align256(kInvalidOff + 8);
+constexpr size_t kCtrlOff = align256(kCntOff + 4 * (size_t)kCntStride * LLAMA_STATIC_MAX_OPS);
+constexpr size_t kOpStartOff = align256(kCtrlOff + 8 * (size_t)kCtrlWords);
+constexpr size_t kGopOff = align256(kOpStartOff + 4 * (size_t)(LLAMA_STATIC_MAX_OPS + 1));
 constexpr size_t kSlotOff = align256(kGopOff + 4 * (size_t)LLAMA_STATIC_MAX_INV);
 constexpr size_t kBInvOff = align256(kSlotOff + 4 * (size_t)LLAMA_STATIC_MAX_INV);
 constexpr size_t kBSlackOff = align256(kBInvOff + 4 * (size_t)LLAMA_STATIC_MAX_INV);
-constexpr size_t kScratchBytes = align256(kBSlackOff + 4 * (size_t)LLAMA_STATIC_MAX_INV * LLAMA_MAX_HW);
+constexpr size_t kTilesOff = align256(kBSlackOff + 4 * (size_t)LLAMA_STATIC_MAX_INV * LLAMA_MAX_HW);
+constexpr size_t kScratchBytes = align256(kTilesOff + 16 * kMaxTiles);
 
 constexpr int kMaxDevices = 64;
 
@@ -115,30 +116,18 @@ extern "C" int llama_schedule_static(llama_ctx *c, int64_t n_inv, const int32_t 
     if (e != cudaSuccess) return cuda_error(c, e, "cudaGetSymbolAddress");
     BucketScratch S{};
     S.cnt = reinterpret_cast<int32_t *>(base + kCntOff);
+    S.ctrl = reinterpret_cast<unsigned long long *>(base + kCtrlOff);
     S.op_start = reinterpret_cast<int32_t *>(base + kOpStartOff);
-    S.wprefix = reinterpret_cast<int64_t *>(base + kWprefixOff);
-    S.n_invalid = reinterpret_cast<unsigned long long *>(base + kInvalidOff);
     S.gop = reinterpret_cast<int32_t *>(base + kGopOff);
     S.slot = reinterpret_cast<int32_t *>(base + kSlotOff);
     S.b_inv = reinterpret_cast<int32_t *>(base + kBInvOff);
     S.b_slack = reinterpret_cast<int32_t *>(base + kBSlackOff);
+    S.tiles = reinterpret_cast<int4 *>(base + kTilesOff);
 
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // the previous call's counters are still in the array: start from zero
-    if ((e = cudaMemsetAsync(S.cnt, 0, sizeof(int32_t) * v.n_ops, s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(S.n_invalid, 0, sizeof(unsigned long long), s)) != cudaSuccess)
-        return cuda_error(c, e, "cudaMemsetAsync");
-    k_critical_path<<<v.n_dags, 64, 0, s>>>(v.P, v.topo, v.lvl_off, v.dag_lvl);
-    const int64_t want = (n_inv + 255) / 256;
-    const int gi = (int)(want < (int64_t)v.num_sms * 16 ? want : (int64_t)v.num_sms * 16);
-    k_bucket_count<<<gi, 256, 0, s>>>(v.P, n_inv, dag, op_local, start_us, now_us, S, out);
-    k_bucket_scan<<<1, 1024, 0, s>>>(v.P, S);
-    k_bucket_scatter<<<gi, 256, 0, s>>>(v.P, n_inv, dag, start_us, now_us, S);
-    const int grid = v.num_sms * v.score_blocks_per_sm;
-    if (v.mode == LLAMA_MODE_ALPHA)
-        k_score_alpha<<<grid, kScoreThreads, v.score_smem, s>>>(v.P, S, out);
-    else
-        k_score_cost_first<<<grid, kScoreThreads, v.score_smem, s>>>(v.P, S, out);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(c, e, "kernel launch");
+    // the previous call's counters are still in the array: enqueue_schedule
+    // clears them on this call's stream before anything reads them
+    e = enqueue_schedule(v, S, n_inv, dag, op_local, start_us, now_us, out,
+                         static_cast<cudaStream_t>(stream), nullptr);
+    if (e != cudaSuccess) return cuda_error(c, e, "enqueue");
     return LLAMA_OK;
 }

@@ -32,8 +32,8 @@ EXPORTS = ("llama_create", "llama_destroy", "llama_set_dags", "llama_set_profile
            "llama_reserve",
            "llama_critical_path", "llama_slack", "llama_set_trace_events", "llama_last_launch_count",
            "llama_last_error")
-TRACE_EVENTS = 6
-TRACE_PHASES = ("critical_path", "bucket_count", "bucket_scan", "bucket_scatter_slack", "score")
+TRACE_EVENTS = 4
+TRACE_PHASES = ("prepare", "scatter_slack", "score")
 
 
 class LlamaError(RuntimeError):

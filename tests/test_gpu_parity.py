@@ -263,3 +263,37 @@ def test_errors(L):
             L.llama_set_queue(ctx, [0, -1, 0])
     finally:
         L.llama_destroy(ctx)
+
+
+# ----------------------------------------------------------- graph replay ---
+
+def test_graph_replay_tracks_now_sizes_and_contents(L):
+    # one context in graph mode: the call is captured once per argument set and
+    # replayed; `now` is patched per call; staging buffers keep host calls on one graph
+    import torch
+    p, inv = W.medium()
+    with L.Scheduler(p, use_graph=True) as s:
+        for k, n in enumerate((65536, 65536, 4096, 4096, 65536)):
+            shift = 1000 * k  # later `now`, same elapsed time as before plus the shift
+            case = W.Invocations(inv.dag[:n], inv.op_local[:n], inv.start_us[:n], inv.now_us + shift)
+            got, rc = s.schedule(case)
+            exp, rc_o = oracle.schedule(p, case)
+            assert rc == rc_o == L.OK
+            assert_same(got, exp, f"call {k}")
+        # traced replay on device pointers: events recorded inside the graph
+        dev = torch.device("cuda:0")
+        dag = torch.from_numpy(inv.dag).to(dev)
+        opl = torch.from_numpy(inv.op_local).to(dev)
+        st = torch.from_numpy(inv.start_us).to(dev)
+        out = torch.zeros(inv.n * 24, dtype=torch.uint8, device=dev)
+        stream = torch.cuda.Stream()
+        exp, _ = oracle.schedule(p, inv)
+        for rep in range(3):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(L.TRACE_EVENTS)]
+            with torch.cuda.stream(stream):
+                L.llama_set_trace_events(s.ctx, ev)
+                L.llama_schedule_async(s.ctx, dag, opl, st, inv.now_us, out, stream)
+            stream.synchronize()
+            assert all(ev[j].elapsed_time(ev[j + 1]) >= 0 for j in range(L.TRACE_EVENTS - 1))
+            assert_same(out.cpu().numpy().view(L.DECISION_DTYPE), exp, f"traced {rep}")
+        L.llama_set_trace_events(s.ctx, [])
