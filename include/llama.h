@@ -147,7 +147,7 @@ int llama_schedule_async(llama_ctx *ctx, int64_t n_inv, const int32_t *dag,
  * latency-bound loop that cannot take the implicit synchronisation of the
  * CUDA allocator, or code running where the allocator must not be entered.
  * This call allocates nothing: its bucketing scratch is one fixed, file-scope
- * device array of about 4.5 MB, which every GPU that loads the library holds
+ * device array of about 5 MB, which every GPU that loads the library holds
  * until the process exits.  Same arguments and results as
  * llama_schedule_async (device pointers, enqueued on `stream`, invalid
  * invocations flagged in `out`), with these limits: n_inv at most
@@ -163,6 +163,20 @@ int llama_schedule_async(llama_ctx *ctx, int64_t n_inv, const int32_t *dag,
 int llama_schedule_static(llama_ctx *ctx, int64_t n_inv, const int32_t *dag,
                           const int32_t *op_local, const int64_t *start_us, int64_t now_us,
                           llama_decision *out, void *stream);
+
+/* Launch schedule of the scoring kernel (no counterpart in the paper; a
+ * B300 schedule that changes speed, never results):
+ *   lanes_min_vectors  each of the lanes sharing one invocation scans at least
+ *                      this many 8-configuration vectors, 1..1024 (default 16);
+ *   inv_per_thread     invocations a thread scores together against each staged
+ *                      vector: 1, 2 or 4 (default 2);
+ *   chunk_entries      table entries staged in shared memory at a time: a
+ *                      multiple of 8 in 8..LLAMA_MAX_CFG, or 0 for the default
+ *                      (the largest table, at most 4096).
+ * Call after llama_set_profiles (which resets the chunk to its default).
+ * Errors: EINVAL, ENOTREADY (no profiles), ECUDA. */
+int llama_set_tuning(llama_ctx *ctx, int32_t lanes_min_vectors, int32_t inv_per_thread,
+                     int32_t chunk_entries);
 
 /* Pre-allocate scratch for calls of up to max_inv invocations. */
 int llama_reserve(llama_ctx *ctx, int64_t max_inv);
@@ -180,12 +194,13 @@ int llama_slack(llama_ctx *ctx, int64_t n_inv, const int32_t *dag, const int32_t
 
 /* Tracing.  events[0..LLAMA_TRACE_EVENTS-1] are caller-owned cudaEvent_t
  * handles; once set, every scheduling call records them on its stream at
- * the phase boundaries: [0] call start, [1] after the prepare kernel
- * (critical path, counting per operation, bucket layout), [2] after the
- * scatter kernel (slack, bucketing), [3] after the scoring kernel.
- * n_events = 0 turns tracing off.  The events must stay valid while tracing
- * is on.  Errors: EINVAL. */
-#define LLAMA_TRACE_EVENTS 4
+ * the phase boundaries: [0] call start, [1] after the bucketing kernel
+ * (critical path, counting per operation, bucket layout, slack), [2] after
+ * the scoring kernel.  Traced calls launch their kernels directly (no CUDA
+ * graph) and the scoring kernel no longer overlaps the end of the bucketing
+ * kernel.  n_events = 0 turns tracing off.  The events must stay valid while
+ * tracing is on.  Errors: EINVAL. */
+#define LLAMA_TRACE_EVENTS 3
 int llama_set_trace_events(llama_ctx *ctx, void *const *events, int32_t n_events);
 
 /* Kernel launches issued by the last scheduling call (for accounting). */

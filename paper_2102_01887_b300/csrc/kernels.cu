@@ -1,11 +1,11 @@
 // kernels.cu -- sm_103a kernels of the scheduling step.
 //
-//   k_prepare   critical path per op (Alg. 1's RemainingPathLatency maximised over
-//               paths; one CTA per DAG, level-synchronous from the sinks upwards),
-//               validation and per-op counts of the invocations, and the bucket
-//               layout (last CTA).
-//   k_scatter   bucket the invocations by operation and compute their slack per
-//               backend (Algorithm 1 through the critical path).
+//   k_bucket    one cooperative launch: critical path per op (Alg. 1's
+//               RemainingPathLatency maximised over paths; one CTA per DAG,
+//               level-synchronous from the sinks upwards), validation and per-op
+//               counts of the invocations, bucket and tile layout; grid barrier;
+//               then the invocations are placed in their op's bucket and their
+//               slack per backend computed (Algorithm 1 through the critical path).
 //   k_score     Eq. 1 over every configuration of each invocation's operation and
 //               the argmin, on the rank-encoded tables.
 //   k_encode_*  build the rank encoding of the tables (once per llama_set_profiles).
@@ -104,6 +104,7 @@ __device__ void critical_path_of_dag(const DevProblem &P, int d, const int32_t *
         for (int k = threadIdx.x; k < n; k += blockDim.x) {
             P.ref[lo + k] = sm.ref[k];
             P.cp[lo + k] = sm.cp[k];
+            P.cp_magic[lo + k] = ~0ull / (uint64_t)sm.cp[k];
         }
         return;
     }
@@ -119,6 +120,7 @@ __device__ void critical_path_of_dag(const DevProblem &P, int d, const int32_t *
         }
         __syncthreads();
     }
+    for (int v = lo + (int)threadIdx.x; v < hi; v += blockDim.x) P.cp_magic[v] = ~0ull / (uint64_t)P.cp[v];
 }
 
 __global__ void k_critical_path(DevProblem P, const int32_t *topo, const int32_t *lvl_off,
@@ -136,147 +138,227 @@ __device__ __forceinline__ int lanes_log2_for(int32_t nvec, int32_t min_vpl) {
     return lg;
 }
 
-// Tiles of one op with cnt invocations: full tiles of kScoreThreads >> lg
-// invocations at 2^lg lanes each, then one tail tile whose invocations get as
-// many lanes as fill a CTA (at most the op's vector count, rounded up).
-__device__ __forceinline__ int32_t tiles_of_op(int32_t cnt, int lg) {
-    const int32_t per = kScoreThreads >> lg;
-    return cnt / per + (cnt % per ? 1 : 0);
+// Tiles of an op with cnt invocations: full tiles of (kScoreThreads >> lg) groups
+// of ipt invocations each, then at most one tail tile.  The tail spreads its m
+// invocations over more lanes: as many as still fit one CTA, and no more than
+// the op has vectors.
+__device__ __forceinline__ int32_t full_tiles(int32_t cnt, int lg, int ipt) {
+    return cnt / ((kScoreThreads >> lg) * ipt);
 }
 
-// Blocks [0, n_dags) compute the critical path of one DAG each; the others
-// validate invocations, count them per op (one counter per 128-byte line, so
-// concurrent atomics on different ops never share a line) and prefetch the
-// encoded tables into L2.  The last block to finish lays out the buckets and
-// the scoring tiles, ops in the order P.op_order (largest tables first).
-__global__ void __launch_bounds__(256) k_prepare(DevProblem P, int64_t n_inv, const int32_t *dag,
-                                                 const int32_t *op_local, const int64_t *start,
-                                                 int64_t now, BucketScratch S, llama_decision *out,
-                                                 const int32_t *topo, const int32_t *lvl_off,
-                                                 const int32_t *dag_lvl, int32_t min_vpl) {
-    __shared__ int32_t warp_pos[32], warp_til[32];
-    __shared__ int last;
-    __shared__ CpSmem sm;
-    if ((int)blockIdx.x < P.n_dags) {
-        critical_path_of_dag(P, blockIdx.x, topo, lvl_off, dag_lvl, sm);
-    } else {
-        const int64_t nb = gridDim.x - P.n_dags;
-        for (int64_t i = (blockIdx.x - P.n_dags) * (int64_t)blockDim.x + threadIdx.x; i < n_inv;
-             i += nb * blockDim.x) {
-            const int32_t d = dag[i], o = op_local[i];
-            if (!invocation_valid(P, d, o, start[i], now)) {
-                S.gop[i] = -1;
-                llama_decision bad;
-                bad.cfg = -1;
-                bad.lat = 0;
-                bad.cost = 0;
-                bad.slack = 0;
-                bad.flags = LLAMA_FLAG_INVALID;
-                out[i] = bad;
-                atomicAdd(&S.ctrl[kCtrlInvalid], 1ull);
-                continue;
-            }
-            const int32_t g = P.dag_op_off[d] + o;
-            S.gop[i] = g;
-            S.slot[i] = atomicAdd(&S.cnt[(int64_t)g * kCntStride], 1);
-        }
-        // Pull the encoded tables into L2 while the buckets are laid out, so the
-        // scoring kernel's staging does not wait on DRAM.
-        if (P.prefetch_lines > 0) {
-            // each array is 2*n_pad bytes; line l < ceil(2*n_pad / 128) starts inside it
-            const char *arr[4] = {reinterpret_cast<const char *>(P.lat_lo),
-                                  reinterpret_cast<const char *>(P.lat_hi),
-                                  reinterpret_cast<const char *>(P.rf),
-                                  reinterpret_cast<const char *>(P.df)};
-            const int n_arr = P.df ? 4 : 3;
-            for (int64_t l = (blockIdx.x - P.n_dags) * (int64_t)blockDim.x + threadIdx.x;
-                 l < P.prefetch_lines * n_arr; l += nb * blockDim.x) {
-                const char *a = arr[l % n_arr] + 128 * (l / n_arr);
-                asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(a));
-            }
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        last = atomicAdd(&S.ctrl[kCtrlTicket], 1ull) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
+__device__ __forceinline__ int tail_lanes_log2(int32_t m, int lg, int ipt, int32_t nvec) {
+    const int32_t groups = (m + ipt - 1) / ipt;
+    while (lg < kScoreThreadsLog2 && (groups << (lg + 1)) <= kScoreThreads && (1 << lg) < nvec) ++lg;
+    return lg;
+}
 
-    // exclusive prefixes, in op_order, of the bucket sizes and of the tile counts
+// Bucket and tile layout, by one block once the counts are final: exclusive
+// prefixes, in op_order, of the bucket sizes, the full tiles and the tail
+// tiles; every op's full tiles come first in the tile list, the tails after.
+__device__ void layout_buckets_and_tiles(const DevProblem &P, const BucketScratch &S, int32_t min_vpl,
+                                         int32_t ipt, int32_t (*warp_sum)[32]) {
     const int n = P.n_ops, T = blockDim.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int per = (n + T - 1) / T;
     const int b = min(n, tid * per), e = min(n, b + per);
-    int32_t c = 0, t = 0;
-    for (int k = b; k < e; ++k) {
-        const int32_t v = P.op_order[k];
-        const int32_t ck = __ldcg(&S.cnt[(int64_t)v * kCntStride]);
-        const int32_t nvec = (int32_t)((P.pad_off[v + 1] - P.pad_off[v]) / kVec);
-        c += ck;
-        t += tiles_of_op(ck, lanes_log2_for(nvec, min_vpl));
-    }
-    int32_t ci = c, ti = t;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int32_t uc = __shfl_up_sync(0xffffffffu, ci, o);
-        const int32_t ut = __shfl_up_sync(0xffffffffu, ti, o);
-        if (lane >= o) { ci += uc; ti += ut; }
-    }
-    if (lane == 31) { warp_pos[wid] = ci; warp_til[wid] = ti; }
-    __syncthreads();
-    if (wid == 0) {
-        const int nw = T >> 5;
-        int32_t wc = lane < nw ? warp_pos[lane] : 0, wt = lane < nw ? warp_til[lane] : 0;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int32_t uc = __shfl_up_sync(0xffffffffu, wc, o);
-            const int32_t ut = __shfl_up_sync(0xffffffffu, wt, o);
-            if (lane >= o) { wc += uc; wt += ut; }
-        }
-        if (lane < nw) { warp_pos[lane] = wc; warp_til[lane] = wt; }
-    }
-    __syncthreads();
-    int32_t c0 = ci - c + (wid > 0 ? warp_pos[wid - 1] : 0);
-    int32_t t0 = ti - t + (wid > 0 ? warp_til[wid - 1] : 0);
+    int32_t loc[3] = {0, 0, 0};
     for (int k = b; k < e; ++k) {
         const int32_t v = P.op_order[k];
         const int32_t ck = __ldcg(&S.cnt[(int64_t)v * kCntStride]);
         const int32_t nvec = (int32_t)((P.pad_off[v + 1] - P.pad_off[v]) / kVec);
         const int lg = lanes_log2_for(nvec, min_vpl);
-        const int32_t per_tile = kScoreThreads >> lg;
-        S.op_start[v] = c0;
-        int32_t j = 0;
-        for (; j + per_tile <= ck; j += per_tile) S.tiles[t0++] = make_int4(v, j, per_tile, lg);
-        if (j < ck) {
-            // tail: more lanes per invocation, up to a CTA, no more than the op has vectors
-            const int32_t m = ck - j;
-            int tlg = lg;
-            while (tlg < kScoreThreadsLog2 && (m << (tlg + 1)) <= kScoreThreads && (1 << tlg) < nvec) ++tlg;
-            S.tiles[t0++] = make_int4(v, j, m, tlg);
+        const int32_t f = full_tiles(ck, lg, ipt);
+        loc[0] += ck;
+        loc[1] += f;
+        loc[2] += ck > f * ((kScoreThreads >> lg) * ipt) ? 1 : 0;
+    }
+    int32_t inc[3] = {loc[0], loc[1], loc[2]};
+    for (int o = 1; o < 32; o <<= 1) {
+        for (int a = 0; a < 3; ++a) {
+            const int32_t u = __shfl_up_sync(0xffffffffu, inc[a], o);
+            if (lane >= o) inc[a] += u;
         }
-        c0 += ck;
+    }
+    if (lane == 31)
+        for (int a = 0; a < 3; ++a) warp_sum[a][wid] = inc[a];
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = T >> 5;
+        for (int a = 0; a < 3; ++a) {
+            int32_t w = lane < nw ? warp_sum[a][lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t u = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += u;
+            }
+            if (lane < nw) warp_sum[a][lane] = w;
+        }
+    }
+    __syncthreads();
+    const int32_t total_full = warp_sum[1][(T >> 5) - 1];
+    int32_t pos = inc[0] - loc[0] + (wid > 0 ? warp_sum[0][wid - 1] : 0);
+    int32_t tf = inc[1] - loc[1] + (wid > 0 ? warp_sum[1][wid - 1] : 0);
+    int32_t tt = total_full + inc[2] - loc[2] + (wid > 0 ? warp_sum[2][wid - 1] : 0);
+    for (int k = b; k < e; ++k) {
+        const int32_t v = P.op_order[k];
+        const int32_t ck = __ldcg(&S.cnt[(int64_t)v * kCntStride]);
+        const int32_t nvec = (int32_t)((P.pad_off[v + 1] - P.pad_off[v]) / kVec);
+        const int lg = lanes_log2_for(nvec, min_vpl);
+        const int32_t per_tile = (kScoreThreads >> lg) * ipt;
+        S.op_start[v] = pos;
+        int32_t j = 0;
+        for (; j + per_tile <= ck; j += per_tile) S.tiles[tf++] = make_int4(v, j, per_tile, lg);
+        if (j < ck) S.tiles[tt++] = make_int4(v, j, ck - j, tail_lanes_log2(ck - j, lg, ipt, nvec));
+        pos += ck;
     }
     if (tid == T - 1) {
-        S.ctrl[kCtrlPositions] = (unsigned long long)c0;
-        S.ctrl[kCtrlTiles] = (unsigned long long)t0;
+        S.ctrl[kCtrlPositions] = (unsigned long long)pos;
+        S.ctrl[kCtrlTiles] = (unsigned long long)tt;
     }
 }
 
-// a2 fused with a3's scatter: place each invocation in its op's bucket and
-// compute its slack for every backend (Algorithm 1 through the critical path).
-__global__ void __launch_bounds__(256) k_scatter(DevProblem P, int64_t n_inv, const int32_t *dag,
-                                                 const int64_t *start, int64_t now, BucketScratch S) {
-    // let the scoring kernel start staging its tables while this one runs
-    asm volatile("griddepcontrol.launch_dependents;");
+// All blocks of a cooperative launch reach this point before any continues.
+// Bounded: after kMaxWaitTries polls the block records a timeout and goes on
+// (the call's results are then invalid and the host reports ETIMEOUT).
+__device__ __forceinline__ void grid_barrier(unsigned long long *count, unsigned long long target,
+                                             unsigned long long *timeout) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(count, 1ull);
+        unsigned long long seen = 0;
+        for (int it = 0; it < kMaxWaitTries; ++it) {
+            asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(seen) : "l"(count) : "memory");
+            if (seen >= target) break;
+            __nanosleep(32);
+        }
+        if (seen < target) atomicOr(timeout, 1ull);
+    }
+    __syncthreads();
+}
+
+// Validate invocation i and count it for its op: g = global op (-1 if invalid,
+// then its decision is written here), slot = its rank in the op's bucket,
+// rbase = target - elapsed time (Algorithm 1 before the queueing time).
+__device__ __forceinline__ void count_invocation(const DevProblem &P, int64_t i, const int32_t *dag,
+                                                 const int32_t *op_local, const int64_t *start,
+                                                 int64_t now, const BucketScratch &S,
+                                                 llama_decision *out, int32_t &g, int32_t &slot,
+                                                 int64_t &rbase) {
+    const int32_t d = dag[i], o = op_local[i];
+    const int64_t st = start[i];
+    if (!invocation_valid(P, d, o, st, now)) {
+        g = -1;
+        S.gop[i] = -1;
+        llama_decision bad;
+        bad.cfg = -1;
+        bad.lat = 0;
+        bad.cost = 0;
+        bad.slack = 0;
+        bad.flags = LLAMA_FLAG_INVALID;
+        out[i] = bad;
+        atomicAdd(&S.ctrl[kCtrlInvalid], 1ull);
+        return;
+    }
+    g = P.dag_op_off[d] + o;
+    rbase = P.slo[d] - (now - st);
+    slot = atomicAdd(&S.cnt[(int64_t)g * kCntStride], 1);
+    S.gop[i] = g;
+    S.slot[i] = slot;
+    S.rbase[i] = rbase;
+}
+
+// Place invocation i in its op's bucket and compute its slack for every
+// backend (Algorithm 1 through the critical path).
+__device__ __forceinline__ void scatter_invocation(const DevProblem &P, const BucketScratch &S, int64_t i,
+                                                   int32_t g, int32_t slot, int64_t rbase) {
+    S.b_inv[S.op_start[g] + slot] = (int32_t)i;
+    const int64_t ref = P.ref[g], cp = P.cp[g];
+    const uint64_t mg = P.cp_magic[g];
     const int H = P.n_hw;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_inv;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    for (int h = 0; h < H; ++h) S.b_slack[i * H + h] = slack_of(ref, cp, mg, rbase - P.q[h]);
+}
+
+// The bucketing step of a call, one cooperative launch (all blocks resident):
+//  1. blocks [0, n_cp) compute the critical paths of DAGs b, b + n_cp, ...; the
+//     other blocks validate invocations, count them per op (one counter per
+//     128-byte line, so concurrent atomics on different ops never share a
+//     line) and prefetch the encoded tables into L2; the last counting block
+//     lays out the buckets and the scoring tiles, ops in the order P.op_order
+//     (largest tables first): every op's full tiles first, then the tails;
+//  2. grid barrier;
+//  3. the counting blocks place their invocations in their buckets and
+//     compute their slack for every backend (Algorithm 1 through the critical
+//     path).
+__global__ void __launch_bounds__(256) k_bucket(DevProblem P, int64_t n_inv, const int32_t *dag,
+                                                const int32_t *op_local, const int64_t *start,
+                                                int64_t now, BucketScratch S, llama_decision *out,
+                                                const int32_t *topo, const int32_t *lvl_off,
+                                                const int32_t *dag_lvl, int32_t min_vpl, int32_t ipt,
+                                                int32_t n_cp) {
+    __shared__ int32_t warp_sum[3][32];
+    __shared__ int last;
+    __shared__ CpSmem sm;
+    if ((int)blockIdx.x < n_cp) {
+        for (int d = blockIdx.x; d < P.n_dags; d += n_cp) {
+            critical_path_of_dag(P, d, topo, lvl_off, dag_lvl, sm);
+            __syncthreads();  // the shared staging area is reused by the next DAG
+        }
+        grid_barrier(&S.ctrl[kCtrlBarrier], gridDim.x, &S.ctrl[kCtrlTimeout]);
+        return;
+    }
+    // counting blocks: each thread takes invocations base, base + stride, ...;
+    // the first kKeep of them stay in registers (op, slot in the bucket,
+    // remaining time before queueing) across the grid barrier
+    const int64_t nb = gridDim.x - n_cp;
+    const int64_t stride = nb * blockDim.x;
+    const int64_t base = (blockIdx.x - n_cp) * (int64_t)blockDim.x + threadIdx.x;
+    int32_t kg[kKeep], ks[kKeep];
+    int64_t kr[kKeep];
+#pragma unroll
+    for (int j = 0; j < kKeep; ++j) {
+        kg[j] = -1;
+        const int64_t i = base + j * stride;
+        if (i < n_inv) count_invocation(P, i, dag, op_local, start, now, S, out, kg[j], ks[j], kr[j]);
+    }
+    for (int64_t i = base + kKeep * stride; i < n_inv; i += stride) {
+        int32_t g, sl;
+        int64_t rb;
+        count_invocation(P, i, dag, op_local, start, now, S, out, g, sl, rb);
+    }
+    // Pull the encoded tables into L2 while the buckets are laid out, so the
+    // scoring kernel's staging does not wait on DRAM.
+    if (P.prefetch_rank_lines > 0) {
+        // lrb, rf (, df): 2*n_pad bytes each; dlat: 4*n_pad bytes; every
+        // prefetched line starts inside its array
+        const char *arr[3] = {reinterpret_cast<const char *>(P.lrb), reinterpret_cast<const char *>(P.rf),
+                              reinterpret_cast<const char *>(P.df)};
+        const int n_arr = P.df ? 3 : 2;
+        const int64_t n_rank = P.prefetch_rank_lines * n_arr;
+        for (int64_t l = base; l < n_rank + P.prefetch_dlat_lines; l += stride) {
+            const char *a = l < n_rank ? arr[l % n_arr] + 128 * (l / n_arr)
+                                       : reinterpret_cast<const char *>(P.dlat) + 128 * (l - n_rank);
+            asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(a));
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&S.ctrl[kCtrlTicket], 1ull) == (unsigned long long)(nb - 1);
+    }
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        layout_buckets_and_tiles(P, S, min_vpl, ipt, warp_sum);
+    }
+    grid_barrier(&S.ctrl[kCtrlBarrier], gridDim.x, &S.ctrl[kCtrlTimeout]);
+
+    // let the scoring kernel start staging its tables while the scatter runs
+    asm volatile("griddepcontrol.launch_dependents;");
+#pragma unroll
+    for (int j = 0; j < kKeep; ++j)
+        if (kg[j] >= 0) scatter_invocation(P, S, base + j * stride, kg[j], ks[j], kr[j]);
+    for (int64_t i = base + kKeep * stride; i < n_inv; i += stride) {
         const int32_t g = S.gop[i];
-        if (g < 0) continue;
-        S.b_inv[S.op_start[g] + S.slot[i]] = (int32_t)i;
-        const int64_t r_base = P.slo[dag[i]] - (now - start[i]);
-        const int64_t ref = P.ref[g], cp = P.cp[g];
-        for (int h = 0; h < H; ++h) S.b_slack[i * H + h] = slack_of(ref, cp, r_base - P.q[h]);
+        if (g >= 0) scatter_invocation(P, S, i, g, S.slot[i], S.rbase[i]);
     }
 }
 
@@ -293,7 +375,8 @@ __global__ void k_slack(DevProblem P, int64_t n_inv, const int32_t *dag, const i
         }
         const int32_t g = P.dag_op_off[d] + o;
         const int64_t r_base = P.slo[d] - (now - start[i]);
-        for (int h = 0; h < H; ++h) slack_out[i * H + h] = slack_of(P.ref[g], P.cp[g], r_base - P.q[h]);
+        for (int h = 0; h < H; ++h)
+            slack_out[i * H + h] = slack_of(P.ref[g], P.cp[g], P.cp_magic[g], r_base - P.q[h]);
     }
 }
 
@@ -301,28 +384,40 @@ __global__ void k_slack(DevProblem P, int64_t n_inv, const int32_t *dag, const i
 // a4: scoring
 // ---------------------------------------------------------------------------
 
-// Eight configurations against slack-1 = sm1: t = sm1 - L is negative exactly
-// when L >= slack (infeasible).  Cost-first: the sign bits of two configs are
-// moved to bits 15 and 31 and OR-ed onto their feasible-branch ranks (an
-// infeasible key is >= 0x8000, above every feasible one); alpha: the sign
-// bytes are replicated into a 0xFFFF mask that selects the infeasible-branch
-// rank rf ^ df.  Then a per-half unsigned 16-bit running minimum.
-__device__ __forceinline__ uint32_t scan8_cost_first(uint32_t best, int32_t sm1, int4 l0, int4 l1,
-                                                     uint4 rk) {
-    best = vmin_u16x2(best, rk.x | (prmt(sm1 - l0.x, sm1 - l0.y, 0x7430u) & 0x80008000u));
-    best = vmin_u16x2(best, rk.y | (prmt(sm1 - l0.z, sm1 - l0.w, 0x7430u) & 0x80008000u));
-    best = vmin_u16x2(best, rk.z | (prmt(sm1 - l1.x, sm1 - l1.y, 0x7430u) & 0x80008000u));
-    best = vmin_u16x2(best, rk.w | (prmt(sm1 - l1.z, sm1 - l1.w, 0x7430u) & 0x80008000u));
+// Eight configurations of one segment, for an invocation whose slack has c
+// distinct latencies of the op below it (c2 = c in both halves).  lk holds
+// 0x8000 + latency rank of each config: lk - c2 subtracts per 16-bit half
+// without borrow (ranks and c are below 8192), and bit 15 of a half is set
+// exactly when rank >= c, i.e. L >= slack (infeasible).  Cost-first: those
+// bits are OR-ed onto the feasible-branch ranks (an infeasible key is >=
+// 0x8000, above every feasible one); alpha: they are replicated into a 0xFFFF
+// mask that selects the infeasible-branch rank rf ^ df.  Then a per-half
+// unsigned 16-bit running minimum.
+__device__ __forceinline__ uint32_t scan8_cost_first(uint32_t best, uint32_t c2, uint4 lk, uint4 rk) {
+    best = vmin_u16x2(best, rk.x | ((lk.x - c2) & 0x80008000u));
+    best = vmin_u16x2(best, rk.y | ((lk.y - c2) & 0x80008000u));
+    best = vmin_u16x2(best, rk.z | ((lk.z - c2) & 0x80008000u));
+    best = vmin_u16x2(best, rk.w | ((lk.w - c2) & 0x80008000u));
     return best;
 }
 
-__device__ __forceinline__ uint32_t scan8_alpha(uint32_t best, int32_t sm1, int4 l0, int4 l1,
-                                                uint4 rk, uint4 dk) {
-    best = vmin_u16x2(best, rk.x ^ (dk.x & prmt(sm1 - l0.x, sm1 - l0.y, 0xFFBBu)));
-    best = vmin_u16x2(best, rk.y ^ (dk.y & prmt(sm1 - l0.z, sm1 - l0.w, 0xFFBBu)));
-    best = vmin_u16x2(best, rk.z ^ (dk.z & prmt(sm1 - l1.x, sm1 - l1.y, 0xFFBBu)));
-    best = vmin_u16x2(best, rk.w ^ (dk.w & prmt(sm1 - l1.z, sm1 - l1.w, 0xFFBBu)));
+__device__ __forceinline__ uint32_t scan8_alpha(uint32_t best, uint32_t c2, uint4 lk, uint4 rk, uint4 dk) {
+    best = vmin_u16x2(best, rk.x ^ (dk.x & prmt(lk.x - c2, 0, 0xBB99u)));
+    best = vmin_u16x2(best, rk.y ^ (dk.y & prmt(lk.y - c2, 0, 0xBB99u)));
+    best = vmin_u16x2(best, rk.z ^ (dk.z & prmt(lk.z - c2, 0, 0xBB99u)));
+    best = vmin_u16x2(best, rk.w ^ (dk.w & prmt(lk.w - c2, 0, 0xBB99u)));
     return best;
+}
+
+// Number of values below s in the ascending array d[0..m); d may point to
+// shared or global memory (generic loads).
+__device__ __forceinline__ int32_t count_below(const int32_t *d, int32_t m, int32_t s) {
+    int32_t lo = 0, hi = m;
+    while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (d[mid] < s) lo = mid + 1; else hi = mid;
+    }
+    return lo;
 }
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -351,54 +446,79 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(bar) : "memory");
 }
 
-// Persistent CTAs walk the tile list (op, first invocation j0, m invocations,
-// 2^lg lanes each).  For a tile, the op's encoded table is staged into shared
+// Persistent CTAs take tiles (op, first invocation j0, m invocations, 2^lg lanes
+// per group) from the tile list: first tile blockIdx.x, the next ones from an
+// atomic counter, so CTAs that finish early take more (the list is ordered
+// longest first).  For a tile, the op's encoded table is staged into shared
 // memory by TMA bulk copies, in chunks of at most `chunk` entries (a multiple
-// of 8); each group of 2^lg lanes scores one invocation: lane s takes the
-// vectors q = s mod 2^lg of every backend segment, against that segment's
-// slack.  Groups reduce with shuffles (and through shared memory when a group
-// spans several warps); lane 0 decodes the winning rank.
-template <int MODE>
+// of 8); while the first chunk lands, the lanes count, for each invocation and
+// segment, the op's distinct latencies below the slack (binary searches).  A
+// group of 2^lg lanes scores IPT consecutive invocations: lane s takes the
+// vectors q = s mod 2^lg of every backend segment, loads each vector once from
+// shared memory and applies it to all IPT invocations, each against its own
+// count for that segment.  Groups reduce with shuffles (and
+// through shared memory when a group spans several warps); lane u mod 2^lg of
+// a group decodes the group's invocation u.
+template <int MODE, int IPT>
 __device__ __forceinline__ void score_body(const DevProblem &P, const BucketScratch &S,
-                                           llama_decision *out, int32_t chunk) {
+                                           llama_decision *out, int32_t chunk, int32_t dl_cap) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    // chunk entries: latency planes (entries 0-3 and 4-7 of each vector), ranks
-    int32_t *lo_s = reinterpret_cast<int32_t *>(smem_raw);
-    int32_t *hi_s = lo_s + chunk / 2;
-    uint16_t *rf_s = reinterpret_cast<uint16_t *>(hi_s + chunk / 2);
+    // chunk entries: latency ranks, feasible-branch ranks (, rank differences);
+    // then, per group, the counts c of distinct latencies below each slack
+    uint16_t *lr_s = reinterpret_cast<uint16_t *>(smem_raw);
+    uint16_t *rf_s = lr_s + chunk;
     uint16_t *df_s = rf_s + chunk;
-    __shared__ __align__(8) unsigned long long mbar;
-    __shared__ uint32_t red[kScoreThreads / 32];
+    uint16_t *c_s = rf_s + chunk * (MODE == LLAMA_MODE_ALPHA ? 2 : 1);
+    // the op's distinct latencies, after the counts (16-byte aligned)
+    int32_t *dl_s = reinterpret_cast<int32_t *>(
+        smem_raw + ((size_t)chunk * (MODE == LLAMA_MODE_ALPHA ? 6 : 4) + (size_t)kScoreThreads * IPT * P.n_hw * 2 + 15) / 16 * 16);
+    __shared__ __align__(8) unsigned long long mbar, mbar_d;
+    __shared__ uint32_t red[IPT][kScoreThreads / 32];
+    __shared__ long long next_tile;
     const int tid = threadIdx.x, H = P.n_hw;
-    const uint32_t bar = smem_addr(&mbar);
+    const uint32_t bar = smem_addr(&mbar), bar_d = smem_addr(&mbar_d);
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_d) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    uint32_t phase = 0;
-    bool ok = true;
-    // tiles and buckets come from k_prepare (complete before k_scatter began);
-    // b_inv and b_slack come from k_scatter: wait for it before the first read
-    const int64_t n_tiles = (int64_t)S.ctrl[kCtrlTiles];
+    uint32_t phase = 0, phase_d = 0;
+    bool ok = true, dl_ok = true;
+    // tiles and buckets were laid out by k_bucket before its grid barrier, b_inv
+    // and b_slack after it: wait for k_bucket to complete before the first read
+    const long long n_tiles = (long long)S.ctrl[kCtrlTiles];
     bool scatter_done = false;
-    for (int64_t ti = blockIdx.x; ti < n_tiles && ok; ti += gridDim.x) {
+    long long ti = blockIdx.x;
+    while (ti < n_tiles) {
+        unsigned long long claim = 0;
+        if (tid == 0) claim = atomicAdd(&S.ctrl[kCtrlNextTile], 1ull);  // the tile after this one
         const int4 tile = S.tiles[ti];
         const int32_t v = tile.x, j0 = tile.y, m = tile.z, lg = tile.w;
         const int L = 1 << lg;
-        const bool active = tid < (m << lg);
         const int g = tid >> lg, s = tid & (L - 1);
         const int64_t p0 = P.pad_off[v];
         const int32_t npad = (int32_t)(P.pad_off[v + 1] - p0);
         const int32_t *sp = P.seg_pad + (int64_t)v * (H + 1);
+        const int32_t dn = P.dlat_n[v];
+        const bool dl_staged = dn <= dl_cap;
+        const int32_t *dl = dl_staged ? dl_s : P.dlat + p0;
+        const int nc = IPT * H;  // counts per group
+        uint16_t *cg = c_s + g * nc;
         if (!scatter_done) {
             asm volatile("griddepcontrol.wait;" ::: "memory");
             scatter_done = true;
         }
-        int32_t i = -1;
-        if (active) i = S.b_inv[S.op_start[v] + j0 + g];
-        const int32_t *slk = S.b_slack + (int64_t)(i < 0 ? 0 : i) * H;
-        uint32_t best = 0xFFFFFFFFu;
+        int32_t inv[IPT];
+        uint32_t best[IPT];
+        bool any = false;
+#pragma unroll
+        for (int u = 0; u < IPT; ++u) {
+            const int32_t j = g * IPT + u;
+            inv[u] = j < m ? S.b_inv[S.op_start[v] + j0 + j] : -1;
+            any |= inv[u] >= 0;
+            best[u] = 0xFFFFFFFFu;
+        }
         for (int32_t c0 = 0; c0 < npad; c0 += chunk) {
             const int32_t cn = min(chunk, npad - c0);
             __syncthreads();  // every thread is done with the previous chunk or tile
@@ -406,57 +526,95 @@ __device__ __forceinline__ void score_body(const DevProblem &P, const BucketScra
                 // the generic-proxy reads of the previous chunk are complete (barrier
                 // above); order them before the async-proxy writes that follow
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                const uint32_t bytes = (uint32_t)cn * (MODE == LLAMA_MODE_ALPHA ? 8u : 6u);
+                if (c0 == 0 && dl_staged) {
+                    // the distinct latencies first (whole 16-byte words: dlat has
+                    // npad >= dn entries at this op)
+                    const uint32_t db = (uint32_t)((dn + 3) / 4) * 16u;
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                                 ::"r"(bar_d), "r"(db) : "memory");
+                    bulk_g2s(dl_s, P.dlat + p0, db, bar_d);
+                }
+                const uint32_t bytes = (uint32_t)cn * (MODE == LLAMA_MODE_ALPHA ? 6u : 4u);
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
                              ::"r"(bar), "r"(bytes) : "memory");
-                bulk_g2s(lo_s, P.lat_lo + (p0 + c0) / 2, 2u * cn, bar);
-                bulk_g2s(hi_s, P.lat_hi + (p0 + c0) / 2, 2u * cn, bar);
+                bulk_g2s(lr_s, P.lrb + p0 + c0, 2u * cn, bar);
                 bulk_g2s(rf_s, P.rf + p0 + c0, 2u * cn, bar);
                 if (MODE == LLAMA_MODE_ALPHA) bulk_g2s(df_s, P.df + p0 + c0, 2u * cn, bar);
             }
+            if (c0 == 0 && dl_staged) {
+                // every thread waits: the vote below must see the same outcome
+                if (!mbar_wait(bar_d, phase_d)) dl_ok = false;
+                phase_d ^= 1u;
+            }
+            if (c0 == 0 && any && dl_ok) {
+                // while the first chunk lands: the lanes of a group share the
+                // searches for c(u, h), one per invocation u and segment h
+                for (int t = s; t < nc; t += L) {
+                    const int u = t / H, h = t - u * H;
+                    int32_t iu = inv[0];  // inv[u] without a runtime index into registers
+#pragma unroll
+                    for (int w = 1; w < IPT; ++w) iu = u == w ? inv[w] : iu;
+                    cg[t] = iu >= 0 ? (uint16_t)count_below(dl, dn, S.b_slack[(int64_t)iu * H + h]) : 0;
+                }
+            }
             // every thread must agree before any leaves the barrier sequence
-            if (!__syncthreads_and(mbar_wait(bar, phase))) {
+            if (!__syncthreads_and(mbar_wait(bar, phase) && dl_ok)) {
                 ok = false;
                 break;
             }
             phase ^= 1u;
-            if (active) {
+            if (any) {
                 const int qc0 = c0 / kVec, qc1 = (c0 + cn) / kVec;
-                const int4 *lo4 = reinterpret_cast<const int4 *>(lo_s);
-                const int4 *hi4 = reinterpret_cast<const int4 *>(hi_s);
+                const uint4 *lr4 = reinterpret_cast<const uint4 *>(lr_s);
                 const uint4 *rf4 = reinterpret_cast<const uint4 *>(rf_s);
                 const uint4 *df4 = reinterpret_cast<const uint4 *>(df_s);
                 for (int h = 0; h < H; ++h) {
                     const int a = max(__ldg(sp + h) / kVec, qc0), b = min(__ldg(sp + h + 1) / kVec, qc1);
                     if (a >= b) continue;
-                    const int32_t sm1 = slk[h] - 1;
+                    uint32_t c2[IPT];
+#pragma unroll
+                    for (int u = 0; u < IPT; ++u) c2[u] = (uint32_t)cg[u * H + h] * 0x00010001u;
                     for (int q = a + ((s - a) & (L - 1)); q < b; q += L) {
                         const int r = q - qc0;
-                        if (MODE == LLAMA_MODE_ALPHA)
-                            best = scan8_alpha(best, sm1, lo4[r], hi4[r], rf4[r], df4[r]);
-                        else
-                            best = scan8_cost_first(best, sm1, lo4[r], hi4[r], rf4[r]);
+                        const uint4 lk = lr4[r], rk = rf4[r];
+                        if (MODE == LLAMA_MODE_ALPHA) {
+                            const uint4 dk = df4[r];
+#pragma unroll
+                            for (int u = 0; u < IPT; ++u) best[u] = scan8_alpha(best[u], c2[u], lk, rk, dk);
+                        } else {
+#pragma unroll
+                            for (int u = 0; u < IPT; ++u) best[u] = scan8_cost_first(best[u], c2[u], lk, rk);
+                        }
                     }
                 }
             }
         }
         if (!ok) break;
-        uint32_t key = active ? min(best & 0xFFFFu, best >> 16) : 0xFFFFu;
+        uint32_t key[IPT];
         const int wl = L < 32 ? L : 32;
-        for (int o = 1; o < wl; o <<= 1) key = min(key, __shfl_xor_sync(0xffffffffu, key, o));
+#pragma unroll
+        for (int u = 0; u < IPT; ++u) {
+            key[u] = inv[u] >= 0 ? min(best[u] & 0xFFFFu, best[u] >> 16) : 0xFFFFu;
+            for (int o = 1; o < wl; o <<= 1) key[u] = min(key[u], __shfl_xor_sync(0xffffffffu, key[u], o));
+        }
         if (L > 32) {
             // a group spans L/32 warps: combine the warps' minima in shared memory
-            if ((tid & 31) == 0) red[tid >> 5] = key;
+            if ((tid & 31) == 0)
+                for (int u = 0; u < IPT; ++u) red[u][tid >> 5] = key[u];
             __syncthreads();
-            if (s == 0) {
-                for (int w = 1; w < (L >> 5); ++w) key = min(key, red[(tid >> 5) + w]);
-            }
+            if (s < IPT)  // the decoding lanes (L > 32 > IPT here)
+                for (int u = 0; u < IPT; ++u)
+                    for (int w = 1; w < (L >> 5); ++w) key[u] = min(key[u], red[u][(tid >> 5) + w]);
         }
-        if (active && s == 0) {
+        // lane u mod 2^lg of the group decodes invocation u (every lane holds every key)
+#pragma unroll
+        for (int u = 0; u < IPT; ++u) {
+            if (s != (u & (L - 1)) || inv[u] < 0) continue;
+            const int32_t i = inv[u];
             const int64_t c_base = P.cfg_off[v];
             int32_t idx;
-            if (MODE == LLAMA_MODE_ALPHA) idx = P.inv[2 * c_base + key];
-            else idx = key < 0x8000u ? (int32_t)P.inv[2 * c_base + key] : P.fast[v];
+            if (MODE == LLAMA_MODE_ALPHA) idx = P.inv[2 * c_base + key[u]];
+            else idx = key[u] < 0x8000u ? (int32_t)P.inv[2 * c_base + key[u]] : P.fast[v];
             const int64_t gx = c_base + idx;
             const int32_t Lx = P.lat[gx];
             const int lam = backend_of(P.hw_off + (int64_t)v * (H + 1), H, idx);
@@ -469,23 +627,36 @@ __device__ __forceinline__ void score_body(const DevProblem &P, const BucketScra
             dsn.flags = Lx < sl ? LLAMA_FLAG_FEASIBLE : 0;
             out[i] = dsn;
         }
+        if (tid == 0) next_tile = (long long)(claim + gridDim.x);
+        __syncthreads();
+        ti = next_tile;
     }
     if (!ok) {
         // a staging copy never completed: report it, wait (bounded) for the copy
         // to land so no transfer targets this CTA's shared memory after exit
         if (tid == 0) atomicOr(&S.ctrl[kCtrlTimeout], 1ull);
         mbar_wait(bar, phase);
+        if (!dl_ok) mbar_wait(bar_d, phase_d ^ 1u);
     }
 }
 
-__global__ void __launch_bounds__(kScoreThreads)
-    k_score_cost_first(DevProblem P, BucketScratch S, llama_decision *out, int32_t chunk) {
-    score_body<LLAMA_MODE_COST_FIRST>(P, S, out, chunk);
-}
+#define LLAMA_SCORE_KERNEL(name, MODE, IPT)                                                      \
+    __global__ void __launch_bounds__(kScoreThreads)                                            \
+        name(DevProblem P, BucketScratch S, llama_decision *out, int32_t chunk, int32_t dl_cap) { \
+        score_body<MODE, IPT>(P, S, out, chunk, dl_cap);                                          \
+    }
+LLAMA_SCORE_KERNEL(k_score_cf1, LLAMA_MODE_COST_FIRST, 1)
+LLAMA_SCORE_KERNEL(k_score_cf2, LLAMA_MODE_COST_FIRST, 2)
+LLAMA_SCORE_KERNEL(k_score_cf4, LLAMA_MODE_COST_FIRST, 4)
+LLAMA_SCORE_KERNEL(k_score_al1, LLAMA_MODE_ALPHA, 1)
+LLAMA_SCORE_KERNEL(k_score_al2, LLAMA_MODE_ALPHA, 2)
+LLAMA_SCORE_KERNEL(k_score_al4, LLAMA_MODE_ALPHA, 4)
+#undef LLAMA_SCORE_KERNEL
 
-__global__ void __launch_bounds__(kScoreThreads)
-    k_score_alpha(DevProblem P, BucketScratch S, llama_decision *out, int32_t chunk) {
-    score_body<LLAMA_MODE_ALPHA>(P, S, out, chunk);
+const void *score_kernel(int mode, int ipt) {
+    if (mode == LLAMA_MODE_ALPHA)
+        return ipt >= 4 ? (const void *)k_score_al4 : ipt == 2 ? (const void *)k_score_al2 : (const void *)k_score_al1;
+    return ipt >= 4 ? (const void *)k_score_cf4 : ipt == 2 ? (const void *)k_score_cf2 : (const void *)k_score_cf1;
 }
 
 // ---------------------------------------------------------------------------
@@ -498,22 +669,37 @@ cudaError_t enqueue_schedule(const ContextView &v, const BucketScratch &S, int64
                              const int32_t *dag, const int32_t *op_local, const int64_t *start,
                              int64_t now, llama_decision *out, cudaStream_t s,
                              const cudaEvent_t *trace) {
-    // external: when captured into a graph the records become event-record nodes
-    auto mark = [&](int k) { if (trace) cudaEventRecordWithFlags(trace[k], s, cudaEventRecordExternal); };
+    auto mark = [&](int k) { if (trace) cudaEventRecord(trace[k], s); };
     mark(0);
     cudaError_t e = cudaMemsetAsync(S.cnt, 0, sizeof(int32_t) * kCntStride * (size_t)v.n_ops, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(S.ctrl, 0, sizeof(unsigned long long) * kCtrlWords, s);
     if (e != cudaSuccess) return e;
-    const int count_blocks =
-        (int)std::max<int64_t>(1, std::min<int64_t>((n_inv + 255) / 256, (int64_t)v.num_sms * 8));
-    k_prepare<<<v.n_dags + count_blocks, 256, 0, s>>>(v.P, n_inv, dag, op_local, start, now, S, out,
-                                                      v.topo, v.lvl_off, v.dag_lvl, v.min_vpl);
+    // bucketing: one cooperative launch (its blocks meet at a grid barrier)
+    const int n_cp = std::max(1, std::min(v.n_dags, std::max(1, v.bucket_max_blocks / 4)));
+    const int count_blocks = (int)std::max<int64_t>(
+        1, std::min<int64_t>((n_inv + 255) / 256, (int64_t)v.bucket_max_blocks - n_cp));
+    {
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(n_cp + count_blocks);
+        cfg.blockDim = dim3(256);
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        DevProblem P = v.P;
+        BucketScratch Sc = S;
+        const int32_t *topo = v.topo, *lvl_off = v.lvl_off, *dag_lvl = v.dag_lvl;
+        int32_t min_vpl = v.min_vpl, ipt = v.ipt, ncp = n_cp;
+        void *args[] = {&P, &n_inv, &dag, &op_local, &start, &now, &Sc, &out,
+                        &topo, &lvl_off, &dag_lvl, &min_vpl, &ipt, &ncp};
+        e = cudaLaunchKernelExC(&cfg, (const void *)k_bucket, args);
+        if (e != cudaSuccess) return e;
+    }
     mark(1);
-    const int gi = (int)std::max<int64_t>(1, std::min<int64_t>((n_inv + 255) / 256, (int64_t)v.num_sms * 16));
-    k_scatter<<<gi, 256, 0, s>>>(v.P, n_inv, dag, start, now, S);
-    mark(2);
-    // the scoring kernel may launch before k_scatter completes (it waits on
-    // griddepcontrol.wait before reading k_scatter's output)
+    // the scoring kernel may launch before k_bucket completes (it waits on
+    // griddepcontrol.wait before reading the scatter's output)
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(v.score_grid);
     cfg.blockDim = dim3(kScoreThreads);
@@ -524,12 +710,13 @@ cudaError_t enqueue_schedule(const ContextView &v, const BucketScratch &S, int64
     attr[0].val.programmaticStreamSerializationAllowed = trace ? 0 : 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (v.mode == LLAMA_MODE_ALPHA)
-        e = cudaLaunchKernelEx(&cfg, k_score_alpha, v.P, S, out, v.score_chunk);
-    else
-        e = cudaLaunchKernelEx(&cfg, k_score_cost_first, v.P, S, out, v.score_chunk);
+    DevProblem P = v.P;
+    BucketScratch Sc = S;
+    int32_t chunk = v.score_chunk, dl_cap = v.dlat_cap;
+    void *args[] = {&P, &Sc, &out, &chunk, &dl_cap};
+    e = cudaLaunchKernelExC(&cfg, score_kernel(v.mode, v.ipt), args);
     if (e != cudaSuccess) return e;
-    mark(3);
+    mark(2);
     return cudaGetLastError();
 }
 
@@ -540,8 +727,9 @@ cudaError_t enqueue_schedule(const ContextView &v, const BucketScratch &S, int64
 // One CTA per op: latencies into the padded layout (INT32_MAX at pads, which no
 // slack can exceed), ranks initialised to the pad rank, and the op's fastest
 // configuration argmin (L, index).
-__global__ void k_encode_pad(DevProblem P, int32_t *lat_lo, int32_t *lat_hi, uint16_t *rf,
-                             uint16_t *df, int32_t *fast) {
+// One CTA per op: pads get the pad ranks (never feasible, never the minimum),
+// and the op's fastest configuration argmin (L, index) is recorded.
+__global__ void k_encode_pad(DevProblem P, uint16_t *lrb, uint16_t *rf, uint16_t *df, int32_t *fast) {
     __shared__ int64_t red[32];
     const int v = blockIdx.x, H = P.n_hw;
     const int64_t c0 = P.cfg_off[v], p0 = P.pad_off[v];
@@ -550,10 +738,8 @@ __global__ void k_encode_pad(DevProblem P, int32_t *lat_lo, int32_t *lat_hi, uin
     for (int h = 0; h < H; ++h) {
         const int src_n = hw[h + 1] - hw[h], dst_n = sp[h + 1] - sp[h];
         for (int k = threadIdx.x; k < dst_n; k += blockDim.x) {
-            const int64_t dst = p0 + sp[h] + k;  // padded position; vector dst/8, entry dst%8
-            const int32_t L = k < src_n ? P.lat[c0 + hw[h] + k] : INT32_MAX;
-            const int64_t plane = dst / kVec * 4 + dst % 4;
-            if (dst % kVec < 4) lat_lo[plane] = L; else lat_hi[plane] = L;
+            const int64_t dst = p0 + sp[h] + k;
+            if (k >= src_n) lrb[dst] = kLatRankPad;
             rf[dst] = kPadRank;
             if (df) df[dst] = 0;
         }
@@ -650,6 +836,79 @@ __global__ void k_encode_rank(DevProblem P, int32_t sort_cap, uint16_t *rf, uint
         rf[dst] = rf_tmp[x];
         df[dst] = (uint16_t)(rf_tmp[x] ^ ri_tmp[x]);
     }
+}
+
+// One CTA per op: sort the op's (latency, index) pairs in shared memory
+// (bitonic network), keep the distinct latencies in ascending order
+// (dlat[pad_off[v] ..], dlat_n[v] of them) and write each configuration's
+// biased latency rank 0x8000 + (position of its latency among the distinct
+// ones) at its padded position.
+__global__ void k_encode_lat(DevProblem P, uint16_t *lrb, int32_t *dlat, int32_t *dlat_n) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t *key = reinterpret_cast<uint64_t *>(smem_raw);
+    __shared__ int32_t warp_tot[32];
+    const int v = blockIdx.x, H = P.n_hw, T = blockDim.x, tid = threadIdx.x;
+    const int lane = tid & 31, wid = tid >> 5;
+    const int64_t c0 = P.cfg_off[v], p0 = P.pad_off[v];
+    const int n = (int)(P.cfg_off[v + 1] - c0);
+    int N = 1;
+    while (N < n) N <<= 1;
+    const int32_t *hw = P.hw_off + (int64_t)v * (H + 1);
+    const int32_t *sp = P.seg_pad + (int64_t)v * (H + 1);
+    for (int k = tid; k < N; k += T)
+        key[k] = k < n ? ((uint64_t)(uint32_t)P.lat[c0 + k] << 16) | (uint64_t)k : ~0ull;
+    __syncthreads();
+    for (int kk = 2; kk <= N; kk <<= 1) {
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < N; i += T) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const bool up = (i & kk) == 0;
+                    if ((key[i] > key[ixj]) == up) {
+                        const uint64_t t = key[i];
+                        key[i] = key[ixj];
+                        key[ixj] = t;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // rank of sorted entry r = (number of distinct latencies among entries 0..r) - 1:
+    // an inclusive block scan of "differs from its predecessor" flags, in
+    // contiguous runs of `per` entries per thread
+    const int per = (n + T - 1) / T;
+    const int b = min(n, tid * per), e = min(n, b + per);
+    int32_t cnt = 0;
+    for (int r = b; r < e; ++r) cnt += (r == 0 || (key[r] >> 16) != (key[r - 1] >> 16)) ? 1 : 0;
+    int32_t inc = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += u;
+    }
+    if (lane == 31) warp_tot[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        int32_t w = lane < (T >> 5) ? warp_tot[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t u = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += u;
+        }
+        if (lane < (T >> 5)) warp_tot[lane] = w;
+    }
+    __syncthreads();
+    int32_t rank = inc - cnt + (wid > 0 ? warp_tot[wid - 1] : 0) - 1;
+    for (int r = b; r < e; ++r) {
+        const int32_t L = (int32_t)(key[r] >> 16);
+        if (r == 0 || L != (int32_t)(key[r - 1] >> 16)) {
+            ++rank;
+            dlat[p0 + rank] = L;
+        }
+        const int x = (int)(key[r] & 0xFFFF);
+        const int lam = backend_of(hw, H, x);
+        lrb[p0 + sp[lam] + (x - hw[lam])] = (uint16_t)(kLatRankBias + rank);
+    }
+    if (tid == T - 1) dlat_n[v] = warp_tot[(T >> 5) - 1];
 }
 
 }  // namespace llama

@@ -72,17 +72,17 @@ struct llama_ctx {
     int32_t n_ops = 0, max_npad = 0;
     int64_t n_cfg = 0, n_pad = 0;
     DevBuf cfg_off, hw_off, lat, cost, ref_cfg, batch, res, res_total;
-    DevBuf pad_off, seg_pad, lat_lo, lat_hi, rf, df, inv, fast, op_order;
+    DevBuf pad_off, seg_pad, lrb, dlat, dlat_n, rf, df, inv, fast, op_order;
     int64_t mean_npad = 0;
-    DevBuf ref, cp;
+    DevBuf ref, cp, cp_magic;
     int64_t q[LLAMA_MAX_HW] = {0};
 
     // bucketing scratch
     int64_t cap_inv = 0, cap_tiles = 0;
     int32_t cap_ops = 0;
-    DevBuf cnt, ctrl, op_start, gop, slot, b_inv, b_slack, tiles;
+    DevBuf cnt, ctrl, op_start, gop, slot, b_inv, b_slack, rbase, tiles;
     // scoring kernel geometry (set by llama_set_profiles)
-    int32_t min_vpl = 16, score_grid = 0, score_chunk = 0;
+    int32_t min_vpl = 16, ipt = 2, score_grid = 0, score_chunk = 0, bucket_max_blocks = 0, dlat_cap = 0;
     size_t score_smem = 0;
 
     // staging for host-memory arguments of the blocking calls
@@ -94,25 +94,22 @@ struct llama_ctx {
     cudaEvent_t trace[LLAMA_TRACE_EVENTS] = {};
     bool tracing = false;
 
-    // CUDA graph of the last scheduling call (opts.use_graph): replayed while
-    // the call's arguments and the context's buffers stay the same; `now` is
-    // patched into the two kernels that take it, trace events are swapped.
+    // CUDA graph of the last untraced scheduling call (opts.use_graph): replayed
+    // while the call's arguments and the context's buffers stay the same; `now`
+    // is patched into the kernel that takes it.  Traced calls launch directly.
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
-    cudaGraphNode_t g_prepare = nullptr, g_scatter = nullptr;
-    cudaGraphNode_t g_events[LLAMA_TRACE_EVENTS] = {};
+    cudaGraphNode_t g_bucket = nullptr;
     int64_t g_n_inv = -1, g_now = 0;
     const void *g_args[4] = {};
-    bool g_traced = false;
 
     void drop_graph() {
         if (gexec) cudaGraphExecDestroy(gexec);
         if (graph) cudaGraphDestroy(graph);
         gexec = nullptr;
         graph = nullptr;
-        g_prepare = g_scatter = nullptr;
-        for (auto &e : g_events) e = nullptr;
+        g_bucket = nullptr;
         g_n_inv = -1;
     }
 
@@ -154,8 +151,9 @@ DevProblem make_problem(const llama_ctx *c) {
     P.res_total = c->res_total.as<int32_t>();
     P.pad_off = c->pad_off.as<int64_t>();
     P.seg_pad = c->seg_pad.as<int32_t>();
-    P.lat_lo = c->lat_lo.as<int32_t>();
-    P.lat_hi = c->lat_hi.as<int32_t>();
+    P.lrb = c->lrb.as<uint16_t>();
+    P.dlat = c->dlat.as<int32_t>();
+    P.dlat_n = c->dlat_n.as<int32_t>();
     P.rf = c->rf.as<uint16_t>();
     P.df = c->df.as<uint16_t>();
     P.inv = c->inv.as<uint16_t>();
@@ -163,11 +161,13 @@ DevProblem make_problem(const llama_ctx *c) {
     P.op_order = c->op_order.as<int32_t>();
     P.max_npad = c->max_npad;
     // prefetch the encoded tables into L2 when they take at most half of it
-    const int64_t tbl_bytes = (int64_t)(c->opts.mode == LLAMA_MODE_ALPHA ? 8 : 6) * c->n_pad;
+    const int64_t tbl_bytes = (int64_t)(c->opts.mode == LLAMA_MODE_ALPHA ? 10 : 8) * c->n_pad;
     const bool pf = c->n_pad > 0 && tbl_bytes <= c->l2_bytes / 2;
-    P.prefetch_lines = pf ? (2 * c->n_pad + 127) / 128 : 0;
+    P.prefetch_rank_lines = pf ? (2 * c->n_pad + 127) / 128 : 0;
+    P.prefetch_dlat_lines = pf ? (4 * c->n_pad + 127) / 128 : 0;
     P.ref = c->ref.as<int64_t>();
     P.cp = c->cp.as<int64_t>();
+    P.cp_magic = c->cp_magic.as<uint64_t>();
     for (int h = 0; h < LLAMA_MAX_HW; ++h) P.q[h] = c->q[h];
     P.alpha_num = c->opts.alpha_num;
     P.alpha_den = c->opts.alpha_den;
@@ -183,6 +183,7 @@ BucketScratch make_scratch(const llama_ctx *c) {
     S.slot = c->slot.as<int32_t>();
     S.b_inv = c->b_inv.as<int32_t>();
     S.b_slack = c->b_slack.as<int32_t>();
+    S.rbase = c->rbase.as<int64_t>();
     S.tiles = c->tiles.as<int4>();
     return S;
 }
@@ -200,8 +201,11 @@ ContextView view_of(const llama_ctx *c) {
     v.device = c->opts.device;
     v.num_sms = c->num_sms;
     v.min_vpl = c->min_vpl;
+    v.ipt = c->ipt;
     v.score_grid = c->score_grid;
+    v.bucket_max_blocks = c->bucket_max_blocks;
     v.score_chunk = c->score_chunk;
+    v.dlat_cap = c->dlat_cap;
     v.score_smem = c->score_smem;
     return v;
 }
@@ -231,6 +235,7 @@ int ensure_scratch(llama_ctx *c, int64_t n_inv) {
         LL_CUDA(c, c->slot.alloc(sizeof(int32_t) * n));
         LL_CUDA(c, c->b_inv.alloc(sizeof(int32_t) * n));
         LL_CUDA(c, c->b_slack.alloc(sizeof(int32_t) * n * H));
+        LL_CUDA(c, c->rbase.alloc(sizeof(int64_t) * n));
         c->cap_inv = n;
         c->cap_tiles = 0;
     }
@@ -269,6 +274,26 @@ int grid_for(const llama_ctx *c, int64_t n, int threads) {
 }
 
 // The launch sequence of one scheduling call (all device pointers).
+// Shared memory of the scoring kernel: a staging chunk of latency ranks and
+// objective ranks (plus rank differences in alpha mode), then one count per
+// (invocation, backend) for every group of the CTA (at most one group per thread).
+size_t score_smem_bytes(const llama_ctx *c) {
+    const size_t tbl = (size_t)c->score_chunk * (c->opts.mode == LLAMA_MODE_ALPHA ? 6 : 4);
+    const size_t counts = (size_t)kScoreThreads * c->ipt * c->opts.n_hw * 2;
+    return (tbl + counts + 15) / 16 * 16 + 4 * (size_t)c->dlat_cap;
+}
+
+// Dynamic shared memory and persistent grid of the scoring kernel for the
+// current profiles and tuning.
+int configure_score(llama_ctx *c) {
+    const void *fn = score_kernel(c->opts.mode, c->ipt);
+    LL_CUDA(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->score_smem));
+    int nb = 0;
+    LL_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kScoreThreads, c->score_smem));
+    c->score_grid = c->num_sms * std::max(1, nb);
+    return LLAMA_OK;
+}
+
 // Replace argument `index` of a captured kernel node by *value (same type).
 template <class T>
 cudaError_t patch_arg(cudaGraphExec_t exec, cudaGraphNode_t node, int n_args, int index, const T *value) {
@@ -288,9 +313,8 @@ int capture_graph(llama_ctx *c, int64_t n_inv, const int32_t *dag, const int32_t
     c->drop_graph();
     const ContextView v = view_of(c);
     const BucketScratch S = make_scratch(c);
-    const cudaEvent_t *tr = c->tracing ? c->trace : nullptr;
     LL_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-    const cudaError_t e = enqueue_schedule(v, S, n_inv, dag, op_local, start, now, out, c->cap_stream, tr);
+    const cudaError_t e = enqueue_schedule(v, S, n_inv, dag, op_local, start, now, out, c->cap_stream, nullptr);
     cudaGraph_t g = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
     if (e != cudaSuccess) {
@@ -310,54 +334,42 @@ int capture_graph(llama_ctx *c, int64_t n_inv, const int32_t *dag, const int32_t
         if (t == cudaGraphNodeTypeKernel) {
             cudaKernelNodeParams p{};
             LL_CUDA(c, cudaGraphKernelNodeGetParams(node, &p));
-            if (p.func == (void *)k_prepare) c->g_prepare = node;
-            if (p.func == (void *)k_scatter) c->g_scatter = node;
-        } else if (t == cudaGraphNodeTypeEventRecord && tr) {
-            cudaEvent_t ev;
-            LL_CUDA(c, cudaGraphEventRecordNodeGetEvent(node, &ev));
-            for (int k = 0; k < LLAMA_TRACE_EVENTS; ++k)
-                if (ev == tr[k]) c->g_events[k] = node;
+            if (p.func == (void *)k_bucket) c->g_bucket = node;
         }
     }
-    if (!c->g_prepare || !c->g_scatter) return c->fail(LLAMA_ECUDA, "graph capture: kernel nodes not found");
+    if (!c->g_bucket) return c->fail(LLAMA_ECUDA, "graph capture: kernel node not found");
     c->g_n_inv = n_inv;
     c->g_now = now;
     c->g_args[0] = dag;
     c->g_args[1] = op_local;
     c->g_args[2] = start;
     c->g_args[3] = out;
-    c->g_traced = tr != nullptr;
     return LLAMA_OK;
 }
 
 int launch_schedule(llama_ctx *c, int64_t n_inv, const int32_t *dag, const int32_t *op_local,
                     const int64_t *start, int64_t now, llama_decision *out, cudaStream_t s) {
-    if (!c->opts.use_graph) {
+    if (!c->opts.use_graph || c->tracing) {
         const ContextView v = view_of(c);
         const BucketScratch S = make_scratch(c);
         LL_CUDA(c, enqueue_schedule(v, S, n_inv, dag, op_local, start, now, out, s,
                                     c->tracing ? c->trace : nullptr));
-        c->last_launches = 3;
+        c->last_launches = 2;
         return LLAMA_OK;
     }
     const bool same = c->gexec && c->g_n_inv == n_inv && c->g_args[0] == dag &&
-                      c->g_args[1] == op_local && c->g_args[2] == start && c->g_args[3] == out &&
-                      c->g_traced == c->tracing;
+                      c->g_args[1] == op_local && c->g_args[2] == start && c->g_args[3] == out;
     if (!same) {
         const int rc = capture_graph(c, n_inv, dag, op_local, start, now, out);
         if (rc) return rc;
     }
     if (now != c->g_now) {
-        // `now` is argument 5 of k_prepare's 12 and argument 4 of k_scatter's 6
-        LL_CUDA(c, patch_arg(c->gexec, c->g_prepare, 12, 5, &now));
-        LL_CUDA(c, patch_arg(c->gexec, c->g_scatter, 6, 4, &now));
+        // `now` is argument 5 of k_bucket's 14
+        LL_CUDA(c, patch_arg(c->gexec, c->g_bucket, 14, 5, &now));
         c->g_now = now;
     }
-    if (c->tracing)
-        for (int k = 0; k < LLAMA_TRACE_EVENTS; ++k)
-            if (c->g_events[k]) LL_CUDA(c, cudaGraphExecEventRecordNodeSetEvent(c->gexec, c->g_events[k], c->trace[k]));
     LL_CUDA(c, cudaGraphLaunch(c->gexec, s));
-    c->last_launches = 3;
+    c->last_launches = 2;
     return LLAMA_OK;
 }
 
@@ -419,6 +431,13 @@ extern "C" int llama_create(llama_ctx **out, const llama_opts *opts) {
         return LLAMA_ECUDA;
     }
     c->l2_bytes = l2;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bucket, 256, 0) != cudaSuccess || nb < 1) {
+        cudaGetLastError();
+        llama_destroy(c);
+        return LLAMA_ECUDA;
+    }
+    c->bucket_max_blocks = nb * c->num_sms;
     *out = c;
     return LLAMA_OK;
 }
@@ -612,13 +631,15 @@ extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cf
         (e = up(c->pad_off, pad_off.data(), 8 * (size_t)(n_ops + 1))) != cudaSuccess ||
         (e = up(c->seg_pad, seg_pad.data(), 4 * seg_pad.size())) != cudaSuccess ||
         (e = up(c->op_order, op_order.data(), 4 * (size_t)n_ops)) != cudaSuccess ||
-        (e = c->lat_lo.alloc(2 * (size_t)n_pad)) != cudaSuccess ||
-        (e = c->lat_hi.alloc(2 * (size_t)n_pad)) != cudaSuccess ||
+        (e = c->lrb.alloc(2 * (size_t)n_pad)) != cudaSuccess ||
+        (e = c->dlat.alloc(4 * (size_t)n_pad)) != cudaSuccess ||
+        (e = c->dlat_n.alloc(4 * (size_t)n_ops)) != cudaSuccess ||
         (e = c->rf.alloc(2 * (size_t)n_pad)) != cudaSuccess ||
         (e = c->inv.alloc(2 * 2 * (size_t)n_cfg)) != cudaSuccess ||
         (e = c->fast.alloc(4 * (size_t)n_ops)) != cudaSuccess ||
         (e = c->ref.alloc(8 * (size_t)n_ops)) != cudaSuccess ||
-        (e = c->cp.alloc(8 * (size_t)n_ops)) != cudaSuccess)
+        (e = c->cp.alloc(8 * (size_t)n_ops)) != cudaSuccess ||
+        (e = c->cp_magic.alloc(8 * (size_t)n_ops)) != cudaSuccess)
         return c->cuda_fail(e, "set_profiles upload");
     if (alpha) {
         if ((e = up(c->batch, batch, 4 * (size_t)n_cfg)) != cudaSuccess ||
@@ -639,7 +660,7 @@ extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cf
     c->cap_ops = 0;  // op count may have changed: re-size the per-op scratch
 
     const DevProblem P = make_problem(c);
-    k_encode_pad<<<n_ops, 256, 0, c->stream>>>(P, c->lat_lo.as<int32_t>(), c->lat_hi.as<int32_t>(), c->rf.as<uint16_t>(),
+    k_encode_pad<<<n_ops, 256, 0, c->stream>>>(P, c->lrb.as<uint16_t>(), c->rf.as<uint16_t>(),
                                                alpha ? c->df.as<uint16_t>() : nullptr,
                                                c->fast.as<int32_t>());
     int32_t sort_cap = 1;
@@ -649,6 +670,12 @@ extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cf
         return c->fail(LLAMA_EINVAL, "set_profiles: configuration space too large for one CTA sort");
     LL_CUDA(c, cudaFuncSetAttribute(k_encode_rank, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)sort_smem));
+    int32_t lat_cap = 1;
+    while (lat_cap < max_n) lat_cap <<= 1;
+    const size_t lat_smem = (size_t)lat_cap * 8;
+    LL_CUDA(c, cudaFuncSetAttribute(k_encode_lat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lat_smem));
+    k_encode_lat<<<n_ops, 1024, lat_smem, c->stream>>>(P, c->lrb.as<uint16_t>(), c->dlat.as<int32_t>(),
+                                                      c->dlat_n.as<int32_t>());
     k_encode_rank<<<n_ops, 1024, sort_smem, c->stream>>>(P, sort_cap, c->rf.as<uint16_t>(),
                                                         alpha ? c->df.as<uint16_t>() : nullptr,
                                                         c->inv.as<uint16_t>());
@@ -658,12 +685,10 @@ extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cf
     // scoring kernel: stage tables in chunks of at most kMaxChunk entries, one
     // persistent CTA per resident slot
     c->score_chunk = std::min<int32_t>(max_npad, kMaxChunk);
-    c->score_smem = (size_t)c->score_chunk * (alpha ? 8 : 6);
-    auto fn = alpha ? (const void *)k_score_alpha : (const void *)k_score_cost_first;
-    LL_CUDA(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->score_smem));
-    int nb = 0;
-    LL_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kScoreThreads, c->score_smem));
-    c->score_grid = c->num_sms * std::max(1, nb);
+    c->dlat_cap = std::min<int32_t>(max_npad, kMaxDlatSmem);
+    c->score_smem = score_smem_bytes(c);
+    const int rc = configure_score(c);
+    if (rc) return rc;
     c->prof_set = true;
     return LLAMA_OK;
 }
@@ -676,6 +701,26 @@ extern "C" int llama_set_queue(llama_ctx *c, const int64_t *q_us) {
     for (int h = 0; h < c->opts.n_hw; ++h) c->q[h] = q_us[h];
     c->drop_graph();  // the queueing times are kernel arguments
     return LLAMA_OK;
+}
+
+extern "C" int llama_set_tuning(llama_ctx *c, int32_t lanes_min_vectors, int32_t inv_per_thread,
+                                int32_t chunk_entries) {
+    if (!c) return LLAMA_EINVAL;
+    if (lanes_min_vectors < 1 || lanes_min_vectors > 1024)
+        return c->fail(LLAMA_EINVAL, "set_tuning: lanes_min_vectors out of 1..1024");
+    if (inv_per_thread != 1 && inv_per_thread != 2 && inv_per_thread != 4)
+        return c->fail(LLAMA_EINVAL, "set_tuning: inv_per_thread must be 1, 2 or 4");
+    if (chunk_entries < 0 || chunk_entries > LLAMA_MAX_CFG || chunk_entries % kVec)
+        return c->fail(LLAMA_EINVAL, "set_tuning: chunk_entries must be a multiple of 8 in 0..8192");
+    if (!c->prof_set) return c->fail(LLAMA_ENOTREADY, "set_tuning: set the profiles first");
+    DeviceGuard g(c->opts.device);
+    c->drop_graph();
+    c->min_vpl = lanes_min_vectors;
+    c->ipt = inv_per_thread;
+    c->score_chunk = chunk_entries ? std::min<int32_t>(chunk_entries, c->max_npad)
+                                   : std::min<int32_t>(c->max_npad, kMaxChunk);
+    c->score_smem = score_smem_bytes(c);
+    return configure_score(c);
 }
 
 extern "C" int llama_reserve(llama_ctx *c, int64_t max_inv) {

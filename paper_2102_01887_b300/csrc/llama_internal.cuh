@@ -11,9 +11,11 @@
 //             pad_off[n_ops+1] int64   start of op v in the padded space, a multiple of 8;
 //             seg_pad[n_ops*(H+1)]     op-local padded start of each backend segment,
 //                                      every segment padded to a multiple of 8 entries;
-//             lat_lo, lat_hi [n_pad/2] int32  L(x) at its padded position, INT32_MAX at
-//                                      pads, split in two planes: entries 0-3 of each
-//                                      8-entry vector in lat_lo, entries 4-7 in lat_hi;
+//             dlat[n_pad] int32        the op's distinct latencies, ascending, at
+//                                      pad_off[v] (dlat_n[v] of them);
+//             lrb[n_pad] u16           0x8000 + rank of L(x) among the op's distinct
+//                                      latencies (kLatRankPad at pads), so that
+//                                      L(x) < s  <=>  rank < #(distinct latencies < s);
 //             rf[n_pad] u16            rank of x's feasible-branch objective;
 //             df[n_pad] u16            rf ^ rank of x's infeasible-branch objective (ALPHA);
 //             inv[2*n_cfg] u16         rank -> op-local index (op base 2*cfg_off[v]);
@@ -30,10 +32,14 @@ namespace llama {
 
 constexpr int kVec = 8;            // configurations per 128-bit rank vector
 constexpr uint16_t kPadRank = 0xFFFF;
+constexpr uint16_t kLatRankBias = 0x8000;  // latency ranks are stored as 0x8000 + rank
+constexpr uint16_t kLatRankPad = 0xBFFF;   // at pads: above any count of distinct latencies
 constexpr int kScoreThreads = 256;
 constexpr int kScoreThreadsLog2 = 8;
 constexpr int kMaxChunk = 4096;        // table entries staged at a time by the scoring kernel
 constexpr int kMaxWaitTries = 1 << 20; // bounded mbarrier waits
+constexpr int kKeep = 4;               // invocations a counting thread keeps in registers
+constexpr int kMaxDlatSmem = 4096;     // distinct latencies staged per op (else searched in L2)
 constexpr int kCntStride = 32;     // int32 slots between per-op counters: one 128-byte line each
 // control words of a call (unsigned long long each)
 constexpr int kCtrlInvalid = 0;    // invalid invocations
@@ -41,6 +47,8 @@ constexpr int kCtrlTicket = 1;     // blocks of k_prepare that have finished
 constexpr int kCtrlPositions = 2;  // bucket positions laid out
 constexpr int kCtrlTiles = 3;      // scoring tiles laid out
 constexpr int kCtrlTimeout = 4;    // nonzero: a bounded device wait gave up
+constexpr int kCtrlNextTile = 5;   // dynamic tile counter of the scoring kernel
+constexpr int kCtrlBarrier = 6;    // grid barrier of k_bucket
 constexpr int kCtrlWords = 8;
 // DAGs up to this size are staged in shared memory for the critical path
 constexpr int kCpSmemOps = 512;
@@ -58,16 +66,18 @@ struct DevProblem {
     const int32_t *batch, *res, *res_total;
     const int64_t *pad_off;
     const int32_t *seg_pad;
-    const int32_t *lat_lo, *lat_hi;
+    const uint16_t *lrb;
+    const int32_t *dlat, *dlat_n;
     const uint16_t *rf, *df, *inv;
     const int32_t *fast;
     const int32_t *op_order;  // ops by padded table size, largest first (bucket order)
     int32_t max_npad;  // largest padded op table (entries)
-    // 128-byte lines of each of lat_lo, lat_hi, rf (and df), all 2*n_pad bytes long,
-    // to pull into L2 before scoring (0: off)
-    int64_t prefetch_lines;
+    // 128-byte lines to pull into L2 before scoring (0: off): of each of lrb, rf
+    // (and df), all 2*n_pad bytes long, and of dlat (4*n_pad bytes)
+    int64_t prefetch_rank_lines, prefetch_dlat_lines;
     int64_t *ref;
     int64_t *cp;
+    uint64_t *cp_magic;  // floor((2^64-1) / cp[v]), for exact division by cp[v]
     int64_t q[LLAMA_MAX_HW];
     int64_t alpha_num, alpha_den;
 };
@@ -80,14 +90,27 @@ struct BucketScratch {
     int32_t *slot;            // [n_inv]     rank of the invocation inside its op's bucket
     int32_t *b_inv;           // [n_inv]     invocation at each bucket position
     int32_t *b_slack;         // [n_inv*H]   slack per invocation and backend
+    int64_t *rbase;           // [n_inv]     target - elapsed time of each invocation
     int4 *tiles;              // [max_tiles] scoring tiles {op, j0, m, lanes_log2}
 };
 
+// floor(n / d) for n < 2^62 and d >= 1, given m = floor((2^64 - 1) / d): the high
+// half of n*m lies within one of n/d from below (m > 2^64/d - 1, so the error is
+// below 2n/2^64 < 1/2), so it is floor(n/d) or one less and one comparison makes it
+// exact.  This is division by an invariant integer through multiplication
+// (Granlund and Montgomery, PLDI 1994), with the divisor fixed per operation.
+__device__ __forceinline__ uint64_t div_invariant(uint64_t n, uint64_t d, uint64_t m) {
+    uint64_t q = __umul64hi(n, m);
+    if (n - q * d >= d) ++q;
+    return q;
+}
+
 // Slack of Algorithm 1 through the longest remaining path (Section 4.1):
-// floor(ref * R / cp), 0 once the target has passed.  ref*R < 2^62.
-__device__ __forceinline__ int32_t slack_of(int64_t ref, int64_t cp, int64_t R) {
+// floor(ref * R / cp), 0 once the target has passed.  ref, R < 2^31, so
+// ref*R < 2^62.
+__device__ __forceinline__ int32_t slack_of(int64_t ref, int64_t cp, uint64_t magic, int64_t R) {
     if (R <= 0) return 0;
-    return (int32_t)((ref * R) / cp);
+    return (int32_t)div_invariant((uint64_t)(ref * R), (uint64_t)cp, magic);
 }
 
 // Read-only view of a ready context for launchers outside llama_host.cu
@@ -97,8 +120,11 @@ struct ContextView {
     const int32_t *topo, *lvl_off, *dag_lvl;
     int32_t n_dags, n_ops, n_hw, mode, device, num_sms;
     int32_t min_vpl;      // vectors a lane should scan at least (sets lanes per invocation)
+    int32_t ipt;          // invocations per scoring thread (1, 2 or 4)
     int32_t score_grid;   // persistent CTAs of the scoring kernel
+    int32_t bucket_max_blocks;  // co-resident blocks of k_bucket (cooperative launch)
     int32_t score_chunk;  // table entries staged per chunk
+    int32_t dlat_cap;     // distinct latencies the scoring kernel stages (a multiple of 4)
     size_t score_smem;    // dynamic shared memory of the scoring kernel
 };
 int context_view(llama_ctx *c, ContextView *v);  // LLAMA_OK or the readiness error
@@ -107,28 +133,32 @@ int context_fail(llama_ctx *c, int code, const char *msg);
 // Kernels (defined in kernels.cu).
 __global__ void k_critical_path(DevProblem P, const int32_t *topo, const int32_t *lvl_off,
                                 const int32_t *dag_lvl);
-__global__ void k_prepare(DevProblem P, int64_t n_inv, const int32_t *dag, const int32_t *op_local,
-                          const int64_t *start, int64_t now, BucketScratch S, llama_decision *out,
-                          const int32_t *topo, const int32_t *lvl_off, const int32_t *dag_lvl,
-                          int32_t min_vpl);
-__global__ void k_scatter(DevProblem P, int64_t n_inv, const int32_t *dag, const int64_t *start,
-                          int64_t now, BucketScratch S);
-__global__ void k_score_cost_first(DevProblem P, BucketScratch S, llama_decision *out, int32_t chunk);
-__global__ void k_score_alpha(DevProblem P, BucketScratch S, llama_decision *out, int32_t chunk);
+__global__ void k_bucket(DevProblem P, int64_t n_inv, const int32_t *dag, const int32_t *op_local,
+                         const int64_t *start, int64_t now, BucketScratch S, llama_decision *out,
+                         const int32_t *topo, const int32_t *lvl_off, const int32_t *dag_lvl,
+                         int32_t min_vpl, int32_t ipt, int32_t n_cp);
+// Scoring kernels: objective mode x invocations per thread (1, 2 or 4).
+__global__ void k_score_cf1(DevProblem P, BucketScratch S, llama_decision *out, int32_t chunk, int32_t dl_cap);
+__global__ void k_score_cf2(DevProblem P, BucketScratch S, llama_decision *out, int32_t chunk, int32_t dl_cap);
+__global__ void k_score_cf4(DevProblem P, BucketScratch S, llama_decision *out, int32_t chunk, int32_t dl_cap);
+__global__ void k_score_al1(DevProblem P, BucketScratch S, llama_decision *out, int32_t chunk, int32_t dl_cap);
+__global__ void k_score_al2(DevProblem P, BucketScratch S, llama_decision *out, int32_t chunk, int32_t dl_cap);
+__global__ void k_score_al4(DevProblem P, BucketScratch S, llama_decision *out, int32_t chunk, int32_t dl_cap);
+const void *score_kernel(int mode, int ipt);
 
 // Scoring tiles a call may lay out (each op: full tiles plus one tail).
 int64_t max_tiles(int64_t n_inv, int32_t n_ops);
 // Enqueue the whole scheduling call on stream s: counters cleared, then
-// k_prepare, k_scatter, k_score.  trace (nullable) = LLAMA_TRACE_EVENTS events
-// recorded at the phase boundaries.
+// k_bucket, k_score.  trace (nullable) = LLAMA_TRACE_EVENTS events recorded at
+// the phase boundaries.
 cudaError_t enqueue_schedule(const ContextView &v, const BucketScratch &S, int64_t n_inv,
                              const int32_t *dag, const int32_t *op_local, const int64_t *start,
                              int64_t now, llama_decision *out, cudaStream_t s,
                              const cudaEvent_t *trace);
 __global__ void k_slack(DevProblem P, int64_t n_inv, const int32_t *dag, const int32_t *op_local,
                         const int64_t *start, int64_t now, int32_t *slack_out);
-__global__ void k_encode_pad(DevProblem P, int32_t *lat_lo, int32_t *lat_hi, uint16_t *rf,
-                             uint16_t *df, int32_t *fast);
+__global__ void k_encode_pad(DevProblem P, uint16_t *lrb, uint16_t *rf, uint16_t *df, int32_t *fast);
+__global__ void k_encode_lat(DevProblem P, uint16_t *lrb, int32_t *dlat, int32_t *dlat_n);
 __global__ void k_encode_rank(DevProblem P, int32_t sort_n, uint16_t *rf, uint16_t *df,
                               uint16_t *inv);
 

@@ -29,11 +29,11 @@ assert DECISION_DTYPE.itemsize == 24
 
 EXPORTS = ("llama_create", "llama_destroy", "llama_set_dags", "llama_set_profiles",
            "llama_set_queue", "llama_schedule", "llama_schedule_async", "llama_schedule_static",
-           "llama_reserve",
+           "llama_set_tuning", "llama_reserve",
            "llama_critical_path", "llama_slack", "llama_set_trace_events", "llama_last_launch_count",
            "llama_last_error")
-TRACE_EVENTS = 4
-TRACE_PHASES = ("prepare", "scatter_slack", "score")
+TRACE_EVENTS = 3
+TRACE_PHASES = ("bucket", "score")
 
 
 class LlamaError(RuntimeError):
@@ -71,6 +71,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "llama_schedule": ([vp, i64, vp, vp, vp, i64, vp], ctypes.c_int),
             "llama_schedule_async": ([vp, i64, vp, vp, vp, i64, vp, vp], ctypes.c_int),
             "llama_schedule_static": ([vp, i64, vp, vp, vp, i64, vp, vp], ctypes.c_int),
+            "llama_set_tuning": ([vp, i32, i32, i32], ctypes.c_int),
             "llama_reserve": ([vp, i64], ctypes.c_int),
             "llama_critical_path": ([vp, vp], ctypes.c_int),
             "llama_slack": ([vp, i64, vp, vp, vp, i64, vp], ctypes.c_int),
@@ -143,6 +144,12 @@ def llama_set_profiles(ctx, cfg_off, hw_off, lat_us, cost_nd, ref_cfg, batch=Non
 def llama_set_queue(ctx, q_us) -> None:
     q = _c(q_us, np.int64)
     _check(ctx, load().llama_set_queue(ctx, _ptr(q)))
+
+
+def llama_set_tuning(ctx, lanes_min_vectors: int = 16, inv_per_thread: int = 2,
+                     chunk_entries: int = 0) -> None:
+    _check(ctx, load().llama_set_tuning(ctx, int(lanes_min_vectors), int(inv_per_thread),
+                                        int(chunk_entries)))
 
 
 def llama_reserve(ctx, max_inv: int) -> None:

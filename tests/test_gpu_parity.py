@@ -280,7 +280,7 @@ def test_graph_replay_tracks_now_sizes_and_contents(L):
             exp, rc_o = oracle.schedule(p, case)
             assert rc == rc_o == L.OK
             assert_same(got, exp, f"call {k}")
-        # traced replay on device pointers: events recorded inside the graph
+        # traced calls on device pointers (direct launches), then untraced replay again
         dev = torch.device("cuda:0")
         dag = torch.from_numpy(inv.dag).to(dev)
         opl = torch.from_numpy(inv.op_local).to(dev)
@@ -297,3 +297,28 @@ def test_graph_replay_tracks_now_sizes_and_contents(L):
             assert all(ev[j].elapsed_time(ev[j + 1]) >= 0 for j in range(L.TRACE_EVENTS - 1))
             assert_same(out.cpu().numpy().view(L.DECISION_DTYPE), exp, f"traced {rep}")
         L.llama_set_trace_events(s.ctx, [])
+        out.zero_()
+        L.llama_schedule_async(s.ctx, dag, opl, st, inv.now_us, out, stream)
+        stream.synchronize()
+        assert_same(out.cpu().numpy().view(L.DECISION_DTYPE), exp, "untraced after traced")
+
+
+# ------------------------------------------------------- launch schedules ---
+
+@pytest.mark.parametrize("tuning", [(1, 1, 0), (4, 2, 0), (16, 4, 0), (64, 2, 0), (1024, 1, 0),
+                                    (16, 2, 64), (2, 4, 8), (8, 1, 136)])
+def test_tunings_change_no_result(L, tuning):
+    # every kernel variant (1/2/4 invocations per thread), lane counts from one
+    # to a whole CTA per invocation, and chunked staging of tables larger than
+    # the chunk, on ties-heavy random problems and on the benchmark's workload
+    p, inv = W.random_small(77, max_cfg=300, n_inv=3000, value_range=200)
+    pm, invm = W.medium()
+    subm = invm.subset(np.arange(0, invm.n, 7))
+    for prob, case in ((p, inv), (pm, subm)):
+        for mode in (0, 1):
+            exp, _ = oracle.schedule(prob, case, mode=mode, alpha=(2, 3))
+            with L.Scheduler(prob, mode=mode, alpha=(2, 3)) as s:
+                L.llama_set_tuning(s.ctx, *tuning)
+                got, rc = s.schedule(case)
+            assert rc == L.OK
+            assert_same(got, exp, f"tuning {tuning} mode {mode}")
