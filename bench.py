@@ -30,7 +30,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "invocations scheduled/sec & configs scored/sec on 1 B300 (HBM%); p99 decision us"
 UNIT = "invocations/s"
-ALGO_OPS_PER_SCORE = 2  # one latency-vs-slack compare + one min-update of the key
+# ALU-pipe instructions per scored configuration in the scan's inner loop: per
+# two configurations one LOP3 (flag the infeasible half) and one packed 16-bit
+# min; the packed subtraction of the latency ranks issues on the FMA pipe.
+# Alpha mode adds one PRMT per two configurations.
+ALU_OPS_PER_SCORE = {"cost_first": 1.0, "alpha": 1.5}
+ALU_LANES_PER_SM = 64  # integer ALU pipe: 16 lanes per SM sub-partition, 4 per SM
 SCAN_BYTES_PER_SCORE = 12  # int32 latency + int64 cost per scored configuration
 
 
@@ -46,6 +51,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch kernels directly, no CUDA graph")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default scoring schedule")
     return ap.parse_args()
 
 
@@ -212,6 +218,12 @@ def main():
     def step():
         L.llama_schedule_async(ctx, dag, opl, st, inv.now_us, out, stream)
 
+    tuning = None
+    if not args.no_autotune:
+        # choose the scoring schedule on this batch before anything is timed
+        from paper_2102_01887_b300.autotune import autotune
+        tuning = autotune(ctx, dag, opl, st, inv.now_us, out, stream, flush)
+
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             flush.fill_(1)
@@ -296,11 +308,14 @@ def main():
     peaks, peak_src = measured_peaks()
     clk = clocks.summary()
     score_ms = float(phase_ms[:, -1].mean())
-    # ALU roofline of the scoring kernel: the tables are staged once per op and reused by all
-    # of that op's invocations, so the scan is bound by integer issue, not HBM.
+    # ALU roofline of the scoring kernel: tables are staged once per tile and
+    # reused by all of that tile's invocations, so the scan is bound by the
+    # integer ALU pipe, not HBM.
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak_tops = sm_count * 128 * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
-    achieved_tops = ALGO_OPS_PER_SCORE * scores / (score_ms / 1e3) / 1e12
+    sm_mhz = float(peaks.get("sm_max_mhz", 2032.0))
+    peak_tops = sm_count * ALU_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+    ops_per_score = ALU_OPS_PER_SCORE[args.mode]
+    achieved_tops = ops_per_score * scores / (score_ms / 1e3) / 1e12
     value = world * inv.n * args.steps / total_s
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -319,7 +334,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": float(step_ms.mean()), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32/int64", "data": "synthetic",
-        "config": workload_config(args.workload, p, inv, args.mode, scores),
+        "config": {**workload_config(args.workload, p, inv, args.mode, scores),
+                   "schedule": tuning["best"] if tuning else "default"},
         "configs_scored_per_s": world * scores * args.steps / total_s,
         "decision_latency_us": {"p50": 1e3 * float(np.median(step_ms)),
                                 "p99": 1e3 * float(np.percentile(step_ms, 99))},
@@ -331,11 +347,14 @@ def main():
         "kernel_ms_note": "per-kernel event times from a second pass of the same steps with trace "
                           "events (direct launches, no overlap between the two kernels)",
         "roofline": {"bound": "alu", "kernel": "k_score", "achieved": achieved_tops,
-                     "peak": peak_tops, "unit": "Tops/s", "frac": achieved_tops / peak_tops,
+                     "peak": peak_tops, "unit": "T ALU-ops/s", "frac": achieved_tops / peak_tops,
                      "traffic": None,
-                     "peak_source": f"{sm_count} SMs x 128 int32 lanes x {peaks.get('sm_max_mhz', 2032.0)} MHz "
-                                    f"({peak_src} clock)",
-                     "ops_per_score": ALGO_OPS_PER_SCORE},
+                     "peak_source": f"{sm_count} SMs x {ALU_LANES_PER_SM} integer ALU lanes x {sm_mhz:.0f} MHz "
+                                    f"({peak_src} max SM clock)",
+                     "alu_ops_per_score": ops_per_score,
+                     "scores_per_s_ceiling": peak_tops * 1e12 / ops_per_score},
+        "schedule_trials": ([{k: t[k] for k in ("lanes_min_vectors", "inv_per_thread", "ms")}
+                             for t in tuning["trials"]] if tuning else None),
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
         "parity_vs_oracle": parity,
     }

@@ -147,7 +147,7 @@ int llama_schedule_async(llama_ctx *ctx, int64_t n_inv, const int32_t *dag,
  * latency-bound loop that cannot take the implicit synchronisation of the
  * CUDA allocator, or code running where the allocator must not be entered.
  * This call allocates nothing: its bucketing scratch is one fixed, file-scope
- * device array of about 5 MB, which every GPU that loads the library holds
+ * device array of about 6 MB, which every GPU that loads the library holds
  * until the process exits.  Same arguments and results as
  * llama_schedule_async (device pointers, enqueued on `stream`, invalid
  * invocations flagged in `out`), with these limits: n_inv at most

@@ -1,0 +1,57 @@
+"""Autotuner of the scoring kernel's launch schedule.
+
+The schedule (lanes sharing one invocation, invocations per thread, staging
+chunk) changes speed, never results (tests check the latter).  For a given
+context and a batch of device-resident invocations, the tuner times every
+candidate on that batch -- whole scheduling calls replayed as the caller
+would replay them, the L2 cache flushed before each call -- and keeps the
+fastest, which it applies with ``llama_set_tuning``.
+"""
+from __future__ import annotations
+
+import itertools
+from typing import Iterable, Optional
+
+from . import llama as L
+
+DEFAULT_LANES_MIN_VECTORS = (4, 8, 16, 32, 64)
+DEFAULT_INV_PER_THREAD = (1, 2, 4)
+
+
+def time_call(ctx, dag, op_local, start, now: int, out, stream, flush, reps: int = 5) -> float:
+    """Median device time (ms) of one scheduling call, L2 flushed before each."""
+    import torch
+    times = []
+    for r in range(reps + 1):
+        with torch.cuda.stream(stream):
+            flush.fill_(r & 0xFF)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            L.llama_schedule_async(ctx, dag, op_local, start, now, out, stream)
+            e1.record(stream)
+        e1.synchronize()
+        if r:  # the first call of a setting (re)captures its graph
+            times.append(e0.elapsed_time(e1))
+    times.sort()
+    return times[len(times) // 2]
+
+
+def autotune(ctx, dag, op_local, start, now: int, out, stream=None, flush=None,
+             lanes: Iterable[int] = DEFAULT_LANES_MIN_VECTORS,
+             ipts: Iterable[int] = DEFAULT_INV_PER_THREAD, chunk: int = 0,
+             reps: int = 5) -> dict:
+    """Sweep the candidates, apply the fastest, return {"best": ..., "trials": [...]}."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if flush is None:
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dag.device)
+    trials = []
+    for lmv, ipt in itertools.product(lanes, ipts):
+        L.llama_set_tuning(ctx, lmv, ipt, chunk)
+        ms = time_call(ctx, dag, op_local, start, now, out, stream, flush, reps)
+        trials.append({"lanes_min_vectors": lmv, "inv_per_thread": ipt, "chunk": chunk, "ms": ms})
+    best = min(trials, key=lambda t: t["ms"])
+    L.llama_set_tuning(ctx, best["lanes_min_vectors"], best["inv_per_thread"], best["chunk"])
+    return {"best": best, "trials": trials}

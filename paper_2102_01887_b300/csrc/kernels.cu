@@ -70,33 +70,28 @@ __device__ __forceinline__ bool invocation_valid(const DevProblem &P, int32_t d,
 struct CpSmem {
     int64_t cp[kCpSmemOps];
     int64_t ref[kCpSmemOps];
-    int32_t rp[kCpSmemOps + 1];
-    int32_t col[kCpSmemEdges];
-    int32_t topo[kCpSmemOps];
-    int32_t lvl[kCpSmemOps + 1];
+    int32_t pk[kCpPackWords];
 };
 
 __device__ void critical_path_of_dag(const DevProblem &P, int d, const int32_t *topo,
                                      const int32_t *lvl_off, const int32_t *dag_lvl, CpSmem &sm) {
-    const int lo = P.dag_op_off[d], hi = P.dag_op_off[d + 1], n = hi - lo;
-    const int e_lo = P.row_ptr[lo], ne = P.row_ptr[hi] - e_lo;
-    const int l_lo = dag_lvl[d], nl = dag_lvl[d + 1] - l_lo;
-    if (n <= kCpSmemOps && ne <= kCpSmemEdges) {
-        for (int k = threadIdx.x; k < n; k += blockDim.x) {
-            const int v = lo + k;
-            sm.ref[k] = (int64_t)P.lat[P.cfg_off[v] + P.ref_cfg[v]];
-            sm.rp[k] = P.row_ptr[v] - e_lo;
-            sm.topo[k] = topo[v] - lo;
-        }
-        for (int k = threadIdx.x; k < ne; k += blockDim.x) sm.col[k] = P.col[e_lo + k] - lo;
-        for (int k = threadIdx.x; k <= nl; k += blockDim.x) sm.lvl[k] = lvl_off[l_lo + k] - lo;
-        if (threadIdx.x == 0) sm.rp[n] = ne;
+    const int64_t off = P.dag_pack_off[d];
+    const int nw = (int)(P.dag_pack_off[d + 1] - off);
+    if (nw > 0) {
+        // the DAG's packed structure in one round of loads: header {first op, ops,
+        // edges, levels}, reference-configuration indices, local successor CSR,
+        // ops by height, level offsets
+        for (int k = threadIdx.x; k < nw; k += blockDim.x) sm.pk[k] = P.dag_pack[off + k];
+        __syncthreads();
+        const int lo = sm.pk[0], n = sm.pk[1], ne = sm.pk[2], nl = sm.pk[3];
+        const int32_t *gidx = sm.pk + 4, *rp = gidx + n, *col = rp + n + 1, *ord = col + ne, *lvl = ord + n;
+        for (int k = threadIdx.x; k < n; k += blockDim.x) sm.ref[k] = (int64_t)P.lat[gidx[k]];
         __syncthreads();
         for (int l = 0; l < nl; ++l) {
-            for (int p = sm.lvl[l] + (int)threadIdx.x; p < sm.lvl[l + 1]; p += blockDim.x) {
-                const int v = sm.topo[p];
+            for (int p = lvl[l] + (int)threadIdx.x; p < lvl[l + 1]; p += blockDim.x) {
+                const int v = ord[p];
                 int64_t best = 0;
-                for (int e = sm.rp[v]; e < sm.rp[v + 1]; ++e) best = max(best, sm.cp[sm.col[e]]);
+                for (int e = rp[v]; e < rp[v + 1]; ++e) best = max(best, sm.cp[col[e]]);
                 sm.cp[v] = sm.ref[v] + best;
             }
             __syncthreads();
@@ -108,8 +103,10 @@ __device__ void critical_path_of_dag(const DevProblem &P, int d, const int32_t *
         }
         return;
     }
+    // a DAG too large for shared memory: the same levels through global memory
+    const int lo = P.dag_op_off[d], hi = P.dag_op_off[d + 1];
     for (int v = lo + (int)threadIdx.x; v < hi; v += blockDim.x)
-        P.ref[v] = (int64_t)P.lat[P.cfg_off[v] + P.ref_cfg[v]];
+        P.ref[v] = (int64_t)P.lat[P.ref_gidx[v]];
     __syncthreads();
     for (int l = dag_lvl[d]; l < dag_lvl[d + 1]; ++l) {
         for (int p = lvl_off[l] + (int)threadIdx.x; p < lvl_off[l + 1]; p += blockDim.x) {
@@ -160,12 +157,27 @@ __device__ void layout_buckets_and_tiles(const DevProblem &P, const BucketScratc
     const int n = P.n_ops, T = blockDim.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int per = (n + T - 1) / T;
     const int b = min(n, tid * per), e = min(n, b + per);
+    // the first kKeepOps ops of this thread's run stay in registers for the second pass
+    int4 ki[kKeepOps];
+    int32_t kc[kKeepOps];
     int32_t loc[3] = {0, 0, 0};
-    for (int k = b; k < e; ++k) {
-        const int32_t v = P.op_order[k];
-        const int32_t ck = __ldcg(&S.cnt[(int64_t)v * kCntStride]);
-        const int32_t nvec = (int32_t)((P.pad_off[v + 1] - P.pad_off[v]) / kVec);
-        const int lg = lanes_log2_for(nvec, min_vpl);
+#pragma unroll
+    for (int j = 0; j < kKeepOps; ++j)
+        if (b + j < e) ki[j] = P.ord_info[b + j];
+#pragma unroll
+    for (int j = 0; j < kKeepOps; ++j) {
+        if (b + j >= e) break;
+        kc[j] = __ldcg(&S.cnt[(int64_t)ki[j].x * kCntStride]);
+        const int lg = lanes_log2_for(ki[j].y, min_vpl);
+        const int32_t f = full_tiles(kc[j], lg, ipt);
+        loc[0] += kc[j];
+        loc[1] += f;
+        loc[2] += kc[j] > f * ((kScoreThreads >> lg) * ipt) ? 1 : 0;
+    }
+    for (int k = b + kKeepOps; k < e; ++k) {
+        const int4 oi = P.ord_info[k];
+        const int32_t ck = __ldcg(&S.cnt[(int64_t)oi.x * kCntStride]);
+        const int lg = lanes_log2_for(oi.y, min_vpl);
         const int32_t f = full_tiles(ck, lg, ipt);
         loc[0] += ck;
         loc[1] += f;
@@ -198,15 +210,33 @@ __device__ void layout_buckets_and_tiles(const DevProblem &P, const BucketScratc
     int32_t tf = inc[1] - loc[1] + (wid > 0 ? warp_sum[1][wid - 1] : 0);
     int32_t tt = total_full + inc[2] - loc[2] + (wid > 0 ? warp_sum[2][wid - 1] : 0);
     for (int k = b; k < e; ++k) {
-        const int32_t v = P.op_order[k];
-        const int32_t ck = __ldcg(&S.cnt[(int64_t)v * kCntStride]);
-        const int32_t nvec = (int32_t)((P.pad_off[v + 1] - P.pad_off[v]) / kVec);
+        int4 oi;
+        int32_t ck;
+        if (k - b < kKeepOps) {
+            // registers, selected without a runtime index
+            oi = ki[0], ck = kc[0];
+#pragma unroll
+            for (int j = 1; j < kKeepOps; ++j)
+                if (k - b == j) oi = ki[j], ck = kc[j];
+        } else {
+            oi = P.ord_info[k];
+            ck = __ldcg(&S.cnt[(int64_t)oi.x * kCntStride]);
+        }
+        const int32_t v = oi.x, nvec = oi.y;
         const int lg = lanes_log2_for(nvec, min_vpl);
         const int32_t per_tile = (kScoreThreads >> lg) * ipt;
+        const int4 tx = make_int4(nvec * kVec, oi.w, oi.z, 0);  // {npad, distinct, offset}
         S.op_start[v] = pos;
         int32_t j = 0;
-        for (; j + per_tile <= ck; j += per_tile) S.tiles[tf++] = make_int4(v, j, per_tile, lg);
-        if (j < ck) S.tiles[tt++] = make_int4(v, j, ck - j, tail_lanes_log2(ck - j, lg, ipt, nvec));
+        for (; j + per_tile <= ck; j += per_tile, ++tf) {
+            S.tiles[2 * tf] = make_int4(v, j, per_tile, lg);
+            S.tiles[2 * tf + 1] = tx;
+        }
+        if (j < ck) {
+            S.tiles[2 * tt] = make_int4(v, j, ck - j, tail_lanes_log2(ck - j, lg, ipt, nvec));
+            S.tiles[2 * tt + 1] = tx;
+            ++tt;
+        }
         pos += ck;
     }
     if (tid == T - 1) {
@@ -228,7 +258,6 @@ __device__ __forceinline__ void grid_barrier(unsigned long long *count, unsigned
         for (int it = 0; it < kMaxWaitTries; ++it) {
             asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(seen) : "l"(count) : "memory");
             if (seen >= target) break;
-            __nanosleep(32);
         }
         if (seen < target) atomicOr(timeout, 1ull);
     }
@@ -297,6 +326,18 @@ __global__ void __launch_bounds__(256) k_bucket(DevProblem P, int64_t n_inv, con
     __shared__ int32_t warp_sum[3][32];
     __shared__ int last;
     __shared__ CpSmem sm;
+    {
+        // one parallel round of L2 prefetches of every small array the dependent
+        // load chains below will touch (each line starts inside its array)
+        int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+        const int64_t step = (int64_t)gridDim.x * blockDim.x;
+#pragma unroll 1
+        for (int a = 0; a < kPfArrays; ++a) {
+            for (; l < P.pf_lines[a]; l += step)
+                asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(P.pf_ptr[a] + 128 * l));
+            l -= P.pf_lines[a];
+        }
+    }
     if ((int)blockIdx.x < n_cp) {
         for (int d = blockIdx.x; d < P.n_dags; d += n_cp) {
             critical_path_of_dag(P, d, topo, lvl_off, dag_lvl, sm);
@@ -485,30 +526,26 @@ __device__ __forceinline__ void score_body(const DevProblem &P, const BucketScra
     __syncthreads();
     uint32_t phase = 0, phase_d = 0;
     bool ok = true, dl_ok = true;
-    // tiles and buckets were laid out by k_bucket before its grid barrier, b_inv
-    // and b_slack after it: wait for k_bucket to complete before the first read
+    // everything k_bucket wrote (tile list, buckets, slack) is visible only after
+    // griddepcontrol.wait; the mbarrier set-up above overlaps its tail
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const long long n_tiles = (long long)S.ctrl[kCtrlTiles];
-    bool scatter_done = false;
     long long ti = blockIdx.x;
     while (ti < n_tiles) {
         unsigned long long claim = 0;
         if (tid == 0) claim = atomicAdd(&S.ctrl[kCtrlNextTile], 1ull);  // the tile after this one
-        const int4 tile = S.tiles[ti];
+        const int4 tile = S.tiles[2 * ti], tx = S.tiles[2 * ti + 1];
         const int32_t v = tile.x, j0 = tile.y, m = tile.z, lg = tile.w;
         const int L = 1 << lg;
         const int g = tid >> lg, s = tid & (L - 1);
-        const int64_t p0 = P.pad_off[v];
-        const int32_t npad = (int32_t)(P.pad_off[v + 1] - p0);
+        const int64_t p0 = tx.z;
+        const int32_t npad = tx.x;
         const int32_t *sp = P.seg_pad + (int64_t)v * (H + 1);
-        const int32_t dn = P.dlat_n[v];
+        const int32_t dn = tx.y;
         const bool dl_staged = dn <= dl_cap;
         const int32_t *dl = dl_staged ? dl_s : P.dlat + p0;
         const int nc = IPT * H;  // counts per group
         uint16_t *cg = c_s + g * nc;
-        if (!scatter_done) {
-            asm volatile("griddepcontrol.wait;" ::: "memory");
-            scatter_done = true;
-        }
         int32_t inv[IPT];
         uint32_t best[IPT];
         bool any = false;

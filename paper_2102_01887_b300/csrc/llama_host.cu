@@ -66,13 +66,17 @@ struct llama_ctx {
     bool dags_set = false;
     int32_t n_dags = 0, n_ops_dag = 0;
     DevBuf dag_op_off, row_ptr, col, slo, topo, lvl_off, dag_lvl;
+    // host copies of the DAG structure (for the packed per-DAG layout)
+    std::vector<int32_t> h_dag_op_off, h_row_ptr, h_col, h_topo, h_lvl_off, h_dag_lvl;
+    std::vector<int64_t> h_ref_gidx;
+    DevBuf dag_pack, dag_pack_off, ord_info;
 
     // profiles
     bool prof_set = false;
     int32_t n_ops = 0, max_npad = 0;
     int64_t n_cfg = 0, n_pad = 0;
     DevBuf cfg_off, hw_off, lat, cost, ref_cfg, batch, res, res_total;
-    DevBuf pad_off, seg_pad, lrb, dlat, dlat_n, rf, df, inv, fast, op_order;
+    DevBuf pad_off, seg_pad, lrb, dlat, dlat_n, rf, df, inv, fast, op_order, ref_gidx;
     int64_t mean_npad = 0;
     DevBuf ref, cp, cp_magic;
     int64_t q[LLAMA_MAX_HW] = {0};
@@ -165,6 +169,32 @@ DevProblem make_problem(const llama_ctx *c) {
     const bool pf = c->n_pad > 0 && tbl_bytes <= c->l2_bytes / 2;
     P.prefetch_rank_lines = pf ? (2 * c->n_pad + 127) / 128 : 0;
     P.prefetch_dlat_lines = pf ? (4 * c->n_pad + 127) / 128 : 0;
+    P.ref_gidx = c->ref_gidx.as<int64_t>();
+    P.ord_info = c->ord_info.as<int4>();
+    P.dag_pack = c->dag_pack.as<int32_t>();
+    P.dag_pack_off = c->dag_pack_off.as<int64_t>();
+    // arrays whose first touch starts a dependent chain: DAG structure, per-op
+    // layout and the decode tables (lat, cost, inv) when they fit the budget
+    {
+        int a = 0;
+        auto add = [&](const DevBuf &b) {
+            if (a < kPfArrays && b.p && b.bytes) {
+                P.pf_ptr[a] = static_cast<const char *>(b.p);
+                P.pf_lines[a] = (int64_t)((b.bytes + 127) / 128);
+                ++a;
+            }
+        };
+        add(c->dag_op_off); add(c->slo); add(c->row_ptr); add(c->col); add(c->topo);
+        add(c->lvl_off); add(c->dag_lvl); add(c->ref_gidx); add(c->op_order); add(c->pad_off);
+        add(c->seg_pad); add(c->dlat_n); add(c->fast); add(c->hw_off);
+        if (c->lat.bytes + c->cost.bytes + c->inv.bytes <= (size_t)c->l2_bytes / 4) {
+            add(c->lat); add(c->cost);
+        }
+        for (; a < kPfArrays; ++a) {
+            P.pf_ptr[a] = nullptr;
+            P.pf_lines[a] = 0;
+        }
+    }
     P.ref = c->ref.as<int64_t>();
     P.cp = c->cp.as<int64_t>();
     P.cp_magic = c->cp_magic.as<uint64_t>();
@@ -210,6 +240,41 @@ ContextView view_of(const llama_ctx *c) {
     return v;
 }
 
+// Per-DAG packed structure for the critical-path pass (see DevProblem::dag_pack),
+// built once both the DAGs and the profiles are known.
+int build_dag_pack(llama_ctx *c) {
+    if (!c->dags_set || !c->prof_set || c->n_ops_dag != c->n_ops) return LLAMA_OK;
+    const int32_t nd = c->n_dags;
+    std::vector<int64_t> off(nd + 1, 0);
+    std::vector<int32_t> pk;
+    for (int32_t d = 0; d < nd; ++d) {
+        off[d] = (int64_t)pk.size();
+        const int32_t lo = c->h_dag_op_off[d], hi = c->h_dag_op_off[d + 1], n = hi - lo;
+        const int32_t e_lo = c->h_row_ptr[lo], ne = c->h_row_ptr[hi] - e_lo;
+        const int32_t l_lo = c->h_dag_lvl[d], nl = c->h_dag_lvl[d + 1] - l_lo;
+        const int64_t words = 4 + (int64_t)n + (n + 1) + ne + n + (nl + 1);
+        if (n > kCpSmemOps || words > kCpPackWords) continue;  // empty: global-memory pass
+        pk.push_back(lo);
+        pk.push_back(n);
+        pk.push_back(ne);
+        pk.push_back(nl);
+        for (int32_t v = lo; v < hi; ++v) pk.push_back((int32_t)c->h_ref_gidx[v]);
+        for (int32_t v = lo; v <= hi; ++v) pk.push_back(c->h_row_ptr[v] - e_lo);
+        for (int32_t e = 0; e < ne; ++e) pk.push_back(c->h_col[e_lo + e] - lo);
+        for (int32_t v = lo; v < hi; ++v) pk.push_back(c->h_topo[v] - lo);
+        for (int32_t l = 0; l <= nl; ++l) pk.push_back(c->h_lvl_off[l_lo + l] - lo);
+    }
+    off[nd] = (int64_t)pk.size();
+    if (pk.empty()) pk.push_back(0);
+    cudaError_t e;
+    if ((e = c->dag_pack.alloc(4 * pk.size())) != cudaSuccess ||
+        (e = cudaMemcpy(c->dag_pack.p, pk.data(), 4 * pk.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = c->dag_pack_off.alloc(8 * off.size())) != cudaSuccess ||
+        (e = cudaMemcpy(c->dag_pack_off.p, off.data(), 8 * off.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return c->cuda_fail(e, "dag pack upload");
+    return LLAMA_OK;
+}
+
 int check_ready(llama_ctx *c) {
     if (!c->dags_set || !c->prof_set)
         return c->fail(LLAMA_ENOTREADY, "schedule called before llama_set_dags and llama_set_profiles");
@@ -241,7 +306,7 @@ int ensure_scratch(llama_ctx *c, int64_t n_inv) {
     }
     const int64_t nt = max_tiles(c->cap_inv, c->n_ops);
     if (c->cap_tiles < nt) {
-        LL_CUDA(c, c->tiles.alloc(sizeof(int4) * nt));
+        LL_CUDA(c, c->tiles.alloc(2 * sizeof(int4) * nt));
         c->cap_tiles = nt;
     }
     return LLAMA_OK;
@@ -275,8 +340,9 @@ int grid_for(const llama_ctx *c, int64_t n, int threads) {
 
 // The launch sequence of one scheduling call (all device pointers).
 // Shared memory of the scoring kernel: a staging chunk of latency ranks and
-// objective ranks (plus rank differences in alpha mode), then one count per
-// (invocation, backend) for every group of the CTA (at most one group per thread).
+// objective ranks (plus rank differences in alpha mode), one count per
+// (invocation, backend) for every group of the CTA (at most one group per
+// thread), then the op's distinct latencies.
 size_t score_smem_bytes(const llama_ctx *c) {
     const size_t tbl = (size_t)c->score_chunk * (c->opts.mode == LLAMA_MODE_ALPHA ? 6 : 4);
     const size_t counts = (size_t)kScoreThreads * c->ipt * c->opts.n_hw * 2;
@@ -555,8 +621,14 @@ extern "C" int llama_set_dags(llama_ctx *c, int32_t n_dags, const int32_t *dag_o
         return c->cuda_fail(e, "set_dags upload");
     c->n_dags = n_dags;
     c->n_ops_dag = n_ops;
+    c->h_dag_op_off.assign(dag_op_off, dag_op_off + n_dags + 1);
+    c->h_row_ptr.assign(row_ptr, row_ptr + n_ops + 1);
+    c->h_col.assign(col, col + n_edges);
+    c->h_topo = topo;
+    c->h_lvl_off = lvl_off;
+    c->h_dag_lvl = dag_lvl;
     c->dags_set = true;
-    return LLAMA_OK;
+    return build_dag_pack(c);
 }
 
 extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cfg_off,
@@ -601,7 +673,11 @@ extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cf
     std::stable_sort(op_order.begin(), op_order.end(), [&](int32_t a, int32_t b) {
         return pad_off[a + 1] - pad_off[a] > pad_off[b + 1] - pad_off[b];
     });
+    std::vector<int64_t> ref_gidx(n_ops);
+    for (int32_t v = 0; v < n_ops; ++v) ref_gidx[v] = cfg_off[v] + ref_cfg[v];
     const int64_t n_cfg = cfg_off[n_ops];
+    if (pad_off[n_ops] >= INT32_MAX) return c->fail(LLAMA_EINVAL, "set_profiles: padded tables too large");
+    if (n_cfg >= INT32_MAX) return c->fail(LLAMA_EINVAL, "set_profiles: more than 2^31-1 configurations");
     for (int64_t x = 0; x < n_cfg; ++x) {
         if (lat_us[x] < 1 || lat_us[x] > INT32_MAX - 1)
             return c->fail(LLAMA_EINVAL, "set_profiles: latency out of 1..INT32_MAX-1");
@@ -631,6 +707,8 @@ extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cf
         (e = up(c->pad_off, pad_off.data(), 8 * (size_t)(n_ops + 1))) != cudaSuccess ||
         (e = up(c->seg_pad, seg_pad.data(), 4 * seg_pad.size())) != cudaSuccess ||
         (e = up(c->op_order, op_order.data(), 4 * (size_t)n_ops)) != cudaSuccess ||
+        (e = up(c->ref_gidx, ref_gidx.data(), 8 * (size_t)n_ops)) != cudaSuccess ||
+        (e = c->ord_info.alloc(16 * (size_t)n_ops)) != cudaSuccess ||
         (e = c->lrb.alloc(2 * (size_t)n_pad)) != cudaSuccess ||
         (e = c->dlat.alloc(4 * (size_t)n_pad)) != cudaSuccess ||
         (e = c->dlat_n.alloc(4 * (size_t)n_ops)) != cudaSuccess ||
@@ -681,6 +759,20 @@ extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cf
                                                         c->inv.as<uint16_t>());
     LL_CUDA(c, cudaGetLastError());
     LL_CUDA(c, cudaStreamSynchronize(c->stream));
+    {
+        // bucket-order info per op: {op, vectors, padded offset, distinct latencies}
+        std::vector<int32_t> dn(n_ops);
+        LL_CUDA(c, cudaMemcpy(dn.data(), c->dlat_n.p, 4 * (size_t)n_ops, cudaMemcpyDeviceToHost));
+        std::vector<int32_t> oi(4 * (size_t)n_ops);
+        for (int32_t k2 = 0; k2 < n_ops; ++k2) {
+            const int32_t v = op_order[k2];
+            oi[4 * k2 + 0] = v;
+            oi[4 * k2 + 1] = (int32_t)((pad_off[v + 1] - pad_off[v]) / kVec);
+            oi[4 * k2 + 2] = (int32_t)pad_off[v];
+            oi[4 * k2 + 3] = dn[v];
+        }
+        LL_CUDA(c, cudaMemcpy(c->ord_info.p, oi.data(), 16 * (size_t)n_ops, cudaMemcpyHostToDevice));
+    }
 
     // scoring kernel: stage tables in chunks of at most kMaxChunk entries, one
     // persistent CTA per resident slot
@@ -689,8 +781,9 @@ extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cf
     c->score_smem = score_smem_bytes(c);
     const int rc = configure_score(c);
     if (rc) return rc;
+    c->h_ref_gidx = std::move(ref_gidx);
     c->prof_set = true;
-    return LLAMA_OK;
+    return build_dag_pack(c);
 }
 
 extern "C" int llama_set_queue(llama_ctx *c, const int64_t *q_us) {

@@ -39,7 +39,9 @@ constexpr int kScoreThreadsLog2 = 8;
 constexpr int kMaxChunk = 4096;        // table entries staged at a time by the scoring kernel
 constexpr int kMaxWaitTries = 1 << 20; // bounded mbarrier waits
 constexpr int kKeep = 4;               // invocations a counting thread keeps in registers
+constexpr int kKeepOps = 2;            // ops the layout keeps in registers per thread
 constexpr int kMaxDlatSmem = 4096;     // distinct latencies staged per op (else searched in L2)
+constexpr int kPfArrays = 16;          // arrays k_bucket prefetches into L2 at its start
 constexpr int kCntStride = 32;     // int32 slots between per-op counters: one 128-byte line each
 // control words of a call (unsigned long long each)
 constexpr int kCtrlInvalid = 0;    // invalid invocations
@@ -52,7 +54,7 @@ constexpr int kCtrlBarrier = 6;    // grid barrier of k_bucket
 constexpr int kCtrlWords = 8;
 // DAGs up to this size are staged in shared memory for the critical path
 constexpr int kCpSmemOps = 512;
-constexpr int kCpSmemEdges = 2048;
+constexpr int kCpPackWords = 5120;  // packed DAG words staged in shared memory
 
 struct DevProblem {
     int32_t n_dags, n_ops, n_hw, mode;
@@ -75,6 +77,21 @@ struct DevProblem {
     // 128-byte lines to pull into L2 before scoring (0: off): of each of lrb, rf
     // (and df), all 2*n_pad bytes long, and of dlat (4*n_pad bytes)
     int64_t prefetch_rank_lines, prefetch_dlat_lines;
+    // small per-op and per-DAG arrays (and the decode tables when they fit) that
+    // the call's dependent load chains touch first: pulled into L2 by every
+    // block of k_bucket at its start, in one parallel round
+    const char *pf_ptr[kPfArrays];
+    int64_t pf_lines[kPfArrays];  // 128-byte lines of each (0: unused)
+    const int64_t *ref_gidx;      // [n_ops] cfg_off[v] + ref_cfg[v]
+    // [n_ops] per bucket-order position k: {op = op_order[k], vectors of its padded
+    // table, its padded offset, its number of distinct latencies}
+    const int4 *ord_info;
+    // per DAG, its structure packed contiguously (local op ids): {first op, ops,
+    // edges, levels}, reference-configuration indices, successor CSR offsets,
+    // successors, ops by height above the sinks, level offsets; empty for a DAG
+    // too large for shared memory
+    const int32_t *dag_pack;
+    const int64_t *dag_pack_off;  // [n_dags+1]
     int64_t *ref;
     int64_t *cp;
     uint64_t *cp_magic;  // floor((2^64-1) / cp[v]), for exact division by cp[v]
@@ -91,7 +108,8 @@ struct BucketScratch {
     int32_t *b_inv;           // [n_inv]     invocation at each bucket position
     int32_t *b_slack;         // [n_inv*H]   slack per invocation and backend
     int64_t *rbase;           // [n_inv]     target - elapsed time of each invocation
-    int4 *tiles;              // [max_tiles] scoring tiles {op, j0, m, lanes_log2}
+    int4 *tiles;              // [2*max_tiles] scoring tiles: {op, j0, m, lanes_log2},
+                              // {padded entries, distinct latencies, padded offset, 0}
 };
 
 // floor(n / d) for n < 2^62 and d >= 1, given m = floor((2^64 - 1) / d): the high

@@ -9,7 +9,7 @@
 // loop that cannot absorb the implicit synchronisation of cudaMalloc/cudaFree,
 // or code that runs where the CUDA allocator must not be entered at all.
 // This entry point uses instead one fixed, file-scope device array: every GPU
-// that loads the library holds it (about 5 MB) until the process exits.  The
+// that loads the library holds it (about 6 MB) until the process exits.  The
 // caller still passes inputs and outputs; the context's tables were copied to
 // the device earlier by llama_set_profiles.
 //
@@ -44,7 +44,7 @@ constexpr size_t kBInvOff = align256(kSlotOff + 4 * (size_t)LLAMA_STATIC_MAX_INV
 constexpr size_t kBSlackOff = align256(kBInvOff + 4 * (size_t)LLAMA_STATIC_MAX_INV);
 constexpr size_t kRbaseOff = align256(kBSlackOff + 4 * (size_t)LLAMA_STATIC_MAX_INV * LLAMA_MAX_HW);
 constexpr size_t kTilesOff = align256(kRbaseOff + 8 * (size_t)LLAMA_STATIC_MAX_INV);
-constexpr size_t kScratchBytes = align256(kTilesOff + 16 * kMaxTiles);
+constexpr size_t kScratchBytes = align256(kTilesOff + 32 * kMaxTiles);
 
 constexpr int kMaxDevices = 64;
 
