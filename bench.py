@@ -71,12 +71,34 @@ def make_workload(name: str, rank: int):
     return fn(inv_seed=None if rank == 0 else 1000 + rank)
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest of the ranks' values (the job is as slow as its slowest rank)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, n_inv: int, steps: int, total_s: float) -> float:
+    """Whole-job invocations/s: every rank schedules its own n_inv per step."""
+    return world * n_inv * steps / total_s
+
+
 def workload_config(name, p, inv, mode, scores):
     return {"workload": name, "dags": p.n_dags, "ops": p.n_ops,
             "configs_per_op": (int(np.diff(p.cfg_off).min()), int(np.diff(p.cfg_off).max())),
             "invocations": inv.n, "backends": p.n_hw, "objective": mode,
             "scores_per_step": int(scores), "table_bytes": p.table_bytes(),
             "l2": "flushed before every timed step (256 MiB write)", "cuda_graph": True}
+
+
+def padded_sizes(p) -> np.ndarray:
+    """Padded table entries per op: every backend segment rounded up to 8 entries."""
+    hw = p.hw_off.reshape(p.n_ops, p.n_hw + 1)
+    return ((np.diff(hw, axis=1) + 7) // 8 * 8).sum(axis=1)
 
 
 def scores_of(p, inv) -> int:
@@ -260,11 +282,8 @@ def main():
     step_ms = np.asarray([s.elapsed_time(e) for s, e in zip(starts, ends)])
     phase_ms = np.asarray([[t[j].elapsed_time(t[j + 1]) for j in range(len(L.TRACE_PHASES))]
                            for t in traces])
-    total_s = float(step_ms.sum()) / 1e3
+    total_s = max_over_ranks(float(step_ms.sum()) / 1e3, world, dev)
     if world > 1:
-        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
         dist.barrier()
     launches = args.steps * L.llama_last_launch_count(ctx)  # pass A's kernels
 
@@ -290,12 +309,8 @@ def main():
             L.llama_schedule(ctx, np_dag, np_opl, np_st, inv.now_us, np_out)
             wall.append(time.perf_counter() - t0)
         assert (np_out["cfg"] == got["cfg"]).all()
-        e2e_s = sum(wall)
-        if world > 1:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": world * inv.n * args.steps / e2e_s, "unit": UNIT,
+        e2e_s = max_over_ranks(sum(wall), world, dev)
+        e2e = {"value": job_throughput(world, inv.n, args.steps, e2e_s), "unit": UNIT,
                "h2d_bytes_per_step": int(inv.n * (4 + 4 + 8)),
                "d2h_bytes_per_step": int(inv.n * 24 + 8),
                "p50_call_us": 1e6 * float(np.median(wall)), "p99_call_us": 1e6 * float(np.percentile(wall, 99))}
@@ -308,15 +323,39 @@ def main():
     peaks, peak_src = measured_peaks()
     clk = clocks.summary()
     score_ms = float(phase_ms[:, -1].mean())
-    # ALU roofline of the scoring kernel: tables are staged once per tile and
-    # reused by all of that tile's invocations, so the scan is bound by the
-    # integer ALU pipe, not HBM.
+    # Roofline of the scoring kernel.  When the encoded tables fit in L2 they are
+    # staged once per tile and reused by all of the tile's invocations, so the
+    # scan is bound by the integer ALU pipe; when they do not (tables streamed
+    # from HBM, few invocations per op) it is bound by HBM bandwidth.
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    l2_bytes = torch.cuda.get_device_properties(dev).L2_cache_size
     sm_mhz = float(peaks.get("sm_max_mhz", 2032.0))
-    peak_tops = sm_count * ALU_LANES_PER_SM * sm_mhz * 1e6 / 1e12
-    ops_per_score = ALU_OPS_PER_SCORE[args.mode]
-    achieved_tops = ops_per_score * scores / (score_ms / 1e3) / 1e12
-    value = world * inv.n * args.steps / total_s
+    npad = padded_sizes(p)
+    gop = p.dag_op_off[inv.dag] + inv.op_local
+    touched = np.unique(gop)
+    tbl_per_entry = 6 if args.mode == "alpha" else 4
+    if tbl_per_entry * int(npad.sum()) + 4 * int(npad.sum()) > l2_bytes // 2:
+        algo_bytes = tbl_per_entry * int(npad[touched].sum()) + inv.n * (4 + 12 + 24)
+        achieved = algo_bytes / (score_ms / 1e3) / 1e9
+        roofline = {"bound": "hbm", "kernel": "k_score", "achieved": achieved,
+                    "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                    "frac": achieved / float(peaks["hbm_gbs"]), "traffic": None,
+                    "peak_source": f"{peak_src} HBM copy bandwidth",
+                    "algorithmic_bytes": algo_bytes,
+                    "bytes_note": f"{tbl_per_entry} B per padded table entry of each op with invocations "
+                                  "(latency rank + objective rank(s)), once, plus 40 B per invocation"}
+    else:
+        peak_tops = sm_count * ALU_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+        ops_per_score = ALU_OPS_PER_SCORE[args.mode]
+        achieved = ops_per_score * scores / (score_ms / 1e3) / 1e12
+        roofline = {"bound": "alu", "kernel": "k_score", "achieved": achieved,
+                    "peak": peak_tops, "unit": "T ALU-ops/s", "frac": achieved / peak_tops,
+                    "traffic": None,
+                    "peak_source": f"{sm_count} SMs x {ALU_LANES_PER_SM} integer ALU lanes x "
+                                   f"{sm_mhz:.0f} MHz ({peak_src} max SM clock)",
+                    "alu_ops_per_score": ops_per_score,
+                    "scores_per_s_ceiling": peak_tops * 1e12 / ops_per_score}
+    value = job_throughput(world, inv.n, args.steps, total_s)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         times = cpu_baseline(p, inv, args.mode, args.cpu_seconds)
@@ -341,18 +380,12 @@ def main():
                                 "p99": 1e3 * float(np.percentile(step_ms, 99))},
         "scan_effective": {"gbs": SCAN_BYTES_PER_SCORE * scores / (score_ms / 1e3) / 1e9,
                            "hbm_frac": SCAN_BYTES_PER_SCORE * scores / (score_ms / 1e3) / 1e9 / peaks["hbm_gbs"],
-                           "note": "12 B per scored configuration / scoring-kernel time; tables are "
-                                   "reused across invocations from shared memory, so this exceeds HBM"},
+                           "note": "12 B per scored configuration / scoring-kernel time; where tables are "
+                                   "reused across invocations from shared memory this exceeds HBM"},
         "kernel_ms": {n: float(phase_ms[:, j].mean()) for j, n in enumerate(L.TRACE_PHASES)},
         "kernel_ms_note": "per-kernel event times from a second pass of the same steps with trace "
                           "events (direct launches, no overlap between the two kernels)",
-        "roofline": {"bound": "alu", "kernel": "k_score", "achieved": achieved_tops,
-                     "peak": peak_tops, "unit": "T ALU-ops/s", "frac": achieved_tops / peak_tops,
-                     "traffic": None,
-                     "peak_source": f"{sm_count} SMs x {ALU_LANES_PER_SM} integer ALU lanes x {sm_mhz:.0f} MHz "
-                                    f"({peak_src} max SM clock)",
-                     "alu_ops_per_score": ops_per_score,
-                     "scores_per_s_ceiling": peak_tops * 1e12 / ops_per_score},
+        "roofline": roofline,
         "schedule_trials": ([{k: t[k] for k in ("lanes_min_vectors", "inv_per_thread", "ms")}
                              for t in tuning["trials"]] if tuning else None),
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,

@@ -149,40 +149,32 @@ __device__ __forceinline__ int tail_lanes_log2(int32_t m, int lg, int ipt, int32
     return lg;
 }
 
-// Bucket and tile layout, by one block once the counts are final: exclusive
-// prefixes, in op_order, of the bucket sizes, the full tiles and the tail
-// tiles; every op's full tiles come first in the tile list, the tails after.
-__device__ void layout_buckets_and_tiles(const DevProblem &P, const BucketScratch &S, int32_t min_vpl,
-                                         int32_t ipt, int32_t (*warp_sum)[32]) {
-    const int n = P.n_ops, T = blockDim.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int per = (n + T - 1) / T;
-    const int b = min(n, tid * per), e = min(n, b + per);
-    // the first kKeepOps ops of this thread's run stay in registers for the second pass
-    int4 ki[kKeepOps];
+// Bucket and tile layout once the counts are final, spread over the counting
+// blocks.  Block b of nb owns a contiguous run of ops in the order P.op_order
+// (largest tables first); each thread a contiguous run of those.  Positions are
+// exclusive prefixes, in that order, of the bucket sizes, of the full tiles and
+// of the tail tiles; every op's full tiles come first in the tile list, the
+// tails after them.
+struct LayoutRun {
+    int32_t kb, ke;          // this thread's ops: op_order[kb .. ke)
+    int4 ki[kKeepOps];       // the first kKeepOps of them stay in registers
     int32_t kc[kKeepOps];
-    int32_t loc[3] = {0, 0, 0};
-#pragma unroll
-    for (int j = 0; j < kKeepOps; ++j)
-        if (b + j < e) ki[j] = P.ord_info[b + j];
-#pragma unroll
-    for (int j = 0; j < kKeepOps; ++j) {
-        if (b + j >= e) break;
-        kc[j] = __ldcg(&S.cnt[(int64_t)ki[j].x * kCntStride]);
-        const int lg = lanes_log2_for(ki[j].y, min_vpl);
-        const int32_t f = full_tiles(kc[j], lg, ipt);
-        loc[0] += kc[j];
-        loc[1] += f;
-        loc[2] += kc[j] > f * ((kScoreThreads >> lg) * ipt) ? 1 : 0;
-    }
-    for (int k = b + kKeepOps; k < e; ++k) {
-        const int4 oi = P.ord_info[k];
-        const int32_t ck = __ldcg(&S.cnt[(int64_t)oi.x * kCntStride]);
-        const int lg = lanes_log2_for(oi.y, min_vpl);
-        const int32_t f = full_tiles(ck, lg, ipt);
-        loc[0] += ck;
-        loc[1] += f;
-        loc[2] += ck > f * ((kScoreThreads >> lg) * ipt) ? 1 : 0;
-    }
+    int32_t loc[3];          // bucket positions, full tiles, tail tiles of the run
+    int32_t excl[3];         // their exclusive prefixes inside the block
+};
+
+__device__ __forceinline__ void op_tiles(int32_t ck, int32_t nvec, int32_t min_vpl, int32_t ipt,
+                                         int32_t &full, int32_t &tail) {
+    const int lg = lanes_log2_for(nvec, min_vpl);
+    full = full_tiles(ck, lg, ipt);
+    tail = ck > full * ((kScoreThreads >> lg) * ipt) ? 1 : 0;
+}
+
+// Inclusive block-wide sums of three values; returns the exclusive prefixes in
+// excl[] and the block totals in tot[].
+__device__ __forceinline__ void block_scan3(const int32_t loc[3], int32_t excl[3], int32_t tot[3],
+                                            int32_t (*warp_sum)[32]) {
+    const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     int32_t inc[3] = {loc[0], loc[1], loc[2]};
     for (int o = 1; o < 32; o <<= 1) {
         for (int a = 0; a < 3; ++a) {
@@ -205,19 +197,85 @@ __device__ void layout_buckets_and_tiles(const DevProblem &P, const BucketScratc
         }
     }
     __syncthreads();
-    const int32_t total_full = warp_sum[1][(T >> 5) - 1];
-    int32_t pos = inc[0] - loc[0] + (wid > 0 ? warp_sum[0][wid - 1] : 0);
-    int32_t tf = inc[1] - loc[1] + (wid > 0 ? warp_sum[1][wid - 1] : 0);
-    int32_t tt = total_full + inc[2] - loc[2] + (wid > 0 ? warp_sum[2][wid - 1] : 0);
-    for (int k = b; k < e; ++k) {
+    for (int a = 0; a < 3; ++a) {
+        excl[a] = inc[a] - loc[a] + (wid > 0 ? warp_sum[a][wid - 1] : 0);
+        tot[a] = warp_sum[a][(T >> 5) - 1];
+    }
+    __syncthreads();  // warp_sum is reused by the caller
+}
+
+// Phase 1: this block's ops, summed; the block's totals go to S.blk[b].
+__device__ void layout_sums(const DevProblem &P, const BucketScratch &S, int32_t b, int32_t nb,
+                            int32_t min_vpl, int32_t ipt, LayoutRun &R, int32_t (*warp_sum)[32]) {
+    const int n = P.n_ops, T = blockDim.x, tid = threadIdx.x;
+    const int32_t per_blk = (n + nb - 1) / nb;
+    const int32_t k0 = min(n, b * per_blk), k1 = min(n, k0 + per_blk);
+    const int32_t per = (k1 - k0 + T - 1) / T;
+    R.kb = min(k1, k0 + tid * per);
+    R.ke = min(k1, R.kb + per);
+    R.loc[0] = R.loc[1] = R.loc[2] = 0;
+#pragma unroll
+    for (int j = 0; j < kKeepOps; ++j)
+        if (R.kb + j < R.ke) R.ki[j] = P.ord_info[R.kb + j];
+#pragma unroll
+    for (int j = 0; j < kKeepOps; ++j)
+        if (R.kb + j < R.ke) R.kc[j] = __ldcg(&S.cnt[(int64_t)R.ki[j].x * kCntStride]);
+#pragma unroll
+    for (int j = 0; j < kKeepOps; ++j) {
+        if (R.kb + j >= R.ke) break;
+        int32_t f, t;
+        op_tiles(R.kc[j], R.ki[j].y, min_vpl, ipt, f, t);
+        R.loc[0] += R.kc[j];
+        R.loc[1] += f;
+        R.loc[2] += t;
+    }
+    for (int k = R.kb + kKeepOps; k < R.ke; ++k) {
+        const int4 oi = P.ord_info[k];
+        const int32_t ck = __ldcg(&S.cnt[(int64_t)oi.x * kCntStride]);
+        int32_t f, t;
+        op_tiles(ck, oi.y, min_vpl, ipt, f, t);
+        R.loc[0] += ck;
+        R.loc[1] += f;
+        R.loc[2] += t;
+    }
+    int32_t tot[3];
+    block_scan3(R.loc, R.excl, tot, warp_sum);
+    if (tid == 0) S.blk[b] = make_int4(tot[0], tot[1], tot[2], 0);
+}
+
+// Phase 2 (after every counting block's sums are visible): offsets of this
+// block from the sums of the blocks before it, then the buckets and tiles.
+__device__ void layout_write(const DevProblem &P, const BucketScratch &S, int32_t b, int32_t nb,
+                             int32_t min_vpl, int32_t ipt, const LayoutRun &R, int32_t (*warp_sum)[32]) {
+    const int T = blockDim.x, tid = threadIdx.x;
+    // before[0..2]: sums of blocks < b; before[3]: full tiles of all blocks
+    int32_t acc[4] = {0, 0, 0, 0};
+    for (int k = tid; k < nb; k += T) {
+        const int4 t = __ldcg(&S.blk[k]);
+        if (k < b) acc[0] += t.x, acc[1] += t.y, acc[2] += t.z;
+        acc[3] += t.y;
+    }
+    for (int a = 0; a < 4; ++a)
+        for (int o = 16; o > 0; o >>= 1) acc[a] += __shfl_xor_sync(0xffffffffu, acc[a], o);
+    __shared__ int32_t red[4][32];
+    if ((tid & 31) == 0)
+        for (int a = 0; a < 4; ++a) red[a][tid >> 5] = acc[a];
+    __syncthreads();
+    int32_t before[4] = {0, 0, 0, 0};
+    for (int w = 0; w < (T >> 5); ++w)
+        for (int a = 0; a < 4; ++a) before[a] += red[a][w];
+    int32_t pos = before[0] + R.excl[0];
+    int32_t tf = before[1] + R.excl[1];
+    int32_t tt = before[3] + before[2] + R.excl[2];
+    for (int k = R.kb; k < R.ke; ++k) {
         int4 oi;
         int32_t ck;
-        if (k - b < kKeepOps) {
+        if (k - R.kb < kKeepOps) {
             // registers, selected without a runtime index
-            oi = ki[0], ck = kc[0];
+            oi = R.ki[0], ck = R.kc[0];
 #pragma unroll
             for (int j = 1; j < kKeepOps; ++j)
-                if (k - b == j) oi = ki[j], ck = kc[j];
+                if (k - R.kb == j) oi = R.ki[j], ck = R.kc[j];
         } else {
             oi = P.ord_info[k];
             ck = __ldcg(&S.cnt[(int64_t)oi.x * kCntStride]);
@@ -239,7 +297,8 @@ __device__ void layout_buckets_and_tiles(const DevProblem &P, const BucketScratc
         }
         pos += ck;
     }
-    if (tid == T - 1) {
+    if (b == nb - 1 && tid == T - 1) {
+        // the last thread of the last block ends both prefixes
         S.ctrl[kCtrlPositions] = (unsigned long long)pos;
         S.ctrl[kCtrlTiles] = (unsigned long long)tt;
     }
@@ -310,11 +369,13 @@ __device__ __forceinline__ void scatter_invocation(const DevProblem &P, const Bu
 //  1. blocks [0, n_cp) compute the critical paths of DAGs b, b + n_cp, ...; the
 //     other blocks validate invocations, count them per op (one counter per
 //     128-byte line, so concurrent atomics on different ops never share a
-//     line) and prefetch the encoded tables into L2; the last counting block
-//     lays out the buckets and the scoring tiles, ops in the order P.op_order
-//     (largest tables first): every op's full tiles first, then the tails;
-//  2. grid barrier;
-//  3. the counting blocks place their invocations in their buckets and
+//     line) and prefetch the encoded tables into L2;
+//  2. the counting blocks lay out the buckets and the scoring tiles, ops in
+//     the order P.op_order (largest tables first), every op's full tiles
+//     first, then the tails: per-block sums, a barrier of the counting
+//     blocks, prefixes over the blocks and the writes;
+//  3. grid barrier;
+//  4. the counting blocks place their invocations in their buckets and
 //     compute their slack for every backend (Algorithm 1 through the critical
 //     path).
 __global__ void __launch_bounds__(256) k_bucket(DevProblem P, int64_t n_inv, const int32_t *dag,
@@ -324,7 +385,6 @@ __global__ void __launch_bounds__(256) k_bucket(DevProblem P, int64_t n_inv, con
                                                 const int32_t *dag_lvl, int32_t min_vpl, int32_t ipt,
                                                 int32_t n_cp) {
     __shared__ int32_t warp_sum[3][32];
-    __shared__ int last;
     __shared__ CpSmem sm;
     {
         // one parallel round of L2 prefetches of every small array the dependent
@@ -380,16 +440,14 @@ __global__ void __launch_bounds__(256) k_bucket(DevProblem P, int64_t n_inv, con
             asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(a));
         }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        last = atomicAdd(&S.ctrl[kCtrlTicket], 1ull) == (unsigned long long)(nb - 1);
-    }
-    __syncthreads();
-    if (last) {
-        __threadfence();
-        layout_buckets_and_tiles(P, S, min_vpl, ipt, warp_sum);
-    }
+    // the counting blocks lay out the buckets and tiles between two barriers of
+    // their own (the critical-path blocks do not take part)
+    const int32_t cb = (int32_t)(blockIdx.x - n_cp);
+    grid_barrier(&S.ctrl[kCtrlCountBarrier], (unsigned long long)nb, &S.ctrl[kCtrlTimeout]);
+    LayoutRun R;
+    layout_sums(P, S, cb, (int32_t)nb, min_vpl, ipt, R, warp_sum);
+    grid_barrier(&S.ctrl[kCtrlCountBarrier], 2ull * (unsigned long long)nb, &S.ctrl[kCtrlTimeout]);
+    layout_write(P, S, cb, (int32_t)nb, min_vpl, ipt, R, warp_sum);
     grid_barrier(&S.ctrl[kCtrlBarrier], gridDim.x, &S.ctrl[kCtrlTimeout]);
 
     // let the scoring kernel start staging its tables while the scatter runs
@@ -583,15 +641,54 @@ __device__ __forceinline__ void score_body(const DevProblem &P, const BucketScra
                 if (!mbar_wait(bar_d, phase_d)) dl_ok = false;
                 phase_d ^= 1u;
             }
-            if (c0 == 0 && any && dl_ok) {
-                // while the first chunk lands: the lanes of a group share the
-                // searches for c(u, h), one per invocation u and segment h
-                for (int t = s; t < nc; t += L) {
-                    const int u = t / H, h = t - u * H;
-                    int32_t iu = inv[0];  // inv[u] without a runtime index into registers
+            if (c0 == 0 && dl_ok) {
+                // while the first chunk lands: the counts c(u, h) of distinct
+                // latencies below each slack, one per invocation u and segment h
+                if (dl_staged) {
+                    // from shared memory: the lanes of a group share the searches
+                    if (any) {
+                        for (int t = s; t < nc; t += L) {
+                            const int u = t / H, h = t - u * H;
+                            int32_t iu = inv[0];  // inv[u] without a runtime index into registers
 #pragma unroll
-                    for (int w = 1; w < IPT; ++w) iu = u == w ? inv[w] : iu;
-                    cg[t] = iu >= 0 ? (uint16_t)count_below(dl, dn, S.b_slack[(int64_t)iu * H + h]) : 0;
+                            for (int w = 1; w < IPT; ++w) iu = u == w ? inv[w] : iu;
+                            cg[t] = iu >= 0 ? (uint16_t)count_below(dl, dn, S.b_slack[(int64_t)iu * H + h]) : 0;
+                        }
+                    }
+                } else {
+                    // from global memory: each search is shared by up to 32 lanes
+                    // (a (G+1)-ary search, a few dependent rounds instead of log2 dn)
+                    const int G = L < 32 ? L : 32, W = L > 32 ? (L >> 5) : 1, sw = s >> 5, gl = s & (G - 1);
+                    const int gbase = (tid & 31) & ~(G - 1);
+                    const uint32_t gmask = G == 32 ? 0xFFFFFFFFu : ((1u << G) - 1u);
+                    for (int t0 = 0; t0 < nc; t0 += W) {
+                        const int t = t0 + sw, u = t / H, h = t - u * H;
+                        int32_t iu = inv[0];
+#pragma unroll
+                        for (int w = 1; w < IPT; ++w) iu = u == w ? inv[w] : iu;
+                        const bool act = t < nc && iu >= 0;
+                        const int32_t sl = act ? S.b_slack[(int64_t)iu * H + h] : 0;
+                        int32_t lo = 0, hi = act ? dn : 0;  // lo <= count <= hi
+                        while (__any_sync(0xFFFFFFFFu, hi > lo)) {
+                            const int32_t n = hi - lo;
+                            const bool exact = n <= G;
+                            const int32_t pos = exact ? lo + gl : lo + (int32_t)(((int64_t)(gl + 1) * n) / (G + 1));
+                            const bool pred = n > 0 && (!exact || gl < n) && __ldg(dl + pos) < sl;
+                            const int32_t c = __popc((__ballot_sync(0xFFFFFFFFu, pred) >> gbase) & gmask);
+                            if (n > 0) {
+                                if (exact) {
+                                    lo += c;
+                                    hi = lo;
+                                } else {
+                                    const int32_t nlo = c > 0 ? lo + (int32_t)(((int64_t)c * n) / (G + 1)) + 1 : lo;
+                                    const int32_t nhi = c < G ? lo + (int32_t)(((int64_t)(c + 1) * n) / (G + 1)) : hi;
+                                    lo = nlo;
+                                    hi = nhi;
+                                }
+                            }
+                        }
+                        if (act && gl == 0) cg[t] = (uint16_t)lo;
+                    }
                 }
             }
             // every thread must agree before any leaves the barrier sequence

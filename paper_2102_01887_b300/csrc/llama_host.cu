@@ -208,6 +208,7 @@ BucketScratch make_scratch(const llama_ctx *c) {
     BucketScratch S{};
     S.cnt = c->cnt.as<int32_t>();
     S.ctrl = c->ctrl.as<unsigned long long>();
+    S.blk = reinterpret_cast<int4 *>(S.ctrl + kCtrlWords);
     S.op_start = c->op_start.as<int32_t>();
     S.gop = c->gop.as<int32_t>();
     S.slot = c->slot.as<int32_t>();
@@ -289,7 +290,7 @@ int ensure_scratch(llama_ctx *c, int64_t n_inv) {
     if (c->cap_ops < c->n_ops + 1) {
         const int32_t n = c->n_ops + 1;
         LL_CUDA(c, c->cnt.alloc(sizeof(int32_t) * kCntStride * n));
-        LL_CUDA(c, c->ctrl.alloc(sizeof(unsigned long long) * kCtrlWords));
+        LL_CUDA(c, c->ctrl.alloc(sizeof(unsigned long long) * kCtrlWords + sizeof(int4) * kMaxBucketBlocks));
         LL_CUDA(c, c->op_start.alloc(sizeof(int32_t) * n));
         c->cap_ops = n;
         c->cap_tiles = 0;
@@ -503,7 +504,7 @@ extern "C" int llama_create(llama_ctx **out, const llama_opts *opts) {
         llama_destroy(c);
         return LLAMA_ECUDA;
     }
-    c->bucket_max_blocks = nb * c->num_sms;
+    c->bucket_max_blocks = std::min(nb * c->num_sms, kMaxBucketBlocks);
     *out = c;
     return LLAMA_OK;
 }
@@ -772,12 +773,17 @@ extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cf
             oi[4 * k2 + 3] = dn[v];
         }
         LL_CUDA(c, cudaMemcpy(c->ord_info.p, oi.data(), 16 * (size_t)n_ops, cudaMemcpyHostToDevice));
+        // shared-memory room for the distinct latencies of the largest op whose
+        // list fits kMaxDlatSmem entries (none: every op searches global memory)
+        int32_t cap = 0;
+        for (int32_t v = 0; v < n_ops; ++v)
+            if (dn[v] <= kMaxDlatSmem) cap = std::max(cap, dn[v]);
+        c->dlat_cap = (cap + 3) / 4 * 4;
     }
 
     // scoring kernel: stage tables in chunks of at most kMaxChunk entries, one
     // persistent CTA per resident slot
     c->score_chunk = std::min<int32_t>(max_npad, kMaxChunk);
-    c->dlat_cap = std::min<int32_t>(max_npad, kMaxDlatSmem);
     c->score_smem = score_smem_bytes(c);
     const int rc = configure_score(c);
     if (rc) return rc;

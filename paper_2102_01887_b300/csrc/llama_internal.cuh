@@ -45,13 +45,15 @@ constexpr int kPfArrays = 16;          // arrays k_bucket prefetches into L2 at 
 constexpr int kCntStride = 32;     // int32 slots between per-op counters: one 128-byte line each
 // control words of a call (unsigned long long each)
 constexpr int kCtrlInvalid = 0;    // invalid invocations
-constexpr int kCtrlTicket = 1;     // blocks of k_prepare that have finished
+constexpr int kCtrlCountBarrier = 1;  // grid barrier of k_bucket's counting blocks
 constexpr int kCtrlPositions = 2;  // bucket positions laid out
 constexpr int kCtrlTiles = 3;      // scoring tiles laid out
 constexpr int kCtrlTimeout = 4;    // nonzero: a bounded device wait gave up
 constexpr int kCtrlNextTile = 5;   // dynamic tile counter of the scoring kernel
 constexpr int kCtrlBarrier = 6;    // grid barrier of k_bucket
 constexpr int kCtrlWords = 8;
+// k_bucket's grid never exceeds this many blocks (per-block layout sums)
+constexpr int kMaxBucketBlocks = 4096;
 // DAGs up to this size are staged in shared memory for the critical path
 constexpr int kCpSmemOps = 512;
 constexpr int kCpPackWords = 5120;  // packed DAG words staged in shared memory
@@ -102,6 +104,8 @@ struct DevProblem {
 struct BucketScratch {
     int32_t *cnt;             // [n_ops*kCntStride] invocations per op (zeroed before each call)
     unsigned long long *ctrl; // [kCtrlWords] control words (zeroed before each call)
+    int4 *blk;                // [kMaxBucketBlocks] per counting block: bucket positions,
+                              // full tiles and tail tiles of its ops (written each call)
     int32_t *op_start;        // [n_ops]     first bucket position of each op
     int32_t *gop;             // [n_inv]     global op of each invocation, -1 if invalid
     int32_t *slot;            // [n_inv]     rank of the invocation inside its op's bucket

@@ -37,7 +37,7 @@ constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t kMaxTiles = (size_t)LLAMA_STATIC_MAX_INV + (size_t)LLAMA_STATIC_MAX_OPS;
 constexpr size_t kCntOff = 0;
 constexpr size_t kCtrlOff = align256(kCntOff + 4 * (size_t)kCntStride * LLAMA_STATIC_MAX_OPS);
-constexpr size_t kOpStartOff = align256(kCtrlOff + 8 * (size_t)kCtrlWords);
+constexpr size_t kOpStartOff = align256(kCtrlOff + 8 * (size_t)kCtrlWords + 16 * (size_t)kMaxBucketBlocks);
 constexpr size_t kGopOff = align256(kOpStartOff + 4 * (size_t)(LLAMA_STATIC_MAX_OPS + 1));
 constexpr size_t kSlotOff = align256(kGopOff + 4 * (size_t)LLAMA_STATIC_MAX_INV);
 constexpr size_t kBInvOff = align256(kSlotOff + 4 * (size_t)LLAMA_STATIC_MAX_INV);
@@ -118,6 +118,7 @@ extern "C" int llama_schedule_static(llama_ctx *c, int64_t n_inv, const int32_t 
     BucketScratch S{};
     S.cnt = reinterpret_cast<int32_t *>(base + kCntOff);
     S.ctrl = reinterpret_cast<unsigned long long *>(base + kCtrlOff);
+    S.blk = reinterpret_cast<int4 *>(base + kCtrlOff + 8 * (size_t)kCtrlWords);
     S.op_start = reinterpret_cast<int32_t *>(base + kOpStartOff);
     S.gop = reinterpret_cast<int32_t *>(base + kGopOff);
     S.slot = reinterpret_cast<int32_t *>(base + kSlotOff);

@@ -320,12 +320,12 @@ def batched_large(seed: int = 3, n_inv: int = 32_768, n_dags: int = 512,
     """512 DAGs of 5-60 ops, every op with 8,192 configurations (tables >> L2).
 
     Few invocations per operation, so each table is streamed from HBM about
-    once per call.  Batch and resource columns are omitted (cost-first mode).
+    once per call.
     """
     rng = np.random.default_rng(seed)
     dags = [_random_dag_edges(rng, int(rng.integers(5, 61))) for _ in range(n_dags)]
     n_ops = sum(len(d) for d in dags)
-    p = _assemble(rng, dags, np.full(n_ops, 8192), _log_uniform_slo(rng), knobs=False, q_max=100_000)
+    p = _assemble(rng, dags, np.full(n_ops, 8192), _log_uniform_slo(rng), q_max=100_000)
     inv_rng = rng if inv_seed is None else np.random.default_rng(inv_seed)
     return p, _invocations(inv_rng, p, n_inv, 10**11)
 

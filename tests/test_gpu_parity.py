@@ -322,3 +322,18 @@ def test_tunings_change_no_result(L, tuning):
                 got, rc = s.schedule(case)
             assert rc == L.OK
             assert_same(got, exp, f"tuning {tuning} mode {mode}")
+
+
+@pytest.fixture(scope="module")
+def batched_large():
+    return W.batched_large()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("mode,alpha", [(0, (1, 1)), (1, (3, 2))])
+def test_batched_large_full(L, batched_large, mode, alpha):
+    # every op at 8,192 configurations (1.6 GB of tables, far beyond L2), about two
+    # invocations per op: the HBM-streaming regime, chunked staging, wide groups
+    p, inv = batched_large
+    got, exp = run_both(L, p, inv, mode=mode, alpha=alpha)
+    assert_same(got, exp)
