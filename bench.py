@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch kernels directly, no CUDA graph")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default scoring schedule")
+    ap.add_argument("--n-dags", type=int, default=None, help="DAG count of the batched workloads")
+    ap.add_argument("--n-inv", type=int, default=None, help="invocations per step (default: the workload's)")
+    ap.add_argument("--tuning", default=None,
+                    help="fixed scoring schedule 'lanes_min_vectors,inv_per_thread,chunk' (no autotuning)")
     return ap.parse_args()
 
 
@@ -62,13 +66,18 @@ def dist_env():
     return world, rank, local
 
 
-def make_workload(name: str, rank: int):
+def make_workload(name: str, rank: int, n_dags=None, n_inv=None):
     from paper_2102_01887_b300 import workloads as W
     if name == "tiny":
         return W.tiny()
     fn = W.WORKLOADS[name]
+    kw = {}
+    if n_dags is not None:
+        kw["n_dags"] = n_dags
+    if n_inv is not None:
+        kw["n_inv"] = n_inv
     # rank 0 draws exactly the named workload; other ranks their own invocations
-    return fn(inv_seed=None if rank == 0 else 1000 + rank)
+    return fn(inv_seed=None if rank == 0 else 1000 + rank, **kw)
 
 
 def max_over_ranks(x: float, world: int, device) -> float:
@@ -189,7 +198,7 @@ def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return
-    p, inv = make_workload(args.workload, 0)
+    p, inv = make_workload(args.workload, 0, args.n_dags, args.n_inv)
     scores = scores_of(p, inv)
     cpu_baseline(p, inv, args.mode, 0, steps=max(1, args.warmup))
     times = cpu_baseline(p, inv, args.mode, 0, steps=args.steps)
@@ -223,7 +232,7 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     B.build()
-    p, inv = make_workload(args.workload, rank)
+    p, inv = make_workload(args.workload, rank, args.n_dags, args.n_inv)
     mode = L.MODE_ALPHA if args.mode == "alpha" else L.MODE_COST_FIRST
     sched = L.Scheduler(p, mode=mode, alpha=(3, 2), device=local, use_graph=not args.no_graph)
     ctx = sched.ctx
@@ -241,10 +250,17 @@ def main():
         L.llama_schedule_async(ctx, dag, opl, st, inv.now_us, out, stream)
 
     tuning = None
-    if not args.no_autotune:
-        # choose the scoring schedule on this batch before anything is timed
+    if args.tuning:
+        lmv, ipt, chunk = (int(x) for x in args.tuning.split(","))
+        L.llama_set_tuning(ctx, lmv, ipt, chunk)
+        tuning = {"best": {"lanes_min_vectors": lmv, "inv_per_thread": ipt, "chunk": chunk}, "trials": []}
+    elif not args.no_autotune:
+        # choose the scoring schedule on this batch before anything is timed;
+        # ops with more than 4,096 configurations may also be staged whole
         from paper_2102_01887_b300.autotune import autotune
-        tuning = autotune(ctx, dag, opl, st, inv.now_us, out, stream, flush)
+        big = int(np.diff(p.cfg_off).max()) > 4096
+        tuning = autotune(ctx, dag, opl, st, inv.now_us, out, stream, flush,
+                          chunks=(0, 8192) if big else (0,))
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -386,8 +402,8 @@ def main():
         "kernel_ms_note": "per-kernel event times from a second pass of the same steps with trace "
                           "events (direct launches, no overlap between the two kernels)",
         "roofline": roofline,
-        "schedule_trials": ([{k: t[k] for k in ("lanes_min_vectors", "inv_per_thread", "ms")}
-                             for t in tuning["trials"]] if tuning else None),
+        "schedule_trials": ([{k: t[k] for k in ("lanes_min_vectors", "inv_per_thread", "chunk", "ms")}
+                             for t in tuning["trials"]] if tuning and tuning["trials"] else None),
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
         "parity_vs_oracle": parity,
     }

@@ -39,16 +39,19 @@ def time_call(ctx, dag, op_local, start, now: int, out, stream, flush, reps: int
 
 def autotune(ctx, dag, op_local, start, now: int, out, stream=None, flush=None,
              lanes: Iterable[int] = DEFAULT_LANES_MIN_VECTORS,
-             ipts: Iterable[int] = DEFAULT_INV_PER_THREAD, chunk: int = 0,
+             ipts: Iterable[int] = DEFAULT_INV_PER_THREAD, chunks: Iterable[int] = (0,),
              reps: int = 5) -> dict:
-    """Sweep the candidates, apply the fastest, return {"best": ..., "trials": [...]}."""
+    """Sweep the candidates, apply the fastest, return {"best": ..., "trials": [...]}.
+
+    ``chunks``: staging chunk sizes in configurations (0 = the library default).
+    """
     import torch
     if stream is None:
         stream = torch.cuda.current_stream()
     if flush is None:
         flush = torch.empty(256 << 20, dtype=torch.uint8, device=dag.device)
     trials = []
-    for lmv, ipt in itertools.product(lanes, ipts):
+    for chunk, lmv, ipt in itertools.product(chunks, lanes, ipts):
         L.llama_set_tuning(ctx, lmv, ipt, chunk)
         ms = time_call(ctx, dag, op_local, start, now, out, stream, flush, reps)
         trials.append({"lanes_min_vectors": lmv, "inv_per_thread": ipt, "chunk": chunk, "ms": ms})

@@ -120,6 +120,62 @@ __device__ void critical_path_of_dag(const DevProblem &P, int d, const int32_t *
     for (int v = lo + (int)threadIdx.x; v < hi; v += blockDim.x) P.cp_magic[v] = ~0ull / (uint64_t)P.cp[v];
 }
 
+// The same levels for a DAG whose packed structure has at most kCpWarpWords
+// words (hence at most kCpWarpOps ops), by one warp in its own slice of shared
+// memory: a level costs a warp barrier.
+struct CpWarpSmem {
+    int64_t cp[kCpWarpOps];
+    int64_t ref[kCpWarpOps];
+    int32_t pk[kCpWarpWords];
+};
+static_assert(sizeof(CpWarpSmem) * (256 / 32) <= sizeof(CpSmem), "warp slices exceed the block's area");
+
+__device__ void critical_path_of_dag_warp(const DevProblem &P, int64_t off, int nw, CpWarpSmem &w) {
+    const int lane = threadIdx.x & 31;
+    for (int k = lane; k < nw; k += 32) w.pk[k] = P.dag_pack[off + k];
+    __syncwarp();
+    const int lo = w.pk[0], n = w.pk[1], ne = w.pk[2], nl = w.pk[3];
+    const int32_t *gidx = w.pk + 4, *rp = gidx + n, *col = rp + n + 1, *ord = col + ne, *lvl = ord + n;
+    for (int k = lane; k < n; k += 32) w.ref[k] = (int64_t)P.lat[gidx[k]];
+    __syncwarp();
+    for (int l = 0; l < nl; ++l) {
+        for (int p = lvl[l] + lane; p < lvl[l + 1]; p += 32) {
+            const int v = ord[p];
+            int64_t best = 0;
+            for (int e = rp[v]; e < rp[v + 1]; ++e) best = max(best, w.cp[col[e]]);
+            w.cp[v] = w.ref[v] + best;
+        }
+        __syncwarp();
+    }
+    for (int k = lane; k < n; k += 32) {
+        P.ref[lo + k] = w.ref[k];
+        P.cp[lo + k] = w.cp[k];
+        P.cp_magic[lo + k] = ~0ull / (uint64_t)w.cp[k];
+    }
+    __syncwarp();  // the slice is reused by the warp's next DAG
+}
+
+// Critical paths of the DAGs that block b of nblk takes: small DAGs one per
+// warp (DAG b*8 + warp, then strides of nblk*8), then the others one per block
+// (DAGs b, b + nblk, ... that did not fit a warp's slice).
+__device__ void critical_paths_of_block(const DevProblem &P, int b, int nblk, const int32_t *topo,
+                                        const int32_t *lvl_off, const int32_t *dag_lvl, CpSmem &sm) {
+    const int nwarp = blockDim.x >> 5, wid = threadIdx.x >> 5;
+    CpWarpSmem &ws = reinterpret_cast<CpWarpSmem *>(&sm)[wid];
+    for (int d = b * nwarp + wid; d < P.n_dags; d += nblk * nwarp) {
+        const int64_t off = P.dag_pack_off[d];
+        const int nw = (int)(P.dag_pack_off[d + 1] - off);
+        if (nw > 0 && nw <= kCpWarpWords) critical_path_of_dag_warp(P, off, nw, ws);
+    }
+    __syncthreads();
+    for (int d = b; d < P.n_dags; d += nblk) {
+        const int nw = (int)(P.dag_pack_off[d + 1] - P.dag_pack_off[d]);
+        if (nw > 0 && nw <= kCpWarpWords) continue;
+        critical_path_of_dag(P, d, topo, lvl_off, dag_lvl, sm);
+        __syncthreads();  // the shared staging area is reused by the next DAG
+    }
+}
+
 __global__ void k_critical_path(DevProblem P, const int32_t *topo, const int32_t *lvl_off,
                                 const int32_t *dag_lvl) {
     __shared__ CpSmem sm;
@@ -366,7 +422,7 @@ __device__ __forceinline__ void scatter_invocation(const DevProblem &P, const Bu
 }
 
 // The bucketing step of a call, one cooperative launch (all blocks resident):
-//  1. blocks [0, n_cp) compute the critical paths of DAGs b, b + n_cp, ...; the
+//  1. blocks [0, n_cp) compute the critical paths (a warp per small DAG); the
 //     other blocks validate invocations, count them per op (one counter per
 //     128-byte line, so concurrent atomics on different ops never share a
 //     line) and prefetch the encoded tables into L2;
@@ -399,10 +455,7 @@ __global__ void __launch_bounds__(256) k_bucket(DevProblem P, int64_t n_inv, con
         }
     }
     if ((int)blockIdx.x < n_cp) {
-        for (int d = blockIdx.x; d < P.n_dags; d += n_cp) {
-            critical_path_of_dag(P, d, topo, lvl_off, dag_lvl, sm);
-            __syncthreads();  // the shared staging area is reused by the next DAG
-        }
+        critical_paths_of_block(P, blockIdx.x, n_cp, topo, lvl_off, dag_lvl, sm);
         grid_barrier(&S.ctrl[kCtrlBarrier], gridDim.x, &S.ctrl[kCtrlTimeout]);
         return;
     }
@@ -656,9 +709,14 @@ __device__ __forceinline__ void score_body(const DevProblem &P, const BucketScra
                         }
                     }
                 } else {
-                    // from global memory: each search is shared by up to 32 lanes
-                    // (a (G+1)-ary search, a few dependent rounds instead of log2 dn)
-                    const int G = L < 32 ? L : 32, W = L > 32 ? (L >> 5) : 1, sw = s >> 5, gl = s & (G - 1);
+                    // from global memory: each search is shared by G <= 32 lanes, a
+                    // G-ary search (a few dependent rounds instead of log2 dn).  A
+                    // round over n > G candidates [lo, lo + n) probes lo + (l+1)n/G - 1
+                    // for l < G (strictly increasing, the last one at lo + n - 1);
+                    // over n <= G candidates it probes each one.  Only shifts: G is
+                    // a power of two and (l+1)n < 2^19.
+                    const int G = L < 32 ? L : 32, lgG = lg < 5 ? lg : 5;
+                    const int W = L > 32 ? (L >> 5) : 1, sw = s >> 5, gl = s & (G - 1);
                     const int gbase = (tid & 31) & ~(G - 1);
                     const uint32_t gmask = G == 32 ? 0xFFFFFFFFu : ((1u << G) - 1u);
                     for (int t0 = 0; t0 < nc; t0 += W) {
@@ -669,10 +727,13 @@ __device__ __forceinline__ void score_body(const DevProblem &P, const BucketScra
                         const bool act = t < nc && iu >= 0;
                         const int32_t sl = act ? S.b_slack[(int64_t)iu * H + h] : 0;
                         int32_t lo = 0, hi = act ? dn : 0;  // lo <= count <= hi
+                        if (G == 1) {  // one lane per invocation (tile-uniform): bisection
+                            lo = hi = act ? count_below(dl, dn, sl) : 0;
+                        }
                         while (__any_sync(0xFFFFFFFFu, hi > lo)) {
                             const int32_t n = hi - lo;
                             const bool exact = n <= G;
-                            const int32_t pos = exact ? lo + gl : lo + (int32_t)(((int64_t)(gl + 1) * n) / (G + 1));
+                            const int32_t pos = exact ? lo + gl : lo + (((gl + 1) * n) >> lgG) - 1;
                             const bool pred = n > 0 && (!exact || gl < n) && __ldg(dl + pos) < sl;
                             const int32_t c = __popc((__ballot_sync(0xFFFFFFFFu, pred) >> gbase) & gmask);
                             if (n > 0) {
@@ -680,9 +741,10 @@ __device__ __forceinline__ void score_body(const DevProblem &P, const BucketScra
                                     lo += c;
                                     hi = lo;
                                 } else {
-                                    const int32_t nlo = c > 0 ? lo + (int32_t)(((int64_t)c * n) / (G + 1)) + 1 : lo;
-                                    const int32_t nhi = c < G ? lo + (int32_t)(((int64_t)(c + 1) * n) / (G + 1)) : hi;
-                                    lo = nlo;
+                                    // the answer lies after the last probe below sl and
+                                    // at or before the first one that is not
+                                    const int32_t nhi = c < G ? lo + (((c + 1) * n) >> lgG) - 1 : hi;
+                                    lo = c > 0 ? lo + ((c * n) >> lgG) : lo;
                                     hi = nhi;
                                 }
                             }
@@ -809,7 +871,7 @@ cudaError_t enqueue_schedule(const ContextView &v, const BucketScratch &S, int64
     if (e == cudaSuccess) e = cudaMemsetAsync(S.ctrl, 0, sizeof(unsigned long long) * kCtrlWords, s);
     if (e != cudaSuccess) return e;
     // bucketing: one cooperative launch (its blocks meet at a grid barrier)
-    const int n_cp = std::max(1, std::min(v.n_dags, std::max(1, v.bucket_max_blocks / 4)));
+    const int n_cp = std::max(1, std::min((v.n_dags + 7) / 8, std::max(1, v.bucket_max_blocks / 4)));
     const int count_blocks = (int)std::max<int64_t>(
         1, std::min<int64_t>((n_inv + 255) / 256, (int64_t)v.bucket_max_blocks - n_cp));
     {

@@ -57,6 +57,8 @@ constexpr int kMaxBucketBlocks = 4096;
 // DAGs up to this size are staged in shared memory for the critical path
 constexpr int kCpSmemOps = 512;
 constexpr int kCpPackWords = 5120;  // packed DAG words staged in shared memory
+constexpr int kCpWarpOps = 128;       // a warp's slice of the critical-path area: ops
+constexpr int kCpWarpWords = 384;     // and packed words (<= 384 words implies <= 126 ops)
 
 struct DevProblem {
     int32_t n_dags, n_ops, n_hw, mode;

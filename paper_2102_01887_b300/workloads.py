@@ -330,6 +330,20 @@ def batched_large(seed: int = 3, n_inv: int = 32_768, n_dags: int = 512,
     return p, _invocations(inv_rng, p, n_inv, 10**11)
 
 
+def dag_sizes(seed: int = 4, sizes: tuple = (1, 3, 40, 100, 126, 127, 200, 511, 513, 1500, 12),
+              n_cfg: int = 24, n_inv: int = 16_384) -> tuple[Problem, Invocations]:
+    """DAGs of the given op counts side by side (small to 1,500 ops), small tables.
+
+    Shapes from tens to thousands of operations in one problem, with SLOs
+    log-uniform 0.5-60 s.
+    """
+    rng = np.random.default_rng(seed)
+    dags = [_random_dag_edges(rng, int(n)) for n in sizes]
+    n_ops = sum(len(d) for d in dags)
+    p = _assemble(rng, dags, np.full(n_ops, n_cfg), _log_uniform_slo(rng), q_max=100_000)
+    return p, _invocations(rng, p, n_inv, 10**11)
+
+
 def random_small(seed: int, max_dags: int = 3, max_ops: int = 6, max_cfg: int = 8,
                  n_inv: int = 64, value_range: int = 40) -> tuple[Problem, Invocations]:
     """Tiny random problems with small value ranges, so ties and boundary hits are common.

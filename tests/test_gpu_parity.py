@@ -65,6 +65,21 @@ def test_critical_path_and_slack(L, name):
         assert (s.slack(sub) == oracle.slacks(p, sub)).all()
 
 
+@pytest.mark.parametrize("mode,alpha", [(0, (1, 1)), (1, (3, 2))])
+def test_dags_of_every_size(L, mode, alpha):
+    # one problem holding DAGs of 1 to 1,500 ops: small DAGs take a warp each in
+    # the critical-path pass, mid-sized ones a block with the DAG in shared
+    # memory, and the largest go through global memory
+    p, inv = W.dag_sizes()
+    with L.Scheduler(p, mode=mode, alpha=alpha) as s:
+        assert (s.critical_path() == oracle.critical_path(p)).all()
+        assert (s.slack(inv) == oracle.slacks(p, inv)).all()
+        got, rc = s.schedule(inv)
+    exp, rc_o = oracle.schedule(p, inv, mode=mode, alpha=alpha)
+    assert rc == rc_o == 0
+    assert_same(got, exp)
+
+
 @pytest.mark.parametrize("seed", range(20))
 def test_slack_random_small(L, seed):
     p, inv = W.random_small(seed)
@@ -314,7 +329,10 @@ def test_tunings_change_no_result(L, tuning):
     p, inv = W.random_small(77, max_cfg=300, n_inv=3000, value_range=200)
     pm, invm = W.medium()
     subm = invm.subset(np.arange(0, invm.n, 7))
-    for prob, case in ((p, inv), (pm, subm)):
+    # ops of 8,192 configurations: their distinct latencies are searched in
+    # global memory by groups of 1 to 256 lanes
+    pl, invl = W.batched_large(n_dags=4, n_inv=2048)
+    for prob, case in ((p, inv), (pm, subm), (pl, invl)):
         for mode in (0, 1):
             exp, _ = oracle.schedule(prob, case, mode=mode, alpha=(2, 3))
             with L.Scheduler(prob, mode=mode, alpha=(2, 3)) as s:
