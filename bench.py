@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--n-dags", type=int, default=None, help="DAG count of the batched workloads")
     ap.add_argument("--n-inv", type=int, default=None, help="invocations per step (default: the workload's)")
     ap.add_argument("--tuning", default=None,
-                    help="fixed scoring schedule 'lanes_min_vectors,inv_per_thread,chunk' (no autotuning)")
+                    help="fixed scoring schedule 'lanes_min_vectors,inv_per_thread,chunk,stages' (no autotuning)")
     return ap.parse_args()
 
 
@@ -251,16 +251,17 @@ def main():
 
     tuning = None
     if args.tuning:
-        lmv, ipt, chunk = (int(x) for x in args.tuning.split(","))
-        L.llama_set_tuning(ctx, lmv, ipt, chunk)
-        tuning = {"best": {"lanes_min_vectors": lmv, "inv_per_thread": ipt, "chunk": chunk}, "trials": []}
+        lmv, ipt, chunk, stages = (int(x) for x in args.tuning.split(","))
+        L.llama_set_tuning(ctx, lmv, ipt, chunk, stages)
+        tuning = {"best": {"lanes_min_vectors": lmv, "inv_per_thread": ipt, "chunk": chunk, "stages": stages},
+                  "trials": []}
     elif not args.no_autotune:
         # choose the scoring schedule on this batch before anything is timed;
         # ops with more than 4,096 configurations may also be staged whole
         from paper_2102_01887_b300.autotune import autotune
         big = int(np.diff(p.cfg_off).max()) > 4096
         tuning = autotune(ctx, dag, opl, st, inv.now_us, out, stream, flush,
-                          chunks=(0, 8192) if big else (0,))
+                          chunks=(0, 8256) if big else (0,))
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -402,7 +403,7 @@ def main():
         "kernel_ms_note": "per-kernel event times from a second pass of the same steps with trace "
                           "events (direct launches, no overlap between the two kernels)",
         "roofline": roofline,
-        "schedule_trials": ([{k: t[k] for k in ("lanes_min_vectors", "inv_per_thread", "chunk", "ms")}
+        "schedule_trials": ([{k: t[k] for k in ("lanes_min_vectors", "inv_per_thread", "chunk", "stages", "ms")}
                              for t in tuning["trials"]] if tuning and tuning["trials"] else None),
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
         "parity_vs_oracle": parity,

@@ -171,12 +171,16 @@ int llama_schedule_static(llama_ctx *ctx, int64_t n_inv, const int32_t *dag,
  *   inv_per_thread     invocations a thread scores together against each staged
  *                      vector: 1, 2 or 4 (default 2);
  *   chunk_entries      table entries staged in shared memory at a time: a
- *                      multiple of 8 in 8..LLAMA_MAX_CFG, or 0 for the default
- *                      (the largest table, at most 4096).
+ *                      multiple of 8 in 8..LLAMA_MAX_CFG + 8*LLAMA_MAX_HW (the
+ *                      largest padded table), or 0 for the default (the largest
+ *                      padded table in the fewest even pieces of about 4096);
+ *   stages             staging buffers per CTA: 1 (tiles claimed from a
+ *                      counter as CTAs finish; default) or 2 (tiles taken
+ *                      round-robin, the next chunk copied while one is scored).
  * Call after llama_set_profiles (which resets the chunk to its default).
  * Errors: EINVAL, ENOTREADY (no profiles), ECUDA. */
 int llama_set_tuning(llama_ctx *ctx, int32_t lanes_min_vectors, int32_t inv_per_thread,
-                     int32_t chunk_entries);
+                     int32_t chunk_entries, int32_t stages);
 
 /* Pre-allocate scratch for calls of up to max_inv invocations. */
 int llama_reserve(llama_ctx *ctx, int64_t max_inv);

@@ -1,7 +1,7 @@
 """Autotuner of the scoring kernel's launch schedule.
 
 The schedule (lanes sharing one invocation, invocations per thread, staging
-chunk) changes speed, never results (tests check the latter).  For a given
+chunk, staging buffers) changes speed, never results (tests check the latter).  For a given
 context and a batch of device-resident invocations, the tuner times every
 candidate on that batch -- whole scheduling calls replayed as the caller
 would replay them, the L2 cache flushed before each call -- and keeps the
@@ -16,6 +16,7 @@ from . import llama as L
 
 DEFAULT_LANES_MIN_VECTORS = (4, 8, 16, 32, 64)
 DEFAULT_INV_PER_THREAD = (1, 2, 4)
+DEFAULT_STAGES = (1, 2)
 
 
 def time_call(ctx, dag, op_local, start, now: int, out, stream, flush, reps: int = 5) -> float:
@@ -40,10 +41,11 @@ def time_call(ctx, dag, op_local, start, now: int, out, stream, flush, reps: int
 def autotune(ctx, dag, op_local, start, now: int, out, stream=None, flush=None,
              lanes: Iterable[int] = DEFAULT_LANES_MIN_VECTORS,
              ipts: Iterable[int] = DEFAULT_INV_PER_THREAD, chunks: Iterable[int] = (0,),
-             reps: int = 5) -> dict:
+             stages: Iterable[int] = DEFAULT_STAGES, reps: int = 5) -> dict:
     """Sweep the candidates, apply the fastest, return {"best": ..., "trials": [...]}.
 
-    ``chunks``: staging chunk sizes in configurations (0 = the library default).
+    ``chunks``: staging chunk sizes in configurations (0 = the library default);
+    ``stages``: staging buffers per CTA (1 or 2).
     """
     import torch
     if stream is None:
@@ -51,10 +53,11 @@ def autotune(ctx, dag, op_local, start, now: int, out, stream=None, flush=None,
     if flush is None:
         flush = torch.empty(256 << 20, dtype=torch.uint8, device=dag.device)
     trials = []
-    for chunk, lmv, ipt in itertools.product(chunks, lanes, ipts):
-        L.llama_set_tuning(ctx, lmv, ipt, chunk)
+    for st, chunk, lmv, ipt in itertools.product(stages, chunks, lanes, ipts):
+        L.llama_set_tuning(ctx, lmv, ipt, chunk, st)
         ms = time_call(ctx, dag, op_local, start, now, out, stream, flush, reps)
-        trials.append({"lanes_min_vectors": lmv, "inv_per_thread": ipt, "chunk": chunk, "ms": ms})
+        trials.append({"lanes_min_vectors": lmv, "inv_per_thread": ipt, "chunk": chunk, "stages": st,
+                       "ms": ms})
     best = min(trials, key=lambda t: t["ms"])
-    L.llama_set_tuning(ctx, best["lanes_min_vectors"], best["inv_per_thread"], best["chunk"])
+    L.llama_set_tuning(ctx, best["lanes_min_vectors"], best["inv_per_thread"], best["chunk"], best["stages"])
     return {"best": best, "trials": trials}

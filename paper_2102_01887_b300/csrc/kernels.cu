@@ -343,11 +343,11 @@ __device__ void layout_write(const DevProblem &P, const BucketScratch &S, int32_
         S.op_start[v] = pos;
         int32_t j = 0;
         for (; j + per_tile <= ck; j += per_tile, ++tf) {
-            S.tiles[2 * tf] = make_int4(v, j, per_tile, lg);
+            S.tiles[2 * tf] = make_int4(v, pos + j, per_tile, lg);
             S.tiles[2 * tf + 1] = tx;
         }
         if (j < ck) {
-            S.tiles[2 * tt] = make_int4(v, j, ck - j, tail_lanes_log2(ck - j, lg, ipt, nvec));
+            S.tiles[2 * tt] = make_int4(v, pos + j, ck - j, tail_lanes_log2(ck - j, lg, ipt, nvec));
             S.tiles[2 * tt + 1] = tx;
             ++tt;
         }
@@ -410,15 +410,16 @@ __device__ __forceinline__ void count_invocation(const DevProblem &P, int64_t i,
     S.rbase[i] = rbase;
 }
 
-// Place invocation i in its op's bucket and compute its slack for every
-// backend (Algorithm 1 through the critical path).
+// Place invocation i in its op's bucket and store its slack for every backend
+// (Algorithm 1 through the critical path) beside it, at the bucket position.
 __device__ __forceinline__ void scatter_invocation(const DevProblem &P, const BucketScratch &S, int64_t i,
                                                    int32_t g, int32_t slot, int64_t rbase) {
-    S.b_inv[S.op_start[g] + slot] = (int32_t)i;
+    const int64_t pos = S.op_start[g] + slot;
+    S.b_inv[pos] = (int32_t)i;
     const int64_t ref = P.ref[g], cp = P.cp[g];
     const uint64_t mg = P.cp_magic[g];
     const int H = P.n_hw;
-    for (int h = 0; h < H; ++h) S.b_slack[i * H + h] = slack_of(ref, cp, mg, rbase - P.q[h]);
+    for (int h = 0; h < H; ++h) S.b_slack[pos * H + h] = slack_of(ref, cp, mg, rbase - P.q[h]);
 }
 
 // The bucketing step of a call, one cooperative launch (all blocks resident):
@@ -598,231 +599,286 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(bar) : "memory");
 }
 
-// Persistent CTAs take tiles (op, first invocation j0, m invocations, 2^lg lanes
-// per group) from the tile list: first tile blockIdx.x, the next ones from an
-// atomic counter, so CTAs that finish early take more (the list is ordered
-// longest first).  For a tile, the op's encoded table is staged into shared
-// memory by TMA bulk copies, in chunks of at most `chunk` entries (a multiple
-// of 8); while the first chunk lands, the lanes count, for each invocation and
-// segment, the op's distinct latencies below the slack (binary searches).  A
-// group of 2^lg lanes scores IPT consecutive invocations: lane s takes the
-// vectors q = s mod 2^lg of every backend segment, loads each vector once from
-// shared memory and applies it to all IPT invocations, each against its own
-// count for that segment.  Groups reduce with shuffles (and
-// through shared memory when a group spans several warps); lane u mod 2^lg of
-// a group decodes the group's invocation u.
+// A tile is (op, first bucket position, m invocations, 2^lg lanes per group).
+// For a tile, the op's encoded table is staged into shared memory by TMA bulk
+// copies, in chunks of at most `chunk` entries (a multiple of 8); the lanes
+// count, for each invocation and segment, the op's distinct latencies below
+// the slack.  A group of 2^lg lanes scores IPT consecutive invocations: lane s
+// takes the vectors q = s mod 2^lg of every backend segment, loads each vector
+// once from shared memory and applies it to all IPT invocations, each against
+// its own count for that segment.  Groups reduce with shuffles (and through
+// shared memory when a group spans several warps); lane u mod 2^lg of a group
+// decodes the group's invocation u.
+
+// Per-thread view of the current tile.
+template <int IPT>
+struct TileState {
+    int32_t v, m, lg, L, g, s, npad, dn;
+    int32_t pos0;  // bucket position of the group's first invocation
+    int64_t p0;
+    int32_t inv[IPT];
+    uint32_t best[IPT];
+    bool any;
+};
+
+template <int IPT>
+__device__ __forceinline__ void tile_begin(const BucketScratch &S, long long ti, TileState<IPT> &T) {
+    const int4 tile = S.tiles[2 * ti], tx = S.tiles[2 * ti + 1];
+    T.v = tile.x;
+    T.m = tile.z;
+    T.lg = tile.w;
+    T.L = 1 << T.lg;
+    T.g = threadIdx.x >> T.lg;
+    T.s = threadIdx.x & (T.L - 1);
+    T.npad = tx.x;
+    T.dn = tx.y;
+    T.p0 = tx.z;
+    T.any = false;
+    T.pos0 = tile.y + T.g * IPT;
+#pragma unroll
+    for (int u = 0; u < IPT; ++u) {
+        const int32_t j = T.g * IPT + u;
+        T.inv[u] = j < T.m ? S.b_inv[tile.y + j] : -1;
+        T.any |= T.inv[u] >= 0;
+        T.best[u] = 0xFFFFFFFFu;
+    }
+}
+
+// inv[u] for a runtime u, without a runtime index into registers.
+template <int IPT>
+__device__ __forceinline__ int32_t inv_at(const TileState<IPT> &T, int u) {
+    int32_t iu = T.inv[0];
+#pragma unroll
+    for (int w = 1; w < IPT; ++w) iu = u == w ? T.inv[w] : iu;
+    return iu;
+}
+
+// Counts c(u, h) of distinct latencies below the slack of invocation u for
+// backend h, into cg[u * H + h], from the sorted list dl (shared memory: the
+// lanes of a group share the bisections).
+template <int IPT>
+__device__ __forceinline__ void counts_from_shared(const BucketScratch &S, const TileState<IPT> &T, int H,
+                                                   const int32_t *dl, uint16_t *cg) {
+    if (!T.any) return;
+    for (int t = T.s; t < IPT * H; t += T.L) {
+        const int u = t / H, h = t - u * H;
+        const int32_t iu = inv_at(T, u);
+        cg[t] = iu >= 0 ? (uint16_t)count_below(dl, T.dn, S.b_slack[(int64_t)(T.pos0 + u) * H + h]) : 0;
+    }
+}
+
+// The same counts from the list in global memory: each search is shared by
+// G <= 32 lanes, a G-ary search (a few dependent rounds instead of log2 dn).
+// A round over n > G candidates [lo, lo + n) probes lo + (l+1)n/G - 1 for
+// l < G (strictly increasing, the last one at lo + n - 1); over n <= G
+// candidates it probes each one.  Only shifts: G is a power of two and
+// (l+1)n < 2^19.  Every thread of the CTA must call this (warp votes).
+template <int IPT>
+__device__ __forceinline__ void counts_from_global(const DevProblem &P, const BucketScratch &S,
+                                                   const TileState<IPT> &T, int H, const int32_t *dl,
+                                                   uint16_t *cg) {
+    const int nc = IPT * H;
+    const int G = T.L < 32 ? T.L : 32, lgG = T.lg < 5 ? T.lg : 5;
+    const int W = T.L > 32 ? (T.L >> 5) : 1, sw = T.s >> 5, gl = T.s & (G - 1);
+    const int gbase = (threadIdx.x & 31) & ~(G - 1);
+    const uint32_t gmask = G == 32 ? 0xFFFFFFFFu : ((1u << G) - 1u);
+    for (int t0 = 0; t0 < nc; t0 += W) {
+        const int t = t0 + sw, u = t / H, h = t - u * H;
+        const int32_t iu = inv_at(T, u);
+        const bool act = t < nc && iu >= 0;
+        const int32_t sl = act ? S.b_slack[(int64_t)(T.pos0 + u) * H + h] : 0;
+        int32_t lo = 0, hi = act ? T.dn : 0;  // lo <= count <= hi
+        if (G == 1) {  // one lane per invocation (tile-uniform): bisection
+            lo = hi = act ? count_below(dl, T.dn, sl) : 0;
+        }
+        while (__any_sync(0xFFFFFFFFu, hi > lo)) {
+            const int32_t n = hi - lo;
+            const bool exact = n <= G;
+            const int32_t pos = exact ? lo + gl : lo + (((gl + 1) * n) >> lgG) - 1;
+            bool pred = false;
+            if (n > 0 && (!exact || gl < n)) {
+                // a 32-lane first round reads the op's probe values from one line
+                const bool first = G == 32 && !exact && n == T.dn;
+                pred = (first ? __ldg(P.dpiv + 32 * (int64_t)T.v + gl) : __ldg(dl + pos)) < sl;
+            }
+            const int32_t c = __popc((__ballot_sync(0xFFFFFFFFu, pred) >> gbase) & gmask);
+            if (n > 0) {
+                if (exact) {
+                    lo += c;
+                    hi = lo;
+                } else {
+                    // the answer lies after the last probe below sl and at or
+                    // before the first one that is not
+                    const int32_t nhi = c < G ? lo + (((c + 1) * n) >> lgG) - 1 : hi;
+                    lo = c > 0 ? lo + ((c * n) >> lgG) : lo;
+                    hi = nhi;
+                }
+            }
+        }
+        if (act && gl == 0) cg[t] = (uint16_t)lo;
+    }
+}
+
+// Score the staged chunk [c0, c0 + cn) of the tile's op.
+template <int MODE, int IPT>
+__device__ __forceinline__ void scan_chunk(const DevProblem &P, TileState<IPT> &T, int32_t c0, int32_t cn,
+                                           const uint16_t *lr_s, const uint16_t *rf_s, const uint16_t *df_s,
+                                           const uint16_t *cg) {
+    if (!T.any) return;
+    const int H = P.n_hw;
+    const int32_t *sp = P.seg_pad + (int64_t)T.v * (H + 1);
+    const int qc0 = c0 / kVec, qc1 = (c0 + cn) / kVec;
+    const uint4 *lr4 = reinterpret_cast<const uint4 *>(lr_s);
+    const uint4 *rf4 = reinterpret_cast<const uint4 *>(rf_s);
+    const uint4 *df4 = reinterpret_cast<const uint4 *>(df_s);
+    for (int h = 0; h < H; ++h) {
+        const int a = max(__ldg(sp + h) / kVec, qc0), b = min(__ldg(sp + h + 1) / kVec, qc1);
+        if (a >= b) continue;
+        uint32_t c2[IPT];
+#pragma unroll
+        for (int u = 0; u < IPT; ++u) c2[u] = (uint32_t)cg[u * H + h] * 0x00010001u;
+        for (int q = a + ((T.s - a) & (T.L - 1)); q < b; q += T.L) {
+            const int r = q - qc0;
+            const uint4 lk = lr4[r], rk = rf4[r];
+            if (MODE == LLAMA_MODE_ALPHA) {
+                const uint4 dk = df4[r];
+#pragma unroll
+                for (int u = 0; u < IPT; ++u) T.best[u] = scan8_alpha(T.best[u], c2[u], lk, rk, dk);
+            } else {
+#pragma unroll
+                for (int u = 0; u < IPT; ++u) T.best[u] = scan8_cost_first(T.best[u], c2[u], lk, rk);
+            }
+        }
+    }
+}
+
+// Reduce each group's keys and decode them into decisions.  Every thread of
+// the CTA must call this (a block barrier when groups span several warps).
+template <int MODE, int IPT>
+__device__ __forceinline__ void finish_tile(const DevProblem &P, const BucketScratch &S, llama_decision *out,
+                                            const TileState<IPT> &T, uint32_t (*red)[kScoreThreads / 32]) {
+    const int tid = threadIdx.x, H = P.n_hw;
+    uint32_t key[IPT];
+    const int wl = T.L < 32 ? T.L : 32;
+#pragma unroll
+    for (int u = 0; u < IPT; ++u) {
+        key[u] = T.inv[u] >= 0 ? min(T.best[u] & 0xFFFFu, T.best[u] >> 16) : 0xFFFFu;
+        for (int o = 1; o < wl; o <<= 1) key[u] = min(key[u], __shfl_xor_sync(0xffffffffu, key[u], o));
+    }
+    if (T.L > 32) {
+        // a group spans L/32 warps: combine the warps' minima in shared memory
+        if ((tid & 31) == 0)
+            for (int u = 0; u < IPT; ++u) red[u][tid >> 5] = key[u];
+        __syncthreads();
+        if (T.s < IPT)  // the decoding lanes (L > 32 > IPT here)
+            for (int u = 0; u < IPT; ++u)
+                for (int w = 1; w < (T.L >> 5); ++w) key[u] = min(key[u], red[u][(tid >> 5) + w]);
+    }
+    // lane u mod 2^lg of the group decodes invocation u (every lane holds every key)
+#pragma unroll
+    for (int u = 0; u < IPT; ++u) {
+        if (T.s != (u & (T.L - 1)) || T.inv[u] < 0) continue;
+        const int32_t i = T.inv[u];
+        const int64_t c_base = P.cfg_off[T.v];
+        int32_t idx;
+        if (MODE == LLAMA_MODE_ALPHA) idx = P.inv[2 * c_base + key[u]];
+        else idx = key[u] < 0x8000u ? (int32_t)P.inv[2 * c_base + key[u]] : P.fast[T.v];
+        const int64_t gx = c_base + idx;
+        const int32_t Lx = P.lat[gx];
+        const int lam = backend_of(P.hw_off + (int64_t)T.v * (H + 1), H, idx);
+        const int32_t sl = S.b_slack[(int64_t)(T.pos0 + u) * H + lam];
+        llama_decision dsn;
+        dsn.cfg = idx;
+        dsn.lat = Lx;
+        dsn.cost = P.cost[gx];
+        dsn.slack = sl;
+        dsn.flags = Lx < sl ? LLAMA_FLAG_FEASIBLE : 0;
+        out[i] = dsn;
+    }
+}
+
+// Queue the bulk copies of chunk [c0, c0 + cn) of the table at padded offset
+// p0 (and, with the first chunk, the op's dn distinct latencies when they are
+// staged) on mbarrier bar.  One thread.
+template <int MODE>
+__device__ __forceinline__ void stage_chunk(const DevProblem &P, int64_t p0, int32_t c0, int32_t cn,
+                                            bool with_dlat, int32_t dn, uint16_t *lr_s, uint16_t *rf_s,
+                                            uint16_t *df_s, int32_t *dl_s, uint32_t bar) {
+    // the generic-proxy reads of this buffer are complete (a block barrier came
+    // before); order them before the async-proxy writes that follow
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    // whole 16-byte words of the distinct latencies: dlat has npad >= dn entries here
+    const uint32_t db = with_dlat ? (uint32_t)((dn + 3) / 4) * 16u : 0u;
+    const uint32_t bytes = (uint32_t)cn * (MODE == LLAMA_MODE_ALPHA ? 6u : 4u) + db;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    if (with_dlat) bulk_g2s(dl_s, P.dlat + p0, db, bar);
+    bulk_g2s(lr_s, P.lrb + p0 + c0, 2u * cn, bar);
+    bulk_g2s(rf_s, P.rf + p0 + c0, 2u * cn, bar);
+    if (MODE == LLAMA_MODE_ALPHA) bulk_g2s(df_s, P.df + p0 + c0, 2u * cn, bar);
+}
+
+__device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+// One staging buffer.  Persistent CTAs take tiles from the tile list: first
+// tile blockIdx.x, the next ones from an atomic counter, so CTAs that finish
+// early take more (the list is ordered longest first).  While the first chunk
+// lands, the distinct latencies are searched.
 template <int MODE, int IPT>
 __device__ __forceinline__ void score_body(const DevProblem &P, const BucketScratch &S,
                                            llama_decision *out, int32_t chunk, int32_t dl_cap) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // chunk entries: latency ranks, feasible-branch ranks (, rank differences);
-    // then, per group, the counts c of distinct latencies below each slack
+    // the op's distinct latencies; per group, the counts of each invocation
     uint16_t *lr_s = reinterpret_cast<uint16_t *>(smem_raw);
     uint16_t *rf_s = lr_s + chunk;
     uint16_t *df_s = rf_s + chunk;
-    uint16_t *c_s = rf_s + chunk * (MODE == LLAMA_MODE_ALPHA ? 2 : 1);
-    // the op's distinct latencies, after the counts (16-byte aligned)
-    int32_t *dl_s = reinterpret_cast<int32_t *>(
-        smem_raw + ((size_t)chunk * (MODE == LLAMA_MODE_ALPHA ? 6 : 4) + (size_t)kScoreThreads * IPT * P.n_hw * 2 + 15) / 16 * 16);
-    __shared__ __align__(8) unsigned long long mbar, mbar_d;
+    const size_t tbl = align16((size_t)chunk * (MODE == LLAMA_MODE_ALPHA ? 6 : 4));
+    int32_t *dl_s = reinterpret_cast<int32_t *>(smem_raw + tbl);
+    uint16_t *c_s = reinterpret_cast<uint16_t *>(smem_raw + tbl + 4 * (size_t)dl_cap);
+    __shared__ __align__(8) unsigned long long mbar;
     __shared__ uint32_t red[IPT][kScoreThreads / 32];
     __shared__ long long next_tile;
     const int tid = threadIdx.x, H = P.n_hw;
-    const uint32_t bar = smem_addr(&mbar), bar_d = smem_addr(&mbar_d);
+    const uint32_t bar = smem_addr(&mbar);
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_d) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    uint32_t phase = 0, phase_d = 0;
-    bool ok = true, dl_ok = true;
+    uint32_t phase = 0;
+    bool ok = true;
     // everything k_bucket wrote (tile list, buckets, slack) is visible only after
     // griddepcontrol.wait; the mbarrier set-up above overlaps its tail
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const long long n_tiles = (long long)S.ctrl[kCtrlTiles];
     long long ti = blockIdx.x;
+    TileState<IPT> T;
     while (ti < n_tiles) {
         unsigned long long claim = 0;
         if (tid == 0) claim = atomicAdd(&S.ctrl[kCtrlNextTile], 1ull);  // the tile after this one
-        const int4 tile = S.tiles[2 * ti], tx = S.tiles[2 * ti + 1];
-        const int32_t v = tile.x, j0 = tile.y, m = tile.z, lg = tile.w;
-        const int L = 1 << lg;
-        const int g = tid >> lg, s = tid & (L - 1);
-        const int64_t p0 = tx.z;
-        const int32_t npad = tx.x;
-        const int32_t *sp = P.seg_pad + (int64_t)v * (H + 1);
-        const int32_t dn = tx.y;
-        const bool dl_staged = dn <= dl_cap;
-        const int32_t *dl = dl_staged ? dl_s : P.dlat + p0;
-        const int nc = IPT * H;  // counts per group
-        uint16_t *cg = c_s + g * nc;
-        int32_t inv[IPT];
-        uint32_t best[IPT];
-        bool any = false;
-#pragma unroll
-        for (int u = 0; u < IPT; ++u) {
-            const int32_t j = g * IPT + u;
-            inv[u] = j < m ? S.b_inv[S.op_start[v] + j0 + j] : -1;
-            any |= inv[u] >= 0;
-            best[u] = 0xFFFFFFFFu;
-        }
-        for (int32_t c0 = 0; c0 < npad; c0 += chunk) {
-            const int32_t cn = min(chunk, npad - c0);
+        tile_begin(S, ti, T);
+        const bool dl_staged = T.dn <= dl_cap;
+        uint16_t *cg = c_s + T.g * IPT * H;
+        for (int32_t c0 = 0; c0 < T.npad; c0 += chunk) {
+            const int32_t cn = min(chunk, T.npad - c0);
             __syncthreads();  // every thread is done with the previous chunk or tile
-            if (tid == 0) {
-                // the generic-proxy reads of the previous chunk are complete (barrier
-                // above); order them before the async-proxy writes that follow
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                if (c0 == 0 && dl_staged) {
-                    // the distinct latencies first (whole 16-byte words: dlat has
-                    // npad >= dn entries at this op)
-                    const uint32_t db = (uint32_t)((dn + 3) / 4) * 16u;
-                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                                 ::"r"(bar_d), "r"(db) : "memory");
-                    bulk_g2s(dl_s, P.dlat + p0, db, bar_d);
-                }
-                const uint32_t bytes = (uint32_t)cn * (MODE == LLAMA_MODE_ALPHA ? 6u : 4u);
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                             ::"r"(bar), "r"(bytes) : "memory");
-                bulk_g2s(lr_s, P.lrb + p0 + c0, 2u * cn, bar);
-                bulk_g2s(rf_s, P.rf + p0 + c0, 2u * cn, bar);
-                if (MODE == LLAMA_MODE_ALPHA) bulk_g2s(df_s, P.df + p0 + c0, 2u * cn, bar);
-            }
-            if (c0 == 0 && dl_staged) {
-                // every thread waits: the vote below must see the same outcome
-                if (!mbar_wait(bar_d, phase_d)) dl_ok = false;
-                phase_d ^= 1u;
-            }
-            if (c0 == 0 && dl_ok) {
-                // while the first chunk lands: the counts c(u, h) of distinct
-                // latencies below each slack, one per invocation u and segment h
-                if (dl_staged) {
-                    // from shared memory: the lanes of a group share the searches
-                    if (any) {
-                        for (int t = s; t < nc; t += L) {
-                            const int u = t / H, h = t - u * H;
-                            int32_t iu = inv[0];  // inv[u] without a runtime index into registers
-#pragma unroll
-                            for (int w = 1; w < IPT; ++w) iu = u == w ? inv[w] : iu;
-                            cg[t] = iu >= 0 ? (uint16_t)count_below(dl, dn, S.b_slack[(int64_t)iu * H + h]) : 0;
-                        }
-                    }
-                } else {
-                    // from global memory: each search is shared by G <= 32 lanes, a
-                    // G-ary search (a few dependent rounds instead of log2 dn).  A
-                    // round over n > G candidates [lo, lo + n) probes lo + (l+1)n/G - 1
-                    // for l < G (strictly increasing, the last one at lo + n - 1);
-                    // over n <= G candidates it probes each one.  Only shifts: G is
-                    // a power of two and (l+1)n < 2^19.
-                    const int G = L < 32 ? L : 32, lgG = lg < 5 ? lg : 5;
-                    const int W = L > 32 ? (L >> 5) : 1, sw = s >> 5, gl = s & (G - 1);
-                    const int gbase = (tid & 31) & ~(G - 1);
-                    const uint32_t gmask = G == 32 ? 0xFFFFFFFFu : ((1u << G) - 1u);
-                    for (int t0 = 0; t0 < nc; t0 += W) {
-                        const int t = t0 + sw, u = t / H, h = t - u * H;
-                        int32_t iu = inv[0];
-#pragma unroll
-                        for (int w = 1; w < IPT; ++w) iu = u == w ? inv[w] : iu;
-                        const bool act = t < nc && iu >= 0;
-                        const int32_t sl = act ? S.b_slack[(int64_t)iu * H + h] : 0;
-                        int32_t lo = 0, hi = act ? dn : 0;  // lo <= count <= hi
-                        if (G == 1) {  // one lane per invocation (tile-uniform): bisection
-                            lo = hi = act ? count_below(dl, dn, sl) : 0;
-                        }
-                        while (__any_sync(0xFFFFFFFFu, hi > lo)) {
-                            const int32_t n = hi - lo;
-                            const bool exact = n <= G;
-                            const int32_t pos = exact ? lo + gl : lo + (((gl + 1) * n) >> lgG) - 1;
-                            const bool pred = n > 0 && (!exact || gl < n) && __ldg(dl + pos) < sl;
-                            const int32_t c = __popc((__ballot_sync(0xFFFFFFFFu, pred) >> gbase) & gmask);
-                            if (n > 0) {
-                                if (exact) {
-                                    lo += c;
-                                    hi = lo;
-                                } else {
-                                    // the answer lies after the last probe below sl and
-                                    // at or before the first one that is not
-                                    const int32_t nhi = c < G ? lo + (((c + 1) * n) >> lgG) - 1 : hi;
-                                    lo = c > 0 ? lo + ((c * n) >> lgG) : lo;
-                                    hi = nhi;
-                                }
-                            }
-                        }
-                        if (act && gl == 0) cg[t] = (uint16_t)lo;
-                    }
-                }
-            }
+            if (tid == 0)
+                stage_chunk<MODE>(P, T.p0, c0, cn, c0 == 0 && dl_staged, T.dn, lr_s, rf_s, df_s, dl_s, bar);
+            if (c0 == 0 && !dl_staged) counts_from_global(P, S, T, H, P.dlat + T.p0, cg);
             // every thread must agree before any leaves the barrier sequence
-            if (!__syncthreads_and(mbar_wait(bar, phase) && dl_ok)) {
+            if (!__syncthreads_and(mbar_wait(bar, phase))) {
                 ok = false;
                 break;
             }
             phase ^= 1u;
-            if (any) {
-                const int qc0 = c0 / kVec, qc1 = (c0 + cn) / kVec;
-                const uint4 *lr4 = reinterpret_cast<const uint4 *>(lr_s);
-                const uint4 *rf4 = reinterpret_cast<const uint4 *>(rf_s);
-                const uint4 *df4 = reinterpret_cast<const uint4 *>(df_s);
-                for (int h = 0; h < H; ++h) {
-                    const int a = max(__ldg(sp + h) / kVec, qc0), b = min(__ldg(sp + h + 1) / kVec, qc1);
-                    if (a >= b) continue;
-                    uint32_t c2[IPT];
-#pragma unroll
-                    for (int u = 0; u < IPT; ++u) c2[u] = (uint32_t)cg[u * H + h] * 0x00010001u;
-                    for (int q = a + ((s - a) & (L - 1)); q < b; q += L) {
-                        const int r = q - qc0;
-                        const uint4 lk = lr4[r], rk = rf4[r];
-                        if (MODE == LLAMA_MODE_ALPHA) {
-                            const uint4 dk = df4[r];
-#pragma unroll
-                            for (int u = 0; u < IPT; ++u) best[u] = scan8_alpha(best[u], c2[u], lk, rk, dk);
-                        } else {
-#pragma unroll
-                            for (int u = 0; u < IPT; ++u) best[u] = scan8_cost_first(best[u], c2[u], lk, rk);
-                        }
-                    }
-                }
+            if (c0 == 0 && dl_staged) {
+                counts_from_shared(S, T, H, dl_s, cg);
+                __syncthreads();
             }
+            scan_chunk<MODE, IPT>(P, T, c0, cn, lr_s, rf_s, df_s, cg);
         }
         if (!ok) break;
-        uint32_t key[IPT];
-        const int wl = L < 32 ? L : 32;
-#pragma unroll
-        for (int u = 0; u < IPT; ++u) {
-            key[u] = inv[u] >= 0 ? min(best[u] & 0xFFFFu, best[u] >> 16) : 0xFFFFu;
-            for (int o = 1; o < wl; o <<= 1) key[u] = min(key[u], __shfl_xor_sync(0xffffffffu, key[u], o));
-        }
-        if (L > 32) {
-            // a group spans L/32 warps: combine the warps' minima in shared memory
-            if ((tid & 31) == 0)
-                for (int u = 0; u < IPT; ++u) red[u][tid >> 5] = key[u];
-            __syncthreads();
-            if (s < IPT)  // the decoding lanes (L > 32 > IPT here)
-                for (int u = 0; u < IPT; ++u)
-                    for (int w = 1; w < (L >> 5); ++w) key[u] = min(key[u], red[u][(tid >> 5) + w]);
-        }
-        // lane u mod 2^lg of the group decodes invocation u (every lane holds every key)
-#pragma unroll
-        for (int u = 0; u < IPT; ++u) {
-            if (s != (u & (L - 1)) || inv[u] < 0) continue;
-            const int32_t i = inv[u];
-            const int64_t c_base = P.cfg_off[v];
-            int32_t idx;
-            if (MODE == LLAMA_MODE_ALPHA) idx = P.inv[2 * c_base + key[u]];
-            else idx = key[u] < 0x8000u ? (int32_t)P.inv[2 * c_base + key[u]] : P.fast[v];
-            const int64_t gx = c_base + idx;
-            const int32_t Lx = P.lat[gx];
-            const int lam = backend_of(P.hw_off + (int64_t)v * (H + 1), H, idx);
-            const int32_t sl = S.b_slack[(int64_t)i * H + lam];
-            llama_decision dsn;
-            dsn.cfg = idx;
-            dsn.lat = Lx;
-            dsn.cost = P.cost[gx];
-            dsn.slack = sl;
-            dsn.flags = Lx < sl ? LLAMA_FLAG_FEASIBLE : 0;
-            out[i] = dsn;
-        }
+        finish_tile<MODE, IPT>(P, S, out, T, red);
         if (tid == 0) next_tile = (long long)(claim + gridDim.x);
         __syncthreads();
         ti = next_tile;
@@ -832,26 +888,121 @@ __device__ __forceinline__ void score_body(const DevProblem &P, const BucketScra
         // to land so no transfer targets this CTA's shared memory after exit
         if (tid == 0) atomicOr(&S.ctrl[kCtrlTimeout], 1ull);
         mbar_wait(bar, phase);
-        if (!dl_ok) mbar_wait(bar_d, phase_d ^ 1u);
     }
 }
 
-#define LLAMA_SCORE_KERNEL(name, MODE, IPT)                                                      \
+// Two staging buffers: while a chunk is scored, the next one (of the same tile,
+// or the first chunk of the CTA's next tile) is already on its way.  Tiles are
+// taken round-robin (blockIdx.x, + gridDim.x, ...), so the next tile is known
+// without waiting on a counter.
+template <int MODE, int IPT>
+__device__ __forceinline__ void score_body_pipe(const DevProblem &P, const BucketScratch &S,
+                                                llama_decision *out, int32_t chunk, int32_t dl_cap) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const size_t tbl = align16((size_t)chunk * (MODE == LLAMA_MODE_ALPHA ? 6 : 4));
+    const size_t stage = tbl + 4 * (size_t)dl_cap;  // dl_cap is a multiple of 4
+    uint16_t *c_s = reinterpret_cast<uint16_t *>(smem_raw + 2 * stage);
+    __shared__ __align__(8) unsigned long long mbar[2];
+    __shared__ uint32_t red[IPT][kScoreThreads / 32];
+    const int tid = threadIdx.x, H = P.n_hw;
+    const uint32_t bar0 = smem_addr(&mbar[0]);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    auto lr_of = [&](int st) { return reinterpret_cast<uint16_t *>(smem_raw + st * stage); };
+    auto dl_of = [&](int st) { return reinterpret_cast<int32_t *>(smem_raw + st * stage + tbl); };
+    auto issue = [&](int st, const int4 &tx, int32_t c0) {
+        // tx = {npad, dn, p0}
+        const int32_t cn = min(chunk, tx.x - c0);
+        uint16_t *lr = lr_of(st);
+        stage_chunk<MODE>(P, (int64_t)tx.z, c0, cn, c0 == 0 && tx.y <= dl_cap, tx.y, lr, lr + chunk,
+                          lr + 2 * chunk, dl_of(st), bar0 + 8 * st);
+    };
+    uint32_t phases = 0;   // bit st: parity of stage st's next completion
+    uint32_t pending = 0;  // bit st: a copy into stage st is in flight
+    bool ok = true;
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const long long n_tiles = (long long)S.ctrl[kCtrlTiles];
+    long long ti = blockIdx.x;
+    if (ti < n_tiles) {
+        if (tid == 0) issue(0, S.tiles[2 * ti + 1], 0);
+        pending = 1u;
+    }
+    int st = 0;
+    TileState<IPT> T;
+    while (ti < n_tiles) {
+        const long long tn = ti + gridDim.x;
+        const int4 txn = tn < n_tiles ? S.tiles[2 * tn + 1] : make_int4(0, 0, 0, 0);
+        tile_begin(S, ti, T);
+        const bool dl_staged = T.dn <= dl_cap;
+        uint16_t *cg = c_s + T.g * IPT * H;
+        for (int32_t c0 = 0; c0 < T.npad; c0 += chunk) {
+            const int32_t cn = min(chunk, T.npad - c0);
+            __syncthreads();  // every thread is done with the other stage and with cg
+            // the item after this one: the next chunk, or the next tile's first
+            if (c0 + chunk < T.npad || tn < n_tiles) {
+                if (tid == 0) {
+                    if (c0 + chunk < T.npad) issue(st ^ 1, make_int4(T.npad, T.dn, (int32_t)T.p0, 0), c0 + chunk);
+                    else issue(st ^ 1, txn, 0);
+                }
+                pending |= 1u << (st ^ 1);
+            }
+            if (c0 == 0 && !dl_staged) counts_from_global(P, S, T, H, P.dlat + T.p0, cg);
+            if (!__syncthreads_and(mbar_wait(bar0 + 8 * st, (phases >> st) & 1u))) {
+                ok = false;
+                break;
+            }
+            phases ^= 1u << st;
+            pending &= ~(1u << st);
+            uint16_t *lr = lr_of(st);
+            if (c0 == 0 && dl_staged) {
+                counts_from_shared(S, T, H, dl_of(st), cg);
+                __syncthreads();
+            }
+            scan_chunk<MODE, IPT>(P, T, c0, cn, lr, lr + chunk, lr + 2 * chunk, cg);
+            st ^= 1;
+        }
+        if (!ok) break;
+        finish_tile<MODE, IPT>(P, S, out, T, red);
+        ti = tn;
+    }
+    if (!ok) {
+        // report, then wait (bounded) for every copy still in flight
+        if (tid == 0) atomicOr(&S.ctrl[kCtrlTimeout], 1ull);
+        for (int k = 0; k < 2; ++k)
+            if (pending & (1u << k)) mbar_wait(bar0 + 8 * k, (phases >> k) & 1u);
+    }
+}
+
+#define LLAMA_SCORE_KERNEL(name, MODE, IPT, BODY)                                                \
     __global__ void __launch_bounds__(kScoreThreads)                                            \
         name(DevProblem P, BucketScratch S, llama_decision *out, int32_t chunk, int32_t dl_cap) { \
-        score_body<MODE, IPT>(P, S, out, chunk, dl_cap);                                          \
+        BODY<MODE, IPT>(P, S, out, chunk, dl_cap);                                                \
     }
-LLAMA_SCORE_KERNEL(k_score_cf1, LLAMA_MODE_COST_FIRST, 1)
-LLAMA_SCORE_KERNEL(k_score_cf2, LLAMA_MODE_COST_FIRST, 2)
-LLAMA_SCORE_KERNEL(k_score_cf4, LLAMA_MODE_COST_FIRST, 4)
-LLAMA_SCORE_KERNEL(k_score_al1, LLAMA_MODE_ALPHA, 1)
-LLAMA_SCORE_KERNEL(k_score_al2, LLAMA_MODE_ALPHA, 2)
-LLAMA_SCORE_KERNEL(k_score_al4, LLAMA_MODE_ALPHA, 4)
+LLAMA_SCORE_KERNEL(k_score_cf1, LLAMA_MODE_COST_FIRST, 1, score_body)
+LLAMA_SCORE_KERNEL(k_score_cf2, LLAMA_MODE_COST_FIRST, 2, score_body)
+LLAMA_SCORE_KERNEL(k_score_cf4, LLAMA_MODE_COST_FIRST, 4, score_body)
+LLAMA_SCORE_KERNEL(k_score_al1, LLAMA_MODE_ALPHA, 1, score_body)
+LLAMA_SCORE_KERNEL(k_score_al2, LLAMA_MODE_ALPHA, 2, score_body)
+LLAMA_SCORE_KERNEL(k_score_al4, LLAMA_MODE_ALPHA, 4, score_body)
+LLAMA_SCORE_KERNEL(k_score2_cf1, LLAMA_MODE_COST_FIRST, 1, score_body_pipe)
+LLAMA_SCORE_KERNEL(k_score2_cf2, LLAMA_MODE_COST_FIRST, 2, score_body_pipe)
+LLAMA_SCORE_KERNEL(k_score2_cf4, LLAMA_MODE_COST_FIRST, 4, score_body_pipe)
+LLAMA_SCORE_KERNEL(k_score2_al1, LLAMA_MODE_ALPHA, 1, score_body_pipe)
+LLAMA_SCORE_KERNEL(k_score2_al2, LLAMA_MODE_ALPHA, 2, score_body_pipe)
+LLAMA_SCORE_KERNEL(k_score2_al4, LLAMA_MODE_ALPHA, 4, score_body_pipe)
 #undef LLAMA_SCORE_KERNEL
 
-const void *score_kernel(int mode, int ipt) {
-    if (mode == LLAMA_MODE_ALPHA)
-        return ipt >= 4 ? (const void *)k_score_al4 : ipt == 2 ? (const void *)k_score_al2 : (const void *)k_score_al1;
+const void *score_kernel(int mode, int ipt, int stages) {
+    const bool al = mode == LLAMA_MODE_ALPHA;
+    if (stages >= 2) {
+        if (al) return ipt >= 4 ? (const void *)k_score2_al4 : ipt == 2 ? (const void *)k_score2_al2 : (const void *)k_score2_al1;
+        return ipt >= 4 ? (const void *)k_score2_cf4 : ipt == 2 ? (const void *)k_score2_cf2 : (const void *)k_score2_cf1;
+    }
+    if (al) return ipt >= 4 ? (const void *)k_score_al4 : ipt == 2 ? (const void *)k_score_al2 : (const void *)k_score_al1;
     return ipt >= 4 ? (const void *)k_score_cf4 : ipt == 2 ? (const void *)k_score_cf2 : (const void *)k_score_cf1;
 }
 
@@ -910,7 +1061,7 @@ cudaError_t enqueue_schedule(const ContextView &v, const BucketScratch &S, int64
     BucketScratch Sc = S;
     int32_t chunk = v.score_chunk, dl_cap = v.dlat_cap;
     void *args[] = {&P, &Sc, &out, &chunk, &dl_cap};
-    e = cudaLaunchKernelExC(&cfg, score_kernel(v.mode, v.ipt), args);
+    e = cudaLaunchKernelExC(&cfg, score_kernel(v.mode, v.ipt, v.stages), args);
     if (e != cudaSuccess) return e;
     mark(2);
     return cudaGetLastError();
@@ -1105,6 +1256,15 @@ __global__ void k_encode_lat(DevProblem P, uint16_t *lrb, int32_t *dlat, int32_t
         lrb[p0 + sp[lam] + (x - hw[lam])] = (uint16_t)(kLatRankBias + rank);
     }
     if (tid == T - 1) dlat_n[v] = warp_tot[(T >> 5) - 1];
+}
+
+// The 32 first-round probe values of every op with more than 32 distinct
+// latencies (one thread per value).
+__global__ void k_encode_piv(DevProblem P, int32_t *dpiv) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= 32 * (int64_t)P.n_ops) return;
+    const int32_t v = (int32_t)(k >> 5), l = (int32_t)(k & 31), dn = P.dlat_n[v];
+    dpiv[k] = dn > 32 ? P.dlat[P.pad_off[v] + (((l + 1) * dn) >> 5) - 1] : INT32_MAX;
 }
 
 }  // namespace llama

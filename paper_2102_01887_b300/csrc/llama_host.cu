@@ -76,7 +76,7 @@ struct llama_ctx {
     int32_t n_ops = 0, max_npad = 0;
     int64_t n_cfg = 0, n_pad = 0;
     DevBuf cfg_off, hw_off, lat, cost, ref_cfg, batch, res, res_total;
-    DevBuf pad_off, seg_pad, lrb, dlat, dlat_n, rf, df, inv, fast, op_order, ref_gidx;
+    DevBuf pad_off, seg_pad, lrb, dlat, dlat_n, dpiv, rf, df, inv, fast, op_order, ref_gidx;
     int64_t mean_npad = 0;
     DevBuf ref, cp, cp_magic;
     int64_t q[LLAMA_MAX_HW] = {0};
@@ -86,7 +86,7 @@ struct llama_ctx {
     int32_t cap_ops = 0;
     DevBuf cnt, ctrl, op_start, gop, slot, b_inv, b_slack, rbase, tiles;
     // scoring kernel geometry (set by llama_set_profiles)
-    int32_t min_vpl = 16, ipt = 2, score_grid = 0, score_chunk = 0, bucket_max_blocks = 0, dlat_cap = 0;
+    int32_t min_vpl = 16, ipt = 2, stages = 1, score_grid = 0, score_chunk = 0, bucket_max_blocks = 0, dlat_cap = 0;
     size_t score_smem = 0;
 
     // staging for host-memory arguments of the blocking calls
@@ -158,6 +158,7 @@ DevProblem make_problem(const llama_ctx *c) {
     P.lrb = c->lrb.as<uint16_t>();
     P.dlat = c->dlat.as<int32_t>();
     P.dlat_n = c->dlat_n.as<int32_t>();
+    P.dpiv = c->dpiv.as<int32_t>();
     P.rf = c->rf.as<uint16_t>();
     P.df = c->df.as<uint16_t>();
     P.inv = c->inv.as<uint16_t>();
@@ -186,7 +187,7 @@ DevProblem make_problem(const llama_ctx *c) {
         };
         add(c->dag_op_off); add(c->slo); add(c->row_ptr); add(c->col); add(c->topo);
         add(c->lvl_off); add(c->dag_lvl); add(c->ref_gidx); add(c->op_order); add(c->pad_off);
-        add(c->seg_pad); add(c->dlat_n); add(c->fast); add(c->hw_off);
+        add(c->seg_pad); add(c->dlat_n); add(c->fast); add(c->hw_off); add(c->dpiv);
         if (c->lat.bytes + c->cost.bytes + c->inv.bytes <= (size_t)c->l2_bytes / 4) {
             add(c->lat); add(c->cost);
         }
@@ -233,6 +234,7 @@ ContextView view_of(const llama_ctx *c) {
     v.num_sms = c->num_sms;
     v.min_vpl = c->min_vpl;
     v.ipt = c->ipt;
+    v.stages = c->stages;
     v.score_grid = c->score_grid;
     v.bucket_max_blocks = c->bucket_max_blocks;
     v.score_chunk = c->score_chunk;
@@ -340,20 +342,31 @@ int grid_for(const llama_ctx *c, int64_t n, int threads) {
 }
 
 // The launch sequence of one scheduling call (all device pointers).
-// Shared memory of the scoring kernel: a staging chunk of latency ranks and
-// objective ranks (plus rank differences in alpha mode), one count per
-// (invocation, backend) for every group of the CTA (at most one group per
-// thread), then the op's distinct latencies.
+// Shared memory of the scoring kernel: per staging buffer, a chunk of latency
+// ranks and objective ranks (plus rank differences in alpha mode) and the op's
+// distinct latencies; then one count per (invocation, backend) for every group
+// of the CTA (at most one group per thread).
 size_t score_smem_bytes(const llama_ctx *c) {
-    const size_t tbl = (size_t)c->score_chunk * (c->opts.mode == LLAMA_MODE_ALPHA ? 6 : 4);
+    const size_t tbl = ((size_t)c->score_chunk * (c->opts.mode == LLAMA_MODE_ALPHA ? 6 : 4) + 15) / 16 * 16;
     const size_t counts = (size_t)kScoreThreads * c->ipt * c->opts.n_hw * 2;
-    return (tbl + counts + 15) / 16 * 16 + 4 * (size_t)c->dlat_cap;
+    return (size_t)c->stages * (tbl + 4 * (size_t)c->dlat_cap) + counts;
+}
+
+// Default staging chunk: the largest padded table split into the fewest pieces
+// of at most kMaxChunk entries plus the padding of its segments, as evenly as
+// multiples of 8 allow (a table of 8,208 entries goes in two chunks of 4,104,
+// not 4,096 + 4,096 + 16).
+int32_t default_chunk(int32_t max_npad) {
+    const int32_t cap = kMaxChunk + kVec * LLAMA_MAX_HW;
+    const int32_t pieces = (max_npad + cap - 1) / cap;
+    const int32_t per = (max_npad + pieces - 1) / pieces;
+    return (per + kVec - 1) / kVec * kVec;
 }
 
 // Dynamic shared memory and persistent grid of the scoring kernel for the
 // current profiles and tuning.
 int configure_score(llama_ctx *c) {
-    const void *fn = score_kernel(c->opts.mode, c->ipt);
+    const void *fn = score_kernel(c->opts.mode, c->ipt, c->stages);
     LL_CUDA(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->score_smem));
     int nb = 0;
     LL_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kScoreThreads, c->score_smem));
@@ -713,6 +726,7 @@ extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cf
         (e = c->lrb.alloc(2 * (size_t)n_pad)) != cudaSuccess ||
         (e = c->dlat.alloc(4 * (size_t)n_pad)) != cudaSuccess ||
         (e = c->dlat_n.alloc(4 * (size_t)n_ops)) != cudaSuccess ||
+        (e = c->dpiv.alloc(4 * 32 * (size_t)n_ops)) != cudaSuccess ||
         (e = c->rf.alloc(2 * (size_t)n_pad)) != cudaSuccess ||
         (e = c->inv.alloc(2 * 2 * (size_t)n_cfg)) != cudaSuccess ||
         (e = c->fast.alloc(4 * (size_t)n_ops)) != cudaSuccess ||
@@ -755,6 +769,7 @@ extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cf
     LL_CUDA(c, cudaFuncSetAttribute(k_encode_lat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lat_smem));
     k_encode_lat<<<n_ops, 1024, lat_smem, c->stream>>>(P, c->lrb.as<uint16_t>(), c->dlat.as<int32_t>(),
                                                       c->dlat_n.as<int32_t>());
+    k_encode_piv<<<(unsigned)((32 * (int64_t)n_ops + 255) / 256), 256, 0, c->stream>>>(P, c->dpiv.as<int32_t>());
     k_encode_rank<<<n_ops, 1024, sort_smem, c->stream>>>(P, sort_cap, c->rf.as<uint16_t>(),
                                                         alpha ? c->df.as<uint16_t>() : nullptr,
                                                         c->inv.as<uint16_t>());
@@ -783,7 +798,7 @@ extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cf
 
     // scoring kernel: stage tables in chunks of at most kMaxChunk entries, one
     // persistent CTA per resident slot
-    c->score_chunk = std::min<int32_t>(max_npad, kMaxChunk);
+    c->score_chunk = default_chunk(max_npad);
     c->score_smem = score_smem_bytes(c);
     const int rc = configure_score(c);
     if (rc) return rc;
@@ -803,21 +818,22 @@ extern "C" int llama_set_queue(llama_ctx *c, const int64_t *q_us) {
 }
 
 extern "C" int llama_set_tuning(llama_ctx *c, int32_t lanes_min_vectors, int32_t inv_per_thread,
-                                int32_t chunk_entries) {
+                                int32_t chunk_entries, int32_t stages) {
     if (!c) return LLAMA_EINVAL;
     if (lanes_min_vectors < 1 || lanes_min_vectors > 1024)
         return c->fail(LLAMA_EINVAL, "set_tuning: lanes_min_vectors out of 1..1024");
     if (inv_per_thread != 1 && inv_per_thread != 2 && inv_per_thread != 4)
         return c->fail(LLAMA_EINVAL, "set_tuning: inv_per_thread must be 1, 2 or 4");
-    if (chunk_entries < 0 || chunk_entries > LLAMA_MAX_CFG || chunk_entries % kVec)
-        return c->fail(LLAMA_EINVAL, "set_tuning: chunk_entries must be a multiple of 8 in 0..8192");
+    if (chunk_entries < 0 || chunk_entries > LLAMA_MAX_CFG + kVec * LLAMA_MAX_HW || chunk_entries % kVec)
+        return c->fail(LLAMA_EINVAL, "set_tuning: chunk_entries must be a multiple of 8 in 0..8256");
+    if (stages != 1 && stages != 2) return c->fail(LLAMA_EINVAL, "set_tuning: stages must be 1 or 2");
     if (!c->prof_set) return c->fail(LLAMA_ENOTREADY, "set_tuning: set the profiles first");
     DeviceGuard g(c->opts.device);
     c->drop_graph();
     c->min_vpl = lanes_min_vectors;
     c->ipt = inv_per_thread;
-    c->score_chunk = chunk_entries ? std::min<int32_t>(chunk_entries, c->max_npad)
-                                   : std::min<int32_t>(c->max_npad, kMaxChunk);
+    c->stages = stages;
+    c->score_chunk = chunk_entries ? std::min<int32_t>(chunk_entries, c->max_npad) : default_chunk(c->max_npad);
     c->score_smem = score_smem_bytes(c);
     return configure_score(c);
 }

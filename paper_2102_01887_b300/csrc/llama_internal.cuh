@@ -41,7 +41,7 @@ constexpr int kMaxWaitTries = 1 << 20; // bounded mbarrier waits
 constexpr int kKeep = 4;               // invocations a counting thread keeps in registers
 constexpr int kKeepOps = 2;            // ops the layout keeps in registers per thread
 constexpr int kMaxDlatSmem = 4096;     // distinct latencies staged per op (else searched in L2)
-constexpr int kPfArrays = 16;          // arrays k_bucket prefetches into L2 at its start
+constexpr int kPfArrays = 20;          // arrays k_bucket prefetches into L2 at its start
 constexpr int kCntStride = 32;     // int32 slots between per-op counters: one 128-byte line each
 // control words of a call (unsigned long long each)
 constexpr int kCtrlInvalid = 0;    // invalid invocations
@@ -74,6 +74,9 @@ struct DevProblem {
     const int32_t *seg_pad;
     const uint16_t *lrb;
     const int32_t *dlat, *dlat_n;
+    // [n_ops*32] per op with more than 32 distinct latencies, the 32 values a
+    // 32-lane search probes first: dlat[pad_off[v] + ((l+1)*dn >> 5) - 1], l < 32
+    const int32_t *dpiv;
     const uint16_t *rf, *df, *inv;
     const int32_t *fast;
     const int32_t *op_order;  // ops by padded table size, largest first (bucket order)
@@ -112,9 +115,9 @@ struct BucketScratch {
     int32_t *gop;             // [n_inv]     global op of each invocation, -1 if invalid
     int32_t *slot;            // [n_inv]     rank of the invocation inside its op's bucket
     int32_t *b_inv;           // [n_inv]     invocation at each bucket position
-    int32_t *b_slack;         // [n_inv*H]   slack per invocation and backend
+    int32_t *b_slack;         // [n_inv*H]   slack per backend of the invocation at each bucket position
     int64_t *rbase;           // [n_inv]     target - elapsed time of each invocation
-    int4 *tiles;              // [2*max_tiles] scoring tiles: {op, j0, m, lanes_log2},
+    int4 *tiles;              // [2*max_tiles] scoring tiles: {op, first bucket position, m, lanes_log2},
                               // {padded entries, distinct latencies, padded offset, 0}
 };
 
@@ -145,6 +148,7 @@ struct ContextView {
     int32_t n_dags, n_ops, n_hw, mode, device, num_sms;
     int32_t min_vpl;      // vectors a lane should scan at least (sets lanes per invocation)
     int32_t ipt;          // invocations per scoring thread (1, 2 or 4)
+    int32_t stages;       // staging buffers of the scoring kernel (1 or 2)
     int32_t score_grid;   // persistent CTAs of the scoring kernel
     int32_t bucket_max_blocks;  // co-resident blocks of k_bucket (cooperative launch)
     int32_t score_chunk;  // table entries staged per chunk
@@ -161,14 +165,25 @@ __global__ void k_bucket(DevProblem P, int64_t n_inv, const int32_t *dag, const 
                          const int64_t *start, int64_t now, BucketScratch S, llama_decision *out,
                          const int32_t *topo, const int32_t *lvl_off, const int32_t *dag_lvl,
                          int32_t min_vpl, int32_t ipt, int32_t n_cp);
-// Scoring kernels: objective mode x invocations per thread (1, 2 or 4).
-__global__ void k_score_cf1(DevProblem P, BucketScratch S, llama_decision *out, int32_t chunk, int32_t dl_cap);
-__global__ void k_score_cf2(DevProblem P, BucketScratch S, llama_decision *out, int32_t chunk, int32_t dl_cap);
-__global__ void k_score_cf4(DevProblem P, BucketScratch S, llama_decision *out, int32_t chunk, int32_t dl_cap);
-__global__ void k_score_al1(DevProblem P, BucketScratch S, llama_decision *out, int32_t chunk, int32_t dl_cap);
-__global__ void k_score_al2(DevProblem P, BucketScratch S, llama_decision *out, int32_t chunk, int32_t dl_cap);
-__global__ void k_score_al4(DevProblem P, BucketScratch S, llama_decision *out, int32_t chunk, int32_t dl_cap);
-const void *score_kernel(int mode, int ipt);
+// Scoring kernels: objective mode x invocations per thread (1, 2 or 4) x
+// staging buffers (k_score: one, tiles claimed dynamically; k_score2: two,
+// tiles round-robin).
+#define LLAMA_DECLARE_SCORE(name) \
+    __global__ void name(DevProblem P, BucketScratch S, llama_decision *out, int32_t chunk, int32_t dl_cap);
+LLAMA_DECLARE_SCORE(k_score_cf1)
+LLAMA_DECLARE_SCORE(k_score_cf2)
+LLAMA_DECLARE_SCORE(k_score_cf4)
+LLAMA_DECLARE_SCORE(k_score_al1)
+LLAMA_DECLARE_SCORE(k_score_al2)
+LLAMA_DECLARE_SCORE(k_score_al4)
+LLAMA_DECLARE_SCORE(k_score2_cf1)
+LLAMA_DECLARE_SCORE(k_score2_cf2)
+LLAMA_DECLARE_SCORE(k_score2_cf4)
+LLAMA_DECLARE_SCORE(k_score2_al1)
+LLAMA_DECLARE_SCORE(k_score2_al2)
+LLAMA_DECLARE_SCORE(k_score2_al4)
+#undef LLAMA_DECLARE_SCORE
+const void *score_kernel(int mode, int ipt, int stages);
 
 // Scoring tiles a call may lay out (each op: full tiles plus one tail).
 int64_t max_tiles(int64_t n_inv, int32_t n_ops);
@@ -183,6 +198,7 @@ __global__ void k_slack(DevProblem P, int64_t n_inv, const int32_t *dag, const i
                         const int64_t *start, int64_t now, int32_t *slack_out);
 __global__ void k_encode_pad(DevProblem P, uint16_t *lrb, uint16_t *rf, uint16_t *df, int32_t *fast);
 __global__ void k_encode_lat(DevProblem P, uint16_t *lrb, int32_t *dlat, int32_t *dlat_n);
+__global__ void k_encode_piv(DevProblem P, int32_t *dpiv);
 __global__ void k_encode_rank(DevProblem P, int32_t sort_n, uint16_t *rf, uint16_t *df,
                               uint16_t *inv);
 

@@ -71,7 +71,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "llama_schedule": ([vp, i64, vp, vp, vp, i64, vp], ctypes.c_int),
             "llama_schedule_async": ([vp, i64, vp, vp, vp, i64, vp, vp], ctypes.c_int),
             "llama_schedule_static": ([vp, i64, vp, vp, vp, i64, vp, vp], ctypes.c_int),
-            "llama_set_tuning": ([vp, i32, i32, i32], ctypes.c_int),
+            "llama_set_tuning": ([vp, i32, i32, i32, i32], ctypes.c_int),
             "llama_reserve": ([vp, i64], ctypes.c_int),
             "llama_critical_path": ([vp, vp], ctypes.c_int),
             "llama_slack": ([vp, i64, vp, vp, vp, i64, vp], ctypes.c_int),
@@ -147,9 +147,9 @@ def llama_set_queue(ctx, q_us) -> None:
 
 
 def llama_set_tuning(ctx, lanes_min_vectors: int = 16, inv_per_thread: int = 2,
-                     chunk_entries: int = 0) -> None:
+                     chunk_entries: int = 0, stages: int = 1) -> None:
     _check(ctx, load().llama_set_tuning(ctx, int(lanes_min_vectors), int(inv_per_thread),
-                                        int(chunk_entries)))
+                                        int(chunk_entries), int(stages)))
 
 
 def llama_reserve(ctx, max_inv: int) -> None:

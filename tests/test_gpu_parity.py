@@ -276,6 +276,14 @@ def test_errors(L):
             L.llama_set_profiles(ctx, [0, n], [0, n, n, n], np.ones(n), np.ones(n), [0])
         with pytest.raises(L.LlamaError):  # negative queueing time
             L.llama_set_queue(ctx, [0, -1, 0])
+        with pytest.raises(L.LlamaError) as e:  # tuning before the profiles
+            L.llama_set_tuning(ctx, 16, 2, 0, 1)
+        assert e.value.code == L.ENOTREADY
+        for bad in ((0, 2, 0, 1), (2048, 2, 0, 1), (16, 3, 0, 1), (16, 2, 12, 1), (16, 2, 8264, 1),
+                    (16, 2, 0, 3), (16, 2, 0, 0)):
+            with pytest.raises(L.LlamaError) as e:
+                L.llama_set_tuning(ctx, *bad)
+            assert e.value.code == L.EINVAL, bad
     finally:
         L.llama_destroy(ctx)
 
@@ -320,8 +328,10 @@ def test_graph_replay_tracks_now_sizes_and_contents(L):
 
 # ------------------------------------------------------- launch schedules ---
 
-@pytest.mark.parametrize("tuning", [(1, 1, 0), (4, 2, 0), (16, 4, 0), (64, 2, 0), (1024, 1, 0),
-                                    (16, 2, 64), (2, 4, 8), (8, 1, 136)])
+@pytest.mark.parametrize("tuning", [(1, 1, 0, 1), (4, 2, 0, 1), (16, 4, 0, 1), (64, 2, 0, 1),
+                                    (1024, 1, 0, 1), (16, 2, 64, 1), (2, 4, 8, 1), (8, 1, 136, 1),
+                                    (1, 1, 0, 2), (16, 2, 0, 2), (32, 1, 0, 2), (64, 4, 0, 2),
+                                    (1024, 2, 0, 2), (16, 2, 64, 2), (2, 1, 8, 2), (8, 4, 136, 2)])
 def test_tunings_change_no_result(L, tuning):
     # every kernel variant (1/2/4 invocations per thread), lane counts from one
     # to a whole CTA per invocation, and chunked staging of tables larger than
