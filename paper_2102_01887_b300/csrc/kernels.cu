@@ -339,7 +339,8 @@ __device__ void layout_write(const DevProblem &P, const BucketScratch &S, int32_
         const int32_t v = oi.x, nvec = oi.y;
         const int lg = lanes_log2_for(nvec, min_vpl);
         const int32_t per_tile = (kScoreThreads >> lg) * ipt;
-        const int4 tx = make_int4(nvec * kVec, oi.w, oi.z, 0);  // {npad, distinct, offset}
+        // {padded entries, distinct latencies, padded offset, first configuration}
+        const int4 tx = make_int4(nvec * kVec, oi.w, oi.z, __ldg(P.ord_cbase + k));
         S.op_start[v] = pos;
         int32_t j = 0;
         for (; j + per_tile <= ck; j += per_tile, ++tf) {
@@ -615,6 +616,7 @@ template <int IPT>
 struct TileState {
     int32_t v, m, lg, L, g, s, npad, dn;
     int32_t pos0;  // bucket position of the group's first invocation
+    int32_t cbase;  // cfg_off of the op
     int64_t p0;
     int32_t inv[IPT];
     uint32_t best[IPT];
@@ -633,6 +635,7 @@ __device__ __forceinline__ void tile_begin(const BucketScratch &S, long long ti,
     T.npad = tx.x;
     T.dn = tx.y;
     T.p0 = tx.z;
+    T.cbase = tx.w;
     T.any = false;
     T.pos0 = tile.y + T.g * IPT;
 #pragma unroll
@@ -779,20 +782,16 @@ __device__ __forceinline__ void finish_tile(const DevProblem &P, const BucketScr
     for (int u = 0; u < IPT; ++u) {
         if (T.s != (u & (T.L - 1)) || T.inv[u] < 0) continue;
         const int32_t i = T.inv[u];
-        const int64_t c_base = P.cfg_off[T.v];
-        int32_t idx;
-        if (MODE == LLAMA_MODE_ALPHA) idx = P.inv[2 * c_base + key[u]];
-        else idx = key[u] < 0x8000u ? (int32_t)P.inv[2 * c_base + key[u]] : P.fast[T.v];
-        const int64_t gx = c_base + idx;
-        const int32_t Lx = P.lat[gx];
-        const int lam = backend_of(P.hw_off + (int64_t)T.v * (H + 1), H, idx);
-        const int32_t sl = S.b_slack[(int64_t)(T.pos0 + u) * H + lam];
+        int4 d;
+        if (MODE == LLAMA_MODE_ALPHA) d = P.dec[2 * (int64_t)T.cbase + key[u]];
+        else d = key[u] < 0x8000u ? P.dec[(int64_t)T.cbase + key[u]] : P.dfast[T.v];
+        const int32_t sl = S.b_slack[(int64_t)(T.pos0 + u) * H + (d.x >> 16)];
         llama_decision dsn;
-        dsn.cfg = idx;
-        dsn.lat = Lx;
-        dsn.cost = P.cost[gx];
+        dsn.cfg = d.x & 0xFFFF;
+        dsn.lat = d.y;
+        dsn.cost = (int64_t)(((uint64_t)(uint32_t)d.w << 32) | (uint32_t)d.z);
         dsn.slack = sl;
-        dsn.flags = Lx < sl ? LLAMA_FLAG_FEASIBLE : 0;
+        dsn.flags = d.y < sl ? LLAMA_FLAG_FEASIBLE : 0;
         out[i] = dsn;
     }
 }
@@ -893,8 +892,9 @@ __device__ __forceinline__ void score_body(const DevProblem &P, const BucketScra
 
 // Two staging buffers: while a chunk is scored, the next one (of the same tile,
 // or the first chunk of the CTA's next tile) is already on its way.  Tiles are
-// taken round-robin (blockIdx.x, + gridDim.x, ...), so the next tile is known
-// without waiting on a counter.
+// claimed from the counter one tile ahead: while tile k is scored the CTA
+// already knows tile k + 1 (its first chunk is staged during tile k) and the
+// claim of tile k + 2 is in flight.
 template <int MODE, int IPT>
 __device__ __forceinline__ void score_body_pipe(const DevProblem &P, const BucketScratch &S,
                                                 llama_decision *out, int32_t chunk, int32_t dl_cap) {
@@ -904,6 +904,7 @@ __device__ __forceinline__ void score_body_pipe(const DevProblem &P, const Bucke
     uint16_t *c_s = reinterpret_cast<uint16_t *>(smem_raw + 2 * stage);
     __shared__ __align__(8) unsigned long long mbar[2];
     __shared__ uint32_t red[IPT][kScoreThreads / 32];
+    __shared__ long long next_tile;
     const int tid = threadIdx.x, H = P.n_hw;
     const uint32_t bar0 = smem_addr(&mbar[0]);
     if (tid == 0) {
@@ -926,15 +927,19 @@ __device__ __forceinline__ void score_body_pipe(const DevProblem &P, const Bucke
     bool ok = true;
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const long long n_tiles = (long long)S.ctrl[kCtrlTiles];
-    long long ti = blockIdx.x;
+    long long ti = blockIdx.x, tn;
+    if (tid == 0) next_tile = (long long)atomicAdd(&S.ctrl[kCtrlNextTile], 1ull) + gridDim.x;
     if (ti < n_tiles) {
         if (tid == 0) issue(0, S.tiles[2 * ti + 1], 0);
         pending = 1u;
     }
+    __syncthreads();
+    tn = next_tile;
     int st = 0;
     TileState<IPT> T;
     while (ti < n_tiles) {
-        const long long tn = ti + gridDim.x;
+        unsigned long long claim = 0;
+        if (tid == 0) claim = atomicAdd(&S.ctrl[kCtrlNextTile], 1ull);  // the tile after tn
         const int4 txn = tn < n_tiles ? S.tiles[2 * tn + 1] : make_int4(0, 0, 0, 0);
         tile_begin(S, ti, T);
         const bool dl_staged = T.dn <= dl_cap;
@@ -967,7 +972,10 @@ __device__ __forceinline__ void score_body_pipe(const DevProblem &P, const Bucke
         }
         if (!ok) break;
         finish_tile<MODE, IPT>(P, S, out, T, red);
+        if (tid == 0) next_tile = (long long)(claim + gridDim.x);
+        __syncthreads();
         ti = tn;
+        tn = next_tile;
     }
     if (!ok) {
         // report, then wait (bounded) for every copy still in flight
@@ -1265,6 +1273,26 @@ __global__ void k_encode_piv(DevProblem P, int32_t *dpiv) {
     if (k >= 32 * (int64_t)P.n_ops) return;
     const int32_t v = (int32_t)(k >> 5), l = (int32_t)(k & 31), dn = P.dlat_n[v];
     dpiv[k] = dn > 32 ? P.dlat[P.pad_off[v] + (((l + 1) * dn) >> 5) - 1] : INT32_MAX;
+}
+
+// Decode tables (one CTA per op): the configuration behind every rank, and the
+// fastest one.
+__global__ void k_encode_dec(DevProblem P, int4 *dec, int4 *dfast) {
+    const int v = blockIdx.x, H = P.n_hw;
+    const int64_t c0 = P.cfg_off[v];
+    const int n = (int)(P.cfg_off[v + 1] - c0);
+    const bool alpha = P.mode == LLAMA_MODE_ALPHA;
+    const int cnt = alpha ? 2 * n : n;
+    const int64_t off = alpha ? 2 * c0 : c0;
+    const int32_t *hw = P.hw_off + (int64_t)v * (H + 1);
+    auto entry = [&](int x) {
+        const int64_t g = c0 + x;
+        const uint64_t cost = (uint64_t)P.cost[g];
+        return make_int4(x | (backend_of(hw, H, x) << 16), P.lat[g], (int32_t)(uint32_t)cost,
+                         (int32_t)(uint32_t)(cost >> 32));
+    };
+    for (int r = threadIdx.x; r < cnt; r += blockDim.x) dec[off + r] = entry(P.inv[2 * c0 + r]);
+    if (threadIdx.x == 0) dfast[v] = entry(P.fast[v]);
 }
 
 }  // namespace llama

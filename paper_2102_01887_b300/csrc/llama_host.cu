@@ -69,7 +69,7 @@ struct llama_ctx {
     // host copies of the DAG structure (for the packed per-DAG layout)
     std::vector<int32_t> h_dag_op_off, h_row_ptr, h_col, h_topo, h_lvl_off, h_dag_lvl;
     std::vector<int64_t> h_ref_gidx;
-    DevBuf dag_pack, dag_pack_off, ord_info;
+    DevBuf dag_pack, dag_pack_off, ord_info, ord_cbase, dec, dfast;
 
     // profiles
     bool prof_set = false;
@@ -172,6 +172,9 @@ DevProblem make_problem(const llama_ctx *c) {
     P.prefetch_dlat_lines = pf ? (4 * c->n_pad + 127) / 128 : 0;
     P.ref_gidx = c->ref_gidx.as<int64_t>();
     P.ord_info = c->ord_info.as<int4>();
+    P.ord_cbase = c->ord_cbase.as<int32_t>();
+    P.dec = c->dec.as<int4>();
+    P.dfast = c->dfast.as<int4>();
     P.dag_pack = c->dag_pack.as<int32_t>();
     P.dag_pack_off = c->dag_pack_off.as<int64_t>();
     // arrays whose first touch starts a dependent chain: DAG structure, per-op
@@ -187,10 +190,8 @@ DevProblem make_problem(const llama_ctx *c) {
         };
         add(c->dag_op_off); add(c->slo); add(c->row_ptr); add(c->col); add(c->topo);
         add(c->lvl_off); add(c->dag_lvl); add(c->ref_gidx); add(c->op_order); add(c->pad_off);
-        add(c->seg_pad); add(c->dlat_n); add(c->fast); add(c->hw_off); add(c->dpiv);
-        if (c->lat.bytes + c->cost.bytes + c->inv.bytes <= (size_t)c->l2_bytes / 4) {
-            add(c->lat); add(c->cost);
-        }
+        add(c->seg_pad); add(c->dlat_n); add(c->dfast); add(c->dpiv); add(c->ord_cbase);
+        if (c->dec.bytes <= (size_t)c->l2_bytes / 4) add(c->dec);
         for (; a < kPfArrays; ++a) {
             P.pf_ptr[a] = nullptr;
             P.pf_lines[a] = 0;
@@ -723,6 +724,9 @@ extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cf
         (e = up(c->op_order, op_order.data(), 4 * (size_t)n_ops)) != cudaSuccess ||
         (e = up(c->ref_gidx, ref_gidx.data(), 8 * (size_t)n_ops)) != cudaSuccess ||
         (e = c->ord_info.alloc(16 * (size_t)n_ops)) != cudaSuccess ||
+        (e = c->ord_cbase.alloc(4 * (size_t)n_ops)) != cudaSuccess ||
+        (e = c->dec.alloc(16 * (alpha ? 2 : 1) * (size_t)n_cfg)) != cudaSuccess ||
+        (e = c->dfast.alloc(16 * (size_t)n_ops)) != cudaSuccess ||
         (e = c->lrb.alloc(2 * (size_t)n_pad)) != cudaSuccess ||
         (e = c->dlat.alloc(4 * (size_t)n_pad)) != cudaSuccess ||
         (e = c->dlat_n.alloc(4 * (size_t)n_ops)) != cudaSuccess ||
@@ -773,6 +777,7 @@ extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cf
     k_encode_rank<<<n_ops, 1024, sort_smem, c->stream>>>(P, sort_cap, c->rf.as<uint16_t>(),
                                                         alpha ? c->df.as<uint16_t>() : nullptr,
                                                         c->inv.as<uint16_t>());
+    k_encode_dec<<<n_ops, 256, 0, c->stream>>>(P, c->dec.as<int4>(), c->dfast.as<int4>());
     LL_CUDA(c, cudaGetLastError());
     LL_CUDA(c, cudaStreamSynchronize(c->stream));
     {
@@ -788,6 +793,9 @@ extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cf
             oi[4 * k2 + 3] = dn[v];
         }
         LL_CUDA(c, cudaMemcpy(c->ord_info.p, oi.data(), 16 * (size_t)n_ops, cudaMemcpyHostToDevice));
+        std::vector<int32_t> cb(n_ops);
+        for (int32_t k2 = 0; k2 < n_ops; ++k2) cb[k2] = (int32_t)cfg_off[op_order[k2]];
+        LL_CUDA(c, cudaMemcpy(c->ord_cbase.p, cb.data(), 4 * (size_t)n_ops, cudaMemcpyHostToDevice));
         // shared-memory room for the distinct latencies of the largest op whose
         // list fits kMaxDlatSmem entries (none: every op searches global memory)
         int32_t cap = 0;

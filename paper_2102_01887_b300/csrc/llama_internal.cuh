@@ -93,6 +93,12 @@ struct DevProblem {
     // [n_ops] per bucket-order position k: {op = op_order[k], vectors of its padded
     // table, its padded offset, its number of distinct latencies}
     const int4 *ord_info;
+    const int32_t *ord_cbase;  // [n_ops] cfg_off[op_order[k]] per bucket-order position k
+    // Decode tables: for rank r of op v (cost-first: the feasible-branch ranks,
+    // dec[cfg_off[v] + r]; alpha: the joint ranks, dec[2*cfg_off[v] + r]), the
+    // configuration it stands for: {index | backend << 16, latency, cost low,
+    // cost high}; dfast[v]: the same for the op's fastest configuration
+    const int4 *dec, *dfast;
     // per DAG, its structure packed contiguously (local op ids): {first op, ops,
     // edges, levels}, reference-configuration indices, successor CSR offsets,
     // successors, ops by height above the sinks, level offsets; empty for a DAG
@@ -199,6 +205,7 @@ __global__ void k_slack(DevProblem P, int64_t n_inv, const int32_t *dag, const i
 __global__ void k_encode_pad(DevProblem P, uint16_t *lrb, uint16_t *rf, uint16_t *df, int32_t *fast);
 __global__ void k_encode_lat(DevProblem P, uint16_t *lrb, int32_t *dlat, int32_t *dlat_n);
 __global__ void k_encode_piv(DevProblem P, int32_t *dpiv);
+__global__ void k_encode_dec(DevProblem P, int4 *dec, int4 *dfast);
 __global__ void k_encode_rank(DevProblem P, int32_t sort_n, uint16_t *rf, uint16_t *df,
                               uint16_t *inv);
 
