@@ -134,8 +134,11 @@ int llama_schedule(llama_ctx *ctx, int64_t n_inv, const int32_t *dag, const int3
  * Invalid invocations are flagged in `out` but the return value does not
  * report them.  Scratch space is library-owned and grows on demand; call
  * llama_reserve first to keep allocations out of the call (for instance
- * before a stream capture).  Errors: EINVAL (bad arguments), ENOTREADY,
- * ENOMEM, ECUDA. */
+ * before a stream capture).  The calls of one context share that scratch:
+ * enqueue them on one stream, or order them, so that no two run at once.
+ * Each call leaves the scratch's counters cleared for the next one, so a
+ * call enqueues kernels only (no memset).  Errors: EINVAL (bad arguments),
+ * ENOTREADY, ENOMEM, ECUDA. */
 int llama_schedule_async(llama_ctx *ctx, int64_t n_inv, const int32_t *dag,
                          const int32_t *op_local, const int64_t *start_us, int64_t now_us,
                          llama_decision *out, void *stream);

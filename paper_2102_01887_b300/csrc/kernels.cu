@@ -611,6 +611,29 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 // shared memory when a group spans several warps); lane u mod 2^lg of a group
 // decodes the group's invocation u.
 
+// Start of a scoring kernel, once the bucketing kernel's results are visible:
+// its per-op counters are no longer read, so they are cleared for the next call.
+__device__ __forceinline__ void clear_counters(const DevProblem &P, const BucketScratch &S) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P.n_ops;
+         k += (int64_t)gridDim.x * blockDim.x)
+        S.cnt[k * kCntStride] = 0;
+}
+
+// End of a scoring kernel: the last CTA to finish publishes the call's status
+// and clears the control words, so the next call needs no memset.
+__device__ __forceinline__ void finish_call(const BucketScratch &S) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&S.ctrl[kCtrlDone], 1ull) == (unsigned long long)gridDim.x - 1) {
+            __threadfence();
+            S.status[0] = atomicAdd(&S.ctrl[kCtrlInvalid], 0ull);
+            S.status[1] = atomicAdd(&S.ctrl[kCtrlTimeout], 0ull);
+            for (int k = 0; k < kCtrlWords; ++k) atomicExch(&S.ctrl[k], 0ull);
+        }
+    }
+}
+
 // Per-thread view of the current tile.
 template <int IPT>
 struct TileState {
@@ -849,6 +872,7 @@ __device__ __forceinline__ void score_body(const DevProblem &P, const BucketScra
     // everything k_bucket wrote (tile list, buckets, slack) is visible only after
     // griddepcontrol.wait; the mbarrier set-up above overlaps its tail
     asm volatile("griddepcontrol.wait;" ::: "memory");
+    clear_counters(P, S);
     const long long n_tiles = (long long)S.ctrl[kCtrlTiles];
     long long ti = blockIdx.x;
     TileState<IPT> T;
@@ -888,6 +912,7 @@ __device__ __forceinline__ void score_body(const DevProblem &P, const BucketScra
         if (tid == 0) atomicOr(&S.ctrl[kCtrlTimeout], 1ull);
         mbar_wait(bar, phase);
     }
+    finish_call(S);
 }
 
 // Two staging buffers: while a chunk is scored, the next one (of the same tile,
@@ -926,6 +951,7 @@ __device__ __forceinline__ void score_body_pipe(const DevProblem &P, const Bucke
     uint32_t pending = 0;  // bit st: a copy into stage st is in flight
     bool ok = true;
     asm volatile("griddepcontrol.wait;" ::: "memory");
+    clear_counters(P, S);
     const long long n_tiles = (long long)S.ctrl[kCtrlTiles];
     long long ti = blockIdx.x, tn;
     if (tid == 0) next_tile = (long long)atomicAdd(&S.ctrl[kCtrlNextTile], 1ull) + gridDim.x;
@@ -983,6 +1009,7 @@ __device__ __forceinline__ void score_body_pipe(const DevProblem &P, const Bucke
         for (int k = 0; k < 2; ++k)
             if (pending & (1u << k)) mbar_wait(bar0 + 8 * k, (phases >> k) & 1u);
     }
+    finish_call(S);
 }
 
 #define LLAMA_SCORE_KERNEL(name, MODE, IPT, BODY)                                                \
@@ -1026,9 +1053,7 @@ cudaError_t enqueue_schedule(const ContextView &v, const BucketScratch &S, int64
                              const cudaEvent_t *trace) {
     auto mark = [&](int k) { if (trace) cudaEventRecord(trace[k], s); };
     mark(0);
-    cudaError_t e = cudaMemsetAsync(S.cnt, 0, sizeof(int32_t) * kCntStride * (size_t)v.n_ops, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(S.ctrl, 0, sizeof(unsigned long long) * kCtrlWords, s);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
     // bucketing: one cooperative launch (its blocks meet at a grid barrier)
     const int n_cp = std::max(1, std::min((v.n_dags + 7) / 8, std::max(1, v.bucket_max_blocks / 4)));
     const int count_blocks = (int)std::max<int64_t>(

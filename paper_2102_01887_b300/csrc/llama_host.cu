@@ -210,7 +210,8 @@ BucketScratch make_scratch(const llama_ctx *c) {
     BucketScratch S{};
     S.cnt = c->cnt.as<int32_t>();
     S.ctrl = c->ctrl.as<unsigned long long>();
-    S.blk = reinterpret_cast<int4 *>(S.ctrl + kCtrlWords);
+    S.status = S.ctrl + kCtrlWords;
+    S.blk = reinterpret_cast<int4 *>(S.ctrl + kCtrlWords + kStatusWords);
     S.op_start = c->op_start.as<int32_t>();
     S.gop = c->gop.as<int32_t>();
     S.slot = c->slot.as<int32_t>();
@@ -293,7 +294,12 @@ int ensure_scratch(llama_ctx *c, int64_t n_inv) {
     if (c->cap_ops < c->n_ops + 1) {
         const int32_t n = c->n_ops + 1;
         LL_CUDA(c, c->cnt.alloc(sizeof(int32_t) * kCntStride * n));
-        LL_CUDA(c, c->ctrl.alloc(sizeof(unsigned long long) * kCtrlWords + sizeof(int4) * kMaxBucketBlocks));
+        LL_CUDA(c, c->ctrl.alloc(sizeof(unsigned long long) * (kCtrlWords + kStatusWords) +
+                                 sizeof(int4) * kMaxBucketBlocks));
+        // counters and control words start at zero; every call leaves them so
+        LL_CUDA(c, cudaMemset(c->cnt.p, 0, c->cnt.bytes));
+        LL_CUDA(c, cudaMemset(c->ctrl.p, 0, c->ctrl.bytes));
+        LL_CUDA(c, cudaDeviceSynchronize());  // before any stream of the caller uses them
         LL_CUDA(c, c->op_start.alloc(sizeof(int32_t) * n));
         c->cap_ops = n;
         c->cap_tiles = 0;
@@ -890,12 +896,12 @@ extern "C" int llama_schedule(llama_ctx *c, int64_t n_inv, const int32_t *dag, c
     if (!sd) LL_CUDA(c, cudaMemcpyAsync((void *)d_start, start_us, 8 * n_inv, cudaMemcpyHostToDevice, s));
     if ((rc = launch_schedule(c, n_inv, d_dag, d_opl, d_start, now_us, d_out, s))) return rc;
     if (!outd) LL_CUDA(c, cudaMemcpyAsync(out, d_out, sizeof(llama_decision) * n_inv, cudaMemcpyDeviceToHost, s));
-    LL_CUDA(c, cudaMemcpyAsync(c->h_ctrl, c->ctrl.p, sizeof(unsigned long long) * kCtrlWords,
-                               cudaMemcpyDeviceToHost, s));
+    LL_CUDA(c, cudaMemcpyAsync(c->h_ctrl, c->ctrl.as<unsigned long long>() + kCtrlWords,
+                               sizeof(unsigned long long) * kStatusWords, cudaMemcpyDeviceToHost, s));
     LL_CUDA(c, cudaStreamSynchronize(s));
-    if (c->h_ctrl[kCtrlTimeout])
+    if (c->h_ctrl[1])
         return c->fail(LLAMA_ETIMEOUT, "schedule: a bounded device wait gave up (table staging)");
-    if (c->h_ctrl[kCtrlInvalid])
+    if (c->h_ctrl[0])
         return c->fail(LLAMA_EINVAL, "schedule: some invocations are invalid (flagged in out)");
     return LLAMA_OK;
 }

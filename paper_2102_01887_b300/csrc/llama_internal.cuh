@@ -51,7 +51,11 @@ constexpr int kCtrlTiles = 3;      // scoring tiles laid out
 constexpr int kCtrlTimeout = 4;    // nonzero: a bounded device wait gave up
 constexpr int kCtrlNextTile = 5;   // dynamic tile counter of the scoring kernel
 constexpr int kCtrlBarrier = 6;    // grid barrier of k_bucket
+constexpr int kCtrlDone = 7;       // CTAs of the scoring kernel that have finished
 constexpr int kCtrlWords = 8;
+// Status of the last completed call, after the control words: {invalid
+// invocations, nonzero if a bounded device wait gave up}
+constexpr int kStatusWords = 2;
 // k_bucket's grid never exceeds this many blocks (per-block layout sums)
 constexpr int kMaxBucketBlocks = 4096;
 // DAGs up to this size are staged in shared memory for the critical path
@@ -113,8 +117,11 @@ struct DevProblem {
 };
 
 struct BucketScratch {
-    int32_t *cnt;             // [n_ops*kCntStride] invocations per op (zeroed before each call)
-    unsigned long long *ctrl; // [kCtrlWords] control words (zeroed before each call)
+    int32_t *cnt;             // [n_ops*kCntStride] invocations per op: zero when a call starts
+                              // (the scoring kernel clears them once bucketing is done)
+    unsigned long long *ctrl; // [kCtrlWords] control words: zero when a call starts; the
+                              // scoring kernel's last CTA clears them for the next call
+    unsigned long long *status;  // [kStatusWords] written by that CTA: {invalid, timeout}
     int4 *blk;                // [kMaxBucketBlocks] per counting block: bucket positions,
                               // full tiles and tail tiles of its ops (written each call)
     int32_t *op_start;        // [n_ops]     first bucket position of each op

@@ -37,7 +37,7 @@ constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t kMaxTiles = (size_t)LLAMA_STATIC_MAX_INV + (size_t)LLAMA_STATIC_MAX_OPS;
 constexpr size_t kCntOff = 0;
 constexpr size_t kCtrlOff = align256(kCntOff + 4 * (size_t)kCntStride * LLAMA_STATIC_MAX_OPS);
-constexpr size_t kOpStartOff = align256(kCtrlOff + 8 * (size_t)kCtrlWords + 16 * (size_t)kMaxBucketBlocks);
+constexpr size_t kOpStartOff = align256(kCtrlOff + 8 * (size_t)(kCtrlWords + kStatusWords) + 16 * (size_t)kMaxBucketBlocks);
 constexpr size_t kGopOff = align256(kOpStartOff + 4 * (size_t)(LLAMA_STATIC_MAX_OPS + 1));
 constexpr size_t kSlotOff = align256(kGopOff + 4 * (size_t)LLAMA_STATIC_MAX_INV);
 constexpr size_t kBInvOff = align256(kSlotOff + 4 * (size_t)LLAMA_STATIC_MAX_INV);
@@ -118,7 +118,8 @@ extern "C" int llama_schedule_static(llama_ctx *c, int64_t n_inv, const int32_t 
     BucketScratch S{};
     S.cnt = reinterpret_cast<int32_t *>(base + kCntOff);
     S.ctrl = reinterpret_cast<unsigned long long *>(base + kCtrlOff);
-    S.blk = reinterpret_cast<int4 *>(base + kCtrlOff + 8 * (size_t)kCtrlWords);
+    S.status = S.ctrl + kCtrlWords;
+    S.blk = reinterpret_cast<int4 *>(base + kCtrlOff + 8 * (size_t)(kCtrlWords + kStatusWords));
     S.op_start = reinterpret_cast<int32_t *>(base + kOpStartOff);
     S.gop = reinterpret_cast<int32_t *>(base + kGopOff);
     S.slot = reinterpret_cast<int32_t *>(base + kSlotOff);
@@ -127,8 +128,8 @@ extern "C" int llama_schedule_static(llama_ctx *c, int64_t n_inv, const int32_t 
     S.rbase = reinterpret_cast<int64_t *>(base + kRbaseOff);
     S.tiles = reinterpret_cast<int4 *>(base + kTilesOff);
 
-    // the previous call's counters are still in the array: enqueue_schedule
-    // clears them on this call's stream before anything reads them
+    // the counters and control words are zero: the array starts zeroed and
+    // every completed call leaves them cleared
     e = enqueue_schedule(v, S, n_inv, dag, op_local, start_us, now_us, out,
                          static_cast<cudaStream_t>(stream), nullptr);
     if (e != cudaSuccess) return cuda_error(c, e, "enqueue");
