@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="medium", choices=["tiny", "medium", "batched", "batched_large"])
     ap.add_argument("--mode", default="cost_first", choices=["cost_first", "alpha"])
+    ap.add_argument("--method", default="scan", choices=["scan", "staircase"],
+                    help="selection method: score every configuration, or the staircase tables")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -254,7 +256,8 @@ def main():
     B.build()
     p, inv = make_workload(args.workload, rank, args.n_dags, args.n_inv)
     mode = L.MODE_ALPHA if args.mode == "alpha" else L.MODE_COST_FIRST
-    sched = L.Scheduler(p, mode=mode, alpha=(3, 2), device=local, use_graph=not args.no_graph)
+    method = L.METHOD_STAIRCASE if args.method == "staircase" else L.METHOD_SCAN
+    sched = L.Scheduler(p, mode=mode, alpha=(3, 2), device=local, use_graph=not args.no_graph, method=method)
     ctx = sched.ctx
     scores = scores_of(p, inv)
 
@@ -275,7 +278,7 @@ def main():
         L.llama_set_tuning(ctx, lmv, ipt, chunk, stages)
         tuning = {"best": {"lanes_min_vectors": lmv, "inv_per_thread": ipt, "chunk": chunk, "stages": stages},
                   "trials": []}
-    elif not args.no_autotune:
+    elif not args.no_autotune and args.method == "scan":
         # choose the scoring schedule on this batch before anything is timed;
         # ops with more than 4,096 configurations may also be staged whole
         from paper_2102_01887_b300.autotune import autotune
@@ -375,7 +378,25 @@ def main():
     tbl_per_entry = 6 if args.mode == "alpha" else 4
     kms = {n: float(phase_ms[:, j].mean()) for j, n in enumerate(L.TRACE_PHASES)}
     rooflines = {}
-    if tbl_per_entry * int(npad.sum()) + 4 * int(npad.sum()) > l2_bytes // 2:
+    if args.method == "staircase":
+        # one thread per invocation: 16 B in, 24 B out; the searches and lookups
+        # are dependent loads into per-op arrays (latency, not bandwidth)
+        s_bytes = inv.n * 40
+        s_ach = s_bytes / (kms["score"] / 1e3) / 1e9
+        rooflines["k_stair"] = {
+            "bound": "hbm", "kernel": "k_stair", "achieved": s_ach, "peak": hbm, "unit": "GB/s",
+            "frac": s_ach / hbm, "traffic": measured_traffic("k_stair", args.workload, args.mode),
+            "peak_source": f"{peak_src} HBM copy bandwidth", "algorithmic_bytes": s_bytes,
+            "bytes_note": "16 B in and 24 B out per invocation"}
+        c_bytes = 16 * p.n_ops
+        c_ach = c_bytes / (kms["bucket"] / 1e3) / 1e9
+        rooflines["k_critical_paths"] = {
+            "bound": "hbm", "kernel": "k_critical_paths", "achieved": c_ach, "peak": hbm, "unit": "GB/s",
+            "frac": c_ach / hbm, "traffic": None, "peak_source": f"{peak_src} HBM copy bandwidth",
+            "algorithmic_bytes": c_bytes, "bytes_note": "critical path and its reciprocal (16 B) per op"}
+        dominant = "k_stair" if kms["score"] >= kms["bucket"] else "k_critical_paths"
+        roofline = rooflines[dominant]
+    elif tbl_per_entry * int(npad.sum()) + 4 * int(npad.sum()) > l2_bytes // 2:
         algo_bytes = tbl_per_entry * int(npad[touched].sum()) + inv.n * (4 + 12 + 24)
         achieved = algo_bytes / (kms["score"] / 1e3) / 1e9
         rooflines["k_score"] = {
@@ -395,16 +416,17 @@ def main():
             "peak_source": f"{sm_count} SMs x {ALU_LANES_PER_SM} integer ALU lanes x "
                            f"{sm_mhz:.0f} MHz ({peak_src} max SM clock)",
             "alu_ops_per_score": ops_per_score, "scores_per_s_ceiling": peak_tops * 1e12 / ops_per_score}
-    b_bytes = inv.n * (16 + 4 + 4 * p.n_hw)
-    b_ach = b_bytes / (kms["bucket"] / 1e3) / 1e9
-    rooflines["k_bucket"] = {
-        "bound": "hbm", "kernel": "k_bucket", "achieved": b_ach, "peak": hbm, "unit": "GB/s",
-        "frac": b_ach / hbm, "traffic": measured_traffic("k_bucket", args.workload, args.mode),
-        "peak_source": f"{peak_src} HBM copy bandwidth", "algorithmic_bytes": b_bytes,
-        "bytes_note": f"16 B in and {4 + 4 * p.n_hw} B of bucket entry out per invocation; "
-                      "time includes its launch (trace events around it)"}
-    dominant = max(rooflines, key=lambda k: kms["score" if k == "k_score" else "bucket"])
-    roofline = rooflines[dominant]
+    if args.method == "scan":
+        b_bytes = inv.n * (16 + 4 + 4 * p.n_hw)
+        b_ach = b_bytes / (kms["bucket"] / 1e3) / 1e9
+        rooflines["k_bucket"] = {
+            "bound": "hbm", "kernel": "k_bucket", "achieved": b_ach, "peak": hbm, "unit": "GB/s",
+            "frac": b_ach / hbm, "traffic": measured_traffic("k_bucket", args.workload, args.mode),
+            "peak_source": f"{peak_src} HBM copy bandwidth", "algorithmic_bytes": b_bytes,
+            "bytes_note": f"16 B in and {4 + 4 * p.n_hw} B of bucket entry out per invocation; "
+                          "time includes its launch (trace events around it)"}
+        dominant = max(rooflines, key=lambda k: kms["score" if k == "k_score" else "bucket"])
+        roofline = rooflines[dominant]
     value = job_throughput(world, inv.n, args.steps, total_s)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -423,16 +445,18 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": float(step_ms.mean()), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32/int64", "data": "synthetic",
-        "config": {**workload_config(args.workload, p, inv, args.mode, scores),
+        "config": {**workload_config(args.workload, p, inv, args.mode, scores), "method": args.method,
                    "schedule": tuning["best"] if tuning else "default"},
         "configs_scored_per_s": world * scores * args.steps / total_s,
         "decision_latency_us": {"p50": 1e3 * float(np.median(step_ms)),
                                 "p99": 1e3 * float(np.percentile(step_ms, 99))},
-        "scan_effective": {"gbs": SCAN_BYTES_PER_SCORE * scores / (score_ms / 1e3) / 1e9,
+        "scan_effective": None if args.method == "staircase" else {
+                           "gbs": SCAN_BYTES_PER_SCORE * scores / (score_ms / 1e3) / 1e9,
                            "hbm_frac": SCAN_BYTES_PER_SCORE * scores / (score_ms / 1e3) / 1e9 / peaks["hbm_gbs"],
                            "note": "12 B per scored configuration / scoring-kernel time; where tables are "
                                    "reused across invocations from shared memory this exceeds HBM"},
-        "kernel_ms": {n: float(phase_ms[:, j].mean()) for j, n in enumerate(L.TRACE_PHASES)},
+        "kernel_ms": {n: float(phase_ms[:, j].mean()) for j, n in
+                      enumerate(("critical_path", "stair") if args.method == "staircase" else L.TRACE_PHASES)},
         "kernel_ms_note": "per-kernel event times from a second pass of the same steps with trace "
                           "events (direct launches, no overlap between the two kernels)",
         "roofline": roofline,

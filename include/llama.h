@@ -185,6 +185,22 @@ int llama_schedule_static(llama_ctx *ctx, int64_t n_inv, const int32_t *dag,
 int llama_set_tuning(llama_ctx *ctx, int32_t lanes_min_vectors, int32_t inv_per_thread,
                      int32_t chunk_entries, int32_t stages);
 
+/* Method of the selection step (a4).  SCAN (default): every configuration of
+ * the invocation's operation is scored (Eq. 1, Section 4.2), tables staged
+ * through shared memory and shared by the op's invocations.  STAIRCASE: an
+ * exact rearrangement of the same argmin that the paper does not describe:
+ * per operation and backend, the configurations sorted by latency, and at
+ * every latency rank k the best key among those below k (the feasible branch)
+ * and, in ALPHA mode, among those at or above k (the infeasible branch), built
+ * once from the profiles (16-bit keys, n_hw * (distinct latencies + 1) per
+ * operation).  A decision is then one search per backend and n_hw lookups
+ * instead of a scan.  Decisions are identical under both methods.  Setting
+ * STAIRCASE builds its tables (again after every llama_set_profiles).
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+#define LLAMA_METHOD_SCAN 0
+#define LLAMA_METHOD_STAIRCASE 1
+int llama_set_method(llama_ctx *ctx, int32_t method);
+
 /* Pre-allocate scratch for calls of up to max_inv invocations. */
 int llama_reserve(llama_ctx *ctx, int64_t max_inv);
 

@@ -1042,6 +1042,195 @@ const void *score_kernel(int mode, int ipt, int stages) {
 }
 
 // ---------------------------------------------------------------------------
+// Staircase method (an exact rearrangement of the argmin of Eq. 1)
+// ---------------------------------------------------------------------------
+
+// Critical paths of every DAG (a1) for the staircase method: small DAGs one per
+// warp, larger ones one per block.
+__global__ void __launch_bounds__(256) k_critical_paths(DevProblem P, const int32_t *topo,
+                                                        const int32_t *lvl_off, const int32_t *dag_lvl) {
+    __shared__ CpSmem sm;
+    critical_paths_of_block(P, blockIdx.x, gridDim.x, topo, lvl_off, dag_lvl, sm);
+    asm volatile("griddepcontrol.launch_dependents;");
+}
+
+// One decision per thread.  For backend h the configurations of segment h that
+// meet the slack are exactly those whose latency rank is below c_h, the number
+// of the op's distinct latencies below slack(op, h); so the best key of the
+// segment is stair[.. h ..][c_h], and the decision is the least of the H keys.
+// c_h comes from the op's 32 first-round probe values (one line), then a
+// bisection of the window they leave, all H searches in lockstep.
+__global__ void __launch_bounds__(256) k_stair(DevProblem P, int64_t n_inv, const int32_t *dag,
+                                               const int32_t *op_local, const int64_t *start,
+                                               int64_t now, BucketScratch S, llama_decision *out) {
+    // the critical paths (previous kernel) are visible after this
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int H = P.n_hw;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n_inv) {
+        const int32_t d = dag[i], o = op_local[i];
+        const int64_t st = start[i];
+        if (!invocation_valid(P, d, o, st, now)) {
+            llama_decision bad;
+            bad.cfg = -1;
+            bad.lat = 0;
+            bad.cost = 0;
+            bad.slack = 0;
+            bad.flags = LLAMA_FLAG_INVALID;
+            out[i] = bad;
+            atomicAdd(&S.ctrl[kCtrlInvalid], 1ull);
+        } else {
+            const int32_t g = P.dag_op_off[d] + o;
+            const int64_t rbase = P.slo[d] - (now - st);
+            const int64_t ref = P.ref[g], cp = P.cp[g];
+            const uint64_t mg = P.cp_magic[g];
+            const int32_t dn = P.dlat_n[g];
+            const int32_t *dl = P.dlat + P.pad_off[g];
+            int32_t sl[LLAMA_MAX_HW], lo[LLAMA_MAX_HW], hi[LLAMA_MAX_HW];
+#pragma unroll
+            for (int h = 0; h < LLAMA_MAX_HW; ++h) {
+                sl[h] = h < H ? slack_of(ref, cp, mg, rbase - P.q[h]) : 0;
+                lo[h] = 0;
+                hi[h] = h < H ? dn : 0;
+            }
+            if (dn > 32) {
+                // probe l sits at ((l+1)*dn >> 5) - 1; c probes below the slack
+                // leave the window [(c*dn >> 5), ((c+1)*dn >> 5) - 1]
+                const int4 *pv = reinterpret_cast<const int4 *>(P.dpiv + 32 * (int64_t)g);
+                int32_t cnt[LLAMA_MAX_HW];
+#pragma unroll
+                for (int h = 0; h < LLAMA_MAX_HW; ++h) cnt[h] = 0;
+#pragma unroll
+                for (int w = 0; w < 8; ++w) {
+                    const int4 q4 = __ldg(pv + w);
+#pragma unroll
+                    for (int h = 0; h < LLAMA_MAX_HW; ++h)
+                        cnt[h] += (q4.x < sl[h]) + (q4.y < sl[h]) + (q4.z < sl[h]) + (q4.w < sl[h]);
+                }
+#pragma unroll
+                for (int h = 0; h < LLAMA_MAX_HW; ++h) {
+                    if (h >= H) continue;
+                    const int32_t c = cnt[h];
+                    lo[h] = (c * dn) >> 5;
+                    hi[h] = c < 32 ? (((c + 1) * dn) >> 5) - 1 : dn;
+                }
+            }
+            for (;;) {
+                int32_t val[LLAMA_MAX_HW];
+                bool more = false;
+#pragma unroll
+                for (int h = 0; h < LLAMA_MAX_HW; ++h) {  // all loads first
+                    const bool a = lo[h] < hi[h];
+                    more |= a;
+                    val[h] = a ? __ldg(dl + ((lo[h] + hi[h]) >> 1)) : 0;
+                }
+                if (!more) break;
+#pragma unroll
+                for (int h = 0; h < LLAMA_MAX_HW; ++h) {
+                    if (lo[h] >= hi[h]) continue;
+                    const int32_t mid = (lo[h] + hi[h]) >> 1;
+                    if (val[h] < sl[h]) lo[h] = mid + 1; else hi[h] = mid;
+                }
+            }
+            const uint16_t *sg = P.stair + P.stair_off[g];
+            uint32_t key = 0xFFFFu;
+#pragma unroll
+            for (int h = 0; h < LLAMA_MAX_HW; ++h)
+                if (h < H) key = min(key, (uint32_t)__ldg(sg + (int64_t)h * (dn + 1) + lo[h]));
+            const int64_t cb = P.cfg_off[g];
+            int4 dd;
+            if (P.mode == LLAMA_MODE_ALPHA) dd = P.dec[2 * cb + key];
+            else dd = key != 0xFFFFu ? P.dec[cb + key] : P.dfast[g];
+            const int lam = dd.x >> 16;
+            const int32_t slam = slack_of(ref, cp, mg, rbase - P.q[lam]);
+            llama_decision dsn;
+            dsn.cfg = dd.x & 0xFFFF;
+            dsn.lat = dd.y;
+            dsn.cost = (int64_t)(((uint64_t)(uint32_t)dd.w << 32) | (uint32_t)dd.z);
+            dsn.slack = slam;
+            dsn.flags = dd.y < slam ? LLAMA_FLAG_FEASIBLE : 0;
+            out[i] = dsn;
+        }
+    }
+    finish_call(S);
+}
+
+// Inclusive minimum scan of a[0..n) in shared memory by the whole block, from
+// the front (reverse = false) or from the back; part[] holds 32 words.
+__device__ void block_min_scan(int32_t *a, int n, bool reverse, int32_t *part) {
+    const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int per = (n + T - 1) / T;
+    const int b = min(n, tid * per), e = min(n, b + per);
+    auto at = [&](int k) -> int32_t & { return a[reverse ? n - 1 - k : k]; };
+    int32_t run = INT32_MAX;
+    for (int k = b; k < e; ++k) run = min(run, at(k));
+    int32_t inc = run;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc = min(inc, u);
+    }
+    if (lane == 31) part[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        int32_t w = lane < (T >> 5) ? part[lane] : INT32_MAX;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t u = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w = min(w, u);
+        }
+        if (lane < (T >> 5)) part[lane] = w;
+    }
+    __syncthreads();
+    // minimum of everything before this thread's run
+    int32_t before = __shfl_up_sync(0xffffffffu, inc, 1);
+    if (lane == 0) before = INT32_MAX;
+    if (wid > 0) before = min(before, part[wid - 1]);
+    for (int k = b; k < e; ++k) {
+        before = min(before, at(k));
+        at(k) = before;
+    }
+    __syncthreads();
+}
+
+// Staircase tables, one CTA per op: for each backend segment, the keys of its
+// configurations at their latency ranks, then a prefix minimum (feasible
+// branch: configurations below rank k) and, in alpha mode, a suffix minimum
+// (infeasible branch: configurations at or above rank k).
+__global__ void k_encode_stair(DevProblem P, uint16_t *stair) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int32_t part[32];
+    const int v = blockIdx.x, H = P.n_hw, T = blockDim.x, tid = threadIdx.x;
+    const bool alpha = P.mode == LLAMA_MODE_ALPHA;
+    const int32_t dn = P.dlat_n[v], m = dn + 1;
+    int32_t *pre = reinterpret_cast<int32_t *>(smem_raw);
+    int32_t *suf = pre + m;
+    const int64_t p0 = P.pad_off[v];
+    const int32_t *hw = P.hw_off + (int64_t)v * (H + 1);
+    const int32_t *sp = P.seg_pad + (int64_t)v * (H + 1);
+    uint16_t *out = stair + P.stair_off[v];
+    for (int h = 0; h < H; ++h) {
+        for (int k = tid; k < m; k += T) {
+            pre[k] = 0xFFFF;
+            suf[k] = 0xFFFF;
+        }
+        __syncthreads();
+        const int n_h = hw[h + 1] - hw[h];
+        for (int j = tid; j < n_h; j += T) {
+            const int64_t pp = p0 + sp[h] + j;
+            const int32_t r = (int32_t)P.lrb[pp] - kLatRankBias;
+            const int32_t f = P.rf[pp];
+            atomicMin(&pre[r + 1], f);
+            if (alpha) atomicMin(&suf[r], f ^ (int32_t)P.df[pp]);
+        }
+        __syncthreads();
+        block_min_scan(pre, m, false, part);
+        if (alpha) block_min_scan(suf, m, true, part);
+        for (int k = tid; k < m; k += T)
+            out[(int64_t)h * m + k] = (uint16_t)(alpha ? min(pre[k], suf[k]) : pre[k]);
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // The launch sequence of one scheduling call
 // ---------------------------------------------------------------------------
 
@@ -1054,6 +1243,27 @@ cudaError_t enqueue_schedule(const ContextView &v, const BucketScratch &S, int64
     auto mark = [&](int k) { if (trace) cudaEventRecord(trace[k], s); };
     mark(0);
     cudaError_t e = cudaSuccess;
+    if (v.method == LLAMA_METHOD_STAIRCASE) {
+        k_critical_paths<<<std::max(1, (v.n_dags + 7) / 8), 256, 0, s>>>(v.P, v.topo, v.lvl_off, v.dag_lvl);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        mark(1);
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3((unsigned)((n_inv + 255) / 256));
+        cfg.blockDim = dim3(256);
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = trace ? 0 : 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        DevProblem P = v.P;
+        BucketScratch Sc = S;
+        void *args[] = {&P, &n_inv, &dag, &op_local, &start, &now, &Sc, &out};
+        e = cudaLaunchKernelExC(&cfg, (const void *)k_stair, args);
+        if (e != cudaSuccess) return e;
+        mark(2);
+        return cudaGetLastError();
+    }
     // bucketing: one cooperative launch (its blocks meet at a grid barrier)
     const int n_cp = std::max(1, std::min((v.n_dags + 7) / 8, std::max(1, v.bucket_max_blocks / 4)));
     const int count_blocks = (int)std::max<int64_t>(

@@ -70,6 +70,11 @@ struct llama_ctx {
     std::vector<int32_t> h_dag_op_off, h_row_ptr, h_col, h_topo, h_lvl_off, h_dag_lvl;
     std::vector<int64_t> h_ref_gidx;
     DevBuf dag_pack, dag_pack_off, ord_info, ord_cbase, dec, dfast;
+    // staircase method (built on demand, see llama_set_method)
+    int32_t method = LLAMA_METHOD_SCAN;
+    bool stair_ready = false;
+    DevBuf stair, stair_off;
+    std::vector<int32_t> h_dn;  // distinct latencies per op
 
     // profiles
     bool prof_set = false;
@@ -104,7 +109,8 @@ struct llama_ctx {
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
-    cudaGraphNode_t g_bucket = nullptr;
+    cudaGraphNode_t g_bucket = nullptr;  // the captured kernel that takes `now`
+    int g_now_nargs = 0;
     int64_t g_n_inv = -1, g_now = 0;
     const void *g_args[4] = {};
 
@@ -175,6 +181,8 @@ DevProblem make_problem(const llama_ctx *c) {
     P.ord_cbase = c->ord_cbase.as<int32_t>();
     P.dec = c->dec.as<int4>();
     P.dfast = c->dfast.as<int4>();
+    P.stair = c->stair.as<uint16_t>();
+    P.stair_off = c->stair_off.as<int64_t>();
     P.dag_pack = c->dag_pack.as<int32_t>();
     P.dag_pack_off = c->dag_pack_off.as<int64_t>();
     // arrays whose first touch starts a dependent chain: DAG structure, per-op
@@ -236,6 +244,7 @@ ContextView view_of(const llama_ctx *c) {
     v.num_sms = c->num_sms;
     v.min_vpl = c->min_vpl;
     v.ipt = c->ipt;
+    v.method = c->method;
     v.stages = c->stages;
     v.score_grid = c->score_grid;
     v.bucket_max_blocks = c->bucket_max_blocks;
@@ -277,6 +286,30 @@ int build_dag_pack(llama_ctx *c) {
         (e = c->dag_pack_off.alloc(8 * off.size())) != cudaSuccess ||
         (e = cudaMemcpy(c->dag_pack_off.p, off.data(), 8 * off.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
         return c->cuda_fail(e, "dag pack upload");
+    return LLAMA_OK;
+}
+
+// Staircase tables of the current profiles: H * (dn + 1) 16-bit keys per op.
+int build_stair(llama_ctx *c) {
+    const int32_t n_ops = c->n_ops, H = c->opts.n_hw;
+    std::vector<int64_t> off(n_ops + 1, 0);
+    int32_t max_dn = 1;
+    for (int32_t v = 0; v < n_ops; ++v) {
+        off[v + 1] = off[v] + (int64_t)H * (c->h_dn[v] + 1);
+        max_dn = std::max(max_dn, c->h_dn[v]);
+    }
+    cudaError_t e;
+    if ((e = c->stair.alloc(2 * (size_t)std::max<int64_t>(off[n_ops], 1))) != cudaSuccess ||
+        (e = c->stair_off.alloc(8 * (size_t)(n_ops + 1))) != cudaSuccess ||
+        (e = cudaMemcpy(c->stair_off.p, off.data(), 8 * (size_t)(n_ops + 1), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return c->cuda_fail(e, "staircase tables");
+    const size_t smem = 2 * 4 * (size_t)(max_dn + 1);
+    LL_CUDA(c, cudaFuncSetAttribute(k_encode_stair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const DevProblem P = make_problem(c);
+    k_encode_stair<<<n_ops, 1024, smem, c->stream>>>(P, c->stair.as<uint16_t>());
+    LL_CUDA(c, cudaGetLastError());
+    LL_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->stair_ready = true;
     return LLAMA_OK;
 }
 
@@ -421,7 +454,9 @@ int capture_graph(llama_ctx *c, int64_t n_inv, const int32_t *dag, const int32_t
         if (t == cudaGraphNodeTypeKernel) {
             cudaKernelNodeParams p{};
             LL_CUDA(c, cudaGraphKernelNodeGetParams(node, &p));
-            if (p.func == (void *)k_bucket) c->g_bucket = node;
+            // `now` is argument 5 of both k_bucket (14 arguments) and k_stair (8)
+            if (p.func == (void *)k_bucket) c->g_bucket = node, c->g_now_nargs = 14;
+            if (p.func == (void *)k_stair) c->g_bucket = node, c->g_now_nargs = 8;
         }
     }
     if (!c->g_bucket) return c->fail(LLAMA_ECUDA, "graph capture: kernel node not found");
@@ -451,8 +486,7 @@ int launch_schedule(llama_ctx *c, int64_t n_inv, const int32_t *dag, const int32
         if (rc) return rc;
     }
     if (now != c->g_now) {
-        // `now` is argument 5 of k_bucket's 14
-        LL_CUDA(c, patch_arg(c->gexec, c->g_bucket, 14, 5, &now));
+        LL_CUDA(c, patch_arg(c->gexec, c->g_bucket, c->g_now_nargs, 5, &now));
         c->g_now = now;
     }
     LL_CUDA(c, cudaGraphLaunch(c->gexec, s));
@@ -808,7 +842,9 @@ extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cf
         for (int32_t v = 0; v < n_ops; ++v)
             if (dn[v] <= kMaxDlatSmem) cap = std::max(cap, dn[v]);
         c->dlat_cap = (cap + 3) / 4 * 4;
+        c->h_dn = std::move(dn);
     }
+    c->stair_ready = false;
 
     // scoring kernel: stage tables in chunks of at most kMaxChunk entries, one
     // persistent CTA per resident slot
@@ -818,7 +854,9 @@ extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cf
     if (rc) return rc;
     c->h_ref_gidx = std::move(ref_gidx);
     c->prof_set = true;
-    return build_dag_pack(c);
+    int rc2 = build_dag_pack(c);
+    if (rc2 == LLAMA_OK && c->method == LLAMA_METHOD_STAIRCASE) rc2 = build_stair(c);
+    return rc2;
 }
 
 extern "C" int llama_set_queue(llama_ctx *c, const int64_t *q_us) {
@@ -850,6 +888,17 @@ extern "C" int llama_set_tuning(llama_ctx *c, int32_t lanes_min_vectors, int32_t
     c->score_chunk = chunk_entries ? std::min<int32_t>(chunk_entries, c->max_npad) : default_chunk(c->max_npad);
     c->score_smem = score_smem_bytes(c);
     return configure_score(c);
+}
+
+extern "C" int llama_set_method(llama_ctx *c, int32_t method) {
+    if (!c) return LLAMA_EINVAL;
+    if (method != LLAMA_METHOD_SCAN && method != LLAMA_METHOD_STAIRCASE)
+        return c->fail(LLAMA_EINVAL, "set_method: method must be LLAMA_METHOD_SCAN or LLAMA_METHOD_STAIRCASE");
+    DeviceGuard g(c->opts.device);
+    c->drop_graph();
+    c->method = method;
+    if (method == LLAMA_METHOD_STAIRCASE && c->prof_set && !c->stair_ready) return build_stair(c);
+    return LLAMA_OK;
 }
 
 extern "C" int llama_reserve(llama_ctx *c, int64_t max_inv) {

@@ -103,6 +103,12 @@ struct DevProblem {
     // configuration it stands for: {index | backend << 16, latency, cost low,
     // cost high}; dfast[v]: the same for the op's fastest configuration
     const int4 *dec, *dfast;
+    // Staircase method: per op v and backend h, at stair[stair_off[v] + h*(dn+1) + k]
+    // for k = 0..dn, the least key among the configurations of segment h whose
+    // latency rank is below k (cost-first: feasible-branch ranks, 0xFFFF if none;
+    // alpha: that, or the least infeasible-branch rank among those at or above k)
+    const uint16_t *stair;
+    const int64_t *stair_off;
     // per DAG, its structure packed contiguously (local op ids): {first op, ops,
     // edges, levels}, reference-configuration indices, successor CSR offsets,
     // successors, ops by height above the sinks, level offsets; empty for a DAG
@@ -159,6 +165,7 @@ struct ContextView {
     DevProblem P;
     const int32_t *topo, *lvl_off, *dag_lvl;
     int32_t n_dags, n_ops, n_hw, mode, device, num_sms;
+    int32_t method;       // LLAMA_METHOD_SCAN or LLAMA_METHOD_STAIRCASE
     int32_t min_vpl;      // vectors a lane should scan at least (sets lanes per invocation)
     int32_t ipt;          // invocations per scoring thread (1, 2 or 4)
     int32_t stages;       // staging buffers of the scoring kernel (1 or 2)
@@ -213,6 +220,12 @@ __global__ void k_encode_pad(DevProblem P, uint16_t *lrb, uint16_t *rf, uint16_t
 __global__ void k_encode_lat(DevProblem P, uint16_t *lrb, int32_t *dlat, int32_t *dlat_n);
 __global__ void k_encode_piv(DevProblem P, int32_t *dpiv);
 __global__ void k_encode_dec(DevProblem P, int4 *dec, int4 *dfast);
+__global__ void k_encode_stair(DevProblem P, uint16_t *stair);
+// Staircase method: critical paths of every DAG, then one thread per invocation.
+__global__ void k_critical_paths(DevProblem P, const int32_t *topo, const int32_t *lvl_off,
+                                 const int32_t *dag_lvl);
+__global__ void k_stair(DevProblem P, int64_t n_inv, const int32_t *dag, const int32_t *op_local,
+                        const int64_t *start, int64_t now, BucketScratch S, llama_decision *out);
 __global__ void k_encode_rank(DevProblem P, int32_t sort_n, uint16_t *rf, uint16_t *df,
                               uint16_t *inv);
 

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libllama.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ENOTREADY, ETIMEOUT = 0, -1, -2, -3, -4, -5
 MODE_COST_FIRST, MODE_ALPHA = 0, 1
+METHOD_SCAN, METHOD_STAIRCASE = 0, 1
 FLAG_FEASIBLE, FLAG_INVALID = 1, 2
 MAX_HW, MAX_CFG = 8, 8192
 
@@ -29,7 +30,7 @@ assert DECISION_DTYPE.itemsize == 24
 
 EXPORTS = ("llama_create", "llama_destroy", "llama_set_dags", "llama_set_profiles",
            "llama_set_queue", "llama_schedule", "llama_schedule_async", "llama_schedule_static",
-           "llama_set_tuning", "llama_reserve",
+           "llama_set_tuning", "llama_set_method", "llama_reserve",
            "llama_critical_path", "llama_slack", "llama_set_trace_events", "llama_last_launch_count",
            "llama_last_error")
 TRACE_EVENTS = 3
@@ -72,6 +73,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "llama_schedule_async": ([vp, i64, vp, vp, vp, i64, vp, vp], ctypes.c_int),
             "llama_schedule_static": ([vp, i64, vp, vp, vp, i64, vp, vp], ctypes.c_int),
             "llama_set_tuning": ([vp, i32, i32, i32, i32], ctypes.c_int),
+            "llama_set_method": ([vp, i32], ctypes.c_int),
             "llama_reserve": ([vp, i64], ctypes.c_int),
             "llama_critical_path": ([vp, vp], ctypes.c_int),
             "llama_slack": ([vp, i64, vp, vp, vp, i64, vp], ctypes.c_int),
@@ -152,6 +154,10 @@ def llama_set_tuning(ctx, lanes_min_vectors: int = 16, inv_per_thread: int = 2,
                                         int(chunk_entries), int(stages)))
 
 
+def llama_set_method(ctx, method: int) -> None:
+    _check(ctx, load().llama_set_method(ctx, int(method)))
+
+
 def llama_reserve(ctx, max_inv: int) -> None:
     _check(ctx, load().llama_reserve(ctx, int(max_inv)))
 
@@ -230,10 +236,12 @@ class Scheduler:
     """A context loaded with one Problem (see ``workloads``)."""
 
     def __init__(self, problem, mode: int = MODE_COST_FIRST, alpha=(1, 1), device: int = 0,
-                 use_graph: bool = False):
+                 use_graph: bool = False, method: int = METHOD_SCAN):
         self.problem = problem
         self.mode = mode
         self.ctx = llama_create(mode, problem.n_hw, alpha, device, use_graph)
+        if method != METHOD_SCAN:
+            llama_set_method(self.ctx, method)
         p = problem
         llama_set_dags(self.ctx, p.dag_op_off, p.row_ptr, p.col, p.slo_us)
         alpha_mode = mode == MODE_ALPHA
