@@ -12,8 +12,8 @@ import sys
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 LIB = os.path.join(PKG, "libllama.so")
-SOURCES = [os.path.join(PKG, "csrc", f) for f in ("kernels.cu", "llama_host.cu", "llama_static.cu")]
-DEPS = SOURCES + glob.glob(os.path.join(PKG, "csrc", "*.cuh")) + [os.path.join(ROOT, "include", "llama.h")]
+SOURCES = [os.path.join(PKG, "csrc", f) for f in ("kernels.cu", "llama_host.cu", "llama_static.cu", "sg_gemm.cu")]
+DEPS = SOURCES + glob.glob(os.path.join(PKG, "csrc", "*.cuh")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2,-Wall", "-shared",

@@ -1,0 +1,299 @@
+// Dense BF16 GEMM on the 5th-generation tensor cores (tcgen05), FP32
+// accumulation in tensor memory: C[M x N] = A[M x K] . B[N x K]^T (+ bias[N],
+// optionally ReLU), both operands K-major.  The building block of the learned
+// latency surrogate (a 4-layer MLP of width 256).
+//
+// One CTA computes a 128 x BN tile.  Warp 0 (one lane) streams 128 x 64 and
+// BN x 64 operand tiles into a ring of shared-memory stages with TMA (128-byte
+// swizzle); warp 1 (one lane) issues tcgen05.mma (M 128, N BN, K 16, four per
+// stage) into a 128 x BN FP32 accumulator in tensor memory and releases each
+// stage with tcgen05.commit; the four warps then read the accumulator back
+// (tcgen05.ld, warp w owns rows 32w..32w+31), add the bias, apply ReLU and store
+// BF16 and/or FP32.  Every wait is bounded: a wait that gives up sets *err and
+// the CTA still waits (bounded) for its copies and MMAs in flight and frees its
+// tensor memory before it returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+
+#include "llama_surrogate.h"
+
+namespace llama_sg {
+
+constexpr int kBM = 128;            // rows per tile (tensor-memory lanes)
+constexpr int kBK = 64;             // K per stage: one 128-byte swizzle row of BF16
+constexpr int kStages = 4;
+constexpr int kThreads = 128;
+constexpr int kMaxTries = 1 << 22;  // bounded mbarrier waits
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (int it = 0; it < kMaxTries; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar) : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, 8-row groups 1024 bytes apart (descriptor version 1).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+    return (uint64_t)((addr & 0x3FFFF) >> 4)      // start address
+           | ((uint64_t)1 << 16)                  // leading byte offset (unused here)
+           | ((uint64_t)(1024 >> 4) << 32)        // stride byte offset
+           | ((uint64_t)1 << 46)                  // version
+           | ((uint64_t)2 << 61);                 // 128-byte swizzle
+}
+
+// Instruction descriptor of kind::f16: BF16 x BF16 -> FP32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
+                int K, const float *__restrict__ bias, int flags, __nv_bfloat16 *__restrict__ c16,
+                float *__restrict__ c32, int ldc, int *err) {
+    constexpr int A_BYTES = kBM * kBK * 2, B_BYTES = BN * kBK * 2, STAGE = A_BYTES + B_BYTES;
+    constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], accf;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int issued, consumed, failed;
+    const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN, nk = K / kBK;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
+        mbar_init(smem_u32(&accf), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        issued = consumed = failed = 0;
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(&tmem_slot)), "r"(TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // producer: TMA into the stage ring
+        int kb = 0;
+        for (; kb < nk; ++kb) {
+            const int s = kb % kStages;
+            if (kb >= kStages && !mbar_wait(smem_u32(&empty[s]), ((kb / kStages) - 1) & 1)) {
+                failed = 1;
+                break;
+            }
+            const uint32_t a = base + s * STAGE, b = a + A_BYTES, bar = smem_u32(&full[s]);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(STAGE) : "memory");
+            tma_load_2d(a, &tmA, kb * kBK, m0, bar);
+            tma_load_2d(b, &tmB, kb * kBK, n0, bar);
+        }
+        issued = kb;
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        constexpr uint32_t idesc = idesc_bf16(kBM, BN);
+        int kb = 0;
+        for (; kb < nk; ++kb) {
+            const int s = kb % kStages;
+            if (!mbar_wait(smem_u32(&full[s]), (kb / kStages) & 1)) {
+                failed = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a = base + s * STAGE, b = a + A_BYTES;
+#pragma unroll
+            for (int j = 0; j < kBK / 16; ++j) {
+                const uint64_t ad = smem_desc_sw128(a + 32 * j), bd = smem_desc_sw128(b + 32 * j);
+                const uint32_t acc = (kb > 0 || j > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                    ::"r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         ::"r"(smem_u32(&empty[s])) : "memory");
+        }
+        consumed = kb;
+        // completes once every MMA issued above has completed
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     ::"r"(smem_u32(&accf)) : "memory");
+    }
+    __syncwarp();
+    // epilogue: thread (warp w, lane l) owns row m0 + 32w + l, tensor-memory lane 32w + l
+    const bool acc_ok = mbar_wait(smem_u32(&accf), 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    const bool ok = acc_ok && !failed && nk > 0;
+    const int row = m0 + warp * 32 + lane;
+    const bool relu = flags & LLAMA_GEMM_RELU;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+        uint32_t r[16];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (!ok || row >= M) continue;
+        float v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            v[j] = __uint_as_float(r[j]) + (bias ? bias[n0 + c0 + j] : 0.f);
+            if (relu) v[j] = fmaxf(v[j], 0.f);
+        }
+        const int64_t o = (int64_t)row * ldc + n0 + c0;
+        if (c32) {
+#pragma unroll
+            for (int j = 0; j < 16; j += 4)
+                *reinterpret_cast<float4 *>(c32 + o + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        }
+        if (c16) {
+            uint32_t p[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                p[j] = *reinterpret_cast<const uint32_t *>(&h);
+            }
+            *reinterpret_cast<uint4 *>(c16 + o) = make_uint4(p[0], p[1], p[2], p[3]);
+            *reinterpret_cast<uint4 *>(c16 + o + 8) = make_uint4(p[4], p[5], p[6], p[7]);
+        }
+    }
+    if (!ok) {
+        if (threadIdx.x == 0) {
+            atomicOr(err, 1);
+            // copies issued but never consumed: let them land before the CTA exits
+            for (int kb = consumed; kb < issued; ++kb)
+                mbar_wait(smem_u32(&full[kb % kStages]), (kb / kStages) & 1);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder() {
+    static EncodeTiled fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    });
+    return fn;
+}
+
+// Row-major BF16 matrix [rows x cols] (cols a multiple of 64), tiles of
+// box_rows x 64 with the 128-byte swizzle.
+int make_map(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, int box_rows) {
+    EncodeTiled enc = encoder();
+    if (!enc) return LLAMA_ECUDA;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box,
+                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? LLAMA_OK : LLAMA_EINVAL;
+}
+
+template <int BN>
+cudaError_t launch_gemm(const CUtensorMap &ta, const CUtensorMap &tb, int64_t M, int N, int K, const float *bias,
+                        int flags, void *c16, float *c32, int ldc, int *err, cudaStream_t s) {
+    constexpr int smem = kStages * (kBM + BN) * kBK * 2 + 1024;
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+        attr = cudaFuncSetAttribute(k_gemm_bf16<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    });
+    if (attr != cudaSuccess) return attr;
+    const dim3 grid((unsigned)((M + kBM - 1) / kBM), (unsigned)(N / BN));
+    k_gemm_bf16<BN><<<grid, kThreads, smem, s>>>(ta, tb, (int)M, N, K, bias, flags,
+                                                  static_cast<__nv_bfloat16 *>(c16), c32, ldc, err);
+    return cudaGetLastError();
+}
+
+int *error_word() {
+    static int *w = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        if (cudaMalloc(&w, sizeof(int)) != cudaSuccess) w = nullptr;
+        else cudaMemset(w, 0, sizeof(int));
+    });
+    return w;
+}
+
+}  // namespace llama_sg
+
+using namespace llama_sg;
+
+extern "C" int llama_gemm_bf16(const void *a, const void *b, const float *bias, void *c_bf16, float *c_f32,
+                               int64_t m, int32_t n, int32_t k, int32_t flags, void *stream) {
+    if (!a || !b || (!c_bf16 && !c_f32)) return LLAMA_EINVAL;
+    if (m < 1 || m > (1 << 30) || k < kBK || k % kBK || k > (1 << 20)) return LLAMA_EINVAL;
+    if (n != 64 && n % 128) return LLAMA_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15) return LLAMA_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(c_bf16) | reinterpret_cast<uintptr_t>(c_f32)) & 15) return LLAMA_EINVAL;
+    int *err = error_word();
+    if (!err) return LLAMA_ENOMEM;
+    const int bn = n == 64 ? 64 : n % 256 == 0 ? 256 : 128;
+    CUtensorMap ta, tb;
+    if (make_map(&ta, a, m, k, kBM) != LLAMA_OK || make_map(&tb, b, n, k, bn) != LLAMA_OK) return LLAMA_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (bn == 64) e = launch_gemm<64>(ta, tb, m, n, k, bias, flags, c_bf16, c_f32, n, err, s);
+    else if (bn == 128) e = launch_gemm<128>(ta, tb, m, n, k, bias, flags, c_bf16, c_f32, n, err, s);
+    else e = launch_gemm<256>(ta, tb, m, n, k, bias, flags, c_bf16, c_f32, n, err, s);
+    return e == cudaSuccess ? LLAMA_OK : LLAMA_ECUDA;
+}
+
+extern "C" int llama_gemm_error(int32_t clear) {
+    int *err = error_word();
+    if (!err) return LLAMA_ENOMEM;
+    int h = 0;
+    if (cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return LLAMA_ECUDA;
+    if (clear && h) cudaMemset(err, 0, sizeof(int));
+    return h ? LLAMA_ETIMEOUT : LLAMA_OK;
+}

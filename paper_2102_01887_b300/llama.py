@@ -32,7 +32,7 @@ EXPORTS = ("llama_create", "llama_destroy", "llama_set_dags", "llama_set_profile
            "llama_set_queue", "llama_schedule", "llama_schedule_async", "llama_schedule_static",
            "llama_set_tuning", "llama_set_method", "llama_reserve",
            "llama_critical_path", "llama_slack", "llama_set_trace_events", "llama_last_launch_count",
-           "llama_last_error")
+           "llama_last_error", "llama_gemm_bf16", "llama_gemm_error")
 TRACE_EVENTS = 3
 TRACE_PHASES = ("bucket", "score")
 
@@ -80,6 +80,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "llama_set_trace_events": ([vp, vp, i32], ctypes.c_int),
             "llama_last_launch_count": ([vp], ctypes.c_int),
             "llama_last_error": ([vp], ctypes.c_char_p),
+            "llama_gemm_bf16": ([vp, vp, vp, vp, vp, i64, i32, i32, i32, vp], ctypes.c_int),
+            "llama_gemm_error": ([i32], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -152,6 +154,35 @@ def llama_set_tuning(ctx, lanes_min_vectors: int = 16, inv_per_thread: int = 2,
                      chunk_entries: int = 0, stages: int = 1) -> None:
     _check(ctx, load().llama_set_tuning(ctx, int(lanes_min_vectors), int(inv_per_thread),
                                         int(chunk_entries), int(stages)))
+
+
+GEMM_RELU = 1
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def llama_gemm_bf16(a, b, bias=None, c_bf16=None, c_f32=None, flags: int = 0, stream=None) -> None:
+    """C = A . B^T (+ bias) (ReLU) on the tensor cores; torch CUDA tensors.
+
+    a: [m, k] bf16, b: [n, k] bf16, bias: [n] float32 or None; c_bf16 [m, n]
+    bf16 and/or c_f32 [m, n] float32 receive the result.
+    """
+    m, k = a.shape
+    n = b.shape[0]
+    ptr = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())
+    rc = load().llama_gemm_bf16(ptr(a), ptr(b), ptr(bias), ptr(c_bf16), ptr(c_f32), m, n, k, int(flags),
+                                _stream_ptr(stream))
+    if rc != OK:
+        raise LlamaError(rc, "gemm_bf16: bad arguments or launch failure")
+
+
+def llama_gemm_error(clear: bool = True) -> int:
+    return load().llama_gemm_error(1 if clear else 0)
 
 
 def llama_set_method(ctx, method: int) -> None:

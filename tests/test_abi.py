@@ -1,5 +1,6 @@
 """Host-side checks of the C ABI (no GPU needed, no compute calls)."""
 import ctypes
+import glob
 import os
 import re
 import subprocess
@@ -11,7 +12,7 @@ from paper_2102_01887_b300 import build as B
 from paper_2102_01887_b300 import llama as L
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "llama.h")
+HEADERS = sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
 @pytest.fixture(scope="module")
@@ -21,9 +22,11 @@ def lib():
 
 
 def declared_functions() -> list[str]:
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(llama_[a-z_]+)\s*\(", text)))
+    names = set()
+    for h in HEADERS:
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"\b(llama_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
 
 
 def test_header_declares_the_binding_exports():
@@ -61,12 +64,13 @@ int main(void) {
 
 
 def test_constants_match_header():
-    text = open(HEADER).read()
+    text = "".join(open(h).read() for h in HEADERS)
     for name, val in [("LLAMA_OK", L.OK), ("LLAMA_EINVAL", L.EINVAL), ("LLAMA_ENOMEM", L.ENOMEM),
                       ("LLAMA_ECUDA", L.ECUDA), ("LLAMA_ENOTREADY", L.ENOTREADY),
                       ("LLAMA_ETIMEOUT", L.ETIMEOUT), ("LLAMA_MODE_ALPHA", L.MODE_ALPHA),
                       ("LLAMA_FLAG_FEASIBLE", L.FLAG_FEASIBLE), ("LLAMA_FLAG_INVALID", L.FLAG_INVALID),
-                      ("LLAMA_MAX_HW", L.MAX_HW), ("LLAMA_MAX_CFG", L.MAX_CFG)]:
+                      ("LLAMA_MAX_HW", L.MAX_HW), ("LLAMA_MAX_CFG", L.MAX_CFG),
+                      ("LLAMA_METHOD_STAIRCASE", L.METHOD_STAIRCASE), ("LLAMA_GEMM_RELU", L.GEMM_RELU)]:
         m = re.search(rf"#define {name} \(?(-?\d+)\)?", text)
         assert m and int(m.group(1)) == val, name
 
