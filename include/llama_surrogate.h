@@ -47,6 +47,50 @@ int llama_gemm_bf16(const void *a, const void *b, const float *bias, void *c_bf1
  * Synchronous (reads one device word); clear != 0 resets the flag. */
 int llama_gemm_error(int32_t clear);
 
+/* The network: LLAMA_MLP_INPUTS inputs (48 features in use: 32 describing the
+ * configuration and its operation, 16 the invocation's frame content; the
+ * rest zero), three hidden layers of 256 with ReLU, LLAMA_MLP_OUTPUTS outputs
+ * of which the first two are read: y0 = log(latency / profiled latency) and
+ * y1 = branch fan-out.  Loss: the batch mean of (y0 - t0)^2 / 2 +
+ * w_fan (y1 - t1)^2 / 2.  Parameters travel as LLAMA_MLP_PARAMS FP32 values in
+ * the order W1[256x64], b1[256], W2[256x256], b2, W3[256x256], b3, W4[64x256],
+ * b4[64] (row-major, W[out x in]).  Products run on the tensor cores in BF16
+ * with FP32 accumulation; the FP32 parameters are the master copy. */
+#define LLAMA_MLP_INPUTS 64
+#define LLAMA_MLP_OUTPUTS 64
+#define LLAMA_MLP_PARAMS 164672
+
+typedef struct llama_mlp llama_mlp;
+
+/* A network on `device` with activation buffers for batches of up to
+ * max_batch rows (128 .. 2^26), parameters zero.  Errors: EINVAL, ENOMEM, ECUDA. */
+int llama_mlp_create(llama_mlp **out, int32_t device, int64_t max_batch);
+void llama_mlp_destroy(llama_mlp *net);
+
+/* Copy LLAMA_MLP_PARAMS FP32 values from / to host memory (blocking).  Setting
+ * the parameters also resets the optimizer state. */
+int llama_mlp_set_params(llama_mlp *net, const float *params);
+int llama_mlp_get_params(llama_mlp *net, float *params);
+
+/* Outputs y0, y1 of n rows of x (BF16 [n x 64], device, 16-byte aligned) into
+ * y (FP32 [n x 2], device).  1 <= n <= max_batch. */
+int llama_mlp_forward(llama_mlp *net, const void *x, int64_t n, float *y, void *stream);
+
+/* Gradient of the mean loss over n rows (a multiple of 128) of x with targets
+ * t (FP32 [n x 2], device): written to grads (FP32 [LLAMA_MLP_PARAMS], device)
+ * unless NULL; the loss is written to *loss (device) unless NULL. */
+int llama_mlp_gradients(llama_mlp *net, const void *x, const float *t, int64_t n, float w_fan,
+                        float *grads, float *loss, void *stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) at
+ * learning rate lr on the gradient of that batch; *loss (device) gets the
+ * batch loss before the step unless NULL. */
+int llama_mlp_train_step(llama_mlp *net, const void *x, const float *t, int64_t n, float w_fan, float lr,
+                         float *loss, void *stream);
+
+/* One-line description of the network's last failure. */
+const char *llama_mlp_last_error(llama_mlp *net);
+
 #ifdef __cplusplus
 }
 #endif

@@ -265,28 +265,33 @@ int *error_word() {
     return w;
 }
 
+// C = A . B^T for row-major BF16 operands (see llama_gemm_bf16), enqueued on s.
+int gemm(const void *a, const void *b, const float *bias, void *c16, float *c32, int64_t m, int n, int k,
+         int flags, cudaStream_t s) {
+    if (!a || !b || (!c16 && !c32)) return LLAMA_EINVAL;
+    if (m < 1 || m > (1 << 30) || k < kBK || k % kBK || k > (1 << 24)) return LLAMA_EINVAL;
+    if (n != 64 && n % 128) return LLAMA_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15) return LLAMA_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(c16) | reinterpret_cast<uintptr_t>(c32)) & 15) return LLAMA_EINVAL;
+    int *err = error_word();
+    if (!err) return LLAMA_ENOMEM;
+    const int bn = n == 64 ? 64 : n % 256 == 0 ? 256 : 128;
+    CUtensorMap ta, tb;
+    if (make_map(&ta, a, m, k, kBM) != LLAMA_OK || make_map(&tb, b, n, k, bn) != LLAMA_OK) return LLAMA_EINVAL;
+    cudaError_t e;
+    if (bn == 64) e = launch_gemm<64>(ta, tb, m, n, k, bias, flags, c16, c32, n, err, s);
+    else if (bn == 128) e = launch_gemm<128>(ta, tb, m, n, k, bias, flags, c16, c32, n, err, s);
+    else e = launch_gemm<256>(ta, tb, m, n, k, bias, flags, c16, c32, n, err, s);
+    return e == cudaSuccess ? LLAMA_OK : LLAMA_ECUDA;
+}
+
 }  // namespace llama_sg
 
 using namespace llama_sg;
 
 extern "C" int llama_gemm_bf16(const void *a, const void *b, const float *bias, void *c_bf16, float *c_f32,
                                int64_t m, int32_t n, int32_t k, int32_t flags, void *stream) {
-    if (!a || !b || (!c_bf16 && !c_f32)) return LLAMA_EINVAL;
-    if (m < 1 || m > (1 << 30) || k < kBK || k % kBK || k > (1 << 20)) return LLAMA_EINVAL;
-    if (n != 64 && n % 128) return LLAMA_EINVAL;
-    if ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15) return LLAMA_EINVAL;
-    if ((reinterpret_cast<uintptr_t>(c_bf16) | reinterpret_cast<uintptr_t>(c_f32)) & 15) return LLAMA_EINVAL;
-    int *err = error_word();
-    if (!err) return LLAMA_ENOMEM;
-    const int bn = n == 64 ? 64 : n % 256 == 0 ? 256 : 128;
-    CUtensorMap ta, tb;
-    if (make_map(&ta, a, m, k, kBM) != LLAMA_OK || make_map(&tb, b, n, k, bn) != LLAMA_OK) return LLAMA_EINVAL;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e;
-    if (bn == 64) e = launch_gemm<64>(ta, tb, m, n, k, bias, flags, c_bf16, c_f32, n, err, s);
-    else if (bn == 128) e = launch_gemm<128>(ta, tb, m, n, k, bias, flags, c_bf16, c_f32, n, err, s);
-    else e = launch_gemm<256>(ta, tb, m, n, k, bias, flags, c_bf16, c_f32, n, err, s);
-    return e == cudaSuccess ? LLAMA_OK : LLAMA_ECUDA;
+    return gemm(a, b, bias, c_bf16, c_f32, m, n, k, flags, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" int llama_gemm_error(int32_t clear) {

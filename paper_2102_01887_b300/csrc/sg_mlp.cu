@@ -1,0 +1,390 @@
+// The latency surrogate's network on the GPU: forward pass, gradients of the
+// mean loss, and Adam training steps, every matrix product on the tensor cores
+// (sg_gemm.cu), the rest in small elementwise kernels here.
+//
+// Network: 64 inputs (48 features, zero padding) -> 256 -> 256 -> 256 (ReLU)
+// -> 64 outputs of which the first two are read: y0 = log(latency / profiled
+// latency), y1 = branch fan-out.  Loss: mean over the batch of
+// (y0 - t0)^2 / 2 + w_fan (y1 - t1)^2 / 2.  Weights are kept in FP32 (the
+// master copy Adam updates) and as BF16 for the products, both as W (forward:
+// h W^T) and W^T (backward: dz W); activations are BF16, accumulation FP32.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <string>
+
+#include "llama_surrogate.h"
+#include "sg_internal.cuh"
+
+using namespace llama_sg;
+
+namespace {
+
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    cudaError_t alloc(size_t n) {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        if (n == 0) return cudaSuccess;
+        const cudaError_t e = cudaMalloc(&p, n);
+        if (e == cudaSuccess) bytes = n;
+        return e;
+    }
+    ~Buf() {
+        if (p) cudaFree(p);
+    }
+    template <class T>
+    T *as() const { return static_cast<T *>(p); }
+};
+
+using bf16 = __nv_bfloat16;
+
+// Transpose a row-major BF16 matrix [rows x cols] into [cols x rows] through
+// 32 x 32 shared-memory tiles (coalesced reads and writes).
+__global__ void k_transpose(const bf16 *__restrict__ src, bf16 *__restrict__ dst, int64_t rows, int cols) {
+    __shared__ bf16 tile[32][33];
+    const int64_t r0 = blockIdx.y * 32ll;
+    const int c0 = blockIdx.x * 32;
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int64_t r = r0 + j;
+        const int c = c0 + threadIdx.x;
+        tile[j][threadIdx.x] = (r < rows && c < cols) ? src[r * cols + c] : __float2bfloat16(0.f);
+    }
+    __syncthreads();
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int c = c0 + j;
+        const int64_t r = r0 + threadIdx.x;
+        if (c < cols && r < rows) dst[(int64_t)c * rows + r] = tile[threadIdx.x][j];
+    }
+}
+
+// Loss and its gradient with respect to the outputs (rows of 64, two read).
+__global__ void k_loss_grad(const float *__restrict__ y, const float *__restrict__ t, int64_t n, float w_fan,
+                            bf16 *__restrict__ dy, float *__restrict__ db4, float *__restrict__ loss) {
+    __shared__ float red[3][8];
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    float l = 0.f, g0 = 0.f, g1 = 0.f;
+    if (r < n) {
+        const float e0 = y[r * kOut] - t[2 * r], e1 = y[r * kOut + 1] - t[2 * r + 1];
+        const float inv = 1.f / (float)n;
+        l = 0.5f * (e0 * e0 + w_fan * e1 * e1) * inv;
+        g0 = e0 * inv;
+        g1 = w_fan * e1 * inv;
+        bf16 *row = dy + r * kOut;
+        row[0] = __float2bfloat16(g0);
+        row[1] = __float2bfloat16(g1);
+        for (int c = 2; c < kOut; ++c) row[c] = __float2bfloat16(0.f);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        l += __shfl_xor_sync(0xffffffffu, l, o);
+        g0 += __shfl_xor_sync(0xffffffffu, g0, o);
+        g1 += __shfl_xor_sync(0xffffffffu, g1, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = l;
+        red[1][threadIdx.x >> 5] = g0;
+        red[2][threadIdx.x >> 5] = g1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s0 += red[0][w], s1 += red[1][w], s2 += red[2][w];
+        if (loss) atomicAdd(loss, s0);
+        atomicAdd(db4, s1);
+        atomicAdd(db4 + 1, s2);
+    }
+}
+
+// Through a ReLU: dz = dh where the layer's output h was positive; dz is
+// written row-major and transposed (32 x 32 tiles), and its column sums
+// (the bias gradient) are accumulated.
+__global__ void k_relu_back(const float *__restrict__ dh, const bf16 *__restrict__ h, int64_t n,
+                            bf16 *__restrict__ dz, bf16 *__restrict__ dzt, float *__restrict__ db) {
+    __shared__ bf16 tile[32][33];
+    __shared__ float colsum[32][33];
+    const int64_t r0 = blockIdx.y * 32ll;
+    const int c0 = blockIdx.x * 32;
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int64_t r = r0 + j;
+        const int c = c0 + threadIdx.x;
+        float v = 0.f;
+        if (r < n) {
+            const int64_t o = r * kHid + c;
+            v = __bfloat162float(h[o]) > 0.f ? dh[o] : 0.f;
+            dz[o] = __float2bfloat16(v);
+        }
+        tile[j][threadIdx.x] = __float2bfloat16(v);
+        colsum[j][threadIdx.x] = v;
+    }
+    __syncthreads();
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int c = c0 + j;
+        const int64_t r = r0 + threadIdx.x;
+        if (r < n) dzt[(int64_t)c * n + r] = tile[threadIdx.x][j];
+    }
+    if (threadIdx.y == 0) {
+        float s = 0.f;
+        for (int j = 0; j < 32; ++j) s += colsum[j][threadIdx.x];
+        atomicAdd(db + c0 + threadIdx.x, s);
+    }
+}
+
+// Adam (Kingma and Ba, 2015), bias-corrected, over the flat FP32 parameters.
+__global__ void k_adam(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m,
+                       float *__restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float c1,
+                       float c2) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// BF16 copies of a weight matrix [rows x cols] (FP32): W and W^T.
+__global__ void k_pack(const float *__restrict__ w, int rows, int cols, bf16 *__restrict__ wb,
+                       bf16 *__restrict__ wt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows * cols) return;
+    const int r = i / cols, c = i % cols;
+    const bf16 b = __float2bfloat16(w[i]);
+    wb[i] = b;
+    if (wt) wt[(int64_t)c * rows + r] = b;
+}
+
+__global__ void k_take2(const float *__restrict__ y, int64_t n, float *__restrict__ out) {
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r < n) {
+        out[2 * r] = y[r * kOut];
+        out[2 * r + 1] = y[r * kOut + 1];
+    }
+}
+
+}  // namespace
+
+struct llama_mlp {
+    int device = 0;
+    int64_t cap = 0;      // batch capacity (rows)
+    int64_t steps = 0;    // Adam steps taken
+    Buf w, g, m, v;       // FP32 parameters, gradients, Adam moments
+    Buf wb[4], wt[4];     // BF16 W_l and W_l^T
+    Buf h1, h2, h3, y;    // activations (BF16) and outputs (FP32, 64 per row)
+    Buf h0t, h1t, h2t, h3t, dy, dyt, dh, dz, dzt;
+    std::string err;
+};
+
+namespace {
+
+const int kRows[4] = {kHid, kHid, kHid, kOut}, kCols[4] = {kIn, kHid, kHid, kHid};
+const int64_t kOffW[4] = {kOffW1, kOffW2, kOffW3, kOffW4}, kOffB[4] = {kOffB1, kOffB2, kOffB3, kOffB4};
+
+struct Guard {
+    int prev = -1;
+    explicit Guard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~Guard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int fail(llama_mlp *m, int code, const char *what, cudaError_t e = cudaSuccess) {
+    m->err = std::string(what) + (e != cudaSuccess ? std::string(": ") + cudaGetErrorString(e) : "");
+    return code;
+}
+
+#define MLP_CUDA(m, call)                                                          \
+    do {                                                                           \
+        const cudaError_t e__ = (call);                                            \
+        if (e__ != cudaSuccess)                                                    \
+            return fail((m), e__ == cudaErrorMemoryAllocation ? LLAMA_ENOMEM : LLAMA_ECUDA, #call, e__); \
+    } while (0)
+
+#define MLP_RC(call)                 \
+    do {                             \
+        const int rc__ = (call);     \
+        if (rc__ != LLAMA_OK) return rc__; \
+    } while (0)
+
+int pack_weights(llama_mlp *m, cudaStream_t s) {
+    const float *w = m->w.as<float>();
+    for (int l = 0; l < 4; ++l) {
+        const int n = kRows[l] * kCols[l];
+        k_pack<<<(n + 255) / 256, 256, 0, s>>>(w + kOffW[l], kRows[l], kCols[l], m->wb[l].as<bf16>(),
+                                              m->wt[l].as<bf16>());
+    }
+    MLP_CUDA(m, cudaGetLastError());
+    return LLAMA_OK;
+}
+
+void transpose(const bf16 *src, bf16 *dst, int64_t rows, int cols, cudaStream_t s) {
+    const dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+    k_transpose<<<grid, dim3(32, 8), 0, s>>>(src, dst, rows, cols);
+}
+
+// Forward pass over n rows of x (BF16 [n x 64]): h1, h2, h3 (BF16), y (FP32 [n x 64]).
+int forward(llama_mlp *m, const void *x, int64_t n, cudaStream_t s) {
+    const float *w = m->w.as<float>();
+    MLP_RC(gemm(x, m->wb[0].p, w + kOffB1, m->h1.p, nullptr, n, kHid, kIn, LLAMA_GEMM_RELU, s));
+    MLP_RC(gemm(m->h1.p, m->wb[1].p, w + kOffB2, m->h2.p, nullptr, n, kHid, kHid, LLAMA_GEMM_RELU, s));
+    MLP_RC(gemm(m->h2.p, m->wb[2].p, w + kOffB3, m->h3.p, nullptr, n, kHid, kHid, LLAMA_GEMM_RELU, s));
+    MLP_RC(gemm(m->h3.p, m->wb[3].p, w + kOffB4, nullptr, m->y.as<float>(), n, kOut, kHid, 0, s));
+    return LLAMA_OK;
+}
+
+// Gradients of the mean loss into m->g (FP32, flat), after a forward pass.
+int backward(llama_mlp *m, const void *x, const float *t, int64_t n, float w_fan, float *loss, cudaStream_t s) {
+    float *g = m->g.as<float>();
+    MLP_CUDA(m, cudaMemsetAsync(g, 0, sizeof(float) * kParams, s));
+    k_loss_grad<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m->y.as<float>(), t, n, w_fan, m->dy.as<bf16>(),
+                                                           g + kOffB4, loss);
+    transpose(m->dy.as<bf16>(), m->dyt.as<bf16>(), n, kOut, s);
+    transpose(static_cast<const bf16 *>(x), m->h0t.as<bf16>(), n, kIn, s);
+    transpose(m->h1.as<bf16>(), m->h1t.as<bf16>(), n, kHid, s);
+    transpose(m->h2.as<bf16>(), m->h2t.as<bf16>(), n, kHid, s);
+    transpose(m->h3.as<bf16>(), m->h3t.as<bf16>(), n, kHid, s);
+    MLP_CUDA(m, cudaGetLastError());
+    // layer 4 (linear): dW4 = dy^T h3, dh3 = dy W4
+    MLP_RC(gemm(m->dyt.p, m->h3t.p, nullptr, nullptr, g + kOffW4, kOut, kHid, (int)n, 0, s));
+    MLP_RC(gemm(m->dy.p, m->wt[3].p, nullptr, nullptr, m->dh.as<float>(), n, kHid, kOut, 0, s));
+    const bf16 *hs[3] = {m->h1.as<bf16>(), m->h2.as<bf16>(), m->h3.as<bf16>()};
+    const void *hts[4] = {m->h0t.p, m->h1t.p, m->h2t.p, m->h3t.p};
+    const dim3 rgrid(kHid / 32, (unsigned)((n + 31) / 32));
+    for (int l = 2; l >= 0; --l) {
+        // through the ReLU of layer l+1, then dW = dz^T h_l and (below layer 1) dh_l = dz W
+        k_relu_back<<<rgrid, dim3(32, 8), 0, s>>>(m->dh.as<float>(), hs[l], n, m->dz.as<bf16>(),
+                                                 m->dzt.as<bf16>(), g + kOffB[l]);
+        MLP_CUDA(m, cudaGetLastError());
+        MLP_RC(gemm(m->dzt.p, hts[l], nullptr, nullptr, g + kOffW[l], kHid, kCols[l], (int)n, 0, s));
+        if (l > 0) MLP_RC(gemm(m->dz.p, m->wt[l].p, nullptr, nullptr, m->dh.as<float>(), n, kHid, kHid, 0, s));
+    }
+    return LLAMA_OK;
+}
+
+int check_batch(llama_mlp *m, const void *x, int64_t n, bool training) {
+    if (!x) return fail(m, LLAMA_EINVAL, "null input");
+    if (n < 1 || n > m->cap) return fail(m, LLAMA_EINVAL, "batch outside 1..max_batch");
+    if (training && n % 128) return fail(m, LLAMA_EINVAL, "training batches must be a multiple of 128 rows");
+    if (reinterpret_cast<uintptr_t>(x) & 15) return fail(m, LLAMA_EINVAL, "input not 16-byte aligned");
+    return LLAMA_OK;
+}
+
+}  // namespace
+
+extern "C" int llama_mlp_create(llama_mlp **out, int32_t device, int64_t max_batch) {
+    if (!out) return LLAMA_EINVAL;
+    *out = nullptr;
+    if (max_batch < 128 || max_batch > (1 << 26)) return LLAMA_EINVAL;
+    llama_mlp *m = new llama_mlp();
+    m->device = device;
+    m->cap = (max_batch + 127) / 128 * 128;
+    Guard gd(device);
+    const int64_t c = m->cap;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](Buf &b, size_t bytes) { if (e == cudaSuccess) e = b.alloc(bytes); };
+    A(m->w, 4 * kParams), A(m->g, 4 * kParams), A(m->m, 4 * kParams), A(m->v, 4 * kParams);
+    for (int l = 0; l < 4; ++l) A(m->wb[l], 2 * kRows[l] * kCols[l]), A(m->wt[l], 2 * kRows[l] * kCols[l]);
+    A(m->h1, 2 * c * kHid), A(m->h2, 2 * c * kHid), A(m->h3, 2 * c * kHid), A(m->y, 4 * c * kOut);
+    A(m->h0t, 2 * c * kIn), A(m->h1t, 2 * c * kHid), A(m->h2t, 2 * c * kHid), A(m->h3t, 2 * c * kHid);
+    A(m->dy, 2 * c * kOut), A(m->dyt, 2 * c * kOut), A(m->dh, 4 * c * kHid), A(m->dz, 2 * c * kHid);
+    A(m->dzt, 2 * c * kHid);
+    if (e == cudaSuccess) e = cudaMemset(m->w.p, 0, 4 * kParams);
+    if (e == cudaSuccess) e = cudaMemset(m->m.p, 0, 4 * kParams);
+    if (e == cudaSuccess) e = cudaMemset(m->v.p, 0, 4 * kParams);
+    if (e == cudaSuccess && pack_weights(m, nullptr) != LLAMA_OK) e = cudaErrorUnknown;
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete m;
+        return e == cudaErrorMemoryAllocation ? LLAMA_ENOMEM : LLAMA_ECUDA;
+    }
+    *out = m;
+    return LLAMA_OK;
+}
+
+extern "C" void llama_mlp_destroy(llama_mlp *m) {
+    if (!m) return;
+    Guard gd(m->device);
+    delete m;
+}
+
+extern "C" int llama_mlp_set_params(llama_mlp *m, const float *params) {
+    if (!m) return LLAMA_EINVAL;
+    if (!params) return fail(m, LLAMA_EINVAL, "set_params: null params");
+    Guard gd(m->device);
+    MLP_CUDA(m, cudaMemcpy(m->w.p, params, 4 * kParams, cudaMemcpyHostToDevice));
+    MLP_CUDA(m, cudaMemset(m->m.p, 0, 4 * kParams));
+    MLP_CUDA(m, cudaMemset(m->v.p, 0, 4 * kParams));
+    m->steps = 0;
+    MLP_RC(pack_weights(m, nullptr));
+    MLP_CUDA(m, cudaDeviceSynchronize());
+    return LLAMA_OK;
+}
+
+extern "C" int llama_mlp_get_params(llama_mlp *m, float *params) {
+    if (!m) return LLAMA_EINVAL;
+    if (!params) return fail(m, LLAMA_EINVAL, "get_params: null params");
+    Guard gd(m->device);
+    MLP_CUDA(m, cudaDeviceSynchronize());
+    MLP_CUDA(m, cudaMemcpy(params, m->w.p, 4 * kParams, cudaMemcpyDeviceToHost));
+    return LLAMA_OK;
+}
+
+extern "C" int llama_mlp_forward(llama_mlp *m, const void *x, int64_t n, float *y, void *stream) {
+    if (!m) return LLAMA_EINVAL;
+    MLP_RC(check_batch(m, x, n, false));
+    if (!y) return fail(m, LLAMA_EINVAL, "forward: null output");
+    Guard gd(m->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    MLP_RC(forward(m, x, n, s));
+    k_take2<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m->y.as<float>(), n, y);
+    MLP_CUDA(m, cudaGetLastError());
+    return LLAMA_OK;
+}
+
+extern "C" int llama_mlp_gradients(llama_mlp *m, const void *x, const float *t, int64_t n, float w_fan,
+                                   float *grads, float *loss, void *stream) {
+    if (!m) return LLAMA_EINVAL;
+    MLP_RC(check_batch(m, x, n, true));
+    if (!t) return fail(m, LLAMA_EINVAL, "gradients: null targets");
+    Guard gd(m->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (loss) MLP_CUDA(m, cudaMemsetAsync(loss, 0, sizeof(float), s));
+    MLP_RC(forward(m, x, n, s));
+    MLP_RC(backward(m, x, t, n, w_fan, loss, s));
+    if (grads) MLP_CUDA(m, cudaMemcpyAsync(grads, m->g.p, 4 * kParams, cudaMemcpyDeviceToDevice, s));
+    return LLAMA_OK;
+}
+
+extern "C" int llama_mlp_train_step(llama_mlp *m, const void *x, const float *t, int64_t n, float w_fan,
+                                    float lr, float *loss, void *stream) {
+    if (!m) return LLAMA_EINVAL;
+    MLP_RC(check_batch(m, x, n, true));
+    if (!t) return fail(m, LLAMA_EINVAL, "train_step: null targets");
+    if (!(lr > 0.f) || lr > 1.f) return fail(m, LLAMA_EINVAL, "train_step: learning rate outside (0, 1]");
+    Guard gd(m->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (loss) MLP_CUDA(m, cudaMemsetAsync(loss, 0, sizeof(float), s));
+    MLP_RC(forward(m, x, n, s));
+    MLP_RC(backward(m, x, t, n, w_fan, loss, s));
+    const int64_t step = ++m->steps;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - (float)std::pow((double)b1, (double)step), c2 = 1.f - (float)std::pow((double)b2, (double)step);
+    k_adam<<<592, 256, 0, s>>>(m->w.as<float>(), m->g.as<float>(), m->m.as<float>(), m->v.as<float>(), kParams,
+                               lr, b1, b2, 1e-8f, c1, c2);
+    MLP_CUDA(m, cudaGetLastError());
+    MLP_RC(pack_weights(m, s));
+    return LLAMA_OK;
+}
+
+extern "C" const char *llama_mlp_last_error(llama_mlp *m) { return m ? m->err.c_str() : "null network"; }

@@ -32,7 +32,9 @@ EXPORTS = ("llama_create", "llama_destroy", "llama_set_dags", "llama_set_profile
            "llama_set_queue", "llama_schedule", "llama_schedule_async", "llama_schedule_static",
            "llama_set_tuning", "llama_set_method", "llama_reserve",
            "llama_critical_path", "llama_slack", "llama_set_trace_events", "llama_last_launch_count",
-           "llama_last_error", "llama_gemm_bf16", "llama_gemm_error")
+           "llama_last_error", "llama_gemm_bf16", "llama_gemm_error",
+           "llama_mlp_create", "llama_mlp_destroy", "llama_mlp_set_params", "llama_mlp_get_params",
+           "llama_mlp_forward", "llama_mlp_gradients", "llama_mlp_train_step", "llama_mlp_last_error")
 TRACE_EVENTS = 3
 TRACE_PHASES = ("bucket", "score")
 
@@ -82,6 +84,14 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "llama_last_error": ([vp], ctypes.c_char_p),
             "llama_gemm_bf16": ([vp, vp, vp, vp, vp, i64, i32, i32, i32, vp], ctypes.c_int),
             "llama_gemm_error": ([i32], ctypes.c_int),
+            "llama_mlp_create": ([ctypes.POINTER(vp), i32, i64], ctypes.c_int),
+            "llama_mlp_destroy": ([vp], None),
+            "llama_mlp_set_params": ([vp, vp], ctypes.c_int),
+            "llama_mlp_get_params": ([vp, vp], ctypes.c_int),
+            "llama_mlp_forward": ([vp, vp, i64, vp, vp], ctypes.c_int),
+            "llama_mlp_gradients": ([vp, vp, vp, i64, ctypes.c_float, vp, vp, vp], ctypes.c_int),
+            "llama_mlp_train_step": ([vp, vp, vp, i64, ctypes.c_float, ctypes.c_float, vp, vp], ctypes.c_int),
+            "llama_mlp_last_error": ([vp], ctypes.c_char_p),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -183,6 +193,59 @@ def llama_gemm_bf16(a, b, bias=None, c_bf16=None, c_f32=None, flags: int = 0, st
 
 def llama_gemm_error(clear: bool = True) -> int:
     return load().llama_gemm_error(1 if clear else 0)
+
+
+MLP_PARAMS = 164672
+MLP_INPUTS = 64
+
+
+class MLP:
+    """The latency surrogate's network on one GPU (torch CUDA tensors in and out)."""
+
+    def __init__(self, device: int = 0, max_batch: int = 8192):
+        self.h = ctypes.c_void_p()
+        rc = load().llama_mlp_create(ctypes.byref(self.h), int(device), int(max_batch))
+        if rc != OK:
+            raise LlamaError(rc, "mlp_create failed")
+
+    def _check(self, rc):
+        if rc != OK:
+            raise LlamaError(rc, load().llama_mlp_last_error(self.h).decode())
+
+    def set_params(self, flat) -> None:
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        assert a.shape == (MLP_PARAMS,)
+        self._check(load().llama_mlp_set_params(self.h, a.ctypes.data))
+
+    def get_params(self) -> np.ndarray:
+        a = np.empty(MLP_PARAMS, np.float32)
+        self._check(load().llama_mlp_get_params(self.h, a.ctypes.data))
+        return a
+
+    def forward(self, x, y, stream=None) -> None:
+        self._check(load().llama_mlp_forward(self.h, ctypes.c_void_p(x.data_ptr()), x.shape[0],
+                                             ctypes.c_void_p(y.data_ptr()), _stream_ptr(stream)))
+
+    def gradients(self, x, t, w_fan: float, grads=None, loss=None, stream=None) -> None:
+        p = lambda v: None if v is None else ctypes.c_void_p(v.data_ptr())
+        self._check(load().llama_mlp_gradients(self.h, p(x), p(t), x.shape[0], float(w_fan), p(grads), p(loss),
+                                               _stream_ptr(stream)))
+
+    def train_step(self, x, t, w_fan: float, lr: float, loss=None, stream=None) -> None:
+        p = lambda v: None if v is None else ctypes.c_void_p(v.data_ptr())
+        self._check(load().llama_mlp_train_step(self.h, p(x), p(t), x.shape[0], float(w_fan), float(lr), p(loss),
+                                                _stream_ptr(stream)))
+
+    def close(self) -> None:
+        if self.h:
+            load().llama_mlp_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def llama_set_method(ctx, method: int) -> None:

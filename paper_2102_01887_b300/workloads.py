@@ -69,6 +69,7 @@ class Problem:
     res: Optional[np.ndarray] = None  # int32[n_cfg]
     res_total: Optional[np.ndarray] = None  # int32[n_hw]
     q_us: Optional[np.ndarray] = None  # int64[n_hw]: queueing time per backend
+    knobs: Optional["Knobs"] = None  # knob values behind every configuration
 
     @property
     def n_dags(self) -> int:
@@ -85,6 +86,19 @@ class Problem:
     def table_bytes(self) -> int:
         """Bytes of the latency + cost columns (12 B per configuration)."""
         return int(self.lat_us.nbytes + self.cost_nd.nbytes)
+
+
+@dataclasses.dataclass
+class Knobs:
+    """Knob values of every configuration and descriptors of every operation
+    (what a profiler knows about a configuration besides its latency)."""
+
+    hw: np.ndarray  # int8[n_cfg]: hardware type
+    res_idx: np.ndarray  # int8[n_cfg]: processing resolution, index into RESOLUTIONS
+    samp_idx: np.ndarray  # int8[n_cfg]: sampling rate index
+    variant: np.ndarray  # float32[n_cfg]: variant speed factor
+    op_base_us: np.ndarray  # float64[n_ops]: the operation's base latency
+    op_gpu_speed: np.ndarray  # float64[n_ops]
 
 
 @dataclasses.dataclass
@@ -195,19 +209,22 @@ def _knob_table(rng: np.random.Generator, n: int, base: float, gpu_speed: float)
     cost = np.rint(lat.astype(np.float64) * r * price / b).astype(np.int64)
     hw_off = np.searchsorted(h, np.arange(N_HW + 1), side="left").astype(np.int32)
     ref = int(np.searchsorted(keep, ref_full))
-    return lat.astype(np.int32), cost, b.astype(np.int32), r.astype(np.int32), hw_off, ref
+    knobs = (h.astype(np.int8), re.astype(np.int8), sa.ravel()[keep].astype(np.int8),
+             var_f[va].astype(np.float32))
+    return lat.astype(np.int32), cost, b.astype(np.int32), r.astype(np.int32), hw_off, ref, knobs
 
 
 def _assemble(rng: np.random.Generator, dags: list[list[list[int]]], sizes: np.ndarray,
               slo_fn, knobs: bool = True, q_max: int = 0) -> Problem:
     dag_op_off, row_ptr, col = _csr(dags)
     n_ops = int(dag_op_off[-1])
-    lats, costs, batches, ress, hw_offs, refs = [], [], [], [], [], []
+    lats, costs, batches, ress, hw_offs, refs, kn, bases, speeds = [], [], [], [], [], [], [], [], []
     for v in range(n_ops):
         base = math.exp(rng.uniform(math.log(5_000.0), math.log(2_000_000.0)))
         gpu_speed = rng.uniform(2.0, 12.0)
-        lat, cost, b, r, hw_off, ref = _knob_table(rng, int(sizes[v]), base, gpu_speed)
+        lat, cost, b, r, hw_off, ref, k = _knob_table(rng, int(sizes[v]), base, gpu_speed)
         lats.append(lat), costs.append(cost), hw_offs.append(hw_off), refs.append(ref)
+        kn.append(k), bases.append(base), speeds.append(gpu_speed)
         if knobs:
             batches.append(b), ress.append(r)
     cfg_off = np.zeros(n_ops + 1, dtype=np.int64)
@@ -224,7 +241,9 @@ def _assemble(rng: np.random.Generator, dags: list[list[list[int]]], sizes: np.n
         cost_nd=np.concatenate(costs).astype(np.int64), ref_cfg=ref_cfg,
         batch=np.concatenate(batches) if knobs else None,
         res=np.concatenate(ress) if knobs else None,
-        res_total=np.asarray(RES_TOTAL, dtype=np.int32), q_us=q)
+        res_total=np.asarray(RES_TOTAL, dtype=np.int32), q_us=q,
+        knobs=Knobs(*(np.concatenate([k[j] for k in kn]) for j in range(4)),
+                    op_base_us=np.asarray(bases), op_gpu_speed=np.asarray(speeds)))
 
 
 def _invocations(rng: np.random.Generator, p: Problem, n_inv: int, now_us: int) -> Invocations:
@@ -386,3 +405,139 @@ def random_small(seed: int, max_dags: int = 3, max_ops: int = 6, max_cfg: int = 
 
 
 WORKLOADS = {"tiny": tiny, "medium": medium, "batched": batched, "batched_large": batched_large}
+
+
+# ----------------------------------------------------------------------------
+# Content-dependent latency: the world the learned surrogate is trained on
+# ----------------------------------------------------------------------------
+#
+# The profile table holds each configuration's latency measured on reference
+# content.  Real invocations carry frames whose content changes the latency
+# (the paper's Fig. 3 motivates this: the same operation on different videos).
+# Here an operation has one of N_OP_TYPES kinds, and its latency on content c
+# is the profiled latency times exp(log_factor(kind, knobs, c) + noise), the
+# factor being 0 on the reference content.  Branch fan-out grows with the
+# number of objects for the branching kinds.
+
+N_OP_TYPES = 8
+N_BRANCH_TYPES = 2  # kinds 0 and 1 fan out per detected object
+N_CFG_FEATURES = 32
+N_CONTENT_FEATURES = 16
+N_FEATURES = N_CFG_FEATURES + N_CONTENT_FEATURES
+REF_OBJECTS, REF_MOTION, REF_IN_RES = 10, 0.5, len(RESOLUTIONS) - 1
+LATENCY_NOISE_SIGMA = 0.1
+
+
+@dataclasses.dataclass
+class ContentWorld:
+    """Per-operation kinds and the per-kind sensitivities of latency to content."""
+
+    op_type: np.ndarray  # int8[n_ops]
+    a_obj: np.ndarray  # float64[N_OP_TYPES]: per 25 objects above the reference
+    b_motion: np.ndarray  # per unit of motion above the reference
+    s_batch: np.ndarray  # objects x batch interaction (saturating at batch 16)
+    r_res: np.ndarray  # per unit of (input resolution / 1080)^1.5 below 1
+    f_fan: np.ndarray  # expected extra fan-out per object (branching kinds)
+
+
+@dataclasses.dataclass
+class Content:
+    """Frame content of invocations."""
+
+    n_obj: np.ndarray  # int32[n]: objects in the frame
+    motion: np.ndarray  # float32[n]: motion score in [0, 1]
+    in_res: np.ndarray  # int8[n]: input resolution, index into RESOLUTIONS
+
+    @property
+    def n(self) -> int:
+        return int(self.n_obj.shape[0])
+
+
+def content_world(p: Problem, seed: int = 101) -> ContentWorld:
+    rng = np.random.default_rng(seed)
+    return ContentWorld(op_type=rng.integers(0, N_OP_TYPES, size=p.n_ops).astype(np.int8),
+                        a_obj=rng.uniform(0.2, 1.2, N_OP_TYPES), b_motion=rng.uniform(0.0, 0.6, N_OP_TYPES),
+                        s_batch=rng.uniform(0.0, 0.5, N_OP_TYPES), r_res=rng.uniform(0.0, 0.8, N_OP_TYPES),
+                        f_fan=rng.uniform(0.02, 0.1, N_OP_TYPES))
+
+
+def draw_content(rng: np.random.Generator, n: int) -> Content:
+    """Objects ~ Poisson(lambda), lambda ~ U(0, 50); motion ~ U(0, 1); input resolution uniform."""
+    lam = rng.uniform(0.0, 50.0, n)
+    return Content(rng.poisson(lam).astype(np.int32), rng.uniform(0.0, 1.0, n).astype(np.float32),
+                   rng.integers(0, len(RESOLUTIONS), n).astype(np.int8))
+
+
+def reference_content(n: int) -> Content:
+    return Content(np.full(n, REF_OBJECTS, np.int32), np.full(n, REF_MOTION, np.float32),
+                   np.full(n, REF_IN_RES, np.int8))
+
+
+def config_features(p: Problem, cw: ContentWorld, gop: np.ndarray, cfg: np.ndarray) -> np.ndarray:
+    """Features of configurations (global op ids, op-local indices): float32[m, 32]."""
+    k = p.knobs
+    g = p.cfg_off[gop] + cfg
+    m = g.shape[0]
+    f = np.zeros((m, N_CFG_FEATURES), np.float32)
+    f[np.arange(m), k.hw[g]] = 1.0
+    f[:, 3] = np.log2(p.res[g]) / 4.0 if p.res is not None else 0.0
+    f[:, 4] = np.log2(p.batch[g]) / 7.0 if p.batch is not None else 0.0
+    f[np.arange(m), 5 + k.res_idx[g]] = 1.0
+    f[np.arange(m), 9 + k.samp_idx[g]] = 1.0
+    f[:, 14] = np.log(k.variant[g])
+    f[:, 15] = (np.log(k.op_base_us[gop]) - math.log(5e3)) / math.log(400.0)
+    f[:, 16] = k.op_gpu_speed[gop] / 12.0
+    f[:, 17] = (np.log(p.lat_us[g]) - 8.0) / 8.0
+    f[np.arange(m), 18 + cw.op_type[gop]] = 1.0
+    return f
+
+
+def content_features(c: Content) -> np.ndarray:
+    """Features of frame content: float32[n, 16]."""
+    f = np.zeros((c.n, N_CONTENT_FEATURES), np.float32)
+    f[:, 0] = c.n_obj / 50.0
+    f[:, 1] = np.log1p(c.n_obj) / 4.0
+    f[:, 2] = c.motion
+    f[np.arange(c.n), 3 + c.in_res] = 1.0
+    f[:, 7] = 1.0
+    return f
+
+
+def true_log_factor(p: Problem, cw: ContentWorld, gop: np.ndarray, cfg: np.ndarray, c: Content) -> np.ndarray:
+    """log(latency on content c / profiled latency), without noise (0 on reference content)."""
+    t = cw.op_type[gop]
+    b = p.batch[p.cfg_off[gop] + cfg].astype(np.float64)
+    dobj = c.n_obj.astype(np.float64) - REF_OBJECTS
+    res = (np.asarray(RESOLUTIONS, np.float64)[c.in_res] / 1080.0) ** 1.5
+    return (cw.a_obj[t] * dobj / 25.0 + cw.b_motion[t] * (c.motion.astype(np.float64) - REF_MOTION)
+            + cw.s_batch[t] * np.minimum(b, 16.0) / 16.0 * dobj / 50.0 + cw.r_res[t] * (res - 1.0))
+
+
+def expected_fanout(cw: ContentWorld, gop: np.ndarray, c: Content) -> np.ndarray:
+    t = cw.op_type[gop]
+    return 1.0 + np.where(t < N_BRANCH_TYPES, cw.f_fan[t] * c.n_obj, 0.0)
+
+
+def surrogate_training_set(p: Problem, cw: ContentWorld, n: int, seed: int = 202):
+    """n profiled samples: features float32[n, 48]; targets float32[n, 2] =
+    (log latency factor with lognormal noise, sampled fan-out)."""
+    rng = np.random.default_rng(seed)
+    gop = rng.integers(0, p.n_ops, n)
+    cfg = (rng.random(n) * np.diff(p.cfg_off)[gop]).astype(np.int64)
+    c = draw_content(rng, n)
+    x = np.concatenate([config_features(p, cw, gop, cfg), content_features(c)], axis=1)
+    t = np.empty((n, 2), np.float32)
+    t[:, 0] = true_log_factor(p, cw, gop, cfg, c) + rng.normal(0.0, LATENCY_NOISE_SIGMA, n)
+    t[:, 1] = 1.0 + np.where(cw.op_type[gop] < N_BRANCH_TYPES,
+                             rng.poisson(cw.f_fan[cw.op_type[gop]] * c.n_obj), 0)
+    return x, t
+
+
+def invocation_content(seed: int, n: int, reference: bool = False) -> Content:
+    """Content of n pending invocations (reference content for all if asked)."""
+    return reference_content(n) if reference else draw_content(np.random.default_rng(seed), n)
+
+
+def latency_noise(seed: int, shape) -> np.ndarray:
+    """The lognormal noise of the latencies actually observed (per invocation and configuration)."""
+    return np.random.default_rng(seed).normal(0.0, LATENCY_NOISE_SIGMA, shape)
