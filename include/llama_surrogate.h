@@ -91,6 +91,50 @@ int llama_mlp_train_step(llama_mlp *net, const void *x, const float *t, int64_t 
 /* One-line description of the network's last failure. */
 const char *llama_mlp_last_error(llama_mlp *net);
 
+/* Scheduling with the surrogate: the decisions of llama_schedule (cost-first,
+ * Algorithm 1's slack on the profiled reference latencies, Eq. 1's selection),
+ * with every configuration's latency and cost replaced by the profiled value
+ * times e^y0, y0 the network's prediction for (configuration, invocation
+ * content).  The context `ctx` supplies the DAGs, SLOs, queueing times and
+ * profile tables; `net` the weights (not copied: later training is seen).  A
+ * prediction that is not finite falls back to the profiled value.  Decisions
+ * report the predicted latency and cost of the chosen configuration and the
+ * slack of its backend; FEASIBLE means predicted latency < slack.  Scratch
+ * grows with the calls; at most max_inv invocations and max_pairs
+ * (invocation, configuration) pairs per call.  Errors: EINVAL. */
+typedef struct llama_sg llama_sg;
+int llama_sg_create(llama_sg **out, llama_ctx *ctx, llama_mlp *net, int64_t max_inv, int64_t max_pairs);
+void llama_sg_destroy(llama_sg *sg);
+
+/* cfg_x: BF16 [n_cfg x 64] device, row g = global configuration g, features
+ * of the configuration in columns 0..31, zeros elsewhere; inv_x: BF16
+ * [n_inv x 64] device, row i = invocation i, content features in columns
+ * 32..47, zeros elsewhere.  dag, op_local, start_us, out: device, as in
+ * llama_schedule_async.  Blocks until the number of pairs is known (one
+ * device-to-host read), then enqueues the rest on `stream`. */
+int llama_sg_schedule(llama_sg *sg, const void *cfg_x, const void *inv_x, int64_t n_inv, const int32_t *dag,
+                      const int32_t *op_local, const int64_t *start_us, int64_t now_us, llama_decision *out,
+                      void *stream);
+
+/* Safety margin in log units (0 .. 1, default 0): the selection uses
+ * e^(y0 + margin) times the profiled latency and cost, an upper quantile of the
+ * prediction when margin is about the model's error.  Selecting the cheapest
+ * configuration among noisy predictions favours underestimated ones; the
+ * margin offsets that.  Errors: EINVAL. */
+int llama_sg_set_margin(llama_sg *sg, float margin);
+
+/* Pairs of the last call (sum over valid invocations of their operation's
+ * configurations), -1 on a null handle. */
+int64_t llama_sg_last_pairs(llama_sg *sg);
+
+/* Per pair of the last call (pairs of invocation i at pair_off[i] ..
+ * pair_off[i+1], in configuration order): predicted latency (int32) and cost
+ * (int64); pair_off has n_inv + 1 entries.  Device pointers, each nullable. */
+int llama_sg_predictions(llama_sg *sg, int32_t *lhat, int64_t *chat, int64_t *pair_off, int64_t n_inv,
+                         void *stream);
+
+const char *llama_sg_last_error(llama_sg *sg);
+
 #ifdef __cplusplus
 }
 #endif

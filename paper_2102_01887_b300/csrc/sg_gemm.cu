@@ -20,8 +20,9 @@
 #include <mutex>
 
 #include "llama_surrogate.h"
+#include "sg_internal.cuh"
 
-namespace llama_sg {
+namespace sgk {
 
 constexpr int kBM = 128;            // rows per tile (tensor-memory lanes)
 constexpr int kBK = 64;             // K per stage: one 128-byte swizzle row of BF16
@@ -70,11 +71,34 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
-template <int BN>
+// Epilogue of the selection GEMM (layer 3 of the surrogate over (invocation,
+// configuration) pairs): per row, h3 = ReLU(acc + bias), the log latency factor
+// r = h3 . w4 + b4, the predicted latency and cost (profiled values times e^r)
+// and the pair's selection key, folded into the invocation's best key.  The
+// prediction is raised by the margin (an upper quantile of the model's error)
+// before use.
+__device__ __forceinline__ void select_row(const SelectArgs &A, int64_t row, float r) {
+    if (!isfinite(r)) r = 0.f;  // the profiled latency stands in for an unusable prediction
+    r = fminf(fmaxf(r + A.margin, -20.f), 20.f);
+    const int32_t i = A.pair_inv[row], g = A.pair_g[row], x = A.pair_x[row];
+    const double f = (double)expf(r);
+    const double lh = fmin(fmax(rint((double)A.lat[g] * f), 1.0), 2147483646.0);
+    const int32_t lhat = (int32_t)lh;
+    const int64_t chat = (int64_t)fmin(rint((double)A.cost[g] * f), 4.0e12);
+    const int32_t sl = A.slack[(int64_t)i * A.n_hw + A.cfg_lam[g]];
+    A.lhat[row] = lhat;
+    A.chat[row] = chat;
+    // cost-first: feasible pairs by (cost, index), else (latency, index) above them
+    const unsigned long long key = lhat < sl ? ((unsigned long long)chat << 13) | (unsigned long long)x
+                                             : (1ull << 62) | ((unsigned long long)lhat << 13) | (unsigned long long)x;
+    atomicMin(A.best + i, key);
+}
+
+template <int BN, bool SELECT>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
                 int K, const float *__restrict__ bias, int flags, __nv_bfloat16 *__restrict__ c16,
-                float *__restrict__ c32, int ldc, int *err) {
+                float *__restrict__ c32, int ldc, int *err, const __grid_constant__ SelectArgs sel) {
     constexpr int A_BYTES = kBM * kBK * 2, B_BYTES = BN * kBK * 2, STAGE = A_BYTES + B_BYTES;
     constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
     extern __shared__ uint8_t smem_raw[];
@@ -155,6 +179,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const bool ok = acc_ok && !failed && nk > 0;
     const int row = m0 + warp * 32 + lane;
     const bool relu = flags & LLAMA_GEMM_RELU;
+    float dot = 0.f;
 #pragma unroll 1
     for (int c0 = 0; c0 < BN; c0 += 16) {
         uint32_t r[16];
@@ -171,6 +196,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int j = 0; j < 16; ++j) {
             v[j] = __uint_as_float(r[j]) + (bias ? bias[n0 + c0 + j] : 0.f);
             if (relu) v[j] = fmaxf(v[j], 0.f);
+        }
+        if (SELECT) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) dot = fmaf(v[j], sel.w4[c0 + j], dot);
+            continue;
         }
         const int64_t o = (int64_t)row * ldc + n0 + c0;
         if (c32) {
@@ -189,6 +219,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             *reinterpret_cast<uint4 *>(c16 + o + 8) = make_uint4(p[4], p[5], p[6], p[7]);
         }
     }
+    if (SELECT && ok && row < M) select_row(sel, row, dot + *sel.b4);
     if (!ok) {
         if (threadIdx.x == 0) {
             atomicOr(err, 1);
@@ -239,19 +270,20 @@ int make_map(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, int 
     return r == CUDA_SUCCESS ? LLAMA_OK : LLAMA_EINVAL;
 }
 
-template <int BN>
+template <int BN, bool SELECT = false>
 cudaError_t launch_gemm(const CUtensorMap &ta, const CUtensorMap &tb, int64_t M, int N, int K, const float *bias,
-                        int flags, void *c16, float *c32, int ldc, int *err, cudaStream_t s) {
+                        int flags, void *c16, float *c32, int ldc, int *err, cudaStream_t s,
+                        const SelectArgs &sel = SelectArgs{}) {
     constexpr int smem = kStages * (kBM + BN) * kBK * 2 + 1024;
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
     std::call_once(once, [] {
-        attr = cudaFuncSetAttribute(k_gemm_bf16<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        attr = cudaFuncSetAttribute(k_gemm_bf16<BN, SELECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     });
     if (attr != cudaSuccess) return attr;
     const dim3 grid((unsigned)((M + kBM - 1) / kBM), (unsigned)(N / BN));
-    k_gemm_bf16<BN><<<grid, kThreads, smem, s>>>(ta, tb, (int)M, N, K, bias, flags,
-                                                  static_cast<__nv_bfloat16 *>(c16), c32, ldc, err);
+    k_gemm_bf16<BN, SELECT><<<grid, kThreads, smem, s>>>(ta, tb, (int)M, N, K, bias, flags,
+                                                          static_cast<__nv_bfloat16 *>(c16), c32, ldc, err, sel);
     return cudaGetLastError();
 }
 
@@ -285,9 +317,23 @@ int gemm(const void *a, const void *b, const float *bias, void *c16, float *c32,
     return e == cudaSuccess ? LLAMA_OK : LLAMA_ECUDA;
 }
 
-}  // namespace llama_sg
+// Layer 3 of the surrogate over m pairs (a: h2 [m x 256], b: W3 [256 x 256])
+// with the fused last layer and selection of the epilogue.
+int gemm_select(const void *a, const void *b, const float *bias, int64_t m, const SelectArgs &sel, cudaStream_t s) {
+    if (!a || !b || m < 1 || m > (1 << 30)) return LLAMA_EINVAL;
+    int *err = error_word();
+    if (!err) return LLAMA_ENOMEM;
+    CUtensorMap ta, tb;
+    if (make_map(&ta, a, m, kHid, kBM) != LLAMA_OK || make_map(&tb, b, kHid, kHid, 256) != LLAMA_OK)
+        return LLAMA_EINVAL;
+    const cudaError_t e = launch_gemm<256, true>(ta, tb, m, kHid, kHid, bias, LLAMA_GEMM_RELU, nullptr, nullptr,
+                                                 kHid, err, s, sel);
+    return e == cudaSuccess ? LLAMA_OK : LLAMA_ECUDA;
+}
 
-using namespace llama_sg;
+}  // namespace sgk
+
+using namespace sgk;
 
 extern "C" int llama_gemm_bf16(const void *a, const void *b, const float *bias, void *c_bf16, float *c_f32,
                                int64_t m, int32_t n, int32_t k, int32_t flags, void *stream) {

@@ -4,11 +4,35 @@
 
 #include <cstdint>
 
-namespace llama_sg {
+namespace sgk {
+
+// Arguments of the fused selection epilogue (see gemm_select).
+struct SelectArgs {
+    const float *w4 = nullptr;        // [256] row 0 of the last layer
+    const float *b4 = nullptr;        // its bias (device)
+    const int32_t *pair_inv = nullptr, *pair_g = nullptr, *pair_x = nullptr;  // per pair
+    const int8_t *cfg_lam = nullptr;  // backend of every configuration
+    const int32_t *lat = nullptr;     // profiled latency of every configuration
+    const int64_t *cost = nullptr;    // profiled cost per invocation of every configuration
+    const int32_t *slack = nullptr;   // [n_inv x n_hw]
+    int n_hw = 0;
+    float margin = 0.f;               // added to the predicted log factor before selection
+    unsigned long long *best = nullptr;  // [n_inv] best key so far
+    int32_t *lhat = nullptr;             // [pairs] predicted latency
+    int64_t *chat = nullptr;             // [pairs] predicted cost
+};
 
 // C = A . B^T on the tensor cores; see llama_gemm_bf16 for shapes and limits.
 int gemm(const void *a, const void *b, const float *bias, void *c16, float *c32, int64_t m, int n, int k,
          int flags, cudaStream_t s);
+struct llama_mlp_view {
+    const float *params;       // FP32 master parameters (flat layout above)
+    const void *w16[4];        // BF16 W1..W4 [out x in]
+    int device;
+};
+
+// Layer 3 of the surrogate with the fused last layer and selection.
+int gemm_select(const void *a, const void *b, const float *bias, int64_t m, const SelectArgs &sel, cudaStream_t s);
 // The device word that bounded waits of the GEMM set when they give up.
 int *error_word();
 
@@ -18,4 +42,9 @@ constexpr int64_t kOffW1 = 0, kOffB1 = kOffW1 + kHid * kIn, kOffW2 = kOffB1 + kH
                   kOffB2 = kOffW2 + kHid * kHid, kOffW3 = kOffB2 + kHid, kOffB3 = kOffW3 + kHid * kHid,
                   kOffW4 = kOffB3 + kHid, kOffB4 = kOffW4 + kOut * kHid, kParams = kOffB4 + kOut;
 
-}  // namespace llama_sg
+}  // namespace sgk
+
+struct llama_mlp;
+namespace sgk {
+llama_mlp_view mlp_view(const llama_mlp *m);
+}  // namespace sgk

@@ -19,7 +19,7 @@
 #include "llama_surrogate.h"
 #include "sg_internal.cuh"
 
-using namespace llama_sg;
+using namespace sgk;
 
 namespace {
 
@@ -388,3 +388,13 @@ extern "C" int llama_mlp_train_step(llama_mlp *m, const void *x, const float *t,
 }
 
 extern "C" const char *llama_mlp_last_error(llama_mlp *m) { return m ? m->err.c_str() : "null network"; }
+
+namespace sgk {
+llama_mlp_view mlp_view(const llama_mlp *m) {
+    llama_mlp_view v{};
+    v.params = m->w.as<float>();
+    for (int l = 0; l < 4; ++l) v.w16[l] = m->wb[l].p;
+    v.device = m->device;
+    return v;
+}
+}  // namespace sgk

@@ -1,0 +1,302 @@
+// Scheduling with the learned latency surrogate in place of the profile table.
+//
+// For every pending invocation i and every configuration x of its operation,
+// the network predicts the log latency factor r(i, x) from the configuration's
+// features and the invocation's content features; the predicted latency and
+// cost are the profiled ones times e^r, and the decision is the cost-first
+// selection of Eq. 1 over those predictions, each against slack(i, lambda(x))
+// (Algorithm 1, through the critical path of the profiled reference
+// latencies).  The first layer splits by linearity: z1(i, x) = A[x] + B[i] with
+// A = (configuration features) W1^T and B = (content features) W1^T + b1, the
+// other input columns being zero in each; so a pair costs one ReLU of a sum
+// and two 256 x 256 products (tensor cores), the last layer and the selection
+// running in the epilogue of the second product.
+#include <cub/cub.cuh>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "llama_internal.cuh"
+#include "llama_surrogate.h"
+#include "sg_internal.cuh"
+
+using namespace sgk;
+
+namespace {
+
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    cudaError_t ensure(size_t n) {
+        if (n <= bytes) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        const cudaError_t e = cudaMalloc(&p, n);
+        if (e == cudaSuccess) bytes = n;
+        return e;
+    }
+    ~Buf() {
+        if (p) cudaFree(p);
+    }
+    template <class T>
+    T *as() const { return static_cast<T *>(p); }
+};
+
+using bf16 = __nv_bfloat16;
+
+// Backend of every configuration (its segment), and pairs per invocation.
+__global__ void k_cfg_backend(llama::DevProblem P, int8_t *lam) {
+    const int v = blockIdx.x, H = P.n_hw;
+    const int64_t c0 = P.cfg_off[v];
+    const int n = (int)(P.cfg_off[v + 1] - c0);
+    const int32_t *hw = P.hw_off + (int64_t)v * (H + 1);
+    for (int x = threadIdx.x; x < n; x += blockDim.x) {
+        int h = 0;
+        while (h + 1 < H && x >= hw[h + 1]) ++h;
+        lam[c0 + x] = (int8_t)h;
+    }
+}
+
+__global__ void k_pair_count(llama::DevProblem P, int64_t n_inv, const int32_t *dag, const int32_t *op_local,
+                             const int32_t *slack, int64_t *npairs) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i > n_inv) return;
+    int64_t k = 0;
+    if (i < n_inv && slack[i * P.n_hw] >= 0) {
+        const int32_t g = P.dag_op_off[dag[i]] + op_local[i];
+        k = P.cfg_off[g + 1] - P.cfg_off[g];
+    }
+    npairs[i] = k;  // entry n_inv is 0: the exclusive scan's last value is the total
+}
+
+// First layer of every pair of invocation i (one block per invocation):
+// h1 = ReLU(A[x] + B[i]) in BF16, and the pair's invocation, configuration and
+// op-local index.
+__global__ void k_pair_h1(llama::DevProblem P, const int32_t *dag, const int32_t *op_local, const int32_t *slack,
+                          const int64_t *pair_off, const float *__restrict__ A, const float *__restrict__ B,
+                          bf16 *__restrict__ h1, int32_t *pair_inv, int32_t *pair_g, int32_t *pair_x) {
+    const int64_t i = blockIdx.x;
+    if (slack[i * P.n_hw] < 0) return;
+    const int32_t g = P.dag_op_off[dag[i]] + op_local[i];
+    const int64_t c0 = P.cfg_off[g];
+    const int n = (int)(P.cfg_off[g + 1] - c0);
+    const int64_t p0 = pair_off[i];
+    const float4 *b4 = reinterpret_cast<const float4 *>(B + i * kHid);
+    // 32 threads per pair row, 8 columns each
+    for (int64_t w = threadIdx.x; w < (int64_t)n * 32; w += blockDim.x) {
+        const int x = (int)(w >> 5), q = (int)(w & 31);
+        const float4 *a4 = reinterpret_cast<const float4 *>(A + (c0 + x) * kHid);
+        const float4 u0 = a4[2 * q], u1 = a4[2 * q + 1], v0 = b4[2 * q], v1 = b4[2 * q + 1];
+        const __nv_bfloat162 r0 = __floats2bfloat162_rn(fmaxf(u0.x + v0.x, 0.f), fmaxf(u0.y + v0.y, 0.f));
+        const __nv_bfloat162 r1 = __floats2bfloat162_rn(fmaxf(u0.z + v0.z, 0.f), fmaxf(u0.w + v0.w, 0.f));
+        const __nv_bfloat162 r2 = __floats2bfloat162_rn(fmaxf(u1.x + v1.x, 0.f), fmaxf(u1.y + v1.y, 0.f));
+        const __nv_bfloat162 r3 = __floats2bfloat162_rn(fmaxf(u1.z + v1.z, 0.f), fmaxf(u1.w + v1.w, 0.f));
+        uint4 o;
+        o.x = *reinterpret_cast<const uint32_t *>(&r0);
+        o.y = *reinterpret_cast<const uint32_t *>(&r1);
+        o.z = *reinterpret_cast<const uint32_t *>(&r2);
+        o.w = *reinterpret_cast<const uint32_t *>(&r3);
+        *reinterpret_cast<uint4 *>(h1 + (p0 + x) * kHid + 8 * q) = o;
+        if (q == 0) {
+            pair_inv[p0 + x] = (int32_t)i;
+            pair_g[p0 + x] = (int32_t)(c0 + x);
+            pair_x[p0 + x] = x;
+        }
+    }
+}
+
+// The decision of every invocation from its best key.
+__global__ void k_sg_decode(llama::DevProblem P, int64_t n_inv, const int32_t *dag, const int32_t *op_local,
+                            const int32_t *slack, const int64_t *pair_off, const unsigned long long *best,
+                            const int32_t *lhat, const int64_t *chat, const int8_t *lam, llama_decision *out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_inv) return;
+    llama_decision d;
+    if (slack[i * P.n_hw] < 0) {
+        d.cfg = -1;
+        d.lat = 0;
+        d.cost = 0;
+        d.slack = 0;
+        d.flags = LLAMA_FLAG_INVALID;
+    } else {
+        const int32_t g = P.dag_op_off[dag[i]] + op_local[i];
+        const int32_t x = (int32_t)(best[i] & 0x1FFFull);
+        const int64_t p = pair_off[i] + x;
+        d.cfg = x;
+        d.lat = lhat[p];
+        d.cost = chat[p];
+        d.slack = slack[i * P.n_hw + lam[P.cfg_off[g] + x]];
+        d.flags = d.lat < d.slack ? LLAMA_FLAG_FEASIBLE : 0;
+    }
+    out[i] = d;
+}
+
+}  // namespace
+
+struct llama_sg {
+    llama_ctx *ctx = nullptr;
+    llama_mlp *net = nullptr;
+    int device = 0;
+    int64_t max_inv = 0, max_pairs = 0;
+    Buf A, B, h1, h2, pair_inv, pair_g, pair_x, lhat, chat, pair_off, npairs, best, slack, lam, scan_tmp, total_h;
+    int64_t last_pairs = 0;
+    float margin = 0.f;
+    std::string err;
+};
+
+namespace {
+
+int sg_fail(llama_sg *s, int code, const std::string &what, cudaError_t e = cudaSuccess) {
+    s->err = what + (e != cudaSuccess ? std::string(": ") + cudaGetErrorString(e) : "");
+    return code;
+}
+
+#define SG_CUDA(s, call)                                                                              \
+    do {                                                                                              \
+        const cudaError_t e__ = (call);                                                               \
+        if (e__ != cudaSuccess)                                                                       \
+            return sg_fail((s), e__ == cudaErrorMemoryAllocation ? LLAMA_ENOMEM : LLAMA_ECUDA, #call, e__); \
+    } while (0)
+
+#define SG_RC(s, call, what)                          \
+    do {                                              \
+        const int rc__ = (call);                      \
+        if (rc__ != LLAMA_OK) return sg_fail((s), rc__, what); \
+    } while (0)
+
+}  // namespace
+
+extern "C" int llama_sg_create(llama_sg **out, llama_ctx *ctx, llama_mlp *net, int64_t max_inv, int64_t max_pairs) {
+    if (!out) return LLAMA_EINVAL;
+    *out = nullptr;
+    if (!ctx || !net || max_inv < 1 || max_inv > (1 << 24) || max_pairs < 128 || max_pairs > (1ll << 30))
+        return LLAMA_EINVAL;
+    llama_sg *s = new llama_sg();
+    s->ctx = ctx;
+    s->net = net;
+    s->device = mlp_view(net).device;
+    s->max_inv = max_inv;
+    s->max_pairs = max_pairs;
+    *out = s;
+    return LLAMA_OK;
+}
+
+extern "C" void llama_sg_destroy(llama_sg *s) { delete s; }
+
+extern "C" int llama_sg_schedule(llama_sg *s, const void *cfg_x, const void *inv_x, int64_t n_inv,
+                                 const int32_t *dag, const int32_t *op_local, const int64_t *start_us,
+                                 int64_t now_us, llama_decision *out, void *stream) {
+    if (!s) return LLAMA_EINVAL;
+    if (n_inv < 0 || n_inv > s->max_inv) return sg_fail(s, LLAMA_EINVAL, "schedule: n_inv outside 0..max_inv");
+    if (n_inv == 0) return LLAMA_OK;
+    if (!cfg_x || !inv_x || !dag || !op_local || !start_us || !out)
+        return sg_fail(s, LLAMA_EINVAL, "schedule: null pointer");
+    llama::ContextView v;
+    SG_RC(s, llama::context_view(s->ctx, &v), "schedule: the scheduling context is not ready");
+    const llama_mlp_view nv = mlp_view(s->net);
+    if (nv.device != v.device) return sg_fail(s, LLAMA_EINVAL, "schedule: network and context on different GPUs");
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != v.device) cudaSetDevice(v.device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int H = v.n_hw;
+    int64_t n_cfg = 0;
+    SG_CUDA(s, cudaMemcpy(&n_cfg, v.P.cfg_off + v.n_ops, sizeof(int64_t), cudaMemcpyDeviceToHost));
+    SG_CUDA(s, s->A.ensure(4 * (size_t)n_cfg * kHid));
+    SG_CUDA(s, s->lam.ensure((size_t)n_cfg));
+    SG_CUDA(s, s->B.ensure(4 * (size_t)s->max_inv * kHid));
+    SG_CUDA(s, s->slack.ensure(4 * (size_t)s->max_inv * H));
+    SG_CUDA(s, s->npairs.ensure(8 * (size_t)(s->max_inv + 1)));
+    SG_CUDA(s, s->pair_off.ensure(8 * (size_t)(s->max_inv + 1)));
+    SG_CUDA(s, s->best.ensure(8 * (size_t)s->max_inv));
+    SG_CUDA(s, s->total_h.ensure(8));
+    // a1 + a2 on the profiled reference latencies
+    llama::k_critical_paths<<<std::max(1, (v.n_dags + 7) / 8), 256, 0, st>>>(v.P, v.topo, v.lvl_off, v.dag_lvl);
+    llama::k_slack<<<(unsigned)std::min<int64_t>((n_inv + 255) / 256, 65535), 256, 0, st>>>(
+        v.P, n_inv, dag, op_local, start_us, now_us, s->slack.as<int32_t>());
+    k_cfg_backend<<<v.n_ops, 256, 0, st>>>(v.P, s->lam.as<int8_t>());
+    k_pair_count<<<(unsigned)((n_inv + 256) / 256), 256, 0, st>>>(v.P, n_inv, dag, op_local, s->slack.as<int32_t>(),
+                                                                  s->npairs.as<int64_t>());
+    SG_CUDA(s, cudaGetLastError());
+    size_t tmp = 0;
+    SG_CUDA(s, cub::DeviceScan::ExclusiveSum(nullptr, tmp, s->npairs.as<int64_t>(), s->pair_off.as<int64_t>(),
+                                             (int)(n_inv + 1), st));
+    SG_CUDA(s, s->scan_tmp.ensure(tmp));
+    SG_CUDA(s, cub::DeviceScan::ExclusiveSum(s->scan_tmp.p, tmp, s->npairs.as<int64_t>(), s->pair_off.as<int64_t>(),
+                                             (int)(n_inv + 1), st));
+    int64_t total = 0;
+    SG_CUDA(s, cudaMemcpyAsync(&total, s->pair_off.as<int64_t>() + n_inv, 8, cudaMemcpyDeviceToHost, st));
+    SG_CUDA(s, cudaStreamSynchronize(st));
+    if (total > s->max_pairs) return sg_fail(s, LLAMA_EINVAL, "schedule: more (invocation, configuration) pairs than max_pairs");
+    s->last_pairs = total;
+    const int64_t cap = std::max<int64_t>(total, 1);
+    SG_CUDA(s, s->h1.ensure(2 * (size_t)cap * kHid));
+    SG_CUDA(s, s->h2.ensure(2 * (size_t)cap * kHid));
+    SG_CUDA(s, s->pair_inv.ensure(4 * (size_t)cap));
+    SG_CUDA(s, s->pair_g.ensure(4 * (size_t)cap));
+    SG_CUDA(s, s->pair_x.ensure(4 * (size_t)cap));
+    SG_CUDA(s, s->lhat.ensure(4 * (size_t)cap));
+    SG_CUDA(s, s->chat.ensure(8 * (size_t)cap));
+    // first layer, split: A = configurations . W1^T, B = contents . W1^T + b1
+    SG_RC(s, gemm(cfg_x, nv.w16[0], nullptr, nullptr, s->A.as<float>(), n_cfg, kHid, kIn, 0, st), "layer 1 (configurations)");
+    SG_RC(s, gemm(inv_x, nv.w16[0], nv.params + kOffB1, nullptr, s->B.as<float>(), n_inv, kHid, kIn, 0, st),
+          "layer 1 (contents)");
+    SG_CUDA(s, cudaMemsetAsync(s->best.p, 0xFF, 8 * (size_t)n_inv, st));
+    if (total > 0) {
+        k_pair_h1<<<(unsigned)n_inv, 256, 0, st>>>(v.P, dag, op_local, s->slack.as<int32_t>(), s->pair_off.as<int64_t>(),
+                                                   s->A.as<float>(), s->B.as<float>(), s->h1.as<bf16>(),
+                                                   s->pair_inv.as<int32_t>(), s->pair_g.as<int32_t>(),
+                                                   s->pair_x.as<int32_t>());
+        SG_CUDA(s, cudaGetLastError());
+        SG_RC(s, gemm(s->h1.p, nv.w16[1], nv.params + kOffB2, s->h2.p, nullptr, total, kHid, kHid, LLAMA_GEMM_RELU, st),
+              "layer 2");
+        SelectArgs a;
+        a.w4 = nv.params + kOffW4;
+        a.b4 = nv.params + kOffB4;
+        a.pair_inv = s->pair_inv.as<int32_t>();
+        a.pair_g = s->pair_g.as<int32_t>();
+        a.pair_x = s->pair_x.as<int32_t>();
+        a.cfg_lam = s->lam.as<int8_t>();
+        a.lat = v.P.lat;
+        a.cost = v.P.cost;
+        a.slack = s->slack.as<int32_t>();
+        a.n_hw = H;
+        a.margin = s->margin;
+        a.best = s->best.as<unsigned long long>();
+        a.lhat = s->lhat.as<int32_t>();
+        a.chat = s->chat.as<int64_t>();
+        SG_RC(s, gemm_select(s->h2.p, nv.w16[2], nv.params + kOffB3, total, a, st), "layer 3 and selection");
+    }
+    k_sg_decode<<<(unsigned)((n_inv + 255) / 256), 256, 0, st>>>(
+        v.P, n_inv, dag, op_local, s->slack.as<int32_t>(), s->pair_off.as<int64_t>(),
+        s->best.as<unsigned long long>(), s->lhat.as<int32_t>(), s->chat.as<int64_t>(), s->lam.as<int8_t>(), out);
+    SG_CUDA(s, cudaGetLastError());
+    if (prev >= 0 && prev != v.device) cudaSetDevice(prev);
+    return LLAMA_OK;
+}
+
+extern "C" int64_t llama_sg_last_pairs(llama_sg *s) { return s ? s->last_pairs : -1; }
+
+extern "C" int llama_sg_set_margin(llama_sg *s, float margin) {
+    if (!s) return LLAMA_EINVAL;
+    if (!(margin >= 0.f && margin <= 1.f)) return sg_fail(s, LLAMA_EINVAL, "set_margin: margin outside [0, 1]");
+    s->margin = margin;
+    return LLAMA_OK;
+}
+
+extern "C" int llama_sg_predictions(llama_sg *s, int32_t *lhat, int64_t *chat, int64_t *pair_off, int64_t n_inv,
+                                    void *stream) {
+    if (!s) return LLAMA_EINVAL;
+    if (n_inv < 0 || n_inv > s->max_inv) return sg_fail(s, LLAMA_EINVAL, "predictions: n_inv outside 0..max_inv");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t n = s->last_pairs;
+    if (lhat && n) SG_CUDA(s, cudaMemcpyAsync(lhat, s->lhat.p, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
+    if (chat && n) SG_CUDA(s, cudaMemcpyAsync(chat, s->chat.p, 8 * (size_t)n, cudaMemcpyDeviceToDevice, st));
+    if (pair_off) SG_CUDA(s, cudaMemcpyAsync(pair_off, s->pair_off.p, 8 * (size_t)(n_inv + 1), cudaMemcpyDeviceToDevice, st));
+    return LLAMA_OK;
+}
+
+extern "C" const char *llama_sg_last_error(llama_sg *s) { return s ? s->err.c_str() : "null surrogate"; }

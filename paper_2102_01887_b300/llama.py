@@ -34,7 +34,9 @@ EXPORTS = ("llama_create", "llama_destroy", "llama_set_dags", "llama_set_profile
            "llama_critical_path", "llama_slack", "llama_set_trace_events", "llama_last_launch_count",
            "llama_last_error", "llama_gemm_bf16", "llama_gemm_error",
            "llama_mlp_create", "llama_mlp_destroy", "llama_mlp_set_params", "llama_mlp_get_params",
-           "llama_mlp_forward", "llama_mlp_gradients", "llama_mlp_train_step", "llama_mlp_last_error")
+           "llama_mlp_forward", "llama_mlp_gradients", "llama_mlp_train_step", "llama_mlp_last_error",
+           "llama_sg_create", "llama_sg_destroy", "llama_sg_schedule", "llama_sg_last_pairs",
+           "llama_sg_predictions", "llama_sg_last_error", "llama_sg_set_margin")
 TRACE_EVENTS = 3
 TRACE_PHASES = ("bucket", "score")
 
@@ -92,6 +94,13 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "llama_mlp_gradients": ([vp, vp, vp, i64, ctypes.c_float, vp, vp, vp], ctypes.c_int),
             "llama_mlp_train_step": ([vp, vp, vp, i64, ctypes.c_float, ctypes.c_float, vp, vp], ctypes.c_int),
             "llama_mlp_last_error": ([vp], ctypes.c_char_p),
+            "llama_sg_create": ([ctypes.POINTER(vp), vp, vp, i64, i64], ctypes.c_int),
+            "llama_sg_destroy": ([vp], None),
+            "llama_sg_schedule": ([vp, vp, vp, i64, vp, vp, vp, i64, vp, vp], ctypes.c_int),
+            "llama_sg_last_pairs": ([vp], i64),
+            "llama_sg_predictions": ([vp, vp, vp, vp, i64, vp], ctypes.c_int),
+            "llama_sg_last_error": ([vp], ctypes.c_char_p),
+            "llama_sg_set_margin": ([vp, ctypes.c_float], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)

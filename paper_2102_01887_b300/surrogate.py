@@ -1,0 +1,144 @@
+"""The learned latency surrogate: features, training and scheduling, on the GPU.
+
+Argument marshalling around the C ABI of ``include/llama_surrogate.h``: the
+network's forward and backward passes, the optimizer and the scheduling with
+predicted latencies all run in the library's kernels.  Training data are the
+profiler's samples (``workloads.surrogate_training_set``).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import llama as L
+from . import workloads as W
+
+
+def _bf16(x: np.ndarray, col0: int, device="cuda"):
+    import torch
+    out = np.zeros((x.shape[0], L.MLP_INPUTS), np.float32)
+    out[:, col0:col0 + x.shape[1]] = x
+    return torch.from_numpy(out).to(device).to(torch.bfloat16)
+
+
+def config_inputs(p, cw, device="cuda"):
+    """Features of every configuration of p (row = global configuration), BF16 [n_cfg, 64]."""
+    sizes = np.diff(p.cfg_off)
+    gop = np.repeat(np.arange(p.n_ops), sizes)
+    cfg = np.arange(p.n_cfg) - np.repeat(p.cfg_off[:-1], sizes)
+    return _bf16(W.config_features(p, cw, gop, cfg), 0, device)
+
+
+def content_inputs(content, device="cuda"):
+    """Features of invocation content, BF16 [n, 64] in columns 32..47."""
+    return _bf16(W.content_features(content), W.N_CFG_FEATURES, device)
+
+
+def training_inputs(x: np.ndarray, t: np.ndarray, device="cuda"):
+    import torch
+    return _bf16(x, 0, device), torch.from_numpy(np.ascontiguousarray(t, np.float32)).to(device)
+
+
+def train(net, x, t, epochs: int, batch: int = 8192, lr: float = 1e-3, w_fan: float = 0.5, seed: int = 0,
+          stream=None) -> list:
+    """Adam over shuffled mini-batches of the device tensors x (BF16 [n, 64]) and
+    t (FP32 [n, 2]); the mean batch loss of every epoch."""
+    import torch
+    n = x.shape[0] // batch * batch
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    loss = torch.zeros(1, dtype=torch.float32, device=x.device)
+    acc = torch.zeros(1, dtype=torch.float32, device=x.device)
+    history = []
+    for _ in range(epochs):
+        perm = torch.randperm(x.shape[0], generator=g)[:n].to(x.device)
+        acc.zero_()
+        for b in range(n // batch):
+            idx = perm[b * batch:(b + 1) * batch]
+            net.train_step(x[idx].contiguous(), t[idx].contiguous(), w_fan, lr, loss, stream)
+            acc += loss
+        history.append(float(acc.item()) / (n // batch))
+    return history
+
+
+def held_out_rmse(net, x, t, batch: int = 8192) -> float:
+    """Root mean square error of the first output on held-out device tensors."""
+    import torch
+    y = torch.empty(x.shape[0], 2, dtype=torch.float32, device=x.device)
+    for i in range(0, x.shape[0], batch):
+        net.forward(x[i:i + batch].contiguous(), y[i:i + batch])
+    return float(torch.sqrt(torch.mean((y[:, 0] - t[:, 0]) ** 2)).item())
+
+
+def margin_from_rmse(rmse: float, noise_sigma: float) -> float:
+    """The model's own error from the held-out error and the profiler's known
+    measurement noise (independent errors add in variance), used as the
+    selection margin."""
+    return float(np.sqrt(max(rmse * rmse - noise_sigma * noise_sigma, 0.0)))
+
+
+def train_schedule(net, x, t, epochs: int = 12, lr: float = 2e-3, halve_every: int = 3, w_fan: float = 0.1,
+                   seed: int = 0) -> list:
+    """Adam with the learning rate halved every few epochs; the epochs' mean losses."""
+    hist = []
+    for e in range(epochs):
+        hist += train(net, x, t, epochs=1, lr=lr * 0.5 ** (e // halve_every), w_fan=w_fan, seed=seed + e)
+    return hist
+
+
+class SurrogateScheduler:
+    """Scheduling with the network's predictions on a context's problem."""
+
+    def __init__(self, sched, net, max_inv: int, max_pairs: int):
+        self.sched, self.net = sched, net
+        self.h = ctypes.c_void_p()
+        rc = L.load().llama_sg_create(ctypes.byref(self.h), sched.ctx, net.h, int(max_inv), int(max_pairs))
+        if rc != L.OK:
+            raise L.LlamaError(rc, "sg_create failed")
+
+    def _check(self, rc):
+        if rc != L.OK:
+            raise L.LlamaError(rc, L.load().llama_sg_last_error(self.h).decode())
+
+    def set_margin(self, margin: float) -> None:
+        self._check(L.load().llama_sg_set_margin(self.h, float(margin)))
+
+    def schedule_device(self, cfg_x, inv_x, dag, op_local, start, now_us: int, out, stream=None) -> None:
+        v = lambda t: ctypes.c_void_p(t.data_ptr())
+        self._check(L.load().llama_sg_schedule(self.h, v(cfg_x), v(inv_x), dag.shape[0], v(dag), v(op_local),
+                                               v(start), int(now_us), v(out), L._stream_ptr(stream)))
+
+    def schedule(self, cfg_x, inv, content):
+        """Decisions (numpy, DECISION_DTYPE) for invocations with their content."""
+        import torch
+        dev = cfg_x.device
+        dag = torch.from_numpy(inv.dag).to(dev)
+        opl = torch.from_numpy(inv.op_local).to(dev)
+        st = torch.from_numpy(inv.start_us).to(dev)
+        out = torch.zeros(inv.n * 24, dtype=torch.uint8, device=dev)
+        self.schedule_device(cfg_x, content_inputs(content, dev), dag, opl, st, inv.now_us, out)
+        torch.cuda.synchronize()
+        return out.cpu().numpy().view(L.DECISION_DTYPE)
+
+    def predictions(self, n_inv: int):
+        """Predicted latency and cost of every pair of the last call, and the pair offsets."""
+        import torch
+        n = int(L.load().llama_sg_last_pairs(self.h))
+        lh = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+        ch = torch.empty(max(n, 1), dtype=torch.int64, device="cuda")
+        po = torch.empty(n_inv + 1, dtype=torch.int64, device="cuda")
+        v = lambda t: ctypes.c_void_p(t.data_ptr())
+        self._check(L.load().llama_sg_predictions(self.h, v(lh), v(ch), v(po), n_inv, L._stream_ptr(None)))
+        torch.cuda.synchronize()
+        return lh[:n].cpu().numpy(), ch[:n].cpu().numpy(), po.cpu().numpy()
+
+    def close(self):
+        if self.h:
+            L.load().llama_sg_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

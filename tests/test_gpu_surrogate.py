@@ -1,0 +1,171 @@
+"""Scheduling with the learned latency surrogate.
+
+Parity: the predicted latencies of every (invocation, configuration) pair
+against the FP64 oracle of the network (a tolerance from BF16 activations:
+|log(predicted / oracle)| <= 0.05), and every decision bit-exact against the
+oracle's selection rule applied to the GPU's own integer predictions.
+Evaluation: after training on the profiler's samples, decisions judged on the
+ground-truth content model against the profile-table path.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp as M
+from oracle import surrogate as OS
+from paper_2102_01887_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L(cuda_device):
+    from paper_2102_01887_b300 import build, llama
+    build.build()
+    llama.load()
+    return llama
+
+
+@pytest.fixture(scope="module")
+def world():
+    p, inv = W.medium()
+    return p, inv, W.content_world(p)
+
+
+def pairs_of(p, inv, valid):
+    """Pair layout: invocation, global configuration, op-local index, offsets."""
+    gop = p.dag_op_off[np.where(valid, inv.dag, 0)] + np.where(valid, inv.op_local, 0)
+    sizes = np.where(valid, np.diff(p.cfg_off)[gop], 0)
+    off = np.zeros(inv.n + 1, np.int64)
+    off[1:] = np.cumsum(sizes)
+    pinv = np.repeat(np.arange(inv.n), sizes)
+    px = np.arange(off[-1]) - np.repeat(off[:-1], sizes)
+    pg = p.cfg_off[gop[pinv]] + px
+    return pinv, pg, px, off, gop
+
+
+def backend_of_cfg(p):
+    lam = np.zeros(p.n_cfg, np.int64)
+    hw = p.hw_off.reshape(p.n_ops, p.n_hw + 1)
+    for v in range(p.n_ops):
+        for h in range(p.n_hw):
+            lam[p.cfg_off[v] + hw[v, h]:p.cfg_off[v] + hw[v, h + 1]] = h
+    return lam
+
+
+def perturbed_params(seed):
+    rng = np.random.default_rng(seed)
+    q = M.init_params(seed)
+    for k in q:
+        q[k] = q[k] + (rng.normal(0, 0.05, q[k].shape) if k in ("W4", "b4") else rng.normal(0, 0.02, q[k].shape))
+    q["W4"][2:] = 0
+    q["b4"][2:] = 0
+    return q
+
+
+def test_predictions_and_decisions_match_oracle(L, world):
+    import torch
+
+    from paper_2102_01887_b300 import surrogate as S
+    p, inv, cw = world
+    sub = inv.subset(np.arange(0, inv.n, 640))
+    # two invalid invocations among them
+    sub.dag = sub.dag.copy()
+    sub.start_us = sub.start_us.copy()
+    sub.dag[3] = -1
+    sub.start_us[7] = sub.now_us + 5
+    content = W.invocation_content(5, sub.n)
+    params = perturbed_params(21)
+    flat = M.pack(params).astype(np.float32)
+    with L.Scheduler(p) as s, L.MLP(max_batch=1024) as net:
+        net.set_params(flat)
+        cfg_x = S.config_inputs(p, cw)
+        with S.SurrogateScheduler(s, net, max_inv=4096, max_pairs=1 << 20) as sg:
+            got = sg.schedule(cfg_x, sub, content)
+            lh, ch, po = sg.predictions(sub.n)
+        cfg_np = cfg_x.float().cpu().numpy()
+        inv_np = S.content_inputs(content).float().cpu().numpy()
+    slack = oracle.slacks(p, sub)
+    valid = slack[:, 0] >= 0
+    assert (got["flags"][~valid] == L.FLAG_INVALID).all() and (got["cfg"][~valid] == -1).all()
+    pinv, pg, px, off, gop = pairs_of(p, sub, valid)
+    assert np.array_equal(po, off)
+    # the network, in FP64 on the same BF16 inputs and weights (last layer in FP32)
+    q = M.unpack(flat.astype(np.float64))
+    for k in ("W1", "W2", "W3"):
+        q[k] = torch.from_numpy(q[k].astype(np.float32)).to(torch.bfloat16).double().numpy()
+    r = OS.forward_log_factor(q, cfg_np, inv_np, pinv, pg)
+    l_or = p.lat_us[pg] * np.exp(np.clip(r, -20, 20))
+    err = np.abs(np.log(lh / l_or))
+    assert err.max() <= 0.05, err.max()
+    # selection: the oracle's rule on the GPU's integer predictions
+    lam = backend_of_cfg(p)
+    spair = slack[pinv, lam[pg]]
+    x_or = OS.select(lh.astype(np.int64), ch, spair, off)
+    assert np.array_equal(got["cfg"][valid], x_or[valid])
+    k = off[:-1][valid] + x_or[valid]
+    assert np.array_equal(got["lat"][valid], lh[k])
+    assert np.array_equal(got["cost"][valid], ch[k])
+    assert np.array_equal(got["slack"][valid], spair[k])
+    assert np.array_equal(got["flags"][valid], (lh[k] < spair[k]).astype(np.int32))
+
+
+def evaluate(p, cw, sub, content, decisions_cfg, slack, lam, noise_seed):
+    """True latency / cost of each invocation's chosen configuration, with the
+    ground-truth content model and its lognormal noise."""
+    valid = slack[:, 0] >= 0
+    pinv, pg, px, off, gop = pairs_of(p, sub, valid)
+    ci = W.Content(content.n_obj[pinv], content.motion[pinv], content.in_res[pinv])
+    f = W.true_log_factor(p, cw, gop[pinv], px, ci) + W.latency_noise(noise_seed, pinv.shape[0])
+    lt = np.maximum(1, np.rint(p.lat_us[pg] * np.exp(f))).astype(np.int64)
+    ct = np.rint(p.cost_nd[pg] * np.exp(f)).astype(np.int64)
+    spair = slack[pinv, lam[pg]]
+    best = OS.select(lt, ct, spair, off)
+    res = {}
+    for name, x in list(decisions_cfg.items()) + [("truth", best)]:
+        k = off[:-1][valid] + x[valid]
+        viol = lt[k] >= spair[k]
+        res[name] = {"violations": float(viol.mean()), "cost": float(ct[k].sum()), "cfg": x[valid]}
+    return res
+
+
+@pytest.mark.slow
+def test_trained_surrogate_against_the_table_path(L, world):
+    # trained on 2M profiler samples, margin from the held-out error, judged on
+    # 16,384 invocations with the ground-truth content model
+    from paper_2102_01887_b300 import surrogate as S
+    p, inv, cw = world
+    x, t = W.surrogate_training_set(p, cw, 2_000_000)
+    xv, tv = W.surrogate_training_set(p, cw, 100_000, seed=303)
+    sub = inv.subset(np.arange(0, inv.n, 4))
+    slack = oracle.slacks(p, sub)
+    lam = backend_of_cfg(p)
+    with L.Scheduler(p) as s, L.MLP(max_batch=8192) as net:
+        net.set_params(M.pack(M.init_params(3)).astype(np.float32))
+        xd, td = S.training_inputs(x, t)
+        hist = S.train_schedule(net, xd, td)
+        rmse = S.held_out_rmse(net, *S.training_inputs(xv, tv))
+        margin = S.margin_from_rmse(rmse, W.LATENCY_NOISE_SIGMA)
+        cfg_x = S.config_inputs(p, cw)
+        out = {}
+        with S.SurrogateScheduler(s, net, max_inv=sub.n, max_pairs=sub.n * 1024) as sg:
+            sg.set_margin(margin)
+            table, _ = s.schedule(sub)
+            for kind in ("content", "reference"):
+                content = W.invocation_content(9, sub.n, reference=(kind == "reference"))
+                dec = sg.schedule(cfg_x, sub, content)
+                out[kind] = evaluate(p, cw, sub, content, {"table": table["cfg"], "surrogate": dec["cfg"]},
+                                     slack, lam, noise_seed=31)
+    print("training loss by epoch", hist, "held-out rmse", rmse, "margin", margin)
+    for kind, r in out.items():
+        agree = float((r["table"]["cfg"] == r["surrogate"]["cfg"]).mean())
+        print(kind, {k: (v["violations"], v["cost"]) for k, v in r.items()}, "agreement", agree)
+    ref, con = out["reference"], out["content"]
+    assert 0.0 < margin < 0.05
+    # on reference content (where the table is exact) the surrogate must not
+    # degrade the table's decisions: cost regret <= 1%, extra misses <= 0.5 points
+    assert ref["surrogate"]["cost"] <= 1.01 * ref["table"]["cost"]
+    assert ref["surrogate"]["violations"] <= ref["table"]["violations"] + 0.005
+    # on varied content it must gain: far fewer missed targets than the content-blind table
+    assert con["surrogate"]["violations"] < 0.5 * con["table"]["violations"]
+    assert hist[-1] < hist[0]
