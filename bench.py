@@ -67,7 +67,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="medium", choices=["tiny", "medium", "batched", "batched_large"])
     ap.add_argument("--mode", default="cost_first", choices=["cost_first", "alpha"])
-    ap.add_argument("--method", default="scan", choices=["scan", "staircase", "surrogate"],
+    ap.add_argument("--rates", default="1e5,3e5,1e6", help="serving: Poisson arrival rates (invocations/s)")
+    ap.add_argument("--seconds", type=float, default=1.5, help="serving: arrival window per rate")
+    ap.add_argument("--method", default="scan", choices=["scan", "staircase", "surrogate", "serve"],
                     help="selection method: score every configuration, the staircase tables, or the "
                          "learned latency surrogate (trained first, untimed)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample budget")
@@ -349,8 +351,83 @@ def run_surrogate(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serve(args):
+    """The serving loop under Poisson arrivals: decision latency (arrival to
+    result) and throughput, per offered rate."""
+    from paper_2102_01887_b300 import build as B
+    from paper_2102_01887_b300 import llama as L
+    B.build()
+    workload = args.workload if args.workload != "medium" else "batched"
+    p, inv = make_workload(workload, 0, args.n_dags, 262_144 if workload == "batched" else None)
+    rng = np.random.default_rng(5)
+    rows = []
+    with L.Scheduler(p, use_graph=False) as s, L.Server(s, slots=4, max_batch=8192) as srv:
+        # warm-up: one pass of every slot
+        warm = np.zeros(32768, L.REQUEST_DTYPE)
+        warm["dag"], warm["op_local"], warm["start_us"] = inv.dag[:32768], inv.op_local[:32768], inv.start_us[:32768]
+        warm["now_us"] = inv.now_us
+        for c in range(0, 32768, 4096):
+            srv.submit(warm[c:c + 4096])
+            srv.poll()
+        srv.drain()
+        with ClockSampler(0) as clocks:
+            for rate in (float(r) for r in args.rates.split(",")):
+                n = int(rate * args.seconds)
+                gaps = rng.exponential(1e9 / rate, n)
+                arrive = np.cumsum(gaps).astype(np.int64)  # ns after t0
+                idx = rng.integers(0, inv.n, n)
+                req = np.zeros(n, L.REQUEST_DTYPE)
+                req["id"] = np.arange(n)
+                req["dag"], req["op_local"], req["start_us"] = inv.dag[idx], inv.op_local[idx], inv.start_us[idx]
+                req["now_us"] = inv.now_us + arrive // 1000  # decided at the arrival time
+                st0 = srv.stats()
+                t0 = time.perf_counter_ns()
+                k, got = 0, []
+                while k < n:
+                    t = time.perf_counter_ns() - t0
+                    j = int(np.searchsorted(arrive, t, side="right"))
+                    if j > k:
+                        while srv.submit(req[k:j]) == L.EAGAIN:
+                            got.append(srv.poll())
+                        k = j
+                    got.append(srv.poll())
+                got.append(srv.drain())
+                t_end = time.perf_counter_ns() - t0
+                res = np.concatenate(got)
+                st = srv.stats()
+                order = np.argsort(res["id"])
+                res = res[order]
+                # latency from the arrival instant; the host's steady clock maps
+                # submission times, and arrival = submission minus its lag
+                lag = res["submit_ns"] - res["submit_ns"].min() - (arrive - arrive[0])
+                lat_us = (res["done_ns"] - res["submit_ns"] + np.maximum(lag, 0)) / 1e3
+                batches = st["batches"] - st0["batches"]
+                rows.append({"offered_per_s": rate, "completed": int(res.shape[0]),
+                             "throughput_per_s": res.shape[0] / (t_end / 1e9),
+                             "p50_us": float(np.percentile(lat_us, 50)), "p99_us": float(np.percentile(lat_us, 99)),
+                             "batches": int(batches), "mean_batch": res.shape[0] / max(batches, 1),
+                             "max_in_flight": st["max_in_flight"],
+                             "overlapped_batches": st["overlapped"] - st0["overlapped"],
+                             "invalid": int((res["decision"]["flags"] & L.FLAG_INVALID).sum())})
+    top = rows[-1]
+    line = {
+        "metric": METRIC, "value": top["throughput_per_s"], "unit": UNIT, "n_gpus": 1, "steps": len(rows),
+        "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32/int64", "data": "synthetic",
+        "config": {"workload": workload, "method": "serve", "dags": p.n_dags, "ops": p.n_ops,
+                   "slots": 4, "max_batch": 8192, "arrivals": "Poisson", "seconds_per_rate": args.seconds},
+        "decision_latency_us": {"p50": top["p50_us"], "p99": top["p99_us"]},
+        "serving": rows, "clocks": clocks.summary(),
+        "cpu_baseline": None, "e2e": None, "gpu_launches": None, "roofline": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.method == "serve":
+        run_serve(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return

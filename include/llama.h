@@ -143,6 +143,27 @@ int llama_schedule_async(llama_ctx *ctx, int64_t n_inv, const int32_t *dag,
                          const int32_t *op_local, const int64_t *start_us, int64_t now_us,
                          llama_decision *out, void *stream);
 
+/* Workspaces: the scratch of one scheduling call, separate from the
+ * context's own, so that calls of one context run concurrently on several
+ * streams (each call with its own workspace, no two calls on one workspace at
+ * once) while sharing the context's read-only tables.  A workspace holds
+ * calls of up to max_inv invocations for the context's current profiles; new
+ * profiles with more operations need a new workspace.  Errors: EINVAL,
+ * ENOTREADY, ENOMEM, ECUDA. */
+typedef struct llama_ws llama_ws;
+int llama_ws_create(llama_ctx *ctx, int64_t max_inv, llama_ws **out);
+void llama_ws_destroy(llama_ws *ws);
+
+/* llama_schedule_async with the workspace ws (direct launches, no graph). */
+int llama_schedule_ws_async(llama_ctx *ctx, llama_ws *ws, int64_t n_inv, const int32_t *dag,
+                            const int32_t *op_local, const int64_t *start_us, int64_t now_us,
+                            llama_decision *out, void *stream);
+
+/* Status of the workspace's last completed call (read once the stream has
+ * passed it; blocking): the number of invalid invocations, and whether a
+ * bounded device wait gave up. */
+int llama_ws_status(llama_ws *ws, int64_t *invalid, int32_t *timeout);
+
 /* Allocation-free variant of llama_schedule_async.  The paper has no
  * counterpart: this is a deployment convenience.  Some callers cannot let a
  * library call cudaMalloc or cudaFree while they schedule: a serving loop

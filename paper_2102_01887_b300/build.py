@@ -12,7 +12,7 @@ import sys
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 LIB = os.path.join(PKG, "libllama.so")
-SOURCES = [os.path.join(PKG, "csrc", f) for f in ("kernels.cu", "llama_host.cu", "llama_static.cu", "sg_gemm.cu", "sg_mlp.cu", "sg_score.cu")]
+SOURCES = [os.path.join(PKG, "csrc", f) for f in ("kernels.cu", "llama_host.cu", "llama_static.cu", "sg_gemm.cu", "sg_mlp.cu", "sg_score.cu", "server.cpp")]
 DEPS = SOURCES + glob.glob(os.path.join(PKG, "csrc", "*.cuh")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

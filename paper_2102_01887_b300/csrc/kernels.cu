@@ -1266,8 +1266,11 @@ cudaError_t enqueue_schedule(const ContextView &v, const BucketScratch &S, int64
     }
     // bucketing: one cooperative launch (its blocks meet at a grid barrier)
     const int n_cp = std::max(1, std::min((v.n_dags + 7) / 8, std::max(1, v.bucket_max_blocks / 4)));
+    // counting blocks: enough for the invocations, and for the bucket layout
+    // (one run of ops per block) enough that no block lays out more than 256 ops
     const int count_blocks = (int)std::max<int64_t>(
-        1, std::min<int64_t>((n_inv + 255) / 256, (int64_t)v.bucket_max_blocks - n_cp));
+        1, std::min<int64_t>(std::max<int64_t>((n_inv + 255) / 256, (v.n_ops + 255) / 256),
+                             (int64_t)v.bucket_max_blocks - n_cp));
     {
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3(n_cp + count_blocks);
@@ -1291,7 +1294,9 @@ cudaError_t enqueue_schedule(const ContextView &v, const BucketScratch &S, int64
     // the scoring kernel may launch before k_bucket completes (it waits on
     // griddepcontrol.wait before reading the scatter's output)
     cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(v.score_grid);
+    // a call has at most n_inv tiles: a small call leaves the rest of the GPU
+    // to calls running beside it
+    cfg.gridDim = dim3((unsigned)std::min<int64_t>(v.score_grid, std::max<int64_t>(1, n_inv)));
     cfg.blockDim = dim3(kScoreThreads);
     cfg.dynamicSmemBytes = v.score_smem;
     cfg.stream = s;

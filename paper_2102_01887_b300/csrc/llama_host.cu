@@ -54,6 +54,15 @@ int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 }  // namespace
 
+// Scratch of one scheduling call at a time: per-op counters and bucket
+// starts, per-invocation bucket entries, the tile list and the control and
+// status words.  Counters and control words are zero between calls.
+struct Workspace {
+    DevBuf cnt, ctrl, op_start, gop, slot, b_inv, b_slack, rbase, tiles;
+    int64_t cap_inv = 0, cap_tiles = 0;
+    int32_t cap_ops = 0;
+};
+
 struct llama_ctx {
     llama_opts opts{};
     int num_sms = 0;
@@ -87,9 +96,7 @@ struct llama_ctx {
     int64_t q[LLAMA_MAX_HW] = {0};
 
     // bucketing scratch
-    int64_t cap_inv = 0, cap_tiles = 0;
-    int32_t cap_ops = 0;
-    DevBuf cnt, ctrl, op_start, gop, slot, b_inv, b_slack, rbase, tiles;
+    Workspace ws;  // the context's own scratch (llama_schedule, llama_schedule_async)
     // scoring kernel geometry (set by llama_set_profiles)
     int32_t min_vpl = 16, ipt = 2, stages = 1, score_grid = 0, score_chunk = 0, bucket_max_blocks = 0, dlat_cap = 0;
     size_t score_smem = 0;
@@ -214,19 +221,19 @@ DevProblem make_problem(const llama_ctx *c) {
     return P;
 }
 
-BucketScratch make_scratch(const llama_ctx *c) {
+BucketScratch make_scratch(const Workspace &w) {
     BucketScratch S{};
-    S.cnt = c->cnt.as<int32_t>();
-    S.ctrl = c->ctrl.as<unsigned long long>();
+    S.cnt = w.cnt.as<int32_t>();
+    S.ctrl = w.ctrl.as<unsigned long long>();
     S.status = S.ctrl + kCtrlWords;
     S.blk = reinterpret_cast<int4 *>(S.ctrl + kCtrlWords + kStatusWords);
-    S.op_start = c->op_start.as<int32_t>();
-    S.gop = c->gop.as<int32_t>();
-    S.slot = c->slot.as<int32_t>();
-    S.b_inv = c->b_inv.as<int32_t>();
-    S.b_slack = c->b_slack.as<int32_t>();
-    S.rbase = c->rbase.as<int64_t>();
-    S.tiles = c->tiles.as<int4>();
+    S.op_start = w.op_start.as<int32_t>();
+    S.gop = w.gop.as<int32_t>();
+    S.slot = w.slot.as<int32_t>();
+    S.b_inv = w.b_inv.as<int32_t>();
+    S.b_slack = w.b_slack.as<int32_t>();
+    S.rbase = w.rbase.as<int64_t>();
+    S.tiles = w.tiles.as<int4>();
     return S;
 }
 
@@ -321,38 +328,44 @@ int check_ready(llama_ctx *c) {
     return LLAMA_OK;
 }
 
-int ensure_scratch(llama_ctx *c, int64_t n_inv) {
+// Grow workspace w for calls of up to n_inv invocations on the context's
+// current operations (buffers move: the caller drops what points at them).
+int ensure_ws(llama_ctx *c, Workspace &w, int64_t n_inv) {
     const int H = c->opts.n_hw;
-    if (c->cap_ops < c->n_ops + 1 || c->cap_inv < n_inv) c->drop_graph();  // buffers move
-    if (c->cap_ops < c->n_ops + 1) {
+    if (w.cap_ops < c->n_ops + 1) {
         const int32_t n = c->n_ops + 1;
-        LL_CUDA(c, c->cnt.alloc(sizeof(int32_t) * kCntStride * n));
-        LL_CUDA(c, c->ctrl.alloc(sizeof(unsigned long long) * (kCtrlWords + kStatusWords) +
-                                 sizeof(int4) * kMaxBucketBlocks));
+        LL_CUDA(c, w.cnt.alloc(sizeof(int32_t) * kCntStride * n));
+        LL_CUDA(c, w.ctrl.alloc(sizeof(unsigned long long) * (kCtrlWords + kStatusWords) +
+                                sizeof(int4) * kMaxBucketBlocks));
         // counters and control words start at zero; every call leaves them so
-        LL_CUDA(c, cudaMemset(c->cnt.p, 0, c->cnt.bytes));
-        LL_CUDA(c, cudaMemset(c->ctrl.p, 0, c->ctrl.bytes));
+        LL_CUDA(c, cudaMemset(w.cnt.p, 0, w.cnt.bytes));
+        LL_CUDA(c, cudaMemset(w.ctrl.p, 0, w.ctrl.bytes));
         LL_CUDA(c, cudaDeviceSynchronize());  // before any stream of the caller uses them
-        LL_CUDA(c, c->op_start.alloc(sizeof(int32_t) * n));
-        c->cap_ops = n;
-        c->cap_tiles = 0;
+        LL_CUDA(c, w.op_start.alloc(sizeof(int32_t) * n));
+        w.cap_ops = n;
+        w.cap_tiles = 0;
     }
-    if (c->cap_inv < n_inv) {
+    if (w.cap_inv < n_inv) {
         const int64_t n = std::max<int64_t>(n_inv, 1024);
-        LL_CUDA(c, c->gop.alloc(sizeof(int32_t) * n));
-        LL_CUDA(c, c->slot.alloc(sizeof(int32_t) * n));
-        LL_CUDA(c, c->b_inv.alloc(sizeof(int32_t) * n));
-        LL_CUDA(c, c->b_slack.alloc(sizeof(int32_t) * n * H));
-        LL_CUDA(c, c->rbase.alloc(sizeof(int64_t) * n));
-        c->cap_inv = n;
-        c->cap_tiles = 0;
+        LL_CUDA(c, w.gop.alloc(sizeof(int32_t) * n));
+        LL_CUDA(c, w.slot.alloc(sizeof(int32_t) * n));
+        LL_CUDA(c, w.b_inv.alloc(sizeof(int32_t) * n));
+        LL_CUDA(c, w.b_slack.alloc(sizeof(int32_t) * n * H));
+        LL_CUDA(c, w.rbase.alloc(sizeof(int64_t) * n));
+        w.cap_inv = n;
+        w.cap_tiles = 0;
     }
-    const int64_t nt = max_tiles(c->cap_inv, c->n_ops);
-    if (c->cap_tiles < nt) {
-        LL_CUDA(c, c->tiles.alloc(2 * sizeof(int4) * nt));
-        c->cap_tiles = nt;
+    const int64_t nt = max_tiles(w.cap_inv, c->n_ops);
+    if (w.cap_tiles < nt) {
+        LL_CUDA(c, w.tiles.alloc(2 * sizeof(int4) * nt));
+        w.cap_tiles = nt;
     }
     return LLAMA_OK;
+}
+
+int ensure_scratch(llama_ctx *c, int64_t n_inv) {
+    if (c->ws.cap_ops < c->n_ops + 1 || c->ws.cap_inv < n_inv) c->drop_graph();  // buffers move
+    return ensure_ws(c, c->ws, n_inv);
 }
 
 int ensure_stage(llama_ctx *c, int64_t n_inv) {
@@ -432,7 +445,7 @@ int capture_graph(llama_ctx *c, int64_t n_inv, const int32_t *dag, const int32_t
                   const int64_t *start, int64_t now, llama_decision *out) {
     c->drop_graph();
     const ContextView v = view_of(c);
-    const BucketScratch S = make_scratch(c);
+    const BucketScratch S = make_scratch(c->ws);
     LL_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
     const cudaError_t e = enqueue_schedule(v, S, n_inv, dag, op_local, start, now, out, c->cap_stream, nullptr);
     cudaGraph_t g = nullptr;
@@ -473,7 +486,7 @@ int launch_schedule(llama_ctx *c, int64_t n_inv, const int32_t *dag, const int32
                     const int64_t *start, int64_t now, llama_decision *out, cudaStream_t s) {
     if (!c->opts.use_graph || c->tracing) {
         const ContextView v = view_of(c);
-        const BucketScratch S = make_scratch(c);
+        const BucketScratch S = make_scratch(c->ws);
         LL_CUDA(c, enqueue_schedule(v, S, n_inv, dag, op_local, start, now, out, s,
                                     c->tracing ? c->trace : nullptr));
         c->last_launches = 2;
@@ -794,7 +807,7 @@ extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cf
     c->n_cfg = n_cfg;
     c->n_pad = n_pad;
     c->max_npad = max_npad;
-    c->cap_ops = 0;  // op count may have changed: re-size the per-op scratch
+    c->ws.cap_ops = 0;  // op count may have changed: re-size the per-op scratch
 
     const DevProblem P = make_problem(c);
     k_encode_pad<<<n_ops, 256, 0, c->stream>>>(P, c->lrb.as<uint16_t>(), c->rf.as<uint16_t>(),
@@ -910,6 +923,67 @@ extern "C" int llama_reserve(llama_ctx *c, int64_t max_inv) {
     return ensure_scratch(c, max_inv);
 }
 
+struct llama_ws {
+    Workspace w;
+    llama_ctx *ctx = nullptr;
+    int device = 0;
+};
+
+extern "C" int llama_ws_create(llama_ctx *c, int64_t max_inv, llama_ws **out) {
+    if (!c || !out) return LLAMA_EINVAL;
+    *out = nullptr;
+    if (max_inv < 1 || max_inv > LLAMA_MAX_INV) return c->fail(LLAMA_EINVAL, "ws_create: max_inv out of range");
+    int rc = check_ready(c);
+    if (rc) return rc;
+    DeviceGuard g(c->opts.device);
+    llama_ws *ws = new llama_ws();
+    ws->ctx = c;
+    ws->device = c->opts.device;
+    if ((rc = ensure_ws(c, ws->w, max_inv))) {
+        delete ws;
+        return rc;
+    }
+    *out = ws;
+    return LLAMA_OK;
+}
+
+extern "C" void llama_ws_destroy(llama_ws *ws) {
+    if (!ws) return;
+    DeviceGuard g(ws->device);
+    delete ws;
+}
+
+extern "C" int llama_schedule_ws_async(llama_ctx *c, llama_ws *ws, int64_t n_inv, const int32_t *dag,
+                                       const int32_t *op_local, const int64_t *start_us, int64_t now_us,
+                                       llama_decision *out, void *stream) {
+    if (!c || !ws) return LLAMA_EINVAL;
+    if (ws->ctx != c) return c->fail(LLAMA_EINVAL, "schedule_ws: workspace of another context");
+    int rc = check_inv_args(c, n_inv, dag, op_local, start_us, out);
+    if (rc) return rc;
+    if ((rc = check_ready(c))) return rc;
+    if (n_inv == 0) return LLAMA_OK;
+    if (n_inv > ws->w.cap_inv) return c->fail(LLAMA_EINVAL, "schedule_ws: more invocations than the workspace holds");
+    if (ws->w.cap_ops < c->n_ops + 1 || ws->w.cap_tiles < max_tiles(n_inv, c->n_ops))
+        return c->fail(LLAMA_EINVAL, "schedule_ws: workspace sized for fewer operations (profiles changed)");
+    DeviceGuard g(c->opts.device);
+    const ContextView v = view_of(c);
+    LL_CUDA(c, enqueue_schedule(v, make_scratch(ws->w), n_inv, dag, op_local, start_us, now_us, out,
+                                static_cast<cudaStream_t>(stream), nullptr));
+    return LLAMA_OK;
+}
+
+extern "C" int llama_ws_status(llama_ws *ws, int64_t *invalid, int32_t *timeout) {
+    if (!ws) return LLAMA_EINVAL;
+    DeviceGuard g(ws->device);
+    unsigned long long st[kStatusWords] = {0, 0};
+    if (cudaMemcpy(st, ws->w.ctrl.as<unsigned long long>() + kCtrlWords, sizeof(st), cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+        return LLAMA_ECUDA;
+    if (invalid) *invalid = (int64_t)st[0];
+    if (timeout) *timeout = st[1] ? 1 : 0;
+    return LLAMA_OK;
+}
+
 extern "C" int llama_schedule_async(llama_ctx *c, int64_t n_inv, const int32_t *dag,
                                     const int32_t *op_local, const int64_t *start_us, int64_t now_us,
                                     llama_decision *out, void *stream) {
@@ -945,7 +1019,7 @@ extern "C" int llama_schedule(llama_ctx *c, int64_t n_inv, const int32_t *dag, c
     if (!sd) LL_CUDA(c, cudaMemcpyAsync((void *)d_start, start_us, 8 * n_inv, cudaMemcpyHostToDevice, s));
     if ((rc = launch_schedule(c, n_inv, d_dag, d_opl, d_start, now_us, d_out, s))) return rc;
     if (!outd) LL_CUDA(c, cudaMemcpyAsync(out, d_out, sizeof(llama_decision) * n_inv, cudaMemcpyDeviceToHost, s));
-    LL_CUDA(c, cudaMemcpyAsync(c->h_ctrl, c->ctrl.as<unsigned long long>() + kCtrlWords,
+    LL_CUDA(c, cudaMemcpyAsync(c->h_ctrl, c->ws.ctrl.as<unsigned long long>() + kCtrlWords,
                                sizeof(unsigned long long) * kStatusWords, cudaMemcpyDeviceToHost, s));
     LL_CUDA(c, cudaStreamSynchronize(s));
     if (c->h_ctrl[1])

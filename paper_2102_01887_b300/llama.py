@@ -36,7 +36,10 @@ EXPORTS = ("llama_create", "llama_destroy", "llama_set_dags", "llama_set_profile
            "llama_mlp_create", "llama_mlp_destroy", "llama_mlp_set_params", "llama_mlp_get_params",
            "llama_mlp_forward", "llama_mlp_gradients", "llama_mlp_train_step", "llama_mlp_last_error",
            "llama_sg_create", "llama_sg_destroy", "llama_sg_schedule", "llama_sg_last_pairs",
-           "llama_sg_predictions", "llama_sg_last_error", "llama_sg_set_margin")
+           "llama_sg_predictions", "llama_sg_last_error", "llama_sg_set_margin",
+           "llama_ws_create", "llama_ws_destroy", "llama_schedule_ws_async", "llama_ws_status",
+           "llama_server_create", "llama_server_destroy", "llama_server_submit", "llama_server_poll",
+           "llama_server_drain", "llama_server_stats_get")
 TRACE_EVENTS = 3
 TRACE_PHASES = ("bucket", "score")
 
@@ -101,6 +104,16 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "llama_sg_predictions": ([vp, vp, vp, vp, i64, vp], ctypes.c_int),
             "llama_sg_last_error": ([vp], ctypes.c_char_p),
             "llama_sg_set_margin": ([vp, ctypes.c_float], ctypes.c_int),
+            "llama_ws_create": ([vp, i64, ctypes.POINTER(vp)], ctypes.c_int),
+            "llama_ws_destroy": ([vp], None),
+            "llama_schedule_ws_async": ([vp, vp, i64, vp, vp, vp, i64, vp, vp], ctypes.c_int),
+            "llama_ws_status": ([vp, vp, vp], ctypes.c_int),
+            "llama_server_create": ([vp, vp, ctypes.POINTER(vp)], ctypes.c_int),
+            "llama_server_destroy": ([vp], None),
+            "llama_server_submit": ([vp, vp, i64], ctypes.c_int),
+            "llama_server_poll": ([vp, vp, i64, vp], ctypes.c_int),
+            "llama_server_drain": ([vp, vp, i64, vp, i64], ctypes.c_int),
+            "llama_server_stats_get": ([vp, vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -248,6 +261,78 @@ class MLP:
     def close(self) -> None:
         if self.h:
             load().llama_mlp_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+EAGAIN = -6
+REQUEST_DTYPE = np.dtype([("id", "<i8"), ("dag", "<i4"), ("op_local", "<i4"), ("start_us", "<i8"),
+                          ("now_us", "<i8")])
+RESULT_DTYPE = np.dtype([("id", "<i8"), ("decision", DECISION_DTYPE), ("submit_ns", "<i8"), ("done_ns", "<i8")])
+assert REQUEST_DTYPE.itemsize == 32 and RESULT_DTYPE.itemsize == 48
+
+
+class llama_server_opts(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("memory_budget", ctypes.c_int64),
+                ("max_queue", ctypes.c_int64)]
+
+
+class llama_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("refused", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("slots", ctypes.c_int32), ("max_in_flight", ctypes.c_int32),
+                ("overlapped", ctypes.c_int64), ("queue_peak", ctypes.c_int64),
+                ("device_busy_ms", ctypes.c_double), ("device_span_ms", ctypes.c_double)]
+
+
+class Server:
+    """Continuous-batching serving loop over a context (see include/llama_server.h)."""
+
+    def __init__(self, sched, slots: int = 4, max_batch: int = 4096, memory_budget: int = 0, max_queue: int = 0):
+        self.h = ctypes.c_void_p()
+        opts = llama_server_opts(slots, max_batch, memory_budget, max_queue)
+        rc = load().llama_server_create(sched.ctx, ctypes.byref(opts), ctypes.byref(self.h))
+        if rc != OK:
+            raise LlamaError(rc, "server_create failed")
+        self.buf = np.zeros(1 << 16, RESULT_DTYPE)
+
+    def submit(self, req: np.ndarray) -> int:
+        req = np.ascontiguousarray(req, REQUEST_DTYPE)
+        return load().llama_server_submit(self.h, req.ctypes.data, req.shape[0])
+
+    def poll(self) -> np.ndarray:
+        n = ctypes.c_int64()
+        rc = load().llama_server_poll(self.h, self.buf.ctypes.data, self.buf.shape[0], ctypes.byref(n))
+        if rc != OK:
+            raise LlamaError(rc, "server_poll failed")
+        return self.buf[:n.value].copy()
+
+    def drain(self, timeout_ms: int = 60000) -> np.ndarray:
+        out = []
+        while True:
+            n = ctypes.c_int64()
+            rc = load().llama_server_drain(self.h, self.buf.ctypes.data, self.buf.shape[0], ctypes.byref(n),
+                                           int(timeout_ms))
+            if rc != OK:
+                raise LlamaError(rc, "server_drain failed")
+            out.append(self.buf[:n.value].copy())
+            if n.value < self.buf.shape[0]:
+                return np.concatenate(out)
+
+    def stats(self) -> dict:
+        st = llama_server_stats()
+        rc = load().llama_server_stats_get(self.h, ctypes.byref(st))
+        if rc != OK:
+            raise LlamaError(rc, "server_stats failed")
+        return {f: getattr(st, f) for f, _ in llama_server_stats._fields_}
+
+    def close(self):
+        if self.h:
+            load().llama_server_destroy(self.h)
             self.h = ctypes.c_void_p()
 
     def __enter__(self):
