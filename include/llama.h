@@ -116,6 +116,38 @@ int llama_set_profiles(llama_ctx *ctx, int32_t n_ops, const int64_t *cfg_off,
  * default all zero. */
 int llama_set_queue(llama_ctx *ctx, const int64_t *q_us);
 
+/* Feedback (Section 3.3: the Manager records every executed invocation's
+ * latency and cost and updates the profiles by exponential smoothing): n
+ * observations (global operation op[i], op-local configuration cfg[i],
+ * measured lat_us[i] >= 1 and cost_nd[i] >= 0) update the tables in place,
+ *   L <- ((beta_den - beta_num) L + beta_num L_obs + beta_den / 2) / beta_den
+ * in exact integers (the same for the cost), a configuration's observations
+ * applied in their order; 0 <= beta_num <= beta_den <= 65535.  The encodings
+ * of the touched operations are rebuilt on the device, on `stream`, so the
+ * calls enqueued after it see the new tables (the critical paths follow the
+ * new reference latencies).  Invalid observations are skipped and counted into
+ * *rejected (device int64, nullable).  Device pointers.  Errors: EINVAL,
+ * ENOTREADY, ENOMEM, ECUDA. */
+int llama_feedback(llama_ctx *ctx, int64_t n, const int32_t *op, const int32_t *cfg, const int32_t *lat_us,
+                   const int64_t *cost_nd, int32_t beta_num, int32_t beta_den, int64_t *rejected,
+                   void *stream);
+
+/* The current latency and cost tables (host arrays of n_cfg; blocking). */
+int llama_get_profiles(llama_ctx *ctx, int32_t *lat_us, int64_t *cost_nd);
+
+/* Queueing time of every backend from the invocations queued on it (Eq. 2,
+ * Section 4.3): Q[lambda] = floor(sum over queued i with lambda(x_i) = lambda
+ * of L(x_i) R(x_i) / R_total(lambda)) -- the exact integer sum, floored once --
+ * from the n decided invocations (dag[i], op_local[i], dec[i]: decisions of
+ * earlier scheduling calls, e.g. the speculative and commit queues; invalid
+ * ones are skipped) and the profiles' resources.  Written to q_out (device,
+ * n_hw int64, nullable); with apply != 0 it also becomes the context's
+ * queueing time for later calls, on the device (no host round trip).  Device
+ * pointers, enqueued on `stream`.  Errors: EINVAL (arguments, or profiles set
+ * without res / res_total), ENOTREADY. */
+int llama_queue_time(llama_ctx *ctx, int64_t n, const int32_t *dag, const int32_t *op_local,
+                     const llama_decision *dec, int64_t *q_out, int32_t apply, void *stream);
+
 /* Schedule n_inv pending invocations at time now_us (blocking).
  *   dag[n_inv], op_local[n_inv]  the invocation's DAG and op-local operation;
  *   start_us[n_inv]              start time of its pipeline instance, 0..now_us;

@@ -171,3 +171,41 @@ def schedule(p, inv, mode: int = MODE_COST_FIRST, alpha: tuple[int, int] = (1, 1
     if rc not in (OK, EINVAL):
         raise ValueError(f"oracle schedule failed: {rc}")
     return out, rc
+
+
+def queue_time(p, inv, decisions) -> np.ndarray:
+    """Eq. 2 (Section 4.3): per backend, the floor of the sum over the decided
+    invocations on it of L(x_i) R(x_i) / R_total(backend), summed exactly in
+    integers before one floor division.  Invalid decisions are skipped."""
+    H = p.n_hw
+    hw = p.hw_off.reshape(p.n_ops, H + 1)
+    total = [0] * H
+    for i in range(inv.n):
+        d = decisions[i]
+        if d["cfg"] < 0 or d["flags"] & FLAG_INVALID:
+            continue
+        v = int(p.dag_op_off[inv.dag[i]]) + int(inv.op_local[i])
+        x = int(d["cfg"])
+        lam = max(h for h in range(H) if x >= hw[v, h])  # the segment holding x
+        total[lam] += int(d["lat"]) * int(p.res[int(p.cfg_off[v]) + x])
+    return np.asarray([min(total[h] // int(p.res_total[h]), 2**31 - 1) for h in range(H)], np.int64)
+
+
+def feedback(p, op, cfg, lat_obs, cost_obs, beta=(1, 4)):
+    """Exponential smoothing of the profile tables by measured invocations
+    (Section 3.3), in place and in the given order, in exact integers:
+    L <- ((d - b) L + b L_obs + d // 2) // d with beta = b / d, the same for the
+    cost; observations outside the tables are skipped (their count is returned)."""
+    b, d = int(beta[0]), int(beta[1])
+    rejected = 0
+    for v, x, lo, co in zip(op, cfg, lat_obs, cost_obs):
+        v, x, lo, co = int(v), int(x), int(lo), int(co)
+        if not (0 <= v < p.n_ops and 0 <= x < int(p.cfg_off[v + 1] - p.cfg_off[v])) or lo < 1 or co < 0 \
+                or lo >= 2**31 - 1 or co >= 2**46:
+            rejected += 1
+            continue
+        g = int(p.cfg_off[v]) + x
+        L = ((d - b) * int(p.lat_us[g]) + b * lo + d // 2) // d
+        p.lat_us[g] = min(max(L, 1), 2**31 - 2)
+        p.cost_nd[g] = ((d - b) * int(p.cost_nd[g]) + b * co + d // 2) // d
+    return rejected

@@ -1133,10 +1133,11 @@ __global__ void __launch_bounds__(256) k_stair(DevProblem P, int64_t n_inv, cons
                 }
             }
             const uint16_t *sg = P.stair + P.stair_off[g];
+            const int64_t stride = P.cfg_off[g + 1] - P.cfg_off[g] + 1;
             uint32_t key = 0xFFFFu;
 #pragma unroll
             for (int h = 0; h < LLAMA_MAX_HW; ++h)
-                if (h < H) key = min(key, (uint32_t)__ldg(sg + (int64_t)h * (dn + 1) + lo[h]));
+                if (h < H) key = min(key, (uint32_t)__ldg(sg + (int64_t)h * stride + lo[h]));
             const int64_t cb = P.cfg_off[g];
             int4 dd;
             if (P.mode == LLAMA_MODE_ALPHA) dd = P.dec[2 * cb + key];
@@ -1199,6 +1200,7 @@ __global__ void k_encode_stair(DevProblem P, uint16_t *stair) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int32_t part[32];
     const int v = blockIdx.x, H = P.n_hw, T = blockDim.x, tid = threadIdx.x;
+    if (P.encode_only && !P.encode_only[v]) return;
     const bool alpha = P.mode == LLAMA_MODE_ALPHA;
     const int32_t dn = P.dlat_n[v], m = dn + 1;
     int32_t *pre = reinterpret_cast<int32_t *>(smem_raw);
@@ -1207,6 +1209,7 @@ __global__ void k_encode_stair(DevProblem P, uint16_t *stair) {
     const int32_t *hw = P.hw_off + (int64_t)v * (H + 1);
     const int32_t *sp = P.seg_pad + (int64_t)v * (H + 1);
     uint16_t *out = stair + P.stair_off[v];
+    const int64_t stride = P.cfg_off[v + 1] - P.cfg_off[v] + 1;  // n_cfg(v) + 1 >= m
     for (int h = 0; h < H; ++h) {
         for (int k = tid; k < m; k += T) {
             pre[k] = 0xFFFF;
@@ -1225,7 +1228,7 @@ __global__ void k_encode_stair(DevProblem P, uint16_t *stair) {
         block_min_scan(pre, m, false, part);
         if (alpha) block_min_scan(suf, m, true, part);
         for (int k = tid; k < m; k += T)
-            out[(int64_t)h * m + k] = (uint16_t)(alpha ? min(pre[k], suf[k]) : pre[k]);
+            out[(int64_t)h * stride + k] = (uint16_t)(alpha ? min(pre[k], suf[k]) : pre[k]);
         __syncthreads();
     }
 }
@@ -1327,6 +1330,7 @@ cudaError_t enqueue_schedule(const ContextView &v, const BucketScratch &S, int64
 __global__ void k_encode_pad(DevProblem P, uint16_t *lrb, uint16_t *rf, uint16_t *df, int32_t *fast) {
     __shared__ int64_t red[32];
     const int v = blockIdx.x, H = P.n_hw;
+    if (P.encode_only && !P.encode_only[v]) return;
     const int64_t c0 = P.cfg_off[v], p0 = P.pad_off[v];
     const int32_t *hw = P.hw_off + (int64_t)v * (H + 1);
     const int32_t *sp = P.seg_pad + (int64_t)v * (H + 1);
@@ -1372,6 +1376,7 @@ __global__ void k_encode_rank(DevProblem P, int32_t sort_cap, uint16_t *rf, uint
     uint64_t *key = reinterpret_cast<uint64_t *>(smem_raw);
     uint32_t *tag = reinterpret_cast<uint32_t *>(smem_raw + 8 * (size_t)sort_cap);
     const int v = blockIdx.x, H = P.n_hw, T = blockDim.x;
+    if (P.encode_only && !P.encode_only[v]) return;
     const bool alpha = P.mode == LLAMA_MODE_ALPHA;
     const int64_t c0 = P.cfg_off[v], p0 = P.pad_off[v];
     const int n = (int)(P.cfg_off[v + 1] - c0);
@@ -1443,6 +1448,7 @@ __global__ void k_encode_lat(DevProblem P, uint16_t *lrb, int32_t *dlat, int32_t
     uint64_t *key = reinterpret_cast<uint64_t *>(smem_raw);
     __shared__ int32_t warp_tot[32];
     const int v = blockIdx.x, H = P.n_hw, T = blockDim.x, tid = threadIdx.x;
+    if (P.encode_only && !P.encode_only[v]) return;
     const int lane = tid & 31, wid = tid >> 5;
     const int64_t c0 = P.cfg_off[v], p0 = P.pad_off[v];
     const int n = (int)(P.cfg_off[v + 1] - c0);
@@ -1512,6 +1518,7 @@ __global__ void k_encode_piv(DevProblem P, int32_t *dpiv) {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= 32 * (int64_t)P.n_ops) return;
     const int32_t v = (int32_t)(k >> 5), l = (int32_t)(k & 31), dn = P.dlat_n[v];
+    if (P.encode_only && !P.encode_only[v]) return;
     dpiv[k] = dn > 32 ? P.dlat[P.pad_off[v] + (((l + 1) * dn) >> 5) - 1] : INT32_MAX;
 }
 
@@ -1519,6 +1526,7 @@ __global__ void k_encode_piv(DevProblem P, int32_t *dpiv) {
 // fastest one.
 __global__ void k_encode_dec(DevProblem P, int4 *dec, int4 *dfast) {
     const int v = blockIdx.x, H = P.n_hw;
+    if (P.encode_only && !P.encode_only[v]) return;
     const int64_t c0 = P.cfg_off[v];
     const int n = (int)(P.cfg_off[v + 1] - c0);
     const bool alpha = P.mode == LLAMA_MODE_ALPHA;
@@ -1533,6 +1541,94 @@ __global__ void k_encode_dec(DevProblem P, int4 *dec, int4 *dfast) {
     };
     for (int r = threadIdx.x; r < cnt; r += blockDim.x) dec[off + r] = entry(P.inv[2 * c0 + r]);
     if (threadIdx.x == 0) dfast[v] = entry(P.fast[v]);
+}
+
+// Eq. 2 over the decided invocations (valid ones): their latency times their
+// requested resources, summed per backend.
+__global__ void k_queue_sum(DevProblem P, int64_t n, const int32_t *dag, const int32_t *op_local,
+                            const llama_decision *dec, unsigned long long *sums) {
+    const int H = P.n_hw;
+    unsigned long long loc[LLAMA_MAX_HW];
+#pragma unroll
+    for (int h = 0; h < LLAMA_MAX_HW; ++h) loc[h] = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const llama_decision d = dec[i];
+        if (d.cfg < 0 || (d.flags & LLAMA_FLAG_INVALID)) continue;
+        const int32_t dg = dag[i], o = op_local[i];
+        if (dg < 0 || dg >= P.n_dags || o < 0 || o >= P.dag_op_off[dg + 1] - P.dag_op_off[dg]) continue;
+        const int32_t v = P.dag_op_off[dg] + o;
+        const int64_t g = P.cfg_off[v] + d.cfg;
+        if (d.cfg >= P.cfg_off[v + 1] - P.cfg_off[v]) continue;
+        const int lam = backend_of(P.hw_off + (int64_t)v * (H + 1), H, d.cfg);
+        const unsigned long long w = (unsigned long long)(uint32_t)d.lat * (unsigned long long)(uint32_t)P.res[g];
+#pragma unroll
+        for (int h = 0; h < LLAMA_MAX_HW; ++h)
+            if (h == lam) loc[h] += w;
+    }
+#pragma unroll
+    for (int h = 0; h < LLAMA_MAX_HW; ++h) {
+        unsigned long long v = loc[h];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0 && h < H && v) atomicAdd(sums + h, v);
+    }
+}
+
+__global__ void k_queue_finish(DevProblem P, const unsigned long long *sums, int64_t *q_out, int64_t *q_ctx) {
+    const int h = threadIdx.x;
+    if (h >= P.n_hw) return;
+    const unsigned long long q = sums[h] / (unsigned long long)P.res_total[h];
+    const int64_t v = q > (unsigned long long)INT32_MAX ? (int64_t)INT32_MAX : (int64_t)q;
+    if (q_out) q_out[h] = v;
+    if (q_ctx) q_ctx[h] = v;
+}
+
+// Feedback, step 1: validate the observations and key them by global
+// configuration (invalid ones get key INT32_MAX and are counted).
+__global__ void k_feedback_keys(DevProblem P, int64_t n, const int32_t *obs_op, const int32_t *obs_cfg,
+                                const int32_t *obs_lat, const int64_t *obs_cost, int32_t *keys, int32_t *idx,
+                                unsigned long long *rejected) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = obs_op[i], x = obs_cfg[i];
+        bool ok = v >= 0 && v < P.n_ops;
+        if (ok) ok = x >= 0 && x < P.cfg_off[v + 1] - P.cfg_off[v];
+        ok = ok && obs_lat[i] >= 1 && obs_lat[i] < INT32_MAX && obs_cost[i] >= 0 && obs_cost[i] < (1ll << 46);
+        keys[i] = ok ? (int32_t)(P.cfg_off[v] + x) : INT32_MAX;
+        idx[i] = (int32_t)i;
+        if (!ok) atomicAdd(rejected, 1ull);
+    }
+}
+
+// Feedback, step 2: the first observation of every configuration (in key
+// order, stable) applies all of that configuration's observations in their
+// order: L <- ((b_den - b_num) L + b_num L_obs + b_den / 2) / b_den, the same
+// for the cost, in exact integers.
+__global__ void k_feedback_apply(DevProblem P, int64_t n, const int32_t *sorted_g, const int32_t *sorted_obs,
+                                 const int32_t *obs_op, const int32_t *obs_lat, const int64_t *obs_cost,
+                                 int32_t beta_num, int32_t beta_den, int32_t *lat, int64_t *cost,
+                                 uint8_t *touched) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t g = sorted_g[k];
+        if (g == INT32_MAX || (k > 0 && sorted_g[k - 1] == g)) continue;
+        const int64_t w = beta_den - beta_num;
+        int64_t L = lat[g], C = cost[g];
+        int64_t j = k;
+        for (; j < n && sorted_g[j] == g; ++j) {
+            const int32_t o = sorted_obs[j];
+            L = (w * L + (int64_t)beta_num * obs_lat[o] + beta_den / 2) / beta_den;
+            C = (w * C + (int64_t)beta_num * obs_cost[o] + beta_den / 2) / beta_den;
+        }
+        lat[g] = (int32_t)min(max(L, (int64_t)1), (int64_t)INT32_MAX - 1);
+        cost[g] = C;
+        touched[obs_op[sorted_obs[k]]] = 1;
+    }
+}
+
+// Feedback, step 4: the distinct-latency count of every re-encoded op in the
+// bucket-order table.
+__global__ void k_refresh_order(DevProblem P, const int32_t *ord_pos, int4 *ord_info) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= P.n_ops || !P.encode_only[v]) return;
+    ord_info[ord_pos[v]].w = P.dlat_n[v];
 }
 
 }  // namespace llama

@@ -1,5 +1,7 @@
 // llama_host.cu -- C ABI of the scheduling step (include/llama.h): argument
 // validation, DAG levelling, padded table layout, device memory, launches.
+#include <cub/cub.cuh>
+
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -83,7 +85,13 @@ struct llama_ctx {
     int32_t method = LLAMA_METHOD_SCAN;
     bool stair_ready = false;
     DevBuf stair, stair_off;
-    std::vector<int32_t> h_dn;  // distinct latencies per op
+    std::vector<int32_t> h_dn;     // distinct latencies per op (as set; feedback changes them on the device)
+    std::vector<int32_t> h_ncfg;   // configurations per op
+    int32_t max_n = 0, sort_cap = 1;
+    size_t sort_smem = 0, lat_smem = 0;
+    DevBuf ord_pos;                // bucket-order position of every op
+    // feedback scratch
+    DevBuf fb_keys, fb_idx, fb_keys2, fb_idx2, fb_touched, fb_rejected, fb_tmp;
 
     // profiles
     bool prof_set = false;
@@ -93,7 +101,8 @@ struct llama_ctx {
     DevBuf pad_off, seg_pad, lrb, dlat, dlat_n, dpiv, rf, df, inv, fast, op_order, ref_gidx;
     int64_t mean_npad = 0;
     DevBuf ref, cp, cp_magic;
-    int64_t q[LLAMA_MAX_HW] = {0};
+    DevBuf q_dev;  // [LLAMA_MAX_HW] queueing time per backend, read by the kernels
+    DevBuf q_sums; // scratch of Eq. 2
 
     // bucketing scratch
     Workspace ws;  // the context's own scratch (llama_schedule, llama_schedule_async)
@@ -190,6 +199,7 @@ DevProblem make_problem(const llama_ctx *c) {
     P.dfast = c->dfast.as<int4>();
     P.stair = c->stair.as<uint16_t>();
     P.stair_off = c->stair_off.as<int64_t>();
+    P.encode_only = nullptr;
     P.dag_pack = c->dag_pack.as<int32_t>();
     P.dag_pack_off = c->dag_pack_off.as<int64_t>();
     // arrays whose first touch starts a dependent chain: DAG structure, per-op
@@ -215,7 +225,7 @@ DevProblem make_problem(const llama_ctx *c) {
     P.ref = c->ref.as<int64_t>();
     P.cp = c->cp.as<int64_t>();
     P.cp_magic = c->cp_magic.as<uint64_t>();
-    for (int h = 0; h < LLAMA_MAX_HW; ++h) P.q[h] = c->q[h];
+    P.q = c->q_dev.as<int64_t>();
     P.alpha_num = c->opts.alpha_num;
     P.alpha_den = c->opts.alpha_den;
     return P;
@@ -296,14 +306,31 @@ int build_dag_pack(llama_ctx *c) {
     return LLAMA_OK;
 }
 
-// Staircase tables of the current profiles: H * (dn + 1) 16-bit keys per op.
+// The encodings of the profile tables (every op, or those P.encode_only flags):
+// pads and fastest configuration, latency ranks and distinct latencies, probe
+// lines, objective ranks, decode tables.  Enqueued on s.
+cudaError_t encode_tables(llama_ctx *c, const DevProblem &P, cudaStream_t s) {
+    const bool alpha = c->opts.mode == LLAMA_MODE_ALPHA;
+    const int32_t n_ops = c->n_ops;
+    k_encode_pad<<<n_ops, 256, 0, s>>>(P, c->lrb.as<uint16_t>(), c->rf.as<uint16_t>(),
+                                       alpha ? c->df.as<uint16_t>() : nullptr, c->fast.as<int32_t>());
+    k_encode_lat<<<n_ops, 1024, c->lat_smem, s>>>(P, c->lrb.as<uint16_t>(), c->dlat.as<int32_t>(),
+                                                  c->dlat_n.as<int32_t>());
+    k_encode_piv<<<(unsigned)((32 * (int64_t)n_ops + 255) / 256), 256, 0, s>>>(P, c->dpiv.as<int32_t>());
+    k_encode_rank<<<n_ops, 1024, c->sort_smem, s>>>(P, c->sort_cap, c->rf.as<uint16_t>(),
+                                                    alpha ? c->df.as<uint16_t>() : nullptr, c->inv.as<uint16_t>());
+    k_encode_dec<<<n_ops, 256, 0, s>>>(P, c->dec.as<int4>(), c->dfast.as<int4>());
+    return cudaGetLastError();
+}
+
+// Staircase tables of the current profiles: H * (n_cfg + 1) 16-bit keys per op.
 int build_stair(llama_ctx *c) {
     const int32_t n_ops = c->n_ops, H = c->opts.n_hw;
     std::vector<int64_t> off(n_ops + 1, 0);
     int32_t max_dn = 1;
     for (int32_t v = 0; v < n_ops; ++v) {
-        off[v + 1] = off[v] + (int64_t)H * (c->h_dn[v] + 1);
-        max_dn = std::max(max_dn, c->h_dn[v]);
+        off[v + 1] = off[v] + (int64_t)H * (c->h_ncfg[v] + 1);  // room for any distinct count
+        max_dn = std::max(max_dn, c->h_ncfg[v]);
     }
     cudaError_t e;
     if ((e = c->stair.alloc(2 * (size_t)std::max<int64_t>(off[n_ops], 1))) != cudaSuccess ||
@@ -559,7 +586,9 @@ extern "C" int llama_create(llama_ctx **out, const llama_opts *opts) {
         cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, opts->device) != cudaSuccess ||
         cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaMallocHost(&c->h_ctrl, sizeof(unsigned long long) * kCtrlWords) != cudaSuccess) {
+        cudaMallocHost(&c->h_ctrl, sizeof(unsigned long long) * kCtrlWords) != cudaSuccess ||
+        c->q_dev.alloc(8 * LLAMA_MAX_HW) != cudaSuccess || c->q_sums.alloc(8 * LLAMA_MAX_HW) != cudaSuccess ||
+        cudaMemset(c->q_dev.p, 0, 8 * LLAMA_MAX_HW) != cudaSuccess) {
         cudaGetLastError();
         delete c;
         return LLAMA_ECUDA;
@@ -711,6 +740,8 @@ extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cf
         return c->fail(LLAMA_EINVAL, "set_profiles: need n_ops >= 1 and non-null arrays");
     if (alpha && (!batch || !res || !res_total))
         return c->fail(LLAMA_EINVAL, "set_profiles: alpha mode needs batch, res and res_total");
+    // resources are kept in either mode when given (Eq. 2's queueing time uses them)
+    const bool with_res = batch && res && res_total;
     if (cfg_off[0] != 0) return c->fail(LLAMA_EINVAL, "set_profiles: cfg_off[0] must be 0");
     std::vector<int64_t> pad_off(n_ops + 1);
     std::vector<int32_t> seg_pad((size_t)n_ops * (H + 1));
@@ -750,10 +781,10 @@ extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cf
         if (lat_us[x] < 1 || lat_us[x] > INT32_MAX - 1)
             return c->fail(LLAMA_EINVAL, "set_profiles: latency out of 1..INT32_MAX-1");
         if (cost_nd[x] < 0) return c->fail(LLAMA_EINVAL, "set_profiles: negative cost");
-        if (alpha && (batch[x] < 1 || batch[x] > LLAMA_MAX_ALPHA || res[x] < 1 || res[x] > LLAMA_MAX_ALPHA))
+        if (with_res && (batch[x] < 1 || batch[x] > LLAMA_MAX_ALPHA || res[x] < 1 || res[x] > LLAMA_MAX_ALPHA))
             return c->fail(LLAMA_EINVAL, "set_profiles: batch or res out of 1..65535");
     }
-    if (alpha)
+    if (with_res)
         for (int h = 0; h < H; ++h)
             if (res_total[h] < 1) return c->fail(LLAMA_EINVAL, "set_profiles: res_total must be >= 1");
 
@@ -791,16 +822,19 @@ extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cf
         (e = c->cp.alloc(8 * (size_t)n_ops)) != cudaSuccess ||
         (e = c->cp_magic.alloc(8 * (size_t)n_ops)) != cudaSuccess)
         return c->cuda_fail(e, "set_profiles upload");
-    if (alpha) {
+    if (with_res) {
         if ((e = up(c->batch, batch, 4 * (size_t)n_cfg)) != cudaSuccess ||
             (e = up(c->res, res, 4 * (size_t)n_cfg)) != cudaSuccess ||
-            (e = up(c->res_total, res_total, 4 * (size_t)H)) != cudaSuccess ||
-            (e = c->df.alloc(2 * (size_t)n_pad)) != cudaSuccess)
+            (e = up(c->res_total, res_total, 4 * (size_t)H)) != cudaSuccess)
             return c->cuda_fail(e, "set_profiles upload");
     } else {
         c->batch.release();
         c->res.release();
         c->res_total.release();
+    }
+    if (alpha) {
+        if ((e = c->df.alloc(2 * (size_t)n_pad)) != cudaSuccess) return c->cuda_fail(e, "set_profiles upload");
+    } else {
         c->df.release();
     }
     c->n_ops = n_ops;
@@ -809,29 +843,19 @@ extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cf
     c->max_npad = max_npad;
     c->ws.cap_ops = 0;  // op count may have changed: re-size the per-op scratch
 
-    const DevProblem P = make_problem(c);
-    k_encode_pad<<<n_ops, 256, 0, c->stream>>>(P, c->lrb.as<uint16_t>(), c->rf.as<uint16_t>(),
-                                               alpha ? c->df.as<uint16_t>() : nullptr,
-                                               c->fast.as<int32_t>());
-    int32_t sort_cap = 1;
-    while (sort_cap < (alpha ? 2 * max_n : max_n)) sort_cap <<= 1;
-    const size_t sort_smem = (size_t)sort_cap * 12;
-    if (sort_smem > (size_t)c->max_smem_optin)
+    c->max_n = max_n;
+    c->sort_cap = 1;
+    while (c->sort_cap < (alpha ? 2 * max_n : max_n)) c->sort_cap <<= 1;
+    c->sort_smem = (size_t)c->sort_cap * 12;
+    if (c->sort_smem > (size_t)c->max_smem_optin)
         return c->fail(LLAMA_EINVAL, "set_profiles: configuration space too large for one CTA sort");
     LL_CUDA(c, cudaFuncSetAttribute(k_encode_rank, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)sort_smem));
+                                    (int)c->sort_smem));
     int32_t lat_cap = 1;
     while (lat_cap < max_n) lat_cap <<= 1;
-    const size_t lat_smem = (size_t)lat_cap * 8;
-    LL_CUDA(c, cudaFuncSetAttribute(k_encode_lat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lat_smem));
-    k_encode_lat<<<n_ops, 1024, lat_smem, c->stream>>>(P, c->lrb.as<uint16_t>(), c->dlat.as<int32_t>(),
-                                                      c->dlat_n.as<int32_t>());
-    k_encode_piv<<<(unsigned)((32 * (int64_t)n_ops + 255) / 256), 256, 0, c->stream>>>(P, c->dpiv.as<int32_t>());
-    k_encode_rank<<<n_ops, 1024, sort_smem, c->stream>>>(P, sort_cap, c->rf.as<uint16_t>(),
-                                                        alpha ? c->df.as<uint16_t>() : nullptr,
-                                                        c->inv.as<uint16_t>());
-    k_encode_dec<<<n_ops, 256, 0, c->stream>>>(P, c->dec.as<int4>(), c->dfast.as<int4>());
-    LL_CUDA(c, cudaGetLastError());
+    c->lat_smem = (size_t)lat_cap * 8;
+    LL_CUDA(c, cudaFuncSetAttribute(k_encode_lat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->lat_smem));
+    LL_CUDA(c, encode_tables(c, make_problem(c), c->stream));
     LL_CUDA(c, cudaStreamSynchronize(c->stream));
     {
         // bucket-order info per op: {op, vectors, padded offset, distinct latencies}
@@ -846,9 +870,13 @@ extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cf
             oi[4 * k2 + 3] = dn[v];
         }
         LL_CUDA(c, cudaMemcpy(c->ord_info.p, oi.data(), 16 * (size_t)n_ops, cudaMemcpyHostToDevice));
-        std::vector<int32_t> cb(n_ops);
-        for (int32_t k2 = 0; k2 < n_ops; ++k2) cb[k2] = (int32_t)cfg_off[op_order[k2]];
+        std::vector<int32_t> cb(n_ops), pos(n_ops);
+        for (int32_t k2 = 0; k2 < n_ops; ++k2) cb[k2] = (int32_t)cfg_off[op_order[k2]], pos[op_order[k2]] = k2;
         LL_CUDA(c, cudaMemcpy(c->ord_cbase.p, cb.data(), 4 * (size_t)n_ops, cudaMemcpyHostToDevice));
+        LL_CUDA(c, c->ord_pos.alloc(4 * (size_t)n_ops));
+        LL_CUDA(c, cudaMemcpy(c->ord_pos.p, pos.data(), 4 * (size_t)n_ops, cudaMemcpyHostToDevice));
+        c->h_ncfg.resize(n_ops);
+        for (int32_t v = 0; v < n_ops; ++v) c->h_ncfg[v] = (int32_t)(cfg_off[v + 1] - cfg_off[v]);
         // shared-memory room for the distinct latencies of the largest op whose
         // list fits kMaxDlatSmem entries (none: every op searches global memory)
         int32_t cap = 0;
@@ -877,8 +905,33 @@ extern "C" int llama_set_queue(llama_ctx *c, const int64_t *q_us) {
     if (!q_us) return c->fail(LLAMA_EINVAL, "set_queue: null q_us");
     for (int h = 0; h < c->opts.n_hw; ++h)
         if (q_us[h] < 0 || q_us[h] > INT32_MAX) return c->fail(LLAMA_EINVAL, "set_queue: q out of 0..INT32_MAX");
-    for (int h = 0; h < c->opts.n_hw; ++h) c->q[h] = q_us[h];
-    c->drop_graph();  // the queueing times are kernel arguments
+    int64_t q[LLAMA_MAX_HW] = {0};
+    for (int h = 0; h < c->opts.n_hw; ++h) q[h] = q_us[h];
+    DeviceGuard g(c->opts.device);
+    // ordered after every call already enqueued on the legacy stream's side
+    LL_CUDA(c, cudaDeviceSynchronize());
+    LL_CUDA(c, cudaMemcpy(c->q_dev.p, q, sizeof(q), cudaMemcpyHostToDevice));
+    return LLAMA_OK;
+}
+
+extern "C" int llama_queue_time(llama_ctx *c, int64_t n, const int32_t *dag, const int32_t *op_local,
+                                const llama_decision *dec, int64_t *q_out, int32_t apply, void *stream) {
+    if (!c) return LLAMA_EINVAL;
+    if (n < 0 || (n > 0 && (!dag || !op_local || !dec))) return c->fail(LLAMA_EINVAL, "queue_time: bad arguments");
+    int rc = check_ready(c);
+    if (rc) return rc;
+    if (!c->res.p || !c->res_total.p)
+        return c->fail(LLAMA_EINVAL, "queue_time: the profiles carry no resources (res, res_total)");
+    DeviceGuard g(c->opts.device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const DevProblem P = make_problem(c);
+    LL_CUDA(c, cudaMemsetAsync(c->q_sums.p, 0, c->q_sums.bytes, s));
+    if (n > 0)
+        k_queue_sum<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(
+            P, n, dag, op_local, dec, c->q_sums.as<unsigned long long>());
+    k_queue_finish<<<1, 32, 0, s>>>(P, c->q_sums.as<unsigned long long>(), q_out,
+                                     apply ? c->q_dev.as<int64_t>() : nullptr);
+    LL_CUDA(c, cudaGetLastError());
     return LLAMA_OK;
 }
 
@@ -911,6 +964,67 @@ extern "C" int llama_set_method(llama_ctx *c, int32_t method) {
     c->drop_graph();
     c->method = method;
     if (method == LLAMA_METHOD_STAIRCASE && c->prof_set && !c->stair_ready) return build_stair(c);
+    return LLAMA_OK;
+}
+
+extern "C" int llama_feedback(llama_ctx *c, int64_t n, const int32_t *op, const int32_t *cfg,
+                              const int32_t *lat_us, const int64_t *cost_nd, int32_t beta_num, int32_t beta_den,
+                              int64_t *rejected, void *stream) {
+    if (!c) return LLAMA_EINVAL;
+    if (n < 0 || n >= INT32_MAX || (n > 0 && (!op || !cfg || !lat_us || !cost_nd)))
+        return c->fail(LLAMA_EINVAL, "feedback: bad arguments");
+    if (beta_den < 1 || beta_den > LLAMA_MAX_ALPHA || beta_num < 0 || beta_num > beta_den)
+        return c->fail(LLAMA_EINVAL, "feedback: need 0 <= beta_num <= beta_den <= 65535, beta_den >= 1");
+    int rc = check_ready(c);
+    if (rc) return rc;
+    DeviceGuard g(c->opts.device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (n == 0) return LLAMA_OK;
+    const size_t cap = 4 * (size_t)n;
+    if (c->fb_keys.bytes < cap) {
+        LL_CUDA(c, c->fb_keys.alloc(cap));
+        LL_CUDA(c, c->fb_idx.alloc(cap));
+        LL_CUDA(c, c->fb_keys2.alloc(cap));
+        LL_CUDA(c, c->fb_idx2.alloc(cap));
+    }
+    if (c->fb_touched.bytes < (size_t)c->n_ops) LL_CUDA(c, c->fb_touched.alloc((size_t)c->n_ops));
+    if (!c->fb_rejected.p) LL_CUDA(c, c->fb_rejected.alloc(8));
+    size_t tmp = 0;
+    LL_CUDA(c, cub::DeviceRadixSort::SortPairs(nullptr, tmp, c->fb_keys.as<int32_t>(), c->fb_keys2.as<int32_t>(),
+                                               c->fb_idx.as<int32_t>(), c->fb_idx2.as<int32_t>(), (int)n, 0, 32, s));
+    if (c->fb_tmp.bytes < tmp) LL_CUDA(c, c->fb_tmp.alloc(tmp));
+    DevProblem P = make_problem(c);
+    LL_CUDA(c, cudaMemsetAsync(c->fb_touched.p, 0, (size_t)c->n_ops, s));
+    LL_CUDA(c, cudaMemsetAsync(c->fb_rejected.p, 0, 8, s));
+    const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
+    k_feedback_keys<<<grid, 256, 0, s>>>(P, n, op, cfg, lat_us, cost_nd, c->fb_keys.as<int32_t>(),
+                                         c->fb_idx.as<int32_t>(), c->fb_rejected.as<unsigned long long>());
+    LL_CUDA(c, cub::DeviceRadixSort::SortPairs(c->fb_tmp.p, tmp, c->fb_keys.as<int32_t>(), c->fb_keys2.as<int32_t>(),
+                                               c->fb_idx.as<int32_t>(), c->fb_idx2.as<int32_t>(), (int)n, 0, 32, s));
+    k_feedback_apply<<<grid, 256, 0, s>>>(P, n, c->fb_keys2.as<int32_t>(), c->fb_idx2.as<int32_t>(), op, lat_us,
+                                          cost_nd, beta_num, beta_den, c->lat.as<int32_t>(), c->cost.as<int64_t>(),
+                                          c->fb_touched.as<uint8_t>());
+    // rebuild the encodings of the touched ops, on the device
+    P.encode_only = c->fb_touched.as<uint8_t>();
+    LL_CUDA(c, encode_tables(c, P, s));
+    k_refresh_order<<<(c->n_ops + 255) / 256, 256, 0, s>>>(P, c->ord_pos.as<int32_t>(), c->ord_info.as<int4>());
+    if (c->stair_ready) {
+        const size_t smem = 2 * 4 * (size_t)(c->max_n + 1);
+        k_encode_stair<<<c->n_ops, 1024, smem, s>>>(P, c->stair.as<uint16_t>());
+    }
+    if (rejected) LL_CUDA(c, cudaMemcpyAsync(rejected, c->fb_rejected.p, 8, cudaMemcpyDeviceToDevice, s));
+    LL_CUDA(c, cudaGetLastError());
+    return LLAMA_OK;
+}
+
+extern "C" int llama_get_profiles(llama_ctx *c, int32_t *lat_us, int64_t *cost_nd) {
+    if (!c) return LLAMA_EINVAL;
+    int rc = check_ready(c);
+    if (rc) return rc;
+    DeviceGuard g(c->opts.device);
+    LL_CUDA(c, cudaDeviceSynchronize());
+    if (lat_us) LL_CUDA(c, cudaMemcpy(lat_us, c->lat.p, 4 * (size_t)c->n_cfg, cudaMemcpyDeviceToHost));
+    if (cost_nd) LL_CUDA(c, cudaMemcpy(cost_nd, c->cost.p, 8 * (size_t)c->n_cfg, cudaMemcpyDeviceToHost));
     return LLAMA_OK;
 }
 

@@ -108,7 +108,9 @@ struct DevProblem {
     // latency rank is below k (cost-first: feasible-branch ranks, 0xFFFF if none;
     // alpha: that, or the least infeasible-branch rank among those at or above k)
     const uint16_t *stair;
-    const int64_t *stair_off;
+    const int64_t *stair_off;   // H * (n_cfg(v) + 1) keys per op, so feedback can change dn in place
+    // encoders only: when set, rebuild just the ops with encode_only[v] != 0
+    const uint8_t *encode_only;
     // per DAG, its structure packed contiguously (local op ids): {first op, ops,
     // edges, levels}, reference-configuration indices, successor CSR offsets,
     // successors, ops by height above the sinks, level offsets; empty for a DAG
@@ -118,7 +120,7 @@ struct DevProblem {
     int64_t *ref;
     int64_t *cp;
     uint64_t *cp_magic;  // floor((2^64-1) / cp[v]), for exact division by cp[v]
-    int64_t q[LLAMA_MAX_HW];
+    const int64_t *q;  // [n_hw] queueing time per backend (device: set by the host or by Eq. 2)
     int64_t alpha_num, alpha_den;
 };
 
@@ -219,6 +221,21 @@ __global__ void k_slack(DevProblem P, int64_t n_inv, const int32_t *dag, const i
 __global__ void k_encode_pad(DevProblem P, uint16_t *lrb, uint16_t *rf, uint16_t *df, int32_t *fast);
 __global__ void k_encode_lat(DevProblem P, uint16_t *lrb, int32_t *dlat, int32_t *dlat_n);
 __global__ void k_encode_piv(DevProblem P, int32_t *dpiv);
+// Eq. 2: per-backend sums of L(x_i) R(x_i) over decided invocations, then the
+// queueing time floor(sum / R_total(lambda)) of every backend.
+__global__ void k_queue_sum(DevProblem P, int64_t n, const int32_t *dag, const int32_t *op_local,
+                            const llama_decision *dec, unsigned long long *sums);
+__global__ void k_queue_finish(DevProblem P, const unsigned long long *sums, int64_t *q_out, int64_t *q_ctx);
+// Feedback: observations sorted by global configuration (stable), applied in
+// order by exponential smoothing; touched ops flagged for re-encoding.
+__global__ void k_feedback_apply(DevProblem P, int64_t n, const int32_t *sorted_g, const int32_t *sorted_obs,
+                                 const int32_t *obs_op, const int32_t *obs_lat, const int64_t *obs_cost,
+                                 int32_t beta_num, int32_t beta_den, int32_t *lat, int64_t *cost,
+                                 uint8_t *touched);
+__global__ void k_feedback_keys(DevProblem P, int64_t n, const int32_t *obs_op, const int32_t *obs_cfg,
+                                const int32_t *obs_lat, const int64_t *obs_cost, int32_t *keys, int32_t *idx,
+                                unsigned long long *rejected);
+__global__ void k_refresh_order(DevProblem P, const int32_t *ord_pos, int4 *ord_info);
 __global__ void k_encode_dec(DevProblem P, int4 *dec, int4 *dfast);
 __global__ void k_encode_stair(DevProblem P, uint16_t *stair);
 // Staircase method: critical paths of every DAG, then one thread per invocation.

@@ -39,7 +39,8 @@ EXPORTS = ("llama_create", "llama_destroy", "llama_set_dags", "llama_set_profile
            "llama_sg_predictions", "llama_sg_last_error", "llama_sg_set_margin",
            "llama_ws_create", "llama_ws_destroy", "llama_schedule_ws_async", "llama_ws_status",
            "llama_server_create", "llama_server_destroy", "llama_server_submit", "llama_server_poll",
-           "llama_server_drain", "llama_server_stats_get")
+           "llama_server_drain", "llama_server_stats_get", "llama_queue_time", "llama_feedback",
+           "llama_get_profiles")
 TRACE_EVENTS = 3
 TRACE_PHASES = ("bucket", "score")
 
@@ -114,6 +115,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "llama_server_poll": ([vp, vp, i64, vp], ctypes.c_int),
             "llama_server_drain": ([vp, vp, i64, vp, i64], ctypes.c_int),
             "llama_server_stats_get": ([vp, vp], ctypes.c_int),
+            "llama_queue_time": ([vp, i64, vp, vp, vp, vp, i32, vp], ctypes.c_int),
+            "llama_feedback": ([vp, i64, vp, vp, vp, vp, i32, i32, vp, vp], ctypes.c_int),
+            "llama_get_profiles": ([vp, vp, vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -342,6 +346,27 @@ class Server:
         self.close()
 
 
+def llama_queue_time(ctx, dag, op_local, dec, q_out=None, apply: bool = True, stream=None) -> None:
+    """Eq. 2 on device tensors: dag, op_local int32 [n], dec uint8 [n*24] (decisions)."""
+    v = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())
+    _check(ctx, load().llama_queue_time(ctx, dag.shape[0], v(dag), v(op_local), v(dec), v(q_out),
+                                        1 if apply else 0, _stream_ptr(stream)))
+
+
+def llama_feedback(ctx, op, cfg, lat_us, cost_nd, beta=(1, 4), rejected=None, stream=None) -> None:
+    """Exponential-smoothing feedback from device tensors (int32 op, cfg, lat; int64 cost)."""
+    v = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())
+    _check(ctx, load().llama_feedback(ctx, op.shape[0], v(op), v(cfg), v(lat_us), v(cost_nd), int(beta[0]),
+                                      int(beta[1]), v(rejected), _stream_ptr(stream)))
+
+
+def llama_get_profiles(ctx, n_cfg: int):
+    lat = np.empty(n_cfg, np.int32)
+    cost = np.empty(n_cfg, np.int64)
+    _check(ctx, load().llama_get_profiles(ctx, lat.ctypes.data, cost.ctypes.data))
+    return lat, cost
+
+
 def llama_set_method(ctx, method: int) -> None:
     _check(ctx, load().llama_set_method(ctx, int(method)))
 
@@ -433,9 +458,10 @@ class Scheduler:
         p = problem
         llama_set_dags(self.ctx, p.dag_op_off, p.row_ptr, p.col, p.slo_us)
         alpha_mode = mode == MODE_ALPHA
+        with_res = alpha_mode or (p.batch is not None and p.res is not None and p.res_total is not None)
         llama_set_profiles(self.ctx, p.cfg_off, p.hw_off, p.lat_us, p.cost_nd, p.ref_cfg,
-                           p.batch if alpha_mode else None, p.res if alpha_mode else None,
-                           p.res_total if alpha_mode else None)
+                           p.batch if with_res else None, p.res if with_res else None,
+                           p.res_total if with_res else None)
         if p.q_us is not None:
             llama_set_queue(self.ctx, p.q_us)
 

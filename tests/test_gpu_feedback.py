@@ -1,0 +1,85 @@
+"""Queueing time (Eq. 2) on the device, and exponential-smoothing feedback that
+updates the tables in place (Section 3.3): tables and later decisions bit-exact
+against the oracle applying the same integer rules."""
+import copy
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2102_01887_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+FIELDS = ("cfg", "lat", "cost", "slack", "flags")
+
+
+@pytest.fixture(scope="module")
+def L(cuda_device):
+    from paper_2102_01887_b300 import build, llama
+    build.build()
+    llama.load()
+    return llama
+
+
+def same(a, b, what=""):
+    for f in FIELDS:
+        bad = np.flatnonzero(a[f] != b[f])
+        assert bad.size == 0, f"{what} {f}: {bad.size} mismatches at {bad[:5]}"
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("method", [0, 1], ids=["scan", "staircase"])
+def test_queue_time_feeds_the_next_call(L, method):
+    import torch
+    p, inv = W.medium()
+    p.q_us = np.zeros(p.n_hw, np.int64)
+    queued = inv.subset(np.arange(0, inv.n, 3))
+    later = inv.subset(np.arange(1, inv.n, 3))
+    with L.Scheduler(p, method=method, use_graph=True) as s:
+        d_q, _ = s.schedule(queued)
+        q = torch.zeros(p.n_hw, dtype=torch.int64, device="cuda")
+        dec = dev(d_q.view(np.uint8))
+        L.llama_queue_time(s.ctx, dev(queued.dag), dev(queued.op_local), dec, q, apply=True)
+        got_q = q.cpu().numpy()
+        d_later, _ = s.schedule(later)
+    exp_q = oracle.queue_time(p, queued, d_q)
+    assert np.array_equal(got_q, exp_q) and (exp_q > 0).any()
+    p2 = copy.deepcopy(p)
+    p2.q_us = exp_q
+    exp, _ = oracle.schedule(p2, later)
+    same(d_later, exp, "after Eq. 2")
+
+
+@pytest.mark.parametrize("mode,alpha", [(0, (1, 1)), (1, (3, 2))], ids=["cost_first", "alpha"])
+@pytest.mark.parametrize("method", [0, 1], ids=["scan", "staircase"])
+def test_feedback_updates_tables_and_decisions(L, mode, alpha, method):
+    p, inv = W.medium()
+    rng = np.random.default_rng(7)
+    n = 40_000
+    hot = rng.integers(0, p.n_cfg, 3000)  # repeated configurations: the order matters
+    g = hot[rng.integers(0, hot.shape[0], n)]
+    op = (np.searchsorted(p.cfg_off, g, side="right") - 1).astype(np.int32)
+    cfg = (g - p.cfg_off[op]).astype(np.int32)
+    lat = np.maximum(1, p.lat_us[g] * rng.uniform(0.3, 3.0, n)).astype(np.int32)
+    cost = (p.cost_nd[g] * rng.uniform(0.5, 2.0, n)).astype(np.int64)
+    op[:3], cfg[3:5], lat[5] = -1, 10**6, 0  # six invalid observations
+    sub = inv.subset(np.arange(0, inv.n, 4))
+    with L.Scheduler(p, mode=mode, alpha=alpha, method=method, use_graph=True) as s:
+        before, _ = s.schedule(sub)  # captures the graph that must see the new tables
+        import torch
+        rej = torch.zeros(1, dtype=torch.int64, device="cuda")
+        L.llama_feedback(s.ctx, dev(op), dev(cfg), dev(lat), dev(cost), beta=(1, 4), rejected=rej)
+        after, _ = s.schedule(sub)
+        lat_d, cost_d = L.llama_get_profiles(s.ctx, p.n_cfg)
+        n_rej = int(rej.item())
+    q = copy.deepcopy(p)
+    exp_rej = oracle.feedback(q, op, cfg, lat, cost, beta=(1, 4))
+    assert n_rej == exp_rej == 6
+    assert np.array_equal(lat_d, q.lat_us) and np.array_equal(cost_d, q.cost_nd)
+    exp, _ = oracle.schedule(q, sub, mode=mode, alpha=alpha)
+    same(after, exp, "after feedback")
+    assert (after["cfg"] != before["cfg"]).any()

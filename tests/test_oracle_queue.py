@@ -1,0 +1,75 @@
+"""Pins of the oracle's Eq. 2 (queueing time) on hand-built cases."""
+import numpy as np
+
+import oracle
+from tests.problems import load_golden
+
+
+def test_queue_time_hand_computed():
+    g, p, inv = load_golden("amber_worked_example.json")
+    p.res = np.arange(1, p.n_cfg + 1, dtype=np.int32) % 4 + 1
+    p.res_total = np.asarray([3, 7, 5][:p.n_hw], np.int32)
+    d, _ = oracle.schedule(p, inv)
+    hw = p.hw_off.reshape(p.n_ops, p.n_hw + 1)
+    want = [0] * p.n_hw
+    for i in range(inv.n):
+        if d["cfg"][i] < 0:
+            continue
+        v = p.dag_op_off[inv.dag[i]] + inv.op_local[i]
+        x = int(d["cfg"][i])
+        lam = int(np.searchsorted(hw[v], x, side="right")) - 1
+        want[lam] += int(d["lat"][i]) * int(p.res[p.cfg_off[v] + x])
+    want = [w // int(p.res_total[h]) for h, w in enumerate(want)]
+    assert oracle.queue_time(p, inv, d).tolist() == want
+
+
+def test_queue_time_skips_invalid_and_floors_once():
+    # two decided invocations of op 1 on backend 1 with latency 3 and R = 1,
+    # R_total = 2: Q = floor(6 / 2) = 3 (flooring each term would give 1 + 1);
+    # a third, invalid, decision is skipped; the other backends are empty
+    g, p, inv = load_golden("amber_worked_example.json")
+    p.res = np.ones(p.n_cfg, np.int32)
+    p.res_total = np.full(p.n_hw, 2, np.int32)
+    hw = p.hw_off.reshape(p.n_ops, p.n_hw + 1)
+    v = 1
+    x = int(hw[v, 1])
+    assert hw[v, 2] > x  # backend 1 of op 1 is not empty
+    import paper_2102_01887_b300.workloads as W
+    q_inv = W.Invocations(np.zeros(3, np.int32), np.full(3, v - p.dag_op_off[0], np.int32),
+                          np.zeros(3, np.int64), 10)
+    d = np.zeros(3, oracle.DECISION_DTYPE)
+    d["cfg"] = [x, x, x]
+    d["lat"] = [3, 3, 1000]
+    d["flags"] = [0, 0, oracle.FLAG_INVALID]
+    q = oracle.queue_time(p, q_inv, d)
+    assert q.tolist() == [0, 3, 0][:p.n_hw]
+
+
+def test_feedback_closed_forms():
+    import copy
+    g, p0, inv = load_golden("amber_worked_example.json")
+    v, x = 1, 2
+    gidx = int(p0.cfg_off[v]) + x
+    # beta = 1: the observation replaces the table entry; beta = 0: nothing moves
+    p = copy.deepcopy(p0)
+    oracle.feedback(p, [v], [x], [777], [55], beta=(1, 1))
+    assert p.lat_us[gidx] == 777 and p.cost_nd[gidx] == 55
+    p = copy.deepcopy(p0)
+    oracle.feedback(p, [v], [x], [777], [55], beta=(0, 5))
+    assert np.array_equal(p.lat_us, p0.lat_us) and np.array_equal(p.cost_nd, p0.cost_nd)
+    # beta = 1/2 from 100: 101 -> (100 + 101 + 1) // 2 = 101 (halves round up)
+    p = copy.deepcopy(p0)
+    p.lat_us[gidx] = 100
+    oracle.feedback(p, [v], [x], [101], [0], beta=(1, 2))
+    assert p.lat_us[gidx] == 101
+    # order matters: from 100 with beta 1/2, 200 then 400 gives 150 then 275; 400 then 200
+    # gives 250 then 225
+    p = copy.deepcopy(p0)
+    p.lat_us[gidx] = 100
+    oracle.feedback(p, [v, v], [x, x], [200, 400], [0, 0], beta=(1, 2))
+    assert p.lat_us[gidx] == 275
+    p.lat_us[gidx] = 100
+    oracle.feedback(p, [v, v], [x, x], [400, 200], [0, 0], beta=(1, 2))
+    assert p.lat_us[gidx] == 225
+    # observations outside the tables are skipped
+    assert oracle.feedback(p, [-1, v, v], [0, 10**6, x], [5, 5, 0], [0, 0, 0]) == 3
