@@ -123,14 +123,38 @@ int llama_set_queue(llama_ctx *ctx, const int64_t *q_us);
  *   L <- ((beta_den - beta_num) L + beta_num L_obs + beta_den / 2) / beta_den
  * in exact integers (the same for the cost), a configuration's observations
  * applied in their order; 0 <= beta_num <= beta_den <= 65535.  The encodings
- * of the touched operations are rebuilt on the device, on `stream`, so the
- * calls enqueued after it see the new tables (the critical paths follow the
- * new reference latencies).  Invalid observations are skipped and counted into
+ * of the touched operations are rebuilt on the device, on `stream`; calls
+ * enqueued after it on that stream, and the blocking calls of this context,
+ * see the new tables (the critical paths follow the new reference latencies);
+ * calls on other streams must be ordered after it by the caller.  Invalid observations are skipped and counted into
  * *rejected (device int64, nullable).  Device pointers.  Errors: EINVAL,
  * ENOTREADY, ENOMEM, ECUDA. */
 int llama_feedback(llama_ctx *ctx, int64_t n, const int32_t *op, const int32_t *cfg, const int32_t *lat_us,
                    const int64_t *cost_nd, int32_t beta_num, int32_t beta_den, int64_t *rejected,
                    void *stream);
+
+/* Eq. 3, per-backend minima (Section 4.4): for every invocation i and backend
+ * h, the least Eq. 1 objective (the numeric one, with the context's alpha:
+ * C/B if L < slack(op, h), else C/B + floor(alpha_num L R / (alpha_den B
+ * R_total(h))), saturating) among op's configurations on h -- INT64_MAX for an
+ * empty backend or an invalid invocation -- into obj_min[i * n_hw + h]
+ * (device int64).  Arguments as llama_schedule_async.  Needs batch, res and
+ * res_total in the profiles.  Errors: EINVAL, ENOTREADY, ECUDA. */
+int llama_backend_objectives(llama_ctx *ctx, int64_t n_inv, const int32_t *dag, const int32_t *op_local,
+                             const int64_t *start_us, int64_t now_us, int64_t *obj_min, void *stream);
+
+/* Priority-based commit (Section 4.4): the order to commit n decided
+ * invocations (dag, op_local, dec as scheduled; obj_min from
+ * llama_backend_objectives) into the backends' commit queues: by the backend
+ * of each decision, then by descending affinity of the invocation's operation
+ * to that backend (Eq. 3: the least objective on the other backends over the
+ * least on its own; +inf when its own is 0), then by index; invalid decisions
+ * last.  order (device int32 [n]) receives invocation indices; affinity
+ * (device double [n], nullable) each invocation's affinity.  Errors: EINVAL,
+ * ENOTREADY, ENOMEM, ECUDA. */
+int llama_commit_order(llama_ctx *ctx, int64_t n, const int32_t *dag, const int32_t *op_local,
+                       const llama_decision *dec, const int64_t *obj_min, int32_t *order, double *affinity,
+                       void *stream);
 
 /* The current latency and cost tables (host arrays of n_cfg; blocking). */
 int llama_get_profiles(llama_ctx *ctx, int32_t *lat_us, int64_t *cost_nd);
@@ -142,7 +166,9 @@ int llama_get_profiles(llama_ctx *ctx, int32_t *lat_us, int64_t *cost_nd);
  * earlier scheduling calls, e.g. the speculative and commit queues; invalid
  * ones are skipped) and the profiles' resources.  Written to q_out (device,
  * n_hw int64, nullable); with apply != 0 it also becomes the context's
- * queueing time for later calls, on the device (no host round trip).  Device
+ * queueing time for later calls, on the device (no host round trip): calls
+ * after it on `stream`, and the blocking calls of this context; calls on
+ * other streams must be ordered after it by the caller.  Device
  * pointers, enqueued on `stream`.  Errors: EINVAL (arguments, or profiles set
  * without res / res_total), ENOTREADY. */
 int llama_queue_time(llama_ctx *ctx, int64_t n, const int32_t *dag, const int32_t *op_local,

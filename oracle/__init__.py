@@ -209,3 +209,55 @@ def feedback(p, op, cfg, lat_obs, cost_obs, beta=(1, 4)):
         p.lat_us[g] = min(max(L, 1), 2**31 - 2)
         p.cost_nd[g] = ((d - b) * int(p.cost_nd[g]) + b * co + d // 2) // d
     return rejected
+
+
+def backend_objectives(p, inv, alpha=(1, 1)) -> np.ndarray:
+    """Eq. 3's per-backend minima (Section 4.4): for every invocation and backend,
+    the least Eq. 1 objective among its op's configurations on that backend
+    (C/B if feasible, else C/B + floor(a L R / (b B R_total)), saturating);
+    INT64_MAX where the backend has none or the invocation is invalid."""
+    H = p.n_hw
+    a, b = int(alpha[0]), int(alpha[1])
+    imax = 2**63 - 1
+    sl = slacks(p, inv)
+    hw = p.hw_off.reshape(p.n_ops, H + 1)
+    out = np.full((inv.n, H), imax, np.int64)
+    for i in range(inv.n):
+        if sl[i, 0] < 0:
+            continue
+        v = int(p.dag_op_off[inv.dag[i]]) + int(inv.op_local[i])
+        for h in range(H):
+            best = imax
+            for x in range(int(hw[v, h]), int(hw[v, h + 1])):
+                g = int(p.cfg_off[v]) + x
+                L, C = int(p.lat_us[g]), int(p.cost_nd[g])
+                if L < sl[i, h]:
+                    obj = C
+                else:
+                    obj = min(C + (a * L * int(p.res[g])) // (b * int(p.batch[g]) * int(p.res_total[h])), imax)
+                best = min(best, obj)
+            out[i, h] = best
+    return out
+
+
+def commit_order(p, inv, decisions, obj_min):
+    """Priority-based commit order (Section 4.4): by the backend of each decision,
+    then descending affinity (Eq. 3: least objective elsewhere over least on its
+    own backend), then index; invalid decisions last.  Returns (order, affinity)."""
+    H = p.n_hw
+    hw = p.hw_off.reshape(p.n_ops, H + 1)
+    keys, aff = [], np.zeros(inv.n)
+    for i in range(inv.n):
+        d = decisions[i]
+        if d["cfg"] < 0 or d["flags"] & FLAG_INVALID:
+            keys.append((H, 0.0, i))
+            continue
+        v = int(p.dag_op_off[inv.dag[i]]) + int(inv.op_local[i])
+        lam = max(h for h in range(H) if int(d["cfg"]) >= hw[v, h])
+        own = int(obj_min[i, lam])
+        other = min(int(obj_min[i, h]) for h in range(H) if h != lam) if H > 1 else 2**63 - 1
+        a = (1.0 if other == 0 else float("inf")) if own == 0 else float(other) / float(own)
+        aff[i] = a
+        keys.append((lam, -a, i))
+    order = [k[2] for k in sorted(keys)]
+    return np.asarray(order, np.int32), aff

@@ -1582,6 +1582,87 @@ __global__ void k_queue_finish(DevProblem P, const unsigned long long *sums, int
     if (q_ctx) q_ctx[h] = v;
 }
 
+// Eq. 3 (Section 4.4): for invocation i and backend h, the least objective of
+// Eq. 1 among op's configurations on h, each against slack(op, h): C/B if
+// L < slack, else C/B + floor(alpha_num L R / (alpha_den B R_total)),
+// saturating at INT64_MAX; INT64_MAX for an empty segment or an invalid
+// invocation.  One warp per invocation.
+__global__ void k_backend_obj(DevProblem P, int64_t n_inv, const int32_t *dag, const int32_t *op_local,
+                              const int64_t *start, int64_t now, int64_t *obj_min) {
+    const int H = P.n_hw, lane = threadIdx.x & 31;
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (i >= n_inv) return;
+    int64_t best[LLAMA_MAX_HW];
+#pragma unroll
+    for (int h = 0; h < LLAMA_MAX_HW; ++h) best[h] = INT64_MAX;
+    const int32_t d = dag[i], o = op_local[i];
+    const bool valid = invocation_valid(P, d, o, start[i], now);
+    if (valid) {
+        const int32_t v = P.dag_op_off[d] + o;
+        const int64_t c0 = P.cfg_off[v];
+        const int n = (int)(P.cfg_off[v + 1] - c0);
+        const int32_t *hw = P.hw_off + (int64_t)v * (H + 1);
+        const int64_t rbase = P.slo[d] - (now - start[i]);
+        int32_t sl[LLAMA_MAX_HW];
+#pragma unroll
+        for (int h = 0; h < LLAMA_MAX_HW; ++h)
+            sl[h] = h < H ? slack_of(P.ref[v], P.cp[v], P.cp_magic[v], rbase - P.q[h]) : 0;
+        for (int x = lane; x < n; x += 32) {
+            const int lam = backend_of(hw, H, x);
+            const int64_t g = c0 + x;
+            int32_t s = sl[0];
+#pragma unroll
+            for (int h = 1; h < LLAMA_MAX_HW; ++h)
+                if (h == lam) s = sl[h];
+            const int64_t obj = P.lat[g] < s ? P.cost[g] : (int64_t)alpha_infeasible_objective(P, g, lam);
+#pragma unroll
+            for (int h = 0; h < LLAMA_MAX_HW; ++h)
+                if (h == lam) best[h] = min(best[h], obj);
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < LLAMA_MAX_HW; ++h) {
+        int64_t b = best[h];
+        for (int k = 16; k > 0; k >>= 1) b = min(b, (int64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)b, k));
+        if (lane == 0 && h < H) obj_min[i * H + h] = b;
+    }
+}
+
+// Priority-based commit (Section 4.4): the affinity of each decided
+// invocation to the backend of its configuration, min over the other
+// backends / min over its own (Eq. 3), and sort keys for the order (backend
+// ascending, affinity descending, then index).
+__global__ void k_commit_keys(DevProblem P, int64_t n, const int32_t *dag, const int32_t *op_local,
+                              const llama_decision *dec, const int64_t *obj_min, uint64_t *aff_key,
+                              uint32_t *lam_key, int32_t *idx, double *aff_out) {
+    const int H = P.n_hw;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const llama_decision dd = dec[i];
+        int lam = H;  // invalid decisions go last
+        double aff = 0.0;
+        if (dd.cfg >= 0 && !(dd.flags & LLAMA_FLAG_INVALID)) {
+            const int32_t v = P.dag_op_off[dag[i]] + op_local[i];
+            lam = backend_of(P.hw_off + (int64_t)v * (H + 1), H, dd.cfg);
+            int64_t other = INT64_MAX;
+            for (int h = 0; h < H; ++h)
+                if (h != lam) other = min(other, obj_min[i * H + h]);
+            const int64_t own = obj_min[i * H + lam];
+            // other / own as doubles (objectives stay below 2^53: exact conversions)
+            aff = own == 0 ? (other == 0 ? 1.0 : INFINITY) : (double)other / (double)own;
+        }
+        // descending affinity: invert the order-preserving bit pattern of a non-negative double
+        aff_key[i] = ~(uint64_t)__double_as_longlong(aff);
+        lam_key[i] = (uint32_t)lam;
+        idx[i] = (int32_t)i;
+        if (aff_out) aff_out[i] = aff;
+    }
+}
+
+__global__ void k_gather_u32(int64_t n, const uint32_t *src, const int32_t *idx, uint32_t *dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[idx[i]];
+}
+
 // Feedback, step 1: validate the observations and key them by global
 // configuration (invalid ones get key INT32_MAX and are counted).
 __global__ void k_feedback_keys(DevProblem P, int64_t n, const int32_t *obs_op, const int32_t *obs_cfg,

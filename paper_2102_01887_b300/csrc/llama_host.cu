@@ -71,6 +71,7 @@ struct llama_ctx {
     int max_smem_optin = 0;
     int64_t l2_bytes = 0;
     cudaStream_t stream = nullptr;
+    cudaEvent_t order_ev = nullptr;  // orders the context's own stream after table updates on other streams
     std::string err = "no error";
 
     // DAGs
@@ -92,6 +93,8 @@ struct llama_ctx {
     DevBuf ord_pos;                // bucket-order position of every op
     // feedback scratch
     DevBuf fb_keys, fb_idx, fb_keys2, fb_idx2, fb_touched, fb_rejected, fb_tmp;
+    // commit-order scratch
+    DevBuf co_aff, co_aff2, co_lam, co_lam2, co_idx, co_idx2, co_tmp;
 
     // profiles
     bool prof_set = false;
@@ -347,6 +350,13 @@ int build_stair(llama_ctx *c) {
     return LLAMA_OK;
 }
 
+// The context's own stream (blocking calls) waits for what is enqueued on s so far.
+int order_context_after(llama_ctx *c, cudaStream_t s) {
+    LL_CUDA(c, cudaEventRecord(c->order_ev, s));
+    LL_CUDA(c, cudaStreamWaitEvent(c->stream, c->order_ev, 0));
+    return LLAMA_OK;
+}
+
 int check_ready(llama_ctx *c) {
     if (!c->dags_set || !c->prof_set)
         return c->fail(LLAMA_ENOTREADY, "schedule called before llama_set_dags and llama_set_profiles");
@@ -586,6 +596,7 @@ extern "C" int llama_create(llama_ctx **out, const llama_opts *opts) {
         cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, opts->device) != cudaSuccess ||
         cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->order_ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaMallocHost(&c->h_ctrl, sizeof(unsigned long long) * kCtrlWords) != cudaSuccess ||
         c->q_dev.alloc(8 * LLAMA_MAX_HW) != cudaSuccess || c->q_sums.alloc(8 * LLAMA_MAX_HW) != cudaSuccess ||
         cudaMemset(c->q_dev.p, 0, 8 * LLAMA_MAX_HW) != cudaSuccess) {
@@ -613,6 +624,7 @@ extern "C" void llama_destroy(llama_ctx *c) {
         c->drop_graph();
         if (c->stream) cudaStreamDestroy(c->stream);
         if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+        if (c->order_ev) cudaEventDestroy(c->order_ev);
         if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
         delete c;  // DevBuf destructors free device memory with the device current
     }
@@ -932,7 +944,7 @@ extern "C" int llama_queue_time(llama_ctx *c, int64_t n, const int32_t *dag, con
     k_queue_finish<<<1, 32, 0, s>>>(P, c->q_sums.as<unsigned long long>(), q_out,
                                      apply ? c->q_dev.as<int64_t>() : nullptr);
     LL_CUDA(c, cudaGetLastError());
-    return LLAMA_OK;
+    return apply ? order_context_after(c, s) : LLAMA_OK;
 }
 
 extern "C" int llama_set_tuning(llama_ctx *c, int32_t lanes_min_vectors, int32_t inv_per_thread,
@@ -1013,6 +1025,70 @@ extern "C" int llama_feedback(llama_ctx *c, int64_t n, const int32_t *op, const 
         k_encode_stair<<<c->n_ops, 1024, smem, s>>>(P, c->stair.as<uint16_t>());
     }
     if (rejected) LL_CUDA(c, cudaMemcpyAsync(rejected, c->fb_rejected.p, 8, cudaMemcpyDeviceToDevice, s));
+    LL_CUDA(c, cudaGetLastError());
+    return order_context_after(c, s);
+}
+
+extern "C" int llama_backend_objectives(llama_ctx *c, int64_t n_inv, const int32_t *dag, const int32_t *op_local,
+                                        const int64_t *start_us, int64_t now_us, int64_t *obj_min, void *stream) {
+    if (!c) return LLAMA_EINVAL;
+    int rc = check_inv_args(c, n_inv, dag, op_local, start_us, obj_min);
+    if (rc) return rc;
+    if ((rc = check_ready(c))) return rc;
+    if (!c->res.p || !c->batch.p || !c->res_total.p)
+        return c->fail(LLAMA_EINVAL, "backend_objectives: Eq. 1 needs batch, res and res_total in the profiles");
+    if (c->opts.alpha_num < 0 || c->opts.alpha_num > LLAMA_MAX_ALPHA || c->opts.alpha_den < 1 ||
+        c->opts.alpha_den > LLAMA_MAX_ALPHA)
+        return c->fail(LLAMA_EINVAL, "backend_objectives: the context's alpha is not usable (llama_opts)");
+    if (n_inv == 0) return LLAMA_OK;
+    DeviceGuard g(c->opts.device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const ContextView v = view_of(c);
+    k_critical_paths<<<std::max(1, (v.n_dags + 7) / 8), 256, 0, s>>>(v.P, v.topo, v.lvl_off, v.dag_lvl);
+    k_backend_obj<<<(unsigned)((n_inv * 32 + 255) / 256), 256, 0, s>>>(v.P, n_inv, dag, op_local, start_us, now_us,
+                                                                       obj_min);
+    LL_CUDA(c, cudaGetLastError());
+    return LLAMA_OK;
+}
+
+extern "C" int llama_commit_order(llama_ctx *c, int64_t n, const int32_t *dag, const int32_t *op_local,
+                                  const llama_decision *dec, const int64_t *obj_min, int32_t *order,
+                                  double *affinity, void *stream) {
+    if (!c) return LLAMA_EINVAL;
+    if (n < 0 || n >= INT32_MAX || (n > 0 && (!dag || !op_local || !dec || !obj_min || !order)))
+        return c->fail(LLAMA_EINVAL, "commit_order: bad arguments");
+    int rc = check_ready(c);
+    if (rc) return rc;
+    if (n == 0) return LLAMA_OK;
+    DeviceGuard g(c->opts.device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t need = 8 * (size_t)n;
+    if (c->co_aff.bytes < need) {
+        LL_CUDA(c, c->co_aff.alloc(need));
+        LL_CUDA(c, c->co_aff2.alloc(need));
+        LL_CUDA(c, c->co_lam.alloc(4 * (size_t)n));
+        LL_CUDA(c, c->co_lam2.alloc(4 * (size_t)n));
+        LL_CUDA(c, c->co_idx.alloc(4 * (size_t)n));
+        LL_CUDA(c, c->co_idx2.alloc(4 * (size_t)n));
+    }
+    const DevProblem P = make_problem(c);
+    k_commit_keys<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(
+        P, n, dag, op_local, dec, obj_min, c->co_aff.as<uint64_t>(), c->co_lam.as<uint32_t>(), c->co_idx.as<int32_t>(),
+        affinity);
+    // two stable sorts: by affinity (descending keys), then by backend
+    size_t t1 = 0, t2 = 0;
+    LL_CUDA(c, cub::DeviceRadixSort::SortPairs(nullptr, t1, c->co_aff.as<uint64_t>(), c->co_aff2.as<uint64_t>(),
+                                               c->co_idx.as<int32_t>(), c->co_idx2.as<int32_t>(), (int)n, 0, 64, s));
+    LL_CUDA(c, cub::DeviceRadixSort::SortPairs(nullptr, t2, c->co_lam.as<uint32_t>(), c->co_lam2.as<uint32_t>(),
+                                               c->co_idx2.as<int32_t>(), order, (int)n, 0, 8, s));
+    if (c->co_tmp.bytes < std::max(t1, t2)) LL_CUDA(c, c->co_tmp.alloc(std::max(t1, t2)));
+    LL_CUDA(c, cub::DeviceRadixSort::SortPairs(c->co_tmp.p, t1, c->co_aff.as<uint64_t>(), c->co_aff2.as<uint64_t>(),
+                                               c->co_idx.as<int32_t>(), c->co_idx2.as<int32_t>(), (int)n, 0, 64, s));
+    // the backend of each entry in affinity order, then the stable sort by it
+    k_gather_u32<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(
+        n, c->co_lam.as<uint32_t>(), c->co_idx2.as<int32_t>(), c->co_lam2.as<uint32_t>());
+    LL_CUDA(c, cub::DeviceRadixSort::SortPairs(c->co_tmp.p, t2, c->co_lam2.as<uint32_t>(), c->co_lam.as<uint32_t>(),
+                                               c->co_idx2.as<int32_t>(), order, (int)n, 0, 8, s));
     LL_CUDA(c, cudaGetLastError());
     return LLAMA_OK;
 }

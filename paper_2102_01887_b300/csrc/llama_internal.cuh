@@ -236,6 +236,14 @@ __global__ void k_feedback_keys(DevProblem P, int64_t n, const int32_t *obs_op, 
                                 const int32_t *obs_lat, const int64_t *obs_cost, int32_t *keys, int32_t *idx,
                                 unsigned long long *rejected);
 __global__ void k_refresh_order(DevProblem P, const int32_t *ord_pos, int4 *ord_info);
+__global__ void k_gather_u32(int64_t n, const uint32_t *src, const int32_t *idx, uint32_t *dst);
+// Eq. 3: per invocation and backend, the least Eq. 1 objective among the op's
+// configurations on that backend (a warp per invocation), and the commit keys.
+__global__ void k_backend_obj(DevProblem P, int64_t n_inv, const int32_t *dag, const int32_t *op_local,
+                              const int64_t *start, int64_t now, int64_t *obj_min);
+__global__ void k_commit_keys(DevProblem P, int64_t n, const int32_t *dag, const int32_t *op_local,
+                              const llama_decision *dec, const int64_t *obj_min, uint64_t *aff_key,
+                              uint32_t *lam_key, int32_t *idx, double *aff_out);
 __global__ void k_encode_dec(DevProblem P, int4 *dec, int4 *dfast);
 __global__ void k_encode_stair(DevProblem P, uint16_t *stair);
 // Staircase method: critical paths of every DAG, then one thread per invocation.

@@ -40,7 +40,7 @@ EXPORTS = ("llama_create", "llama_destroy", "llama_set_dags", "llama_set_profile
            "llama_ws_create", "llama_ws_destroy", "llama_schedule_ws_async", "llama_ws_status",
            "llama_server_create", "llama_server_destroy", "llama_server_submit", "llama_server_poll",
            "llama_server_drain", "llama_server_stats_get", "llama_queue_time", "llama_feedback",
-           "llama_get_profiles")
+           "llama_get_profiles", "llama_backend_objectives", "llama_commit_order")
 TRACE_EVENTS = 3
 TRACE_PHASES = ("bucket", "score")
 
@@ -118,6 +118,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "llama_queue_time": ([vp, i64, vp, vp, vp, vp, i32, vp], ctypes.c_int),
             "llama_feedback": ([vp, i64, vp, vp, vp, vp, i32, i32, vp, vp], ctypes.c_int),
             "llama_get_profiles": ([vp, vp, vp], ctypes.c_int),
+            "llama_backend_objectives": ([vp, i64, vp, vp, vp, i64, vp, vp], ctypes.c_int),
+            "llama_commit_order": ([vp, i64, vp, vp, vp, vp, vp, vp, vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -358,6 +360,18 @@ def llama_feedback(ctx, op, cfg, lat_us, cost_nd, beta=(1, 4), rejected=None, st
     v = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())
     _check(ctx, load().llama_feedback(ctx, op.shape[0], v(op), v(cfg), v(lat_us), v(cost_nd), int(beta[0]),
                                       int(beta[1]), v(rejected), _stream_ptr(stream)))
+
+
+def llama_backend_objectives(ctx, dag, op_local, start, now_us: int, obj_min, stream=None) -> None:
+    v = lambda t: ctypes.c_void_p(t.data_ptr())
+    _check(ctx, load().llama_backend_objectives(ctx, dag.shape[0], v(dag), v(op_local), v(start), int(now_us),
+                                                v(obj_min), _stream_ptr(stream)))
+
+
+def llama_commit_order(ctx, dag, op_local, dec, obj_min, order, affinity=None, stream=None) -> None:
+    v = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())
+    _check(ctx, load().llama_commit_order(ctx, dag.shape[0], v(dag), v(op_local), v(dec), v(obj_min), v(order),
+                                          v(affinity), _stream_ptr(stream)))
 
 
 def llama_get_profiles(ctx, n_cfg: int):

@@ -83,3 +83,27 @@ def test_feedback_updates_tables_and_decisions(L, mode, alpha, method):
     exp, _ = oracle.schedule(q, sub, mode=mode, alpha=alpha)
     same(after, exp, "after feedback")
     assert (after["cfg"] != before["cfg"]).any()
+
+
+@pytest.mark.parametrize("method", [0, 1], ids=["scan", "staircase"])
+def test_affinity_and_commit_order(L, method):
+    import torch
+    p, inv = W.medium()
+    sub = inv.subset(np.arange(0, inv.n, 160))  # 410 invocations
+    sub.dag = sub.dag.copy()
+    sub.dag[4] = -1  # one invalid
+    with L.Scheduler(p, alpha=(3, 2), method=method) as s:
+        d, _ = s.schedule(sub)
+        dag, opl, st = dev(sub.dag), dev(sub.op_local), dev(sub.start_us)
+        obj = torch.empty(sub.n * p.n_hw, dtype=torch.int64, device="cuda")
+        L.llama_backend_objectives(s.ctx, dag, opl, st, sub.now_us, obj)
+        order = torch.empty(sub.n, dtype=torch.int32, device="cuda")
+        aff = torch.empty(sub.n, dtype=torch.float64, device="cuda")
+        L.llama_commit_order(s.ctx, dag, opl, dev(d.view(np.uint8)), obj, order, aff)
+        got_obj = obj.cpu().numpy().reshape(sub.n, p.n_hw)
+        got_order, got_aff = order.cpu().numpy(), aff.cpu().numpy()
+    exp_obj = oracle.backend_objectives(p, sub, alpha=(3, 2))
+    assert np.array_equal(got_obj, exp_obj)
+    exp_order, exp_aff = oracle.commit_order(p, sub, d, exp_obj)
+    assert np.array_equal(got_aff, exp_aff)
+    assert np.array_equal(got_order, exp_order)

@@ -73,3 +73,49 @@ def test_feedback_closed_forms():
     assert p.lat_us[gidx] == 225
     # observations outside the tables are skipped
     assert oracle.feedback(p, [-1, v, v], [0, 10**6, x], [5, 5, 0], [0, 0, 0]) == 3
+
+
+def test_backend_minima_agree_with_the_alpha_decision():
+    # the least of an invocation's per-backend minima is the objective of the
+    # configuration Eq. 1 selects (the C oracle's alpha mode, another code path)
+    from paper_2102_01887_b300 import workloads as W
+    for seed in range(6):
+        p, inv = W.random_small(seed, max_cfg=12, n_inv=40)
+        a = (2 + seed % 3, 3)
+        obj = oracle.backend_objectives(p, inv, alpha=a)
+        d, _ = oracle.schedule(p, inv, mode=oracle.MODE_ALPHA, alpha=a)
+        sl = oracle.slacks(p, inv)
+        hw = p.hw_off.reshape(p.n_ops, p.n_hw + 1)
+        for i in range(inv.n):
+            if d["flags"][i] & oracle.FLAG_INVALID:
+                assert (obj[i] == 2**63 - 1).all()
+                continue
+            v = p.dag_op_off[inv.dag[i]] + inv.op_local[i]
+            x = int(d["cfg"][i])
+            g = p.cfg_off[v] + x
+            lam = int(np.searchsorted(hw[v], x, side="right")) - 1
+            L, C = int(p.lat_us[g]), int(p.cost_nd[g])
+            want = C if L < sl[i, lam] else C + (a[0] * L * int(p.res[g])) // (a[1] * int(p.batch[g]) * int(p.res_total[lam]))
+            assert obj[i].min() == want, (seed, i)
+
+
+def test_commit_order_invariants():
+    from paper_2102_01887_b300 import workloads as W
+    p, inv = W.random_small(3, max_cfg=10, n_inv=60)
+    d, _ = oracle.schedule(p, inv)
+    obj = oracle.backend_objectives(p, inv, alpha=(1, 1))
+    order, aff = oracle.commit_order(p, inv, d, obj)
+    assert sorted(order.tolist()) == list(range(inv.n))
+    hw = p.hw_off.reshape(p.n_ops, p.n_hw + 1)
+    lam = []
+    for i in order:
+        if d["cfg"][i] < 0:
+            lam.append(p.n_hw)
+        else:
+            v = p.dag_op_off[inv.dag[i]] + inv.op_local[i]
+            lam.append(int(np.searchsorted(hw[v], d["cfg"][i], side="right")) - 1)
+    assert lam == sorted(lam)  # grouped by backend
+    for k in range(1, inv.n):  # within a backend: affinity descending, then index
+        if lam[k] == lam[k - 1] and lam[k] < p.n_hw:
+            i, j = order[k - 1], order[k]
+            assert aff[i] > aff[j] or (aff[i] == aff[j] and i < j)
