@@ -150,7 +150,8 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        import tempfile
+        self.path = os.path.join(tempfile.gettempdir(), f"llama_bench_clocks_{os.getpid()}_{index}.csv")
 
     def __enter__(self):
         try:
