@@ -19,8 +19,9 @@ pytestmark = pytest.mark.gpu
 FIELDS = ("cfg", "lat", "cost", "slack", "flags")
 
 
-@pytest.mark.parametrize("method", [0, 1], ids=["scan", "staircase"])
-def test_static_scratch_matches_allocating_entry_point(cuda_device, method):
+@pytest.mark.parametrize("variant", [dict(method=0), dict(method=0, fused=False), dict(method=1)],
+                         ids=["scan", "scan2", "staircase"])
+def test_static_scratch_matches_allocating_entry_point(cuda_device, variant):
     import torch
 
     from paper_2102_01887_b300 import build, llama as L
@@ -29,7 +30,7 @@ def test_static_scratch_matches_allocating_entry_point(cuda_device, method):
     dev = torch.device("cuda", cuda_device)
     p, inv = W.medium()  # 65,536 invocations: the largest size the static array takes
     sub = inv.subset(np.arange(0, inv.n, 5))
-    with L.Scheduler(p, device=cuda_device, method=method) as s:
+    with L.Scheduler(p, device=cuda_device, **variant) as s:
         stream = torch.cuda.Stream(device=dev)
         for case in (inv, sub, inv):  # consecutive calls: a smaller one in between
             expected, rc = s.schedule(case)  # the allocating entry point
