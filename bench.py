@@ -77,8 +77,6 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch kernels directly, no CUDA graph")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default scoring schedule")
-    ap.add_argument("--no-fusion", action="store_true",
-                    help="scan calls in two launches (bucketing, scoring) instead of one fused kernel")
     ap.add_argument("--n-dags", type=int, default=None, help="DAG count of the batched workloads")
     ap.add_argument("--n-inv", type=int, default=None, help="invocations per step (default: the workload's)")
     ap.add_argument("--tuning", default=None,
@@ -452,8 +450,7 @@ def main():
     p, inv = make_workload(args.workload, rank, args.n_dags, args.n_inv)
     mode = L.MODE_ALPHA if args.mode == "alpha" else L.MODE_COST_FIRST
     method = L.METHOD_STAIRCASE if args.method == "staircase" else L.METHOD_SCAN
-    sched = L.Scheduler(p, mode=mode, alpha=(3, 2), device=local, use_graph=not args.no_graph, method=method,
-                        fused=not args.no_fusion)
+    sched = L.Scheduler(p, mode=mode, alpha=(3, 2), device=local, use_graph=not args.no_graph, method=method)
     ctx = sched.ctx
     scores = scores_of(p, inv)
 
@@ -558,11 +555,7 @@ def main():
 
     peaks, peak_src = measured_peaks()
     clk = clocks.summary()
-    # a fused scan call is one kernel (k_sched_*): its trace phases are the
-    # whole call and an empty one
-    fused = args.method == "scan" and L.llama_last_launch_count(ctx) == 1
-    score_ms = float(phase_ms.sum(axis=1).mean()) if fused else float(phase_ms[:, -1].mean())
-    score_kernel = "k_sched" if fused else "k_score"
+    score_ms = float(phase_ms[:, -1].mean())
     # Rooflines.  Scoring: when the encoded tables fit in L2 they are staged once
     # per tile and reused by all of the tile's invocations, so the scan is bound
     # by the integer ALU pipe; when they do not (tables streamed from HBM, few
@@ -598,31 +591,25 @@ def main():
         roofline = rooflines[dominant]
     elif tbl_per_entry * int(npad.sum()) + 4 * int(npad.sum()) > l2_bytes // 2:
         algo_bytes = tbl_per_entry * int(npad[touched].sum()) + inv.n * (4 + 12 + 24)
-        achieved = algo_bytes / (score_ms / 1e3) / 1e9
-        rooflines[score_kernel] = {
-            "bound": "hbm", "kernel": score_kernel, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": measured_traffic(score_kernel, args.workload, args.mode),
+        achieved = algo_bytes / (kms["score"] / 1e3) / 1e9
+        rooflines["k_score"] = {
+            "bound": "hbm", "kernel": "k_score", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": measured_traffic("k_score", args.workload, args.mode),
             "peak_source": f"{peak_src} HBM copy bandwidth", "algorithmic_bytes": algo_bytes,
             "bytes_note": f"{tbl_per_entry} B per padded table entry of each op with invocations "
                           "(latency rank + objective rank(s)), once, plus 40 B per invocation"}
     else:
         peak_tops = sm_count * ALU_LANES_PER_SM * sm_mhz * 1e6 / 1e12
         ops_per_score = ALU_OPS_PER_SCORE[args.mode]
-        achieved = ops_per_score * scores / (score_ms / 1e3) / 1e12
-        rooflines[score_kernel] = {
-            "bound": "alu", "kernel": score_kernel, "achieved": achieved, "peak": peak_tops,
+        achieved = ops_per_score * scores / (kms["score"] / 1e3) / 1e12
+        rooflines["k_score"] = {
+            "bound": "alu", "kernel": "k_score", "achieved": achieved, "peak": peak_tops,
             "unit": "T ALU-ops/s", "frac": achieved / peak_tops,
-            "traffic": measured_traffic(score_kernel, args.workload, args.mode),
+            "traffic": measured_traffic("k_score", args.workload, args.mode),
             "peak_source": f"{sm_count} SMs x {ALU_LANES_PER_SM} integer ALU lanes x "
                            f"{sm_mhz:.0f} MHz ({peak_src} max SM clock)",
             "alu_ops_per_score": ops_per_score, "scores_per_s_ceiling": peak_tops * 1e12 / ops_per_score}
-        if fused:
-            rooflines[score_kernel]["time_note"] = (
-                "the whole call (critical paths, bucketing, slack, scoring) is this one kernel; "
-                "its duration includes its launch (trace events around it)")
-    if fused:
-        roofline = rooflines[score_kernel]
-    elif args.method == "scan":
+    if args.method == "scan":
         b_bytes = inv.n * (16 + 4 + 4 * p.n_hw)
         b_ach = b_bytes / (kms["bucket"] / 1e3) / 1e9
         rooflines["k_bucket"] = {
@@ -652,7 +639,6 @@ def main():
         "warmup": args.warmup, "ms_per_step": float(step_ms.mean()), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32/int64", "data": "synthetic",
         "config": {**workload_config(args.workload, p, inv, args.mode, scores), "method": args.method,
-                   "launches_per_call": L.llama_last_launch_count(ctx),
                    "schedule": tuning["best"] if tuning else "default"},
         "configs_scored_per_s": world * scores * args.steps / total_s,
         "decision_latency_us": {"p50": 1e3 * float(np.median(step_ms)),
@@ -662,11 +648,10 @@ def main():
                            "hbm_frac": SCAN_BYTES_PER_SCORE * scores / (score_ms / 1e3) / 1e9 / peaks["hbm_gbs"],
                            "note": "12 B per scored configuration / scoring-kernel time; where tables are "
                                    "reused across invocations from shared memory this exceeds HBM"},
-        "kernel_ms": ({"sched": score_ms} if fused else
-                      {n: float(phase_ms[:, j].mean()) for j, n in
-                       enumerate(("critical_path", "stair") if args.method == "staircase" else L.TRACE_PHASES)}),
+        "kernel_ms": {n: float(phase_ms[:, j].mean()) for j, n in
+                      enumerate(("critical_path", "stair") if args.method == "staircase" else L.TRACE_PHASES)},
         "kernel_ms_note": "per-kernel event times from a second pass of the same steps with trace "
-                          "events (direct launches, no overlap between kernels)",
+                          "events (direct launches, no overlap between the two kernels)",
         "roofline": roofline,
         "rooflines": rooflines,
         "schedule_trials": ([{k: t[k] for k in ("lanes_min_vectors", "inv_per_thread", "chunk", "stages", "ms")}

@@ -264,20 +264,6 @@ int llama_schedule_static(llama_ctx *ctx, int64_t n_inv, const int32_t *dag,
 int llama_set_tuning(llama_ctx *ctx, int32_t lanes_min_vectors, int32_t inv_per_thread,
                      int32_t chunk_entries, int32_t stages);
 
-/* Launch plan of a scan call (no counterpart in the paper; changes speed,
- * never results).  on = 1 (default): when the profiles have at most 2048
- * operations, llama_schedule, llama_schedule_async and llama_schedule_static
- * run the whole call as ONE cooperative kernel launch that fills the GPU:
- * critical paths and the per-op counts, a barrier, every scoring block lays
- * out the buckets itself and takes an equal share of the work, the
- * invocations are placed, a grid barrier, then the scoring, where each
- * invocation's slack is computed as its pass starts.
- * on = 0: two launches (a cooperative bucketing kernel that also computes the
- * slack, then the persistent scoring kernel).  Calls on workspaces
- * (llama_schedule_ws_async), which are meant to run beside each other, always
- * take the two-launch path.  Errors: EINVAL. */
-int llama_set_fusion(llama_ctx *ctx, int32_t on);
-
 /* Method of the selection step (a4).  SCAN (default): every configuration of
  * the invocation's operation is scored (Eq. 1, Section 4.2), tables staged
  * through shared memory and shared by the op's invocations.  STAIRCASE: an
@@ -312,8 +298,7 @@ int llama_slack(llama_ctx *ctx, int64_t n_inv, const int32_t *dag, const int32_t
  * handles; once set, every scheduling call records them on its stream at
  * the phase boundaries: [0] call start, [1] after the bucketing kernel
  * (critical path, counting per operation, bucket layout, slack), [2] after
- * the scoring kernel (a fused call, one launch, records [1] and [2] both
- * after its kernel).  Traced calls launch their kernels directly (no CUDA
+ * the scoring kernel.  Traced calls launch their kernels directly (no CUDA
  * graph) and the scoring kernel no longer overlaps the end of the bucketing
  * kernel.  n_events = 0 turns tracing off.  The events must stay valid while
  * tracing is on.  Errors: EINVAL. */

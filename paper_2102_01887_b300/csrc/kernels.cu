@@ -131,42 +131,18 @@ struct CpWarpSmem {
 static_assert(sizeof(CpWarpSmem) * (256 / 32) <= sizeof(CpSmem), "warp slices exceed the block's area");
 
 __device__ void critical_path_of_dag_warp(const DevProblem &P, int64_t off, int nw, CpWarpSmem &w) {
-    constexpr int kOwn = kCpWarpOps / 32;  // ops per lane: v = lane + 32*j
     const int lane = threadIdx.x & 31;
     for (int k = lane; k < nw; k += 32) w.pk[k] = P.dag_pack[off + k];
     __syncwarp();
     const int lo = w.pk[0], n = w.pk[1], ne = w.pk[2], nl = w.pk[3];
     const int32_t *gidx = w.pk + 4, *rp = gidx + n, *col = rp + n + 1, *ord = col + ne, *lvl = ord + n;
     for (int k = lane; k < n; k += 32) w.ref[k] = (int64_t)P.lat[gidx[k]];
-    // height of every op (its level), parked in cp[] until the levels run: the
-    // op at position p of the height order is in the last level starting at or
-    // before p
-    for (int p = lane; p < n; p += 32) {
-        int a = 0, b = nl - 1;
-        while (a < b) {
-            const int mid = (a + b + 1) >> 1;
-            if (lvl[mid] <= p) a = mid; else b = mid - 1;
-        }
-        w.cp[ord[p]] = a;
-    }
-    __syncwarp();
-    // each lane keeps its ops' heights and successor ranges in registers
-    int hv[kOwn], e0[kOwn], e1[kOwn];
-#pragma unroll
-    for (int j = 0; j < kOwn; ++j) {
-        const int v = lane + 32 * j;
-        hv[j] = v < n ? (int)w.cp[v] : -1;
-        e0[j] = v < n ? rp[v] : 0;
-        e1[j] = v < n ? rp[v + 1] : 0;
-    }
     __syncwarp();
     for (int l = 0; l < nl; ++l) {
-#pragma unroll
-        for (int j = 0; j < kOwn; ++j) {
-            if (hv[j] != l) continue;
-            const int v = lane + 32 * j;
+        for (int p = lvl[l] + lane; p < lvl[l + 1]; p += 32) {
+            const int v = ord[p];
             int64_t best = 0;
-            for (int e = e0[j]; e < e1[j]; ++e) best = max(best, w.cp[col[e]]);
+            for (int e = rp[v]; e < rp[v + 1]; ++e) best = max(best, w.cp[col[e]]);
             w.cp[v] = w.ref[v] + best;
         }
         __syncwarp();
@@ -447,41 +423,6 @@ __device__ __forceinline__ void scatter_invocation(const DevProblem &P, const Bu
     for (int h = 0; h < H; ++h) S.b_slack[pos * H + h] = slack_of(ref, cp, mg, rbase - P.q[h]);
 }
 
-// One parallel round of L2 prefetches, by thread `base` of `step`, of every
-// small array the call's dependent load chains touch (each line starts inside
-// its array).
-__device__ __forceinline__ void prefetch_small_arrays(const DevProblem &P, int64_t base, int64_t step) {
-    int64_t l = base;
-#pragma unroll 1
-    for (int a = 0; a < kPfArrays; ++a) {
-        const int64_t lines = (P.pf_bytes[a] + 127) / 128;
-        for (; l < lines; l += step)
-            asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(P.pf_ptr[a] + 128 * l));
-        l -= lines;
-    }
-}
-
-// Pull the encoded tables into L2 while the buckets are laid out, so the
-// scoring's staging does not wait on DRAM (when they fit half of L2; the host
-// sets their size to zero otherwise).  Thread `base` of `stride`.
-__device__ __forceinline__ void prefetch_tables(const DevProblem &P, int64_t base, int64_t stride) {
-    if (P.prefetch_table_bytes <= 0) return;
-    // lrb, rf (, df): prefetch_table_bytes each; dlat: twice that; every
-    // prefetched line starts inside its array
-    const int64_t rank_lines = (P.prefetch_table_bytes + 127) / 128;
-    const int64_t dlat_lines = (2 * P.prefetch_table_bytes + 127) / 128;
-    const int n_arr = P.df ? 3 : 2;
-    const int64_t n_rank = rank_lines * n_arr;
-    for (int64_t l = base; l < n_rank + dlat_lines; l += stride) {
-        const int64_t a = l % n_arr, r = l / n_arr;
-        const char *ptr = l >= n_rank ? reinterpret_cast<const char *>(P.dlat) + 128 * (l - n_rank)
-                          : a == 0   ? reinterpret_cast<const char *>(P.lrb) + 128 * r
-                          : a == 1   ? reinterpret_cast<const char *>(P.rf) + 128 * r
-                                     : reinterpret_cast<const char *>(P.df) + 128 * r;
-        asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(ptr));
-    }
-}
-
 // The bucketing step of a call, one cooperative launch (all blocks resident):
 //  1. blocks [0, n_cp) compute the critical paths (a warp per small DAG); the
 //     other blocks validate invocations, count them per op (one counter per
@@ -503,7 +444,18 @@ __global__ void __launch_bounds__(256) k_bucket(DevProblem P, int64_t n_inv, con
                                                 int32_t n_cp) {
     __shared__ int32_t warp_sum[3][32];
     __shared__ CpSmem sm;
-    prefetch_small_arrays(P, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+    {
+        // one parallel round of L2 prefetches of every small array the dependent
+        // load chains below will touch (each line starts inside its array)
+        int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+        const int64_t step = (int64_t)gridDim.x * blockDim.x;
+#pragma unroll 1
+        for (int a = 0; a < kPfArrays; ++a) {
+            for (; l < P.pf_lines[a]; l += step)
+                asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(P.pf_ptr[a] + 128 * l));
+            l -= P.pf_lines[a];
+        }
+    }
     if ((int)blockIdx.x < n_cp) {
         critical_paths_of_block(P, blockIdx.x, n_cp, topo, lvl_off, dag_lvl, sm);
         grid_barrier(&S.ctrl[kCtrlBarrier], gridDim.x, &S.ctrl[kCtrlTimeout]);
@@ -528,7 +480,21 @@ __global__ void __launch_bounds__(256) k_bucket(DevProblem P, int64_t n_inv, con
         int64_t rb;
         count_invocation(P, i, dag, op_local, start, now, S, out, g, sl, rb);
     }
-    prefetch_tables(P, base, stride);
+    // Pull the encoded tables into L2 while the buckets are laid out, so the
+    // scoring kernel's staging does not wait on DRAM.
+    if (P.prefetch_rank_lines > 0) {
+        // lrb, rf (, df): 2*n_pad bytes each; dlat: 4*n_pad bytes; every
+        // prefetched line starts inside its array
+        const char *arr[3] = {reinterpret_cast<const char *>(P.lrb), reinterpret_cast<const char *>(P.rf),
+                              reinterpret_cast<const char *>(P.df)};
+        const int n_arr = P.df ? 3 : 2;
+        const int64_t n_rank = P.prefetch_rank_lines * n_arr;
+        for (int64_t l = base; l < n_rank + P.prefetch_dlat_lines; l += stride) {
+            const char *a = l < n_rank ? arr[l % n_arr] + 128 * (l / n_arr)
+                                       : reinterpret_cast<const char *>(P.dlat) + 128 * (l - n_rank);
+            asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(a));
+        }
+    }
     // the counting blocks lay out the buckets and tiles between two barriers of
     // their own (the critical-path blocks do not take part)
     const int32_t cb = (int32_t)(blockIdx.x - n_cp);
@@ -663,8 +629,7 @@ __device__ __forceinline__ void finish_call(const BucketScratch &S) {
             __threadfence();
             S.status[0] = atomicAdd(&S.ctrl[kCtrlInvalid], 0ull);
             S.status[1] = atomicAdd(&S.ctrl[kCtrlTimeout], 0ull);
-            for (int k = 0; k < 8; ++k) atomicExch(&S.ctrl[k], 0ull);
-            for (int k = kCtrlCountArrive; k < kCtrlWords; k += 16) atomicExch(&S.ctrl[k], 0ull);
+            for (int k = 0; k < kCtrlWords; ++k) atomicExch(&S.ctrl[k], 0ull);
         }
     }
 }
@@ -679,23 +644,11 @@ struct TileState {
     int32_t inv[IPT];
     uint32_t best[IPT];
     bool any;
-    // fused path only: each invocation's remaining time before queueing,
-    // max(0, SLO - elapsed), and the op's reference latency, critical path and
-    // its division constant, from which the slack is computed per backend
-    int32_t rb[IPT];
-    int64_t ref, cp;
-    uint64_t mg;
-    const int64_t *q;  // queueing time per backend (the fused kernel's copy in shared memory)
 };
 
-// The tile list and the buckets are read through L2 only (ld.global.cg): in the
-// fused kernel other CTAs of the same launch wrote them.  FUSED: the bucket
-// entry after the invocation index is its remaining time, and the op's
-// critical path (written by the same launch) is read for the slack.
-template <int IPT, bool FUSED>
-__device__ __forceinline__ void tile_begin(const DevProblem &P, const BucketScratch &S, long long ti,
-                                           TileState<IPT> &T) {
-    const int4 tile = __ldcg(&S.tiles[2 * ti]), tx = __ldcg(&S.tiles[2 * ti + 1]);
+template <int IPT>
+__device__ __forceinline__ void tile_begin(const BucketScratch &S, long long ti, TileState<IPT> &T) {
+    const int4 tile = S.tiles[2 * ti], tx = S.tiles[2 * ti + 1];
     T.v = tile.x;
     T.m = tile.z;
     T.lg = tile.w;
@@ -706,21 +659,14 @@ __device__ __forceinline__ void tile_begin(const DevProblem &P, const BucketScra
     T.dn = tx.y;
     T.p0 = tx.z;
     T.cbase = tx.w;
-    T.q = P.q;
     T.any = false;
     T.pos0 = tile.y + T.g * IPT;
 #pragma unroll
     for (int u = 0; u < IPT; ++u) {
         const int32_t j = T.g * IPT + u;
-        T.inv[u] = j < T.m ? __ldcg(&S.b_inv[tile.y + j]) : -1;
-        if (FUSED) T.rb[u] = j < T.m ? __ldcg(&S.b_slack[tile.y + j]) : 0;
+        T.inv[u] = j < T.m ? S.b_inv[tile.y + j] : -1;
         T.any |= T.inv[u] >= 0;
         T.best[u] = 0xFFFFFFFFu;
-    }
-    if (FUSED) {
-        T.ref = __ldcg(&P.ref[T.v]);
-        T.cp = __ldcg(&P.cp[T.v]);
-        T.mg = __ldcg(reinterpret_cast<const unsigned long long *>(&P.cp_magic[T.v]));
     }
 }
 
@@ -733,62 +679,17 @@ __device__ __forceinline__ int32_t inv_at(const TileState<IPT> &T, int u) {
     return iu;
 }
 
-// Slack of the tile's invocation u for backend h (Algorithm 1): stored beside
-// the bucket entry by the two-kernel path; computed here from the remaining
-// time and the op's critical path by the fused path.
-template <int IPT, bool FUSED>
-__device__ __forceinline__ int32_t slack_at(const DevProblem &P, const BucketScratch &S,
-                                            const TileState<IPT> &T, int u, int h) {
-    if (!FUSED) return S.b_slack[(int64_t)(T.pos0 + u) * P.n_hw + h];
-    int32_t r = T.rb[0];
-#pragma unroll
-    for (int w = 1; w < IPT; ++w) r = u == w ? T.rb[w] : r;
-    return slack_of(T.ref, T.cp, T.mg, (int64_t)r - T.q[h]);
-}
-
 // Counts c(u, h) of distinct latencies below the slack of invocation u for
 // backend h, into cg[u * H + h], from the sorted list dl (shared memory: the
 // lanes of a group share the bisections).
-template <int IPT, bool FUSED>
-__device__ __forceinline__ void counts_from_shared(const DevProblem &P, const BucketScratch &S,
-                                                   const TileState<IPT> &T, int H, const int32_t *dl,
-                                                   uint16_t *cg) {
+template <int IPT>
+__device__ __forceinline__ void counts_from_shared(const BucketScratch &S, const TileState<IPT> &T, int H,
+                                                   const int32_t *dl, uint16_t *cg) {
     if (!T.any) return;
-    // a lane's searches (t = s, s + L, ...) run in lockstep, four at a time, so
-    // their shared-memory loads overlap
-    constexpr int kB = 4;
-    for (int t0 = T.s; t0 < IPT * H; t0 += kB * T.L) {
-        int32_t sl[kB], lo[kB], hi[kB];
-#pragma unroll
-        for (int q = 0; q < kB; ++q) {
-            const int t = t0 + q * T.L, u = t / H, h = t - u * H;
-            const bool act = t < IPT * H && inv_at(T, u) >= 0;
-            sl[q] = act ? slack_at<IPT, FUSED>(P, S, T, u, h) : 0;
-            lo[q] = 0;
-            hi[q] = act ? T.dn : 0;
-        }
-        for (;;) {
-            int32_t val[kB];
-            bool more = false;
-#pragma unroll
-            for (int q = 0; q < kB; ++q) {  // all loads first
-                const bool a = lo[q] < hi[q];
-                more |= a;
-                val[q] = a ? dl[(lo[q] + hi[q]) >> 1] : 0;
-            }
-            if (!more) break;
-#pragma unroll
-            for (int q = 0; q < kB; ++q) {
-                if (lo[q] >= hi[q]) continue;
-                const int32_t mid = (lo[q] + hi[q]) >> 1;
-                if (val[q] < sl[q]) lo[q] = mid + 1; else hi[q] = mid;
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < kB; ++q) {
-            const int t = t0 + q * T.L;
-            if (t < IPT * H) cg[t] = (uint16_t)lo[q];  // 0 for an empty group slot
-        }
+    for (int t = T.s; t < IPT * H; t += T.L) {
+        const int u = t / H, h = t - u * H;
+        const int32_t iu = inv_at(T, u);
+        cg[t] = iu >= 0 ? (uint16_t)count_below(dl, T.dn, S.b_slack[(int64_t)(T.pos0 + u) * H + h]) : 0;
     }
 }
 
@@ -798,7 +699,7 @@ __device__ __forceinline__ void counts_from_shared(const DevProblem &P, const Bu
 // l < G (strictly increasing, the last one at lo + n - 1); over n <= G
 // candidates it probes each one.  Only shifts: G is a power of two and
 // (l+1)n < 2^19.  Every thread of the CTA must call this (warp votes).
-template <int IPT, bool FUSED>
+template <int IPT>
 __device__ __forceinline__ void counts_from_global(const DevProblem &P, const BucketScratch &S,
                                                    const TileState<IPT> &T, int H, const int32_t *dl,
                                                    uint16_t *cg) {
@@ -811,7 +712,7 @@ __device__ __forceinline__ void counts_from_global(const DevProblem &P, const Bu
         const int t = t0 + sw, u = t / H, h = t - u * H;
         const int32_t iu = inv_at(T, u);
         const bool act = t < nc && iu >= 0;
-        const int32_t sl = act ? slack_at<IPT, FUSED>(P, S, T, u, h) : 0;
+        const int32_t sl = act ? S.b_slack[(int64_t)(T.pos0 + u) * H + h] : 0;
         int32_t lo = 0, hi = act ? T.dn : 0;  // lo <= count <= hi
         if (G == 1) {  // one lane per invocation (tile-uniform): bisection
             lo = hi = act ? count_below(dl, T.dn, sl) : 0;
@@ -879,10 +780,10 @@ __device__ __forceinline__ void scan_chunk(const DevProblem &P, TileState<IPT> &
 
 // Reduce each group's keys and decode them into decisions.  Every thread of
 // the CTA must call this (a block barrier when groups span several warps).
-template <int MODE, int IPT, bool FUSED>
+template <int MODE, int IPT>
 __device__ __forceinline__ void finish_tile(const DevProblem &P, const BucketScratch &S, llama_decision *out,
                                             const TileState<IPT> &T, uint32_t (*red)[kScoreThreads / 32]) {
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, H = P.n_hw;
     uint32_t key[IPT];
     const int wl = T.L < 32 ? T.L : 32;
 #pragma unroll
@@ -907,7 +808,7 @@ __device__ __forceinline__ void finish_tile(const DevProblem &P, const BucketScr
         int4 d;
         if (MODE == LLAMA_MODE_ALPHA) d = P.dec[2 * (int64_t)T.cbase + key[u]];
         else d = key[u] < 0x8000u ? P.dec[(int64_t)T.cbase + key[u]] : P.dfast[T.v];
-        const int32_t sl = slack_at<IPT, FUSED>(P, S, T, u, d.x >> 16);
+        const int32_t sl = S.b_slack[(int64_t)(T.pos0 + u) * H + (d.x >> 16)];
         llama_decision dsn;
         dsn.cfg = d.x & 0xFFFF;
         dsn.lat = d.y;
@@ -938,17 +839,16 @@ __device__ __forceinline__ void stage_chunk(const DevProblem &P, int64_t p0, int
     if (MODE == LLAMA_MODE_ALPHA) bulk_g2s(df_s, P.df + p0 + c0, 2u * cn, bar);
 }
 
-__host__ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+__device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 // One staging buffer.  Persistent CTAs take tiles from the tile list: first
 // tile blockIdx.x, the next ones from an atomic counter, so CTAs that finish
 // early take more (the list is ordered longest first).  While the first chunk
-// lands, the distinct latencies are searched.  The caller has made the tile
-// list and the buckets visible and clears the control words afterwards.
-template <int MODE, int IPT, bool FUSED>
-__device__ __forceinline__ void score_tiles(const DevProblem &P, const BucketScratch &S,
-                                            llama_decision *out, int32_t chunk, int32_t dl_cap,
-                                            unsigned char *smem_raw) {
+// lands, the distinct latencies are searched.
+template <int MODE, int IPT>
+__device__ __forceinline__ void score_body(const DevProblem &P, const BucketScratch &S,
+                                           llama_decision *out, int32_t chunk, int32_t dl_cap) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     // chunk entries: latency ranks, feasible-branch ranks (, rank differences);
     // the op's distinct latencies; per group, the counts of each invocation
     uint16_t *lr_s = reinterpret_cast<uint16_t *>(smem_raw);
@@ -969,18 +869,17 @@ __device__ __forceinline__ void score_tiles(const DevProblem &P, const BucketScr
     __syncthreads();
     uint32_t phase = 0;
     bool ok = true;
-    // two-kernel path: everything k_bucket wrote (tile list, buckets, slack) is
-    // visible only after griddepcontrol.wait; the mbarrier set-up above overlaps
-    // its tail.  Either way the per-op counters are no longer read.
-    if (!FUSED) asm volatile("griddepcontrol.wait;" ::: "memory");
+    // everything k_bucket wrote (tile list, buckets, slack) is visible only after
+    // griddepcontrol.wait; the mbarrier set-up above overlaps its tail
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     clear_counters(P, S);
-    const long long n_tiles = (long long)__ldcg(&S.ctrl[kCtrlTiles]);
+    const long long n_tiles = (long long)S.ctrl[kCtrlTiles];
     long long ti = blockIdx.x;
     TileState<IPT> T;
     while (ti < n_tiles) {
         unsigned long long claim = 0;
         if (tid == 0) claim = atomicAdd(&S.ctrl[kCtrlNextTile], 1ull);  // the tile after this one
-        tile_begin<IPT, FUSED>(P, S, ti, T);
+        tile_begin(S, ti, T);
         const bool dl_staged = T.dn <= dl_cap;
         uint16_t *cg = c_s + T.g * IPT * H;
         for (int32_t c0 = 0; c0 < T.npad; c0 += chunk) {
@@ -988,7 +887,7 @@ __device__ __forceinline__ void score_tiles(const DevProblem &P, const BucketScr
             __syncthreads();  // every thread is done with the previous chunk or tile
             if (tid == 0)
                 stage_chunk<MODE>(P, T.p0, c0, cn, c0 == 0 && dl_staged, T.dn, lr_s, rf_s, df_s, dl_s, bar);
-            if (c0 == 0 && !dl_staged) counts_from_global<IPT, FUSED>(P, S, T, H, P.dlat + T.p0, cg);
+            if (c0 == 0 && !dl_staged) counts_from_global(P, S, T, H, P.dlat + T.p0, cg);
             // every thread must agree before any leaves the barrier sequence
             if (!__syncthreads_and(mbar_wait(bar, phase))) {
                 ok = false;
@@ -996,13 +895,13 @@ __device__ __forceinline__ void score_tiles(const DevProblem &P, const BucketScr
             }
             phase ^= 1u;
             if (c0 == 0 && dl_staged) {
-                counts_from_shared<IPT, FUSED>(P, S, T, H, dl_s, cg);
+                counts_from_shared(S, T, H, dl_s, cg);
                 __syncthreads();
             }
             scan_chunk<MODE, IPT>(P, T, c0, cn, lr_s, rf_s, df_s, cg);
         }
         if (!ok) break;
-        finish_tile<MODE, IPT, FUSED>(P, S, out, T, red);
+        finish_tile<MODE, IPT>(P, S, out, T, red);
         if (tid == 0) next_tile = (long long)(claim + gridDim.x);
         __syncthreads();
         ti = next_tile;
@@ -1013,13 +912,6 @@ __device__ __forceinline__ void score_tiles(const DevProblem &P, const BucketScr
         if (tid == 0) atomicOr(&S.ctrl[kCtrlTimeout], 1ull);
         mbar_wait(bar, phase);
     }
-}
-
-template <int MODE, int IPT>
-__device__ __forceinline__ void score_body(const DevProblem &P, const BucketScratch &S,
-                                           llama_decision *out, int32_t chunk, int32_t dl_cap) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    score_tiles<MODE, IPT, false>(P, S, out, chunk, dl_cap, smem_raw);
     finish_call(S);
 }
 
@@ -1075,7 +967,7 @@ __device__ __forceinline__ void score_body_pipe(const DevProblem &P, const Bucke
         unsigned long long claim = 0;
         if (tid == 0) claim = atomicAdd(&S.ctrl[kCtrlNextTile], 1ull);  // the tile after tn
         const int4 txn = tn < n_tiles ? S.tiles[2 * tn + 1] : make_int4(0, 0, 0, 0);
-        tile_begin<IPT, false>(P, S, ti, T);
+        tile_begin(S, ti, T);
         const bool dl_staged = T.dn <= dl_cap;
         uint16_t *cg = c_s + T.g * IPT * H;
         for (int32_t c0 = 0; c0 < T.npad; c0 += chunk) {
@@ -1089,7 +981,7 @@ __device__ __forceinline__ void score_body_pipe(const DevProblem &P, const Bucke
                 }
                 pending |= 1u << (st ^ 1);
             }
-            if (c0 == 0 && !dl_staged) counts_from_global<IPT, false>(P, S, T, H, P.dlat + T.p0, cg);
+            if (c0 == 0 && !dl_staged) counts_from_global(P, S, T, H, P.dlat + T.p0, cg);
             if (!__syncthreads_and(mbar_wait(bar0 + 8 * st, (phases >> st) & 1u))) {
                 ok = false;
                 break;
@@ -1098,14 +990,14 @@ __device__ __forceinline__ void score_body_pipe(const DevProblem &P, const Bucke
             pending &= ~(1u << st);
             uint16_t *lr = lr_of(st);
             if (c0 == 0 && dl_staged) {
-                counts_from_shared<IPT, false>(P, S, T, H, dl_of(st), cg);
+                counts_from_shared(S, T, H, dl_of(st), cg);
                 __syncthreads();
             }
             scan_chunk<MODE, IPT>(P, T, c0, cn, lr, lr + chunk, lr + 2 * chunk, cg);
             st ^= 1;
         }
         if (!ok) break;
-        finish_tile<MODE, IPT, false>(P, S, out, T, red);
+        finish_tile<MODE, IPT>(P, S, out, T, red);
         if (tid == 0) next_tile = (long long)(claim + gridDim.x);
         __syncthreads();
         ti = tn;
@@ -1147,391 +1039,6 @@ const void *score_kernel(int mode, int ipt, int stages) {
     }
     if (al) return ipt >= 4 ? (const void *)k_score_al4 : ipt == 2 ? (const void *)k_score_al2 : (const void *)k_score_al1;
     return ipt >= 4 ? (const void *)k_score_cf4 : ipt == 2 ? (const void *)k_score_cf2 : (const void *)k_score_cf1;
-}
-
-// ---------------------------------------------------------------------------
-// Fused path: the whole call in one cooperative launch
-// ---------------------------------------------------------------------------
-
-// Split grid barrier on a counter alone on its 128-byte line.  Arrival: after
-// a block barrier, one release add (the block's earlier writes become visible
-// to whoever acquires the count); work that nothing waits for may run between
-// arrival and wait.  Wait: one thread polls the count with acquire loads until
-// all n blocks have arrived, then a block barrier.  Bounded: after
-// kMaxWaitTries polls the block records a timeout and goes on.
-__device__ __forceinline__ void barrier_arrive(unsigned long long *counter) {
-    __syncthreads();
-    if (threadIdx.x == 0) asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(counter), "l"(1ull) : "memory");
-}
-
-__device__ __forceinline__ void barrier_wait(unsigned long long *counter, unsigned long long n,
-                                             unsigned long long *timeout) {
-    if (threadIdx.x == 0) {
-        unsigned long long seen = 0;
-        for (int it = 0; it < kMaxWaitTries; ++it) {
-            asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(seen) : "l"(counter) : "memory");
-            if (seen >= n) break;
-        }
-        if (seen < n) atomicOr(timeout, 1ull);
-    }
-    __syncthreads();
-}
-
-// Work of one invocation of an op in the fused kernel's balance, in units of
-// 8-configuration vectors scanned: the op's vectors plus a fixed share for the
-// slack, the searches and the decode.
-constexpr int kInvCost = 16;
-
-// Layout of the fused kernel's shared memory in a scoring CTA, ops in id order:
-// bucket start (n_ops + 1 entries), work prefix (n_ops + 1), vectors of the
-// padded table (n_ops), the queueing times; then the staging area of one
-// table chunk.
-struct FusedLayout {
-    int32_t *pos;
-    long long *cst;
-    int32_t *nvec;
-    int64_t *q;
-    unsigned char *stage;
-};
-
-__host__ __device__ __forceinline__ size_t fused_layout_bytes(int32_t n_ops) {
-    const size_t a = ((size_t)4 * (n_ops + 1) + 15) & ~size_t(15);
-    const size_t b = ((size_t)8 * (n_ops + 1) + 15) & ~size_t(15);
-    const size_t c = ((size_t)4 * n_ops + 15) & ~size_t(15);
-    return a + b + c + 8 * LLAMA_MAX_HW;
-}
-
-__device__ __forceinline__ FusedLayout fused_layout(unsigned char *smem, int32_t n_ops) {
-    FusedLayout F;
-    const size_t a = ((size_t)4 * (n_ops + 1) + 15) & ~size_t(15);
-    const size_t b = ((size_t)8 * (n_ops + 1) + 15) & ~size_t(15);
-    const size_t c = ((size_t)4 * n_ops + 15) & ~size_t(15);
-    F.pos = reinterpret_cast<int32_t *>(smem);
-    F.cst = reinterpret_cast<long long *>(smem + a);
-    F.nvec = reinterpret_cast<int32_t *>(smem + a + b);
-    F.q = reinterpret_cast<int64_t *>(smem + a + b + c);
-    F.stage = smem + a + b + c + 8 * LLAMA_MAX_HW;
-    return F;
-}
-
-// Exclusive block-wide prefix of one 32-bit and one 64-bit value; returns the
-// block totals.  part holds 2 x 32 words.
-__device__ __forceinline__ void block_scan_2(int32_t x, long long y, int32_t &ex, long long &ey,
-                                             int32_t &tx, long long &ty, long long (*part)[32]) {
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-    int32_t ix = x;
-    long long iy = y;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int32_t ux = __shfl_up_sync(0xffffffffu, ix, o);
-        const long long uy = __shfl_up_sync(0xffffffffu, iy, o);
-        if (lane >= o) ix += ux, iy += uy;
-    }
-    if (lane == 31) part[0][wid] = ix, part[1][wid] = iy;
-    __syncthreads();
-    if (wid == 0) {
-        long long wx = lane < nw ? part[0][lane] : 0, wy = lane < nw ? part[1][lane] : 0;
-        for (int o = 1; o < 32; o <<= 1) {
-            const long long ux = __shfl_up_sync(0xffffffffu, wx, o);
-            const long long uy = __shfl_up_sync(0xffffffffu, wy, o);
-            if (lane >= o) wx += ux, wy += uy;
-        }
-        if (lane < nw) part[0][lane] = wx, part[1][lane] = wy;
-    }
-    __syncthreads();
-    ex = ix - x + (wid > 0 ? (int32_t)part[0][wid - 1] : 0);
-    ey = iy - y + (wid > 0 ? part[1][wid - 1] : 0);
-    tx = (int32_t)part[0][nw - 1];
-    ty = part[1][nw - 1];
-    __syncthreads();  // part is reused
-}
-
-// Bucket layout from the final counts, computed by every scoring CTA for
-// itself, ops in id order: bucket starts and the prefix of the work (each
-// invocation of op v weighs nvec(v) + kInvCost).  The counts and the table
-// sizes are loaded in one round.  Returns the total work.
-__device__ long long fused_layout_prefix(const DevProblem &P, const BucketScratch &S, const FusedLayout &F,
-                                         long long (*part)[32]) {
-    const int n = P.n_ops, T = blockDim.x, tid = threadIdx.x;
-    const int32_t per = (n + T - 1) / T;
-    const int32_t kb = min(n, tid * per), ke = min(n, kb + per);
-    for (int v = kb; v < ke; ++v) {
-        F.pos[v] = __ldcg(&S.cnt[(int64_t)v * kCntStride]);  // the count, until the second pass
-        F.nvec[v] = (int32_t)((__ldg(P.pad_off + v + 1) - __ldg(P.pad_off + v)) / kVec);
-    }
-    int32_t cnt = 0;
-    long long work = 0;
-    for (int v = kb; v < ke; ++v) {
-        cnt += F.pos[v];
-        work += (long long)F.pos[v] * (F.nvec[v] + kInvCost);
-    }
-    int32_t ex, tot;
-    long long ew, totw;
-    block_scan_2(cnt, work, ex, ew, tot, totw, part);
-    for (int v = kb; v < ke; ++v) {
-        const int32_t ck = F.pos[v];
-        F.pos[v] = ex;
-        F.cst[v] = ew;
-        ex += ck;
-        ew += (long long)ck * (F.nvec[v] + kInvCost);
-    }
-    if (tid == 0) {
-        F.pos[n] = tot;
-        F.cst[n] = totw;
-    }
-    __syncthreads();
-    return totw;
-}
-
-// The CTA's share of the work: invocation j of op k belongs to the CTA whose
-// range [lo, hi) holds cst[k] + j*(nvec(k) + kInvCost).  First op whose work
-// can reach lo (binary search).
-__device__ __forceinline__ int32_t fused_first_op(const FusedLayout &F, int32_t n, long long lo) {
-    int32_t a = 0, b = n;  // the last k with cst[k + 1] <= lo lies before the answer
-    while (a < b) {
-        const int32_t mid = (a + b) >> 1;
-        if (F.cst[mid + 1] <= lo) a = mid + 1; else b = mid;
-    }
-    return a;
-}
-
-// Invocations [j0, j1) of op k in [lo, hi).
-__device__ __forceinline__ void fused_segment(const FusedLayout &F, int32_t k, long long lo, long long hi,
-                                              int32_t &j0, int32_t &j1) {
-    const int32_t ck = F.pos[k + 1] - F.pos[k];
-    const long long w = F.nvec[k] + kInvCost, c0 = F.cst[k];
-    j0 = lo <= c0 ? 0 : (int32_t)min((long long)ck, (lo - c0 + w - 1) / w);
-    j1 = hi <= c0 ? 0 : (int32_t)min((long long)ck, (hi - c0 + w - 1) / w);
-}
-
-// Tile state for a pass over m invocations at bucket positions [pos, pos + m)
-// of op v, 2^lg lanes per invocation (loads of what other CTAs of this launch
-// wrote go through L2 only).
-template <int IPT>
-__device__ __forceinline__ void tile_set_fused(const DevProblem &P, const BucketScratch &S, TileState<IPT> &T,
-                                               int32_t v, int32_t pos, int32_t m, int lg, int32_t npad,
-                                               int32_t dn, int64_t p0, int32_t cbase, const int64_t *q) {
-    T.v = v;
-    T.m = m;
-    T.lg = lg;
-    T.L = 1 << lg;
-    T.g = threadIdx.x >> lg;
-    T.s = threadIdx.x & (T.L - 1);
-    T.npad = npad;
-    T.dn = dn;
-    T.p0 = p0;
-    T.cbase = cbase;
-    T.q = q;
-    T.any = false;
-    T.pos0 = pos + T.g * IPT;
-#pragma unroll
-    for (int u = 0; u < IPT; ++u) {
-        const int32_t j = T.g * IPT + u;
-        T.inv[u] = j < m ? __ldcg(&S.b_inv[pos + j]) : -1;
-        T.rb[u] = j < m ? __ldcg(&S.b_slack[pos + j]) : 0;
-        T.any |= T.inv[u] >= 0;
-        T.best[u] = 0xFFFFFFFFu;
-    }
-    T.ref = __ldcg(&P.ref[v]);
-    T.cp = __ldcg(&P.cp[v]);
-    T.mg = __ldcg(reinterpret_cast<const unsigned long long *>(&P.cp_magic[v]));
-}
-
-// Place invocation i in its op's bucket with its remaining time before
-// queueing, max(0, SLO - elapsed) <= SLO < 2^31 (a non-positive remaining time
-// gives slack 0 for every backend, since queueing times are >= 0).
-__device__ __forceinline__ void scatter_remaining(const BucketScratch &S, const int32_t *opst, int64_t i,
-                                                  int32_t g, int32_t slot, int64_t rbase) {
-    const int64_t pos = (int64_t)opst[g] + slot;
-    S.b_inv[pos] = (int32_t)i;
-    S.b_slack[pos] = (int32_t)max(rbase, (int64_t)0);
-}
-
-// The whole scheduling call, one cooperative launch of co-resident CTAs:
-//  1. CTAs [0, n_cp) compute the critical paths (a1), arrive at the final
-//     barrier and finish;
-//  2. the other CTAs (the scoring CTAs) validate and count the invocations per
-//     op (a3) and meet at the counting barrier (no L2 prefetches: measured, they
-//     delay the barrier's release fences more than they save later);
-//  3. once every count is in, every scoring CTA lays out the buckets itself
-//     (whole prefix in shared memory), takes an equal share of the work
-//     (invocations weighted by their op's table size), places its own counted
-//     invocations in their buckets with their remaining time while the TMA
-//     copy of its first table is queued, and arrives at the final barrier;
-//  4. after the final barrier (critical paths and buckets complete) each
-//     scoring CTA scores its share op by op (a4), computing every invocation's
-//     slack per backend as its pass starts (a2, Algorithm 1 through the
-//     critical path).
-template <int MODE, int IPT>
-__device__ __forceinline__ void sched_body(const DevProblem &P, int64_t n_inv, const int32_t *dag,
-                                           const int32_t *op_local, const int64_t *start, int64_t now,
-                                           const BucketScratch &S, llama_decision *out, const int32_t *topo,
-                                           const int32_t *lvl_off, const int32_t *dag_lvl, int32_t n_cp,
-                                           int32_t chunk, int32_t dl_cap) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ long long part[2][32];
-    __shared__ __align__(8) unsigned long long mbar;
-    __shared__ uint32_t red[IPT][kScoreThreads / 32];
-    const int32_t b = (int32_t)blockIdx.x, tid = threadIdx.x, H = P.n_hw;
-    const int32_t n_main = (int32_t)gridDim.x - n_cp;
-    if (b < n_cp) {
-        critical_paths_of_block(P, b, n_cp, topo, lvl_off, dag_lvl, *reinterpret_cast<CpSmem *>(smem_raw));
-        barrier_arrive(&S.ctrl[kCtrlFinalArrive]);  // nothing here waits for the buckets
-        finish_call(S);
-        return;
-    }
-    const int32_t cb = b - n_cp;
-    const FusedLayout F = fused_layout(smem_raw, P.n_ops);
-    const uint32_t bar = smem_addr(&mbar);
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (tid < H) F.q[tid] = P.q[tid];
-    // 2. count, then the counting barrier
-    const int64_t stride = (int64_t)n_main * blockDim.x;
-    const int64_t base = (int64_t)cb * blockDim.x + tid;
-    int32_t kg = -1, ks = 0;
-    int64_t kr = 0;
-    if (base < n_inv) count_invocation(P, base, dag, op_local, start, now, S, out, kg, ks, kr);
-    for (int64_t i = base + stride; i < n_inv; i += stride) {
-        int32_t g, sl;
-        int64_t rb;
-        count_invocation(P, i, dag, op_local, start, now, S, out, g, sl, rb);
-    }
-    barrier_arrive(&S.ctrl[kCtrlCountArrive]);
-    barrier_wait(&S.ctrl[kCtrlCountArrive], (unsigned long long)n_main, &S.ctrl[kCtrlTimeout]);
-    // 3. layout, the CTA's share, the scatter beside the first table's copy
-    const int32_t n_ops = P.n_ops;
-    const long long W = fused_layout_prefix(P, S, F, part);
-    const long long lo = W * cb / n_main, hi = W * (cb + 1) / n_main;
-    int32_t k = fused_first_op(F, n_ops, lo);
-    int32_t j0 = 0, j1 = 0;
-    for (; k < n_ops && F.cst[k] < hi; ++k) {
-        fused_segment(F, k, lo, hi, j0, j1);
-        if (j0 < j1) break;  // skip ops with nothing in [lo, hi)
-    }
-    const bool have = k < n_ops && F.cst[k] < hi && j0 < j1;
-    uint16_t *lr_s = reinterpret_cast<uint16_t *>(F.stage);
-    uint16_t *rf_s = lr_s + chunk;
-    uint16_t *df_s = rf_s + chunk;
-    const size_t tbl = align16((size_t)chunk * (MODE == LLAMA_MODE_ALPHA ? 6 : 4));
-    int32_t *dl_s = reinterpret_cast<int32_t *>(F.stage + tbl);
-    uint16_t *c_s = reinterpret_cast<uint16_t *>(F.stage + tbl + 4 * (size_t)dl_cap);
-    int64_t p0_first = 0;
-    int32_t dn_first = 0;
-    if (have && tid == 0) {  // loads in flight during the scatter
-        p0_first = __ldg(P.pad_off + k);
-        dn_first = __ldg(P.dlat_n + k);
-    }
-    if (kg >= 0) scatter_remaining(S, F.pos, base, kg, ks, kr);
-    for (int64_t i = base + stride; i < n_inv; i += stride) {
-        const int32_t g = S.gop[i];
-        if (g >= 0) scatter_remaining(S, F.pos, i, g, S.slot[i], S.rbase[i]);
-    }
-    // the chunk in the staging buffer: op and first entry; pending: its copy
-    // is in flight
-    int32_t buf_k = -1, buf_c0 = 0;
-    bool pending = false;
-    uint32_t phase = 0;
-    if (have) {
-        if (tid == 0)
-            stage_chunk<MODE>(P, p0_first, 0, min(chunk, F.nvec[k] * kVec), dn_first <= dl_cap, dn_first, lr_s,
-                              rf_s, df_s, dl_s, bar);
-        buf_k = k;
-        pending = true;
-    }
-    // 4.
-    barrier_arrive(&S.ctrl[kCtrlFinalArrive]);
-    barrier_wait(&S.ctrl[kCtrlFinalArrive], (unsigned long long)gridDim.x, &S.ctrl[kCtrlTimeout]);
-    // the counters are no longer read: clear them for the next call
-    for (int64_t v = (int64_t)cb * blockDim.x + tid; v < n_ops; v += stride) S.cnt[v * kCntStride] = 0;
-    // score the share, op by op, in passes of at most kScoreThreads*IPT invocations
-    bool ok = true;
-    TileState<IPT> T;
-    for (; ok && k < n_ops && F.cst[k] < hi; ++k) {
-        fused_segment(F, k, lo, hi, j0, j1);
-        if (j0 >= j1) continue;
-        const int32_t nvec = F.nvec[k], npad = nvec * kVec;
-        const int32_t dn = __ldg(P.dlat_n + k);
-        const int64_t p0 = __ldg(P.pad_off + k);
-        const int32_t cbase = (int32_t)__ldg(P.cfg_off + k);
-        const bool dl_staged = dn <= dl_cap;
-        for (int32_t a = j0; ok && a < j1; a += kScoreThreads * IPT) {
-            const int32_t m = min(j1 - a, kScoreThreads * IPT);
-            const int lg = tail_lanes_log2(m, 0, IPT, nvec);
-            tile_set_fused<IPT>(P, S, T, k, F.pos[k] + a, m, lg, npad, dn, p0, cbase, F.q);
-            uint16_t *cg = c_s + T.g * IPT * H;
-            for (int32_t c0 = 0; c0 < npad; c0 += chunk) {
-                const int32_t cn = min(chunk, npad - c0);
-                if (!(buf_k == k && buf_c0 == c0)) {
-                    __syncthreads();  // every thread is done with the buffer
-                    if (tid == 0)
-                        stage_chunk<MODE>(P, p0, c0, cn, c0 == 0 && dl_staged, dn, lr_s, rf_s, df_s, dl_s, bar);
-                    buf_k = k;
-                    buf_c0 = c0;
-                    pending = true;
-                }
-                if (c0 == 0 && !dl_staged) counts_from_global<IPT, true>(P, S, T, H, P.dlat + p0, cg);
-                if (pending) {
-                    if (!__syncthreads_and(mbar_wait(bar, phase))) {
-                        ok = false;
-                        break;
-                    }
-                    phase ^= 1u;
-                    pending = false;
-                }
-                if (c0 == 0 && dl_staged) {
-                    // the distinct latencies come with the op's first chunk
-                    counts_from_shared<IPT, true>(P, S, T, H, dl_s, cg);
-                    __syncthreads();
-                }
-                scan_chunk<MODE, IPT>(P, T, c0, cn, lr_s, rf_s, df_s, cg);
-            }
-            if (!ok) break;
-            finish_tile<MODE, IPT, true>(P, S, out, T, red);
-            // a later pass of this op restages unless its whole table is staged
-            if (npad > chunk) buf_k = -1;
-            __syncthreads();  // cg is reused
-        }
-    }
-    if (pending) {
-        // a copy that was never waited for (after a timeout): wait (bounded) so
-        // no transfer targets this CTA's shared memory after it exits
-        mbar_wait(bar, phase);
-        if (tid == 0) atomicOr(&S.ctrl[kCtrlTimeout], 1ull);
-    } else if (!ok) {
-        if (tid == 0) atomicOr(&S.ctrl[kCtrlTimeout], 1ull);
-    }
-    finish_call(S);
-}
-
-#define LLAMA_SCHED_KERNEL(name, MODE, IPT)                                                             \
-    __global__ void __launch_bounds__(kScoreThreads, 4)                                                \
-        name(DevProblem P, int64_t n_inv, const int32_t *dag, const int32_t *op_local,                 \
-             const int64_t *start, int64_t now, BucketScratch S, llama_decision *out,                  \
-             const int32_t *topo, const int32_t *lvl_off, const int32_t *dag_lvl, int32_t n_cp,       \
-             int32_t chunk, int32_t dl_cap) {                                                           \
-        sched_body<MODE, IPT>(P, n_inv, dag, op_local, start, now, S, out, topo, lvl_off, dag_lvl,    \
-                              n_cp, chunk, dl_cap);                                                     \
-    }
-LLAMA_SCHED_KERNEL(k_sched_cf1, LLAMA_MODE_COST_FIRST, 1)
-LLAMA_SCHED_KERNEL(k_sched_cf2, LLAMA_MODE_COST_FIRST, 2)
-LLAMA_SCHED_KERNEL(k_sched_cf4, LLAMA_MODE_COST_FIRST, 4)
-LLAMA_SCHED_KERNEL(k_sched_al1, LLAMA_MODE_ALPHA, 1)
-LLAMA_SCHED_KERNEL(k_sched_al2, LLAMA_MODE_ALPHA, 2)
-LLAMA_SCHED_KERNEL(k_sched_al4, LLAMA_MODE_ALPHA, 4)
-#undef LLAMA_SCHED_KERNEL
-
-const void *sched_kernel(int mode, int ipt) {
-    if (mode == LLAMA_MODE_ALPHA)
-        return ipt >= 4 ? (const void *)k_sched_al4 : ipt == 2 ? (const void *)k_sched_al2 : (const void *)k_sched_al1;
-    return ipt >= 4 ? (const void *)k_sched_cf4 : ipt == 2 ? (const void *)k_sched_cf2 : (const void *)k_sched_cf1;
-}
-
-size_t sched_smem_bytes(int mode, int32_t n_ops, int32_t n_hw, int32_t ipt, int32_t chunk, int32_t dl_cap) {
-    const size_t tbl = align16((size_t)chunk * (mode == LLAMA_MODE_ALPHA ? 6 : 4));
-    const size_t stage = tbl + 4 * (size_t)dl_cap + (size_t)kScoreThreads * ipt * n_hw * 2;
-    return std::max(sizeof(CpSmem), fused_layout_bytes(n_ops) + stage);
 }
 
 // ---------------------------------------------------------------------------
@@ -1757,33 +1264,6 @@ cudaError_t enqueue_schedule(const ContextView &v, const BucketScratch &S, int64
         void *args[] = {&P, &n_inv, &dag, &op_local, &start, &now, &Sc, &out};
         e = cudaLaunchKernelExC(&cfg, (const void *)k_stair, args);
         if (e != cudaSuccess) return e;
-        mark(2);
-        return cudaGetLastError();
-    }
-    if (v.fused) {
-        // the whole call in one cooperative launch: critical-path CTAs, then
-        // scoring CTAs up to the co-resident limit (at most one per invocation)
-        const int n_cp = std::max(1, std::min((v.n_dags + 7) / 8, std::max(1, v.sched_grid / 4)));
-        const int grid = n_cp + (int)std::max<int64_t>(1, std::min<int64_t>(n_inv, (int64_t)v.sched_grid - n_cp));
-        cudaLaunchConfig_t cfg{};
-        cfg.gridDim = dim3(grid);
-        cfg.blockDim = dim3(kScoreThreads);
-        cfg.dynamicSmemBytes = v.sched_smem;
-        cfg.stream = s;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeCooperative;
-        attr[0].val.cooperative = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        DevProblem P = v.P;
-        BucketScratch Sc = S;
-        const int32_t *topo = v.topo, *lvl_off = v.lvl_off, *dag_lvl = v.dag_lvl;
-        int32_t ncp = n_cp, chunk = v.score_chunk, dl_cap = v.dlat_cap;
-        void *args[] = {&P, &n_inv, &dag, &op_local, &start, &now, &Sc, &out,
-                        &topo, &lvl_off, &dag_lvl, &ncp, &chunk, &dl_cap};
-        e = cudaLaunchKernelExC(&cfg, sched_kernel(v.mode, v.ipt), args);
-        if (e != cudaSuccess) return e;
-        mark(1);
         mark(2);
         return cudaGetLastError();
     }

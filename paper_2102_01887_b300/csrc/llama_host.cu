@@ -112,10 +112,6 @@ struct llama_ctx {
     // scoring kernel geometry (set by llama_set_profiles)
     int32_t min_vpl = 16, ipt = 2, stages = 1, score_grid = 0, score_chunk = 0, bucket_max_blocks = 0, dlat_cap = 0;
     size_t score_smem = 0;
-    // fused path (llama_set_fusion): one launch per call when the profiles have
-    // at most kFusedMaxOps operations; its co-resident grid and shared memory
-    int32_t fusion = 1, sched_grid = 0;
-    size_t sched_smem = 0;
 
     // staging for host-memory arguments of the blocking calls
     int64_t cap_stage = 0;
@@ -134,7 +130,6 @@ struct llama_ctx {
     cudaGraphExec_t gexec = nullptr;
     cudaGraphNode_t g_bucket = nullptr;  // the captured kernel that takes `now`
     int g_now_nargs = 0;
-    bool g_fused = false;  // the captured call is one fused launch
     int64_t g_n_inv = -1, g_now = 0;
     const void *g_args[4] = {};
 
@@ -198,7 +193,8 @@ DevProblem make_problem(const llama_ctx *c) {
     // prefetch the encoded tables into L2 when they take at most half of it
     const int64_t tbl_bytes = (int64_t)(c->opts.mode == LLAMA_MODE_ALPHA ? 10 : 8) * c->n_pad;
     const bool pf = c->n_pad > 0 && tbl_bytes <= c->l2_bytes / 2;
-    P.prefetch_table_bytes = pf ? 2 * c->n_pad : 0;
+    P.prefetch_rank_lines = pf ? (2 * c->n_pad + 127) / 128 : 0;
+    P.prefetch_dlat_lines = pf ? (4 * c->n_pad + 127) / 128 : 0;
     P.ref_gidx = c->ref_gidx.as<int64_t>();
     P.ord_info = c->ord_info.as<int4>();
     P.ord_cbase = c->ord_cbase.as<int32_t>();
@@ -216,7 +212,7 @@ DevProblem make_problem(const llama_ctx *c) {
         auto add = [&](const DevBuf &b) {
             if (a < kPfArrays && b.p && b.bytes) {
                 P.pf_ptr[a] = static_cast<const char *>(b.p);
-                P.pf_bytes[a] = (int64_t)b.bytes;
+                P.pf_lines[a] = (int64_t)((b.bytes + 127) / 128);
                 ++a;
             }
         };
@@ -226,7 +222,7 @@ DevProblem make_problem(const llama_ctx *c) {
         if (c->dec.bytes <= (size_t)c->l2_bytes / 4) add(c->dec);
         for (; a < kPfArrays; ++a) {
             P.pf_ptr[a] = nullptr;
-            P.pf_bytes[a] = 0;
+            P.pf_lines[a] = 0;
         }
     }
     P.ref = c->ref.as<int64_t>();
@@ -275,9 +271,6 @@ ContextView view_of(const llama_ctx *c) {
     v.score_chunk = c->score_chunk;
     v.dlat_cap = c->dlat_cap;
     v.score_smem = c->score_smem;
-    v.fused = c->fusion && c->method == LLAMA_METHOD_SCAN && c->n_ops <= kFusedMaxOps && c->sched_grid >= 2;
-    v.sched_grid = c->sched_grid;
-    v.sched_smem = c->sched_smem;
     return v;
 }
 
@@ -468,17 +461,6 @@ int configure_score(llama_ctx *c) {
     int nb = 0;
     LL_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kScoreThreads, c->score_smem));
     c->score_grid = c->num_sms * std::max(1, nb);
-    // the fused kernel: its grid must be co-resident (cooperative launch); a
-    // grid of 0 or 1 CTA disables the fused path
-    c->sched_grid = 0;
-    if (c->n_ops <= kFusedMaxOps) {
-        const void *fk = sched_kernel(c->opts.mode, c->ipt);
-        c->sched_smem = sched_smem_bytes(c->opts.mode, c->n_ops, c->opts.n_hw, c->ipt, c->score_chunk, c->dlat_cap);
-        LL_CUDA(c, cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->sched_smem));
-        int nf = 0;
-        LL_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nf, fk, kScoreThreads, c->sched_smem));
-        c->sched_grid = c->num_sms * nf;
-    }
     return LLAMA_OK;
 }
 
@@ -525,11 +507,9 @@ int capture_graph(llama_ctx *c, int64_t n_inv, const int32_t *dag, const int32_t
             // `now` is argument 5 of both k_bucket (14 arguments) and k_stair (8)
             if (p.func == (void *)k_bucket) c->g_bucket = node, c->g_now_nargs = 14;
             if (p.func == (void *)k_stair) c->g_bucket = node, c->g_now_nargs = 8;
-            if (v.fused && p.func == sched_kernel(v.mode, v.ipt)) c->g_bucket = node, c->g_now_nargs = kSchedArgs;
         }
     }
     if (!c->g_bucket) return c->fail(LLAMA_ECUDA, "graph capture: kernel node not found");
-    c->g_fused = v.fused != 0;
     c->g_n_inv = n_inv;
     c->g_now = now;
     c->g_args[0] = dag;
@@ -546,7 +526,7 @@ int launch_schedule(llama_ctx *c, int64_t n_inv, const int32_t *dag, const int32
         const BucketScratch S = make_scratch(c->ws);
         LL_CUDA(c, enqueue_schedule(v, S, n_inv, dag, op_local, start, now, out, s,
                                     c->tracing ? c->trace : nullptr));
-        c->last_launches = v.fused ? 1 : 2;
+        c->last_launches = 2;
         return LLAMA_OK;
     }
     const bool same = c->gexec && c->g_n_inv == n_inv && c->g_args[0] == dag &&
@@ -560,7 +540,7 @@ int launch_schedule(llama_ctx *c, int64_t n_inv, const int32_t *dag, const int32
         c->g_now = now;
     }
     LL_CUDA(c, cudaGraphLaunch(c->gexec, s));
-    c->last_launches = c->g_fused ? 1 : 2;
+    c->last_launches = 2;
     return LLAMA_OK;
 }
 
@@ -988,15 +968,6 @@ extern "C" int llama_set_tuning(llama_ctx *c, int32_t lanes_min_vectors, int32_t
     return configure_score(c);
 }
 
-extern "C" int llama_set_fusion(llama_ctx *c, int32_t on) {
-    if (!c) return LLAMA_EINVAL;
-    if (on != 0 && on != 1) return c->fail(LLAMA_EINVAL, "set_fusion: on must be 0 or 1");
-    DeviceGuard g(c->opts.device);
-    c->drop_graph();
-    c->fusion = on;
-    return LLAMA_OK;
-}
-
 extern "C" int llama_set_method(llama_ctx *c, int32_t method) {
     if (!c) return LLAMA_EINVAL;
     if (method != LLAMA_METHOD_SCAN && method != LLAMA_METHOD_STAIRCASE)
@@ -1185,10 +1156,7 @@ extern "C" int llama_schedule_ws_async(llama_ctx *c, llama_ws *ws, int64_t n_inv
     if (ws->w.cap_ops < c->n_ops + 1 || ws->w.cap_tiles < max_tiles(n_inv, c->n_ops))
         return c->fail(LLAMA_EINVAL, "schedule_ws: workspace sized for fewer operations (profiles changed)");
     DeviceGuard g(c->opts.device);
-    ContextView v = view_of(c);
-    // calls on workspaces run beside each other: the two-kernel path, whose
-    // cooperative bucketing grid is a fraction of the GPU (a fused grid fills it)
-    v.fused = 0;
+    const ContextView v = view_of(c);
     LL_CUDA(c, enqueue_schedule(v, make_scratch(ws->w), n_inv, dag, op_local, start_us, now_us, out,
                                 static_cast<cudaStream_t>(stream), nullptr));
     return LLAMA_OK;

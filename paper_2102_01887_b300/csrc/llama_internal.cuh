@@ -39,7 +39,6 @@ constexpr int kScoreThreadsLog2 = 8;
 constexpr int kMaxChunk = 4096;        // table entries staged at a time by the scoring kernel
 constexpr int kMaxWaitTries = 1 << 20; // bounded mbarrier waits
 constexpr int kKeep = 4;               // invocations a counting thread keeps in registers
-constexpr int kKeepFused = 1;          // the same in the fused kernel (its grid fills the GPU)
 constexpr int kKeepOps = 2;            // ops the layout keeps in registers per thread
 constexpr int kMaxDlatSmem = 4096;     // distinct latencies staged per op (else searched in L2)
 constexpr int kPfArrays = 20;          // arrays k_bucket prefetches into L2 at its start
@@ -53,11 +52,7 @@ constexpr int kCtrlTimeout = 4;    // nonzero: a bounded device wait gave up
 constexpr int kCtrlNextTile = 5;   // dynamic tile counter of the scoring kernel
 constexpr int kCtrlBarrier = 6;    // grid barrier of k_bucket
 constexpr int kCtrlDone = 7;       // CTAs of the scoring kernel that have finished
-// the fused kernel's two grid barriers: an arrival counter each, alone on its
-// 128-byte line (its polls do not queue behind the other control words' atomics)
-constexpr int kCtrlCountArrive = 16;
-constexpr int kCtrlFinalArrive = 32;
-constexpr int kCtrlWords = 48;
+constexpr int kCtrlWords = 8;
 // Status of the last completed call, after the control words: {invalid
 // invocations, nonzero if a bounded device wait gave up}
 constexpr int kStatusWords = 2;
@@ -90,14 +85,14 @@ struct DevProblem {
     const int32_t *fast;
     const int32_t *op_order;  // ops by padded table size, largest first (bucket order)
     int32_t max_npad;  // largest padded op table (entries)
+    // 128-byte lines to pull into L2 before scoring (0: off): of each of lrb, rf
+    // (and df), all 2*n_pad bytes long, and of dlat (4*n_pad bytes)
+    int64_t prefetch_rank_lines, prefetch_dlat_lines;
     // small per-op and per-DAG arrays (and the decode tables when they fit) that
-    // the call's dependent load chains touch: pulled into L2 by bulk prefetches
-    // from one warp as the call starts
+    // the call's dependent load chains touch first: pulled into L2 by every
+    // block of k_bucket at its start, in one parallel round
     const char *pf_ptr[kPfArrays];
-    int64_t pf_bytes[kPfArrays];  // bytes of each (0: unused)
-    // bytes of each of lrb, rf (, df) (2*n_pad; dlat: twice that) when the
-    // encoded tables fit half of L2 and are prefetched too, else 0
-    int64_t prefetch_table_bytes;
+    int64_t pf_lines[kPfArrays];  // 128-byte lines of each (0: unused)
     const int64_t *ref_gidx;      // [n_ops] cfg_off[v] + ref_cfg[v]
     // [n_ops] per bucket-order position k: {op = op_order[k], vectors of its padded
     // table, its padded offset, its number of distinct latencies}
@@ -142,7 +137,6 @@ struct BucketScratch {
     int32_t *slot;            // [n_inv]     rank of the invocation inside its op's bucket
     int32_t *b_inv;           // [n_inv]     invocation at each bucket position
     int32_t *b_slack;         // [n_inv*H]   slack per backend of the invocation at each bucket position
-                              //             (fused path: [n_inv] its remaining time, max(0, SLO - elapsed))
     int64_t *rbase;           // [n_inv]     target - elapsed time of each invocation
     int4 *tiles;              // [2*max_tiles] scoring tiles: {op, first bucket position, m, lanes_log2},
                               // {padded entries, distinct latencies, padded offset, 0}
@@ -182,9 +176,6 @@ struct ContextView {
     int32_t score_chunk;  // table entries staged per chunk
     int32_t dlat_cap;     // distinct latencies the scoring kernel stages (a multiple of 4)
     size_t score_smem;    // dynamic shared memory of the scoring kernel
-    int32_t fused;        // nonzero: the call is one launch of the fused kernel k_sched_*
-    int32_t sched_grid;   // co-resident CTAs of the fused kernel (cooperative launch)
-    size_t sched_smem;    // its dynamic shared memory
 };
 int context_view(llama_ctx *c, ContextView *v);  // LLAMA_OK or the readiness error
 int context_fail(llama_ctx *c, int code, const char *msg);
@@ -215,29 +206,6 @@ LLAMA_DECLARE_SCORE(k_score2_al2)
 LLAMA_DECLARE_SCORE(k_score2_al4)
 #undef LLAMA_DECLARE_SCORE
 const void *score_kernel(int mode, int ipt, int stages);
-// Fused path: the whole call (critical paths, bucketing, slack, scoring) in one
-// cooperative launch, for profiles of at most kFusedMaxOps operations (every
-// scoring CTA keeps the bucket layout of every op in shared memory, 16 bytes
-// per op).  Kernels by objective mode x invocations per thread; one staging
-// buffer.  `now` is argument 5 (graph replays patch it).
-constexpr int kFusedMaxOps = 2048;
-constexpr int kSchedArgs = 14;
-#define LLAMA_DECLARE_SCHED(name)                                                                      \
-    __global__ void name(DevProblem P, int64_t n_inv, const int32_t *dag, const int32_t *op_local,     \
-                         const int64_t *start, int64_t now, BucketScratch S, llama_decision *out,      \
-                         const int32_t *topo, const int32_t *lvl_off, const int32_t *dag_lvl,          \
-                         int32_t n_cp, int32_t chunk, int32_t dl_cap);
-LLAMA_DECLARE_SCHED(k_sched_cf1)
-LLAMA_DECLARE_SCHED(k_sched_cf2)
-LLAMA_DECLARE_SCHED(k_sched_cf4)
-LLAMA_DECLARE_SCHED(k_sched_al1)
-LLAMA_DECLARE_SCHED(k_sched_al2)
-LLAMA_DECLARE_SCHED(k_sched_al4)
-#undef LLAMA_DECLARE_SCHED
-const void *sched_kernel(int mode, int ipt);
-// Dynamic shared memory of the fused kernel: the critical-path CTAs' staging,
-// or a scoring CTA's bucket layout and one staging buffer.
-size_t sched_smem_bytes(int mode, int32_t n_ops, int32_t n_hw, int32_t ipt, int32_t chunk, int32_t dl_cap);
 
 // Scoring tiles a call may lay out (each op: full tiles plus one tail).
 int64_t max_tiles(int64_t n_inv, int32_t n_ops);

@@ -30,7 +30,7 @@ assert DECISION_DTYPE.itemsize == 24
 
 EXPORTS = ("llama_create", "llama_destroy", "llama_set_dags", "llama_set_profiles",
            "llama_set_queue", "llama_schedule", "llama_schedule_async", "llama_schedule_static",
-           "llama_set_tuning", "llama_set_method", "llama_set_fusion", "llama_reserve",
+           "llama_set_tuning", "llama_set_method", "llama_reserve",
            "llama_critical_path", "llama_slack", "llama_set_trace_events", "llama_last_launch_count",
            "llama_last_error", "llama_gemm_bf16", "llama_gemm_error",
            "llama_mlp_create", "llama_mlp_destroy", "llama_mlp_set_params", "llama_mlp_get_params",
@@ -82,7 +82,6 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "llama_schedule_static": ([vp, i64, vp, vp, vp, i64, vp, vp], ctypes.c_int),
             "llama_set_tuning": ([vp, i32, i32, i32, i32], ctypes.c_int),
             "llama_set_method": ([vp, i32], ctypes.c_int),
-            "llama_set_fusion": ([vp, i32], ctypes.c_int),
             "llama_reserve": ([vp, i64], ctypes.c_int),
             "llama_critical_path": ([vp, vp], ctypes.c_int),
             "llama_slack": ([vp, i64, vp, vp, vp, i64, vp], ctypes.c_int),
@@ -386,11 +385,6 @@ def llama_set_method(ctx, method: int) -> None:
     _check(ctx, load().llama_set_method(ctx, int(method)))
 
 
-def llama_set_fusion(ctx, on: bool) -> None:
-    """One launch per scan call (True, the default) or two (False)."""
-    _check(ctx, load().llama_set_fusion(ctx, 1 if on else 0))
-
-
 def llama_reserve(ctx, max_inv: int) -> None:
     _check(ctx, load().llama_reserve(ctx, int(max_inv)))
 
@@ -469,14 +463,12 @@ class Scheduler:
     """A context loaded with one Problem (see ``workloads``)."""
 
     def __init__(self, problem, mode: int = MODE_COST_FIRST, alpha=(1, 1), device: int = 0,
-                 use_graph: bool = False, method: int = METHOD_SCAN, fused: bool = True):
+                 use_graph: bool = False, method: int = METHOD_SCAN):
         self.problem = problem
         self.mode = mode
         self.ctx = llama_create(mode, problem.n_hw, alpha, device, use_graph)
         if method != METHOD_SCAN:
             llama_set_method(self.ctx, method)
-        if not fused:
-            llama_set_fusion(self.ctx, False)
         p = problem
         llama_set_dags(self.ctx, p.dag_op_off, p.row_ptr, p.col, p.slo_us)
         alpha_mode = mode == MODE_ALPHA

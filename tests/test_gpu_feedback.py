@@ -11,10 +11,6 @@ from paper_2102_01887_b300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 FIELDS = ("cfg", "lat", "cost", "slack", "flags")
-# selection method and launch plan: the scan in one fused launch, the scan in
-# two launches, the staircase
-VARIANTS = [dict(method=0), dict(method=0, fused=False), dict(method=1)]
-VARIANT_IDS = ["scan", "scan2", "staircase"]
 
 
 @pytest.fixture(scope="module")
@@ -36,14 +32,14 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-@pytest.mark.parametrize("variant", VARIANTS, ids=VARIANT_IDS)
-def test_queue_time_feeds_the_next_call(L, variant):
+@pytest.mark.parametrize("method", [0, 1], ids=["scan", "staircase"])
+def test_queue_time_feeds_the_next_call(L, method):
     import torch
     p, inv = W.medium()
     p.q_us = np.zeros(p.n_hw, np.int64)
     queued = inv.subset(np.arange(0, inv.n, 3))
     later = inv.subset(np.arange(1, inv.n, 3))
-    with L.Scheduler(p, **variant, use_graph=True) as s:
+    with L.Scheduler(p, method=method, use_graph=True) as s:
         d_q, _ = s.schedule(queued)
         q = torch.zeros(p.n_hw, dtype=torch.int64, device="cuda")
         dec = dev(d_q.view(np.uint8))
@@ -59,8 +55,8 @@ def test_queue_time_feeds_the_next_call(L, variant):
 
 
 @pytest.mark.parametrize("mode,alpha", [(0, (1, 1)), (1, (3, 2))], ids=["cost_first", "alpha"])
-@pytest.mark.parametrize("variant", VARIANTS, ids=VARIANT_IDS)
-def test_feedback_updates_tables_and_decisions(L, mode, alpha, variant):
+@pytest.mark.parametrize("method", [0, 1], ids=["scan", "staircase"])
+def test_feedback_updates_tables_and_decisions(L, mode, alpha, method):
     p, inv = W.medium()
     rng = np.random.default_rng(7)
     n = 40_000
@@ -72,7 +68,7 @@ def test_feedback_updates_tables_and_decisions(L, mode, alpha, variant):
     cost = (p.cost_nd[g] * rng.uniform(0.5, 2.0, n)).astype(np.int64)
     op[:3], cfg[3:5], lat[5] = -1, 10**6, 0  # six invalid observations
     sub = inv.subset(np.arange(0, inv.n, 4))
-    with L.Scheduler(p, mode=mode, alpha=alpha, **variant, use_graph=True) as s:
+    with L.Scheduler(p, mode=mode, alpha=alpha, method=method, use_graph=True) as s:
         before, _ = s.schedule(sub)  # captures the graph that must see the new tables
         import torch
         rej = torch.zeros(1, dtype=torch.int64, device="cuda")
@@ -89,14 +85,14 @@ def test_feedback_updates_tables_and_decisions(L, mode, alpha, variant):
     assert (after["cfg"] != before["cfg"]).any()
 
 
-@pytest.mark.parametrize("variant", VARIANTS, ids=VARIANT_IDS)
-def test_affinity_and_commit_order(L, variant):
+@pytest.mark.parametrize("method", [0, 1], ids=["scan", "staircase"])
+def test_affinity_and_commit_order(L, method):
     import torch
     p, inv = W.medium()
     sub = inv.subset(np.arange(0, inv.n, 160))  # 410 invocations
     sub.dag = sub.dag.copy()
     sub.dag[4] = -1  # one invalid
-    with L.Scheduler(p, alpha=(3, 2), **variant) as s:
+    with L.Scheduler(p, alpha=(3, 2), method=method) as s:
         d, _ = s.schedule(sub)
         dag, opl, st = dev(sub.dag), dev(sub.op_local), dev(sub.start_us)
         obj = torch.empty(sub.n * p.n_hw, dtype=torch.int64, device="cuda")

@@ -31,17 +31,14 @@ def assert_same(got, exp, what=""):
                               f"got {got[bad[:5]]} expected {exp[bad[:5]]}"
 
 
-@pytest.fixture(params=[dict(method=0, fused=True), dict(method=0, fused=False), dict(method=1)],
-                ids=["scan", "scan2", "staircase"])
-def variant(request):
-    """Selection method and launch plan: the scan of every configuration in one
-    fused launch (profiles of up to 2,048 ops; larger ones take two launches)
-    or in two launches, or the staircase."""
+@pytest.fixture(params=[0, 1], ids=["scan", "staircase"])
+def method(request):
+    """Selection method: the scan of every configuration, or the staircase."""
     return request.param
 
 
-def run_both(L, p, inv, mode=0, alpha=(1, 1), variant=None):
-    with L.Scheduler(p, mode=mode, alpha=alpha, **(variant or {})) as s:
+def run_both(L, p, inv, mode=0, alpha=(1, 1), method=0):
+    with L.Scheduler(p, mode=mode, alpha=alpha, method=method) as s:
         got, rc = s.schedule(inv)
     exp, rc_o = oracle.schedule(p, inv, mode=mode, alpha=alpha)
     assert rc == rc_o
@@ -51,10 +48,10 @@ def run_both(L, p, inv, mode=0, alpha=(1, 1), variant=None):
 # ---------------------------------------------------------------- golden ---
 
 @pytest.mark.parametrize("mode", ["cost_first", "alpha"])
-def test_golden_worked_example(L, mode, variant):
+def test_golden_worked_example(L, mode, method):
     g, p, inv = load_golden("amber_worked_example.json")
     m = L.MODE_ALPHA if mode == "alpha" else L.MODE_COST_FIRST
-    with L.Scheduler(p, mode=m, alpha=tuple(g["alpha"]), **variant) as s:
+    with L.Scheduler(p, mode=m, alpha=tuple(g["alpha"]), method=method) as s:
         assert s.critical_path().tolist() == g["expected_critical_path"]
         assert s.slack(inv).tolist() == g["expected_slack"]
         d, rc = s.schedule(inv)
@@ -74,19 +71,13 @@ def test_critical_path_and_slack(L, name):
         assert (s.slack(sub) == oracle.slacks(p, sub)).all()
 
 
-# DAGs of 1 to 1,500 ops (3,133 ops: above the fused kernel's 2,048), and of 1
-# to 600 ops (1,933 ops: fused)
-DAG_SIZE_SETS = {"to1500": {}, "to600": {"sizes": (1, 3, 40, 126, 127, 511, 513, 600, 12)}}
-
-
-@pytest.mark.parametrize("sizes", list(DAG_SIZE_SETS))
 @pytest.mark.parametrize("mode,alpha", [(0, (1, 1)), (1, (3, 2))])
-def test_dags_of_every_size(L, mode, alpha, variant, sizes):
-    # one problem holding DAGs of many sizes: small DAGs take a warp each in
+def test_dags_of_every_size(L, mode, alpha, method):
+    # one problem holding DAGs of 1 to 1,500 ops: small DAGs take a warp each in
     # the critical-path pass, mid-sized ones a block with the DAG in shared
     # memory, and the largest go through global memory
-    p, inv = W.dag_sizes(**DAG_SIZE_SETS[sizes])
-    with L.Scheduler(p, mode=mode, alpha=alpha, **variant) as s:
+    p, inv = W.dag_sizes()
+    with L.Scheduler(p, mode=mode, alpha=alpha, method=method) as s:
         assert (s.critical_path() == oracle.critical_path(p)).all()
         assert (s.slack(inv) == oracle.slacks(p, inv)).all()
         got, rc = s.schedule(inv)
@@ -107,55 +98,55 @@ def test_slack_random_small(L, seed):
 
 @pytest.mark.parametrize("seed", range(40))
 @pytest.mark.parametrize("mode", [0, 1])
-def test_random_small(L, seed, mode, variant):
+def test_random_small(L, seed, mode, method):
     p, inv = W.random_small(seed, max_cfg=24, n_inv=300)
-    got, exp = run_both(L, p, inv, mode, alpha=(1 + seed % 7, 1 + seed % 3), variant=variant)
+    got, exp = run_both(L, p, inv, mode, alpha=(1 + seed % 7, 1 + seed % 3), method=method)
     assert_same(got, exp, f"seed {seed}")
 
 
-def test_tiny(L, variant):
+def test_tiny(L, method):
     p, inv = W.tiny()
-    got, exp = run_both(L, p, inv, variant=variant)
+    got, exp = run_both(L, p, inv, method=method)
     assert_same(got, exp)
 
 
-def test_medium_full(L, variant):
+def test_medium_full(L, method):
     # the benchmark's workload, every invocation
     p, inv = W.medium()
-    got, exp = run_both(L, p, inv, variant=variant)
+    got, exp = run_both(L, p, inv, method=method)
     assert_same(got, exp)
     assert 0.5 < (got["flags"] & 1).mean() < 1.0  # both branches exercised
 
 
-def test_medium_alpha(L, variant):
+def test_medium_alpha(L, method):
     p, inv = W.medium()
     sub = inv.subset(np.arange(0, inv.n, 3))
-    got, exp = run_both(L, p, sub, mode=1, alpha=(3, 2), variant=variant)
+    got, exp = run_both(L, p, sub, mode=1, alpha=(3, 2), method=method)
     assert_same(got, exp)
 
 
 @pytest.mark.slow
-def test_batched_full(L, variant):
+def test_batched_full(L, method):
     p, inv = W.batched()
-    got, exp = run_both(L, p, inv, variant=variant)
+    got, exp = run_both(L, p, inv, method=method)
     assert_same(got, exp)
 
 
 # ------------------------------------------------------------ edge cases ---
 
-def test_empty_call(L, variant):
+def test_empty_call(L, method):
     p, inv = W.tiny()
-    with L.Scheduler(p, **variant) as s:
+    with L.Scheduler(p, method=method) as s:
         d, rc = s.schedule(inv.subset(np.arange(0)))
     assert rc == L.OK and d.shape == (0,)
 
 
-def test_invalid_invocations_mixed_with_valid(L, variant):
+def test_invalid_invocations_mixed_with_valid(L, method):
     g, p, inv = load_golden("amber_worked_example.json")
     bad = W.Invocations(np.asarray([0, 1, 0, 0, -1, 0], np.int32),
                         np.asarray([1, 0, 4, 2, 0, -3], np.int32),
                         np.asarray([9400, 9400, 9400, 10001, 0, 9400], np.int64), 10000)
-    with L.Scheduler(p, **variant) as s:
+    with L.Scheduler(p, method=method) as s:
         d, rc = s.schedule(bad)
     exp, rc_o = oracle.schedule(p, bad)
     assert rc == L.EINVAL == rc_o
@@ -163,24 +154,24 @@ def test_invalid_invocations_mixed_with_valid(L, variant):
     assert d["cfg"].tolist() == [5, -1, -1, -1, -1, -1]
 
 
-def test_all_targets_passed(L, variant):
+def test_all_targets_passed(L, method):
     p, inv = W.medium()
     late = W.Invocations(inv.dag, inv.op_local, np.zeros(inv.n, np.int64), inv.now_us)
-    got, exp = run_both(L, p, late.subset(np.arange(5000)), variant=variant)
+    got, exp = run_both(L, p, late.subset(np.arange(5000)), method=method)
     assert_same(got, exp)
     assert (got["flags"] == 0).all() and (got["slack"] == 0).all()
 
 
-def test_all_ties(L, variant):
+def test_all_ties(L, method):
     # identical latency and cost everywhere: the lowest index must win
     p, inv = W.medium()
     p.lat_us[:] = 1000
     p.cost_nd[:] = 7
-    got, exp = run_both(L, p, inv.subset(np.arange(3000)), variant=variant)
+    got, exp = run_both(L, p, inv.subset(np.arange(3000)), method=method)
     assert_same(got, exp)
 
 
-def test_single_config_ops_and_single_backend_segments(L, variant):
+def test_single_config_ops_and_single_backend_segments(L, method):
     # ops with one configuration, ops whose configurations all sit on one backend
     p = single_table_problem([[1, 2], [3], [3], []], [10, 20, 30, 40], slo=400,
                              extra=[[], [(2, 5, 100), (2, 4, 100), (2, 4, 50)], [(1, 29, 1)],
@@ -190,11 +181,11 @@ def test_single_config_ops_and_single_backend_segments(L, variant):
     inv = W.Invocations(np.zeros(n, np.int32), rng.integers(0, 4, n).astype(np.int32),
                         (10**6 - rng.integers(0, 500, n)).astype(np.int64), 10**6)
     for mode in (0, 1):
-        got, exp = run_both(L, p, inv, mode, variant=variant)
+        got, exp = run_both(L, p, inv, mode, method=method)
         assert_same(got, exp)
 
 
-def test_largest_config_space_with_ties(L, variant):
+def test_largest_config_space_with_ties(L, method):
     # 8,192 configurations per op (the limit), heavy ties, several tiles per op
     p, inv = W.random_small(3, max_dags=1, max_ops=4, max_cfg=2, n_inv=2000, value_range=5000)
     n = 8192
@@ -210,12 +201,12 @@ def test_largest_config_space_with_ties(L, variant):
     p.res = rng.integers(1, 4, size=k * n).astype(np.int32)
     p.slo_us[:] = 20000
     for mode in (0, 1):
-        got, exp = run_both(L, p, inv, mode, alpha=(2, 3), variant=variant)
+        got, exp = run_both(L, p, inv, mode, alpha=(2, 3), method=method)
         assert_same(got, exp)
 
 
 @pytest.mark.parametrize("n_hw", [1, 2, 8])
-def test_backend_counts(L, n_hw, variant):
+def test_backend_counts(L, n_hw, method):
     rng = np.random.default_rng(n_hw)
     p, inv = W.random_small(100 + n_hw, max_cfg=40, n_inv=1000)
     k = p.n_ops
@@ -230,13 +221,13 @@ def test_backend_counts(L, n_hw, variant):
     p.res_total = rng.integers(1, 9, size=n_hw).astype(np.int32)
     assert p.hw_off.shape[0] == k * (n_hw + 1)
     for mode in (0, 1):
-        got, exp = run_both(L, p, inv, mode, alpha=(5, 2), variant=variant)
+        got, exp = run_both(L, p, inv, mode, alpha=(5, 2), method=method)
         assert_same(got, exp)
 
 
 # ---------------------------------------------------- device-side calls ---
 
-def test_device_pointers_and_async_stream(L, variant):
+def test_device_pointers_and_async_stream(L, method):
     import torch
     p, inv = W.medium()
     exp, _ = oracle.schedule(p, inv)
@@ -244,7 +235,7 @@ def test_device_pointers_and_async_stream(L, variant):
     dag = torch.from_numpy(inv.dag).to(dev)
     opl = torch.from_numpy(inv.op_local).to(dev)
     st = torch.from_numpy(inv.start_us).to(dev)
-    with L.Scheduler(p, **variant) as s:
+    with L.Scheduler(p, method=method) as s:
         out = torch.zeros(inv.n * 24, dtype=torch.uint8, device=dev)
         L.llama_schedule(s.ctx, dag, opl, st, inv.now_us, out)  # blocking, device pointers
         got = out.cpu().numpy().view(L.DECISION_DTYPE)
@@ -259,10 +250,10 @@ def test_device_pointers_and_async_stream(L, variant):
         assert L.llama_last_launch_count(s.ctx) >= 1
 
 
-def test_growing_and_shrinking_batches(L, variant):
+def test_growing_and_shrinking_batches(L, method):
     p, inv = W.medium()
     exp, _ = oracle.schedule(p, inv)
-    with L.Scheduler(p, **variant) as s:
+    with L.Scheduler(p, method=method) as s:
         for n in (17, 65536, 1, 4096, 65535):
             idx = np.arange(n)
             got, rc = s.schedule(inv.subset(idx))
@@ -299,7 +290,6 @@ def test_errors(L):
             with pytest.raises(L.LlamaError) as e:
                 L.llama_set_tuning(ctx, *bad)
             assert e.value.code == L.EINVAL, bad
-        assert L.load().llama_set_fusion(ctx, 2) == L.EINVAL
     finally:
         L.llama_destroy(ctx)
 
@@ -329,32 +319,14 @@ def test_method_switch_and_profile_reload(L):
         assert e.value.code == L.EINVAL
 
 
-def test_launch_plan(L):
-    # one launch per call while the profiles have at most 2,048 operations (the
-    # fused kernel), two launches when fusion is off or the profiles are larger;
-    # the same decisions every way
-    for prob, case in (W.medium(), W.dag_sizes(**DAG_SIZE_SETS["to600"]), W.dag_sizes(), W.batched()):
-        case = case.subset(np.arange(0, case.n, max(1, case.n // 20000)))
-        exp, _ = oracle.schedule(prob, case)
-        for fused in (True, False):
-            for graph in (False, True):
-                with L.Scheduler(prob, fused=fused, use_graph=graph) as s:
-                    for _ in range(2):
-                        got, rc = s.schedule(case)
-                        assert rc == L.OK
-                        assert_same(got, exp, f"{prob.n_ops} ops fused={fused} graph={graph}")
-                        want = 1 if fused and prob.n_ops <= 2048 else 2
-                        assert L.llama_last_launch_count(s.ctx) == want
-
-
 # ----------------------------------------------------------- graph replay ---
 
-def test_graph_replay_tracks_now_sizes_and_contents(L, variant):
+def test_graph_replay_tracks_now_sizes_and_contents(L, method):
     # one context in graph mode: the call is captured once per argument set and
     # replayed; `now` is patched per call; staging buffers keep host calls on one graph
     import torch
     p, inv = W.medium()
-    with L.Scheduler(p, use_graph=True, **variant) as s:
+    with L.Scheduler(p, use_graph=True, method=method) as s:
         for k, n in enumerate((65536, 65536, 4096, 4096, 65536)):
             shift = 1000 * k  # later `now`, same elapsed time as before plus the shift
             case = W.Invocations(inv.dag[:n], inv.op_local[:n], inv.start_us[:n], inv.now_us + shift)
@@ -391,8 +363,7 @@ def test_graph_replay_tracks_now_sizes_and_contents(L, variant):
                                     (1024, 1, 0, 1), (16, 2, 64, 1), (2, 4, 8, 1), (8, 1, 136, 1),
                                     (1, 1, 0, 2), (16, 2, 0, 2), (32, 1, 0, 2), (64, 4, 0, 2),
                                     (1024, 2, 0, 2), (16, 2, 64, 2), (2, 1, 8, 2), (8, 4, 136, 2)])
-@pytest.mark.parametrize("fused", [True, False], ids=["fused", "two"])
-def test_tunings_change_no_result(L, tuning, fused):
+def test_tunings_change_no_result(L, tuning):
     # every kernel variant (1/2/4 invocations per thread), lane counts from one
     # to a whole CTA per invocation, and chunked staging of tables larger than
     # the chunk, on ties-heavy random problems and on the benchmark's workload
@@ -405,7 +376,7 @@ def test_tunings_change_no_result(L, tuning, fused):
     for prob, case in ((p, inv), (pm, subm), (pl, invl)):
         for mode in (0, 1):
             exp, _ = oracle.schedule(prob, case, mode=mode, alpha=(2, 3))
-            with L.Scheduler(prob, mode=mode, alpha=(2, 3), fused=fused) as s:
+            with L.Scheduler(prob, mode=mode, alpha=(2, 3)) as s:
                 L.llama_set_tuning(s.ctx, *tuning)
                 got, rc = s.schedule(case)
             assert rc == L.OK
@@ -419,9 +390,9 @@ def batched_large():
 
 @pytest.mark.slow
 @pytest.mark.parametrize("mode,alpha", [(0, (1, 1)), (1, (3, 2))])
-def test_batched_large_full(L, batched_large, mode, alpha, variant):
+def test_batched_large_full(L, batched_large, mode, alpha, method):
     # every op at 8,192 configurations (1.6 GB of tables, far beyond L2), about two
     # invocations per op: the HBM-streaming regime, chunked staging, wide groups
     p, inv = batched_large
-    got, exp = run_both(L, p, inv, mode=mode, alpha=alpha, variant=variant)
+    got, exp = run_both(L, p, inv, mode=mode, alpha=alpha, method=method)
     assert_same(got, exp)
