@@ -41,7 +41,15 @@ SCAN_BYTES_PER_SCORE = 12  # int32 latency + int64 cost per scored configuration
 # kernel, from ncu captures of the kernel sources whose digest is "digest"
 # (profiles/ holds the summaries and the commands); reported as null as soon as
 # the sources differ.  Keys: workload/objective.
-MEASURED_TRAFFIC = {"digest": None}
+MEASURED_TRAFFIC = {
+    "digest": "29742dee85033a27",
+    # profiles/k_bucket_medium.md, profiles/k_score_medium.md
+    "k_bucket:medium/cost_first": 6.812416e6,
+    "k_score:medium/cost_first": 3.184896e6,
+    # profiles/k_score_batched_large_192dags.md: 194.02 MB at 192 DAGs, scaled to
+    # the full launch by its algorithmic bytes (459.50 / 172.25 MB)
+    "k_score:batched_large/cost_first": 194.02e6 * 459.50 / 172.25,
+}
 
 
 def kernel_digest() -> str:

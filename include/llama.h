@@ -229,7 +229,7 @@ int llama_ws_status(llama_ws *ws, int64_t *invalid, int32_t *timeout);
  * latency-bound loop that cannot take the implicit synchronisation of the
  * CUDA allocator, or code running where the allocator must not be entered.
  * This call allocates nothing: its bucketing scratch is one fixed, file-scope
- * device array of about 6 MB, which every GPU that loads the library holds
+ * device array of about 4.2 MB, which every GPU that loads the library holds
  * until the process exits.  Same arguments and results as
  * llama_schedule_async (device pointers, enqueued on `stream`, invalid
  * invocations flagged in `out`), with these limits: n_inv at most

@@ -361,6 +361,61 @@ __device__ void layout_write(const DevProblem &P, const BucketScratch &S, int32_
     }
 }
 
+// Bucket layout with no barrier of its own, for profiles whose bucket starts
+// fit a block's shared memory: every counting block computes the whole prefix
+// over the final counts (ops in bucket order) into op_start_s (by op), and
+// block cb of nc writes the tiles of the ops at bucket-order positions
+// [cb*tper, (cb+1)*tper).  Positions and tile indices are those of
+// layout_sums/layout_write (every op's full tiles first, then the tails).
+// Block 0 publishes the number of tiles.
+__device__ void layout_whole(const DevProblem &P, const BucketScratch &S, int32_t cb, int32_t nc,
+                             int32_t min_vpl, int32_t ipt, int32_t *op_start_s, int32_t (*warp_sum)[32]) {
+    const int n = P.n_ops, T = blockDim.x, tid = threadIdx.x;
+    const int32_t per = (n + T - 1) / T;
+    const int32_t kb = min(n, tid * per), ke = min(n, kb + per);
+    int32_t loc[3] = {0, 0, 0};
+    for (int k = kb; k < ke; ++k) {
+        const int4 oi = P.ord_info[k];
+        const int32_t ck = __ldcg(&S.cnt[(int64_t)oi.x * kCntStride]);
+        int32_t f, t;
+        op_tiles(ck, oi.y, min_vpl, ipt, f, t);
+        loc[0] += ck;
+        loc[1] += f;
+        loc[2] += t;
+    }
+    int32_t excl[3], tot[3];
+    block_scan3(loc, excl, tot, warp_sum);
+    const int32_t tper = (n + nc - 1) / nc;
+    const int32_t t0 = cb * tper, t1 = min(n, t0 + tper);
+    int32_t pos = excl[0], tf = excl[1], tt = tot[1] + excl[2];
+    for (int k = kb; k < ke; ++k) {
+        const int4 oi = P.ord_info[k];
+        const int32_t ck = __ldcg(&S.cnt[(int64_t)oi.x * kCntStride]);
+        const int32_t v = oi.x, nvec = oi.y;
+        const int lg = lanes_log2_for(nvec, min_vpl);
+        const int32_t per_tile = (kScoreThreads >> lg) * ipt;
+        const int32_t full = full_tiles(ck, lg, ipt), rest = ck - full * per_tile;
+        op_start_s[v] = pos;
+        if (k >= t0 && k < t1) {
+            // {padded entries, distinct latencies, padded offset, first configuration}
+            const int4 tx = make_int4(nvec * kVec, oi.w, oi.z, __ldg(P.ord_cbase + k));
+            for (int32_t j = 0; j < full; ++j) {
+                S.tiles[2 * (tf + j)] = make_int4(v, pos + j * per_tile, per_tile, lg);
+                S.tiles[2 * (tf + j) + 1] = tx;
+            }
+            if (rest > 0) {
+                S.tiles[2 * tt] = make_int4(v, pos + full * per_tile, rest, tail_lanes_log2(rest, lg, ipt, nvec));
+                S.tiles[2 * tt + 1] = tx;
+            }
+        }
+        tf += full;
+        tt += rest > 0 ? 1 : 0;
+        pos += ck;
+    }
+    if (cb == 0 && tid == 0) S.ctrl[kCtrlTiles] = (unsigned long long)(tot[1] + tot[2]);
+    __syncthreads();  // op_start_s complete
+}
+
 // All blocks of a cooperative launch reach this point before any continues.
 // Bounded: after kMaxWaitTries polls the block records a timeout and goes on
 // (the call's results are then invalid and the host reports ETIMEOUT).
@@ -411,16 +466,16 @@ __device__ __forceinline__ void count_invocation(const DevProblem &P, int64_t i,
     S.rbase[i] = rbase;
 }
 
-// Place invocation i in its op's bucket and store its slack for every backend
-// (Algorithm 1 through the critical path) beside it, at the bucket position.
-__device__ __forceinline__ void scatter_invocation(const DevProblem &P, const BucketScratch &S, int64_t i,
+// Place invocation i in its op's bucket (op_start: first bucket position of
+// every op) with its remaining time before queueing, max(0, SLO - elapsed)
+// <= SLO < 2^31.  The scoring kernel turns it into the slack per backend
+// (Algorithm 1 through the critical path); a non-positive remaining time gives
+// slack 0 for every backend, since queueing times are >= 0.
+__device__ __forceinline__ void scatter_invocation(const BucketScratch &S, const int32_t *op_start, int64_t i,
                                                    int32_t g, int32_t slot, int64_t rbase) {
-    const int64_t pos = S.op_start[g] + slot;
+    const int64_t pos = (int64_t)op_start[g] + slot;
     S.b_inv[pos] = (int32_t)i;
-    const int64_t ref = P.ref[g], cp = P.cp[g];
-    const uint64_t mg = P.cp_magic[g];
-    const int H = P.n_hw;
-    for (int h = 0; h < H; ++h) S.b_slack[pos * H + h] = slack_of(ref, cp, mg, rbase - P.q[h]);
+    S.b_rem[pos] = (int32_t)max(rbase, (int64_t)0);
 }
 
 // The bucketing step of a call, one cooperative launch (all blocks resident):
@@ -457,8 +512,9 @@ __global__ void __launch_bounds__(256) k_bucket(DevProblem P, int64_t n_inv, con
         }
     }
     if ((int)blockIdx.x < n_cp) {
+        // nothing in this kernel waits for the critical paths: the scoring
+        // kernel reads them after griddepcontrol.wait
         critical_paths_of_block(P, blockIdx.x, n_cp, topo, lvl_off, dag_lvl, sm);
-        grid_barrier(&S.ctrl[kCtrlBarrier], gridDim.x, &S.ctrl[kCtrlTimeout]);
         return;
     }
     // counting blocks: each thread takes invocations base, base + stride, ...;
@@ -495,24 +551,36 @@ __global__ void __launch_bounds__(256) k_bucket(DevProblem P, int64_t n_inv, con
             asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(a));
         }
     }
-    // the counting blocks lay out the buckets and tiles between two barriers of
-    // their own (the critical-path blocks do not take part)
+    // the counting blocks lay out the buckets and tiles (the critical-path
+    // blocks do not take part): once the counts are final, either every block
+    // computes the whole layout itself (bucket starts in shared memory, in the
+    // critical-path staging area these blocks do not use), or, for more ops,
+    // per-block sums, prefixes over the blocks and the writes between two more
+    // barriers of the counting blocks
     const int32_t cb = (int32_t)(blockIdx.x - n_cp);
     grid_barrier(&S.ctrl[kCtrlCountBarrier], (unsigned long long)nb, &S.ctrl[kCtrlTimeout]);
-    LayoutRun R;
-    layout_sums(P, S, cb, (int32_t)nb, min_vpl, ipt, R, warp_sum);
-    grid_barrier(&S.ctrl[kCtrlCountBarrier], 2ull * (unsigned long long)nb, &S.ctrl[kCtrlTimeout]);
-    layout_write(P, S, cb, (int32_t)nb, min_vpl, ipt, R, warp_sum);
-    grid_barrier(&S.ctrl[kCtrlBarrier], gridDim.x, &S.ctrl[kCtrlTimeout]);
+    const int32_t *op_start;
+    if (P.n_ops <= kLayoutSmemOps) {
+        int32_t *op_start_s = reinterpret_cast<int32_t *>(&sm);
+        layout_whole(P, S, cb, (int32_t)nb, min_vpl, ipt, op_start_s, warp_sum);
+        op_start = op_start_s;
+    } else {
+        LayoutRun R;
+        layout_sums(P, S, cb, (int32_t)nb, min_vpl, ipt, R, warp_sum);
+        grid_barrier(&S.ctrl[kCtrlCountBarrier], 2ull * (unsigned long long)nb, &S.ctrl[kCtrlTimeout]);
+        layout_write(P, S, cb, (int32_t)nb, min_vpl, ipt, R, warp_sum);
+        grid_barrier(&S.ctrl[kCtrlCountBarrier], 3ull * (unsigned long long)nb, &S.ctrl[kCtrlTimeout]);
+        op_start = S.op_start;
+    }
 
     // let the scoring kernel start staging its tables while the scatter runs
     asm volatile("griddepcontrol.launch_dependents;");
 #pragma unroll
     for (int j = 0; j < kKeep; ++j)
-        if (kg[j] >= 0) scatter_invocation(P, S, base + j * stride, kg[j], ks[j], kr[j]);
+        if (kg[j] >= 0) scatter_invocation(S, op_start, base + j * stride, kg[j], ks[j], kr[j]);
     for (int64_t i = base + kKeep * stride; i < n_inv; i += stride) {
         const int32_t g = S.gop[i];
-        if (g >= 0) scatter_invocation(P, S, i, g, S.slot[i], S.rbase[i]);
+        if (g >= 0) scatter_invocation(S, op_start, i, g, S.slot[i], S.rbase[i]);
     }
 }
 
@@ -646,8 +714,19 @@ struct TileState {
     bool any;
 };
 
+// What every thread of a tile needs for the slack, in shared memory: the
+// queueing time per backend (per call) and the tile's op's reference latency,
+// critical path and floor((2^64-1) / critical path) (per tile, written by one
+// thread in tile_begin; a block barrier separates it from the readers).
+struct TileConst {
+    int64_t ref, cp;
+    uint64_t mg;
+    int64_t q[LLAMA_MAX_HW];
+};
+
 template <int IPT>
-__device__ __forceinline__ void tile_begin(const BucketScratch &S, long long ti, TileState<IPT> &T) {
+__device__ __forceinline__ void tile_begin(const DevProblem &P, const BucketScratch &S, long long ti,
+                                           TileConst &tc, TileState<IPT> &T) {
     const int4 tile = S.tiles[2 * ti], tx = S.tiles[2 * ti + 1];
     T.v = tile.x;
     T.m = tile.z;
@@ -668,6 +747,11 @@ __device__ __forceinline__ void tile_begin(const BucketScratch &S, long long ti,
         T.any |= T.inv[u] >= 0;
         T.best[u] = 0xFFFFFFFFu;
     }
+    if (threadIdx.x == 0) {
+        tc.ref = P.ref[T.v];
+        tc.cp = P.cp[T.v];
+        tc.mg = P.cp_magic[T.v];
+    }
 }
 
 // inv[u] for a runtime u, without a runtime index into registers.
@@ -679,17 +763,26 @@ __device__ __forceinline__ int32_t inv_at(const TileState<IPT> &T, int u) {
     return iu;
 }
 
+// Slack of the tile's invocation u for backend h: Algorithm 1 through the
+// critical path, floor(ref * (rem - Q[h]) / cp), 0 once the target has passed,
+// rem being the invocation's remaining time stored beside its bucket entry.
+template <int IPT>
+__device__ __forceinline__ int32_t slack_at(const BucketScratch &S, const TileState<IPT> &T, const TileConst &tc,
+                                            int u, int h) {
+    return slack_of(tc.ref, tc.cp, tc.mg, (int64_t)S.b_rem[T.pos0 + u] - tc.q[h]);
+}
+
 // Counts c(u, h) of distinct latencies below the slack of invocation u for
 // backend h, into cg[u * H + h], from the sorted list dl (shared memory: the
 // lanes of a group share the bisections).
 template <int IPT>
-__device__ __forceinline__ void counts_from_shared(const BucketScratch &S, const TileState<IPT> &T, int H,
-                                                   const int32_t *dl, uint16_t *cg) {
+__device__ __forceinline__ void counts_from_shared(const BucketScratch &S, const TileState<IPT> &T,
+                                                   const TileConst &tc, int H, const int32_t *dl, uint16_t *cg) {
     if (!T.any) return;
     for (int t = T.s; t < IPT * H; t += T.L) {
         const int u = t / H, h = t - u * H;
         const int32_t iu = inv_at(T, u);
-        cg[t] = iu >= 0 ? (uint16_t)count_below(dl, T.dn, S.b_slack[(int64_t)(T.pos0 + u) * H + h]) : 0;
+        cg[t] = iu >= 0 ? (uint16_t)count_below(dl, T.dn, slack_at(S, T, tc, u, h)) : 0;
     }
 }
 
@@ -701,8 +794,8 @@ __device__ __forceinline__ void counts_from_shared(const BucketScratch &S, const
 // (l+1)n < 2^19.  Every thread of the CTA must call this (warp votes).
 template <int IPT>
 __device__ __forceinline__ void counts_from_global(const DevProblem &P, const BucketScratch &S,
-                                                   const TileState<IPT> &T, int H, const int32_t *dl,
-                                                   uint16_t *cg) {
+                                                   const TileState<IPT> &T, const TileConst &tc, int H,
+                                                   const int32_t *dl, uint16_t *cg) {
     const int nc = IPT * H;
     const int G = T.L < 32 ? T.L : 32, lgG = T.lg < 5 ? T.lg : 5;
     const int W = T.L > 32 ? (T.L >> 5) : 1, sw = T.s >> 5, gl = T.s & (G - 1);
@@ -712,7 +805,7 @@ __device__ __forceinline__ void counts_from_global(const DevProblem &P, const Bu
         const int t = t0 + sw, u = t / H, h = t - u * H;
         const int32_t iu = inv_at(T, u);
         const bool act = t < nc && iu >= 0;
-        const int32_t sl = act ? S.b_slack[(int64_t)(T.pos0 + u) * H + h] : 0;
+        const int32_t sl = act ? slack_at(S, T, tc, u, h) : 0;
         int32_t lo = 0, hi = act ? T.dn : 0;  // lo <= count <= hi
         if (G == 1) {  // one lane per invocation (tile-uniform): bisection
             lo = hi = act ? count_below(dl, T.dn, sl) : 0;
@@ -782,8 +875,9 @@ __device__ __forceinline__ void scan_chunk(const DevProblem &P, TileState<IPT> &
 // the CTA must call this (a block barrier when groups span several warps).
 template <int MODE, int IPT>
 __device__ __forceinline__ void finish_tile(const DevProblem &P, const BucketScratch &S, llama_decision *out,
-                                            const TileState<IPT> &T, uint32_t (*red)[kScoreThreads / 32]) {
-    const int tid = threadIdx.x, H = P.n_hw;
+                                            const TileState<IPT> &T, const TileConst &tc,
+                                            uint32_t (*red)[kScoreThreads / 32]) {
+    const int tid = threadIdx.x;
     uint32_t key[IPT];
     const int wl = T.L < 32 ? T.L : 32;
 #pragma unroll
@@ -808,7 +902,7 @@ __device__ __forceinline__ void finish_tile(const DevProblem &P, const BucketScr
         int4 d;
         if (MODE == LLAMA_MODE_ALPHA) d = P.dec[2 * (int64_t)T.cbase + key[u]];
         else d = key[u] < 0x8000u ? P.dec[(int64_t)T.cbase + key[u]] : P.dfast[T.v];
-        const int32_t sl = S.b_slack[(int64_t)(T.pos0 + u) * H + (d.x >> 16)];
+        const int32_t sl = slack_at(S, T, tc, u, d.x >> 16);
         llama_decision dsn;
         dsn.cfg = d.x & 0xFFFF;
         dsn.lat = d.y;
@@ -860,6 +954,7 @@ __device__ __forceinline__ void score_body(const DevProblem &P, const BucketScra
     __shared__ __align__(8) unsigned long long mbar;
     __shared__ uint32_t red[IPT][kScoreThreads / 32];
     __shared__ long long next_tile;
+    __shared__ TileConst tc;
     const int tid = threadIdx.x, H = P.n_hw;
     const uint32_t bar = smem_addr(&mbar);
     if (tid == 0) {
@@ -873,13 +968,15 @@ __device__ __forceinline__ void score_body(const DevProblem &P, const BucketScra
     // griddepcontrol.wait; the mbarrier set-up above overlaps its tail
     asm volatile("griddepcontrol.wait;" ::: "memory");
     clear_counters(P, S);
+    if (tid < H) tc.q[tid] = P.q[tid];
+    __syncthreads();
     const long long n_tiles = (long long)S.ctrl[kCtrlTiles];
     long long ti = blockIdx.x;
     TileState<IPT> T;
     while (ti < n_tiles) {
         unsigned long long claim = 0;
         if (tid == 0) claim = atomicAdd(&S.ctrl[kCtrlNextTile], 1ull);  // the tile after this one
-        tile_begin(S, ti, T);
+        tile_begin(P, S, ti, tc, T);
         const bool dl_staged = T.dn <= dl_cap;
         uint16_t *cg = c_s + T.g * IPT * H;
         for (int32_t c0 = 0; c0 < T.npad; c0 += chunk) {
@@ -887,7 +984,7 @@ __device__ __forceinline__ void score_body(const DevProblem &P, const BucketScra
             __syncthreads();  // every thread is done with the previous chunk or tile
             if (tid == 0)
                 stage_chunk<MODE>(P, T.p0, c0, cn, c0 == 0 && dl_staged, T.dn, lr_s, rf_s, df_s, dl_s, bar);
-            if (c0 == 0 && !dl_staged) counts_from_global(P, S, T, H, P.dlat + T.p0, cg);
+            if (c0 == 0 && !dl_staged) counts_from_global(P, S, T, tc, H, P.dlat + T.p0, cg);
             // every thread must agree before any leaves the barrier sequence
             if (!__syncthreads_and(mbar_wait(bar, phase))) {
                 ok = false;
@@ -895,13 +992,13 @@ __device__ __forceinline__ void score_body(const DevProblem &P, const BucketScra
             }
             phase ^= 1u;
             if (c0 == 0 && dl_staged) {
-                counts_from_shared(S, T, H, dl_s, cg);
+                counts_from_shared(S, T, tc, H, dl_s, cg);
                 __syncthreads();
             }
             scan_chunk<MODE, IPT>(P, T, c0, cn, lr_s, rf_s, df_s, cg);
         }
         if (!ok) break;
-        finish_tile<MODE, IPT>(P, S, out, T, red);
+        finish_tile<MODE, IPT>(P, S, out, T, tc, red);
         if (tid == 0) next_tile = (long long)(claim + gridDim.x);
         __syncthreads();
         ti = next_tile;
@@ -930,6 +1027,7 @@ __device__ __forceinline__ void score_body_pipe(const DevProblem &P, const Bucke
     __shared__ __align__(8) unsigned long long mbar[2];
     __shared__ uint32_t red[IPT][kScoreThreads / 32];
     __shared__ long long next_tile;
+    __shared__ TileConst tc;
     const int tid = threadIdx.x, H = P.n_hw;
     const uint32_t bar0 = smem_addr(&mbar[0]);
     if (tid == 0) {
@@ -952,6 +1050,7 @@ __device__ __forceinline__ void score_body_pipe(const DevProblem &P, const Bucke
     bool ok = true;
     asm volatile("griddepcontrol.wait;" ::: "memory");
     clear_counters(P, S);
+    if (tid < H) tc.q[tid] = P.q[tid];
     const long long n_tiles = (long long)S.ctrl[kCtrlTiles];
     long long ti = blockIdx.x, tn;
     if (tid == 0) next_tile = (long long)atomicAdd(&S.ctrl[kCtrlNextTile], 1ull) + gridDim.x;
@@ -967,7 +1066,7 @@ __device__ __forceinline__ void score_body_pipe(const DevProblem &P, const Bucke
         unsigned long long claim = 0;
         if (tid == 0) claim = atomicAdd(&S.ctrl[kCtrlNextTile], 1ull);  // the tile after tn
         const int4 txn = tn < n_tiles ? S.tiles[2 * tn + 1] : make_int4(0, 0, 0, 0);
-        tile_begin(S, ti, T);
+        tile_begin(P, S, ti, tc, T);
         const bool dl_staged = T.dn <= dl_cap;
         uint16_t *cg = c_s + T.g * IPT * H;
         for (int32_t c0 = 0; c0 < T.npad; c0 += chunk) {
@@ -981,7 +1080,7 @@ __device__ __forceinline__ void score_body_pipe(const DevProblem &P, const Bucke
                 }
                 pending |= 1u << (st ^ 1);
             }
-            if (c0 == 0 && !dl_staged) counts_from_global(P, S, T, H, P.dlat + T.p0, cg);
+            if (c0 == 0 && !dl_staged) counts_from_global(P, S, T, tc, H, P.dlat + T.p0, cg);
             if (!__syncthreads_and(mbar_wait(bar0 + 8 * st, (phases >> st) & 1u))) {
                 ok = false;
                 break;
@@ -990,14 +1089,14 @@ __device__ __forceinline__ void score_body_pipe(const DevProblem &P, const Bucke
             pending &= ~(1u << st);
             uint16_t *lr = lr_of(st);
             if (c0 == 0 && dl_staged) {
-                counts_from_shared(S, T, H, dl_of(st), cg);
+                counts_from_shared(S, T, tc, H, dl_of(st), cg);
                 __syncthreads();
             }
             scan_chunk<MODE, IPT>(P, T, c0, cn, lr, lr + chunk, lr + 2 * chunk, cg);
             st ^= 1;
         }
         if (!ok) break;
-        finish_tile<MODE, IPT>(P, S, out, T, red);
+        finish_tile<MODE, IPT>(P, S, out, T, tc, red);
         if (tid == 0) next_tile = (long long)(claim + gridDim.x);
         __syncthreads();
         ti = tn;

@@ -60,7 +60,7 @@ int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 // starts, per-invocation bucket entries, the tile list and the control and
 // status words.  Counters and control words are zero between calls.
 struct Workspace {
-    DevBuf cnt, ctrl, op_start, gop, slot, b_inv, b_slack, rbase, tiles;
+    DevBuf cnt, ctrl, op_start, gop, slot, b_inv, b_rem, rbase, tiles;
     int64_t cap_inv = 0, cap_tiles = 0;
     int32_t cap_ops = 0;
 };
@@ -244,7 +244,7 @@ BucketScratch make_scratch(const Workspace &w) {
     S.gop = w.gop.as<int32_t>();
     S.slot = w.slot.as<int32_t>();
     S.b_inv = w.b_inv.as<int32_t>();
-    S.b_slack = w.b_slack.as<int32_t>();
+    S.b_rem = w.b_rem.as<int32_t>();
     S.rbase = w.rbase.as<int64_t>();
     S.tiles = w.tiles.as<int4>();
     return S;
@@ -368,7 +368,6 @@ int check_ready(llama_ctx *c) {
 // Grow workspace w for calls of up to n_inv invocations on the context's
 // current operations (buffers move: the caller drops what points at them).
 int ensure_ws(llama_ctx *c, Workspace &w, int64_t n_inv) {
-    const int H = c->opts.n_hw;
     if (w.cap_ops < c->n_ops + 1) {
         const int32_t n = c->n_ops + 1;
         LL_CUDA(c, w.cnt.alloc(sizeof(int32_t) * kCntStride * n));
@@ -387,7 +386,7 @@ int ensure_ws(llama_ctx *c, Workspace &w, int64_t n_inv) {
         LL_CUDA(c, w.gop.alloc(sizeof(int32_t) * n));
         LL_CUDA(c, w.slot.alloc(sizeof(int32_t) * n));
         LL_CUDA(c, w.b_inv.alloc(sizeof(int32_t) * n));
-        LL_CUDA(c, w.b_slack.alloc(sizeof(int32_t) * n * H));
+        LL_CUDA(c, w.b_rem.alloc(sizeof(int32_t) * n));
         LL_CUDA(c, w.rbase.alloc(sizeof(int64_t) * n));
         w.cap_inv = n;
         w.cap_tiles = 0;

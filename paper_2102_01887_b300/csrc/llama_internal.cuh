@@ -63,6 +63,10 @@ constexpr int kCpSmemOps = 512;
 constexpr int kCpPackWords = 5120;  // packed DAG words staged in shared memory
 constexpr int kCpWarpOps = 128;       // a warp's slice of the critical-path area: ops
 constexpr int kCpWarpWords = 384;     // and packed words (<= 384 words implies <= 126 ops)
+// k_bucket lays out the buckets without barriers of its own when every
+// counting block can hold all bucket starts in its (otherwise unused)
+// critical-path staging area
+constexpr int kLayoutSmemOps = (kCpSmemOps * 16 + kCpPackWords * 4) / 4;
 
 struct DevProblem {
     int32_t n_dags, n_ops, n_hw, mode;
@@ -136,7 +140,8 @@ struct BucketScratch {
     int32_t *gop;             // [n_inv]     global op of each invocation, -1 if invalid
     int32_t *slot;            // [n_inv]     rank of the invocation inside its op's bucket
     int32_t *b_inv;           // [n_inv]     invocation at each bucket position
-    int32_t *b_slack;         // [n_inv*H]   slack per backend of the invocation at each bucket position
+    int32_t *b_rem;           // [n_inv]     remaining time before queueing, max(0, SLO - elapsed), of the
+                              //             invocation at each bucket position
     int64_t *rbase;           // [n_inv]     target - elapsed time of each invocation
     int4 *tiles;              // [2*max_tiles] scoring tiles: {op, first bucket position, m, lanes_log2},
                               // {padded entries, distinct latencies, padded offset, 0}

@@ -9,7 +9,7 @@
 // loop that cannot absorb the implicit synchronisation of cudaMalloc/cudaFree,
 // or code that runs where the CUDA allocator must not be entered at all.
 // This entry point uses instead one fixed, file-scope device array: every GPU
-// that loads the library holds it (about 6 MB) until the process exits.  The
+// that loads the library holds it (about 4.2 MB) until the process exits.  The
 // caller still passes inputs and outputs; the context's tables were copied to
 // the device earlier by llama_set_profiles.
 //
@@ -41,8 +41,8 @@ constexpr size_t kOpStartOff = align256(kCtrlOff + 8 * (size_t)(kCtrlWords + kSt
 constexpr size_t kGopOff = align256(kOpStartOff + 4 * (size_t)(LLAMA_STATIC_MAX_OPS + 1));
 constexpr size_t kSlotOff = align256(kGopOff + 4 * (size_t)LLAMA_STATIC_MAX_INV);
 constexpr size_t kBInvOff = align256(kSlotOff + 4 * (size_t)LLAMA_STATIC_MAX_INV);
-constexpr size_t kBSlackOff = align256(kBInvOff + 4 * (size_t)LLAMA_STATIC_MAX_INV);
-constexpr size_t kRbaseOff = align256(kBSlackOff + 4 * (size_t)LLAMA_STATIC_MAX_INV * LLAMA_MAX_HW);
+constexpr size_t kBRemOff = align256(kBInvOff + 4 * (size_t)LLAMA_STATIC_MAX_INV);
+constexpr size_t kRbaseOff = align256(kBRemOff + 4 * (size_t)LLAMA_STATIC_MAX_INV);
 constexpr size_t kTilesOff = align256(kRbaseOff + 8 * (size_t)LLAMA_STATIC_MAX_INV);
 constexpr size_t kScratchBytes = align256(kTilesOff + 32 * kMaxTiles);
 
@@ -124,7 +124,7 @@ extern "C" int llama_schedule_static(llama_ctx *c, int64_t n_inv, const int32_t 
     S.gop = reinterpret_cast<int32_t *>(base + kGopOff);
     S.slot = reinterpret_cast<int32_t *>(base + kSlotOff);
     S.b_inv = reinterpret_cast<int32_t *>(base + kBInvOff);
-    S.b_slack = reinterpret_cast<int32_t *>(base + kBSlackOff);
+    S.b_rem = reinterpret_cast<int32_t *>(base + kBRemOff);
     S.rbase = reinterpret_cast<int64_t *>(base + kRbaseOff);
     S.tiles = reinterpret_cast<int4 *>(base + kTilesOff);
 
