@@ -370,16 +370,24 @@ __device__ void layout_write(const DevProblem &P, const BucketScratch &S, int32_
 // Block 0 publishes the number of tiles.
 __device__ void layout_whole(const DevProblem &P, const BucketScratch &S, int32_t cb, int32_t nc,
                              int32_t min_vpl, int32_t ipt, int32_t *op_start_s, int32_t (*warp_sum)[32]) {
+    constexpr int kW = kLayoutWholeOps / 256;  // ops per thread at most (blockDim.x == 256)
     const int n = P.n_ops, T = blockDim.x, tid = threadIdx.x;
     const int32_t per = (n + T - 1) / T;
     const int32_t kb = min(n, tid * per), ke = min(n, kb + per);
+    // the thread's ops and their counts, each set of loads in one round
+    int4 oi[kW];
+    int32_t ck[kW];
+#pragma unroll
+    for (int j = 0; j < kW; ++j) oi[j] = kb + j < ke ? P.ord_info[kb + j] : make_int4(0, 0, 0, 0);
+#pragma unroll
+    for (int j = 0; j < kW; ++j) ck[j] = kb + j < ke ? __ldcg(&S.cnt[(int64_t)oi[j].x * kCntStride]) : 0;
     int32_t loc[3] = {0, 0, 0};
-    for (int k = kb; k < ke; ++k) {
-        const int4 oi = P.ord_info[k];
-        const int32_t ck = __ldcg(&S.cnt[(int64_t)oi.x * kCntStride]);
+#pragma unroll
+    for (int j = 0; j < kW; ++j) {
+        if (kb + j >= ke) continue;
         int32_t f, t;
-        op_tiles(ck, oi.y, min_vpl, ipt, f, t);
-        loc[0] += ck;
+        op_tiles(ck[j], oi[j].y, min_vpl, ipt, f, t);
+        loc[0] += ck[j];
         loc[1] += f;
         loc[2] += t;
     }
@@ -388,17 +396,18 @@ __device__ void layout_whole(const DevProblem &P, const BucketScratch &S, int32_
     const int32_t tper = (n + nc - 1) / nc;
     const int32_t t0 = cb * tper, t1 = min(n, t0 + tper);
     int32_t pos = excl[0], tf = excl[1], tt = tot[1] + excl[2];
-    for (int k = kb; k < ke; ++k) {
-        const int4 oi = P.ord_info[k];
-        const int32_t ck = __ldcg(&S.cnt[(int64_t)oi.x * kCntStride]);
-        const int32_t v = oi.x, nvec = oi.y;
+#pragma unroll
+    for (int j = 0; j < kW; ++j) {
+        const int k = kb + j;
+        if (k >= ke) continue;
+        const int32_t v = oi[j].x, nvec = oi[j].y, c = ck[j];
         const int lg = lanes_log2_for(nvec, min_vpl);
         const int32_t per_tile = (kScoreThreads >> lg) * ipt;
-        const int32_t full = full_tiles(ck, lg, ipt), rest = ck - full * per_tile;
+        const int32_t full = full_tiles(c, lg, ipt), rest = c - full * per_tile;
         op_start_s[v] = pos;
         if (k >= t0 && k < t1) {
             // {padded entries, distinct latencies, padded offset, first configuration}
-            const int4 tx = make_int4(nvec * kVec, oi.w, oi.z, __ldg(P.ord_cbase + k));
+            const int4 tx = make_int4(nvec * kVec, oi[j].w, oi[j].z, __ldg(P.ord_cbase + k));
             for (int32_t j = 0; j < full; ++j) {
                 S.tiles[2 * (tf + j)] = make_int4(v, pos + j * per_tile, per_tile, lg);
                 S.tiles[2 * (tf + j) + 1] = tx;
@@ -410,7 +419,7 @@ __device__ void layout_whole(const DevProblem &P, const BucketScratch &S, int32_
         }
         tf += full;
         tt += rest > 0 ? 1 : 0;
-        pos += ck;
+        pos += c;
     }
     if (cb == 0 && tid == 0) S.ctrl[kCtrlTiles] = (unsigned long long)(tot[1] + tot[2]);
     __syncthreads();  // op_start_s complete
@@ -560,7 +569,7 @@ __global__ void __launch_bounds__(256) k_bucket(DevProblem P, int64_t n_inv, con
     const int32_t cb = (int32_t)(blockIdx.x - n_cp);
     grid_barrier(&S.ctrl[kCtrlCountBarrier], (unsigned long long)nb, &S.ctrl[kCtrlTimeout]);
     const int32_t *op_start;
-    if (P.n_ops <= kLayoutSmemOps) {
+    if (P.n_ops <= kLayoutWholeOps) {
         int32_t *op_start_s = reinterpret_cast<int32_t *>(&sm);
         layout_whole(P, S, cb, (int32_t)nb, min_vpl, ipt, op_start_s, warp_sum);
         op_start = op_start_s;

@@ -63,10 +63,12 @@ constexpr int kCpSmemOps = 512;
 constexpr int kCpPackWords = 5120;  // packed DAG words staged in shared memory
 constexpr int kCpWarpOps = 128;       // a warp's slice of the critical-path area: ops
 constexpr int kCpWarpWords = 384;     // and packed words (<= 384 words implies <= 126 ops)
-// k_bucket lays out the buckets without barriers of its own when every
-// counting block can hold all bucket starts in its (otherwise unused)
-// critical-path staging area
-constexpr int kLayoutSmemOps = (kCpSmemOps * 16 + kCpPackWords * 4) / 4;
+// k_bucket lays out the buckets without barriers of its own (every counting
+// block computes the whole layout) when the ops are at most this many: four
+// per thread, their loads all in flight at once; the bucket starts go to the
+// block's otherwise unused critical-path staging area
+constexpr int kLayoutWholeOps = 4 * 256;
+static_assert(kLayoutWholeOps * 4 <= kCpSmemOps * 16 + kCpPackWords * 4, "bucket starts exceed the staging area");
 
 struct DevProblem {
     int32_t n_dags, n_ops, n_hw, mode;
