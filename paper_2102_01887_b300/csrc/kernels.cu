@@ -721,15 +721,15 @@ struct TileState {
     int32_t inv[IPT];
     uint32_t best[IPT];
     bool any;
-};
-
-// What every thread of a tile needs for the slack, in shared memory: the
-// queueing time per backend (per call) and the tile's op's reference latency,
-// critical path and floor((2^64-1) / critical path) (per tile, written by one
-// thread in tile_begin; a block barrier separates it from the readers).
-struct TileConst {
+    // the op's reference latency, critical path and floor((2^64-1) / critical
+    // path), loaded by every thread as the tile starts (one request per warp;
+    // nothing waits for them before the table copy is issued)
     int64_t ref, cp;
     uint64_t mg;
+};
+
+// The queueing time per backend, copied into shared memory once per call.
+struct TileConst {
     int64_t q[LLAMA_MAX_HW];
 };
 
@@ -756,11 +756,9 @@ __device__ __forceinline__ void tile_begin(const DevProblem &P, const BucketScra
         T.any |= T.inv[u] >= 0;
         T.best[u] = 0xFFFFFFFFu;
     }
-    if (threadIdx.x == 0) {
-        tc.ref = P.ref[T.v];
-        tc.cp = P.cp[T.v];
-        tc.mg = P.cp_magic[T.v];
-    }
+    T.ref = P.ref[T.v];
+    T.cp = P.cp[T.v];
+    T.mg = P.cp_magic[T.v];
 }
 
 // inv[u] for a runtime u, without a runtime index into registers.
@@ -778,7 +776,7 @@ __device__ __forceinline__ int32_t inv_at(const TileState<IPT> &T, int u) {
 template <int IPT>
 __device__ __forceinline__ int32_t slack_at(const BucketScratch &S, const TileState<IPT> &T, const TileConst &tc,
                                             int u, int h) {
-    return slack_of(tc.ref, tc.cp, tc.mg, (int64_t)S.b_rem[T.pos0 + u] - tc.q[h]);
+    return slack_of(T.ref, T.cp, T.mg, (int64_t)S.b_rem[T.pos0 + u] - tc.q[h]);
 }
 
 // Counts c(u, h) of distinct latencies below the slack of invocation u for
