@@ -42,13 +42,13 @@ SCAN_BYTES_PER_SCORE = 12  # int32 latency + int64 cost per scored configuration
 # (profiles/ holds the summaries and the commands); reported as null as soon as
 # the sources differ.  Keys: workload/objective.
 MEASURED_TRAFFIC = {
-    "digest": "29742dee85033a27",
+    "digest": "271ae14307695fc7",
     # profiles/k_bucket_medium.md, profiles/k_score_medium.md
-    "k_bucket:medium/cost_first": 6.812416e6,
-    "k_score:medium/cost_first": 3.184896e6,
-    # profiles/k_score_batched_large_192dags.md: 194.02 MB at 192 DAGs, scaled to
+    "k_bucket:medium/cost_first": 6.810624e6,
+    "k_score:medium/cost_first": 2.670080e6,
+    # profiles/k_score_batched_large_192dags.md: measured at 192 DAGs, scaled to
     # the full launch by its algorithmic bytes (459.50 / 172.25 MB)
-    "k_score:batched_large/cost_first": 194.02e6 * 459.50 / 172.25,
+    "k_score:batched_large/cost_first": 514.689e6,
 }
 
 
@@ -618,13 +618,13 @@ def main():
                            f"{sm_mhz:.0f} MHz ({peak_src} max SM clock)",
             "alu_ops_per_score": ops_per_score, "scores_per_s_ceiling": peak_tops * 1e12 / ops_per_score}
     if args.method == "scan":
-        b_bytes = inv.n * (16 + 4 + 4 * p.n_hw)
+        b_bytes = inv.n * (16 + 8)
         b_ach = b_bytes / (kms["bucket"] / 1e3) / 1e9
         rooflines["k_bucket"] = {
             "bound": "hbm", "kernel": "k_bucket", "achieved": b_ach, "peak": hbm, "unit": "GB/s",
             "frac": b_ach / hbm, "traffic": measured_traffic("k_bucket", args.workload, args.mode),
             "peak_source": f"{peak_src} HBM copy bandwidth", "algorithmic_bytes": b_bytes,
-            "bytes_note": f"16 B in and {4 + 4 * p.n_hw} B of bucket entry out per invocation; "
+            "bytes_note": "16 B in and 8 B of bucket entry (index, remaining time) out per invocation; "
                           "time includes its launch (trace events around it)"}
         dominant = max(rooflines, key=lambda k: kms["score" if k == "k_score" else "bucket"])
         roofline = rooflines[dominant]
