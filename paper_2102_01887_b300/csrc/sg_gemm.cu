@@ -16,6 +16,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <mutex>
 
@@ -71,8 +72,8 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
-// Epilogue of the selection GEMM (layer 3 of the surrogate over (invocation,
-// configuration) pairs): per row, h3 = ReLU(acc + bias), the log latency factor
+// Epilogue of the last hidden layer of the surrogate over (invocation,
+// configuration) pairs (k_mlp_layer<true>): per row, h3 = ReLU(acc + bias), the log latency factor
 // r = h3 . w4 + b4, the predicted latency and cost (profiled values times e^r)
 // and the pair's selection key, folded into the invocation's best key.  The
 // prediction is raised by the margin (an upper quantile of the model's error)
@@ -94,11 +95,11 @@ __device__ __forceinline__ void select_row(const SelectArgs &A, int64_t row, flo
     atomicMin(A.best + i, key);
 }
 
-template <int BN, bool SELECT>
+template <int BN>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
                 int K, const float *__restrict__ bias, int flags, __nv_bfloat16 *__restrict__ c16,
-                float *__restrict__ c32, int ldc, int *err, const __grid_constant__ SelectArgs sel) {
+                float *__restrict__ c32, int ldc, int *err) {
     constexpr int A_BYTES = kBM * kBK * 2, B_BYTES = BN * kBK * 2, STAGE = A_BYTES + B_BYTES;
     constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
     extern __shared__ uint8_t smem_raw[];
@@ -179,7 +180,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     const bool ok = acc_ok && !failed && nk > 0;
     const int row = m0 + warp * 32 + lane;
     const bool relu = flags & LLAMA_GEMM_RELU;
-    float dot = 0.f;
 #pragma unroll 1
     for (int c0 = 0; c0 < BN; c0 += 16) {
         uint32_t r[16];
@@ -196,11 +196,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int j = 0; j < 16; ++j) {
             v[j] = __uint_as_float(r[j]) + (bias ? bias[n0 + c0 + j] : 0.f);
             if (relu) v[j] = fmaxf(v[j], 0.f);
-        }
-        if (SELECT) {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) dot = fmaf(v[j], sel.w4[c0 + j], dot);
-            continue;
         }
         const int64_t o = (int64_t)row * ldc + n0 + c0;
         if (c32) {
@@ -219,7 +214,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             *reinterpret_cast<uint4 *>(c16 + o + 8) = make_uint4(p[4], p[5], p[6], p[7]);
         }
     }
-    if (SELECT && ok && row < M) select_row(sel, row, dot + *sel.b4);
     if (!ok) {
         if (threadIdx.x == 0) {
             atomicOr(err, 1);
@@ -232,6 +226,238 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Persistent hidden layer of the surrogate: C[M x 256] = ReLU(A[M x 256] . W^T + b)
+// ---------------------------------------------------------------------------
+//
+// For the pair layers of the scheduling path (M in the millions, N = K = 256):
+// one CTA per SM loads W (256 x 256 BF16, 128 KB, four 256 x 64 slices with the
+// 128-byte swizzle) into shared memory once and keeps it; warp 0 (one lane)
+// streams the A tiles of the CTA's row tiles (blockIdx.x, + gridDim.x, ...)
+// through a ring of 128 x 64 slices; warp 1 (one lane) issues the MMAs of a tile
+// into one of two 128 x 256 FP32 accumulators in tensor memory (512 columns)
+// and commits; the epilogue warps read an accumulator back (warp w: tensor-memory
+// lanes 32(w%4) .. 32(w%4)+31), add the bias, apply ReLU and store BF16 rows
+// or, for the last hidden layer, fold every row into the last layer's dot
+// product and the selection (eight warps, two per lane quarter, each half of the
+// columns; the halves of a row's dot product meet in shared memory); then they
+// release the accumulator, so the next tile's MMAs overlap this tile's
+// epilogue.  Every wait is bounded; a wait that gives up sets *err, and the CTA
+// waits (bounded) for its copies and MMAs in flight and frees its tensor memory
+// before it returns.
+//
+// Warp 0 TMA, warp 1 MMA, then the epilogue warps.
+__host__ __device__ constexpr int epi_warps(bool) { return 8; }
+constexpr int kEpiBarrier = 1;  // named barrier of the epilogue warps (0 is __syncthreads)
+__host__ __device__ constexpr int layer_threads(bool select) { return 32 * (2 + epi_warps(select)); }
+constexpr int kLStages = 5;               // A ring of 128 x 64 BF16 slices
+constexpr int kLSlices = kHid / kBK;      // K slices per tile (4)
+constexpr int kLWSlice = kHid * kBK * 2;  // 256 x 64 BF16 = 32 KB
+constexpr int kLWBytes = kLSlices * kLWSlice;
+constexpr int kLABytes = kBM * kBK * 2;   // 16 KB
+constexpr int kLSmem = kLWBytes + kLStages * kLABytes + 1024;
+
+// All lanes of the warp agree: true only if every lane's bounded wait completed.
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity) {
+    return __all_sync(0xffffffffu, mbar_wait(bar, parity));
+}
+
+template <bool SELECT>
+__global__ void __launch_bounds__(layer_threads(SELECT), 1)
+    k_mlp_layer(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmW, int M,
+                const float *__restrict__ bias, __nv_bfloat16 *__restrict__ c16, int *err,
+                const __grid_constant__ SelectArgs sel) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full[kLStages], empty[kLStages], wbar, accf[2], acce[2];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int failed, issued, consumed, committed;
+    __shared__ float half_dot[SELECT ? kBM : 1];  // second halves of the rows' last-layer dot products
+    const uint32_t wbase = (smem_u32(smem_raw) + 1023u) & ~1023u, abase = wbase + kLWBytes;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_tiles = (M + kBM - 1) / kBM;
+    const int my_tiles = (int)blockIdx.x < n_tiles ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < kLStages; ++k) {
+            mbar_init(smem_u32(&full[k]), 1);
+            mbar_init(smem_u32(&empty[k]), 1);
+        }
+        mbar_init(smem_u32(&wbar), 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&accf[b]), 1);
+            mbar_init(smem_u32(&acce[b]), epi_warps(SELECT));  // one arrival per epilogue warp
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        failed = issued = consumed = committed = 0;
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(&tmem_slot)), "r"(512) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    volatile int *vfailed = &failed;
+
+    if (warp == 0 && lane == 0) {
+        // producer: W once, then the A slices of every tile of this CTA
+        const uint32_t wb = smem_u32(&wbar);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(wb), "r"(kLWBytes) : "memory");
+        for (int k = 0; k < kLSlices; ++k) tma_load_2d(wbase + k * kLWSlice, &tmW, k * kBK, 0, wb);
+        int g = 0;
+        for (int j = 0; j < my_tiles && !*vfailed; ++j) {
+            const int m0 = ((int)blockIdx.x + j * (int)gridDim.x) * kBM;
+            int k = 0;
+            for (; k < kLSlices; ++k, ++g) {
+                const int st = g % kLStages;
+                if (g >= kLStages && !mbar_wait(smem_u32(&empty[st]), ((g / kLStages) - 1) & 1)) {
+                    *vfailed = 1;
+                    break;
+                }
+                const uint32_t bar = smem_u32(&full[st]);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kLABytes)
+                             : "memory");
+                tma_load_2d(abase + st * kLABytes, &tmA, k * kBK, m0, bar);
+            }
+            if (k < kLSlices) break;
+        }
+        issued = g;
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        constexpr uint32_t idesc = idesc_bf16(kBM, kHid);
+        bool ok = mbar_wait(smem_u32(&wbar), 0);
+        int g = 0, j = 0;
+        for (; ok && j < my_tiles && !*vfailed; ++j) {
+            const int b = j & 1, u = j >> 1;
+            if (u >= 1 && !mbar_wait(smem_u32(&acce[b]), (u - 1) & 1)) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t acc = tmem + (uint32_t)(b * kHid);
+            for (int k = 0; k < kLSlices; ++k, ++g) {
+                const int st = g % kLStages;
+                if (!mbar_wait(smem_u32(&full[st]), (g / kLStages) & 1)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t a = abase + st * kLABytes, w = wbase + k * kLWSlice;
+#pragma unroll
+                for (int q = 0; q < kBK / 16; ++q) {
+                    const uint64_t ad = smem_desc_sw128(a + 32 * q), bd = smem_desc_sw128(w + 32 * q);
+                    const uint32_t accum = (k > 0 || q > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                        ::"r"(acc), "l"(ad), "l"(bd), "r"(idesc), "r"(accum) : "memory");
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             ::"r"(smem_u32(&empty[st])) : "memory");
+            }
+            if (!ok) break;
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         ::"r"(smem_u32(&accf[b])) : "memory");
+        }
+        if (!ok) *vfailed = 1;
+        consumed = g;
+        committed = j;  // tiles whose accumulator commit was issued
+    } else if (warp >= 2) {
+        // epilogue: this warp's quarter of every tile's rows, its share of the columns
+        constexpr int kCols = kHid * 4 / epi_warps(SELECT);
+        const int quad = warp & 3, half = (warp - 2) >> 2, cbeg = half * kCols;
+        for (int j = 0; j < my_tiles; ++j) {
+            const int b = j & 1, u = j >> 1;
+            // every epilogue warp agrees on the outcome of the wait (the named
+            // barriers below need all of them, or none)
+            const bool got = warp_wait(smem_u32(&accf[b]), u & 1);
+            if (SELECT) {
+                int all_ok;
+                asm volatile("{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n"
+                             " bar.red.and.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+                             : "=r"(all_ok) : "r"((unsigned)got), "n"(kEpiBarrier), "n"(32 * epi_warps(SELECT)));
+                if (!all_ok) {
+                    if (lane == 0) *vfailed = 1;
+                    break;
+                }
+            } else if (!got) {
+                if (lane == 0) *vfailed = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int row = ((int)blockIdx.x + j * (int)gridDim.x) * kBM + quad * 32 + lane;
+            const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * kHid);
+            float dot = 0.f;
+#pragma unroll 1
+            for (int c0 = cbeg; c0 < cbeg + kCols; c0 += 32) {
+                uint32_t r[32];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                      "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                      "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                    : "r"(tbase + (uint32_t)c0));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (row >= M) continue;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    float v[16];
+#pragma unroll
+                    for (int q = 0; q < 16; ++q)
+                        v[q] = fmaxf(__uint_as_float(r[16 * h + q]) + bias[c0 + 16 * h + q], 0.f);
+                    if (SELECT) {
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) dot = fmaf(v[q], sel.w4[c0 + 16 * h + q], dot);
+                    } else {
+                        uint32_t pk[8];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+                            pk[q] = *reinterpret_cast<const uint32_t *>(&b2);
+                        }
+                        __nv_bfloat16 *o = c16 + (int64_t)row * kHid + c0 + 16 * h;
+                        *reinterpret_cast<uint4 *>(o) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                        *reinterpret_cast<uint4 *>(o + 8) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                    }
+                }
+            }
+            // the accumulator is read: the MMAs of tile j + 2 may overwrite it
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[b])) : "memory");
+            if (SELECT) {
+                // second halves hand their partial sums to the first halves
+                if (half == 1) half_dot[quad * 32 + lane] = dot;
+                asm volatile("bar.sync %0, %1;" ::"n"(kEpiBarrier), "n"(32 * epi_warps(SELECT)) : "memory");
+                if (half == 0 && row < M) select_row(sel, row, dot + half_dot[quad * 32 + lane] + *sel.b4);
+                asm volatile("bar.sync %0, %1;" ::"n"(kEpiBarrier), "n"(32 * epi_warps(SELECT)) : "memory");
+            }
+        }
+    }
+    __syncwarp();
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (failed && threadIdx.x == 0) {
+        atomicOr(err, 1);
+        // let every copy and MMA in flight finish before the shared and tensor
+        // memory go away: W, the A slices issued but not consumed, and the
+        // accumulators committed (their commits cover every MMA issued before)
+        mbar_wait(smem_u32(&wbar), 0);
+        for (int g = consumed; g < issued; ++g) mbar_wait(smem_u32(&full[g % kLStages]), (g / kLStages) & 1);
+        for (int j = (committed >= 2 ? committed - 2 : 0); j < committed; ++j)
+            mbar_wait(smem_u32(&accf[j & 1]), (j >> 1) & 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -270,20 +496,19 @@ int make_map(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, int 
     return r == CUDA_SUCCESS ? LLAMA_OK : LLAMA_EINVAL;
 }
 
-template <int BN, bool SELECT = false>
+template <int BN>
 cudaError_t launch_gemm(const CUtensorMap &ta, const CUtensorMap &tb, int64_t M, int N, int K, const float *bias,
-                        int flags, void *c16, float *c32, int ldc, int *err, cudaStream_t s,
-                        const SelectArgs &sel = SelectArgs{}) {
+                        int flags, void *c16, float *c32, int ldc, int *err, cudaStream_t s) {
     constexpr int smem = kStages * (kBM + BN) * kBK * 2 + 1024;
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
     std::call_once(once, [] {
-        attr = cudaFuncSetAttribute(k_gemm_bf16<BN, SELECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        attr = cudaFuncSetAttribute(k_gemm_bf16<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     });
     if (attr != cudaSuccess) return attr;
     const dim3 grid((unsigned)((M + kBM - 1) / kBM), (unsigned)(N / BN));
-    k_gemm_bf16<BN, SELECT><<<grid, kThreads, smem, s>>>(ta, tb, (int)M, N, K, bias, flags,
-                                                          static_cast<__nv_bfloat16 *>(c16), c32, ldc, err, sel);
+    k_gemm_bf16<BN><<<grid, kThreads, smem, s>>>(ta, tb, (int)M, N, K, bias, flags,
+                                                  static_cast<__nv_bfloat16 *>(c16), c32, ldc, err);
     return cudaGetLastError();
 }
 
@@ -317,18 +542,43 @@ int gemm(const void *a, const void *b, const float *bias, void *c16, float *c32,
     return e == cudaSuccess ? LLAMA_OK : LLAMA_ECUDA;
 }
 
-// Layer 3 of the surrogate over m pairs (a: h2 [m x 256], b: W3 [256 x 256])
-// with the fused last layer and selection of the epilogue.
-int gemm_select(const void *a, const void *b, const float *bias, int64_t m, const SelectArgs &sel, cudaStream_t s) {
-    if (!a || !b || m < 1 || m > (1 << 30)) return LLAMA_EINVAL;
+// The persistent pair layer (see k_mlp_layer): a [m x 256] BF16, w [256 x 256]
+// BF16 (row n = output n), bias [256] FP32; c16 [m x 256] BF16 (SELECT false)
+// or the fused last layer and selection (SELECT true).
+template <bool SELECT>
+int mlp_layer_impl(const void *a, const void *w, const float *bias, void *c16, int64_t m, const SelectArgs &sel,
+                   cudaStream_t s) {
+    if (!a || !w || !bias || (!SELECT && !c16) || m < 1 || m > (1 << 30)) return LLAMA_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(w) | reinterpret_cast<uintptr_t>(c16)) & 15)
+        return LLAMA_EINVAL;
     int *err = error_word();
     if (!err) return LLAMA_ENOMEM;
-    CUtensorMap ta, tb;
-    if (make_map(&ta, a, m, kHid, kBM) != LLAMA_OK || make_map(&tb, b, kHid, kHid, 256) != LLAMA_OK)
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+        attr = cudaFuncSetAttribute(k_mlp_layer<SELECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kLSmem);
+    });
+    if (attr != cudaSuccess) return LLAMA_ECUDA;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return LLAMA_ECUDA;
+    CUtensorMap ta, tw;
+    if (make_map(&ta, a, m, kHid, kBM) != LLAMA_OK || make_map(&tw, w, kHid, kHid, kHid) != LLAMA_OK)
         return LLAMA_EINVAL;
-    const cudaError_t e = launch_gemm<256, true>(ta, tb, m, kHid, kHid, bias, LLAMA_GEMM_RELU, nullptr, nullptr,
-                                                 kHid, err, s, sel);
-    return e == cudaSuccess ? LLAMA_OK : LLAMA_ECUDA;
+    const int64_t tiles = (m + kBM - 1) / kBM;
+    const unsigned grid = (unsigned)std::min<int64_t>(tiles, sms);
+    k_mlp_layer<SELECT><<<grid, layer_threads(SELECT), kLSmem, s>>>(ta, tw, (int)m, bias, static_cast<__nv_bfloat16 *>(c16), err,
+                                                        sel);
+    return cudaGetLastError() == cudaSuccess ? LLAMA_OK : LLAMA_ECUDA;
+}
+
+int mlp_layer(const void *a, const void *w, const float *bias, void *c16, int64_t m, cudaStream_t s) {
+    return mlp_layer_impl<false>(a, w, bias, c16, m, SelectArgs{}, s);
+}
+
+int mlp_layer_select(const void *a, const void *w, const float *bias, int64_t m, const SelectArgs &sel,
+                     cudaStream_t s) {
+    return mlp_layer_impl<true>(a, w, bias, nullptr, m, sel, s);
 }
 
 }  // namespace sgk

@@ -6,7 +6,7 @@
 
 namespace sgk {
 
-// Arguments of the fused selection epilogue (see gemm_select).
+// Arguments of the fused selection epilogue (see mlp_layer_select).
 struct SelectArgs {
     const float *w4 = nullptr;        // [256] row 0 of the last layer
     const float *b4 = nullptr;        // its bias (device)
@@ -31,8 +31,13 @@ struct llama_mlp_view {
     int device;
 };
 
-// Layer 3 of the surrogate with the fused last layer and selection.
-int gemm_select(const void *a, const void *b, const float *bias, int64_t m, const SelectArgs &sel, cudaStream_t s);
+// The pair layers of the scheduling path on the persistent kernel (weights kept
+// in shared memory, double-buffered accumulators): c16 = ReLU(a . w^T + bias),
+// a [m x 256], w [256 x 256], BF16; and the same layer with the fused last layer
+// and selection in place of the store.
+int mlp_layer(const void *a, const void *w, const float *bias, void *c16, int64_t m, cudaStream_t s);
+int mlp_layer_select(const void *a, const void *w, const float *bias, int64_t m, const SelectArgs &sel,
+                     cudaStream_t s);
 // The device word that bounded waits of the GEMM set when they give up.
 int *error_word();
 

@@ -9,8 +9,9 @@
 // latencies).  The first layer splits by linearity: z1(i, x) = A[x] + B[i] with
 // A = (configuration features) W1^T and B = (content features) W1^T + b1, the
 // other input columns being zero in each; so a pair costs one ReLU of a sum
-// and two 256 x 256 products (tensor cores), the last layer and the selection
-// running in the epilogue of the second product.
+// and two 256 x 256 products (tensor cores; a persistent kernel keeps each
+// layer's weights in shared memory), the last layer and the selection running
+// in the epilogue of the second product.
 #include <cub/cub.cuh>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -251,8 +252,7 @@ extern "C" int llama_sg_schedule(llama_sg *s, const void *cfg_x, const void *inv
                                                    s->pair_inv.as<int32_t>(), s->pair_g.as<int32_t>(),
                                                    s->pair_x.as<int32_t>());
         SG_CUDA(s, cudaGetLastError());
-        SG_RC(s, gemm(s->h1.p, nv.w16[1], nv.params + kOffB2, s->h2.p, nullptr, total, kHid, kHid, LLAMA_GEMM_RELU, st),
-              "layer 2");
+        SG_RC(s, mlp_layer(s->h1.p, nv.w16[1], nv.params + kOffB2, s->h2.p, total, st), "layer 2");
         SelectArgs a;
         a.w4 = nv.params + kOffW4;
         a.b4 = nv.params + kOffB4;
@@ -268,7 +268,7 @@ extern "C" int llama_sg_schedule(llama_sg *s, const void *cfg_x, const void *inv
         a.best = s->best.as<unsigned long long>();
         a.lhat = s->lhat.as<int32_t>();
         a.chat = s->chat.as<int64_t>();
-        SG_RC(s, gemm_select(s->h2.p, nv.w16[2], nv.params + kOffB3, total, a, st), "layer 3 and selection");
+        SG_RC(s, mlp_layer_select(s->h2.p, nv.w16[2], nv.params + kOffB3, total, a, st), "layer 3 and selection");
     }
     k_sg_decode<<<(unsigned)((n_inv + 255) / 256), 256, 0, st>>>(
         v.P, n_inv, dag, op_local, s->slack.as<int32_t>(), s->pair_off.as<int64_t>(),
