@@ -78,15 +78,16 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
 // and the pair's selection key, folded into the invocation's best key.  The
 // prediction is raised by the margin (an upper quantile of the model's error)
 // before use.
-__device__ __forceinline__ void select_row(const SelectArgs &A, int64_t row, float r) {
+// ps is the pair's selection record (invocation, op-local index, profiled
+// latency, slack on its backend), cost its profiled cost.
+__device__ __forceinline__ void select_row(const SelectArgs &A, int64_t row, float r, int4 ps, int64_t cost) {
     if (!isfinite(r)) r = 0.f;  // the profiled latency stands in for an unusable prediction
     r = fminf(fmaxf(r + A.margin, -20.f), 20.f);
-    const int32_t i = A.pair_inv[row], g = A.pair_g[row], x = A.pair_x[row];
+    const int32_t i = ps.x, x = ps.y, sl = ps.w;
     const double f = (double)expf(r);
-    const double lh = fmin(fmax(rint((double)A.lat[g] * f), 1.0), 2147483646.0);
+    const double lh = fmin(fmax(rint((double)ps.z * f), 1.0), 2147483646.0);
     const int32_t lhat = (int32_t)lh;
-    const int64_t chat = (int64_t)fmin(rint((double)A.cost[g] * f), 4.0e12);
-    const int32_t sl = A.slack[(int64_t)i * A.n_hw + A.cfg_lam[g]];
+    const int64_t chat = (int64_t)fmin(rint((double)cost * f), 4.0e12);
     A.lhat[row] = lhat;
     A.chat[row] = chat;
     // cost-first: feasible pairs by (cost, index), else (latency, index) above them
@@ -274,6 +275,8 @@ __global__ void __launch_bounds__(layer_threads(SELECT), 1)
     __shared__ uint32_t tmem_slot;
     __shared__ int failed, issued, consumed, committed;
     __shared__ float half_dot[SELECT ? kBM : 1];  // second halves of the rows' last-layer dot products
+    __shared__ __align__(16) float s_bias[kHid];
+    __shared__ __align__(16) float s_w4[SELECT ? kHid : 4];
     const uint32_t wbase = (smem_u32(smem_raw) + 1023u) & ~1023u, abase = wbase + kLWBytes;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_tiles = (M + kBM - 1) / kBM;
@@ -290,6 +293,10 @@ __global__ void __launch_bounds__(layer_threads(SELECT), 1)
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         failed = issued = consumed = committed = 0;
+    }
+    for (int c = threadIdx.x; c < kHid; c += blockDim.x) {
+        s_bias[c] = bias[c];
+        if (SELECT) s_w4[c] = sel.w4[c];
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -369,8 +376,24 @@ __global__ void __launch_bounds__(layer_threads(SELECT), 1)
         // epilogue: this warp's quarter of every tile's rows, its share of the columns
         constexpr int kCols = kHid * 4 / epi_warps(SELECT);
         const int quad = warp & 3, half = (warp - 2) >> 2, cbeg = half * kCols;
+        const auto row_of = [&](int jj) { return ((int)blockIdx.x + jj * (int)gridDim.x) * kBM + quad * 32 + lane; };
+        const bool selector = SELECT && half == 0;
+        const float b4 = SELECT ? *sel.b4 : 0.f;
+        // the selection records of a tile's rows are loaded one tile ahead
+        int4 ps = make_int4(0, 0, 0, 0);
+        int64_t pcost = 0;
+        if (selector && my_tiles > 0 && row_of(0) < M) {
+            ps = __ldg(sel.pair_sel + row_of(0));
+            pcost = __ldg(sel.pair_cost + row_of(0));
+        }
         for (int j = 0; j < my_tiles; ++j) {
             const int b = j & 1, u = j >> 1;
+            int4 ps_next = make_int4(0, 0, 0, 0);
+            int64_t pcost_next = 0;
+            if (selector && j + 1 < my_tiles && row_of(j + 1) < M) {
+                ps_next = __ldg(sel.pair_sel + row_of(j + 1));
+                pcost_next = __ldg(sel.pair_cost + row_of(j + 1));
+            }
             // every epilogue warp agrees on the outcome of the wait (the named
             // barriers below need all of them, or none)
             const bool got = warp_wait(smem_u32(&accf[b]), u & 1);
@@ -388,7 +411,7 @@ __global__ void __launch_bounds__(layer_threads(SELECT), 1)
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int row = ((int)blockIdx.x + j * (int)gridDim.x) * kBM + quad * 32 + lane;
+            const int row = row_of(j);
             const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * kHid);
             float dot = 0.f;
 #pragma unroll 1
@@ -408,12 +431,25 @@ __global__ void __launch_bounds__(layer_threads(SELECT), 1)
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     float v[16];
+                    const float4 *bb = reinterpret_cast<const float4 *>(s_bias + c0 + 16 * h);
 #pragma unroll
-                    for (int q = 0; q < 16; ++q)
-                        v[q] = fmaxf(__uint_as_float(r[16 * h + q]) + bias[c0 + 16 * h + q], 0.f);
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 t = bb[q];
+                        v[4 * q + 0] = fmaxf(__uint_as_float(r[16 * h + 4 * q + 0]) + t.x, 0.f);
+                        v[4 * q + 1] = fmaxf(__uint_as_float(r[16 * h + 4 * q + 1]) + t.y, 0.f);
+                        v[4 * q + 2] = fmaxf(__uint_as_float(r[16 * h + 4 * q + 2]) + t.z, 0.f);
+                        v[4 * q + 3] = fmaxf(__uint_as_float(r[16 * h + 4 * q + 3]) + t.w, 0.f);
+                    }
                     if (SELECT) {
+                        const float4 *ww = reinterpret_cast<const float4 *>(s_w4 + c0 + 16 * h);
 #pragma unroll
-                        for (int q = 0; q < 16; ++q) dot = fmaf(v[q], sel.w4[c0 + 16 * h + q], dot);
+                        for (int q = 0; q < 4; ++q) {
+                            const float4 t = ww[q];
+                            dot = fmaf(v[4 * q + 0], t.x, dot);
+                            dot = fmaf(v[4 * q + 1], t.y, dot);
+                            dot = fmaf(v[4 * q + 2], t.z, dot);
+                            dot = fmaf(v[4 * q + 3], t.w, dot);
+                        }
                     } else {
                         uint32_t pk[8];
 #pragma unroll
@@ -432,11 +468,14 @@ __global__ void __launch_bounds__(layer_threads(SELECT), 1)
             __syncwarp();
             if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[b])) : "memory");
             if (SELECT) {
-                // second halves hand their partial sums to the first halves
+                // second halves hand their partial sums to the first halves; the
+                // barrier at the top of the next tile orders this read before the
+                // next write
                 if (half == 1) half_dot[quad * 32 + lane] = dot;
                 asm volatile("bar.sync %0, %1;" ::"n"(kEpiBarrier), "n"(32 * epi_warps(SELECT)) : "memory");
-                if (half == 0 && row < M) select_row(sel, row, dot + half_dot[quad * 32 + lane] + *sel.b4);
-                asm volatile("bar.sync %0, %1;" ::"n"(kEpiBarrier), "n"(32 * epi_warps(SELECT)) : "memory");
+                if (selector && row < M) select_row(sel, row, dot + half_dot[quad * 32 + lane] + b4, ps, pcost);
+                ps = ps_next;
+                pcost = pcost_next;
             }
         }
     }

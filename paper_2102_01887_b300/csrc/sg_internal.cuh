@@ -10,12 +10,10 @@ namespace sgk {
 struct SelectArgs {
     const float *w4 = nullptr;        // [256] row 0 of the last layer
     const float *b4 = nullptr;        // its bias (device)
-    const int32_t *pair_inv = nullptr, *pair_g = nullptr, *pair_x = nullptr;  // per pair
-    const int8_t *cfg_lam = nullptr;  // backend of every configuration
-    const int32_t *lat = nullptr;     // profiled latency of every configuration
-    const int64_t *cost = nullptr;    // profiled cost per invocation of every configuration
-    const int32_t *slack = nullptr;   // [n_inv x n_hw]
-    int n_hw = 0;
+    // per pair: (invocation, op-local configuration index, profiled latency,
+    // slack of the invocation on the configuration's backend)
+    const int4 *pair_sel = nullptr;
+    const int64_t *pair_cost = nullptr;  // per pair: profiled cost per invocation
     float margin = 0.f;               // added to the predicted log factor before selection
     unsigned long long *best = nullptr;  // [n_inv] best key so far
     int32_t *lhat = nullptr;             // [pairs] predicted latency

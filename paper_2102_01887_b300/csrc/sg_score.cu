@@ -74,11 +74,13 @@ __global__ void k_pair_count(llama::DevProblem P, int64_t n_inv, const int32_t *
 }
 
 // First layer of every pair of invocation i (one block per invocation):
-// h1 = ReLU(A[x] + B[i]) in BF16, and the pair's invocation, configuration and
-// op-local index.
+// h1 = ReLU(A[x] + B[i]) in BF16, and the pair's selection record (invocation,
+// op-local index, profiled latency, slack on the configuration's backend) and
+// profiled cost.
 __global__ void k_pair_h1(llama::DevProblem P, const int32_t *dag, const int32_t *op_local, const int32_t *slack,
                           const int64_t *pair_off, const float *__restrict__ A, const float *__restrict__ B,
-                          bf16 *__restrict__ h1, int32_t *pair_inv, int32_t *pair_g, int32_t *pair_x) {
+                          const int8_t *__restrict__ lam, bf16 *__restrict__ h1, int4 *__restrict__ pair_sel,
+                          int64_t *__restrict__ pair_cost) {
     const int64_t i = blockIdx.x;
     if (slack[i * P.n_hw] < 0) return;
     const int32_t g = P.dag_op_off[dag[i]] + op_local[i];
@@ -102,9 +104,9 @@ __global__ void k_pair_h1(llama::DevProblem P, const int32_t *dag, const int32_t
         o.w = *reinterpret_cast<const uint32_t *>(&r3);
         *reinterpret_cast<uint4 *>(h1 + (p0 + x) * kHid + 8 * q) = o;
         if (q == 0) {
-            pair_inv[p0 + x] = (int32_t)i;
-            pair_g[p0 + x] = (int32_t)(c0 + x);
-            pair_x[p0 + x] = x;
+            const int64_t gc = c0 + x;
+            pair_sel[p0 + x] = make_int4((int)i, x, P.lat[gc], slack[i * P.n_hw + lam[gc]]);
+            pair_cost[p0 + x] = P.cost[gc];
         }
     }
 }
@@ -142,7 +144,7 @@ struct llama_sg {
     llama_mlp *net = nullptr;
     int device = 0;
     int64_t max_inv = 0, max_pairs = 0;
-    Buf A, B, h1, h2, pair_inv, pair_g, pair_x, lhat, chat, pair_off, npairs, best, slack, lam, scan_tmp, total_h;
+    Buf A, B, h1, h2, pair_sel, pair_cost, lhat, chat, pair_off, npairs, best, slack, lam, scan_tmp, total_h;
     int64_t last_pairs = 0;
     float margin = 0.f;
     std::string err;
@@ -236,9 +238,8 @@ extern "C" int llama_sg_schedule(llama_sg *s, const void *cfg_x, const void *inv
     const int64_t cap = std::max<int64_t>(total, 1);
     SG_CUDA(s, s->h1.ensure(2 * (size_t)cap * kHid));
     SG_CUDA(s, s->h2.ensure(2 * (size_t)cap * kHid));
-    SG_CUDA(s, s->pair_inv.ensure(4 * (size_t)cap));
-    SG_CUDA(s, s->pair_g.ensure(4 * (size_t)cap));
-    SG_CUDA(s, s->pair_x.ensure(4 * (size_t)cap));
+    SG_CUDA(s, s->pair_sel.ensure(16 * (size_t)cap));
+    SG_CUDA(s, s->pair_cost.ensure(8 * (size_t)cap));
     SG_CUDA(s, s->lhat.ensure(4 * (size_t)cap));
     SG_CUDA(s, s->chat.ensure(8 * (size_t)cap));
     // first layer, split: A = configurations . W1^T, B = contents . W1^T + b1
@@ -248,22 +249,16 @@ extern "C" int llama_sg_schedule(llama_sg *s, const void *cfg_x, const void *inv
     SG_CUDA(s, cudaMemsetAsync(s->best.p, 0xFF, 8 * (size_t)n_inv, st));
     if (total > 0) {
         k_pair_h1<<<(unsigned)n_inv, 256, 0, st>>>(v.P, dag, op_local, s->slack.as<int32_t>(), s->pair_off.as<int64_t>(),
-                                                   s->A.as<float>(), s->B.as<float>(), s->h1.as<bf16>(),
-                                                   s->pair_inv.as<int32_t>(), s->pair_g.as<int32_t>(),
-                                                   s->pair_x.as<int32_t>());
+                                                   s->A.as<float>(), s->B.as<float>(), s->lam.as<int8_t>(),
+                                                   s->h1.as<bf16>(), s->pair_sel.as<int4>(),
+                                                   s->pair_cost.as<int64_t>());
         SG_CUDA(s, cudaGetLastError());
         SG_RC(s, mlp_layer(s->h1.p, nv.w16[1], nv.params + kOffB2, s->h2.p, total, st), "layer 2");
         SelectArgs a;
         a.w4 = nv.params + kOffW4;
         a.b4 = nv.params + kOffB4;
-        a.pair_inv = s->pair_inv.as<int32_t>();
-        a.pair_g = s->pair_g.as<int32_t>();
-        a.pair_x = s->pair_x.as<int32_t>();
-        a.cfg_lam = s->lam.as<int8_t>();
-        a.lat = v.P.lat;
-        a.cost = v.P.cost;
-        a.slack = s->slack.as<int32_t>();
-        a.n_hw = H;
+        a.pair_sel = s->pair_sel.as<int4>();
+        a.pair_cost = s->pair_cost.as<int64_t>();
         a.margin = s->margin;
         a.best = s->best.as<unsigned long long>();
         a.lhat = s->lhat.as<int32_t>();
