@@ -347,7 +347,7 @@ def run_surrogate(args):
                    "training_samples": int(x.shape[0]), "margin": margin,
                    "l2": "flushed before every timed step (256 MiB write)"},
         "pairs_per_s": n_pairs / (step_ms / 1e3),
-        "roofline": {"bound": "tensor", "kernel": "k_mlp_layer (layers 2, 3 + selection)", "achieved": achieved,
+        "roofline": {"bound": "tensor", "kernel": "k_mlp_layer (layers 1 + 2, 3 + selection)", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                      "peak_source": f"{peak_src} sustained cuBLAS bf16", "flops_per_pair": SURROGATE_FLOPS_PER_PAIR,
                      "note": "whole scheduling call (slack, pair set-up, both GEMMs, decode) in the denominator"},
@@ -355,9 +355,10 @@ def run_surrogate(args):
                      "loss_by_epoch": hist},
         "decision_quality": quality,
         "clocks": clocks.summary(),
-        # own kernels per call: critical paths, slack, configuration backends, pair counts,
-        # layer 1 twice, pair set-up, layer 2, layer 3 + selection, decode (CUB's scan not counted)
-        "gpu_launches": 10 * args.steps, "cpu_baseline": None, "e2e": None,
+        # own kernels per call: critical paths, slack, configuration backends, pair keys, rows per
+        # invocation, layer 1 twice, pair set-up, layers 1 + 2, layer 3 + selection, decode
+        # (CUB's sort and scan not counted)
+        "gpu_launches": 11 * args.steps, "cpu_baseline": None, "e2e": None,
     }
     print(json.dumps(line), flush=True)
 

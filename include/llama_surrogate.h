@@ -129,7 +129,8 @@ int64_t llama_sg_last_pairs(llama_sg *sg);
 
 /* Per pair of the last call (pairs of invocation i at pair_off[i] ..
  * pair_off[i+1], in configuration order): predicted latency (int32) and cost
- * (int64); pair_off has n_inv + 1 entries.  Device pointers, each nullable. */
+ * (int64); pair_off has n_inv + 1 entries.  Device pointers, each nullable;
+ * enqueued on `stream`.  n_inv must be the last call's.  Errors: EINVAL. */
 int llama_sg_predictions(llama_sg *sg, int32_t *lhat, int64_t *chat, int64_t *pair_off, int64_t n_inv,
                          void *stream);
 

@@ -30,6 +30,7 @@ constexpr int kBK = 64;             // K per stage: one 128-byte swizzle row of 
 constexpr int kStages = 4;
 constexpr int kThreads = 128;
 constexpr int kMaxTries = 1 << 22;  // bounded mbarrier waits
+static_assert(kBM == kTileRows, "the pair layers' tiles are the GEMM's row tiles");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -249,34 +250,75 @@ __global__ void __launch_bounds__(kThreads, 1)
 // waits (bounded) for its copies and MMAs in flight and frees its tensor memory
 // before it returns.
 //
-// Warp 0 TMA, warp 1 MMA, then the epilogue warps.
-__host__ __device__ constexpr int epi_warps(bool) { return 8; }
-constexpr int kEpiBarrier = 1;  // named barrier of the epilogue warps (0 is __syncthreads)
-__host__ __device__ constexpr int layer_threads(bool select) { return 32 * (2 + epi_warps(select)); }
-constexpr int kLStages = 5;               // A ring of 128 x 64 BF16 slices
+// Layer 2 (kLayerFirst) builds its A operand itself: the first layer splits by
+// linearity into a configuration part (BF16 rows of n_cfg x 256) and an
+// invocation part (FP32 rows of n_inv x 256, bias included), and the pair rows
+// are laid out so that every 128-row tile holds consecutive configurations of
+// one invocation's operation.  Warp 0 loads the tile's configuration rows with
+// TMA into the operand ring; eight converter warps add the invocation's row,
+// apply ReLU and write the BF16 result back in place (same swizzled layout);
+// only then does warp 1 issue the MMAs on that slice.
+//
+// Warp 0 TMA, warp 1 MMA, then the epilogue warps, then the converter warps.
+constexpr int kLayerSelect = 1;  // A rows from a BF16 matrix; last layer and selection
+constexpr int kLayerFirst = 2;   // A rows built from the split first layer; BF16 rows out
+__host__ __device__ constexpr int epi_warps() { return 8; }
+__host__ __device__ constexpr int conv_warps(int mode) { return mode == kLayerFirst ? 8 : 0; }
+constexpr int kConvPasses = kBM / 8 / 4;  // four rows per pass, kBM / 8 rows per converter warp
+constexpr int kEpiBarrier = 1;   // named barrier of the epilogue warps (0 is __syncthreads)
+constexpr int kConvBarrier = 2;  // named barrier of the converter warps
+__host__ __device__ constexpr int layer_threads(int mode) { return 32 * (2 + epi_warps() + conv_warps(mode)); }
+constexpr int kLStagesMax = 5;            // A ring of 128 x 64 BF16 slices
 constexpr int kLSlices = kHid / kBK;      // K slices per tile (4)
 constexpr int kLWSlice = kHid * kBK * 2;  // 256 x 64 BF16 = 32 KB
 constexpr int kLWBytes = kLSlices * kLWSlice;
 constexpr int kLABytes = kBM * kBK * 2;   // 16 KB
-constexpr int kLSmem = kLWBytes + kLStages * kLABytes + 1024;
+// kLayerFirst stages its output through shared memory (a 32 x 32 BF16 block
+// per epilogue warp, stored by TMA) and keeps one A slice fewer for it
+constexpr int kLStageBytes = 32 * 32 * 2;
+__host__ __device__ constexpr int layer_stages(int mode) { return mode == kLayerFirst ? 4 : kLStagesMax; }
+__host__ __device__ constexpr int layer_smem(int mode) {
+    return kLWBytes + layer_stages(mode) * kLABytes + (mode == kLayerFirst ? epi_warps() * kLStageBytes : 0) + 1024;
+}
 
 // All lanes of the warp agree: true only if every lane's bounded wait completed.
 __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity) {
     return __all_sync(0xffffffffu, mbar_wait(bar, parity));
 }
 
-template <bool SELECT>
-__global__ void __launch_bounds__(layer_threads(SELECT), 1)
-    k_mlp_layer(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmW, int M,
-                const float *__restrict__ bias, __nv_bfloat16 *__restrict__ c16, int *err,
-                const __grid_constant__ SelectArgs sel) {
+// One 16-byte unit (eight BF16 columns) of a swizzled slice: ReLU(a + b), b
+// the invocation part of those columns.
+__device__ __forceinline__ uint4 relu_add_unit(uint4 a, const float *b) {
+    uint32_t v[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float lo = __uint_as_float(v[q] << 16) + b[2 * q], hi = __uint_as_float(v[q] & 0xFFFF0000u) + b[2 * q + 1];
+        const __nv_bfloat162 r = __floats2bfloat162_rn(fmaxf(lo, 0.f), fmaxf(hi, 0.f));
+        v[q] = *reinterpret_cast<const uint32_t *>(&r);
+    }
+    return make_uint4(v[0], v[1], v[2], v[3]);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(layer_threads(MODE), 1)
+    k_mlp_layer(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmW,
+                const __grid_constant__ CUtensorMap tmC, int M, const float *__restrict__ bias,
+                __nv_bfloat16 *__restrict__ c16, int *err,
+                const __grid_constant__ SelectArgs sel, const int2 *__restrict__ tile_info,
+                const float4 *__restrict__ b_inv) {
+    constexpr bool SELECT = MODE == kLayerSelect, FIRST = MODE == kLayerFirst;
+    constexpr int kLStages = layer_stages(MODE);
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t full[kLStages], empty[kLStages], wbar, accf[2], acce[2];
+    __shared__ __align__(8) uint64_t full[kLStages], empty[kLStages], ready[FIRST ? kLStages : 1], wbar, accf[2],
+        acce[2];
     __shared__ uint32_t tmem_slot;
     __shared__ int failed, issued, consumed, committed;
     __shared__ float half_dot[SELECT ? kBM : 1];  // second halves of the rows' last-layer dot products
     __shared__ __align__(16) float s_bias[kHid];
     __shared__ __align__(16) float s_w4[SELECT ? kHid : 4];
+    // invocation part of this and the last tile, float4 (k, half, unit) at
+    // 16k + 8half + unit: unit u of K-slice k covers columns 64k + 8u .. 64k + 8u + 7
+    __shared__ __align__(16) float4 s_binv[FIRST ? 2 : 1][kHid / 4];
     const uint32_t wbase = (smem_u32(smem_raw) + 1023u) & ~1023u, abase = wbase + kLWBytes;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_tiles = (M + kBM - 1) / kBM;
@@ -285,11 +327,12 @@ __global__ void __launch_bounds__(layer_threads(SELECT), 1)
         for (int k = 0; k < kLStages; ++k) {
             mbar_init(smem_u32(&full[k]), 1);
             mbar_init(smem_u32(&empty[k]), 1);
+            if (FIRST) mbar_init(smem_u32(&ready[k]), conv_warps(MODE));  // one arrival per converter warp
         }
         mbar_init(smem_u32(&wbar), 1);
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&accf[b]), 1);
-            mbar_init(smem_u32(&acce[b]), epi_warps(SELECT));  // one arrival per epilogue warp
+            mbar_init(smem_u32(&acce[b]), epi_warps());  // one arrival per epilogue warp
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         failed = issued = consumed = committed = 0;
@@ -315,8 +358,13 @@ __global__ void __launch_bounds__(layer_threads(SELECT), 1)
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(wb), "r"(kLWBytes) : "memory");
         for (int k = 0; k < kLSlices; ++k) tma_load_2d(wbase + k * kLWSlice, &tmW, k * kBK, 0, wb);
         int g = 0;
+        // the first configuration row of each tile (kLayerFirst), loaded a tile ahead
+        int arow = 0, arow_next = 0;
+        if (FIRST && my_tiles > 0) arow = __ldg(&tile_info[blockIdx.x].x);
         for (int j = 0; j < my_tiles && !*vfailed; ++j) {
-            const int m0 = ((int)blockIdx.x + j * (int)gridDim.x) * kBM;
+            const int t = (int)blockIdx.x + j * (int)gridDim.x;
+            if (FIRST && j + 1 < my_tiles) arow_next = __ldg(&tile_info[t + (int)gridDim.x].x);
+            const int m0 = FIRST ? arow : t * kBM;
             int k = 0;
             for (; k < kLSlices; ++k, ++g) {
                 const int st = g % kLStages;
@@ -330,6 +378,7 @@ __global__ void __launch_bounds__(layer_threads(SELECT), 1)
                 tma_load_2d(abase + st * kLABytes, &tmA, k * kBK, m0, bar);
             }
             if (k < kLSlices) break;
+            arow = arow_next;
         }
         issued = g;
     } else if (warp == 1 && lane == 0) {
@@ -347,7 +396,8 @@ __global__ void __launch_bounds__(layer_threads(SELECT), 1)
             const uint32_t acc = tmem + (uint32_t)(b * kHid);
             for (int k = 0; k < kLSlices; ++k, ++g) {
                 const int st = g % kLStages;
-                if (!mbar_wait(smem_u32(&full[st]), (g / kLStages) & 1)) {
+                // kLayerFirst: the converters have finished the slice
+                if (!mbar_wait(smem_u32(FIRST ? &ready[st] : &full[st]), (g / kLStages) & 1)) {
                     ok = false;
                     break;
                 }
@@ -372,11 +422,70 @@ __global__ void __launch_bounds__(layer_threads(SELECT), 1)
         if (!ok) *vfailed = 1;
         consumed = g;
         committed = j;  // tiles whose accumulator commit was issued
+    } else if (FIRST && warp >= 2 + epi_warps()) {
+        // converters: warp cw owns rows 16cw .. 16cw+15 of every slice; a pass
+        // covers four rows, lane l the 16-byte unit l%8 (physical position) of
+        // row l/8 of the pass, so every 8-lane phase touches one 128-byte row
+        const int cw = warp - 2 - epi_warps(), ct = (int)threadIdx.x - 32 * (2 + epi_warps());
+        // lane l converts logical unit u = l % 8 (columns 8u .. 8u + 7 of the
+        // slice) of row l / 8 of each pass; the 128-byte swizzle puts unit u of
+        // row r at position u ^ (r % 8), so a phase of eight lanes still covers
+        // one whole 128-byte row
+        const int uu = lane & 7, rr = lane >> 3;
+        const int p0 = uu ^ rr, p1 = uu ^ (rr + 4);  // positions in even and odd passes
+        uint8_t *const ring = smem_raw + (abase - smem_u32(smem_raw));  // generic address of the A ring
+        // float4 f of the invocation part (columns 4f .. 4f + 3) goes to 16k + 8half + unit
+        const int sbf = ct < kHid / 4 ? (ct / 16) * 16 + (ct % 2) * 8 + (ct % 16) / 2 : 0;
+        float4 bnext = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (my_tiles > 0 && ct < kHid / 4) bnext = __ldg(&b_inv[(int64_t)__ldg(&tile_info[blockIdx.x].y) * (kHid / 4) + ct]);
+        int g = 0;
+        bool ok = true;
+        for (int j = 0; j < my_tiles; ++j) {
+            const int t = (int)blockIdx.x + j * (int)gridDim.x;
+            float4 *sb = s_binv[j & 1];
+            if (ct < kHid / 4) sb[sbf] = bnext;
+            if (j + 1 < my_tiles && ct < kHid / 4)
+                bnext = __ldg(&b_inv[(int64_t)__ldg(&tile_info[t + (int)gridDim.x].y) * (kHid / 4) + ct]);
+            // every converter warp agrees to go on (and has finished the tile
+            // before last, whose buffer of the invocation part is rewritten above)
+            int all_ok;
+            asm volatile("{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n"
+                         " bar.red.and.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+                         : "=r"(all_ok) : "r"((unsigned)ok), "n"(kConvBarrier), "n"(32 * conv_warps(MODE)));
+            if (!all_ok) break;
+            for (int k = 0; k < kLSlices; ++k, ++g) {
+                const int st = g % kLStages;
+                if (!warp_wait(smem_u32(&full[st]), (g / kLStages) & 1)) {
+                    ok = false;
+                    break;
+                }
+                float bu[8];
+                *reinterpret_cast<float4 *>(bu) = sb[16 * k + uu];
+                *reinterpret_cast<float4 *>(bu + 4) = sb[16 * k + 8 + uu];
+                uint8_t *const rows = ring + st * kLABytes + (16 * cw + rr) * 128;
+                uint4 v[kConvPasses];
+#pragma unroll
+                for (int pass = 0; pass < kConvPasses; ++pass)
+                    v[pass] = *reinterpret_cast<const uint4 *>(rows + pass * 4 * 128 + ((pass & 1) ? p1 : p0) * 16);
+#pragma unroll
+                for (int pass = 0; pass < kConvPasses; ++pass)
+                    *reinterpret_cast<uint4 *>(rows + pass * 4 * 128 + ((pass & 1) ? p1 : p0) * 16) =
+                        relu_add_unit(v[pass], bu);
+                // the generic-proxy writes become visible to the tensor cores
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ready[st])) : "memory");
+            }
+        }
+        if (!ok && lane == 0) *vfailed = 1;
     } else if (warp >= 2) {
         // epilogue: this warp's quarter of every tile's rows, its share of the columns
-        constexpr int kCols = kHid * 4 / epi_warps(SELECT);
+        constexpr int kCols = kHid * 4 / epi_warps();
         const int quad = warp & 3, half = (warp - 2) >> 2, cbeg = half * kCols;
         const auto row_of = [&](int jj) { return ((int)blockIdx.x + jj * (int)gridDim.x) * kBM + quad * 32 + lane; };
+        // kLayerFirst: this warp's staging block (32 rows of 64 bytes, 64-byte swizzle)
+        const uint32_t stage = abase + kLStages * kLABytes + (uint32_t)(warp - 2) * kLStageBytes;
+        uint8_t *const stage_g = smem_raw + (stage - smem_u32(smem_raw));
         const bool selector = SELECT && half == 0;
         const float b4 = SELECT ? *sel.b4 : 0.f;
         // the selection records of a tile's rows are loaded one tile ahead
@@ -401,7 +510,7 @@ __global__ void __launch_bounds__(layer_threads(SELECT), 1)
                 int all_ok;
                 asm volatile("{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n"
                              " bar.red.and.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}\n"
-                             : "=r"(all_ok) : "r"((unsigned)got), "n"(kEpiBarrier), "n"(32 * epi_warps(SELECT)));
+                             : "=r"(all_ok) : "r"((unsigned)got), "n"(kEpiBarrier), "n"(32 * epi_warps()));
                 if (!all_ok) {
                     if (lane == 0) *vfailed = 1;
                     break;
@@ -427,7 +536,8 @@ __global__ void __launch_bounds__(layer_threads(SELECT), 1)
                       "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
                     : "r"(tbase + (uint32_t)c0));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (row >= M) continue;
+                if (SELECT && row >= M) continue;  // (kLayerFirst: M is a whole number of tiles)
+                uint32_t pk[16];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     float v[16];
@@ -451,15 +561,29 @@ __global__ void __launch_bounds__(layer_threads(SELECT), 1)
                             dot = fmaf(v[4 * q + 3], t.w, dot);
                         }
                     } else {
-                        uint32_t pk[8];
 #pragma unroll
                         for (int q = 0; q < 8; ++q) {
                             const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
-                            pk[q] = *reinterpret_cast<const uint32_t *>(&b2);
+                            pk[8 * h + q] = *reinterpret_cast<const uint32_t *>(&b2);
                         }
-                        __nv_bfloat16 *o = c16 + (int64_t)row * kHid + c0 + 16 * h;
-                        *reinterpret_cast<uint4 *>(o) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                        *reinterpret_cast<uint4 *>(o + 8) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                    }
+                }
+                if (FIRST) {
+                    // the staging block is free once the last store from it has read it
+                    if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                    __syncwarp();
+                    uint4 *srow = reinterpret_cast<uint4 *>(stage_g + lane * 64);
+                    const int sw = (lane >> 1) & 3;  // 64-byte swizzle: unit c of row r at c ^ ((r / 2) % 4)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        srow[c ^ sw] = make_uint4(pk[4 * c], pk[4 * c + 1], pk[4 * c + 2], pk[4 * c + 3]);
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) {
+                        asm volatile(
+                            "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];"
+                            ::"l"(reinterpret_cast<uint64_t>(&tmC)), "r"(c0), "r"(row - lane), "r"(stage) : "memory");
+                        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
                     }
                 }
             }
@@ -472,12 +596,15 @@ __global__ void __launch_bounds__(layer_threads(SELECT), 1)
                 // barrier at the top of the next tile orders this read before the
                 // next write
                 if (half == 1) half_dot[quad * 32 + lane] = dot;
-                asm volatile("bar.sync %0, %1;" ::"n"(kEpiBarrier), "n"(32 * epi_warps(SELECT)) : "memory");
-                if (selector && row < M) select_row(sel, row, dot + half_dot[quad * 32 + lane] + b4, ps, pcost);
+                asm volatile("bar.sync %0, %1;" ::"n"(kEpiBarrier), "n"(32 * epi_warps()) : "memory");
+                if (selector && row < M && ps.x >= 0)  // padding rows have no invocation
+                    select_row(sel, row, dot + half_dot[quad * 32 + lane] + b4, ps, pcost);
                 ps = ps_next;
                 pcost = pcost_next;
             }
         }
+        // the output stores are complete before the CTA (and its shared memory) ends
+        if (FIRST && lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     }
     __syncwarp();
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -535,6 +662,21 @@ int make_map(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, int 
     return r == CUDA_SUCCESS ? LLAMA_OK : LLAMA_EINVAL;
 }
 
+// Output map of kLayerFirst: row-major BF16 [rows x cols], 32 x 32 blocks,
+// 64-byte swizzle (the staging layout of the epilogue).
+int make_store_map(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols) {
+    EncodeTiled enc = encoder();
+    if (!enc) return LLAMA_ECUDA;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    const cuuint32_t box[2] = {32, 32};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box,
+                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                           CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? LLAMA_OK : LLAMA_EINVAL;
+}
+
 template <int BN>
 cudaError_t launch_gemm(const CUtensorMap &ta, const CUtensorMap &tb, int64_t M, int N, int K, const float *bias,
                         int flags, void *c16, float *c32, int ldc, int *err, cudaStream_t s) {
@@ -581,43 +723,56 @@ int gemm(const void *a, const void *b, const float *bias, void *c16, float *c32,
     return e == cudaSuccess ? LLAMA_OK : LLAMA_ECUDA;
 }
 
-// The persistent pair layer (see k_mlp_layer): a [m x 256] BF16, w [256 x 256]
-// BF16 (row n = output n), bias [256] FP32; c16 [m x 256] BF16 (SELECT false)
-// or the fused last layer and selection (SELECT true).
-template <bool SELECT>
-int mlp_layer_impl(const void *a, const void *w, const float *bias, void *c16, int64_t m, const SelectArgs &sel,
-                   cudaStream_t s) {
-    if (!a || !w || !bias || (!SELECT && !c16) || m < 1 || m > (1 << 30)) return LLAMA_EINVAL;
-    if ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(w) | reinterpret_cast<uintptr_t>(c16)) & 15)
+// The persistent pair layer (see k_mlp_layer) over m rows: a, BF16 with 256
+// columns, holds the rows of A (a_rows of them: m, or the configurations for
+// kLayerFirst); w [256 x 256] BF16 (row n = output n), bias [256] FP32; c16
+// [m x 256] BF16 out (kLayerFirst) or the fused last layer and selection
+// (kLayerSelect).
+template <int MODE>
+int mlp_layer_impl(const void *a, int64_t a_rows, const void *w, const float *bias, void *c16, int64_t m,
+                   const SelectArgs &sel, const int2 *tile_info, const float *b_inv, cudaStream_t s) {
+    if (!a || !w || !bias || (MODE != kLayerSelect && !c16) || m < 1 || m > (1 << 30) || a_rows < 1 ||
+        a_rows > (1 << 30))
+        return LLAMA_EINVAL;
+    if (MODE == kLayerFirst && (!tile_info || !b_inv || m % kBM)) return LLAMA_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(w) | reinterpret_cast<uintptr_t>(c16) |
+         reinterpret_cast<uintptr_t>(b_inv)) & 15)
         return LLAMA_EINVAL;
     int *err = error_word();
     if (!err) return LLAMA_ENOMEM;
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
     std::call_once(once, [] {
-        attr = cudaFuncSetAttribute(k_mlp_layer<SELECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kLSmem);
+        attr = cudaFuncSetAttribute(k_mlp_layer<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, layer_smem(MODE));
     });
     if (attr != cudaSuccess) return LLAMA_ECUDA;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return LLAMA_ECUDA;
-    CUtensorMap ta, tw;
-    if (make_map(&ta, a, m, kHid, kBM) != LLAMA_OK || make_map(&tw, w, kHid, kHid, kHid) != LLAMA_OK)
+    CUtensorMap ta, tw, tc;
+    if (make_map(&ta, a, a_rows, kHid, kBM) != LLAMA_OK || make_map(&tw, w, kHid, kHid, kHid) != LLAMA_OK)
         return LLAMA_EINVAL;
+    if (MODE == kLayerFirst) {
+        if (make_store_map(&tc, c16, m, kHid) != LLAMA_OK) return LLAMA_EINVAL;
+    } else {
+        tc = ta;  // unused
+    }
     const int64_t tiles = (m + kBM - 1) / kBM;
     const unsigned grid = (unsigned)std::min<int64_t>(tiles, sms);
-    k_mlp_layer<SELECT><<<grid, layer_threads(SELECT), kLSmem, s>>>(ta, tw, (int)m, bias, static_cast<__nv_bfloat16 *>(c16), err,
-                                                        sel);
+    k_mlp_layer<MODE><<<grid, layer_threads(MODE), layer_smem(MODE), s>>>(
+        ta, tw, tc, (int)m, bias, static_cast<__nv_bfloat16 *>(c16), err, sel, tile_info,
+        reinterpret_cast<const float4 *>(b_inv));
     return cudaGetLastError() == cudaSuccess ? LLAMA_OK : LLAMA_ECUDA;
 }
 
-int mlp_layer(const void *a, const void *w, const float *bias, void *c16, int64_t m, cudaStream_t s) {
-    return mlp_layer_impl<false>(a, w, bias, c16, m, SelectArgs{}, s);
+int mlp_layer_first(const void *a_cfg, int64_t n_cfg, const float *b_inv, const int2 *tile_info, const void *w,
+                    const float *bias, void *c16, int64_t m, cudaStream_t s) {
+    return mlp_layer_impl<kLayerFirst>(a_cfg, n_cfg, w, bias, c16, m, SelectArgs{}, tile_info, b_inv, s);
 }
 
 int mlp_layer_select(const void *a, const void *w, const float *bias, int64_t m, const SelectArgs &sel,
                      cudaStream_t s) {
-    return mlp_layer_impl<true>(a, w, bias, nullptr, m, sel, s);
+    return mlp_layer_impl<kLayerSelect>(a, m, w, bias, nullptr, m, sel, nullptr, nullptr, s);
 }
 
 }  // namespace sgk

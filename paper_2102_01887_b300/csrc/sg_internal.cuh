@@ -30,16 +30,22 @@ struct llama_mlp_view {
 };
 
 // The pair layers of the scheduling path on the persistent kernel (weights kept
-// in shared memory, double-buffered accumulators): c16 = ReLU(a . w^T + bias),
-// a [m x 256], w [256 x 256], BF16; and the same layer with the fused last layer
-// and selection in place of the store.
-int mlp_layer(const void *a, const void *w, const float *bias, void *c16, int64_t m, cudaStream_t s);
+// in shared memory, double-buffered accumulators), w [256 x 256] BF16.
+// Layer 2 with the first layer built in the kernel: row r of tile t (128 rows)
+// has h1 = ReLU(a_cfg[tile_info[t].x + r] + b_inv[tile_info[t].y]) (a_cfg BF16
+// [n_cfg x 256], b_inv FP32 [n_inv x 256]), c16 [m x 256] = ReLU(h1 . w^T + bias)
+// in BF16, m a multiple of 128.
+int mlp_layer_first(const void *a_cfg, int64_t n_cfg, const float *b_inv, const int2 *tile_info, const void *w,
+                    const float *bias, void *c16, int64_t m, cudaStream_t s);
+// Layer 3 over a [m x 256] BF16 with the fused last layer and selection; rows
+// whose selection record has a negative invocation are skipped.
 int mlp_layer_select(const void *a, const void *w, const float *bias, int64_t m, const SelectArgs &sel,
                      cudaStream_t s);
 // The device word that bounded waits of the GEMM set when they give up.
 int *error_word();
 
 constexpr int kIn = 64, kHid = 256, kOut = 64;  // network widths (inputs and outputs padded)
+constexpr int kTileRows = 128;                   // rows per tile of the pair layers
 // flat parameter layout: W1[256x64] b1 W2[256x256] b2 W3[256x256] b3 W4[64x256] b4[64]
 constexpr int64_t kOffW1 = 0, kOffB1 = kOffW1 + kHid * kIn, kOffW2 = kOffB1 + kHid,
                   kOffB2 = kOffW2 + kHid * kHid, kOffW3 = kOffB2 + kHid, kOffB3 = kOffW3 + kHid * kHid,

@@ -46,9 +46,7 @@ struct Buf {
     T *as() const { return static_cast<T *>(p); }
 };
 
-using bf16 = __nv_bfloat16;
-
-// Backend of every configuration (its segment), and pairs per invocation.
+// Backend of every configuration (its segment).
 __global__ void k_cfg_backend(llama::DevProblem P, int8_t *lam) {
     const int v = blockIdx.x, H = P.n_hw;
     const int64_t c0 = P.cfg_off[v];
@@ -61,59 +59,86 @@ __global__ void k_cfg_backend(llama::DevProblem P, int8_t *lam) {
     }
 }
 
-__global__ void k_pair_count(llama::DevProblem P, int64_t n_inv, const int32_t *dag, const int32_t *op_local,
-                             const int32_t *slack, int64_t *npairs) {
+// Grouping of the invocations by operation: the key of invocation i is its
+// operation (n_ops when it has no decision, so it sorts last), the value i; the
+// number of its pairs is kept and added to the total.
+__global__ void k_pair_keys(llama::DevProblem P, int64_t n_inv, const int32_t *dag, const int32_t *op_local,
+                            const int32_t *slack, int32_t *key, int32_t *idx, int64_t *npairs,
+                            unsigned long long *total) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i > n_inv) return;
-    int64_t k = 0;
-    if (i < n_inv && slack[i * P.n_hw] >= 0) {
-        const int32_t g = P.dag_op_off[dag[i]] + op_local[i];
-        k = P.cfg_off[g + 1] - P.cfg_off[g];
+    unsigned k = 0;
+    if (i == n_inv) npairs[i] = 0;  // the exclusive scan's last value is the total
+    if (i < n_inv) {
+        int32_t g = P.n_ops;
+        if (slack[i * P.n_hw] >= 0) {
+            g = P.dag_op_off[dag[i]] + op_local[i];
+            k = (unsigned)(P.cfg_off[g + 1] - P.cfg_off[g]);
+        }
+        key[i] = g;
+        idx[i] = (int32_t)i;
+        npairs[i] = k;
     }
-    npairs[i] = k;  // entry n_inv is 0: the exclusive scan's last value is the total
+    const unsigned w = __reduce_add_sync(0xffffffffu, k);
+    if ((threadIdx.x & 31) == 0 && w) atomicAdd(total, (unsigned long long)w);
 }
 
-// First layer of every pair of invocation i (one block per invocation):
-// h1 = ReLU(A[x] + B[i]) in BF16, and the pair's selection record (invocation,
-// op-local index, profiled latency, slack on the configuration's backend) and
-// profiled cost.
-__global__ void k_pair_h1(llama::DevProblem P, const int32_t *dag, const int32_t *op_local, const int32_t *slack,
-                          const int64_t *pair_off, const float *__restrict__ A, const float *__restrict__ B,
-                          const int8_t *__restrict__ lam, bf16 *__restrict__ h1, int4 *__restrict__ pair_sel,
-                          int64_t *__restrict__ pair_cost) {
-    const int64_t i = blockIdx.x;
-    if (slack[i * P.n_hw] < 0) return;
-    const int32_t g = P.dag_op_off[dag[i]] + op_local[i];
-    const int64_t c0 = P.cfg_off[g];
-    const int n = (int)(P.cfg_off[g + 1] - c0);
-    const int64_t p0 = pair_off[i];
-    const float4 *b4 = reinterpret_cast<const float4 *>(B + i * kHid);
-    // 32 threads per pair row, 8 columns each
-    for (int64_t w = threadIdx.x; w < (int64_t)n * 32; w += blockDim.x) {
-        const int x = (int)(w >> 5), q = (int)(w & 31);
-        const float4 *a4 = reinterpret_cast<const float4 *>(A + (c0 + x) * kHid);
-        const float4 u0 = a4[2 * q], u1 = a4[2 * q + 1], v0 = b4[2 * q], v1 = b4[2 * q + 1];
-        const __nv_bfloat162 r0 = __floats2bfloat162_rn(fmaxf(u0.x + v0.x, 0.f), fmaxf(u0.y + v0.y, 0.f));
-        const __nv_bfloat162 r1 = __floats2bfloat162_rn(fmaxf(u0.z + v0.z, 0.f), fmaxf(u0.w + v0.w, 0.f));
-        const __nv_bfloat162 r2 = __floats2bfloat162_rn(fmaxf(u1.x + v1.x, 0.f), fmaxf(u1.y + v1.y, 0.f));
-        const __nv_bfloat162 r3 = __floats2bfloat162_rn(fmaxf(u1.z + v1.z, 0.f), fmaxf(u1.w + v1.w, 0.f));
-        uint4 o;
-        o.x = *reinterpret_cast<const uint32_t *>(&r0);
-        o.y = *reinterpret_cast<const uint32_t *>(&r1);
-        o.z = *reinterpret_cast<const uint32_t *>(&r2);
-        o.w = *reinterpret_cast<const uint32_t *>(&r3);
-        *reinterpret_cast<uint4 *>(h1 + (p0 + x) * kHid + 8 * q) = o;
-        if (q == 0) {
+// Rows of every invocation in operation order: its pairs rounded up to whole
+// 128-row tiles (entry n_inv is 0: the exclusive scan's last value is the total).
+__global__ void k_pair_rows(llama::DevProblem P, int64_t n_inv, const int32_t *key, int64_t *nrows) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k > n_inv) return;
+    int64_t r = 0;
+    if (k < n_inv && key[k] < P.n_ops) {
+        const int32_t g = key[k];
+        r = (P.cfg_off[g + 1] - P.cfg_off[g] + kTileRows - 1) / kTileRows * kTileRows;
+    }
+    nrows[k] = r;
+}
+
+// The rows of the k-th invocation in operation order (one block each): each
+// pair's selection record (invocation, op-local index, profiled latency, slack
+// on the configuration's backend; invocation -1 on a padding row) and profiled
+// cost, every tile's first configuration row and invocation, and the
+// invocation's first row.
+__global__ void k_pair_index(llama::DevProblem P, const int32_t *key, const int32_t *idx, const int64_t *row_off,
+                             const int32_t *slack, const int8_t *__restrict__ lam, int64_t *inv_row,
+                             int4 *__restrict__ pair_sel, int64_t *__restrict__ pair_cost, int2 *__restrict__ tile_info) {
+    const int64_t k = blockIdx.x;
+    const int32_t i = idx[k], g = key[k];
+    if (g >= P.n_ops) {
+        if (threadIdx.x == 0) inv_row[i] = -1;
+        return;
+    }
+    const int64_t c0 = P.cfg_off[g], r0 = row_off[k];
+    const int n = (int)(P.cfg_off[g + 1] - c0), nr = (int)(row_off[k + 1] - r0);
+    if (threadIdx.x == 0) inv_row[i] = r0;
+    for (int x = threadIdx.x; x < nr; x += blockDim.x) {
+        if (x < n) {
             const int64_t gc = c0 + x;
-            pair_sel[p0 + x] = make_int4((int)i, x, P.lat[gc], slack[i * P.n_hw + lam[gc]]);
-            pair_cost[p0 + x] = P.cost[gc];
+            pair_sel[r0 + x] = make_int4(i, x, P.lat[gc], slack[(int64_t)i * P.n_hw + lam[gc]]);
+            pair_cost[r0 + x] = P.cost[gc];
+        } else {
+            pair_sel[r0 + x] = make_int4(-1, 0, 0, 0);
         }
+        if (x % kTileRows == 0) tile_info[(r0 + x) / kTileRows] = make_int2((int)(c0 + x), i);
+    }
+}
+
+// Predictions of the last call in invocation order (pairs of invocation i at
+// pair_off[i] ..), from the rows in operation order.
+__global__ void k_pair_compact(int64_t n_inv, const int64_t *pair_off, const int64_t *inv_row,
+                               const int32_t *lhat_rows, const int64_t *chat_rows, int32_t *lhat, int64_t *chat) {
+    const int64_t i = blockIdx.x;
+    const int64_t p0 = pair_off[i], n = pair_off[i + 1] - p0, r0 = inv_row[i];
+    for (int64_t x = threadIdx.x; x < n; x += blockDim.x) {
+        if (lhat) lhat[p0 + x] = lhat_rows[r0 + x];
+        if (chat) chat[p0 + x] = chat_rows[r0 + x];
     }
 }
 
 // The decision of every invocation from its best key.
 __global__ void k_sg_decode(llama::DevProblem P, int64_t n_inv, const int32_t *dag, const int32_t *op_local,
-                            const int32_t *slack, const int64_t *pair_off, const unsigned long long *best,
+                            const int32_t *slack, const int64_t *inv_row, const unsigned long long *best,
                             const int32_t *lhat, const int64_t *chat, const int8_t *lam, llama_decision *out) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n_inv) return;
@@ -127,7 +152,7 @@ __global__ void k_sg_decode(llama::DevProblem P, int64_t n_inv, const int32_t *d
     } else {
         const int32_t g = P.dag_op_off[dag[i]] + op_local[i];
         const int32_t x = (int32_t)(best[i] & 0x1FFFull);
-        const int64_t p = pair_off[i] + x;
+        const int64_t p = inv_row[i] + x;
         d.cfg = x;
         d.lat = lhat[p];
         d.cost = chat[p];
@@ -144,8 +169,11 @@ struct llama_sg {
     llama_mlp *net = nullptr;
     int device = 0;
     int64_t max_inv = 0, max_pairs = 0;
-    Buf A, B, h1, h2, pair_sel, pair_cost, lhat, chat, pair_off, npairs, best, slack, lam, scan_tmp, total_h;
-    int64_t last_pairs = 0;
+    // A: configuration part of layer 1 (BF16), B: invocation part (FP32); rows of
+    // the pair layers in operation order, 128 per tile
+    Buf A, B, h2, pair_sel, pair_cost, lhat, chat, tile_info, key, key_sorted, idx, idx_sorted, npairs, nrows,
+        row_off, inv_row, pair_off, best, slack, lam, scan_tmp, total;
+    int64_t last_pairs = 0, last_n_inv = 0;
     float margin = 0.f;
     std::string err;
 };
@@ -194,7 +222,10 @@ extern "C" int llama_sg_schedule(llama_sg *s, const void *cfg_x, const void *inv
                                  int64_t now_us, llama_decision *out, void *stream) {
     if (!s) return LLAMA_EINVAL;
     if (n_inv < 0 || n_inv > s->max_inv) return sg_fail(s, LLAMA_EINVAL, "schedule: n_inv outside 0..max_inv");
-    if (n_inv == 0) return LLAMA_OK;
+    if (n_inv == 0) {
+        s->last_pairs = s->last_n_inv = 0;
+        return LLAMA_OK;
+    }
     if (!cfg_x || !inv_x || !dag || !op_local || !start_us || !out)
         return sg_fail(s, LLAMA_EINVAL, "schedule: null pointer");
     llama::ContextView v;
@@ -208,52 +239,80 @@ extern "C" int llama_sg_schedule(llama_sg *s, const void *cfg_x, const void *inv
     const int H = v.n_hw;
     int64_t n_cfg = 0;
     SG_CUDA(s, cudaMemcpy(&n_cfg, v.P.cfg_off + v.n_ops, sizeof(int64_t), cudaMemcpyDeviceToHost));
-    SG_CUDA(s, s->A.ensure(4 * (size_t)n_cfg * kHid));
+    const size_t ni = (size_t)s->max_inv;
+    SG_CUDA(s, s->A.ensure(2 * (size_t)n_cfg * kHid));
     SG_CUDA(s, s->lam.ensure((size_t)n_cfg));
-    SG_CUDA(s, s->B.ensure(4 * (size_t)s->max_inv * kHid));
-    SG_CUDA(s, s->slack.ensure(4 * (size_t)s->max_inv * H));
-    SG_CUDA(s, s->npairs.ensure(8 * (size_t)(s->max_inv + 1)));
-    SG_CUDA(s, s->pair_off.ensure(8 * (size_t)(s->max_inv + 1)));
-    SG_CUDA(s, s->best.ensure(8 * (size_t)s->max_inv));
-    SG_CUDA(s, s->total_h.ensure(8));
+    SG_CUDA(s, s->B.ensure(4 * ni * kHid));
+    SG_CUDA(s, s->slack.ensure(4 * ni * H));
+    SG_CUDA(s, s->key.ensure(4 * ni));
+    SG_CUDA(s, s->key_sorted.ensure(4 * ni));
+    SG_CUDA(s, s->idx.ensure(4 * ni));
+    SG_CUDA(s, s->idx_sorted.ensure(4 * ni));
+    SG_CUDA(s, s->npairs.ensure(8 * (ni + 1)));
+    SG_CUDA(s, s->nrows.ensure(8 * (ni + 1)));
+    SG_CUDA(s, s->row_off.ensure(8 * (ni + 1)));
+    SG_CUDA(s, s->inv_row.ensure(8 * ni));
+    SG_CUDA(s, s->best.ensure(8 * ni));
+    SG_CUDA(s, s->total.ensure(8));
     // a1 + a2 on the profiled reference latencies
     llama::k_critical_paths<<<std::max(1, (v.n_dags + 7) / 8), 256, 0, st>>>(v.P, v.topo, v.lvl_off, v.dag_lvl);
     llama::k_slack<<<(unsigned)std::min<int64_t>((n_inv + 255) / 256, 65535), 256, 0, st>>>(
         v.P, n_inv, dag, op_local, start_us, now_us, s->slack.as<int32_t>());
     k_cfg_backend<<<v.n_ops, 256, 0, st>>>(v.P, s->lam.as<int8_t>());
-    k_pair_count<<<(unsigned)((n_inv + 256) / 256), 256, 0, st>>>(v.P, n_inv, dag, op_local, s->slack.as<int32_t>(),
-                                                                  s->npairs.as<int64_t>());
+    SG_CUDA(s, cudaMemsetAsync(s->total.p, 0, 8, st));
+    k_pair_keys<<<(unsigned)((n_inv + 256) / 256), 256, 0, st>>>(v.P, n_inv, dag, op_local, s->slack.as<int32_t>(),
+                                                                 s->key.as<int32_t>(), s->idx.as<int32_t>(),
+                                                                 s->npairs.as<int64_t>(),
+                                                                 s->total.as<unsigned long long>());
     SG_CUDA(s, cudaGetLastError());
-    size_t tmp = 0;
-    SG_CUDA(s, cub::DeviceScan::ExclusiveSum(nullptr, tmp, s->npairs.as<int64_t>(), s->pair_off.as<int64_t>(),
+    // invocations grouped by operation, so that the tiles running at one time
+    // read the same configuration rows
+    int bits = 1;
+    while ((1ll << bits) <= (int64_t)v.n_ops) ++bits;
+    size_t t_sort = 0, t_scan = 0;
+    SG_CUDA(s, cub::DeviceRadixSort::SortPairs(nullptr, t_sort, s->key.as<int32_t>(), s->key_sorted.as<int32_t>(),
+                                               s->idx.as<int32_t>(), s->idx_sorted.as<int32_t>(), (int)n_inv, 0,
+                                               bits, st));
+    SG_CUDA(s, cub::DeviceScan::ExclusiveSum(nullptr, t_scan, s->nrows.as<int64_t>(), s->row_off.as<int64_t>(),
                                              (int)(n_inv + 1), st));
-    SG_CUDA(s, s->scan_tmp.ensure(tmp));
-    SG_CUDA(s, cub::DeviceScan::ExclusiveSum(s->scan_tmp.p, tmp, s->npairs.as<int64_t>(), s->pair_off.as<int64_t>(),
+    SG_CUDA(s, s->scan_tmp.ensure(std::max(t_sort, t_scan)));
+    SG_CUDA(s, cub::DeviceRadixSort::SortPairs(s->scan_tmp.p, t_sort, s->key.as<int32_t>(),
+                                               s->key_sorted.as<int32_t>(), s->idx.as<int32_t>(),
+                                               s->idx_sorted.as<int32_t>(), (int)n_inv, 0, bits, st));
+    k_pair_rows<<<(unsigned)((n_inv + 256) / 256), 256, 0, st>>>(v.P, n_inv, s->key_sorted.as<int32_t>(),
+                                                                 s->nrows.as<int64_t>());
+    SG_CUDA(s, cudaGetLastError());
+    SG_CUDA(s, cub::DeviceScan::ExclusiveSum(s->scan_tmp.p, t_scan, s->nrows.as<int64_t>(), s->row_off.as<int64_t>(),
                                              (int)(n_inv + 1), st));
-    int64_t total = 0;
-    SG_CUDA(s, cudaMemcpyAsync(&total, s->pair_off.as<int64_t>() + n_inv, 8, cudaMemcpyDeviceToHost, st));
+    int64_t pairs = 0, rows = 0;
+    SG_CUDA(s, cudaMemcpyAsync(&pairs, s->total.p, 8, cudaMemcpyDeviceToHost, st));
+    SG_CUDA(s, cudaMemcpyAsync(&rows, s->row_off.as<int64_t>() + n_inv, 8, cudaMemcpyDeviceToHost, st));
     SG_CUDA(s, cudaStreamSynchronize(st));
-    if (total > s->max_pairs) return sg_fail(s, LLAMA_EINVAL, "schedule: more (invocation, configuration) pairs than max_pairs");
-    s->last_pairs = total;
-    const int64_t cap = std::max<int64_t>(total, 1);
-    SG_CUDA(s, s->h1.ensure(2 * (size_t)cap * kHid));
-    SG_CUDA(s, s->h2.ensure(2 * (size_t)cap * kHid));
-    SG_CUDA(s, s->pair_sel.ensure(16 * (size_t)cap));
-    SG_CUDA(s, s->pair_cost.ensure(8 * (size_t)cap));
-    SG_CUDA(s, s->lhat.ensure(4 * (size_t)cap));
-    SG_CUDA(s, s->chat.ensure(8 * (size_t)cap));
-    // first layer, split: A = configurations . W1^T, B = contents . W1^T + b1
-    SG_RC(s, gemm(cfg_x, nv.w16[0], nullptr, nullptr, s->A.as<float>(), n_cfg, kHid, kIn, 0, st), "layer 1 (configurations)");
+    if (pairs > s->max_pairs) return sg_fail(s, LLAMA_EINVAL, "schedule: more (invocation, configuration) pairs than max_pairs");
+    s->last_pairs = pairs;
+    s->last_n_inv = n_inv;
+    const size_t cap = (size_t)std::max<int64_t>(rows, kTileRows);
+    SG_CUDA(s, s->h2.ensure(2 * cap * kHid));
+    SG_CUDA(s, s->pair_sel.ensure(16 * cap));
+    SG_CUDA(s, s->pair_cost.ensure(8 * cap));
+    SG_CUDA(s, s->lhat.ensure(4 * cap));
+    SG_CUDA(s, s->chat.ensure(8 * cap));
+    SG_CUDA(s, s->tile_info.ensure(8 * (cap / kTileRows)));
+    // first layer, split: A = configurations . W1^T (BF16), B = contents . W1^T + b1
+    SG_RC(s, gemm(cfg_x, nv.w16[0], nullptr, s->A.p, nullptr, n_cfg, kHid, kIn, 0, st), "layer 1 (configurations)");
     SG_RC(s, gemm(inv_x, nv.w16[0], nv.params + kOffB1, nullptr, s->B.as<float>(), n_inv, kHid, kIn, 0, st),
           "layer 1 (contents)");
     SG_CUDA(s, cudaMemsetAsync(s->best.p, 0xFF, 8 * (size_t)n_inv, st));
-    if (total > 0) {
-        k_pair_h1<<<(unsigned)n_inv, 256, 0, st>>>(v.P, dag, op_local, s->slack.as<int32_t>(), s->pair_off.as<int64_t>(),
-                                                   s->A.as<float>(), s->B.as<float>(), s->lam.as<int8_t>(),
-                                                   s->h1.as<bf16>(), s->pair_sel.as<int4>(),
-                                                   s->pair_cost.as<int64_t>());
-        SG_CUDA(s, cudaGetLastError());
-        SG_RC(s, mlp_layer(s->h1.p, nv.w16[1], nv.params + kOffB2, s->h2.p, total, st), "layer 2");
+    k_pair_index<<<(unsigned)n_inv, 256, 0, st>>>(v.P, s->key_sorted.as<int32_t>(), s->idx_sorted.as<int32_t>(),
+                                                  s->row_off.as<int64_t>(), s->slack.as<int32_t>(),
+                                                  s->lam.as<int8_t>(), s->inv_row.as<int64_t>(),
+                                                  s->pair_sel.as<int4>(), s->pair_cost.as<int64_t>(),
+                                                  s->tile_info.as<int2>());
+    SG_CUDA(s, cudaGetLastError());
+    if (rows > 0) {
+        SG_RC(s, mlp_layer_first(s->A.p, n_cfg, s->B.as<float>(), s->tile_info.as<int2>(), nv.w16[1],
+                                 nv.params + kOffB2, s->h2.p, rows, st),
+              "layers 1 and 2");
         SelectArgs a;
         a.w4 = nv.params + kOffW4;
         a.b4 = nv.params + kOffB4;
@@ -263,10 +322,10 @@ extern "C" int llama_sg_schedule(llama_sg *s, const void *cfg_x, const void *inv
         a.best = s->best.as<unsigned long long>();
         a.lhat = s->lhat.as<int32_t>();
         a.chat = s->chat.as<int64_t>();
-        SG_RC(s, mlp_layer_select(s->h2.p, nv.w16[2], nv.params + kOffB3, total, a, st), "layer 3 and selection");
+        SG_RC(s, mlp_layer_select(s->h2.p, nv.w16[2], nv.params + kOffB3, rows, a, st), "layer 3 and selection");
     }
     k_sg_decode<<<(unsigned)((n_inv + 255) / 256), 256, 0, st>>>(
-        v.P, n_inv, dag, op_local, s->slack.as<int32_t>(), s->pair_off.as<int64_t>(),
+        v.P, n_inv, dag, op_local, s->slack.as<int32_t>(), s->inv_row.as<int64_t>(),
         s->best.as<unsigned long long>(), s->lhat.as<int32_t>(), s->chat.as<int64_t>(), s->lam.as<int8_t>(), out);
     SG_CUDA(s, cudaGetLastError());
     if (prev >= 0 && prev != v.device) cudaSetDevice(prev);
@@ -285,12 +344,27 @@ extern "C" int llama_sg_set_margin(llama_sg *s, float margin) {
 extern "C" int llama_sg_predictions(llama_sg *s, int32_t *lhat, int64_t *chat, int64_t *pair_off, int64_t n_inv,
                                     void *stream) {
     if (!s) return LLAMA_EINVAL;
-    if (n_inv < 0 || n_inv > s->max_inv) return sg_fail(s, LLAMA_EINVAL, "predictions: n_inv outside 0..max_inv");
+    if (n_inv != s->last_n_inv) return sg_fail(s, LLAMA_EINVAL, "predictions: n_inv is not the last call's");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int64_t n = s->last_pairs;
-    if (lhat && n) SG_CUDA(s, cudaMemcpyAsync(lhat, s->lhat.p, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
-    if (chat && n) SG_CUDA(s, cudaMemcpyAsync(chat, s->chat.p, 8 * (size_t)n, cudaMemcpyDeviceToDevice, st));
-    if (pair_off) SG_CUDA(s, cudaMemcpyAsync(pair_off, s->pair_off.p, 8 * (size_t)(n_inv + 1), cudaMemcpyDeviceToDevice, st));
+    if (n_inv == 0) {
+        if (pair_off) SG_CUDA(s, cudaMemsetAsync(pair_off, 0, 8, st));
+        return LLAMA_OK;
+    }
+    // pair offsets in invocation order, then the rows gathered into them
+    SG_CUDA(s, s->pair_off.ensure(8 * (size_t)(s->max_inv + 1)));
+    size_t tmp = 0;
+    SG_CUDA(s, cub::DeviceScan::ExclusiveSum(nullptr, tmp, s->npairs.as<int64_t>(), s->pair_off.as<int64_t>(),
+                                             (int)(n_inv + 1), st));
+    SG_CUDA(s, s->scan_tmp.ensure(tmp));
+    SG_CUDA(s, cub::DeviceScan::ExclusiveSum(s->scan_tmp.p, tmp, s->npairs.as<int64_t>(), s->pair_off.as<int64_t>(),
+                                             (int)(n_inv + 1), st));
+    if ((lhat || chat) && s->last_pairs > 0) {
+        k_pair_compact<<<(unsigned)n_inv, 256, 0, st>>>(n_inv, s->pair_off.as<int64_t>(), s->inv_row.as<int64_t>(),
+                                                        s->lhat.as<int32_t>(), s->chat.as<int64_t>(), lhat, chat);
+        SG_CUDA(s, cudaGetLastError());
+    }
+    if (pair_off)
+        SG_CUDA(s, cudaMemcpyAsync(pair_off, s->pair_off.p, 8 * (size_t)(n_inv + 1), cudaMemcpyDeviceToDevice, st));
     return LLAMA_OK;
 }
 
