@@ -87,6 +87,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default scoring schedule")
     ap.add_argument("--n-dags", type=int, default=None, help="DAG count of the batched workloads")
     ap.add_argument("--n-inv", type=int, default=None, help="invocations per step (default: the workload's)")
+    ap.add_argument("--train-epochs", type=int, default=11,
+                    help="surrogate: training epochs before the timed calls (0: untrained network, for profiling)")
     ap.add_argument("--tuning", default=None,
                     help="fixed scoring schedule 'lanes_min_vectors,inv_per_thread,chunk,stages' (no autotuning)")
     return ap.parse_args()
@@ -279,13 +281,15 @@ def run_surrogate(args):
     with L.Scheduler(p) as s, L.MLP(max_batch=8192) as net:
         net.set_params(M.pack(M.init_params(3)).astype(np.float32))
         xd, td = S.training_inputs(x, t)
-        S.train(net, xd, td, epochs=1, lr=2e-3, w_fan=0.1)  # warm-up epoch
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        hist = S.train_schedule(net, xd, td, epochs=11)
-        torch.cuda.synchronize()
-        train_s = time.perf_counter() - t0
-        samples = 11 * (x.shape[0] // 8192) * 8192
+        hist, train_s, samples = [], float("nan"), 0
+        if args.train_epochs > 0:
+            S.train(net, xd, td, epochs=1, lr=2e-3, w_fan=0.1)  # warm-up epoch
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            hist = S.train_schedule(net, xd, td, epochs=args.train_epochs)
+            torch.cuda.synchronize()
+            train_s = time.perf_counter() - t0
+            samples = args.train_epochs * (x.shape[0] // 8192) * 8192
         margin = S.margin_from_rmse(S.held_out_rmse(net, *S.training_inputs(xv, tv)), W.LATENCY_NOISE_SIGMA)
         cfg_x = S.config_inputs(p, cw)
         inv_x = S.content_inputs(content)
@@ -316,7 +320,7 @@ def run_surrogate(args):
     value = sub.n / (step_ms / 1e3)
     achieved = SURROGATE_FLOPS_PER_PAIR * n_pairs / (step_ms / 1e3) / 1e12
     peak = float(peaks.get("bf16_tflops_sustained", 1400.0))
-    train_tflops = SURROGATE_FLOPS_PER_SAMPLE * samples / train_s / 1e12
+    train_tflops = SURROGATE_FLOPS_PER_SAMPLE * samples / train_s / 1e12 if samples else None
     # decision quality on this batch, judged with the ground-truth content model
     slack = oracle.slacks(p, sub)
     valid = slack[:, 0] >= 0
@@ -351,8 +355,8 @@ def run_surrogate(args):
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                      "peak_source": f"{peak_src} sustained cuBLAS bf16", "flops_per_pair": SURROGATE_FLOPS_PER_PAIR,
                      "note": "whole scheduling call (slack, pair set-up, both GEMMs, decode) in the denominator"},
-        "training": {"samples_per_s": samples / train_s, "tflops": train_tflops, "seconds": train_s,
-                     "loss_by_epoch": hist},
+        "training": {"samples_per_s": samples / train_s if samples else None, "tflops": train_tflops,
+                     "seconds": train_s if samples else None, "epochs": args.train_epochs, "loss_by_epoch": hist},
         "decision_quality": quality,
         "clocks": clocks.summary(),
         # own kernels per call: critical paths, slack, configuration backends, pair keys, rows per

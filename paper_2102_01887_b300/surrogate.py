@@ -73,8 +73,8 @@ def held_out_rmse(net, x, t, batch: int = 8192) -> float:
 def margin_from_rmse(rmse: float, noise_sigma: float) -> float:
     """The model's own error from the held-out error and the profiler's known
     measurement noise (independent errors add in variance), used as the
-    selection margin."""
-    return float(np.sqrt(max(rmse * rmse - noise_sigma * noise_sigma, 0.0)))
+    selection margin (at most 1, the largest margin the scheduler takes)."""
+    return float(min(np.sqrt(max(rmse * rmse - noise_sigma * noise_sigma, 0.0)), 1.0))
 
 
 def train_schedule(net, x, t, epochs: int = 12, lr: float = 2e-3, halve_every: int = 3, w_fan: float = 0.1,
