@@ -561,6 +561,8 @@ def main():
         e2e = {"value": job_throughput(world, inv.n, args.steps, e2e_s), "unit": UNIT,
                "h2d_bytes_per_step": int(inv.n * (4 + 4 + 8)),
                "d2h_bytes_per_step": int(inv.n * 24 + 8),
+               "transfer": "inputs read in place from page-locked host memory by the kernels; "
+                           "decisions copied back from device memory",
                "p50_call_us": 1e6 * float(np.median(wall)), "p99_call_us": 1e6 * float(np.percentile(wall, 99))}
 
     if rank != 0:

@@ -178,8 +178,10 @@ int llama_queue_time(llama_ctx *ctx, int64_t n, const int32_t *dag, const int32_
  *   dag[n_inv], op_local[n_inv]  the invocation's DAG and op-local operation;
  *   start_us[n_inv]              start time of its pipeline instance, 0..now_us;
  *   out[n_inv]                   decisions, written in invocation order.
- * Each pointer may be host or device memory (detected per pointer).  An
- * invalid invocation (bad DAG or op index, start outside 0..now) gets
+ * Each pointer may be host or device memory (detected per pointer); inputs
+ * in page-locked host memory are read in place by the kernels, pageable ones
+ * are copied to the device first.  The arrays must not change during the
+ * call.  An invalid invocation (bad DAG or op index, start outside 0..now) gets
  * cfg = -1 and LLAMA_FLAG_INVALID, every valid one is still decided, and the
  * call returns EINVAL.  n_inv = 0 is a no-op.  Errors: EINVAL, ENOTREADY,
  * ENOMEM, ECUDA. */

@@ -425,6 +425,21 @@ bool is_device_ptr(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// The address at which the current device's kernels can read p in place:
+// device or managed memory, or page-locked host memory mapped into the device's
+// address space (the kernels then read it over the host link, overlapped with
+// their work); nullptr for pageable host memory, which must be copied.
+const void *kernel_readable(const void *p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return p;
+    if (a.type == cudaMemoryTypeHost) return a.devicePointer;
+    return nullptr;
+}
+
 int grid_for(const llama_ctx *c, int64_t n, int threads) {
     const int64_t want = (n + threads - 1) / threads;
     return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)c->num_sms * 16));
@@ -1195,17 +1210,22 @@ extern "C" int llama_schedule(llama_ctx *c, int64_t n_inv, const int32_t *dag, c
     if (n_inv == 0) return LLAMA_OK;
     DeviceGuard g(c->opts.device);
     if ((rc = ensure_scratch(c, n_inv))) return rc;
-    const bool dd = is_device_ptr(dag), od = is_device_ptr(op_local), sd = is_device_ptr(start_us),
-               outd = is_device_ptr(out);
-    if (!(dd && od && sd && outd) && (rc = ensure_stage(c, n_inv))) return rc;
+    // inputs in device memory or page-locked host memory are read in place
+    // (reading over the host link from the kernels measured faster than a copy
+    // engine transfer followed by the kernels); pageable ones are copied; the
+    // decisions are written to device memory and copied back (scattered writes
+    // of 24-byte records over the host link are slow)
+    const void *rd = kernel_readable(dag), *ro = kernel_readable(op_local), *rs = kernel_readable(start_us);
+    const bool outd = is_device_ptr(out);
+    if (!(rd && ro && rs && outd) && (rc = ensure_stage(c, n_inv))) return rc;
     cudaStream_t s = c->stream;
-    const int32_t *d_dag = dd ? dag : c->s_dag.as<int32_t>();
-    const int32_t *d_opl = od ? op_local : c->s_opl.as<int32_t>();
-    const int64_t *d_start = sd ? start_us : c->s_start.as<int64_t>();
+    const int32_t *d_dag = rd ? static_cast<const int32_t *>(rd) : c->s_dag.as<int32_t>();
+    const int32_t *d_opl = ro ? static_cast<const int32_t *>(ro) : c->s_opl.as<int32_t>();
+    const int64_t *d_start = rs ? static_cast<const int64_t *>(rs) : c->s_start.as<int64_t>();
     llama_decision *d_out = outd ? out : c->s_out.as<llama_decision>();
-    if (!dd) LL_CUDA(c, cudaMemcpyAsync((void *)d_dag, dag, 4 * n_inv, cudaMemcpyHostToDevice, s));
-    if (!od) LL_CUDA(c, cudaMemcpyAsync((void *)d_opl, op_local, 4 * n_inv, cudaMemcpyHostToDevice, s));
-    if (!sd) LL_CUDA(c, cudaMemcpyAsync((void *)d_start, start_us, 8 * n_inv, cudaMemcpyHostToDevice, s));
+    if (!rd) LL_CUDA(c, cudaMemcpyAsync((void *)d_dag, dag, 4 * n_inv, cudaMemcpyHostToDevice, s));
+    if (!ro) LL_CUDA(c, cudaMemcpyAsync((void *)d_opl, op_local, 4 * n_inv, cudaMemcpyHostToDevice, s));
+    if (!rs) LL_CUDA(c, cudaMemcpyAsync((void *)d_start, start_us, 8 * n_inv, cudaMemcpyHostToDevice, s));
     if ((rc = launch_schedule(c, n_inv, d_dag, d_opl, d_start, now_us, d_out, s))) return rc;
     if (!outd) LL_CUDA(c, cudaMemcpyAsync(out, d_out, sizeof(llama_decision) * n_inv, cudaMemcpyDeviceToHost, s));
     LL_CUDA(c, cudaMemcpyAsync(c->h_ctrl, c->ws.ctrl.as<unsigned long long>() + kCtrlWords,

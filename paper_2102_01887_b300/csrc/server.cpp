@@ -32,6 +32,11 @@ struct Slot {
     int32_t *h_dag = nullptr, *h_opl = nullptr, *d_dag = nullptr, *d_opl = nullptr;
     int64_t *h_start = nullptr, *d_start = nullptr;
     llama_decision *h_out = nullptr, *d_out = nullptr;
+    // device addresses of the page-locked request arrays: the kernels read a
+    // batch's requests in place (no copy launches); null if the host memory
+    // is not mapped into the device's address space, then they are copied
+    const int32_t *m_dag = nullptr, *m_opl = nullptr;
+    const int64_t *m_start = nullptr;
     std::vector<int64_t> ids, t_submit;
     int64_t n = 0;
     bool busy = false;
@@ -94,6 +99,16 @@ int init_slot(llama_server *srv, Slot &s, int64_t B) {
         cudaMalloc(&s.d_start, 8 * B) != cudaSuccess ||
         cudaMalloc(&s.d_out, sizeof(llama_decision) * B) != cudaSuccess)
         return LLAMA_ENOMEM;
+    void *md = nullptr, *mo = nullptr, *ms = nullptr;
+    if (cudaHostGetDevicePointer(&md, s.h_dag, 0) == cudaSuccess &&
+        cudaHostGetDevicePointer(&mo, s.h_opl, 0) == cudaSuccess &&
+        cudaHostGetDevicePointer(&ms, s.h_start, 0) == cudaSuccess) {
+        s.m_dag = static_cast<const int32_t *>(md);
+        s.m_opl = static_cast<const int32_t *>(mo);
+        s.m_start = static_cast<const int64_t *>(ms);
+    } else {
+        cudaGetLastError();
+    }
     const int rc = llama_ws_create(srv->ctx, B, &s.ws);
     if (rc) return rc;
     s.ids.resize(B);
@@ -127,11 +142,14 @@ int launch(llama_server *srv, Slot &s) {
     if (n == 0) return LLAMA_OK;
     s.n = n;
     cudaEventRecord(s.begin, s.stream);
-    if (cudaMemcpyAsync(s.d_dag, s.h_dag, 4 * n, cudaMemcpyHostToDevice, s.stream) != cudaSuccess ||
-        cudaMemcpyAsync(s.d_opl, s.h_opl, 4 * n, cudaMemcpyHostToDevice, s.stream) != cudaSuccess ||
-        cudaMemcpyAsync(s.d_start, s.h_start, 8 * n, cudaMemcpyHostToDevice, s.stream) != cudaSuccess)
+    const bool mapped = s.m_dag && s.m_opl && s.m_start;
+    if (!mapped && (cudaMemcpyAsync(s.d_dag, s.h_dag, 4 * n, cudaMemcpyHostToDevice, s.stream) != cudaSuccess ||
+                    cudaMemcpyAsync(s.d_opl, s.h_opl, 4 * n, cudaMemcpyHostToDevice, s.stream) != cudaSuccess ||
+                    cudaMemcpyAsync(s.d_start, s.h_start, 8 * n, cudaMemcpyHostToDevice, s.stream) != cudaSuccess))
         return LLAMA_ECUDA;
-    const int rc = llama_schedule_ws_async(srv->ctx, s.ws, n, s.d_dag, s.d_opl, s.d_start, now_b, s.d_out, s.stream);
+    // (the slot's host arrays are not rewritten before its end event: the slot is busy until then)
+    const int rc = llama_schedule_ws_async(srv->ctx, s.ws, n, mapped ? s.m_dag : s.d_dag, mapped ? s.m_opl : s.d_opl,
+                                           mapped ? s.m_start : s.d_start, now_b, s.d_out, s.stream);
     if (rc) return rc;
     if (cudaMemcpyAsync(s.h_out, s.d_out, sizeof(llama_decision) * n, cudaMemcpyDeviceToHost, s.stream) !=
         cudaSuccess)

@@ -250,6 +250,34 @@ def test_device_pointers_and_async_stream(L, method):
         assert L.llama_last_launch_count(s.ctx) >= 1
 
 
+def test_pinned_host_inputs(L, method):
+    """Page-locked host inputs are read in place by the kernels; pageable ones
+    are copied first; the decisions are the same either way, with host or
+    device output, and with invalid invocations among them."""
+    import torch
+    p, inv = W.medium()
+    inv = inv.subset(np.arange(0, inv.n, 3))
+    inv.dag = inv.dag.copy()
+    inv.start_us = inv.start_us.copy()
+    inv.dag[5] = -1
+    inv.start_us[9] = inv.now_us + 1
+    exp, _ = oracle.schedule(p, inv)
+    h_dag = torch.from_numpy(inv.dag).pin_memory()
+    h_opl = torch.from_numpy(inv.op_local).pin_memory()
+    h_st = torch.from_numpy(inv.start_us).pin_memory()
+    with L.Scheduler(p, method=method) as s:
+        for out in (np.zeros(inv.n, dtype=L.DECISION_DTYPE),
+                    torch.zeros(inv.n * 24, dtype=torch.uint8).pin_memory(),
+                    torch.zeros(inv.n * 24, dtype=torch.uint8, device="cuda:0")):
+            got, rc = L.llama_schedule(s.ctx, h_dag, h_opl, h_st, inv.now_us, out)
+            assert rc == L.EINVAL  # the two invalid invocations
+            got = got if isinstance(got, np.ndarray) else got.cpu().numpy().view(L.DECISION_DTYPE)
+            assert_same(got, exp, "pinned inputs")
+        # one pinned, two pageable
+        got, _ = L.llama_schedule(s.ctx, h_dag, inv.op_local, inv.start_us, inv.now_us)
+        assert_same(got, exp, "mixed inputs")
+
+
 def test_growing_and_shrinking_batches(L, method):
     p, inv = W.medium()
     exp, _ = oracle.schedule(p, inv)
