@@ -945,7 +945,10 @@ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(
 // One staging buffer.  Persistent CTAs take tiles from the tile list: first
 // tile blockIdx.x, the next ones from an atomic counter, so CTAs that finish
 // early take more (the list is ordered longest first).  While the first chunk
-// lands, the distinct latencies are searched.
+// lands, the distinct latencies are searched.  The next tile is claimed as a
+// tile starts and its descriptor read while the tile's copy lands, so its
+// first chunk is copied as soon as the scan is done with the buffer, while
+// this tile's decisions are decoded.
 template <int MODE, int IPT>
 __device__ __forceinline__ void score_body(const DevProblem &P, const BucketScratch &S,
                                            llama_decision *out, int32_t chunk, int32_t dl_cap) {
@@ -976,9 +979,16 @@ __device__ __forceinline__ void score_body(const DevProblem &P, const BucketScra
     asm volatile("griddepcontrol.wait;" ::: "memory");
     clear_counters(P, S);
     if (tid < H) tc.q[tid] = P.q[tid];
-    __syncthreads();
     const long long n_tiles = (long long)S.ctrl[kCtrlTiles];
     long long ti = blockIdx.x;
+    // the first chunk of a tile, from the tile's descriptor tx = {npad, dn, p0}
+    // (every op has at least one configuration: npad > 0)
+    const auto first_chunk = [&](const int4 &tx) {
+        stage_chunk<MODE>(P, (int64_t)tx.z, 0, min(chunk, tx.x), tx.y <= dl_cap, tx.y, lr_s, rf_s, df_s, dl_s, bar);
+    };
+    if (ti < n_tiles && tid == 0) first_chunk(S.tiles[2 * ti + 1]);
+    bool pending = ti < n_tiles;  // a copy into the buffer is in flight
+    __syncthreads();
     TileState<IPT> T;
     while (ti < n_tiles) {
         unsigned long long claim = 0;
@@ -986,11 +996,14 @@ __device__ __forceinline__ void score_body(const DevProblem &P, const BucketScra
         tile_begin(P, S, ti, tc, T);
         const bool dl_staged = T.dn <= dl_cap;
         uint16_t *cg = c_s + T.g * IPT * H;
+        int4 txn = make_int4(0, 0, 0, 0);
         for (int32_t c0 = 0; c0 < T.npad; c0 += chunk) {
             const int32_t cn = min(chunk, T.npad - c0);
-            __syncthreads();  // every thread is done with the previous chunk or tile
-            if (tid == 0)
-                stage_chunk<MODE>(P, T.p0, c0, cn, c0 == 0 && dl_staged, T.dn, lr_s, rf_s, df_s, dl_s, bar);
+            if (c0 > 0) {
+                __syncthreads();  // every thread is done with the previous chunk
+                if (tid == 0) stage_chunk<MODE>(P, T.p0, c0, cn, false, T.dn, lr_s, rf_s, df_s, dl_s, bar);
+                pending = true;
+            }
             if (c0 == 0 && !dl_staged) counts_from_global(P, S, T, tc, H, P.dlat + T.p0, cg);
             // every thread must agree before any leaves the barrier sequence
             if (!__syncthreads_and(mbar_wait(bar, phase))) {
@@ -998,22 +1011,34 @@ __device__ __forceinline__ void score_body(const DevProblem &P, const BucketScra
                 break;
             }
             phase ^= 1u;
-            if (c0 == 0 && dl_staged) {
-                counts_from_shared(S, T, tc, H, dl_s, cg);
-                __syncthreads();
+            pending = false;
+            if (c0 == 0) {
+                if (tid == 0) {
+                    const long long tn = (long long)(claim + gridDim.x);
+                    next_tile = tn;
+                    if (tn < n_tiles) txn = S.tiles[2 * tn + 1];
+                }
+                if (dl_staged) {
+                    counts_from_shared(S, T, tc, H, dl_s, cg);
+                    __syncthreads();
+                }
             }
             scan_chunk<MODE, IPT>(P, T, c0, cn, lr_s, rf_s, df_s, cg);
         }
         if (!ok) break;
+        __syncthreads();  // the scan is done with the buffer; next_tile is published
+        const long long tn = next_tile;
+        if (tn < n_tiles) {
+            if (tid == 0) first_chunk(txn);
+            pending = true;
+        }
         finish_tile<MODE, IPT>(P, S, out, T, tc, red);
-        if (tid == 0) next_tile = (long long)(claim + gridDim.x);
-        __syncthreads();
-        ti = next_tile;
+        ti = tn;
     }
-    if (!ok) {
+    if (!ok || pending) {
         // a staging copy never completed: report it, wait (bounded) for the copy
         // to land so no transfer targets this CTA's shared memory after exit
-        if (tid == 0) atomicOr(&S.ctrl[kCtrlTimeout], 1ull);
+        if (!ok && tid == 0) atomicOr(&S.ctrl[kCtrlTimeout], 1ull);
         mbar_wait(bar, phase);
     }
     finish_call(S);
