@@ -63,38 +63,39 @@ def perturbed_params(seed):
     return q
 
 
-def test_predictions_and_decisions_match_oracle(L, world):
+def check_predictions(L, p, sub, cw, seed):
+    """Predictions and decisions of the GPU against the oracle on the invocations
+    sub (two of them made invalid) with random content and perturbed weights."""
     import torch
 
     from paper_2102_01887_b300 import surrogate as S
-    p, inv, cw = world
-    sub = inv.subset(np.arange(0, inv.n, 640))
-    # two invalid invocations among them
     sub.dag = sub.dag.copy()
     sub.start_us = sub.start_us.copy()
     sub.dag[3] = -1
     sub.start_us[7] = sub.now_us + 5
-    content = W.invocation_content(5, sub.n)
-    params = perturbed_params(21)
+    content = W.invocation_content(seed, sub.n)
+    params = perturbed_params(seed + 16)
     flat = M.pack(params).astype(np.float32)
+    slack = oracle.slacks(p, sub)
+    valid = slack[:, 0] >= 0
+    pinv, pg, px, off, gop = pairs_of(p, sub, valid)
     with L.Scheduler(p) as s, L.MLP(max_batch=1024) as net:
         net.set_params(flat)
         cfg_x = S.config_inputs(p, cw)
         with S.SurrogateScheduler(s, net, max_inv=4096, max_pairs=1 << 20) as sg:
             got = sg.schedule(cfg_x, sub, content)
             lh, ch, po = sg.predictions(sub.n)
-        cfg_np = cfg_x.float().cpu().numpy()
+        # the features of the configurations that occur, rows renumbered
+        used, pg_used = np.unique(pg, return_inverse=True)
+        cfg_np = cfg_x[torch.from_numpy(used).to(cfg_x.device)].float().cpu().numpy()
         inv_np = S.content_inputs(content).float().cpu().numpy()
-    slack = oracle.slacks(p, sub)
-    valid = slack[:, 0] >= 0
     assert (got["flags"][~valid] == L.FLAG_INVALID).all() and (got["cfg"][~valid] == -1).all()
-    pinv, pg, px, off, gop = pairs_of(p, sub, valid)
     assert np.array_equal(po, off)
     # the network, in FP64 on the same BF16 inputs and weights (last layer in FP32)
     q = M.unpack(flat.astype(np.float64))
     for k in ("W1", "W2", "W3"):
         q[k] = torch.from_numpy(q[k].astype(np.float32)).to(torch.bfloat16).double().numpy()
-    r = OS.forward_log_factor(q, cfg_np, inv_np, pinv, pg)
+    r = OS.forward_log_factor(q, cfg_np, inv_np, pinv, pg_used)
     l_or = p.lat_us[pg] * np.exp(np.clip(r, -20, 20))
     err = np.abs(np.log(lh / l_or))
     assert err.max() <= 0.05, err.max()
@@ -108,6 +109,20 @@ def test_predictions_and_decisions_match_oracle(L, world):
     assert np.array_equal(got["cost"][valid], ch[k])
     assert np.array_equal(got["slack"][valid], spair[k])
     assert np.array_equal(got["flags"][valid], (lh[k] < spair[k]).astype(np.int32))
+
+
+def test_predictions_and_decisions_match_oracle(L, world):
+    p, inv, cw = world
+    check_predictions(L, p, inv.subset(np.arange(0, inv.n, 640)), cw, 5)
+
+
+def test_predictions_uneven_configuration_spaces(L):
+    """Zipf-sized configuration spaces (96 .. 8,192, most not a multiple of the
+    128-row tile): every invocation's last tile is partly padding."""
+    p, inv = W.batched(n_inv=4096)
+    sizes = np.diff(p.cfg_off)[p.dag_op_off[inv.dag] + inv.op_local]
+    assert (sizes % 128 != 0).mean() > 0.3
+    check_predictions(L, p, inv.subset(np.arange(0, inv.n, 29)), W.content_world(p), 7)
 
 
 def evaluate(p, cw, sub, content, decisions_cfg, slack, lam, noise_seed):
