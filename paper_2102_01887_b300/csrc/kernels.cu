@@ -942,6 +942,12 @@ __device__ __forceinline__ void stage_chunk(const DevProblem &P, int64_t p0, int
 
 __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
+// Bring [src, src + bytes) into L2 (16-byte aligned, bytes a multiple of 16).
+__device__ __forceinline__ void prefetch_l2(const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<uint64_t>(src)), "r"(bytes)
+                 : "memory");
+}
+
 // One staging buffer.  Persistent CTAs take tiles from the tile list: first
 // tile blockIdx.x, the next ones from an atomic counter, so CTAs that finish
 // early take more (the list is ordered longest first).  While the first chunk
@@ -1016,7 +1022,14 @@ __device__ __forceinline__ void score_body(const DevProblem &P, const BucketScra
                 if (tid == 0) {
                     const long long tn = (long long)(claim + gridDim.x);
                     next_tile = tn;
-                    if (tn < n_tiles) txn = S.tiles[2 * tn + 1];
+                    if (tn < n_tiles) {
+                        // the next tile's first chunk goes to L2 while this one is scored
+                        txn = S.tiles[2 * tn + 1];
+                        const uint32_t pb = 2u * (uint32_t)min(chunk, txn.x);
+                        prefetch_l2(P.lrb + txn.z, pb);
+                        prefetch_l2(P.rf + txn.z, pb);
+                        if (MODE == LLAMA_MODE_ALPHA) prefetch_l2(P.df + txn.z, pb);
+                    }
                 }
                 if (dl_staged) {
                     counts_from_shared(S, T, tc, H, dl_s, cg);
