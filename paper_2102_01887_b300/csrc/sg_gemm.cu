@@ -286,17 +286,17 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity) {
     return __all_sync(0xffffffffu, mbar_wait(bar, parity));
 }
 
-// One 16-byte unit (eight BF16 columns) of a swizzled slice: ReLU(a + b), b
-// the invocation part of those columns.
-__device__ __forceinline__ uint4 relu_add_unit(uint4 a, const float *b) {
-    uint32_t v[4] = {a.x, a.y, a.z, a.w};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const float lo = __uint_as_float(v[q] << 16) + b[2 * q], hi = __uint_as_float(v[q] & 0xFFFF0000u) + b[2 * q + 1];
-        const __nv_bfloat162 r = __floats2bfloat162_rn(fmaxf(lo, 0.f), fmaxf(hi, 0.f));
-        v[q] = *reinterpret_cast<const uint32_t *>(&r);
-    }
-    return make_uint4(v[0], v[1], v[2], v[3]);
+// One 16-byte unit (eight BF16 columns) of a swizzled slice: ReLU(a + b) with
+// b the invocation part of those columns, in BF16 pairs: a * 1 + b rounded once
+// to BF16, negative results clamped to 0 (one instruction per two columns).
+__device__ __forceinline__ uint4 relu_add_unit(uint4 a, uint4 b) {
+    constexpr uint32_t one = 0x3F803F80u;  // (1, 1) in BF16
+    uint4 r;
+    asm("fma.rn.relu.bf16x2 %0, %1, %2, %3;" : "=r"(r.x) : "r"(a.x), "r"(one), "r"(b.x));
+    asm("fma.rn.relu.bf16x2 %0, %1, %2, %3;" : "=r"(r.y) : "r"(a.y), "r"(one), "r"(b.y));
+    asm("fma.rn.relu.bf16x2 %0, %1, %2, %3;" : "=r"(r.z) : "r"(a.z), "r"(one), "r"(b.z));
+    asm("fma.rn.relu.bf16x2 %0, %1, %2, %3;" : "=r"(r.w) : "r"(a.w), "r"(one), "r"(b.w));
+    return r;
 }
 
 template <int MODE>
@@ -316,9 +316,10 @@ __global__ void __launch_bounds__(layer_threads(MODE), 1)
     __shared__ float half_dot[SELECT ? kBM : 1];  // second halves of the rows' last-layer dot products
     __shared__ __align__(16) float s_bias[kHid];
     __shared__ __align__(16) float s_w4[SELECT ? kHid : 4];
-    // invocation part of this and the last tile, float4 (k, half, unit) at
-    // 16k + 8half + unit: unit u of K-slice k covers columns 64k + 8u .. 64k + 8u + 7
-    __shared__ __align__(16) float4 s_binv[FIRST ? 2 : 1][kHid / 4];
+    // invocation part of this and the last tile in BF16, columns in order (the
+    // eight columns of unit u of K-slice k, 64k + 8u .. 64k + 8u + 7, are the
+    // 16-byte word 8k + u)
+    __shared__ __align__(16) uint2 s_binv[FIRST ? 2 : 1][kHid / 4];
     const uint32_t wbase = (smem_u32(smem_raw) + 1023u) & ~1023u, abase = wbase + kLWBytes;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_tiles = (M + kBM - 1) / kBM;
@@ -434,16 +435,19 @@ __global__ void __launch_bounds__(layer_threads(MODE), 1)
         const int uu = lane & 7, rr = lane >> 3;
         const int p0 = uu ^ rr, p1 = uu ^ (rr + 4);  // positions in even and odd passes
         uint8_t *const ring = smem_raw + (abase - smem_u32(smem_raw));  // generic address of the A ring
-        // float4 f of the invocation part (columns 4f .. 4f + 3) goes to 16k + 8half + unit
-        const int sbf = ct < kHid / 4 ? (ct / 16) * 16 + (ct % 2) * 8 + (ct % 16) / 2 : 0;
+
         float4 bnext = make_float4(0.f, 0.f, 0.f, 0.f);
         if (my_tiles > 0 && ct < kHid / 4) bnext = __ldg(&b_inv[(int64_t)__ldg(&tile_info[blockIdx.x].y) * (kHid / 4) + ct]);
         int g = 0;
         bool ok = true;
         for (int j = 0; j < my_tiles; ++j) {
             const int t = (int)blockIdx.x + j * (int)gridDim.x;
-            float4 *sb = s_binv[j & 1];
-            if (ct < kHid / 4) sb[sbf] = bnext;
+            uint2 *sb = s_binv[j & 1];
+            if (ct < kHid / 4) {
+                const __nv_bfloat162 lo = __floats2bfloat162_rn(bnext.x, bnext.y);
+                const __nv_bfloat162 hi = __floats2bfloat162_rn(bnext.z, bnext.w);
+                sb[ct] = make_uint2(*reinterpret_cast<const uint32_t *>(&lo), *reinterpret_cast<const uint32_t *>(&hi));
+            }
             if (j + 1 < my_tiles && ct < kHid / 4)
                 bnext = __ldg(&b_inv[(int64_t)__ldg(&tile_info[t + (int)gridDim.x].y) * (kHid / 4) + ct]);
             // every converter warp agrees to go on (and has finished the tile
@@ -459,9 +463,7 @@ __global__ void __launch_bounds__(layer_threads(MODE), 1)
                     ok = false;
                     break;
                 }
-                float bu[8];
-                *reinterpret_cast<float4 *>(bu) = sb[16 * k + uu];
-                *reinterpret_cast<float4 *>(bu + 4) = sb[16 * k + 8 + uu];
+                const uint4 bu = reinterpret_cast<const uint4 *>(sb)[8 * k + uu];
                 uint8_t *const rows = ring + st * kLABytes + (16 * cw + rr) * 128;
                 uint4 v[kConvPasses];
 #pragma unroll
