@@ -497,9 +497,9 @@ __device__ __forceinline__ void scatter_invocation(const BucketScratch &S, const
 //     first, then the tails: per-block sums, a barrier of the counting
 //     blocks, prefixes over the blocks and the writes;
 //  3. grid barrier;
-//  4. the counting blocks place their invocations in their buckets and
-//     compute their slack for every backend (Algorithm 1 through the critical
-//     path).
+//  4. the counting blocks place their invocations in their buckets, each with
+//     its remaining time (the scoring kernel turns it into the slack per
+//     backend, Algorithm 1 through the critical path).
 __global__ void __launch_bounds__(256) k_bucket(DevProblem P, int64_t n_inv, const int32_t *dag,
                                                 const int32_t *op_local, const int64_t *start,
                                                 int64_t now, BucketScratch S, llama_decision *out,

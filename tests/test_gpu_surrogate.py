@@ -145,6 +145,41 @@ def evaluate(p, cw, sub, content, decisions_cfg, slack, lam, noise_seed):
 
 
 @pytest.mark.slow
+def test_edge_cases(L, world):
+    """A single invocation; a call in which every invocation is invalid (no pair
+    rows: only the decode runs); more pairs than max_pairs; predictions asked
+    for another invocation count than the last call's."""
+    from paper_2102_01887_b300 import surrogate as S
+    p, inv, cw = world
+    params = perturbed_params(33)
+    flat = M.pack(params).astype(np.float32)
+    with L.Scheduler(p) as s, L.MLP(max_batch=1024) as net:
+        net.set_params(flat)
+        cfg_x = S.config_inputs(p, cw)
+        with S.SurrogateScheduler(s, net, max_inv=64, max_pairs=4096) as sg:
+            one = inv.subset(np.array([5]))
+            got = sg.schedule(cfg_x, one, W.invocation_content(3, 1))
+            lh, ch, po = sg.predictions(1)
+            n = int(np.diff(p.cfg_off)[p.dag_op_off[one.dag[0]] + one.op_local[0]])
+            assert po.tolist() == [0, n] and lh.shape == (n,)
+            x = OS.select(lh.astype(np.int64), ch,
+                          oracle.slacks(p, one)[0][backend_of_cfg(p)[p.cfg_off[p.dag_op_off[one.dag[0]] +
+                                                                           one.op_local[0]] + np.arange(n)]],
+                          po)
+            assert got["cfg"][0] == x[0]
+            with pytest.raises(L.LlamaError):
+                sg.predictions(2)
+            bad = inv.subset(np.arange(8))
+            bad.dag = np.full(8, -1, np.int32)
+            got = sg.schedule(cfg_x, bad, W.invocation_content(4, 8))
+            assert (got["flags"] == L.FLAG_INVALID).all() and (got["cfg"] == -1).all()
+            lh, ch, po = sg.predictions(8)
+            assert lh.shape == (0,) and (po == 0).all()
+            many = inv.subset(np.arange(16))  # 16 x 1,024 pairs > 4,096
+            with pytest.raises(L.LlamaError):
+                sg.schedule(cfg_x, many, W.invocation_content(5, 16))
+
+
 def test_trained_surrogate_against_the_table_path(L, world):
     # trained on 2M profiler samples, margin from the held-out error, judged on
     # 16,384 invocations with the ground-truth content model
