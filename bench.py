@@ -90,7 +90,8 @@ def parse():
     ap.add_argument("--train-epochs", type=int, default=11,
                     help="surrogate: training epochs before the timed calls (0: untrained network, for profiling)")
     ap.add_argument("--tuning", default=None,
-                    help="fixed scoring schedule 'lanes_min_vectors,inv_per_thread,chunk,stages' (no autotuning)")
+                    help="fixed scoring schedule 'lanes_min_vectors,inv_per_thread,chunk,stages[,count_pass]' "
+                         "(no autotuning; count_pass 0 auto, 1 on, 2 off)")
     return ap.parse_args()
 
 
@@ -482,9 +483,11 @@ def main():
 
     tuning = None
     if args.tuning:
-        lmv, ipt, chunk, stages = (int(x) for x in args.tuning.split(","))
+        lmv, ipt, chunk, stages, *cpass = (int(x) for x in args.tuning.split(","))
         L.llama_set_tuning(ctx, lmv, ipt, chunk, stages)
-        tuning = {"best": {"lanes_min_vectors": lmv, "inv_per_thread": ipt, "chunk": chunk, "stages": stages},
+        L.llama_set_count_pass(ctx, cpass[0] if cpass else L.COUNT_PASS_AUTO)
+        tuning = {"best": {"lanes_min_vectors": lmv, "inv_per_thread": ipt, "chunk": chunk, "stages": stages,
+                           "count_pass": cpass[0] if cpass else L.COUNT_PASS_AUTO},
                   "trials": []}
     elif not args.no_autotune and args.method == "scan":
         # choose the scoring schedule on this batch before anything is timed;
@@ -533,7 +536,10 @@ def main():
     total_s = max_over_ranks(float(step_ms.sum()) / 1e3, world, dev)
     if world > 1:
         dist.barrier()
-    launches = args.steps * L.llama_last_launch_count(ctx)  # pass A's kernels
+    per_call = L.llama_last_launch_count(ctx)
+    launches = args.steps * per_call  # pass A's kernels
+    # the scan's count pass (k_counts) runs between the two phases' kernels
+    count_pass = args.method == "scan" and per_call == 3
 
     # parity of the timed output against the oracle (untimed), rank 0
     got = out.cpu().numpy().view(L.DECISION_DTYPE)
@@ -614,7 +620,8 @@ def main():
             "frac": achieved / hbm, "traffic": measured_traffic("k_score", args.workload, args.mode),
             "peak_source": f"{peak_src} HBM copy bandwidth", "algorithmic_bytes": algo_bytes,
             "bytes_note": f"{tbl_per_entry} B per padded table entry of each op with invocations "
-                          "(latency rank + objective rank(s)), once, plus 40 B per invocation"}
+                          "(latency rank + objective rank(s)), once, plus 40 B per invocation",
+            "timed": "k_counts + k_score (trace events around both)" if count_pass else "k_score"}
     else:
         peak_tops = sm_count * ALU_LANES_PER_SM * sm_mhz * 1e6 / 1e12
         ops_per_score = ALU_OPS_PER_SCORE[args.mode]
@@ -668,10 +675,12 @@ def main():
         "kernel_ms": {n: float(phase_ms[:, j].mean()) for j, n in
                       enumerate(("critical_path", "stair") if args.method == "staircase" else L.TRACE_PHASES)},
         "kernel_ms_note": "per-kernel event times from a second pass of the same steps with trace "
-                          "events (direct launches, no overlap between the two kernels)",
+                          "events (direct launches, no overlap between the kernels)"
+                          + ("; 'score' is the count pass (k_counts) and the scoring kernel" if count_pass else ""),
         "roofline": roofline,
         "rooflines": rooflines,
-        "schedule_trials": ([{k: t[k] for k in ("lanes_min_vectors", "inv_per_thread", "chunk", "stages", "ms")}
+        "schedule_trials": ([{k: t[k] for k in ("lanes_min_vectors", "inv_per_thread", "chunk", "stages",
+                                                "count_pass", "ms") if k in t}
                              for t in tuning["trials"]] if tuning and tuning["trials"] else None),
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
         "parity_vs_oracle": parity,

@@ -266,6 +266,23 @@ int llama_schedule_static(llama_ctx *ctx, int64_t n_inv, const int32_t *dag,
 int llama_set_tuning(llama_ctx *ctx, int32_t lanes_min_vectors, int32_t inv_per_thread,
                      int32_t chunk_entries, int32_t stages);
 
+/* Count pass of the scan method (no counterpart in the paper; changes speed,
+ * never results).  Operations with more distinct latencies than the scoring
+ * kernel stages in shared memory need, per invocation and backend, the number
+ * of them below the slack (the feasibility threshold of Eq. 1 in latency-rank
+ * form).  ON: a separate kernel between bucketing and scoring computes these
+ * counts, one thread per invocation (a probe line, a second-level probe line
+ * and a short bisection per backend); OFF: the scoring kernel searches them
+ * itself, a warp-wide search per (invocation, backend), overlapped with the
+ * staging of the table.  AUTO (default): ON when at least half of the
+ * operations have padded tables larger than the staged distinct latencies.
+ * The pass is never launched when no operation needs it, nor by
+ * llama_schedule_static.  Errors: EINVAL. */
+#define LLAMA_COUNT_PASS_AUTO 0
+#define LLAMA_COUNT_PASS_ON 1
+#define LLAMA_COUNT_PASS_OFF 2
+int llama_set_count_pass(llama_ctx *ctx, int32_t mode);
+
 /* Method of the selection step (a4).  SCAN (default): every configuration of
  * the invocation's operation is scored (Eq. 1, Section 4.2), tables staged
  * through shared memory and shared by the op's invocations.  STAIRCASE: an
@@ -300,7 +317,7 @@ int llama_slack(llama_ctx *ctx, int64_t n_inv, const int32_t *dag, const int32_t
  * handles; once set, every scheduling call records them on its stream at
  * the phase boundaries: [0] call start, [1] after the bucketing kernel
  * (critical path, counting per operation, bucket layout, slack), [2] after
- * the scoring kernel.  Traced calls launch their kernels directly (no CUDA
+ * the scoring kernel (and the count pass before it, when it runs).  Traced calls launch their kernels directly (no CUDA
  * graph) and the scoring kernel no longer overlaps the end of the bucketing
  * kernel.  n_events = 0 turns tracing off.  The events must stay valid while
  * tracing is on.  Errors: EINVAL. */

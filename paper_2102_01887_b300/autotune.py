@@ -1,7 +1,8 @@
 """Autotuner of the scoring kernel's launch schedule.
 
 The schedule (lanes sharing one invocation, invocations per thread, staging
-chunk, staging buffers) changes speed, never results (tests check the latter).  For a given
+chunk, staging buffers, and whether a count pass precedes the scoring kernel)
+changes speed, never results (tests check the latter).  For a given
 context and a batch of device-resident invocations, the tuner times every
 candidate on that batch -- whole scheduling calls replayed as the caller
 would replay them, the L2 cache flushed before each call -- and keeps the
@@ -53,6 +54,7 @@ def autotune(ctx, dag, op_local, start, now: int, out, stream=None, flush=None,
     if flush is None:
         flush = torch.empty(256 << 20, dtype=torch.uint8, device=dag.device)
     trials = []
+    L.llama_set_count_pass(ctx, L.COUNT_PASS_AUTO)
     for st, chunk, lmv, ipt in itertools.product(stages, chunks, lanes, ipts):
         L.llama_set_tuning(ctx, lmv, ipt, chunk, st)
         ms = time_call(ctx, dag, op_local, start, now, out, stream, flush, reps)
@@ -60,4 +62,16 @@ def autotune(ctx, dag, op_local, start, now: int, out, stream=None, flush=None,
                        "ms": ms})
     best = min(trials, key=lambda t: t["ms"])
     L.llama_set_tuning(ctx, best["lanes_min_vectors"], best["inv_per_thread"], best["chunk"], best["stages"])
+    # the count pass, forced on and off, against the default for the best
+    # schedule -- where it can run at all (forced on, a call launches it)
+    best = dict(best, count_pass=L.COUNT_PASS_AUTO)
+    for mode in (L.COUNT_PASS_ON, L.COUNT_PASS_OFF):
+        L.llama_set_count_pass(ctx, mode)
+        ms = time_call(ctx, dag, op_local, start, now, out, stream, flush, reps)
+        if mode == L.COUNT_PASS_ON and L.llama_last_launch_count(ctx) < 3:
+            break  # no op needs the pass: nothing to choose
+        trials.append(dict(best, count_pass=mode, ms=ms))
+        if ms < best["ms"]:
+            best = trials[-1]
+    L.llama_set_count_pass(ctx, best["count_pass"])
     return {"best": best, "trials": trials}

@@ -367,7 +367,7 @@ __device__ void layout_write(const DevProblem &P, const BucketScratch &S, int32_
 // block cb of nc writes the tiles of the ops at bucket-order positions
 // [cb*tper, (cb+1)*tper).  Positions and tile indices are those of
 // layout_sums/layout_write (every op's full tiles first, then the tails).
-// Block 0 publishes the number of tiles.
+// Block 0 publishes the numbers of bucket positions and tiles.
 __device__ void layout_whole(const DevProblem &P, const BucketScratch &S, int32_t cb, int32_t nc,
                              int32_t min_vpl, int32_t ipt, int32_t *op_start_s, int32_t (*warp_sum)[32]) {
     constexpr int kW = kLayoutWholeOps / 256;  // ops per thread at most (blockDim.x == 256)
@@ -406,6 +406,7 @@ __device__ void layout_whole(const DevProblem &P, const BucketScratch &S, int32_
         const int32_t full = full_tiles(c, lg, ipt), rest = c - full * per_tile;
         op_start_s[v] = pos;
         if (k >= t0 && k < t1) {
+            S.op_start[v] = pos;  // for the count pass
             // {padded entries, distinct latencies, padded offset, first configuration}
             const int4 tx = make_int4(nvec * kVec, oi[j].w, oi[j].z, __ldg(P.ord_cbase + k));
             for (int32_t j = 0; j < full; ++j) {
@@ -421,7 +422,10 @@ __device__ void layout_whole(const DevProblem &P, const BucketScratch &S, int32_
         tt += rest > 0 ? 1 : 0;
         pos += c;
     }
-    if (cb == 0 && tid == 0) S.ctrl[kCtrlTiles] = (unsigned long long)(tot[1] + tot[2]);
+    if (cb == 0 && tid == 0) {
+        S.ctrl[kCtrlPositions] = (unsigned long long)tot[0];
+        S.ctrl[kCtrlTiles] = (unsigned long long)(tot[1] + tot[2]);
+    }
     __syncthreads();  // op_start_s complete
 }
 
@@ -845,6 +849,18 @@ __device__ __forceinline__ void counts_from_global(const DevProblem &P, const Bu
     }
 }
 
+// The counts of the tile's invocations computed by the count pass (k_counts):
+// c_s[j * H + h] = b_cnt[(b0 + j) * H + h] for the tile's j-th invocation,
+// which is cg[u * H + h] of the group holding j = g * IPT + u.  Every thread of
+// the CTA must call this; a block barrier must separate it from the reads.
+template <int IPT>
+__device__ __forceinline__ void counts_from_pass(const BucketScratch &S, const TileState<IPT> &T, int H,
+                                                 uint16_t *c_s) {
+    const int nc = T.m * H;
+    const uint16_t *src = S.b_cnt + (int64_t)(T.pos0 - T.g * IPT) * H;
+    for (int t = threadIdx.x; t < nc; t += kScoreThreads) c_s[t] = src[t];
+}
+
 // Score the staged chunk [c0, c0 + cn) of the tile's op.
 template <int MODE, int IPT>
 __device__ __forceinline__ void scan_chunk(const DevProblem &P, TileState<IPT> &T, int32_t c0, int32_t cn,
@@ -1010,7 +1026,10 @@ __device__ __forceinline__ void score_body(const DevProblem &P, const BucketScra
                 if (tid == 0) stage_chunk<MODE>(P, T.p0, c0, cn, false, T.dn, lr_s, rf_s, df_s, dl_s, bar);
                 pending = true;
             }
-            if (c0 == 0 && !dl_staged) counts_from_global(P, S, T, tc, H, P.dlat + T.p0, cg);
+            if (c0 == 0 && !dl_staged) {
+                if (S.b_cnt) counts_from_pass(S, T, H, c_s);
+                else counts_from_global(P, S, T, tc, H, P.dlat + T.p0, cg);
+            }
             // every thread must agree before any leaves the barrier sequence
             if (!__syncthreads_and(mbar_wait(bar, phase))) {
                 ok = false;
@@ -1125,7 +1144,10 @@ __device__ __forceinline__ void score_body_pipe(const DevProblem &P, const Bucke
                 }
                 pending |= 1u << (st ^ 1);
             }
-            if (c0 == 0 && !dl_staged) counts_from_global(P, S, T, tc, H, P.dlat + T.p0, cg);
+            if (c0 == 0 && !dl_staged) {
+                if (S.b_cnt) counts_from_pass(S, T, H, c_s);
+                else counts_from_global(P, S, T, tc, H, P.dlat + T.p0, cg);
+            }
             if (!__syncthreads_and(mbar_wait(bar0 + 8 * st, (phases >> st) & 1u))) {
                 ok = false;
                 break;
@@ -1204,6 +1226,122 @@ __global__ void __launch_bounds__(256) k_critical_paths(DevProblem P, const int3
 // segment is stair[.. h ..][c_h], and the decision is the least of the H keys.
 // c_h comes from the op's 32 first-round probe values (one line), then a
 // bisection of the window they leave, all H searches in lockstep.
+// For each backend h < n_hw <= MAXH, the count lo[h] of op g's distinct
+// latencies below the invocation's slack floor(ref * (rbase - Q[h]) / cp) (0
+// once the target has passed), one thread, every backend in lockstep: the op's
+// 32 first-round probe values (one 128-byte line, probe l at ((l+1)*dn >> 5) -
+// 1) leave, after c of them fall below the slack, the window [lo, hi] =
+// [(c*dn >> 5), ((c+1)*dn >> 5) - 1].  With SECOND, a window of more than 32
+// candidates is narrowed the same way by the 32 values of its second-round
+// line (op, c).  A bisection closes what is left; each round issues every
+// backend's loads before using any.
+template <int MAXH, bool SECOND>
+__device__ __forceinline__ void counts_all_backends(const DevProblem &P, int32_t g, int64_t ref, int64_t cp,
+                                                    uint64_t mg, int64_t rbase, int32_t (&lo)[MAXH]) {
+    const int H = P.n_hw;
+    const int32_t dn = P.dlat_n[g];
+    const int32_t *dl = P.dlat + P.pad_off[g];
+    int32_t sl[MAXH], hi[MAXH];
+#pragma unroll
+    for (int h = 0; h < MAXH; ++h) {
+        sl[h] = h < H ? slack_of(ref, cp, mg, rbase - P.q[h]) : 0;
+        lo[h] = 0;
+        hi[h] = h < H ? dn : 0;
+    }
+    if (dn > 32) {
+        const int4 *pv = reinterpret_cast<const int4 *>(P.dpiv + 32 * (int64_t)g);
+        int32_t cnt[MAXH];
+#pragma unroll
+        for (int h = 0; h < MAXH; ++h) cnt[h] = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            const int4 q4 = __ldg(pv + w);
+#pragma unroll
+            for (int h = 0; h < MAXH; ++h)
+                cnt[h] += (q4.x < sl[h]) + (q4.y < sl[h]) + (q4.z < sl[h]) + (q4.w < sl[h]);
+        }
+#pragma unroll
+        for (int h = 0; h < MAXH; ++h) {
+            if (h >= H) continue;
+            const int32_t c = cnt[h];
+            lo[h] = (c * dn) >> 5;
+            hi[h] = c < 32 ? (((c + 1) * dn) >> 5) - 1 : dn;
+        }
+        if (SECOND && P.dpiv2 && dn > 32 * 33) {  // only then can a window exceed 32
+            const int4 *lines[MAXH];
+#pragma unroll
+            for (int h = 0; h < MAXH; ++h) {
+                lines[h] = reinterpret_cast<const int4 *>(P.dpiv2 + ((32 * (int64_t)g + cnt[h]) << 5));
+                cnt[h] = 0;
+            }
+#pragma unroll
+            for (int w = 0; w < 8; ++w) {
+#pragma unroll
+                for (int h = 0; h < MAXH; ++h) {
+                    if (h >= H || hi[h] - lo[h] <= 32) continue;
+                    const int4 q4 = __ldg(lines[h] + w);
+                    cnt[h] += (q4.x < sl[h]) + (q4.y < sl[h]) + (q4.z < sl[h]) + (q4.w < sl[h]);
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < MAXH; ++h) {
+                const int32_t n = hi[h] - lo[h], c = cnt[h];
+                if (h >= H || n <= 32) continue;
+                hi[h] = c < 32 ? lo[h] + (((c + 1) * n) >> 5) - 1 : hi[h];
+                lo[h] += (c * n) >> 5;
+            }
+        }
+    }
+    for (;;) {
+        int32_t val[MAXH];
+        bool more = false;
+#pragma unroll
+        for (int h = 0; h < MAXH; ++h) {  // all loads first
+            const bool a = lo[h] < hi[h];
+            more |= a;
+            val[h] = a ? __ldg(dl + ((lo[h] + hi[h]) >> 1)) : 0;
+        }
+        if (!more) break;
+#pragma unroll
+        for (int h = 0; h < MAXH; ++h) {
+            if (lo[h] >= hi[h]) continue;
+            const int32_t mid = (lo[h] + hi[h]) >> 1;
+            if (val[h] < sl[h]) lo[h] = mid + 1; else hi[h] = mid;
+        }
+    }
+}
+
+// The count pass of the scan method, between bucketing and scoring, for the
+// ops whose distinct latencies the scoring kernel does not stage (more than
+// dl_cap): one thread per bucket position computes the counts of every backend
+// (counts_all_backends) into b_cnt, so the scoring kernel reads them instead of
+// running a 32-lane search per (invocation, backend) -- a thread's search
+// issues a few instructions per step where a warp-wide one issues a few
+// hundred per search.  Only ops among the first n_big_ops of the bucket order
+// can need counts, so only the positions before the first bucket of the
+// others are visited.
+template <int MAXH>
+__global__ void __launch_bounds__(256, 4) k_counts(DevProblem P, BucketScratch S, int32_t dl_cap) {
+    // the bucket entries and starts and the critical paths are visible after this
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int H = P.n_hw;
+    const int64_t n_pos = P.n_big_ops < P.n_ops ? (int64_t)S.op_start[P.op_order[P.n_big_ops]]
+                                                 : (int64_t)S.ctrl[kCtrlPositions];
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n_pos;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t g = S.gop[S.b_inv[p]];
+        if (P.dlat_n[g] <= dl_cap) continue;
+        int32_t lo[MAXH];
+        counts_all_backends<MAXH, true>(P, g, P.ref[g], P.cp[g], P.cp_magic[g], (int64_t)S.b_rem[p], lo);
+#pragma unroll
+        for (int h = 0; h < MAXH; ++h)
+            if (h < H) S.b_cnt[p * H + h] = (uint16_t)lo[h];
+    }
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+template __global__ void k_counts<4>(DevProblem, BucketScratch, int32_t);
+template __global__ void k_counts<LLAMA_MAX_HW>(DevProblem, BucketScratch, int32_t);
+
 __global__ void __launch_bounds__(256) k_stair(DevProblem P, int64_t n_inv, const int32_t *dag,
                                                const int32_t *op_local, const int64_t *start,
                                                int64_t now, BucketScratch S, llama_decision *out) {
@@ -1228,54 +1366,8 @@ __global__ void __launch_bounds__(256) k_stair(DevProblem P, int64_t n_inv, cons
             const int64_t rbase = P.slo[d] - (now - st);
             const int64_t ref = P.ref[g], cp = P.cp[g];
             const uint64_t mg = P.cp_magic[g];
-            const int32_t dn = P.dlat_n[g];
-            const int32_t *dl = P.dlat + P.pad_off[g];
-            int32_t sl[LLAMA_MAX_HW], lo[LLAMA_MAX_HW], hi[LLAMA_MAX_HW];
-#pragma unroll
-            for (int h = 0; h < LLAMA_MAX_HW; ++h) {
-                sl[h] = h < H ? slack_of(ref, cp, mg, rbase - P.q[h]) : 0;
-                lo[h] = 0;
-                hi[h] = h < H ? dn : 0;
-            }
-            if (dn > 32) {
-                // probe l sits at ((l+1)*dn >> 5) - 1; c probes below the slack
-                // leave the window [(c*dn >> 5), ((c+1)*dn >> 5) - 1]
-                const int4 *pv = reinterpret_cast<const int4 *>(P.dpiv + 32 * (int64_t)g);
-                int32_t cnt[LLAMA_MAX_HW];
-#pragma unroll
-                for (int h = 0; h < LLAMA_MAX_HW; ++h) cnt[h] = 0;
-#pragma unroll
-                for (int w = 0; w < 8; ++w) {
-                    const int4 q4 = __ldg(pv + w);
-#pragma unroll
-                    for (int h = 0; h < LLAMA_MAX_HW; ++h)
-                        cnt[h] += (q4.x < sl[h]) + (q4.y < sl[h]) + (q4.z < sl[h]) + (q4.w < sl[h]);
-                }
-#pragma unroll
-                for (int h = 0; h < LLAMA_MAX_HW; ++h) {
-                    if (h >= H) continue;
-                    const int32_t c = cnt[h];
-                    lo[h] = (c * dn) >> 5;
-                    hi[h] = c < 32 ? (((c + 1) * dn) >> 5) - 1 : dn;
-                }
-            }
-            for (;;) {
-                int32_t val[LLAMA_MAX_HW];
-                bool more = false;
-#pragma unroll
-                for (int h = 0; h < LLAMA_MAX_HW; ++h) {  // all loads first
-                    const bool a = lo[h] < hi[h];
-                    more |= a;
-                    val[h] = a ? __ldg(dl + ((lo[h] + hi[h]) >> 1)) : 0;
-                }
-                if (!more) break;
-#pragma unroll
-                for (int h = 0; h < LLAMA_MAX_HW; ++h) {
-                    if (lo[h] >= hi[h]) continue;
-                    const int32_t mid = (lo[h] + hi[h]) >> 1;
-                    if (val[h] < sl[h]) lo[h] = mid + 1; else hi[h] = mid;
-                }
-            }
+            int32_t lo[LLAMA_MAX_HW];
+            counts_all_backends<LLAMA_MAX_HW, false>(P, g, ref, cp, mg, rbase, lo);
             const uint16_t *sg = P.stair + P.stair_off[g];
             const int64_t stride = P.cfg_off[g + 1] - P.cfg_off[g] + 1;
             uint32_t key = 0xFFFFu;
@@ -1383,6 +1475,11 @@ __global__ void k_encode_stair(DevProblem P, uint16_t *stair) {
 
 int64_t max_tiles(int64_t n_inv, int32_t n_ops) { return n_inv + n_ops; }
 
+int schedule_launches(const ContextView &v, const BucketScratch &S) {
+    if (v.method == LLAMA_METHOD_STAIRCASE) return 2;
+    return S.b_cnt && v.need_counts ? 3 : 2;
+}
+
 cudaError_t enqueue_schedule(const ContextView &v, const BucketScratch &S, int64_t n_inv,
                              const int32_t *dag, const int32_t *op_local, const int64_t *start,
                              int64_t now, llama_decision *out, cudaStream_t s,
@@ -1438,8 +1535,34 @@ cudaError_t enqueue_schedule(const ContextView &v, const BucketScratch &S, int64
         if (e != cudaSuccess) return e;
     }
     mark(1);
-    // the scoring kernel may launch before k_bucket completes (it waits on
-    // griddepcontrol.wait before reading the scatter's output)
+    // the count pass, where some op's distinct latencies are not staged by the
+    // scoring kernel (and the scratch has room for the counts); the scoring
+    // kernel reads the counts only when it ran
+    BucketScratch Sc = S;
+    if (S.b_cnt && v.need_counts) {
+        cudaLaunchConfig_t cfg{};
+        // a thread per bucket position, at most four resident blocks per SM (the
+        // threads stride over the positions, whose number only the device knows)
+        cfg.gridDim = dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>((n_inv + 255) / 256,
+                                                                            (int64_t)v.num_sms * 4)));
+        cfg.blockDim = dim3(256);
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = trace ? 0 : 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        DevProblem P = v.P;
+        int32_t dl_cap = v.dlat_cap;
+        void *args[] = {&P, &Sc, &dl_cap};
+        e = cudaLaunchKernelExC(&cfg, v.n_hw <= 4 ? (const void *)k_counts<4> : (const void *)k_counts<LLAMA_MAX_HW>,
+                                args);
+        if (e != cudaSuccess) return e;
+    } else {
+        Sc.b_cnt = nullptr;
+    }
+    // the scoring kernel may launch before the previous kernel completes (it
+    // waits on griddepcontrol.wait before reading the bucketing output)
     cudaLaunchConfig_t cfg{};
     // a call has at most n_inv tiles: a small call leaves the rest of the GPU
     // to calls running beside it
@@ -1453,7 +1576,6 @@ cudaError_t enqueue_schedule(const ContextView &v, const BucketScratch &S, int64
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     DevProblem P = v.P;
-    BucketScratch Sc = S;
     int32_t chunk = v.score_chunk, dl_cap = v.dlat_cap;
     void *args[] = {&P, &Sc, &out, &chunk, &dl_cap};
     e = cudaLaunchKernelExC(&cfg, score_kernel(v.mode, v.ipt, v.stages), args);
@@ -1664,6 +1786,20 @@ __global__ void k_encode_piv(DevProblem P, int32_t *dpiv) {
     const int32_t v = (int32_t)(k >> 5), l = (int32_t)(k & 31), dn = P.dlat_n[v];
     if (P.encode_only && !P.encode_only[v]) return;
     dpiv[k] = dn > 32 ? P.dlat[P.pad_off[v] + (((l + 1) * dn) >> 5) - 1] : INT32_MAX;
+}
+
+// Second-round probe lines: one 128-byte line per (op, outcome c of the first
+// round), so a search's second round reads one line instead of bisecting the
+// window the first round leaves.  Lines of windows of 32 or fewer candidates
+// are unused.
+__global__ void k_encode_piv2(DevProblem P, int32_t *dpiv2) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= 1024 * (int64_t)P.n_ops) return;
+    const int32_t v = (int32_t)(k >> 10), c = (int32_t)((k >> 5) & 31), l = (int32_t)(k & 31);
+    if (P.encode_only && !P.encode_only[v]) return;
+    const int32_t dn = P.dlat_n[v];
+    const int32_t lo = (c * dn) >> 5, n = ((((c + 1) * dn) >> 5) - 1) - lo;
+    dpiv2[k] = dn > 32 && n > 32 ? P.dlat[P.pad_off[v] + lo + (((l + 1) * n) >> 5) - 1] : INT32_MAX;
 }
 
 // Decode tables (one CTA per op): the configuration behind every rank, and the

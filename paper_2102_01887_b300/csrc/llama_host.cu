@@ -60,7 +60,7 @@ int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 // starts, per-invocation bucket entries, the tile list and the control and
 // status words.  Counters and control words are zero between calls.
 struct Workspace {
-    DevBuf cnt, ctrl, op_start, gop, slot, b_inv, b_rem, rbase, tiles;
+    DevBuf cnt, ctrl, op_start, gop, slot, b_inv, b_rem, rbase, tiles, b_cnt;
     int64_t cap_inv = 0, cap_tiles = 0;
     int32_t cap_ops = 0;
 };
@@ -101,7 +101,7 @@ struct llama_ctx {
     int32_t n_ops = 0, max_npad = 0;
     int64_t n_cfg = 0, n_pad = 0;
     DevBuf cfg_off, hw_off, lat, cost, ref_cfg, batch, res, res_total;
-    DevBuf pad_off, seg_pad, lrb, dlat, dlat_n, dpiv, rf, df, inv, fast, op_order, ref_gidx;
+    DevBuf pad_off, seg_pad, lrb, dlat, dlat_n, dpiv, dpiv2, rf, df, inv, fast, op_order, ref_gidx;
     int64_t mean_npad = 0;
     DevBuf ref, cp, cp_magic;
     DevBuf q_dev;  // [LLAMA_MAX_HW] queueing time per backend, read by the kernels
@@ -119,6 +119,9 @@ struct llama_ctx {
     unsigned long long *h_ctrl = nullptr;  // pinned copy of the control words
 
     int last_launches = 0;
+    int32_t max_ncfg = 0;  // configurations of the largest op
+    int32_t n_big_ops = 0;  // ops with more padded entries than dlat_cap
+    int32_t count_pass = LLAMA_COUNT_PASS_AUTO;
     cudaEvent_t trace[LLAMA_TRACE_EVENTS] = {};
     bool tracing = false;
 
@@ -130,6 +133,7 @@ struct llama_ctx {
     cudaGraphExec_t gexec = nullptr;
     cudaGraphNode_t g_bucket = nullptr;  // the captured kernel that takes `now`
     int g_now_nargs = 0;
+    int g_launches = 2;  // kernel launches in the captured graph
     int64_t g_n_inv = -1, g_now = 0;
     const void *g_args[4] = {};
 
@@ -184,12 +188,14 @@ DevProblem make_problem(const llama_ctx *c) {
     P.dlat = c->dlat.as<int32_t>();
     P.dlat_n = c->dlat_n.as<int32_t>();
     P.dpiv = c->dpiv.as<int32_t>();
+    P.dpiv2 = c->dpiv2.p ? c->dpiv2.as<int32_t>() : nullptr;
     P.rf = c->rf.as<uint16_t>();
     P.df = c->df.as<uint16_t>();
     P.inv = c->inv.as<uint16_t>();
     P.fast = c->fast.as<int32_t>();
     P.op_order = c->op_order.as<int32_t>();
     P.max_npad = c->max_npad;
+    P.n_big_ops = c->n_big_ops;
     // prefetch the encoded tables into L2 when they take at most half of it
     const int64_t tbl_bytes = (int64_t)(c->opts.mode == LLAMA_MODE_ALPHA ? 10 : 8) * c->n_pad;
     const bool pf = c->n_pad > 0 && tbl_bytes <= c->l2_bytes / 2;
@@ -247,6 +253,7 @@ BucketScratch make_scratch(const Workspace &w) {
     S.b_rem = w.b_rem.as<int32_t>();
     S.rbase = w.rbase.as<int64_t>();
     S.tiles = w.tiles.as<int4>();
+    S.b_cnt = w.b_cnt.p ? w.b_cnt.as<uint16_t>() : nullptr;
     return S;
 }
 
@@ -271,6 +278,13 @@ ContextView view_of(const llama_ctx *c) {
     v.score_chunk = c->score_chunk;
     v.dlat_cap = c->dlat_cap;
     v.score_smem = c->score_smem;
+    // the count pass: where some op may have more distinct latencies than the
+    // scoring kernel stages, if asked for, or by default when such ops are at
+    // least half of them (few invocations per table: the scoring kernel's own
+    // searches would stand between the table copies)
+    v.need_counts = c->max_ncfg > c->dlat_cap &&
+                    (c->count_pass == LLAMA_COUNT_PASS_ON ||
+                     (c->count_pass == LLAMA_COUNT_PASS_AUTO && 2 * (int64_t)c->n_big_ops >= c->n_ops));
     return v;
 }
 
@@ -320,6 +334,8 @@ cudaError_t encode_tables(llama_ctx *c, const DevProblem &P, cudaStream_t s) {
     k_encode_lat<<<n_ops, 1024, c->lat_smem, s>>>(P, c->lrb.as<uint16_t>(), c->dlat.as<int32_t>(),
                                                   c->dlat_n.as<int32_t>());
     k_encode_piv<<<(unsigned)((32 * (int64_t)n_ops + 255) / 256), 256, 0, s>>>(P, c->dpiv.as<int32_t>());
+    if (c->dpiv2.p)
+        k_encode_piv2<<<(unsigned)((1024 * (int64_t)n_ops + 255) / 256), 256, 0, s>>>(P, c->dpiv2.as<int32_t>());
     k_encode_rank<<<n_ops, 1024, c->sort_smem, s>>>(P, c->sort_cap, c->rf.as<uint16_t>(),
                                                     alpha ? c->df.as<uint16_t>() : nullptr, c->inv.as<uint16_t>());
     k_encode_dec<<<n_ops, 256, 0, s>>>(P, c->dec.as<int4>(), c->dfast.as<int4>());
@@ -388,6 +404,7 @@ int ensure_ws(llama_ctx *c, Workspace &w, int64_t n_inv) {
         LL_CUDA(c, w.b_inv.alloc(sizeof(int32_t) * n));
         LL_CUDA(c, w.b_rem.alloc(sizeof(int32_t) * n));
         LL_CUDA(c, w.rbase.alloc(sizeof(int64_t) * n));
+        LL_CUDA(c, w.b_cnt.alloc(sizeof(uint16_t) * LLAMA_MAX_HW * n));
         w.cap_inv = n;
         w.cap_tiles = 0;
     }
@@ -499,6 +516,7 @@ int capture_graph(llama_ctx *c, int64_t n_inv, const int32_t *dag, const int32_t
     const BucketScratch S = make_scratch(c->ws);
     LL_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
     const cudaError_t e = enqueue_schedule(v, S, n_inv, dag, op_local, start, now, out, c->cap_stream, nullptr);
+    c->g_launches = schedule_launches(v, S);
     cudaGraph_t g = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
     if (e != cudaSuccess) {
@@ -540,7 +558,7 @@ int launch_schedule(llama_ctx *c, int64_t n_inv, const int32_t *dag, const int32
         const BucketScratch S = make_scratch(c->ws);
         LL_CUDA(c, enqueue_schedule(v, S, n_inv, dag, op_local, start, now, out, s,
                                     c->tracing ? c->trace : nullptr));
-        c->last_launches = 2;
+        c->last_launches = schedule_launches(v, S);
         return LLAMA_OK;
     }
     const bool same = c->gexec && c->g_n_inv == n_inv && c->g_args[0] == dag &&
@@ -554,7 +572,7 @@ int launch_schedule(llama_ctx *c, int64_t n_inv, const int32_t *dag, const int32
         c->g_now = now;
     }
     LL_CUDA(c, cudaGraphLaunch(c->gexec, s));
-    c->last_launches = 2;
+    c->last_launches = c->g_launches;
     return LLAMA_OK;
 }
 
@@ -863,6 +881,16 @@ extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cf
     } else {
         c->df.release();
     }
+    // second-round probe lines (4 KB per op) where a search can use them: more
+    // than 1,056 distinct latencies, so more than 1,024 configurations
+    int64_t max_n_cfg = 0;
+    for (int32_t v = 0; v < n_ops; ++v) max_n_cfg = std::max<int64_t>(max_n_cfg, cfg_off[v + 1] - cfg_off[v]);
+    if (max_n_cfg > 1024) {
+        if ((e = c->dpiv2.alloc(4 * 1024 * (size_t)n_ops)) != cudaSuccess)
+            return c->cuda_fail(e, "set_profiles upload");
+    } else {
+        c->dpiv2.release();
+    }
     c->n_ops = n_ops;
     c->n_cfg = n_cfg;
     c->n_pad = n_pad;
@@ -902,13 +930,19 @@ extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cf
         LL_CUDA(c, c->ord_pos.alloc(4 * (size_t)n_ops));
         LL_CUDA(c, cudaMemcpy(c->ord_pos.p, pos.data(), 4 * (size_t)n_ops, cudaMemcpyHostToDevice));
         c->h_ncfg.resize(n_ops);
-        for (int32_t v = 0; v < n_ops; ++v) c->h_ncfg[v] = (int32_t)(cfg_off[v + 1] - cfg_off[v]);
+        c->max_ncfg = 0;
+        for (int32_t v = 0; v < n_ops; ++v) {
+            c->h_ncfg[v] = (int32_t)(cfg_off[v + 1] - cfg_off[v]);
+            c->max_ncfg = std::max(c->max_ncfg, c->h_ncfg[v]);
+        }
         // shared-memory room for the distinct latencies of the largest op whose
         // list fits kMaxDlatSmem entries (none: every op searches global memory)
         int32_t cap = 0;
         for (int32_t v = 0; v < n_ops; ++v)
             if (dn[v] <= kMaxDlatSmem) cap = std::max(cap, dn[v]);
         c->dlat_cap = (cap + 3) / 4 * 4;
+        c->n_big_ops = 0;
+        for (int32_t v = 0; v < n_ops; ++v) c->n_big_ops += pad_off[v + 1] - pad_off[v] > c->dlat_cap;
         c->h_dn = std::move(dn);
     }
     c->stair_ready = false;
@@ -980,6 +1014,18 @@ extern "C" int llama_set_tuning(llama_ctx *c, int32_t lanes_min_vectors, int32_t
     c->score_chunk = chunk_entries ? std::min<int32_t>(chunk_entries, c->max_npad) : default_chunk(c->max_npad);
     c->score_smem = score_smem_bytes(c);
     return configure_score(c);
+}
+
+extern "C" int llama_set_count_pass(llama_ctx *c, int32_t mode) {
+    if (!c) return LLAMA_EINVAL;
+    if (mode != LLAMA_COUNT_PASS_AUTO && mode != LLAMA_COUNT_PASS_ON && mode != LLAMA_COUNT_PASS_OFF)
+        return c->fail(LLAMA_EINVAL, "set_count_pass: mode must be LLAMA_COUNT_PASS_AUTO, _ON or _OFF");
+    if (mode != c->count_pass) {
+        DeviceGuard g(c->opts.device);
+        c->drop_graph();  // the captured launch sequence changes
+        c->count_pass = mode;
+    }
+    return LLAMA_OK;
 }
 
 extern "C" int llama_set_method(llama_ctx *c, int32_t method) {

@@ -87,10 +87,19 @@ struct DevProblem {
     // [n_ops*32] per op with more than 32 distinct latencies, the 32 values a
     // 32-lane search probes first: dlat[pad_off[v] + ((l+1)*dn >> 5) - 1], l < 32
     const int32_t *dpiv;
+    // [n_ops*32*32] (null when no op has more than 1,024 configurations) per op
+    // and outcome c of a 32-probe first round (c of the dpiv values below the
+    // slack), the 32 values a second round probes in the window [lo, hi) that
+    // round leaves, lo = c*dn >> 5, hi = ((c+1)*dn >> 5) - 1:
+    // dlat[pad_off[v] + lo + ((l+1)*(hi-lo) >> 5) - 1], l < 32, when hi - lo > 32
+    const int32_t *dpiv2;
     const uint16_t *rf, *df, *inv;
     const int32_t *fast;
     const int32_t *op_order;  // ops by padded table size, largest first (bucket order)
     int32_t max_npad;  // largest padded op table (entries)
+    // ops whose padded tables exceed the distinct latencies the scoring kernel
+    // stages: the first n_big_ops of op_order, so their bucket positions come first
+    int32_t n_big_ops;
     // 128-byte lines to pull into L2 before scoring (0: off): of each of lrb, rf
     // (and df), all 2*n_pad bytes long, and of dlat (4*n_pad bytes)
     int64_t prefetch_rank_lines, prefetch_dlat_lines;
@@ -147,6 +156,9 @@ struct BucketScratch {
     int64_t *rbase;           // [n_inv]     target - elapsed time of each invocation
     int4 *tiles;              // [2*max_tiles] scoring tiles: {op, first bucket position, m, lanes_log2},
                               // {padded entries, distinct latencies, padded offset, 0}
+    uint16_t *b_cnt;          // [n_inv*n_hw] or null: for the invocation at each bucket position
+                              //             whose op's distinct latencies are not staged in shared
+                              //             memory, the count of them below its slack per backend
 };
 
 // floor(n / d) for n < 2^62 and d >= 1, given m = floor((2^64 - 1) / d): the high
@@ -183,6 +195,7 @@ struct ContextView {
     int32_t score_chunk;  // table entries staged per chunk
     int32_t dlat_cap;     // distinct latencies the scoring kernel stages (a multiple of 4)
     size_t score_smem;    // dynamic shared memory of the scoring kernel
+    bool need_counts;     // some op may have more distinct latencies than dlat_cap
 };
 int context_view(llama_ctx *c, ContextView *v);  // LLAMA_OK or the readiness error
 int context_fail(llama_ctx *c, int code, const char *msg);
@@ -228,6 +241,12 @@ __global__ void k_slack(DevProblem P, int64_t n_inv, const int32_t *dag, const i
 __global__ void k_encode_pad(DevProblem P, uint16_t *lrb, uint16_t *rf, uint16_t *df, int32_t *fast);
 __global__ void k_encode_lat(DevProblem P, uint16_t *lrb, int32_t *dlat, int32_t *dlat_n);
 __global__ void k_encode_piv(DevProblem P, int32_t *dpiv);
+__global__ void k_encode_piv2(DevProblem P, int32_t *dpiv2);
+template <int MAXH>
+__global__ void k_counts(DevProblem P, BucketScratch S, int32_t dl_cap);
+// Kernel launches of one scheduling call (scan method): bucketing, the count
+// pass when it runs, scoring.
+int schedule_launches(const ContextView &v, const BucketScratch &S);
 // Eq. 2: per-backend sums of L(x_i) R(x_i) over decided invocations, then the
 // queueing time floor(sum / R_total(lambda)) of every backend.
 __global__ void k_queue_sum(DevProblem P, int64_t n, const int32_t *dag, const int32_t *op_local,

@@ -23,11 +23,40 @@ def test_autotune_picks_a_schedule_and_results_stay_exact(cuda_device):
         st = torch.from_numpy(sub.start_us).to(dev)
         out = torch.zeros(sub.n * 24, dtype=torch.uint8, device=dev)
         res = autotune(s.ctx, dag, opl, st, sub.now_us, out, lanes=(8, 32), ipts=(1, 2), reps=2)
-        assert len(res["trials"]) == 8 and res["best"]["ms"] > 0  # 2 lanes x 2 ipt x 2 stagings
+        # 2 lanes x 2 ipt x 2 stagings; no count-pass trials: every op's distinct
+        # latencies are staged by the scoring kernel
+        assert len(res["trials"]) == 8 and res["best"]["ms"] > 0
+        assert res["best"]["count_pass"] == L.COUNT_PASS_AUTO
         out.zero_()
         L.llama_schedule_async(s.ctx, dag, opl, st, sub.now_us, out)
         torch.cuda.synchronize()
     got = out.cpu().numpy().view(L.DECISION_DTYPE)
     exp, _ = oracle.schedule(p, sub)
+    for k in ("cfg", "lat", "cost", "slack", "flags"):
+        assert np.array_equal(got[k], exp[k]), k
+
+
+def test_autotune_chooses_the_count_pass_and_results_stay_exact(cuda_device):
+    import torch
+
+    from paper_2102_01887_b300 import build, llama as L
+    from paper_2102_01887_b300.autotune import autotune
+    build.build()
+    p, inv = W.batched_large(n_dags=16, n_inv=4096)  # every op beyond the staged latencies
+    dev = torch.device("cuda", cuda_device)
+    with L.Scheduler(p, use_graph=True) as s:
+        dag = torch.from_numpy(inv.dag).to(dev)
+        opl = torch.from_numpy(inv.op_local).to(dev)
+        st = torch.from_numpy(inv.start_us).to(dev)
+        out = torch.zeros(inv.n * 24, dtype=torch.uint8, device=dev)
+        res = autotune(s.ctx, dag, opl, st, inv.now_us, out, lanes=(32,), ipts=(1,), stages=(1,), reps=2)
+        assert [t.get("count_pass") for t in res["trials"]] == [None, L.COUNT_PASS_ON, L.COUNT_PASS_OFF]
+        assert res["best"]["ms"] == min(t["ms"] for t in res["trials"])
+        out.zero_()
+        L.llama_schedule_async(s.ctx, dag, opl, st, inv.now_us, out)
+        torch.cuda.synchronize()
+        assert L.llama_last_launch_count(s.ctx) == (2 if res["best"]["count_pass"] == L.COUNT_PASS_OFF else 3)
+    got = out.cpu().numpy().view(L.DECISION_DTYPE)
+    exp, _ = oracle.schedule(p, inv)
     for k in ("cfg", "lat", "cost", "slack", "flags"):
         assert np.array_equal(got[k], exp[k]), k

@@ -398,17 +398,40 @@ def test_tunings_change_no_result(L, tuning):
     p, inv = W.random_small(77, max_cfg=300, n_inv=3000, value_range=200)
     pm, invm = W.medium()
     subm = invm.subset(np.arange(0, invm.n, 7))
-    # ops of 8,192 configurations: their distinct latencies are searched in
-    # global memory by groups of 1 to 256 lanes
+    # ops of 8,192 configurations: their distinct latencies are not staged, so
+    # they are counted below each slack by the count pass, or (pass off)
+    # searched in global memory by groups of 1 to 256 lanes
     pl, invl = W.batched_large(n_dags=4, n_inv=2048)
-    for prob, case in ((p, inv), (pm, subm), (pl, invl)):
+    for prob, case, passes in ((p, inv, (L.COUNT_PASS_AUTO,)), (pm, subm, (L.COUNT_PASS_AUTO,)),
+                               (pl, invl, (L.COUNT_PASS_ON, L.COUNT_PASS_OFF))):
         for mode in (0, 1):
             exp, _ = oracle.schedule(prob, case, mode=mode, alpha=(2, 3))
-            with L.Scheduler(prob, mode=mode, alpha=(2, 3)) as s:
-                L.llama_set_tuning(s.ctx, *tuning)
+            for cp in passes:
+                with L.Scheduler(prob, mode=mode, alpha=(2, 3)) as s:
+                    L.llama_set_tuning(s.ctx, *tuning)
+                    L.llama_set_count_pass(s.ctx, cp)
+                    got, rc = s.schedule(case)
+                assert rc == L.OK
+                assert_same(got, exp, f"tuning {tuning} mode {mode} count pass {cp}")
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["cost_first", "alpha"])
+def test_count_pass_changes_no_result(L, mode):
+    # Zipf-sized tables (a few ops beyond the staged distinct latencies, each
+    # with many invocations: AUTO leaves the pass off) and all ops at 8,192
+    # configurations (AUTO turns it on); every setting gives the oracle's
+    # decisions, and the launch count shows whether the pass ran
+    cases = ((W.batched(n_inv=65536), 2), (W.batched_large(n_dags=24, n_inv=6000), 3))
+    for (prob, case), auto_launches in cases:
+        exp, _ = oracle.schedule(prob, case, mode=mode, alpha=(2, 3))
+        with L.Scheduler(prob, mode=mode, alpha=(2, 3)) as s:
+            for cp, launches in ((L.COUNT_PASS_AUTO, auto_launches), (L.COUNT_PASS_ON, 3),
+                                 (L.COUNT_PASS_OFF, 2), (L.COUNT_PASS_ON, 3)):
+                L.llama_set_count_pass(s.ctx, cp)
                 got, rc = s.schedule(case)
-            assert rc == L.OK
-            assert_same(got, exp, f"tuning {tuning} mode {mode}")
+                assert rc == L.OK
+                assert L.llama_last_launch_count(s.ctx) == launches, cp
+                assert_same(got, exp, f"count pass {cp}")
 
 
 @pytest.fixture(scope="module")

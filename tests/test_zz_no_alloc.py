@@ -66,3 +66,43 @@ def test_static_rejects_too_many_operations(cuda_device):
         rc = lib.llama_schedule_static(s.ctx, 0, None, None, None, inv.now_us, None, None)
         assert rc == L.EINVAL
         assert "LLAMA_STATIC_MAX_OPS" in L.llama_last_error(s.ctx)
+
+
+@pytest.mark.parametrize("tuning", [(16, 2, 0, 1), (4, 1, 0, 1), (128, 4, 0, 2)],
+                         ids=["default", "256-lanes", "8-lanes-two-stages"])
+def test_static_searches_unstaged_latencies_like_the_count_pass(cuda_device, tuning):
+    """Ops of 8,192 configurations have more distinct latencies than the scoring
+    kernel stages.  The allocating entry point counts them below each slack in a
+    separate pass; the allocation-free one, whose array has no room for those
+    counts, searches them inside the scoring kernel.  Both must give the oracle's
+    decisions, under launch schedules with 32-lane and narrower searches."""
+    import torch
+
+    import oracle
+    from paper_2102_01887_b300 import build, llama as L
+    build.build()
+    lib = L.load()
+    dev = torch.device("cuda", cuda_device)
+    p, inv = W.batched_large(n_dags=32, n_inv=8192)
+    assert p.n_ops <= L.STATIC_MAX_OPS
+    exp, rc_o = oracle.schedule(p, inv)
+    assert rc_o == 0
+    with L.Scheduler(p, device=cuda_device) as s:
+        L.llama_set_tuning(s.ctx, *tuning)
+        got, rc = s.schedule(inv)
+        assert rc == L.OK
+        assert L.llama_last_launch_count(s.ctx) == 3  # bucketing, count pass, scoring
+        dag = torch.from_numpy(inv.dag).to(dev)
+        opl = torch.from_numpy(inv.op_local).to(dev)
+        st = torch.from_numpy(inv.start_us).to(dev)
+        stream = torch.cuda.Stream(device=dev)
+        for _ in range(2):
+            out = torch.full((inv.n * 24,), 0xA5, dtype=torch.uint8, device=dev)
+            rc = lib.llama_schedule_static(s.ctx, inv.n, dag.data_ptr(), opl.data_ptr(), st.data_ptr(),
+                                           inv.now_us, out.data_ptr(), ctypes.c_void_p(stream.cuda_stream))
+            assert rc == L.OK, L.llama_last_error(s.ctx)
+            stream.synchronize()
+            got_static = out.cpu().numpy().view(L.DECISION_DTYPE)
+            for k in FIELDS:
+                assert np.array_equal(got[k], exp[k]), k
+                assert np.array_equal(got_static[k], exp[k]), k
