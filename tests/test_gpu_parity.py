@@ -225,6 +225,33 @@ def test_backend_counts(L, n_hw, method):
         assert_same(got, exp)
 
 
+@pytest.mark.parametrize("n_hw", [5, 8])
+def test_count_pass_with_more_than_four_backends(L, n_hw):
+    # 8,192-configuration tables split into 5 or 8 backend segments: the count
+    # pass's eight-backend variant and the scoring kernel's own searches (pass
+    # off) against the oracle, in both objectives
+    rng = np.random.default_rng(40 + n_hw)
+    p, inv = W.batched_large(n_dags=4, n_inv=2048)
+    hw = []
+    for n in np.diff(p.cfg_off):
+        cuts = np.sort(rng.integers(1, n, size=n_hw - 1))  # the reference configuration stays on backend 0
+        hw.append(np.concatenate([[0], cuts, [n]]))
+    p.n_hw = n_hw
+    p.hw_off = np.concatenate(hw).astype(np.int32)
+    p.q_us = rng.integers(0, 100_000, size=n_hw).astype(np.int64)
+    p.res_total = rng.integers(1, 9, size=n_hw).astype(np.int32)
+    for mode in (0, 1):
+        exp, _ = oracle.schedule(p, inv, mode=mode, alpha=(5, 2))
+        with L.Scheduler(p, mode=mode, alpha=(5, 2)) as s:
+            assert L.load().llama_set_count_pass(s.ctx, 7) == L.EINVAL
+            for cp, launches in ((L.COUNT_PASS_ON, 3), (L.COUNT_PASS_OFF, 2)):
+                L.llama_set_count_pass(s.ctx, cp)
+                got, rc = s.schedule(inv)
+                assert rc == L.OK
+                assert L.llama_last_launch_count(s.ctx) == launches
+                assert_same(got, exp, f"{n_hw} backends, mode {mode}, count pass {cp}")
+
+
 # ---------------------------------------------------- device-side calls ---
 
 def test_device_pointers_and_async_stream(L, method):
