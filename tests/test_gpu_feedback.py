@@ -85,6 +85,35 @@ def test_feedback_updates_tables_and_decisions(L, mode, alpha, method):
     assert (after["cfg"] != before["cfg"]).any()
 
 
+@pytest.mark.parametrize("count_pass", [1, 2], ids=["count_pass_on", "count_pass_off"])
+def test_feedback_on_tables_beyond_the_staged_latencies(L, count_pass):
+    # 8,192-configuration ops: the feedback re-encodes the touched ops' distinct
+    # latencies and both levels of probe lines, which the count pass (or, with
+    # it off, the scoring kernel's own searches) reads on the next call
+    p, inv = W.batched_large(n_dags=8, n_inv=4096)
+    rng = np.random.default_rng(11)
+    n = 20_000
+    ops = np.unique(p.dag_op_off[inv.dag] + inv.op_local)[:120]  # invoked ops
+    g = np.concatenate([rng.integers(p.cfg_off[v], p.cfg_off[v + 1], 100) for v in ops])
+    g = g[rng.integers(0, g.shape[0], n)]
+    op = (np.searchsorted(p.cfg_off, g, side="right") - 1).astype(np.int32)
+    cfg = (g - p.cfg_off[op]).astype(np.int32)
+    # faster and cheaper than profiled: about a third of the decisions change
+    lat = np.maximum(1, p.lat_us[g] * rng.uniform(0.05, 0.5, n)).astype(np.int32)
+    cost = (p.cost_nd[g] * rng.uniform(0.1, 0.5, n)).astype(np.int64)
+    with L.Scheduler(p, use_graph=True) as s:
+        L.llama_set_count_pass(s.ctx, count_pass)
+        before, _ = s.schedule(inv)
+        L.llama_feedback(s.ctx, dev(op), dev(cfg), dev(lat), dev(cost), beta=(1, 2))
+        after, _ = s.schedule(inv)
+        assert L.llama_last_launch_count(s.ctx) == (3 if count_pass == 1 else 2)
+    q = copy.deepcopy(p)
+    assert oracle.feedback(q, op, cfg, lat, cost, beta=(1, 2)) == 0
+    exp, _ = oracle.schedule(q, inv)
+    same(after, exp, "after feedback")
+    assert (after["cfg"] != before["cfg"]).sum() > 1000
+
+
 @pytest.mark.parametrize("method", [0, 1], ids=["scan", "staircase"])
 def test_affinity_and_commit_order(L, method):
     import torch
