@@ -104,3 +104,42 @@ def test_memory_budget_sets_the_slots(L):
     with L.Scheduler(p) as s, L.Server(s, slots=0, max_batch=1024, memory_budget=64 << 20) as srv:
         st = srv.stats()
     assert 1 <= st["slots"] <= 64
+
+
+def test_workspaces_run_the_count_pass_side_by_side(L):
+    # two workspaces of one context on two streams at once, tables of 8,192
+    # configurations (count pass on): each call keeps its counts in its own
+    # workspace, and both equal the oracle's decisions
+    import ctypes
+
+    import torch
+    lib = L.load()
+    p, inv = W.batched_large(n_dags=8, n_inv=8192)
+    halves = (inv.subset(np.arange(0, inv.n, 2)), inv.subset(np.arange(1, inv.n, 2)))
+    exp = [oracle.schedule(p, h)[0] for h in halves]
+    with L.Scheduler(p) as s:
+        L.llama_set_count_pass(s.ctx, L.COUNT_PASS_ON)
+        wss, streams, outs, args = [], [], [], []
+        try:
+            for h in halves:
+                ws = ctypes.c_void_p()
+                assert lib.llama_ws_create(s.ctx, h.n, ctypes.byref(ws)) == L.OK, L.llama_last_error(s.ctx)
+                wss.append(ws)
+                streams.append(torch.cuda.Stream())
+                outs.append(torch.full((h.n * 24,), 0xA5, dtype=torch.uint8, device="cuda"))
+                args.append([torch.from_numpy(a).cuda() for a in (h.dag, h.op_local, h.start_us)])
+            for _ in range(3):  # repeated, the two calls overlapping on the device
+                for k, h in enumerate(halves):
+                    d, o, st = args[k]
+                    rc = lib.llama_schedule_ws_async(s.ctx, wss[k], h.n, d.data_ptr(), o.data_ptr(), st.data_ptr(),
+                                                     h.now_us, outs[k].data_ptr(),
+                                                     ctypes.c_void_p(streams[k].cuda_stream))
+                    assert rc == L.OK, L.llama_last_error(s.ctx)
+                torch.cuda.synchronize()
+                for k in range(2):
+                    got = outs[k].cpu().numpy().view(L.DECISION_DTYPE)
+                    for f in FIELDS:
+                        assert np.array_equal(got[f], exp[k][f]), (k, f)
+        finally:
+            for ws in wss:
+                lib.llama_ws_destroy(ws)
