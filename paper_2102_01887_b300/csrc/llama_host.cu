@@ -885,6 +885,7 @@ extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cf
     // than 1,056 distinct latencies, so more than 1,024 configurations
     int64_t max_n_cfg = 0;
     for (int32_t v = 0; v < n_ops; ++v) max_n_cfg = std::max<int64_t>(max_n_cfg, cfg_off[v + 1] - cfg_off[v]);
+    c->max_ncfg = (int32_t)max_n_cfg;
     if (max_n_cfg > 1024) {
         if ((e = c->dpiv2.alloc(4 * 1024 * (size_t)n_ops)) != cudaSuccess)
             return c->cuda_fail(e, "set_profiles upload");
@@ -930,11 +931,7 @@ extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cf
         LL_CUDA(c, c->ord_pos.alloc(4 * (size_t)n_ops));
         LL_CUDA(c, cudaMemcpy(c->ord_pos.p, pos.data(), 4 * (size_t)n_ops, cudaMemcpyHostToDevice));
         c->h_ncfg.resize(n_ops);
-        c->max_ncfg = 0;
-        for (int32_t v = 0; v < n_ops; ++v) {
-            c->h_ncfg[v] = (int32_t)(cfg_off[v + 1] - cfg_off[v]);
-            c->max_ncfg = std::max(c->max_ncfg, c->h_ncfg[v]);
-        }
+        for (int32_t v = 0; v < n_ops; ++v) c->h_ncfg[v] = (int32_t)(cfg_off[v + 1] - cfg_off[v]);
         // shared-memory room for the distinct latencies of the largest op whose
         // list fits kMaxDlatSmem entries (none: every op searches global memory)
         int32_t cap = 0;
