@@ -47,6 +47,8 @@ extern "C" {
 /* llama_decision.flags */
 #define LLAMA_FLAG_FEASIBLE 1 /* the chosen configuration meets its slack */
 #define LLAMA_FLAG_INVALID 2  /* the invocation was rejected; cfg = -1 */
+#define LLAMA_FLAG_TIMEOUT 4  /* not decided: a bounded device wait of the call gave up
+                                 (the call reports LLAMA_ETIMEOUT); cfg = -1 */
 
 /* Limits enforced by validation. */
 #define LLAMA_MAX_HW 8          /* backends lambda */
@@ -74,7 +76,11 @@ typedef struct llama_decision {
     int32_t flags; /* LLAMA_FLAG_* */
 } llama_decision;
 
-/* Create a context on opts->device.  *out is set on success.
+/* Create a context on opts->device: the state of one Configurator (Section
+ * 4: the Logic Plane's slack allotment, Algorithm 1, and cost-based
+ * optimizer, Eq. 1), with the objective of Eq. 1 chosen by opts->mode and
+ * alpha = alpha_num / alpha_den.  *out is set on success (the caller owns
+ * the context and releases it with llama_destroy).
  * Errors: EINVAL (bad opts), ENOMEM, ECUDA. */
 int llama_create(llama_ctx **out, const llama_opts *opts);
 
@@ -174,7 +180,11 @@ int llama_get_profiles(llama_ctx *ctx, int32_t *lat_us, int64_t *cost_nd);
 int llama_queue_time(llama_ctx *ctx, int64_t n, const int32_t *dag, const int32_t *op_local,
                      const llama_decision *dec, int64_t *q_out, int32_t apply, void *stream);
 
-/* Schedule n_inv pending invocations at time now_us (blocking).
+/* Schedule n_inv pending invocations at time now_us (blocking): for each,
+ * its slack on every backend (Section 4.1, Algorithm 1: the target minus the
+ * elapsed time and the backend's queueing time, times the op's share of its
+ * longest remaining reference path) and the configuration that Eq. 1
+ * (Section 4.2) selects against the slack of the configuration's own backend.
  *   dag[n_inv], op_local[n_inv]  the invocation's DAG and op-local operation;
  *   start_us[n_inv]              start time of its pipeline instance, 0..now_us;
  *   out[n_inv]                   decisions, written in invocation order.
@@ -188,8 +198,9 @@ int llama_queue_time(llama_ctx *ctx, int64_t n, const int32_t *dag, const int32_
 int llama_schedule(llama_ctx *ctx, int64_t n_inv, const int32_t *dag, const int32_t *op_local,
                    const int64_t *start_us, int64_t now_us, llama_decision *out);
 
-/* Same as llama_schedule, enqueued on `stream` (a cudaStream_t; NULL = the
- * legacy default stream) and returning without waiting.  Every pointer must
+/* Same as llama_schedule (Algorithm 1 and Eq. 1, Sections 4.1-4.2),
+ * enqueued on `stream` (a cudaStream_t; NULL = the legacy default stream)
+ * and returning without waiting.  Every pointer must
  * be device memory that stays valid until the stream passes the call.
  * Invalid invocations are flagged in `out` but the return value does not
  * report them.  Scratch space is library-owned and grows on demand; call
@@ -239,14 +250,34 @@ int llama_ws_status(llama_ws *ws, int64_t *invalid, int32_t *timeout);
  * profiles; larger sizes are rejected with EINVAL before anything is
  * launched.  The first call on a device looks up the array's device address
  * (once per device, with that device current); make that first call before
- * any stream capture.  Every call shares the one array and each call clears
- * the counters it needs at zero; calls that overlap on the GPU race on the
- * array: serialise them.  Errors: EINVAL, ENOTREADY, ECUDA. */
+ * any stream capture.  The address stays cached for the process: after
+ * cudaDeviceReset (or anything else that destroys the device's primary
+ * context) this entry point must not be called again in that process.
+ * Every call shares the one array, which keeps the last call's contents.
+ * The counters and control words a call needs at zero are zero when it
+ * starts: the array starts zeroed, every completed call leaves them cleared
+ * (its last kernel clears them), and a call whose later launch fails clears
+ * them with memsets on its stream before returning ECUDA.  Calls that overlap
+ * on the GPU race on the array: serialise them.  A bounded device wait that
+ * gives up, and invalid invocations, are not reported by the return value
+ * (the call returns once its kernels are enqueued): read them with
+ * llama_static_status.  llama_last_launch_count reports this call's kernels.
+ * Errors: EINVAL, ENOTREADY, ECUDA. */
 #define LLAMA_STATIC_MAX_INV 65536
 #define LLAMA_STATIC_MAX_OPS 4096
 int llama_schedule_static(llama_ctx *ctx, int64_t n_inv, const int32_t *dag,
                           const int32_t *op_local, const int64_t *start_us, int64_t now_us,
                           llama_decision *out, void *stream);
+
+/* Status of the last llama_schedule_static call completed on the context's
+ * device (no counterpart in the paper): the number of invalid invocations
+ * and whether a bounded device wait gave up (then every valid invocation of
+ * that call is flagged LLAMA_FLAG_TIMEOUT with cfg = -1).  Enqueues a copy of
+ * the array's two status words on `stream` (order it after the call) and
+ * waits for it; allocates nothing.  invalid and timeout are host pointers,
+ * each nullable.  Errors: EINVAL (a null context, a device ordinal above 63),
+ * ENOTREADY, ECUDA. */
+int llama_static_status(llama_ctx *ctx, void *stream, int64_t *invalid, int32_t *timeout);
 
 /* Launch schedule of the scoring kernel (no counterpart in the paper; a
  * B300 schedule that changes speed, never results):
@@ -298,6 +329,18 @@ int llama_set_count_pass(llama_ctx *ctx, int32_t mode);
 #define LLAMA_METHOD_SCAN 0
 #define LLAMA_METHOD_STAIRCASE 1
 int llama_set_method(llama_ctx *ctx, int32_t method);
+
+/* Bounded device waits (no counterpart in the paper).  The bucketing kernel's
+ * grid barriers poll at most `tries` times before they give up: the call then
+ * decides nothing (every valid invocation is flagged LLAMA_FLAG_TIMEOUT with
+ * cfg = -1) and reports LLAMA_ETIMEOUT (llama_schedule), or through
+ * llama_ws_status / llama_static_status.  The default,
+ * LLAMA_WAIT_LIMIT_DEFAULT, is never reached by a launch whose blocks are all
+ * resident; a lower value (0: give up at once) exercises the give-up path.
+ * Table staging waits keep their own fixed bound.  Errors: EINVAL (tries
+ * outside 0..LLAMA_WAIT_LIMIT_DEFAULT). */
+#define LLAMA_WAIT_LIMIT_DEFAULT (1 << 20)
+int llama_set_wait_limit(llama_ctx *ctx, int32_t tries);
 
 /* Pre-allocate scratch for calls of up to max_inv invocations. */
 int llama_reserve(llama_ctx *ctx, int64_t max_inv);

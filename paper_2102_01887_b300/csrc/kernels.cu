@@ -430,22 +430,35 @@ __device__ void layout_whole(const DevProblem &P, const BucketScratch &S, int32_
 }
 
 // All blocks of a cooperative launch reach this point before any continues.
-// Bounded: after kMaxWaitTries polls the block records a timeout and goes on
-// (the call's results are then invalid and the host reports ETIMEOUT).
-__device__ __forceinline__ void grid_barrier(unsigned long long *count, unsigned long long target,
-                                             unsigned long long *timeout) {
+// Bounded: after `tries` polls the block records a timeout and the barrier
+// returns false in every thread of the block; the block must then stop (it
+// does not arrive at later barriers, so every other block gives up at its next
+// one).  The call's later kernels see the flag and decode nothing.
+__device__ __forceinline__ bool grid_barrier(unsigned long long *count, unsigned long long target,
+                                             unsigned long long *timeout, int32_t tries) {
     __syncthreads();
+    int gave_up = 0;
     if (threadIdx.x == 0) {
         __threadfence();
         atomicAdd(count, 1ull);
         unsigned long long seen = 0;
-        for (int it = 0; it < kMaxWaitTries; ++it) {
+        for (int it = 0; it < tries; ++it) {
             asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(seen) : "l"(count) : "memory");
             if (seen >= target) break;
         }
-        if (seen < target) atomicOr(timeout, 1ull);
+        if (seen < target) {
+            atomicOr(timeout, 1ull);
+            gave_up = 1;
+        }
     }
-    __syncthreads();
+    return !__syncthreads_or(gave_up);
+}
+
+// Nonzero once a bounded wait of the call gave up.  Read by the kernels that
+// follow k_bucket after griddepcontrol.wait (k_bucket has completed and its
+// writes are visible): they then read no bucket entry and no tile.
+__device__ __forceinline__ bool call_timed_out(const BucketScratch &S) {
+    return *reinterpret_cast<volatile unsigned long long *>(&S.ctrl[kCtrlTimeout]) != 0ull;
 }
 
 // Validate invocation i and count it for its op: g = global op (-1 if invalid,
@@ -570,8 +583,11 @@ __global__ void __launch_bounds__(256) k_bucket(DevProblem P, int64_t n_inv, con
     // critical-path staging area these blocks do not use), or, for more ops,
     // per-block sums, prefixes over the blocks and the writes between two more
     // barriers of the counting blocks
+    // A barrier that gives up ends the block: counts that are not final give
+    // no layout, and a layout that is not complete no scatter.
     const int32_t cb = (int32_t)(blockIdx.x - n_cp);
-    grid_barrier(&S.ctrl[kCtrlCountBarrier], (unsigned long long)nb, &S.ctrl[kCtrlTimeout]);
+    unsigned long long *const bar = &S.ctrl[kCtrlCountBarrier], *const tmo = &S.ctrl[kCtrlTimeout];
+    if (!grid_barrier(bar, (unsigned long long)nb, tmo, P.wait_tries)) return;
     const int32_t *op_start;
     if (P.n_ops <= kLayoutWholeOps) {
         int32_t *op_start_s = reinterpret_cast<int32_t *>(&sm);
@@ -580,9 +596,9 @@ __global__ void __launch_bounds__(256) k_bucket(DevProblem P, int64_t n_inv, con
     } else {
         LayoutRun R;
         layout_sums(P, S, cb, (int32_t)nb, min_vpl, ipt, R, warp_sum);
-        grid_barrier(&S.ctrl[kCtrlCountBarrier], 2ull * (unsigned long long)nb, &S.ctrl[kCtrlTimeout]);
+        if (!grid_barrier(bar, 2ull * (unsigned long long)nb, tmo, P.wait_tries)) return;
         layout_write(P, S, cb, (int32_t)nb, min_vpl, ipt, R, warp_sum);
-        grid_barrier(&S.ctrl[kCtrlCountBarrier], 3ull * (unsigned long long)nb, &S.ctrl[kCtrlTimeout]);
+        if (!grid_barrier(bar, 3ull * (unsigned long long)nb, tmo, P.wait_tries)) return;
         op_start = S.op_start;
     }
 
@@ -701,18 +717,42 @@ __device__ __forceinline__ void clear_counters(const DevProblem &P, const Bucket
 }
 
 // End of a scoring kernel: the last CTA to finish publishes the call's status
-// and clears the control words, so the next call needs no memset.
-__device__ __forceinline__ void finish_call(const BucketScratch &S) {
+// and clears the control words, so the next call needs no memset.  If a
+// bounded wait of the call gave up (bucketing barrier or table staging), that
+// CTA first marks every valid invocation not decided (cfg = -1,
+// LLAMA_FLAG_TIMEOUT): every other CTA has finished, so nothing overwrites
+// them, and decisions of tiles scored before the wait gave up are dropped too.
+// Invalid invocations keep what k_bucket wrote.  S.gop was written for every
+// invocation of the call before k_bucket's first barrier; k_stair (mark =
+// false) writes no S.gop and has no bounded wait.
+__device__ __forceinline__ void finish_call(const BucketScratch &S, llama_decision *out, bool mark) {
+    __shared__ int role;  // 0: not the last CTA; 1: the last; 2: the last, and the call timed out
     __syncthreads();
     if (threadIdx.x == 0) {
+        role = 0;
         __threadfence();
         if (atomicAdd(&S.ctrl[kCtrlDone], 1ull) == (unsigned long long)gridDim.x - 1) {
             __threadfence();
+            const unsigned long long tmo = atomicAdd(&S.ctrl[kCtrlTimeout], 0ull);
             S.status[0] = atomicAdd(&S.ctrl[kCtrlInvalid], 0ull);
-            S.status[1] = atomicAdd(&S.ctrl[kCtrlTimeout], 0ull);
-            for (int k = 0; k < kCtrlWords; ++k) atomicExch(&S.ctrl[k], 0ull);
+            S.status[1] = tmo;
+            role = tmo && mark ? 2 : 1;
         }
     }
+    __syncthreads();
+    if (role == 2) {  // block-uniform
+        llama_decision nd;
+        nd.cfg = -1;
+        nd.lat = 0;
+        nd.cost = 0;
+        nd.slack = 0;
+        nd.flags = LLAMA_FLAG_TIMEOUT;
+        for (int64_t i = threadIdx.x; i < S.n_inv; i += blockDim.x)
+            if (__ldcg(&S.gop[i]) >= 0) out[i] = nd;
+        __syncthreads();
+    }
+    if (role != 0 && threadIdx.x == 0)
+        for (int k = 0; k < kCtrlWords; ++k) atomicExch(&S.ctrl[k], 0ull);
 }
 
 // Per-thread view of the current tile.
@@ -1001,7 +1041,8 @@ __device__ __forceinline__ void score_body(const DevProblem &P, const BucketScra
     asm volatile("griddepcontrol.wait;" ::: "memory");
     clear_counters(P, S);
     if (tid < H) tc.q[tid] = P.q[tid];
-    const long long n_tiles = (long long)S.ctrl[kCtrlTiles];
+    // after a bucketing barrier gave up, no tile list or bucket entry is read
+    const long long n_tiles = call_timed_out(S) ? 0 : (long long)S.ctrl[kCtrlTiles];
     long long ti = blockIdx.x;
     // the first chunk of a tile, from the tile's descriptor tx = {npad, dn, p0}
     // (every op has at least one configuration: npad > 0)
@@ -1073,7 +1114,7 @@ __device__ __forceinline__ void score_body(const DevProblem &P, const BucketScra
         if (!ok && tid == 0) atomicOr(&S.ctrl[kCtrlTimeout], 1ull);
         mbar_wait(bar, phase);
     }
-    finish_call(S);
+    finish_call(S, out, true);
 }
 
 // Two staging buffers: while a chunk is scored, the next one (of the same tile,
@@ -1115,7 +1156,8 @@ __device__ __forceinline__ void score_body_pipe(const DevProblem &P, const Bucke
     asm volatile("griddepcontrol.wait;" ::: "memory");
     clear_counters(P, S);
     if (tid < H) tc.q[tid] = P.q[tid];
-    const long long n_tiles = (long long)S.ctrl[kCtrlTiles];
+    // after a bucketing barrier gave up, no tile list or bucket entry is read
+    const long long n_tiles = call_timed_out(S) ? 0 : (long long)S.ctrl[kCtrlTiles];
     long long ti = blockIdx.x, tn;
     if (tid == 0) next_tile = (long long)atomicAdd(&S.ctrl[kCtrlNextTile], 1ull) + gridDim.x;
     if (ti < n_tiles) {
@@ -1175,7 +1217,7 @@ __device__ __forceinline__ void score_body_pipe(const DevProblem &P, const Bucke
         for (int k = 0; k < 2; ++k)
             if (pending & (1u << k)) mbar_wait(bar0 + 8 * k, (phases >> k) & 1u);
     }
-    finish_call(S);
+    finish_call(S, out, true);
 }
 
 #define LLAMA_SCORE_KERNEL(name, MODE, IPT, BODY)                                                \
@@ -1325,8 +1367,11 @@ __global__ void __launch_bounds__(256, 4) k_counts(DevProblem P, BucketScratch S
     // the bucket entries and starts and the critical paths are visible after this
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const int H = P.n_hw;
-    const int64_t n_pos = P.n_big_ops < P.n_ops ? (int64_t)S.op_start[P.op_order[P.n_big_ops]]
-                                                 : (int64_t)S.ctrl[kCtrlPositions];
+    // after a bucketing barrier gave up, the bucket starts and entries are not
+    // this call's: nothing is read
+    const int64_t n_pos = call_timed_out(S)             ? 0
+                          : P.n_big_ops < P.n_ops ? (int64_t)S.op_start[P.op_order[P.n_big_ops]]
+                                                  : (int64_t)S.ctrl[kCtrlPositions];
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n_pos;
          p += (int64_t)gridDim.x * blockDim.x) {
         const int32_t g = S.gop[S.b_inv[p]];
@@ -1389,7 +1434,7 @@ __global__ void __launch_bounds__(256) k_stair(DevProblem P, int64_t n_inv, cons
             out[i] = dsn;
         }
     }
-    finish_call(S);
+    finish_call(S, out, false);
 }
 
 // Inclusive minimum scan of a[0..n) in shared memory by the whole block, from
@@ -1480,16 +1525,46 @@ int schedule_launches(const ContextView &v, const BucketScratch &S) {
     return S.b_cnt && v.need_counts ? 3 : 2;
 }
 
-cudaError_t enqueue_schedule(const ContextView &v, const BucketScratch &S, int64_t n_inv,
+// After a failed launch that followed a successful one: the kernels already
+// enqueued may have counted invocations, so the per-op counters and the
+// control and status words are cleared on the same stream (memsets, nothing
+// allocated) and the scratch is ready for the next call.
+static cudaError_t clear_scratch_after_error(const ContextView &v, const BucketScratch &S, cudaStream_t s,
+                                             cudaError_t err) {
+    cudaGetLastError();  // the launch error itself is not sticky
+    cudaMemsetAsync(S.cnt, 0, sizeof(int32_t) * kCntStride * (size_t)v.n_ops, s);
+    cudaMemsetAsync(S.ctrl, 0, sizeof(unsigned long long) * (kCtrlWords + kStatusWords), s);
+    return err;
+}
+
+static cudaError_t enqueue_schedule_impl(const ContextView &v, const BucketScratch &S, int64_t n_inv,
+                                         const int32_t *dag, const int32_t *op_local, const int64_t *start,
+                                         int64_t now, llama_decision *out, cudaStream_t s,
+                                         const cudaEvent_t *trace, bool &launched);
+
+cudaError_t enqueue_schedule(const ContextView &v, const BucketScratch &S0, int64_t n_inv,
                              const int32_t *dag, const int32_t *op_local, const int64_t *start,
                              int64_t now, llama_decision *out, cudaStream_t s,
                              const cudaEvent_t *trace) {
+    BucketScratch S = S0;
+    S.n_inv = n_inv;
+    bool launched = false;
+    const cudaError_t e = enqueue_schedule_impl(v, S, n_inv, dag, op_local, start, now, out, s, trace, launched);
+    if (e != cudaSuccess && launched) return clear_scratch_after_error(v, S, s, e);
+    return e;
+}
+
+static cudaError_t enqueue_schedule_impl(const ContextView &v, const BucketScratch &S, int64_t n_inv,
+                                         const int32_t *dag, const int32_t *op_local, const int64_t *start,
+                                         int64_t now, llama_decision *out, cudaStream_t s,
+                                         const cudaEvent_t *trace, bool &launched) {
     auto mark = [&](int k) { if (trace) cudaEventRecord(trace[k], s); };
     mark(0);
     cudaError_t e = cudaSuccess;
     if (v.method == LLAMA_METHOD_STAIRCASE) {
         k_critical_paths<<<std::max(1, (v.n_dags + 7) / 8), 256, 0, s>>>(v.P, v.topo, v.lvl_off, v.dag_lvl);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        launched = true;
         mark(1);
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3((unsigned)((n_inv + 255) / 256));
@@ -1533,6 +1608,7 @@ cudaError_t enqueue_schedule(const ContextView &v, const BucketScratch &S, int64
                         &topo, &lvl_off, &dag_lvl, &min_vpl, &ipt, &ncp};
         e = cudaLaunchKernelExC(&cfg, (const void *)k_bucket, args);
         if (e != cudaSuccess) return e;
+        launched = true;
     }
     mark(1);
     // the count pass, where some op's distinct latencies are not staged by the
@@ -1824,13 +1900,25 @@ __global__ void k_encode_dec(DevProblem P, int4 *dec, int4 *dfast) {
 }
 
 // Eq. 2 over the decided invocations (valid ones): their latency times their
-// requested resources, summed per backend.
+// requested resources, summed per backend.  A backend's sum saturates at
+// cap(h) = INT32_MAX * R_total(h): every sum at or above it floors to a
+// queueing time of at least INT32_MAX, which k_queue_finish clamps to
+// INT32_MAX, so saturating keeps the result exact while no partial sum can
+// wrap (each term is below 2^47, every saturated value below 2^62, so a sum
+// of two never exceeds 2^63).
+__device__ __forceinline__ unsigned long long queue_cap(const DevProblem &P, int h) {
+    return (unsigned long long)INT32_MAX * (unsigned long long)(uint32_t)P.res_total[h];
+}
+
 __global__ void k_queue_sum(DevProblem P, int64_t n, const int32_t *dag, const int32_t *op_local,
                             const llama_decision *dec, unsigned long long *sums) {
     const int H = P.n_hw;
-    unsigned long long loc[LLAMA_MAX_HW];
+    unsigned long long loc[LLAMA_MAX_HW], cap[LLAMA_MAX_HW];
 #pragma unroll
-    for (int h = 0; h < LLAMA_MAX_HW; ++h) loc[h] = 0;
+    for (int h = 0; h < LLAMA_MAX_HW; ++h) {
+        loc[h] = 0;
+        cap[h] = h < H ? queue_cap(P, h) : 0;
+    }
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const llama_decision d = dec[i];
         if (d.cfg < 0 || (d.flags & LLAMA_FLAG_INVALID)) continue;
@@ -1843,13 +1931,20 @@ __global__ void k_queue_sum(DevProblem P, int64_t n, const int32_t *dag, const i
         const unsigned long long w = (unsigned long long)(uint32_t)d.lat * (unsigned long long)(uint32_t)P.res[g];
 #pragma unroll
         for (int h = 0; h < LLAMA_MAX_HW; ++h)
-            if (h == lam) loc[h] += w;
+            if (h == lam) loc[h] = min(loc[h] + w, cap[h]);
     }
 #pragma unroll
     for (int h = 0; h < LLAMA_MAX_HW; ++h) {
         unsigned long long v = loc[h];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if ((threadIdx.x & 31) == 0 && h < H && v) atomicAdd(sums + h, v);
+        for (int o = 16; o > 0; o >>= 1) v = min(v + __shfl_xor_sync(0xffffffffu, v, o), cap[h]);
+        if ((threadIdx.x & 31) == 0 && h < H && v) {
+            // saturating atomic add: both operands are at most cap(h) < 2^62
+            unsigned long long old = sums[h], seen;
+            do {
+                seen = old;
+                old = atomicCAS(sums + h, seen, min(seen + v, cap[h]));
+            } while (old != seen);
+        }
     }
 }
 

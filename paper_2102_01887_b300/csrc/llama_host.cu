@@ -122,6 +122,7 @@ struct llama_ctx {
     int32_t max_ncfg = 0;  // configurations of the largest op
     int32_t n_big_ops = 0;  // ops with more padded entries than dlat_cap
     int32_t count_pass = LLAMA_COUNT_PASS_AUTO;
+    int32_t wait_tries = kMaxWaitTries;  // polls of a bucketing grid barrier (llama_set_wait_limit)
     cudaEvent_t trace[LLAMA_TRACE_EVENTS] = {};
     bool tracing = false;
 
@@ -237,6 +238,7 @@ DevProblem make_problem(const llama_ctx *c) {
     P.q = c->q_dev.as<int64_t>();
     P.alpha_num = c->opts.alpha_num;
     P.alpha_den = c->opts.alpha_den;
+    P.wait_tries = c->wait_tries;
     return P;
 }
 
@@ -595,6 +597,8 @@ int context_view(llama_ctx *c, ContextView *v) {
 }
 
 int context_fail(llama_ctx *c, int code, const char *msg) { return c->fail(code, msg); }
+
+void context_set_launches(llama_ctx *c, int launches) { c->last_launches = launches; }
 
 }  // namespace llama
 
@@ -1025,6 +1029,18 @@ extern "C" int llama_set_count_pass(llama_ctx *c, int32_t mode) {
     return LLAMA_OK;
 }
 
+extern "C" int llama_set_wait_limit(llama_ctx *c, int32_t tries) {
+    if (!c) return LLAMA_EINVAL;
+    if (tries < 0 || tries > kMaxWaitTries)
+        return c->fail(LLAMA_EINVAL, "set_wait_limit: tries must be in 0..LLAMA_WAIT_LIMIT_DEFAULT");
+    if (tries != c->wait_tries) {
+        DeviceGuard g(c->opts.device);
+        c->drop_graph();  // the limit is a kernel argument of the captured launches
+        c->wait_tries = tries;
+    }
+    return LLAMA_OK;
+}
+
 extern "C" int llama_set_method(llama_ctx *c, int32_t method) {
     if (!c) return LLAMA_EINVAL;
     if (method != LLAMA_METHOD_SCAN && method != LLAMA_METHOD_STAIRCASE)
@@ -1275,7 +1291,8 @@ extern "C" int llama_schedule(llama_ctx *c, int64_t n_inv, const int32_t *dag, c
                                sizeof(unsigned long long) * kStatusWords, cudaMemcpyDeviceToHost, s));
     LL_CUDA(c, cudaStreamSynchronize(s));
     if (c->h_ctrl[1])
-        return c->fail(LLAMA_ETIMEOUT, "schedule: a bounded device wait gave up (table staging)");
+        return c->fail(LLAMA_ETIMEOUT, "schedule: a bounded device wait gave up (bucketing barrier or table "
+                                       "staging); valid invocations are flagged LLAMA_FLAG_TIMEOUT in out");
     if (c->h_ctrl[0])
         return c->fail(LLAMA_EINVAL, "schedule: some invocations are invalid (flagged in out)");
     return LLAMA_OK;

@@ -37,7 +37,7 @@ constexpr uint16_t kLatRankPad = 0xBFFF;   // at pads: above any count of distin
 constexpr int kScoreThreads = 256;
 constexpr int kScoreThreadsLog2 = 8;
 constexpr int kMaxChunk = 4096;        // table entries staged at a time by the scoring kernel
-constexpr int kMaxWaitTries = 1 << 20; // bounded mbarrier waits
+constexpr int kMaxWaitTries = LLAMA_WAIT_LIMIT_DEFAULT;  // bounded waits (mbarrier, grid barrier)
 constexpr int kKeep = 4;               // invocations a counting thread keeps in registers
 constexpr int kKeepOps = 2;            // ops the layout keeps in registers per thread
 constexpr int kMaxDlatSmem = 4096;     // distinct latencies staged per op (else searched in L2)
@@ -137,6 +137,9 @@ struct DevProblem {
     uint64_t *cp_magic;  // floor((2^64-1) / cp[v]), for exact division by cp[v]
     const int64_t *q;  // [n_hw] queueing time per backend (device: set by the host or by Eq. 2)
     int64_t alpha_num, alpha_den;
+    // polls of a grid barrier of k_bucket before it gives up (kMaxWaitTries
+    // unless a caller lowers it to exercise the give-up path)
+    int32_t wait_tries;
 };
 
 struct BucketScratch {
@@ -159,6 +162,7 @@ struct BucketScratch {
     uint16_t *b_cnt;          // [n_inv*n_hw] or null: for the invocation at each bucket position
                               //             whose op's distinct latencies are not staged in shared
                               //             memory, the count of them below its slack per backend
+    int64_t n_inv;            // invocations of the call (set by enqueue_schedule)
 };
 
 // floor(n / d) for n < 2^62 and d >= 1, given m = floor((2^64 - 1) / d): the high
@@ -199,6 +203,7 @@ struct ContextView {
 };
 int context_view(llama_ctx *c, ContextView *v);  // LLAMA_OK or the readiness error
 int context_fail(llama_ctx *c, int code, const char *msg);
+void context_set_launches(llama_ctx *c, int launches);  // what llama_last_launch_count reports
 
 // Kernels (defined in kernels.cu).
 __global__ void k_critical_path(DevProblem P, const int32_t *topo, const int32_t *lvl_off,
@@ -229,9 +234,12 @@ const void *score_kernel(int mode, int ipt, int stages);
 
 // Scoring tiles a call may lay out (each op: full tiles plus one tail).
 int64_t max_tiles(int64_t n_inv, int32_t n_ops);
-// Enqueue the whole scheduling call on stream s: counters cleared, then
-// k_bucket, k_score.  trace (nullable) = LLAMA_TRACE_EVENTS events recorded at
-// the phase boundaries.
+// Enqueue the whole scheduling call on stream s: k_bucket, the count pass
+// when it runs, k_score (the previous call left the counters and control
+// words cleared).  trace (nullable) = LLAMA_TRACE_EVENTS events recorded at
+// the phase boundaries.  If a launch fails after the first one went in, the
+// counters and control words are cleared by memsets on s (nothing allocated)
+// so that the scratch is usable by the next call, and the error is returned.
 cudaError_t enqueue_schedule(const ContextView &v, const BucketScratch &S, int64_t n_inv,
                              const int32_t *dag, const int32_t *op_local, const int64_t *start,
                              int64_t now, llama_decision *out, cudaStream_t s,

@@ -14,14 +14,21 @@
 // the device earlier by llama_set_profiles.
 //
 // Sharing.  Every call on a device uses the same array, and the array keeps
-// the contents of the last call; the counters that must start at zero are
-// cleared by each call on its own stream.  Calls that overlap on the GPU
-// (two streams, or two contexts on one device, in flight at once) race on
-// the array and give wrong results: serialise them.
+// the contents of the last call.  The counters and control words that must be
+// zero when a call starts are zero: the array starts zeroed, the last kernel
+// of every completed call clears them, and a call whose later launch fails
+// clears them with memsets on its stream (enqueue_schedule) before returning
+// ECUDA.  Calls that overlap on the GPU (two streams, or two contexts on one
+// device, in flight at once) race on the array and give wrong results:
+// serialise them.  The status of the last completed call (invalid
+// invocations, a bounded wait that gave up) stays in the array's status
+// words; llama_static_status reads it.
 //
 // Set-up.  The device address of the array is looked up once per device with
 // cudaGetSymbolAddress, by the first call on that device, with that device
-// current.  Make that first call before any stream capture.
+// current.  Make that first call before any stream capture.  The address is
+// cached for the process: after cudaDeviceReset it would be stale, so the
+// entry point must not be used again after a reset.
 #include <mutex>
 #include <string>
 
@@ -128,10 +135,33 @@ extern "C" int llama_schedule_static(llama_ctx *c, int64_t n_inv, const int32_t 
     S.rbase = reinterpret_cast<int64_t *>(base + kRbaseOff);
     S.tiles = reinterpret_cast<int4 *>(base + kTilesOff);
 
-    // the counters and control words are zero: the array starts zeroed and
-    // every completed call leaves them cleared
+    // the counters and control words are zero: the array starts zeroed, and
+    // every completed call, or a failed enqueue, leaves them cleared
     e = enqueue_schedule(v, S, n_inv, dag, op_local, start_us, now_us, out,
                          static_cast<cudaStream_t>(stream), nullptr);
     if (e != cudaSuccess) return cuda_error(c, e, "enqueue");
+    context_set_launches(c, schedule_launches(v, S));
+    return LLAMA_OK;
+}
+
+extern "C" int llama_static_status(llama_ctx *c, void *stream, int64_t *invalid, int32_t *timeout) {
+    if (!c) return LLAMA_EINVAL;
+    ContextView v;
+    const int rc = context_view(c, &v);
+    if (rc) return rc;
+    const int device = v.device;
+    if (device < 0 || device >= kMaxDevices)
+        return context_fail(c, LLAMA_EINVAL, "static_status: device ordinal above 63");
+    CurrentDevice guard(device);
+    unsigned char *base = nullptr;
+    cudaError_t e = scratch_address(device, reinterpret_cast<void **>(&base));
+    if (e != cudaSuccess) return cuda_error(c, e, "cudaGetSymbolAddress");
+    unsigned long long st[kStatusWords] = {0, 0};
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    e = cudaMemcpyAsync(st, base + kCtrlOff + 8 * (size_t)kCtrlWords, sizeof(st), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_error(c, e, "status copy");
+    if (invalid) *invalid = (int64_t)st[0];
+    if (timeout) *timeout = st[1] ? 1 : 0;
     return LLAMA_OK;
 }

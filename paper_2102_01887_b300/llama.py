@@ -21,7 +21,8 @@ LIB_PATH = os.path.join(_HERE, "libllama.so")
 OK, EINVAL, ENOMEM, ECUDA, ENOTREADY, ETIMEOUT = 0, -1, -2, -3, -4, -5
 MODE_COST_FIRST, MODE_ALPHA = 0, 1
 METHOD_SCAN, METHOD_STAIRCASE = 0, 1
-FLAG_FEASIBLE, FLAG_INVALID = 1, 2
+FLAG_FEASIBLE, FLAG_INVALID, FLAG_TIMEOUT = 1, 2, 4
+WAIT_LIMIT_DEFAULT = 1 << 20
 MAX_HW, MAX_CFG = 8, 8192
 
 DECISION_DTYPE = np.dtype([("cfg", "<i4"), ("lat", "<i4"), ("cost", "<i8"),
@@ -40,7 +41,8 @@ EXPORTS = ("llama_create", "llama_destroy", "llama_set_dags", "llama_set_profile
            "llama_ws_create", "llama_ws_destroy", "llama_schedule_ws_async", "llama_ws_status",
            "llama_server_create", "llama_server_destroy", "llama_server_submit", "llama_server_poll",
            "llama_server_drain", "llama_server_stats_get", "llama_queue_time", "llama_feedback",
-           "llama_get_profiles", "llama_backend_objectives", "llama_commit_order")
+           "llama_get_profiles", "llama_backend_objectives", "llama_commit_order",
+           "llama_static_status", "llama_set_wait_limit")
 TRACE_EVENTS = 3
 TRACE_PHASES = ("bucket", "score")
 
@@ -121,6 +123,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "llama_get_profiles": ([vp, vp, vp], ctypes.c_int),
             "llama_backend_objectives": ([vp, i64, vp, vp, vp, i64, vp, vp], ctypes.c_int),
             "llama_commit_order": ([vp, i64, vp, vp, vp, vp, vp, vp, vp], ctypes.c_int),
+            "llama_static_status": ([vp, vp, vp, vp], ctypes.c_int),
+            "llama_set_wait_limit": ([vp, i32], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -434,6 +438,23 @@ def llama_schedule_static(ctx, dag, op_local, start_us, now_us: int, out, stream
     _check(ctx, load().llama_schedule_static(ctx, int(dag.shape[0]), _ptr(dag), _ptr(op_local),
                                              _ptr(start_us), int(now_us), _ptr(out),
                                              ctypes.c_void_p(stream.cuda_stream)))
+
+
+def llama_static_status(ctx, stream=None) -> tuple[int, int]:
+    """(invalid invocations, timeout flag) of the last completed llama_schedule_static
+    call on the context's device, read on `stream` (default: torch's current stream)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    inv, tmo = ctypes.c_int64(), ctypes.c_int32()
+    _check(ctx, load().llama_static_status(ctx, ctypes.c_void_p(stream.cuda_stream), ctypes.byref(inv),
+                                           ctypes.byref(tmo)))
+    return inv.value, tmo.value
+
+
+def llama_set_wait_limit(ctx, tries: int) -> None:
+    """Polls of a bucketing grid barrier before it gives up (WAIT_LIMIT_DEFAULT; 0 gives up at once)."""
+    _check(ctx, load().llama_set_wait_limit(ctx, int(tries)))
 
 
 def llama_critical_path(ctx, n_ops: int) -> np.ndarray:

@@ -136,3 +136,39 @@ def test_affinity_and_commit_order(L, method):
     exp_order, exp_aff = oracle.commit_order(p, sub, d, exp_obj)
     assert np.array_equal(got_aff, exp_aff)
     assert np.array_equal(got_order, exp_order)
+
+
+def test_queue_time_saturates_exactly_at_extreme_sums(L):
+    """Eq. 2 (Section 4.3) with latencies near 2^31 and resources of 65,535: the
+    exact per-backend sum exceeds 2^64 after about 1.3e5 such decisions.  The
+    oracle sums exact integers and clamps the floored quotient to INT32_MAX;
+    the device must give the same clamp (not a wrapped sum), and stay exact on
+    a backend whose sum is small."""
+    import torch
+    p, inv = W.medium()
+    p = copy.deepcopy(p)
+    p.res = np.full(p.n_cfg, 65535, np.int32)
+    p.res_total = np.asarray([1, 2**31 - 1, 1000], np.int32)
+    n = 300_000
+    idx = np.arange(n) % inv.n
+    q_inv = inv.subset(idx)
+    gop = p.dag_op_off[q_inv.dag] + q_inv.op_local
+    hw = p.hw_off.reshape(p.n_ops, p.n_hw + 1)
+    # backend of each decision: 0 and 1 alternate with extreme latencies, the
+    # last 1,000 go to backend 2 with small ones
+    lam = np.where(np.arange(n) % 2 == 0, 0, 1)
+    lam[-1000:] = 2
+    dec = np.zeros(n, dtype=L.DECISION_DTYPE)
+    seg_start, seg_end = hw[gop, lam], hw[gop, lam + 1]
+    has = seg_end > seg_start
+    dec["cfg"] = np.where(has, seg_start, 0)
+    dec["lat"] = np.where(lam == 2, 1000, 2**31 - 2)
+    dec["flags"] = L.FLAG_FEASIBLE
+    dec["cfg"][~has] = -1  # a backend with no configuration of that op: not queued
+    with L.Scheduler(p) as s:
+        q = torch.zeros(p.n_hw, dtype=torch.int64, device="cuda")
+        L.llama_queue_time(s.ctx, dev(q_inv.dag), dev(q_inv.op_local), dev(dec.view(np.uint8)), q, apply=False)
+        got = q.cpu().numpy()
+    exp = oracle.queue_time(p, q_inv, dec)
+    assert exp[0] == exp[1] == 2**31 - 1 and 0 < exp[2] < 2**31 - 1
+    assert np.array_equal(got, exp), (got, exp)

@@ -5,6 +5,7 @@ import pytest
 
 from oracle import mlp as M
 from paper_2102_01887_b300 import workloads as W
+from tests import bf16_bounds as BB
 
 pytestmark = pytest.mark.gpu
 
@@ -65,7 +66,12 @@ def test_forward_matches_oracle(L, world):
         net.forward(xd, y)
         got = y.cpu().numpy()
     q = rounded(M.unpack(M.pack(p).astype(np.float32)))
-    ref = M.forward(q, bf16_round(M.pad_features(xs)))[0][:, :2]
+    y, sy, _, _ = BB.forward_errors(q, bf16_round(M.pad_features(xs)))
+    ref, tol = y[:, :2], BB.tol(sy)[:, :2]
+    # element by element, within the tolerance derived from BF16 rounding
+    # (tests/bf16_bounds.py: 8 sigma of the propagated rounding error)
+    bad = np.abs(got - ref) > tol
+    assert not bad.any(), (int(bad.sum()), float((np.abs(got - ref) / tol).max()))
     scale = np.abs(ref).max(axis=0) + 1e-3
     assert (np.abs(got - ref) / scale).max() < 0.03, (np.abs(got - ref) / scale).max()
 
@@ -85,13 +91,16 @@ def test_gradients_match_oracle(L, world):
         got = M.unpack(g.cpu().numpy().astype(np.float64))
         got_loss = float(loss.item())
     q = rounded(M.unpack(M.pack(p).astype(np.float32)))
-    ref_loss, ref = M.gradients(q, bf16_round(M.pad_features(xs)), ts.astype(np.float64), w_fan)
+    ref_loss, ref, tol = BB.gradient_errors(q, bf16_round(M.pad_features(xs)), ts.astype(np.float64), w_fan)
     assert got_loss == pytest.approx(ref_loss, rel=0.02)
     for name, _ in M.SHAPES:
-        a, b = got[name], ref[name]
+        a, b, e = got[name], ref[name], tol[name]
         if name in ("W4", "b4"):
-            a, b = a[:2], b[:2]
+            a, b, e = a[:2], b[:2], e[:2]
             assert not got[name][2:].any()  # outputs the loss never reads
+        # element by element, within the tolerance derived from BF16 rounding
+        bad = np.abs(a - b) > e + 1e-30
+        assert not bad.any(), (name, int(bad.sum()), float((np.abs(a - b) / (e + 1e-30)).max()))
         rel = np.linalg.norm(a - b) / (np.linalg.norm(b) + 1e-12)
         assert rel < 0.05, (name, rel)
 

@@ -12,6 +12,7 @@ import pytest
 
 import oracle
 from oracle import mlp as M
+from tests import bf16_bounds as BB
 from oracle import surrogate as OS
 from paper_2102_01887_b300 import workloads as W
 
@@ -99,6 +100,18 @@ def check_predictions(L, p, sub, cw, seed):
     l_or = p.lat_us[pg] * np.exp(np.clip(r, -20, 20))
     err = np.abs(np.log(lh / l_or))
     assert err.max() <= 0.05, err.max()
+    # element by element: the log factor within the tolerance derived from BF16
+    # rounding of the split first layer, h1 and h2 (tests/bf16_bounds.py), plus
+    # expf (a few float ulps) and the rounding of L e^r to whole microseconds
+    x_cfg = np.zeros((pinv.shape[0], M.IN))
+    x_cfg[:, :32] = cfg_np[pg_used, :32]
+    x_inv = np.zeros((pinv.shape[0], M.IN))
+    x_inv[:, 32:48] = inv_np[pinv, 32:48]
+    y0, tol = BB.split_forward_errors(q, x_cfg, x_inv)
+    assert np.allclose(y0, r)
+    bound = tol + 1e-6 + 0.5 / np.maximum(lh - 0.5, 0.5)
+    bad = err > bound
+    assert not bad.any(), (int(bad.sum()), float((err / bound).max()))
     # selection: the oracle's rule on the GPU's integer predictions
     lam = backend_of_cfg(p)
     spair = slack[pinv, lam[pg]]
