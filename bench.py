@@ -75,14 +75,21 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="medium", choices=["tiny", "medium", "batched", "batched_large"])
+    ap.add_argument("--workload", default="batched", choices=["tiny", "medium", "batched", "batched_large"],
+                    help="default: batched (256 DAGs of 5-60 ops, Zipf 96-8,192 configurations, 1,048,576 "
+                         "invocations), the largest single-GPU configuration")
     ap.add_argument("--mode", default="cost_first", choices=["cost_first", "alpha"])
     ap.add_argument("--rates", default="1e5,3e5,1e6", help="serving: Poisson arrival rates (invocations/s)")
     ap.add_argument("--seconds", type=float, default=1.5, help="serving: arrival window per rate")
     ap.add_argument("--method", default="scan", choices=["scan", "staircase", "surrogate", "serve"],
                     help="selection method: score every configuration, the staircase tables, or the "
                          "learned latency surrogate (trained first, untimed)")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample budget")
+    ap.add_argument("--cpu-seconds", type=float, default=8.0, help="CPU-baseline budget per leg (all cores, one core)")
+    ap.add_argument("--hbm-dags", type=int, default=192,
+                    help="DAGs of the HBM-streaming line (8,192 configurations per op, 64 invocations "
+                         "per DAG; 0: no such line)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the tiny-call latency, host-link and ALU-peak measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch kernels directly, no CUDA graph")
@@ -217,19 +224,72 @@ def measured_peaks():
         return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
 
 
-def cpu_baseline(p, inv, mode, budget_s: float, steps=None):
-    """The oracle as it stands, single-threaded, on the full workload (repeated)."""
+def host_cores() -> int:
+    return len(os.sched_getaffinity(0))
+
+
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_call(p, inv, mode, threads: int = 1, pool=None):
+    """One oracle scheduling call, as it stands; with threads > 1 the invocations
+    are split into that many contiguous shards scheduled at once (the C oracle
+    releases the GIL while it runs, so each thread has a core)."""
     import oracle
     m = oracle.MODE_ALPHA if mode == "alpha" else oracle.MODE_COST_FIRST
+    if threads <= 1:
+        return oracle.schedule(p, inv, mode=m, alpha=(3, 2))
+    cuts = np.linspace(0, inv.n, threads + 1).astype(np.int64)
+    futs = [pool.submit(oracle.schedule, p, inv.subset(np.arange(cuts[k], cuts[k + 1])), m, (3, 2))
+            for k in range(threads)]
+    return [f.result() for f in futs]
+
+
+def cpu_baseline(p, inv, mode, budget_s: float, steps=None, threads: int = 1):
+    """Times of repeated oracle calls on inv (steps of them, or as many as fit budget_s)."""
+    from concurrent.futures import ThreadPoolExecutor
     times = []
-    t_end = time.perf_counter() + budget_s
-    while (steps is None and (not times or time.perf_counter() < t_end)) or (steps is not None and len(times) < steps):
-        t0 = time.perf_counter()
-        oracle.schedule(p, inv, mode=m, alpha=(3, 2))
-        times.append(time.perf_counter() - t0)
-        if steps is None and len(times) >= 200:
-            break
+    with ThreadPoolExecutor(max_workers=max(1, threads)) as pool:
+        t_end = time.perf_counter() + budget_s
+        while (steps is None and (not times or time.perf_counter() < t_end)) or \
+                (steps is not None and len(times) < steps):
+            t0 = time.perf_counter()
+            oracle_call(p, inv, mode, threads, pool)
+            times.append(time.perf_counter() - t0)
+            if steps is None and len(times) >= 200:
+                break
     return times
+
+
+def cpu_sample(inv, name: str, cores: int):
+    """A bounded sample of the workload for the timed oracle: every k-th invocation."""
+    per_core = {"tiny": 64, "medium": 16_384, "batched": 8_192, "batched_large": 512}.get(name, 8192)
+    k = max(1, inv.n // (per_core * max(1, cores)))
+    return inv.subset(np.arange(0, inv.n, k)), k
+
+
+def cpu_baselines(p, inv, name, mode, budget_s):
+    """The oracle timed on the host: on every core (the reported baseline), and on one."""
+    cores = host_cores()
+    sub_all, k_all = cpu_sample(inv, name, cores)
+    t_all = cpu_baseline(p, sub_all, mode, budget_s, threads=cores)
+    sub_one, k_one = cpu_sample(inv, name, 1)
+    t_one = cpu_baseline(p, sub_one, mode, budget_s)
+    every = lambda k: "all" if k == 1 else f"every {k}th"
+    return {"value": sub_all.n * len(t_all) / sum(t_all), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{every(k_all)} invocation of {name} ({sub_all.n} invocations) per call, split over "
+                      f"{cores} threads (one shard each), {len(t_all)} calls, {sum(t_all):.1f} s",
+            "cpu_model": cpu_model(),
+            "single_core": {"value": sub_one.n * len(t_one) / sum(t_one), "unit": UNIT, "cores": 1,
+                            "sample": f"{every(k_one)} invocation ({sub_one.n} invocations) per call, "
+                                      f"{len(t_one)} calls, {sum(t_one):.1f} s"}}
 
 
 def run_reference(args):
@@ -237,21 +297,199 @@ def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return
-    p, inv = make_workload(args.workload, 0, args.n_dags, args.n_inv)
+    p, full = make_workload(args.workload, 0, args.n_dags, args.n_inv)
+    cores = host_cores()
+    # each step schedules a bounded sample of the workload (every k-th invocation)
+    inv, k = cpu_sample(full, args.workload, 4 * cores)
     scores = scores_of(p, inv)
-    cpu_baseline(p, inv, args.mode, 0, steps=max(1, args.warmup))
-    times = cpu_baseline(p, inv, args.mode, 0, steps=args.steps)
+    cpu_baseline(p, inv, args.mode, 0, steps=max(1, args.warmup), threads=cores)
+    times = cpu_baseline(p, inv, args.mode, 0, steps=args.steps, threads=cores)
     t = sum(times)
     value = inv.n * args.steps / t
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-            "data": "synthetic", "config": workload_config(args.workload, p, inv, args.mode, scores),
+            "data": "synthetic", "config": workload_config(args.workload, p, full, args.mode, scores_of(p, full)),
             "configs_scored_per_s": scores * args.steps / t,
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"full {args.workload} workload ({inv.n} invocations) per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "cpu_model": cpu_model(),
+                             "sample": f"{'all' if k == 1 else f'every {k}th'} invocation of {args.workload} "
+                                       f"({inv.n} of {full.n}) per step, split over {cores} threads"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def oracle_decisions(p, inv, mode):
+    """The oracle's decisions for every invocation of inv (shards on all host cores)."""
+    from concurrent.futures import ThreadPoolExecutor
+    cores = host_cores()
+    with ThreadPoolExecutor(max_workers=cores) as pool:
+        parts = oracle_call(p, inv, mode, cores, pool) if inv.n >= 4 * cores else [oracle_call(p, inv, mode)]
+    return np.concatenate([d for d, _ in parts])
+
+
+def same_decisions(got, exp) -> bool:
+    return bool(all((got[k] == exp[k]).all() for k in ("cfg", "lat", "cost", "slack", "flags")))
+
+
+def traced_steps(L, ctx, step, stream, flush, steps: int):
+    """Per-phase device times of `steps` calls with trace events (direct launches)."""
+    import torch
+    traces = [[torch.cuda.Event(enable_timing=True) for _ in range(L.TRACE_EVENTS)] for _ in range(steps)]
+    for t in traces:
+        for e in t:
+            e.record(stream)
+    with torch.cuda.stream(stream):
+        for k in range(steps):
+            flush.fill_(k & 0xFF)
+            L.llama_set_trace_events(ctx, traces[k])
+            step()
+        L.llama_set_trace_events(ctx, [])
+    torch.cuda.synchronize()
+    return np.asarray([[t[j].elapsed_time(t[j + 1]) for j in range(len(L.TRACE_PHASES))] for t in traces])
+
+
+def hbm_streaming_line(args, peaks, peak_src, dev, flush):
+    """The scan where tables exceed L2 and each op has few invocations (the
+    batched workload's 8,192-configuration variant): the scoring pass (count
+    pass and scoring kernel) against the HBM roofline."""
+    import torch
+
+    from paper_2102_01887_b300 import llama as L
+    from paper_2102_01887_b300 import workloads as W
+    from paper_2102_01887_b300.autotune import autotune
+    # the variant's ratio of invocations to DAGs (32,768 for 512: about two per op)
+    p, inv = W.batched_large(n_dags=args.hbm_dags, n_inv=64 * args.hbm_dags)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sched = L.Scheduler(p, use_graph=True, device=dev.index or 0)
+    torch.cuda.synchronize()
+    set_ms = 1e3 * (time.perf_counter() - t0)
+    ctx = sched.ctx
+    dag = torch.from_numpy(inv.dag).to(dev)
+    opl = torch.from_numpy(inv.op_local).to(dev)
+    st = torch.from_numpy(inv.start_us).to(dev)
+    out = torch.zeros(inv.n * 24, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    L.llama_reserve(ctx, inv.n)
+    tuning = autotune(ctx, dag, opl, st, inv.now_us, out, stream, flush, chunks=(0, 8256))
+
+    def step():
+        L.llama_schedule_async(ctx, dag, opl, st, inv.now_us, out, stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            flush.fill_(1)
+            step()
+    n_steps = 20
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(n_steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(n_steps)]
+    with torch.cuda.stream(stream):
+        for k in range(n_steps):
+            flush.fill_(k & 0xFF)
+            starts[k].record(stream)
+            step()
+            ends[k].record(stream)
+    torch.cuda.synchronize()
+    step_ms = np.asarray([a.elapsed_time(b) for a, b in zip(starts, ends)])
+    got = out.cpu().numpy().view(L.DECISION_DTYPE).copy()
+    phase_ms = traced_steps(L, ctx, step, stream, flush, n_steps)
+    per_call = L.llama_last_launch_count(ctx)
+    sched.close()
+    parity = same_decisions(got, oracle_decisions(p, inv, "cost_first"))
+    npad = padded_sizes(p)
+    gop = p.dag_op_off[inv.dag] + inv.op_local
+    touched = np.unique(gop)
+    scores = scores_of(p, inv)
+    score_ms = float(phase_ms[:, -1].mean())
+    hbm = float(peaks["hbm_gbs"])
+    algo = 4 * int(npad[touched].sum()) + 40 * inv.n
+    ach = algo / (score_ms / 1e3) / 1e9
+    per12 = SCAN_BYTES_PER_SCORE * scores / (score_ms / 1e3) / 1e9
+    return {
+        "workload": f"batched_large: {p.n_dags} DAGs of 5-60 ops, {p.n_ops} ops x 8,192 configurations, "
+                    f"{inv.n} invocations",
+        "invocations_per_s": inv.n / (float(step_ms.mean()) / 1e3), "ms_per_step": float(step_ms.mean()),
+        "encoded_table_bytes": int(4 * npad.sum()), "caller_table_bytes": int(p.table_bytes()),
+        "scoring_pass": {
+            "bound": "hbm", "kernel": "k_counts + k_score" if per_call == 3 else "k_score",
+            "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+            "peak_source": f"{peak_src} HBM copy bandwidth", "algorithmic_bytes": algo, "ms": score_ms,
+            "bytes_note": "4 B per padded table entry (16-bit latency rank + 16-bit objective rank) of each "
+                          "op with invocations, read once, plus 40 B per invocation"},
+        "scan_12B_per_config": {"gbs": per12, "frac": per12 / hbm,
+                                "note": "12 B (int32 latency + int64 cost) per scored configuration over the "
+                                        "same time: the work the rank encoding replaces; above the HBM peak "
+                                        "because each configuration is read as 4 B of ranks"},
+        "set_profiles_ms": set_ms,
+        "set_profiles_note": "llama_create + llama_set_dags + llama_set_profiles, host wall time: table copies "
+                             "and the on-device encoding (ranks, distinct latencies, probe lines, decode tables)",
+        "schedule": tuning["best"], "gpu_launches_per_call": per_call, "parity_vs_oracle": parity,
+        "l2": "flushed before every timed step (256 MiB write)",
+    }
+
+
+def tiny_call_latency(dev, n_calls: int = 10_000):
+    """Launch-bound latency of the tiny workload: device time of each
+    graph-launched call (events around it) and the host round trip of the
+    blocking call with host buffers."""
+    import torch
+
+    from paper_2102_01887_b300 import llama as L
+    from paper_2102_01887_b300 import workloads as W
+    p, inv = W.tiny()
+    with L.Scheduler(p, use_graph=True, device=dev.index or 0) as s:
+        dag = torch.from_numpy(inv.dag).to(dev)
+        opl = torch.from_numpy(inv.op_local).to(dev)
+        st = torch.from_numpy(inv.start_us).to(dev)
+        out = torch.zeros(inv.n * 24, dtype=torch.uint8, device=dev)
+        stream = torch.cuda.Stream(device=dev)
+        for _ in range(100):
+            L.llama_schedule_async(s.ctx, dag, opl, st, inv.now_us, out, stream)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_calls)]
+        for a, b in ev:
+            a.record(stream)
+            L.llama_schedule_async(s.ctx, dag, opl, st, inv.now_us, out, stream)
+            b.record(stream)
+        stream.synchronize()
+        dev_us = np.asarray([1e3 * a.elapsed_time(b) for a, b in ev])
+        h_out = np.zeros(inv.n, L.DECISION_DTYPE)
+        wall = []
+        for _ in range(n_calls):
+            t0 = time.perf_counter()
+            L.llama_schedule(s.ctx, inv.dag, inv.op_local, inv.start_us, inv.now_us, h_out)
+            wall.append(1e6 * (time.perf_counter() - t0))
+    return {"workload": "tiny: 1 DAG of 4 ops, 24 configurations each, 64 invocations", "calls": n_calls,
+            "device_us": {"p50": float(np.percentile(dev_us, 50)), "p99": float(np.percentile(dev_us, 99))},
+            "blocking_call_us": {"p50": float(np.percentile(wall, 50)), "p99": float(np.percentile(wall, 99))},
+            "note": "device: CUDA events around each graph launch on its stream (2.048 us timestamp steps); "
+                    "blocking: llama_schedule from pageable host arrays, copies and sync included"}
+
+
+def host_link(dev):
+    """Page-locked host <-> device copy rates at several sizes (copy engine,
+    CUDA events), the transfers an end-to-end call makes."""
+    import torch
+    rows = []
+    stream = torch.cuda.Stream(device=dev)
+    for size in (4 << 10, 64 << 10, 1 << 20, 16 << 20, 64 << 20):
+        h = torch.empty(size, dtype=torch.uint8).pin_memory()
+        d = torch.empty(size, dtype=torch.uint8, device=dev)
+        res = {}
+        for name, (dst, src) in (("h2d", (d, h)), ("d2h", (h, d))):
+            with torch.cuda.stream(stream):
+                for _ in range(3):
+                    dst.copy_(src, non_blocking=True)
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(21)]
+                e[0].record(stream)
+                for k in range(20):
+                    dst.copy_(src, non_blocking=True)
+                    e[k + 1].record(stream)
+            stream.synchronize()
+            us = sorted(1e3 * e[k].elapsed_time(e[k + 1]) for k in range(20))
+            res[name] = {"us_p50": us[10], "gbs": size / (us[10] * 1e3)}
+        rows.append({"bytes": size, **res})
+    return rows
 
 
 SURROGATE_FLOPS_PER_PAIR = 2 * 2 * 256 * 256 + 2 * 256  # layers 2 and 3, fused last layer
@@ -468,7 +706,11 @@ def main():
     p, inv = make_workload(args.workload, rank, args.n_dags, args.n_inv)
     mode = L.MODE_ALPHA if args.mode == "alpha" else L.MODE_COST_FIRST
     method = L.METHOD_STAIRCASE if args.method == "staircase" else L.METHOD_SCAN
+    torch.cuda.synchronize()
+    t_set = time.perf_counter()
     sched = L.Scheduler(p, mode=mode, alpha=(3, 2), device=local, use_graph=not args.no_graph, method=method)
+    torch.cuda.synchronize()
+    set_profiles_ms = 1e3 * (time.perf_counter() - t_set)
     ctx = sched.ctx
     scores = scores_of(p, inv)
 
@@ -625,16 +867,23 @@ def main():
                           "(latency rank + objective rank(s)), once, plus 40 B per invocation",
             "timed": "k_counts + k_score (trace events around both)" if count_pass else "k_score"}
     else:
-        peak_tops = sm_count * ALU_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+        nominal_tops = sm_count * ALU_LANES_PER_SM * sm_mhz * 1e6 / 1e12
         ops_per_score = ALU_OPS_PER_SCORE[args.mode]
+        # the measured ceiling of the scan's own instruction mix (llama_alu_peak)
+        mix_scores = L.llama_alu_peak(local, mode)
+        peak_tops = mix_scores * ops_per_score / 1e12
         achieved = ops_per_score * scores / (kms["score"] / 1e3) / 1e12
         rooflines["k_score"] = {
             "bound": "alu", "kernel": "k_score", "achieved": achieved, "peak": peak_tops,
             "unit": "T ALU-ops/s", "frac": achieved / peak_tops,
             "traffic": measured_traffic("k_score", args.workload, args.mode),
-            "peak_source": f"{sm_count} SMs x {ALU_LANES_PER_SM} integer ALU lanes x "
-                           f"{sm_mhz:.0f} MHz ({peak_src} max SM clock)",
-            "alu_ops_per_score": ops_per_score, "scores_per_s_ceiling": peak_tops * 1e12 / ops_per_score}
+            "peak_source": "measured: llama_alu_peak, the scan's per-two-configuration instruction mix "
+                           "(packed subtract, LOP3, 16-bit min" + (", PRMT" if args.mode == "alpha" else "")
+                           + ") from registers on every SM",
+            "peak_nominal": nominal_tops,
+            "peak_nominal_source": f"{sm_count} SMs x {ALU_LANES_PER_SM} integer ALU lanes x {sm_mhz:.0f} MHz",
+            "frac_of_nominal": achieved / nominal_tops,
+            "alu_ops_per_score": ops_per_score, "scores_per_s_ceiling": mix_scores}
     if args.method == "scan":
         b_bytes = inv.n * (16 + 8)
         b_ach = b_bytes / (kms["bucket"] / 1e3) / 1e9
@@ -649,17 +898,15 @@ def main():
     value = job_throughput(world, inv.n, args.steps, total_s)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        times = cpu_baseline(p, inv, args.mode, args.cpu_seconds)
-        cpu = {"value": inv.n * len(times) / sum(times), "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"full {args.workload} workload ({inv.n} invocations) x {len(times)} calls, "
-                         f"{sum(times):.1f} s single-threaded"}
-    exp = None
-    try:
-        import oracle
-        exp, _ = oracle.schedule(p, inv, mode=oracle.MODE_ALPHA if mode else 0, alpha=(3, 2))
-    except Exception:
-        pass
-    parity = None if exp is None else bool(all((got[k] == exp[k]).all() for k in ("cfg", "lat", "cost", "slack", "flags")))
+        cpu = cpu_baselines(p, inv, args.workload, args.mode, args.cpu_seconds)
+    # parity of the timed step's output against the oracle on every invocation
+    parity = same_decisions(got, oracle_decisions(p, inv, args.mode))
+    extras = {}
+    if world == 1 and args.method == "scan" and args.hbm_dags > 0 and args.mode == "cost_first":
+        extras["hbm_streaming"] = hbm_streaming_line(args, peaks, peak_src, dev, flush)
+    if world == 1 and not args.no_extras:
+        extras["tiny_call_latency"] = tiny_call_latency(dev)
+        extras["host_link"] = host_link(dev)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": float(step_ms.mean()), "higher_is_better": True,
@@ -685,7 +932,7 @@ def main():
                                                 "count_pass", "ms") if k in t}
                              for t in tuning["trials"]] if tuning and tuning["trials"] else None),
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-        "parity_vs_oracle": parity,
+        "parity_vs_oracle": parity, "set_profiles_ms": set_profiles_ms, **extras,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -370,6 +370,16 @@ int llama_set_trace_events(llama_ctx *ctx, void *const *events, int32_t n_events
 /* Kernel launches issued by the last scheduling call (for accounting). */
 int llama_last_launch_count(llama_ctx *ctx);
 
+/* Measured ceiling of the scan's inner loop (no counterpart in the paper; the
+ * denominator of the scoring kernel's ALU roofline): the rate at which the
+ * device issues the scan's instruction mix for two configurations -- one
+ * packed subtract of latency ranks, one LOP3, one per-half 16-bit minimum
+ * (LLAMA_MODE_COST_FIRST), plus one PRMT (LLAMA_MODE_ALPHA) -- on operands
+ * already in registers, on every SM.  *scores_per_s receives configurations
+ * per second (best of five timed launches after one warm-up).  Allocates a
+ * 16-byte buffer for the duration of the call.  Errors: EINVAL, ECUDA. */
+int llama_alu_peak(int32_t device, int32_t mode, double *scores_per_s);
+
 /* One-line description of the last error on ctx (never NULL). */
 const char *llama_last_error(llama_ctx *ctx);
 

@@ -42,7 +42,7 @@ EXPORTS = ("llama_create", "llama_destroy", "llama_set_dags", "llama_set_profile
            "llama_server_create", "llama_server_destroy", "llama_server_submit", "llama_server_poll",
            "llama_server_drain", "llama_server_stats_get", "llama_queue_time", "llama_feedback",
            "llama_get_profiles", "llama_backend_objectives", "llama_commit_order",
-           "llama_static_status", "llama_set_wait_limit")
+           "llama_static_status", "llama_set_wait_limit", "llama_alu_peak")
 TRACE_EVENTS = 3
 TRACE_PHASES = ("bucket", "score")
 
@@ -125,6 +125,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "llama_commit_order": ([vp, i64, vp, vp, vp, vp, vp, vp, vp], ctypes.c_int),
             "llama_static_status": ([vp, vp, vp, vp], ctypes.c_int),
             "llama_set_wait_limit": ([vp, i32], ctypes.c_int),
+            "llama_alu_peak": ([i32, i32, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -455,6 +456,15 @@ def llama_static_status(ctx, stream=None) -> tuple[int, int]:
 def llama_set_wait_limit(ctx, tries: int) -> None:
     """Polls of a bucketing grid barrier before it gives up (WAIT_LIMIT_DEFAULT; 0 gives up at once)."""
     _check(ctx, load().llama_set_wait_limit(ctx, int(tries)))
+
+
+def llama_alu_peak(device: int = 0, mode: int = MODE_COST_FIRST) -> float:
+    """Measured configurations per second of the scan's instruction mix on every SM."""
+    v = ctypes.c_double()
+    rc = load().llama_alu_peak(int(device), int(mode), ctypes.byref(v))
+    if rc != OK:
+        raise LlamaError(rc, "llama_alu_peak failed")
+    return v.value
 
 
 def llama_critical_path(ctx, n_ops: int) -> np.ndarray:
