@@ -1387,12 +1387,43 @@ __global__ void __launch_bounds__(256, 4) k_counts(DevProblem P, BucketScratch S
 template __global__ void k_counts<4>(DevProblem, BucketScratch, int32_t);
 template __global__ void k_counts<LLAMA_MAX_HW>(DevProblem, BucketScratch, int32_t);
 
+// The staircase decision of one valid invocation of global op g whose
+// remaining time before queueing is rbase = SLO - elapsed (Algorithm 1 with
+// the queueing times P.q, Eq. 1 through the staircase tables): the decision,
+// and its backend in *lam.
+__device__ llama_decision stair_decide(const DevProblem &P, int32_t g, int64_t rbase, int *lam_out) {
+    const int H = P.n_hw;
+    const int64_t ref = P.ref[g], cp = P.cp[g];
+    const uint64_t mg = P.cp_magic[g];
+    int32_t lo[LLAMA_MAX_HW];
+    counts_all_backends<LLAMA_MAX_HW, false>(P, g, ref, cp, mg, rbase, lo);
+    const uint16_t *sg = P.stair + P.stair_off[g];
+    const int64_t stride = P.cfg_off[g + 1] - P.cfg_off[g] + 1;
+    uint32_t key = 0xFFFFu;
+#pragma unroll
+    for (int h = 0; h < LLAMA_MAX_HW; ++h)
+        if (h < H) key = min(key, (uint32_t)__ldg(sg + (int64_t)h * stride + lo[h]));
+    const int64_t cb = P.cfg_off[g];
+    int4 dd;
+    if (P.mode == LLAMA_MODE_ALPHA) dd = P.dec[2 * cb + key];
+    else dd = key != 0xFFFFu ? P.dec[cb + key] : P.dfast[g];
+    const int lam = dd.x >> 16;
+    const int32_t slam = slack_of(ref, cp, mg, rbase - P.q[lam]);
+    llama_decision dsn;
+    dsn.cfg = dd.x & 0xFFFF;
+    dsn.lat = dd.y;
+    dsn.cost = (int64_t)(((uint64_t)(uint32_t)dd.w << 32) | (uint32_t)dd.z);
+    dsn.slack = slam;
+    dsn.flags = dd.y < slam ? LLAMA_FLAG_FEASIBLE : 0;
+    if (lam_out) *lam_out = lam;
+    return dsn;
+}
+
 __global__ void __launch_bounds__(256) k_stair(DevProblem P, int64_t n_inv, const int32_t *dag,
                                                const int32_t *op_local, const int64_t *start,
                                                int64_t now, BucketScratch S, llama_decision *out) {
     // the critical paths (previous kernel) are visible after this
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    const int H = P.n_hw;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n_inv) {
         const int32_t d = dag[i], o = op_local[i];
@@ -1407,31 +1438,7 @@ __global__ void __launch_bounds__(256) k_stair(DevProblem P, int64_t n_inv, cons
             out[i] = bad;
             atomicAdd(&S.ctrl[kCtrlInvalid], 1ull);
         } else {
-            const int32_t g = P.dag_op_off[d] + o;
-            const int64_t rbase = P.slo[d] - (now - st);
-            const int64_t ref = P.ref[g], cp = P.cp[g];
-            const uint64_t mg = P.cp_magic[g];
-            int32_t lo[LLAMA_MAX_HW];
-            counts_all_backends<LLAMA_MAX_HW, false>(P, g, ref, cp, mg, rbase, lo);
-            const uint16_t *sg = P.stair + P.stair_off[g];
-            const int64_t stride = P.cfg_off[g + 1] - P.cfg_off[g] + 1;
-            uint32_t key = 0xFFFFu;
-#pragma unroll
-            for (int h = 0; h < LLAMA_MAX_HW; ++h)
-                if (h < H) key = min(key, (uint32_t)__ldg(sg + (int64_t)h * stride + lo[h]));
-            const int64_t cb = P.cfg_off[g];
-            int4 dd;
-            if (P.mode == LLAMA_MODE_ALPHA) dd = P.dec[2 * cb + key];
-            else dd = key != 0xFFFFu ? P.dec[cb + key] : P.dfast[g];
-            const int lam = dd.x >> 16;
-            const int32_t slam = slack_of(ref, cp, mg, rbase - P.q[lam]);
-            llama_decision dsn;
-            dsn.cfg = dd.x & 0xFFFF;
-            dsn.lat = dd.y;
-            dsn.cost = (int64_t)(((uint64_t)(uint32_t)dd.w << 32) | (uint32_t)dd.z);
-            dsn.slack = slam;
-            dsn.flags = dd.y < slam ? LLAMA_FLAG_FEASIBLE : 0;
-            out[i] = dsn;
+            out[i] = stair_decide(P, P.dag_op_off[d] + o, P.slo[d] - (now - st), nullptr);
         }
     }
     finish_call(S, out, false);
@@ -1962,6 +1969,48 @@ __global__ void k_queue_finish(DevProblem P, const unsigned long long *sums, int
 // L < slack, else C/B + floor(alpha_num L R / (alpha_den B R_total)),
 // saturating at INT64_MAX; INT64_MAX for an empty segment or an invalid
 // invocation.  One warp per invocation.
+// The least Eq. 1 objective per backend among the configurations of global op
+// v, each against the slack of its own backend sl[lambda(x)], by the 32 lanes
+// of a warp (configurations strided over the lanes, then a warp minimum):
+// every lane returns the minima in best[] (INT64_MAX for an empty backend).
+__device__ void warp_backend_minima(const DevProblem &P, int32_t v, const int32_t (&sl)[LLAMA_MAX_HW],
+                                    int64_t (&best)[LLAMA_MAX_HW]) {
+    const int H = P.n_hw, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int h = 0; h < LLAMA_MAX_HW; ++h) best[h] = INT64_MAX;
+    const int64_t c0 = P.cfg_off[v];
+    const int n = (int)(P.cfg_off[v + 1] - c0);
+    const int32_t *hw = P.hw_off + (int64_t)v * (H + 1);
+    for (int x = lane; x < n; x += 32) {
+        const int lam = backend_of(hw, H, x);
+        const int64_t g = c0 + x;
+        int32_t s = sl[0];
+#pragma unroll
+        for (int h = 1; h < LLAMA_MAX_HW; ++h)
+            if (h == lam) s = sl[h];
+        const int64_t obj = P.lat[g] < s ? P.cost[g] : (int64_t)alpha_infeasible_objective(P, g, lam);
+#pragma unroll
+        for (int h = 0; h < LLAMA_MAX_HW; ++h)
+            if (h == lam) best[h] = min(best[h], obj);
+    }
+#pragma unroll
+    for (int h = 0; h < LLAMA_MAX_HW; ++h)
+        for (int k = 16; k > 0; k >>= 1)
+            best[h] = min(best[h], (int64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)best[h], k));
+}
+
+// Eq. 3's affinity of a decision on backend lam given the per-backend minima:
+// the least objective on the other backends over the least on lam, as doubles
+// (objectives stay below 2^53: exact conversions); +inf when its own is 0,
+// 1.0 when both are.
+__device__ __forceinline__ double affinity_of(const int64_t *obj_min, int H, int lam) {
+    int64_t other = INT64_MAX;
+    for (int h = 0; h < H; ++h)
+        if (h != lam) other = min(other, obj_min[h]);
+    const int64_t own = obj_min[lam];
+    return own == 0 ? (other == 0 ? 1.0 : INFINITY) : (double)other / (double)own;
+}
+
 __global__ void k_backend_obj(DevProblem P, int64_t n_inv, const int32_t *dag, const int32_t *op_local,
                               const int64_t *start, int64_t now, int64_t *obj_min) {
     const int H = P.n_hw, lane = threadIdx.x & 31;
@@ -1971,36 +2020,17 @@ __global__ void k_backend_obj(DevProblem P, int64_t n_inv, const int32_t *dag, c
 #pragma unroll
     for (int h = 0; h < LLAMA_MAX_HW; ++h) best[h] = INT64_MAX;
     const int32_t d = dag[i], o = op_local[i];
-    const bool valid = invocation_valid(P, d, o, start[i], now);
-    if (valid) {
+    if (invocation_valid(P, d, o, start[i], now)) {
         const int32_t v = P.dag_op_off[d] + o;
-        const int64_t c0 = P.cfg_off[v];
-        const int n = (int)(P.cfg_off[v + 1] - c0);
-        const int32_t *hw = P.hw_off + (int64_t)v * (H + 1);
         const int64_t rbase = P.slo[d] - (now - start[i]);
         int32_t sl[LLAMA_MAX_HW];
 #pragma unroll
         for (int h = 0; h < LLAMA_MAX_HW; ++h)
             sl[h] = h < H ? slack_of(P.ref[v], P.cp[v], P.cp_magic[v], rbase - P.q[h]) : 0;
-        for (int x = lane; x < n; x += 32) {
-            const int lam = backend_of(hw, H, x);
-            const int64_t g = c0 + x;
-            int32_t s = sl[0];
-#pragma unroll
-            for (int h = 1; h < LLAMA_MAX_HW; ++h)
-                if (h == lam) s = sl[h];
-            const int64_t obj = P.lat[g] < s ? P.cost[g] : (int64_t)alpha_infeasible_objective(P, g, lam);
-#pragma unroll
-            for (int h = 0; h < LLAMA_MAX_HW; ++h)
-                if (h == lam) best[h] = min(best[h], obj);
-        }
+        warp_backend_minima(P, v, sl, best);
     }
-#pragma unroll
-    for (int h = 0; h < LLAMA_MAX_HW; ++h) {
-        int64_t b = best[h];
-        for (int k = 16; k > 0; k >>= 1) b = min(b, (int64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)b, k));
-        if (lane == 0 && h < H) obj_min[i * H + h] = b;
-    }
+    if (lane == 0)
+        for (int h = 0; h < H; ++h) obj_min[i * H + h] = best[h];
 }
 
 // Priority-based commit (Section 4.4): the affinity of each decided
@@ -2018,12 +2048,7 @@ __global__ void k_commit_keys(DevProblem P, int64_t n, const int32_t *dag, const
         if (dd.cfg >= 0 && !(dd.flags & LLAMA_FLAG_INVALID)) {
             const int32_t v = P.dag_op_off[dag[i]] + op_local[i];
             lam = backend_of(P.hw_off + (int64_t)v * (H + 1), H, dd.cfg);
-            int64_t other = INT64_MAX;
-            for (int h = 0; h < H; ++h)
-                if (h != lam) other = min(other, obj_min[i * H + h]);
-            const int64_t own = obj_min[i * H + lam];
-            // other / own as doubles (objectives stay below 2^53: exact conversions)
-            aff = own == 0 ? (other == 0 ? 1.0 : INFINITY) : (double)other / (double)own;
+            aff = affinity_of(obj_min + i * H, H, lam);
         }
         // descending affinity: invert the order-preserving bit pattern of a non-negative double
         aff_key[i] = ~(uint64_t)__double_as_longlong(aff);
@@ -2085,6 +2110,278 @@ __global__ void k_refresh_order(DevProblem P, const int32_t *ord_pos, int4 *ord_
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= P.n_ops || !P.encode_only[v]) return;
     ord_info[ord_pos[v]].w = P.dlat_n[v];
+}
+
+
+// ---------------------------------------------------------------------------
+// Serving loop: one tick of early speculation and late commit (Section 4.3)
+// with priority-based commit (Section 4.4), by one CTA of 1024 threads; the
+// state lives in device memory (LoopState, the slot arrays and the queues).
+// ---------------------------------------------------------------------------
+
+// For each thread, how many threads before it have their flag set; *total is
+// the block's count.  Every thread must call it (two barriers).
+__device__ __forceinline__ int block_excl_count(bool f, int *total, int *wsum) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const unsigned b = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) wsum[wid] = __popc(b);
+    __syncthreads();
+    int before = 0, tot = 0;
+    for (int w = 0; w < nw; ++w) {
+        const int c = wsum[w];
+        tot += c;
+        if (w < wid) before += c;
+    }
+    __syncthreads();  // wsum is reused by the next call
+    *total = tot;
+    return before + __popc(b & ((1u << lane) - 1u));
+}
+
+// Eq. 2 over both queues: floor(s / R_total), clamped at INT32_MAX (every sum
+// at or above INT32_MAX * R_total clamps, and a smaller one fits 64 bits).
+__device__ __forceinline__ int64_t loop_queue_time(unsigned __int128 s, int32_t r_total) {
+    const unsigned __int128 cap = (unsigned __int128)INT32_MAX * (uint32_t)r_total;
+    if (s >= cap) return INT32_MAX;
+    return (int64_t)((uint64_t)s / (uint32_t)r_total);
+}
+
+__device__ __forceinline__ unsigned long long decision_lr(const DevProblem &P, int32_t g, const llama_decision &d) {
+    return (unsigned long long)(uint32_t)d.lat * (unsigned long long)(uint32_t)P.res[P.cfg_off[g] + d.cfg];
+}
+
+__device__ __forceinline__ void loop_record(const LoopDev &L, long long pos, long long res_read, int64_t id,
+                                            int32_t kind, int32_t tick, const llama_decision &d, int32_t lam) {
+    if (pos - res_read >= L.res_cap) {  // the host has not taken enough records: drop, count
+        atomicAdd(reinterpret_cast<unsigned long long *>(&L.st->dropped), 1ull);
+        return;
+    }
+    llama_loop_result rec;
+    rec.id = id;
+    rec.kind = kind;
+    rec.tick = tick;
+    rec.decision = d;
+    rec.backend = lam;
+    rec.pad = 0;
+    L.res[pos & (L.res_cap - 1)] = rec;
+}
+
+__global__ void __launch_bounds__(kLoopThreads) k_loop_tick(DevProblem P, LoopDev L, LoopTickArgs a) {
+    const int H = P.n_hw, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    LoopState &S = *L.st;
+    __shared__ int wsum[32];
+    __shared__ int sh_n_adm, sh_free_top, sh_tick;
+    __shared__ long long sh_head, sh_res, sh_res_read;
+    __shared__ long long sh_sq_head[LLAMA_MAX_HW], sh_sq_tail[LLAMA_MAX_HW], sh_cq_tail[LLAMA_MAX_HW];
+    __shared__ int sh_room[LLAMA_MAX_HW], sh_cnt[LLAMA_MAX_HW], sh_w[LLAMA_MAX_HW + 1], sh_group[LLAMA_MAX_HW],
+        sh_ncommit_src[LLAMA_MAX_HW];
+    __shared__ unsigned long long sh_lr_in[LLAMA_MAX_HW], sh_lr_out[LLAMA_MAX_HW];
+    __shared__ int32_t c_g[kLoopThreads];
+    __shared__ long long c_rbase[kLoopThreads];
+    __shared__ double c_aff[kLoopThreads];
+    __shared__ int8_t c_lam[kLoopThreads], c_commit[kLoopThreads];
+
+    // 1. dispatch (one thread, so the free stack's order is reproducible), then
+    //    the queueing time at the tick's start (Eq. 2 over both queues)
+    if (tid == 0) {
+        int32_t ft = S.free_top;
+        for (int h = 0; h < H; ++h) {
+            const long long len = S.cq_tail[h] - S.cq_head[h];
+            const long long k = min((long long)max(a.dispatch[h], 0), len);
+            for (long long j = 0; j < k; ++j) {
+                const int32_t slot = L.cq[(int64_t)h * L.cq_stride + (S.cq_head[h] + j) % L.cq_cap[h]];
+                S.s_cq[h] -= L.slot_lr_commit[slot];
+                L.free_stack[ft++] = slot;
+            }
+            S.cq_head[h] += k;
+            S.dispatched += k;
+        }
+        S.free_top = ft;
+        for (int h = 0; h < H; ++h) L.q[h] = loop_queue_time(S.s_sq[h] + S.s_cq[h], P.res_total[h]);
+        const long long avail = max(0ll, a.limit - S.head);
+        sh_n_adm = (int)min(avail, (long long)min(ft, L.max_admit));
+        sh_free_top = ft;
+        sh_head = S.head;
+        sh_res = S.res_count;
+        sh_tick = (int)S.ticks;
+        sh_res_read = (long long)*reinterpret_cast<volatile unsigned long long *>(&L.ctl->res_read);
+        for (int h = 0; h < H; ++h) {
+            sh_sq_head[h] = S.sq_head[h];
+            sh_sq_tail[h] = S.sq_tail[h];
+            sh_cq_tail[h] = S.cq_tail[h];
+            sh_room[h] = L.cq_cap[h] - (int)(S.cq_tail[h] - S.cq_head[h]);
+            sh_lr_in[h] = 0;
+            sh_lr_out[h] = 0;
+            sh_group[h] = 0;
+            sh_ncommit_src[h] = 0;
+        }
+    }
+    __syncthreads();
+
+    // 2. admit in arrival order and speculate (Algorithm 1 under the queueing
+    //    time at the tick's start, Eq. 1 through the staircase tables)
+    const int n_adm = sh_n_adm;
+    bool valid = false;
+    int lam = -1;
+    llama_decision dsn;
+    dsn.cfg = -1;
+    dsn.lat = 0;
+    dsn.cost = 0;
+    dsn.slack = 0;
+    dsn.flags = LLAMA_FLAG_INVALID;
+    unsigned long long lr = 0;
+    llama_loop_request r;
+    r.id = 0;
+    if (tid < n_adm) {
+        r = L.ring[(sh_head + tid) & L.ring_mask];
+        if (invocation_valid(P, r.dag, r.op_local, r.start_us, a.now)) {
+            valid = true;
+            const int32_t g = P.dag_op_off[r.dag] + r.op_local;
+            dsn = stair_decide(P, g, P.slo[r.dag] - (a.now - r.start_us), &lam);
+            lr = decision_lr(P, g, dsn);
+        }
+    }
+    int n_valid;
+    const int vrank = block_excl_count(valid, &n_valid, wsum);
+    int hrank = 0;
+    for (int h = 0; h < H; ++h) {  // rank among this tick's admissions speculated onto backend h
+        int tot;
+        const int rk = block_excl_count(valid && lam == h, &tot, wsum);
+        if (lam == h) hrank = rk;
+        if (tid == 0) sh_cnt[h] = tot;
+    }
+    if (valid) {
+        const int32_t slot = L.free_stack[sh_free_top - 1 - vrank];
+        L.slot_id[slot] = r.id;
+        L.slot_dag[slot] = r.dag;
+        L.slot_opl[slot] = r.op_local;
+        L.slot_start[slot] = r.start_us;
+        L.slot_lr_spec[slot] = lr;
+        L.sq[(int64_t)lam * L.slots + (sh_sq_tail[lam] + hrank) % L.slots] = slot;
+        atomicAdd(&sh_lr_in[lam], lr);
+    }
+    if (tid < n_adm)
+        loop_record(L, sh_res + tid, sh_res_read, r.id, valid ? LLAMA_LOOP_SPECULATED : LLAMA_LOOP_REJECTED, sh_tick,
+                    dsn, lam);
+    __syncthreads();
+    if (tid == 0) {
+        for (int h = 0; h < H; ++h) {
+            S.s_sq[h] += sh_lr_in[h];
+            S.sq_tail[h] += sh_cnt[h];
+            sh_sq_tail[h] += sh_cnt[h];
+            sh_lr_in[h] = 0;
+        }
+        S.free_top = sh_free_top - n_valid;
+        S.head += n_adm;
+        S.res_count += n_adm;
+        S.admitted += n_valid;
+        S.rejected += n_adm - n_valid;
+        sh_res = S.res_count;
+        // the queueing time after speculation: what the revisited heads see
+        for (int h = 0; h < H; ++h) L.q[h] = loop_queue_time(S.s_sq[h] + S.s_cq[h], P.res_total[h]);
+        int c = 0;
+        for (int h = 0; h < H; ++h) {
+            sh_w[h] = c;
+            c += (int)min(sh_sq_tail[h] - sh_sq_head[h], (long long)L.cq_cap[h]);
+        }
+        sh_w[H] = c;
+    }
+    __syncthreads();
+
+    // 3. late commit: the heads of every speculative queue, re-scored together
+    //    (Algorithm 1 and Eq. 1 again, at the tick's time)
+    const int C = sh_w[H];
+    int src = 0, lam2 = -1;
+    int32_t slot = -1, g2 = 0;
+    llama_decision d2 = dsn;
+    if (tid < C) {
+        while (src + 1 < H && tid >= sh_w[src + 1]) ++src;
+        slot = L.sq[(int64_t)src * L.slots + (sh_sq_head[src] + (tid - sh_w[src])) % L.slots];
+        const int32_t d = L.slot_dag[slot];
+        g2 = P.dag_op_off[d] + L.slot_opl[slot];
+        const long long rb = P.slo[d] - (a.now - L.slot_start[slot]);
+        d2 = stair_decide(P, g2, rb, &lam2);
+        c_g[tid] = g2;
+        c_rbase[tid] = rb;
+        c_lam[tid] = (int8_t)lam2;
+    }
+    __syncthreads();
+    // Eq. 3: the least objective per backend of each candidate (a warp each)
+    for (int c = wid; c < C; c += kLoopThreads / 32) {
+        const int32_t g = c_g[c];
+        const long long rb = c_rbase[c];
+        int32_t sl[LLAMA_MAX_HW];
+#pragma unroll
+        for (int h = 0; h < LLAMA_MAX_HW; ++h)
+            sl[h] = h < H ? slack_of(P.ref[g], P.cp[g], P.cp_magic[g], rb - P.q[h]) : 0;
+        int64_t best[LLAMA_MAX_HW];
+        warp_backend_minima(P, g, sl, best);
+        if (lane == 0) c_aff[c] = affinity_of(best, H, c_lam[c]);
+    }
+    __syncthreads();
+    // the commit order: by backend, descending affinity, then candidate order
+    int rank = 0;
+    if (tid < C) {
+        const double my = c_aff[tid];
+        for (int k = 0; k < C; ++k) {
+            if (c_lam[k] != lam2) continue;
+            const double o = c_aff[k];
+            rank += (o > my) || (o == my && k < tid);
+        }
+        atomicAdd(&sh_group[lam2], 1);
+    }
+    const bool commit = tid < C && rank < sh_room[lam2 < 0 ? 0 : lam2];
+    if (tid < C) c_commit[tid] = commit ? 1 : 0;
+    __syncthreads();
+    if (commit) {
+        int before = 0;  // commits of the backends before lam2 (their records come first)
+        for (int t = 0; t < lam2; ++t) before += min(sh_group[t], max(sh_room[t], 0));
+        L.cq[(int64_t)lam2 * L.cq_stride + (sh_cq_tail[lam2] + rank) % L.cq_cap[lam2]] = slot;
+        const unsigned long long lr2 = decision_lr(P, g2, d2);
+        L.slot_lr_commit[slot] = lr2;
+        atomicAdd(&sh_lr_in[lam2], lr2);
+        atomicAdd(&sh_lr_out[src], L.slot_lr_spec[slot]);
+        atomicAdd(&sh_ncommit_src[src], 1);
+        loop_record(L, sh_res + before + rank, sh_res_read, L.slot_id[slot], LLAMA_LOOP_COMMITTED, sh_tick, d2, lam2);
+    }
+    __syncthreads();
+    if (tid < C && !commit) {
+        // a candidate that stays keeps its place behind the ones removed before it
+        int u = 0;
+        for (int k = sh_w[src]; k < tid; ++k) u += c_commit[k] ? 0 : 1;
+        L.sq[(int64_t)src * L.slots + (sh_sq_head[src] + sh_ncommit_src[src] + u) % L.slots] = slot;
+    }
+    __threadfence_system();  // records before the count that publishes them
+    __syncthreads();
+    if (tid == 0) {
+        long long n_commit = 0;
+        for (int h = 0; h < H; ++h) {
+            const int k = min(sh_group[h], max(sh_room[h], 0));
+            S.s_cq[h] += sh_lr_in[h];
+            S.s_sq[h] -= sh_lr_out[h];
+            S.sq_head[h] += sh_ncommit_src[h];
+            S.cq_tail[h] += k;
+            n_commit += k;
+        }
+        S.committed += n_commit;
+        S.res_count += n_commit;
+        S.ticks += 1;
+        volatile LoopCtl *ctl = L.ctl;
+        ctl->head = (unsigned long long)S.head;
+        ctl->dropped = (unsigned long long)S.dropped;
+        ctl->ticks = (unsigned long long)S.ticks;
+        __threadfence_system();
+        ctl->res_count = (unsigned long long)S.res_count;
+    }
+}
+
+cudaError_t enqueue_loop_tick(const DevProblem &P, const LoopDev &L, const LoopTickArgs &a, cudaStream_t s) {
+    k_loop_tick<<<1, kLoopThreads, 0, s>>>(P, L, a);
+    return cudaGetLastError();
+}
+
+cudaError_t enqueue_critical_paths(const ContextView &v, cudaStream_t s) {
+    k_critical_paths<<<std::max(1, (v.n_dags + 7) / 8), 256, 0, s>>>(v.P, v.topo, v.lvl_off, v.dag_lvl);
+    return cudaGetLastError();
 }
 
 }  // namespace llama

@@ -600,6 +600,12 @@ int context_fail(llama_ctx *c, int code, const char *msg) { return c->fail(code,
 
 void context_set_launches(llama_ctx *c, int launches) { c->last_launches = launches; }
 
+int context_ensure_stair(llama_ctx *c) {
+    DeviceGuard g(c->opts.device);
+    if (!c->prof_set) return c->fail(LLAMA_ENOTREADY, "staircase tables before llama_set_profiles");
+    return c->stair_ready ? LLAMA_OK : build_stair(c);
+}
+
 }  // namespace llama
 
 // ---------------------------------------------------------------------------

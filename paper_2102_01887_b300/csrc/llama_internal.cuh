@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/llama.h"
+#include "../../include/llama_loop.h"
 
 namespace llama {
 
@@ -287,5 +288,58 @@ __global__ void k_stair(DevProblem P, int64_t n_inv, const int32_t *dag, const i
                         const int64_t *start, int64_t now, BucketScratch S, llama_decision *out);
 __global__ void k_encode_rank(DevProblem P, int32_t sort_n, uint16_t *rf, uint16_t *df,
                               uint16_t *inv);
+
+// ---------------------------------------------------------------------------
+// Serving loop (early speculation and late commit, Section 4.3; priority-based
+// commit, Section 4.4): state on the device, one CTA per tick.
+// ---------------------------------------------------------------------------
+constexpr int kLoopThreads = 1024;  // = LLAMA_LOOP_MAX_ADMIT = LLAMA_LOOP_MAX_COMMIT
+static_assert(kLoopThreads == LLAMA_LOOP_MAX_ADMIT && kLoopThreads == LLAMA_LOOP_MAX_COMMIT, "one thread each");
+
+// Page-locked, mapped control words (device writes, host reads; res_read the
+// other way round).
+struct LoopCtl {
+    unsigned long long head;       // requests the device has taken from the ring
+    unsigned long long res_count;  // result records published
+    unsigned long long res_read;   // records the host has taken (host writes)
+    unsigned long long dropped;    // records lost to a full result ring
+    unsigned long long ticks;
+};
+
+// Device-resident counters and queue state (one struct in device memory).
+struct LoopState {
+    unsigned __int128 s_sq[LLAMA_MAX_HW], s_cq[LLAMA_MAX_HW];  // exact sums of L(x) R(x) per queue
+    long long sq_head[LLAMA_MAX_HW], sq_tail[LLAMA_MAX_HW], cq_head[LLAMA_MAX_HW], cq_tail[LLAMA_MAX_HW];
+    long long head, ticks, admitted, rejected, committed, dispatched, res_count, dropped;
+    int32_t free_top;  // free slots on the stack
+};
+
+struct LoopDev {
+    LoopState *st;
+    LoopCtl *ctl;                       // device view of the mapped control words
+    const llama_loop_request *ring;     // device view of the mapped request ring
+    llama_loop_result *res;             // device view of the mapped result ring
+    int64_t ring_mask, res_cap;
+    int32_t *free_stack;                // [slots]
+    int64_t *slot_id, *slot_start;      // [slots]
+    int32_t *slot_dag, *slot_opl;       // [slots]
+    unsigned long long *slot_lr_spec, *slot_lr_commit;  // [slots] L(x) R(x) of each decision
+    int32_t *sq;                        // [n_hw][slots] speculative queues (rings of slot ids)
+    int32_t *cq;                        // [n_hw][cq_stride] commit queues
+    int64_t *q;                         // [LLAMA_MAX_HW] the tick's queueing time (P.q points here)
+    int32_t slots, cq_stride, max_admit;
+    int32_t cq_cap[LLAMA_MAX_HW];
+};
+
+struct LoopTickArgs {
+    int64_t now, limit;                 // the tick's time; requests submitted before it (ring tail)
+    int32_t dispatch[LLAMA_MAX_HW];     // invocations each backend took from its commit queue
+};
+
+// Enqueue one tick on s (P.q must be L.q).
+cudaError_t enqueue_loop_tick(const DevProblem &P, const LoopDev &L, const LoopTickArgs &a, cudaStream_t s);
+// Critical paths of every DAG (a1), on s.
+cudaError_t enqueue_critical_paths(const ContextView &v, cudaStream_t s);
+int context_ensure_stair(llama_ctx *c);  // staircase tables for the current profiles
 
 }  // namespace llama

@@ -42,7 +42,9 @@ EXPORTS = ("llama_create", "llama_destroy", "llama_set_dags", "llama_set_profile
            "llama_server_create", "llama_server_destroy", "llama_server_submit", "llama_server_poll",
            "llama_server_drain", "llama_server_stats_get", "llama_queue_time", "llama_feedback",
            "llama_get_profiles", "llama_backend_objectives", "llama_commit_order",
-           "llama_static_status", "llama_set_wait_limit", "llama_alu_peak")
+           "llama_static_status", "llama_set_wait_limit", "llama_alu_peak",
+           "llama_loop_create", "llama_loop_destroy", "llama_loop_submit", "llama_loop_tick", "llama_loop_poll",
+           "llama_loop_sync", "llama_loop_state_get", "llama_loop_refresh")
 TRACE_EVENTS = 3
 TRACE_PHASES = ("bucket", "score")
 
@@ -58,6 +60,26 @@ class llama_opts(ctypes.Structure):
                 ("alpha_num", ctypes.c_int64), ("alpha_den", ctypes.c_int64),
                 ("device", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
 
+
+class llama_loop_opts(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("ring", ctypes.c_int32), ("results", ctypes.c_int32),
+                ("max_admit", ctypes.c_int32), ("cq_cap", ctypes.c_int32 * MAX_HW)]
+
+
+class llama_loop_state(ctypes.Structure):
+    _fields_ = [("ticks", ctypes.c_int64), ("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64),
+                ("rejected", ctypes.c_int64), ("committed", ctypes.c_int64), ("dispatched", ctypes.c_int64),
+                ("results", ctypes.c_int64), ("results_dropped", ctypes.c_int64), ("free_slots", ctypes.c_int32),
+                ("sq_len", ctypes.c_int32 * MAX_HW), ("cq_len", ctypes.c_int32 * MAX_HW),
+                ("q_us", ctypes.c_int64 * MAX_HW)]
+
+
+LOOP_REQUEST_DTYPE = np.dtype([("id", "<i8"), ("dag", "<i4"), ("op_local", "<i4"), ("start_us", "<i8")])
+LOOP_RESULT_DTYPE = np.dtype([("id", "<i8"), ("kind", "<i4"), ("tick", "<i4"), ("decision", DECISION_DTYPE),
+                              ("backend", "<i4"), ("pad", "<i4")])
+assert LOOP_REQUEST_DTYPE.itemsize == 24 and LOOP_RESULT_DTYPE.itemsize == 48
+LOOP_SPECULATED, LOOP_COMMITTED, LOOP_REJECTED = 1, 2, 3
+LOOP_MAX_ADMIT = LOOP_MAX_COMMIT = 1024
 
 _lib = None
 _lock = threading.Lock()
@@ -126,6 +148,14 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "llama_static_status": ([vp, vp, vp, vp], ctypes.c_int),
             "llama_set_wait_limit": ([vp, i32], ctypes.c_int),
             "llama_alu_peak": ([i32, i32, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+            "llama_loop_create": ([vp, ctypes.POINTER(llama_loop_opts), ctypes.POINTER(vp)], ctypes.c_int),
+            "llama_loop_destroy": ([vp], None),
+            "llama_loop_submit": ([vp, vp, i64], ctypes.c_int),
+            "llama_loop_tick": ([vp, i64, vp], ctypes.c_int),
+            "llama_loop_poll": ([vp, vp, i64, ctypes.POINTER(i64)], ctypes.c_int),
+            "llama_loop_sync": ([vp], ctypes.c_int),
+            "llama_loop_state_get": ([vp, ctypes.POINTER(llama_loop_state)], ctypes.c_int),
+            "llama_loop_refresh": ([vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -496,6 +526,67 @@ def llama_set_trace_events(ctx, events) -> None:
 
 def llama_last_launch_count(ctx) -> int:
     return load().llama_last_launch_count(ctx)
+
+
+class Loop:
+    """The device-resident serving loop (early speculation and late commit,
+    priority-based commit) over a Scheduler's context."""
+
+    def __init__(self, sched, slots: int = 65536, ring: int = 1 << 16, results: int = 1 << 18,
+                 max_admit: int = 1024, cq_cap=(64, 64, 64)):
+        self.lib = load()
+        self.sched = sched
+        opts = llama_loop_opts(slots, ring, results, max_admit, (ctypes.c_int32 * MAX_HW)(*cq_cap))
+        h = ctypes.c_void_p()
+        _check(sched.ctx, self.lib.llama_loop_create(sched.ctx, ctypes.byref(opts), ctypes.byref(h)))
+        self.h = h
+        self.n_hw = sched.problem.n_hw
+        self._buf = np.zeros(max(results, 1), LOOP_RESULT_DTYPE)
+
+    def _check(self, rc):
+        _check(self.sched.ctx, rc)
+
+    def submit(self, req: np.ndarray) -> int:
+        req = np.ascontiguousarray(req, LOOP_REQUEST_DTYPE)
+        rc = self.lib.llama_loop_submit(self.h, req.ctypes.data, req.shape[0])
+        if rc not in (OK, EAGAIN):
+            self._check(rc)
+        return rc
+
+    def tick(self, now_us: int, dispatch=None) -> None:
+        d = None if dispatch is None else np.ascontiguousarray(dispatch, np.int32)
+        self._check(self.lib.llama_loop_tick(self.h, int(now_us), None if d is None else d.ctypes.data))
+
+    def poll(self) -> np.ndarray:
+        n = ctypes.c_int64()
+        self._check(self.lib.llama_loop_poll(self.h, self._buf.ctypes.data, self._buf.shape[0], ctypes.byref(n)))
+        return self._buf[:n.value].copy()
+
+    def sync(self) -> None:
+        self._check(self.lib.llama_loop_sync(self.h))
+
+    def state(self) -> dict:
+        st = llama_loop_state()
+        self._check(self.lib.llama_loop_state_get(self.h, ctypes.byref(st)))
+        H = self.n_hw
+        return {"ticks": st.ticks, "submitted": st.submitted, "admitted": st.admitted, "rejected": st.rejected,
+                "committed": st.committed, "dispatched": st.dispatched, "results": st.results,
+                "results_dropped": st.results_dropped, "free_slots": st.free_slots,
+                "sq_len": list(st.sq_len)[:H], "cq_len": list(st.cq_len)[:H], "q_us": list(st.q_us)[:H]}
+
+    def refresh(self) -> None:
+        self._check(self.lib.llama_loop_refresh(self.h))
+
+    def close(self) -> None:
+        if self.h:
+            self.lib.llama_loop_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 class Scheduler:
