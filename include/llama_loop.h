@@ -99,10 +99,12 @@ typedef struct llama_loop_state {
 typedef struct llama_loop llama_loop;
 
 /* A loop over a ready context: DAGs and profiles set, with batch, res and
- * res_total (Eq. 2 and Eq. 3 need B(x), R(x) and R_total).  Builds the staircase tables and
- * the per-backend suffix minima of Eq. 1's infeasible branch for the current
- * profiles and computes the critical paths; call llama_loop_refresh after the
- * context's tables change (feedback).  The loop owns a CUDA stream, device
+ * res_total (Eq. 2 and Eq. 3 need B(x), R(x) and R_total).  Builds the
+ * staircase tables for the current profiles (if the context has none) and
+ * computes the critical paths; Eq. 3's per-backend minima are taken per commit
+ * candidate over its operation's configurations (a warp each).  Call
+ * llama_loop_refresh after the context's tables change (feedback); a new
+ * llama_set_profiles needs a new loop.  The loop owns a CUDA stream, device
  * state sized by opts, and two page-locked rings.  Errors: EINVAL, ENOTREADY,
  * ENOMEM, ECUDA. */
 int llama_loop_create(llama_ctx *ctx, const llama_loop_opts *opts, llama_loop **out);
