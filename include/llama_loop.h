@@ -126,6 +126,10 @@ int llama_loop_tick(llama_loop *loop, int64_t now_us, const int32_t *dispatch);
  * number in *n_out.  Never waits for the GPU. */
 int llama_loop_poll(llama_loop *loop, llama_loop_result *out, int64_t max_out, int64_t *n_out);
 
+/* Ticks completed so far (read from the page-locked control words the last
+ * tick published; never waits), or -1 for a null loop. */
+int64_t llama_loop_ticks_done(llama_loop *loop);
+
 /* Wait until every enqueued tick has completed.  Errors: ECUDA. */
 int llama_loop_sync(llama_loop *loop);
 

@@ -116,6 +116,15 @@ int llama_sg_schedule(llama_sg *sg, const void *cfg_x, const void *inv_x, int64_
                       const int32_t *op_local, const int64_t *start_us, int64_t now_us, llama_decision *out,
                       void *stream);
 
+/* Layer 1's configuration part (cfg_x times W1, every configuration) is
+ * computed by the first call and kept while later calls pass the same cfg_x
+ * pointer, the network's weights are unchanged (llama_mlp_set_params and
+ * llama_mlp_train_step change them) and the context's profiles are the same
+ * buffers; calls that reuse it must be ordered after the call that computed it
+ * (one stream, or an event).  After changing cfg_x's contents in place, call
+ * llama_sg_invalidate.  No counterpart in the paper.  Errors: EINVAL. */
+int llama_sg_invalidate(llama_sg *sg);
+
 /* Safety margin in log units (0 .. 1, default 0): the selection uses
  * e^(y0 + margin) times the profiled latency and cost, an upper quantile of the
  * prediction when margin is about the model's error.  Selecting the cheapest

@@ -233,6 +233,11 @@ extern "C" int llama_loop_poll(llama_loop *lp, llama_loop_result *out, int64_t m
     return LLAMA_OK;
 }
 
+extern "C" int64_t llama_loop_ticks_done(llama_loop *lp) {
+    if (!lp) return -1;
+    return (int64_t)*reinterpret_cast<volatile unsigned long long *>(&lp->h_ctl->ticks);
+}
+
 extern "C" int llama_loop_sync(llama_loop *lp) {
     if (!lp) return LLAMA_EINVAL;
     CurrentDevice guard(lp->device);

@@ -27,6 +27,7 @@ struct llama_mlp_view {
     const float *params;       // FP32 master parameters (flat layout above)
     const void *w16[4];        // BF16 W1..W4 [out x in]
     int device;
+    int64_t version;           // changes whenever the weights change
 };
 
 // The pair layers of the scheduling path on the persistent kernel (weights kept

@@ -173,6 +173,7 @@ struct llama_mlp {
     int device = 0;
     int64_t cap = 0;      // batch capacity (rows)
     int64_t steps = 0;    // Adam steps taken
+    int64_t version = 0;  // bumped whenever the weights change (set_params, train_step)
     Buf w, g, m, v;       // FP32 parameters, gradients, Adam moments
     Buf wb[4], wt[4];     // BF16 W_l and W_l^T
     Buf h1, h2, h3, y;    // activations (BF16) and outputs (FP32, 64 per row)
@@ -326,6 +327,7 @@ extern "C" int llama_mlp_set_params(llama_mlp *m, const float *params) {
     MLP_CUDA(m, cudaMemset(m->m.p, 0, 4 * kParams));
     MLP_CUDA(m, cudaMemset(m->v.p, 0, 4 * kParams));
     m->steps = 0;
+    ++m->version;
     MLP_RC(pack_weights(m, nullptr));
     MLP_CUDA(m, cudaDeviceSynchronize());
     return LLAMA_OK;
@@ -378,6 +380,7 @@ extern "C" int llama_mlp_train_step(llama_mlp *m, const void *x, const float *t,
     MLP_RC(forward(m, x, n, s));
     MLP_RC(backward(m, x, t, n, w_fan, loss, s));
     const int64_t step = ++m->steps;
+    ++m->version;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.f - (float)std::pow((double)b1, (double)step), c2 = 1.f - (float)std::pow((double)b2, (double)step);
     k_adam<<<592, 256, 0, s>>>(m->w.as<float>(), m->g.as<float>(), m->m.as<float>(), m->v.as<float>(), kParams,
@@ -395,6 +398,7 @@ llama_mlp_view mlp_view(const llama_mlp *m) {
     v.params = m->w.as<float>();
     for (int l = 0; l < 4; ++l) v.w16[l] = m->wb[l].p;
     v.device = m->device;
+    v.version = m->version;
     return v;
 }
 }  // namespace sgk

@@ -37,14 +37,14 @@ EXPORTS = ("llama_create", "llama_destroy", "llama_set_dags", "llama_set_profile
            "llama_mlp_create", "llama_mlp_destroy", "llama_mlp_set_params", "llama_mlp_get_params",
            "llama_mlp_forward", "llama_mlp_gradients", "llama_mlp_train_step", "llama_mlp_last_error",
            "llama_sg_create", "llama_sg_destroy", "llama_sg_schedule", "llama_sg_last_pairs",
-           "llama_sg_predictions", "llama_sg_last_error", "llama_sg_set_margin",
+           "llama_sg_predictions", "llama_sg_last_error", "llama_sg_set_margin", "llama_sg_invalidate",
            "llama_ws_create", "llama_ws_destroy", "llama_schedule_ws_async", "llama_ws_status",
            "llama_server_create", "llama_server_destroy", "llama_server_submit", "llama_server_poll",
            "llama_server_drain", "llama_server_stats_get", "llama_queue_time", "llama_feedback",
            "llama_get_profiles", "llama_backend_objectives", "llama_commit_order",
            "llama_static_status", "llama_set_wait_limit", "llama_alu_peak",
            "llama_loop_create", "llama_loop_destroy", "llama_loop_submit", "llama_loop_tick", "llama_loop_poll",
-           "llama_loop_sync", "llama_loop_state_get", "llama_loop_refresh")
+           "llama_loop_sync", "llama_loop_state_get", "llama_loop_refresh", "llama_loop_ticks_done")
 TRACE_EVENTS = 3
 TRACE_PHASES = ("bucket", "score")
 
@@ -130,6 +130,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "llama_sg_predictions": ([vp, vp, vp, vp, i64, vp], ctypes.c_int),
             "llama_sg_last_error": ([vp], ctypes.c_char_p),
             "llama_sg_set_margin": ([vp, ctypes.c_float], ctypes.c_int),
+            "llama_sg_invalidate": ([vp], ctypes.c_int),
             "llama_ws_create": ([vp, i64, ctypes.POINTER(vp)], ctypes.c_int),
             "llama_ws_destroy": ([vp], None),
             "llama_schedule_ws_async": ([vp, vp, i64, vp, vp, vp, i64, vp, vp], ctypes.c_int),
@@ -156,6 +157,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "llama_loop_sync": ([vp], ctypes.c_int),
             "llama_loop_state_get": ([vp, ctypes.POINTER(llama_loop_state)], ctypes.c_int),
             "llama_loop_refresh": ([vp], ctypes.c_int),
+            "llama_loop_ticks_done": ([vp], i64),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -564,6 +566,9 @@ class Loop:
 
     def sync(self) -> None:
         self._check(self.lib.llama_loop_sync(self.h))
+
+    def ticks_done(self) -> int:
+        return int(self.lib.llama_loop_ticks_done(self.h))
 
     def state(self) -> dict:
         st = llama_loop_state()

@@ -103,6 +103,11 @@ class SurrogateScheduler:
     def set_margin(self, margin: float) -> None:
         self._check(L.load().llama_sg_set_margin(self.h, float(margin)))
 
+    def invalidate(self) -> None:
+        """Recompute layer 1's configuration part at the next call (after the
+        configuration features changed in place)."""
+        self._check(L.load().llama_sg_invalidate(self.h))
+
     def schedule_device(self, cfg_x, inv_x, dag, op_local, start, now_us: int, out, stream=None) -> None:
         v = lambda t: ctypes.c_void_p(t.data_ptr())
         self._check(L.load().llama_sg_schedule(self.h, v(cfg_x), v(inv_x), dag.shape[0], v(dag), v(op_local),

@@ -157,6 +157,38 @@ def evaluate(p, cw, sub, content, decisions_cfg, slack, lam, noise_seed):
     return res
 
 
+def test_layer1_configuration_part_is_kept_while_valid(L, world):
+    """Layer 1's configuration part is computed once and kept across calls; a
+    weight change (set_params) or llama_sg_invalidate after an in-place change
+    of the features makes the next call recompute it.  Every call must equal a
+    fresh scheduler's."""
+    import torch
+
+    from paper_2102_01887_b300 import surrogate as S
+    p, inv, cw = world
+    sub = inv.subset(np.arange(0, inv.n, 512))
+    content = W.invocation_content(3, sub.n)
+    with L.Scheduler(p) as s, L.MLP(max_batch=1024) as net:
+        cfg_x = S.config_inputs(p, cw)
+
+        def fresh():
+            with S.SurrogateScheduler(s, net, max_inv=4096, max_pairs=1 << 20) as f:
+                return f.schedule(cfg_x, sub, content)
+
+        with S.SurrogateScheduler(s, net, max_inv=4096, max_pairs=1 << 20) as sg:
+            net.set_params(M.pack(perturbed_params(21)).astype(np.float32))
+            a = sg.schedule(cfg_x, sub, content)
+            assert np.array_equal(sg.schedule(cfg_x, sub, content), a)  # kept
+            assert np.array_equal(a, fresh())
+            net.set_params(M.pack(perturbed_params(22)).astype(np.float32))  # new weights
+            b = sg.schedule(cfg_x, sub, content)
+            assert np.array_equal(b, fresh()) and not np.array_equal(b, a)
+            # features changed in place: stale until invalidated
+            cfg_x[:, :32] = torch.flip(cfg_x[:, :32], dims=[0])
+            sg.invalidate()
+            assert np.array_equal(sg.schedule(cfg_x, sub, content), fresh())
+
+
 @pytest.mark.slow
 def test_edge_cases(L, world):
     """A single invocation; a call in which every invocation is invalid (no pair
