@@ -496,9 +496,25 @@ SURROGATE_FLOPS_PER_PAIR = 2 * 2 * 256 * 256 + 2 * 256  # layers 2 and 3, fused 
 SURROGATE_FLOPS_PER_SAMPLE = 3 * 2 * (64 * 256 + 2 * 256 * 256 + 256 * 64)  # forward + backward
 
 
+def surrogate_chunks(p, inv, max_pairs: int):
+    """Contiguous invocation ranges whose (invocation, configuration) pairs fit
+    max_pairs each."""
+    sizes = np.diff(p.cfg_off)[p.dag_op_off[inv.dag] + inv.op_local]
+    cuts, a, acc = [], 0, 0
+    for i, z in enumerate(sizes):
+        if acc + int(z) > max_pairs and i > a:
+            cuts.append((a, i))
+            a, acc = i, 0
+        acc += int(z)
+    cuts.append((a, inv.n))
+    return cuts, int(sizes.sum())
+
+
 def run_surrogate(args):
     """The learned-surrogate path: train on the profiler's samples (timed on its
-    own), then schedule batches of invocations with content (timed)."""
+    own), then schedule every invocation of the workload with its content
+    (timed), in calls whose pair buffers stay bounded; decision quality against
+    the ground-truth content model on a sample of the invocations."""
     import torch
 
     import oracle
@@ -509,16 +525,20 @@ def run_surrogate(args):
     from paper_2102_01887_b300 import surrogate as S
     from paper_2102_01887_b300 import workloads as W
     B.build()
-    p, inv = make_workload(args.workload, 0, args.n_dags, None)
-    n_inv = args.n_inv or 4096
-    sub = inv.subset(np.arange(n_inv) % inv.n)
+    default_n = 1_048_576 if args.workload == "batched" else 4096
+    p, inv_all = make_workload(args.workload, 0, args.n_dags, None)
+    n_inv = args.n_inv or default_n
+    inv = inv_all.subset(np.arange(n_inv) % inv_all.n)
+    max_pairs = 1 << 24
+    chunks, n_pairs = surrogate_chunks(p, inv, max_pairs)
     cw = W.content_world(p)
     x, t = W.surrogate_training_set(p, cw, 2_000_000)
     xv, tv = W.surrogate_training_set(p, cw, 100_000, seed=303)
-    content = W.invocation_content(9, sub.n)
+    content = W.invocation_content(9, inv.n)
     peaks, peak_src = measured_peaks()
     dev = torch.device("cuda", 0)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    steps = max(1, min(args.steps, 5))
     with L.Scheduler(p) as s, L.MLP(max_batch=8192) as net:
         net.set_params(M.pack(M.init_params(3)).astype(np.float32))
         xd, td = S.training_inputs(x, t)
@@ -534,35 +554,52 @@ def run_surrogate(args):
         margin = S.margin_from_rmse(S.held_out_rmse(net, *S.training_inputs(xv, tv)), W.LATENCY_NOISE_SIGMA)
         cfg_x = S.config_inputs(p, cw)
         inv_x = S.content_inputs(content)
-        dag = torch.from_numpy(sub.dag).to(dev)
-        opl = torch.from_numpy(sub.op_local).to(dev)
-        st = torch.from_numpy(sub.start_us).to(dev)
-        out = torch.zeros(sub.n * 24, dtype=torch.uint8, device=dev)
-        n_pairs = int(np.diff(p.cfg_off)[p.dag_op_off[sub.dag] + sub.op_local].sum())
-        with S.SurrogateScheduler(s, net, max_inv=sub.n, max_pairs=n_pairs) as sg:
+        dag = torch.from_numpy(inv.dag).to(dev)
+        opl = torch.from_numpy(inv.op_local).to(dev)
+        st = torch.from_numpy(inv.start_us).to(dev)
+        out = torch.zeros(inv.n * 24, dtype=torch.uint8, device=dev)
+        max_chunk = max(b - a for a, b in chunks)
+        with S.SurrogateScheduler(s, net, max_inv=max_chunk, max_pairs=max_pairs) as sg:
             sg.set_margin(margin)
             stream = torch.cuda.current_stream()
-            for _ in range(args.warmup):
-                sg.schedule_device(cfg_x, inv_x, dag, opl, st, sub.now_us, out, stream)
+
+            def full_pass():
+                for a, b in chunks:
+                    sg.schedule_device(cfg_x, inv_x[a:b], dag[a:b], opl[a:b], st[a:b], inv.now_us,
+                                       out[24 * a:24 * b], stream)
+
+            torch.cuda.synchronize()
+            t_first = time.perf_counter()
+            full_pass()  # the first pass also computes layer 1's configuration part
+            torch.cuda.synchronize()
+            first_ms = 1e3 * (time.perf_counter() - t_first)
+            for _ in range(max(0, args.warmup - 1)):
+                full_pass()
             torch.cuda.synchronize()
             ms = []
             with ClockSampler(0) as clocks:
-                for k in range(args.steps):
+                for k in range(steps):
                     flush.fill_(k & 0xFF)
                     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                     e0.record(stream)
-                    sg.schedule_device(cfg_x, inv_x, dag, opl, st, sub.now_us, out, stream)
+                    full_pass()
                     e1.record(stream)
                     e1.synchronize()
                     ms.append(e0.elapsed_time(e1))
-            got = out.cpu().numpy().view(L.DECISION_DTYPE)
+            got_all = out.cpu().numpy().view(L.DECISION_DTYPE)
+            # decision quality on a sample of the invocations
+            k_s = max(1, inv.n // 16_384)
+            qidx = np.arange(0, inv.n, k_s)
+            sub = inv.subset(qidx)
             table, _ = s.schedule(sub)
+            got = got_all[qidx]
     step_ms = float(np.mean(ms))
-    value = sub.n / (step_ms / 1e3)
+    value = inv.n / (step_ms / 1e3)
     achieved = SURROGATE_FLOPS_PER_PAIR * n_pairs / (step_ms / 1e3) / 1e12
     peak = float(peaks.get("bf16_tflops_sustained", 1400.0))
     train_tflops = SURROGATE_FLOPS_PER_SAMPLE * samples / train_s / 1e12 if samples else None
-    # decision quality on this batch, judged with the ground-truth content model
+    # decision quality, judged with the ground-truth content model
+    cs = W.Content(content.n_obj[qidx], content.motion[qidx], content.in_res[qidx])
     slack = oracle.slacks(p, sub)
     valid = slack[:, 0] >= 0
     gop = p.dag_op_off[sub.dag] + sub.op_local
@@ -573,7 +610,7 @@ def run_surrogate(args):
     px = np.arange(off[-1]) - np.repeat(off[:-1], sizes)
     pg = p.cfg_off[gop[pinv]] + px
     hw = p.hw_off.reshape(p.n_ops, p.n_hw + 1)
-    ci = W.Content(content.n_obj[pinv], content.motion[pinv], content.in_res[pinv])
+    ci = W.Content(cs.n_obj[pinv], cs.motion[pinv], cs.in_res[pinv])
     f = W.true_log_factor(p, cw, gop[pinv], px, ci) + W.latency_noise(31, pinv.shape[0])
     lt = np.maximum(1, np.rint(p.lat_us[pg] * np.exp(f))).astype(np.int64)
     ct = np.rint(p.cost_nd[pg] * np.exp(f)).astype(np.int64)
@@ -581,29 +618,34 @@ def run_surrogate(args):
     spair = slack[pinv, seg]
     quality = {}
     for name, xs in (("table", table["cfg"]), ("surrogate", got["cfg"]), ("truth", OS.select(lt, ct, spair, off))):
-        k = off[:-1][valid] + xs[valid]
-        quality[name] = {"violations": float((lt[k] >= spair[k]).mean()), "true_cost": float(ct[k].sum())}
+        kk = off[:-1][valid] + xs[valid]
+        quality[name] = {"violations": float((lt[kk] >= spair[kk]).mean()), "true_cost": float(ct[kk].sum())}
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": args.warmup,
         "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16 (fp32 accumulate)", "data": "synthetic",
-        "config": {"workload": args.workload, "method": "surrogate", "invocations": sub.n, "pairs_per_step": n_pairs,
+        "config": {"workload": args.workload, "method": "surrogate", "invocations": inv.n, "pairs_per_step": n_pairs,
+                   "calls_per_step": len(chunks), "max_pairs_per_call": max_pairs,
                    "network": "64-256-256-256-64 MLP (48 features), BF16, FP32 accumulation",
                    "training_samples": int(x.shape[0]), "margin": margin,
-                   "l2": "flushed before every timed step (256 MiB write)"},
+                   "l2": "flushed before every timed step (256 MiB write)",
+                   "layer1_configuration_part": "computed by the first pass, kept while weights and features "
+                                                "are unchanged"},
         "pairs_per_s": n_pairs / (step_ms / 1e3),
+        "first_pass_ms": first_ms,
         "roofline": {"bound": "tensor", "kernel": "k_mlp_layer (layers 1 + 2, 3 + selection)", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                      "peak_source": f"{peak_src} sustained cuBLAS bf16", "flops_per_pair": SURROGATE_FLOPS_PER_PAIR,
-                     "note": "whole scheduling call (slack, pair set-up, both GEMMs, decode) in the denominator"},
+                     "note": "whole scheduling calls (slack, pair set-up, both pair layers, decode, and the "
+                             "host read of each call's pair count) in the denominator"},
         "training": {"samples_per_s": samples / train_s if samples else None, "tflops": train_tflops,
                      "seconds": train_s if samples else None, "epochs": args.train_epochs, "loss_by_epoch": hist},
         "decision_quality": quality,
+        "decision_quality_sample": f"every {k_s}th invocation ({sub.n}), ground-truth latencies with noise",
         "clocks": clocks.summary(),
-        # own kernels per call: critical paths, slack, configuration backends, pair keys, rows per
-        # invocation, layer 1 twice, pair set-up, layers 1 + 2, layer 3 + selection, decode
-        # (CUB's sort and scan not counted)
-        "gpu_launches": 11 * args.steps, "cpu_baseline": None, "e2e": None,
+        # own kernels per call: critical paths, slack, pair keys, rows per invocation, layer 1 (contents),
+        # pair set-up, layers 1 + 2, layer 3 + selection, decode (CUB's sort and scan not counted)
+        "gpu_launches": 9 * len(chunks) * steps, "cpu_baseline": None, "e2e": None,
     }
     print(json.dumps(line), flush=True)
 

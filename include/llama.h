@@ -367,6 +367,33 @@ int llama_slack(llama_ctx *ctx, int64_t n_inv, const int32_t *dag, const int32_t
 #define LLAMA_TRACE_EVENTS 3
 int llama_set_trace_events(llama_ctx *ctx, void *const *events, int32_t n_events);
 
+/* Per-call statistics (no counterpart in the paper): once set, every blocking
+ * llama_schedule call appends one JSON object per line to the file at path
+ * (opened for appending; NULL or "" closes it): the call's index, n_inv,
+ * now_us, method, kernel launches, whether a CUDA graph was replayed, the
+ * invalid count, whether a bounded wait gave up, the device time of its
+ * kernels (events around them) and the host time of the whole call.  Errors:
+ * EINVAL (the file cannot be opened), ECUDA. */
+int llama_set_stats_file(llama_ctx *ctx, const char *path);
+
+/* Checked build (no counterpart in the paper).  A library compiled with
+ * -DLLAMA_CHECK bounds-checks the indices its kernels compute (bucket
+ * positions, tile entries, staged table ranges, count-pass positions, decode
+ * keys, serving-loop slots); a failed check sets its bit in the context's
+ * check word and skips the access (never a trap), so the call completes with
+ * a wrong result that the word reports.  llama_check_build returns 1 in such
+ * a build and 0 otherwise; llama_check_word copies the word into *bits
+ * (blocking; all zero in a normal build) and clears it when clear != 0.
+ * Errors: EINVAL, ECUDA. */
+#define LLAMA_CHECK_SCATTER 1u
+#define LLAMA_CHECK_TILE 2u
+#define LLAMA_CHECK_STAGE 4u
+#define LLAMA_CHECK_COUNTS 8u
+#define LLAMA_CHECK_DECODE 16u
+#define LLAMA_CHECK_LOOP 32u
+int llama_check_build(void);
+int llama_check_word(llama_ctx *ctx, uint32_t *bits, int32_t clear);
+
 /* Kernel launches issued by the last scheduling call (for accounting). */
 int llama_last_launch_count(llama_ctx *ctx);
 

@@ -17,6 +17,7 @@ from concurrent.futures import ThreadPoolExecutor
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 LIB = os.path.join(PKG, "libllama.so")
+CHECK_LIB = os.path.join(PKG, "libllama_check.so")  # bounds checks that set bits (-DLLAMA_CHECK)
 OBJ_DIR = os.path.join(ROOT, "_build")
 SOURCES = [os.path.join(PKG, "csrc", f) for f in ("kernels.cu", "llama_host.cu", "llama_static.cu", "sg_gemm.cu", "sg_mlp.cu", "sg_score.cu", "server.cpp", "alu_peak.cu", "loop.cu")]
 HEADERS = glob.glob(os.path.join(PKG, "csrc", "*.cuh")) + glob.glob(os.path.join(PKG, "csrc", "*.h")) + \
@@ -73,5 +74,12 @@ def build(force: bool = False, out: str = LIB, extra: tuple = (), verbose: bool 
     return out
 
 
+def build_check(force: bool = False, verbose: bool = False) -> str:
+    """The checked build, libllama_check.so (-DLLAMA_CHECK)."""
+    return build(force=force, out=CHECK_LIB, extra=("-DLLAMA_CHECK",), verbose=verbose)
+
+
 if __name__ == "__main__":
     build(force="--force" in sys.argv, verbose=True)
+    if "--check" in sys.argv:
+        build_check(force="--force" in sys.argv, verbose=True)

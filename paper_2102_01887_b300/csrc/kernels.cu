@@ -43,6 +43,20 @@ __device__ __forceinline__ uint32_t vmin_u16x2(uint32_t a, uint32_t b) {
     return d;
 }
 
+// Whether a decode key indexes op v's decode table: below twice its
+// configurations (alpha: the joint ranks), below its configurations for a
+// feasible-branch rank (cost-first; 0x8000 and above decode the fastest
+// configuration).  Evaluated in the -DLLAMA_CHECK build only.
+__device__ __forceinline__ bool decode_key_ok(const DevProblem &P, int32_t v, uint32_t key, int mode) {
+#ifdef LLAMA_CHECK
+    if (v < 0 || v >= P.n_ops) return false;
+    const int64_t n = P.cfg_off[v + 1] - P.cfg_off[v];
+    return mode == LLAMA_MODE_ALPHA ? (int64_t)key < 2 * n : (key >= 0x8000u || (int64_t)key < n);
+#else
+    return true;
+#endif
+}
+
 // Backend lambda(x) of op-local configuration x: the segment containing it.
 __device__ __forceinline__ int backend_of(const int32_t *hw_off_v, int H, int x) {
     int lam = 0;
@@ -497,9 +511,11 @@ __device__ __forceinline__ void count_invocation(const DevProblem &P, int64_t i,
 // <= SLO < 2^31.  The scoring kernel turns it into the slack per backend
 // (Algorithm 1 through the critical path); a non-positive remaining time gives
 // slack 0 for every backend, since queueing times are >= 0.
-__device__ __forceinline__ void scatter_invocation(const BucketScratch &S, const int32_t *op_start, int64_t i,
-                                                   int32_t g, int32_t slot, int64_t rbase) {
+__device__ __forceinline__ void scatter_invocation(const DevProblem &P, const BucketScratch &S,
+                                                   const int32_t *op_start, int64_t i, int32_t g, int32_t slot,
+                                                   int64_t rbase) {
     const int64_t pos = (int64_t)op_start[g] + slot;
+    if (!LLAMA_IN_BOUNDS(P, pos >= 0 && pos < S.n_inv, LLAMA_CHECK_SCATTER)) return;
     S.b_inv[pos] = (int32_t)i;
     S.b_rem[pos] = (int32_t)max(rbase, (int64_t)0);
 }
@@ -606,10 +622,10 @@ __global__ void __launch_bounds__(256) k_bucket(DevProblem P, int64_t n_inv, con
     asm volatile("griddepcontrol.launch_dependents;");
 #pragma unroll
     for (int j = 0; j < kKeep; ++j)
-        if (kg[j] >= 0) scatter_invocation(S, op_start, base + j * stride, kg[j], ks[j], kr[j]);
+        if (kg[j] >= 0) scatter_invocation(P, S, op_start, base + j * stride, kg[j], ks[j], kr[j]);
     for (int64_t i = base + kKeep * stride; i < n_inv; i += stride) {
         const int32_t g = S.gop[i];
-        if (g >= 0) scatter_invocation(S, op_start, i, g, S.slot[i], S.rbase[i]);
+        if (g >= 0) scatter_invocation(P, S, op_start, i, g, S.slot[i], S.rbase[i]);
     }
 }
 
@@ -796,7 +812,10 @@ __device__ __forceinline__ void tile_begin(const DevProblem &P, const BucketScra
 #pragma unroll
     for (int u = 0; u < IPT; ++u) {
         const int32_t j = T.g * IPT + u;
-        T.inv[u] = j < T.m ? S.b_inv[tile.y + j] : -1;
+        T.inv[u] = j < T.m && LLAMA_IN_BOUNDS(P, tile.y + j >= 0 && tile.y + j < S.n_inv, LLAMA_CHECK_TILE)
+                       ? S.b_inv[tile.y + j]
+                       : -1;
+        if (!LLAMA_IN_BOUNDS(P, T.inv[u] < S.n_inv, LLAMA_CHECK_TILE)) T.inv[u] = -1;
         T.any |= T.inv[u] >= 0;
         T.best[u] = 0xFFFFFFFFu;
     }
@@ -963,6 +982,7 @@ __device__ __forceinline__ void finish_tile(const DevProblem &P, const BucketScr
         if (T.s != (u & (T.L - 1)) || T.inv[u] < 0) continue;
         const int32_t i = T.inv[u];
         int4 d;
+        if (!LLAMA_IN_BOUNDS(P, decode_key_ok(P, T.v, key[u], MODE), LLAMA_CHECK_DECODE)) continue;
         if (MODE == LLAMA_MODE_ALPHA) d = P.dec[2 * (int64_t)T.cbase + key[u]];
         else d = key[u] < 0x8000u ? P.dec[(int64_t)T.cbase + key[u]] : P.dfast[T.v];
         const int32_t sl = slack_at(S, T, tc, u, d.x >> 16);
@@ -988,6 +1008,13 @@ __device__ __forceinline__ void stage_chunk(const DevProblem &P, int64_t p0, int
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     // whole 16-byte words of the distinct latencies: dlat has npad >= dn entries here
     const uint32_t db = with_dlat ? (uint32_t)((dn + 3) / 4) * 16u : 0u;
+    // checked build: a range outside the padded tables is not copied (the
+    // mbarrier still completes, with no bytes expected)
+    if (!LLAMA_IN_BOUNDS(P, p0 >= 0 && c0 >= 0 && p0 + c0 + cn <= P.n_pad && p0 + (int64_t)db / 4 <= P.n_pad,
+                         LLAMA_CHECK_STAGE)) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(0u) : "memory");
+        return;
+    }
     const uint32_t bytes = (uint32_t)cn * (MODE == LLAMA_MODE_ALPHA ? 6u : 4u) + db;
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
     if (with_dlat) bulk_g2s(dl_s, P.dlat + p0, db, bar);
@@ -1374,7 +1401,10 @@ __global__ void __launch_bounds__(256, 4) k_counts(DevProblem P, BucketScratch S
                                                   : (int64_t)S.ctrl[kCtrlPositions];
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n_pos;
          p += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t g = S.gop[S.b_inv[p]];
+        const int32_t bi = S.b_inv[p];
+        if (!LLAMA_IN_BOUNDS(P, bi >= 0 && bi < S.n_inv, LLAMA_CHECK_COUNTS)) continue;
+        const int32_t g = S.gop[bi];
+        if (!LLAMA_IN_BOUNDS(P, g >= 0 && g < P.n_ops, LLAMA_CHECK_COUNTS)) continue;
         if (P.dlat_n[g] <= dl_cap) continue;
         int32_t lo[MAXH];
         counts_all_backends<MAXH, true>(P, g, P.ref[g], P.cp[g], P.cp_magic[g], (int64_t)S.b_rem[p], lo);
@@ -1404,6 +1434,8 @@ __device__ llama_decision stair_decide(const DevProblem &P, int32_t g, int64_t r
     for (int h = 0; h < LLAMA_MAX_HW; ++h)
         if (h < H) key = min(key, (uint32_t)__ldg(sg + (int64_t)h * stride + lo[h]));
     const int64_t cb = P.cfg_off[g];
+    if (!LLAMA_IN_BOUNDS(P, decode_key_ok(P, g, key, P.mode), LLAMA_CHECK_DECODE))
+        key = P.mode == LLAMA_MODE_ALPHA ? 0u : 0xFFFFu;  // a key in bounds (the decision is then wrong)
     int4 dd;
     if (P.mode == LLAMA_MODE_ALPHA) dd = P.dec[2 * cb + key];
     else dd = key != 0xFFFFu ? P.dec[cb + key] : P.dfast[g];
@@ -2189,6 +2221,7 @@ __global__ void __launch_bounds__(kLoopThreads) k_loop_tick(DevProblem P, LoopDe
             const long long k = min((long long)max(a.dispatch[h], 0), len);
             for (long long j = 0; j < k; ++j) {
                 const int32_t slot = L.cq[(int64_t)h * L.cq_stride + (S.cq_head[h] + j) % L.cq_cap[h]];
+                if (!LLAMA_IN_BOUNDS(P, slot >= 0 && slot < L.slots, LLAMA_CHECK_LOOP)) continue;
                 S.s_cq[h] -= L.slot_lr_commit[slot];
                 L.free_stack[ft++] = slot;
             }
@@ -2296,6 +2329,7 @@ __global__ void __launch_bounds__(kLoopThreads) k_loop_tick(DevProblem P, LoopDe
     if (tid < C) {
         while (src + 1 < H && tid >= sh_w[src + 1]) ++src;
         slot = L.sq[(int64_t)src * L.slots + (sh_sq_head[src] + (tid - sh_w[src])) % L.slots];
+        if (!LLAMA_IN_BOUNDS(P, slot >= 0 && slot < L.slots, LLAMA_CHECK_LOOP)) slot = 0;
         const int32_t d = L.slot_dag[slot];
         g2 = P.dag_op_off[d] + L.slot_opl[slot];
         const long long rb = P.slo[d] - (a.now - L.slot_start[slot]);

@@ -2,7 +2,10 @@
 // validation, DAG levelling, padded table layout, device memory, launches.
 #include <cub/cub.cuh>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
+#include <chrono>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -53,6 +56,13 @@ struct DeviceGuard {
 };
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// An NVTX range over an API call (shown by Nsight tools; costs nothing when no
+// tool is attached).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
 
 }  // namespace
 
@@ -105,6 +115,7 @@ struct llama_ctx {
     int64_t mean_npad = 0;
     DevBuf ref, cp, cp_magic;
     DevBuf q_dev;  // [LLAMA_MAX_HW] queueing time per backend, read by the kernels
+    DevBuf check;  // the -DLLAMA_CHECK build's violation bits
     DevBuf q_sums; // scratch of Eq. 2
 
     // bucketing scratch
@@ -125,6 +136,11 @@ struct llama_ctx {
     int32_t wait_tries = kMaxWaitTries;  // polls of a bucketing grid barrier (llama_set_wait_limit)
     cudaEvent_t trace[LLAMA_TRACE_EVENTS] = {};
     bool tracing = false;
+
+    // per-call statistics of the blocking scheduling call (llama_set_stats_file)
+    FILE *stats = nullptr;
+    int64_t stats_calls = 0;
+    cudaEvent_t stats_ev[2] = {};
 
     // CUDA graph of the last untraced scheduling call (opts.use_graph): replayed
     // while the call's arguments and the context's buffers stay the same; `now`
@@ -150,6 +166,12 @@ struct llama_ctx {
     int fail(int code, const std::string &msg) {
         err = msg;
         return code;
+    }
+    void close_stats() {
+        if (stats) fclose(stats);
+        stats = nullptr;
+        for (cudaEvent_t &e : stats_ev)
+            if (e) cudaEventDestroy(e), e = nullptr;
     }
     int cuda_fail(cudaError_t e, const char *what) {
         err = std::string(what) + ": " + cudaGetErrorString(e);
@@ -238,6 +260,9 @@ DevProblem make_problem(const llama_ctx *c) {
     P.q = c->q_dev.as<int64_t>();
     P.alpha_num = c->opts.alpha_num;
     P.alpha_den = c->opts.alpha_den;
+    P.n_cfg = c->n_cfg;
+    P.n_pad = c->n_pad;
+    P.check = c->check.as<unsigned int>();
     P.wait_tries = c->wait_tries;
     return P;
 }
@@ -641,7 +666,8 @@ extern "C" int llama_create(llama_ctx **out, const llama_opts *opts) {
         cudaEventCreateWithFlags(&c->order_ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaMallocHost(&c->h_ctrl, sizeof(unsigned long long) * kCtrlWords) != cudaSuccess ||
         c->q_dev.alloc(8 * LLAMA_MAX_HW) != cudaSuccess || c->q_sums.alloc(8 * LLAMA_MAX_HW) != cudaSuccess ||
-        cudaMemset(c->q_dev.p, 0, 8 * LLAMA_MAX_HW) != cudaSuccess) {
+        cudaMemset(c->q_dev.p, 0, 8 * LLAMA_MAX_HW) != cudaSuccess || c->check.alloc(16) != cudaSuccess ||
+        cudaMemset(c->check.p, 0, 16) != cudaSuccess) {
         cudaGetLastError();
         delete c;
         return LLAMA_ECUDA;
@@ -668,6 +694,7 @@ extern "C" void llama_destroy(llama_ctx *c) {
         if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
         if (c->order_ev) cudaEventDestroy(c->order_ev);
         if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
+        c->close_stats();
         delete c;  // DevBuf destructors free device memory with the device current
     }
 }
@@ -788,6 +815,7 @@ extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cf
                                   const int32_t *batch, const int32_t *res,
                                   const int32_t *res_total) {
     if (!c) return LLAMA_EINVAL;
+    Range range("llama:set_profiles");
     const int H = c->opts.n_hw;
     const bool alpha = c->opts.mode == LLAMA_MODE_ALPHA;
     if (n_ops < 1 || !cfg_off || !hw_off || !lat_us || !cost_nd || !ref_cfg)
@@ -1035,6 +1063,35 @@ extern "C" int llama_set_count_pass(llama_ctx *c, int32_t mode) {
     return LLAMA_OK;
 }
 
+extern "C" int llama_check_build(void) {
+#ifdef LLAMA_CHECK
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+extern "C" int llama_check_word(llama_ctx *c, uint32_t *bits, int32_t clear) {
+    if (!c || !bits) return LLAMA_EINVAL;
+    DeviceGuard g(c->opts.device);
+    LL_CUDA(c, cudaDeviceSynchronize());
+    LL_CUDA(c, cudaMemcpy(bits, c->check.p, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    if (clear) LL_CUDA(c, cudaMemset(c->check.p, 0, sizeof(uint32_t)));
+    return LLAMA_OK;
+}
+
+extern "C" int llama_set_stats_file(llama_ctx *c, const char *path) {
+    if (!c) return LLAMA_EINVAL;
+    DeviceGuard g(c->opts.device);
+    c->close_stats();
+    if (!path || !*path) return LLAMA_OK;
+    c->stats = fopen(path, "a");
+    if (!c->stats) return c->fail(LLAMA_EINVAL, std::string("set_stats_file: cannot open ") + path);
+    LL_CUDA(c, cudaEventCreate(&c->stats_ev[0]));
+    LL_CUDA(c, cudaEventCreate(&c->stats_ev[1]));
+    return LLAMA_OK;
+}
+
 extern "C" int llama_set_wait_limit(llama_ctx *c, int32_t tries) {
     if (!c) return LLAMA_EINVAL;
     if (tries < 0 || tries > kMaxWaitTries)
@@ -1062,6 +1119,7 @@ extern "C" int llama_feedback(llama_ctx *c, int64_t n, const int32_t *op, const 
                               const int32_t *lat_us, const int64_t *cost_nd, int32_t beta_num, int32_t beta_den,
                               int64_t *rejected, void *stream) {
     if (!c) return LLAMA_EINVAL;
+    Range range("llama:feedback");
     if (n < 0 || n >= INT32_MAX || (n > 0 && (!op || !cfg || !lat_us || !cost_nd)))
         return c->fail(LLAMA_EINVAL, "feedback: bad arguments");
     if (beta_den < 1 || beta_den > LLAMA_MAX_ALPHA || beta_num < 0 || beta_num > beta_den)
@@ -1257,6 +1315,7 @@ extern "C" int llama_schedule_async(llama_ctx *c, int64_t n_inv, const int32_t *
                                     const int32_t *op_local, const int64_t *start_us, int64_t now_us,
                                     llama_decision *out, void *stream) {
     if (!c) return LLAMA_EINVAL;
+    Range range("llama:schedule_async");
     int rc = check_inv_args(c, n_inv, dag, op_local, start_us, out);
     if (rc) return rc;
     if ((rc = check_ready(c))) return rc;
@@ -1269,6 +1328,8 @@ extern "C" int llama_schedule_async(llama_ctx *c, int64_t n_inv, const int32_t *
 extern "C" int llama_schedule(llama_ctx *c, int64_t n_inv, const int32_t *dag, const int32_t *op_local,
                               const int64_t *start_us, int64_t now_us, llama_decision *out) {
     if (!c) return LLAMA_EINVAL;
+    Range range("llama:schedule");
+    const auto t_call = std::chrono::steady_clock::now();
     int rc = check_inv_args(c, n_inv, dag, op_local, start_us, out);
     if (rc) return rc;
     if ((rc = check_ready(c))) return rc;
@@ -1291,11 +1352,30 @@ extern "C" int llama_schedule(llama_ctx *c, int64_t n_inv, const int32_t *dag, c
     if (!rd) LL_CUDA(c, cudaMemcpyAsync((void *)d_dag, dag, 4 * n_inv, cudaMemcpyHostToDevice, s));
     if (!ro) LL_CUDA(c, cudaMemcpyAsync((void *)d_opl, op_local, 4 * n_inv, cudaMemcpyHostToDevice, s));
     if (!rs) LL_CUDA(c, cudaMemcpyAsync((void *)d_start, start_us, 8 * n_inv, cudaMemcpyHostToDevice, s));
+    if (c->stats) LL_CUDA(c, cudaEventRecord(c->stats_ev[0], s));
     if ((rc = launch_schedule(c, n_inv, d_dag, d_opl, d_start, now_us, d_out, s))) return rc;
+    if (c->stats) LL_CUDA(c, cudaEventRecord(c->stats_ev[1], s));
     if (!outd) LL_CUDA(c, cudaMemcpyAsync(out, d_out, sizeof(llama_decision) * n_inv, cudaMemcpyDeviceToHost, s));
     LL_CUDA(c, cudaMemcpyAsync(c->h_ctrl, c->ws.ctrl.as<unsigned long long>() + kCtrlWords,
                                sizeof(unsigned long long) * kStatusWords, cudaMemcpyDeviceToHost, s));
     LL_CUDA(c, cudaStreamSynchronize(s));
+    if (c->stats) {
+        // one JSON object per line: the call's size, its kernels, what it found
+        // and how long it took on the device (kernels only) and on the host (whole call)
+        float dev_ms = 0.f;
+        cudaEventElapsedTime(&dev_ms, c->stats_ev[0], c->stats_ev[1]);
+        const double host_us =
+            std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t_call).count();
+        fprintf(c->stats,
+                "{\"call\": %lld, \"n_inv\": %lld, \"now_us\": %lld, \"method\": \"%s\", \"launches\": %d, "
+                "\"graph\": %s, \"invalid\": %llu, \"timeout\": %s, \"device_us\": %.3f, \"host_us\": %.3f, "
+                "\"inputs\": \"%s\"}\n",
+                (long long)c->stats_calls++, (long long)n_inv, (long long)now_us,
+                c->method == LLAMA_METHOD_STAIRCASE ? "staircase" : "scan", c->last_launches,
+                c->opts.use_graph && !c->tracing ? "true" : "false", c->h_ctrl[0], c->h_ctrl[1] ? "true" : "false",
+                1e3 * dev_ms, host_us, rd && ro && rs ? "read in place" : "copied");
+        fflush(c->stats);
+    }
     if (c->h_ctrl[1])
         return c->fail(LLAMA_ETIMEOUT, "schedule: a bounded device wait gave up (bucketing barrier or table "
                                        "staging); valid invocations are flagged LLAMA_FLAG_TIMEOUT in out");

@@ -141,7 +141,19 @@ struct DevProblem {
     // polls of a grid barrier of k_bucket before it gives up (kMaxWaitTries
     // unless a caller lowers it to exercise the give-up path)
     int32_t wait_tries;
+    int64_t n_cfg, n_pad;  // configurations, padded table entries (bounds of the checked build)
+    unsigned int *check;   // the -DLLAMA_CHECK build's violation bits (LLAMA_CHECK_*)
 };
+
+// Bounds checks of the -DLLAMA_CHECK build: a check that fails sets its bit in
+// the context's check word (P.check) and the guarded access is skipped -- no
+// trap, the call completes and llama_check_word reports it.  In the normal
+// build every check is the constant true.
+#ifdef LLAMA_CHECK
+#define LLAMA_IN_BOUNDS(P, cond, bit) ((cond) ? true : (atomicOr((P).check, (unsigned)(bit)), false))
+#else
+#define LLAMA_IN_BOUNDS(P, cond, bit) true
+#endif
 
 struct BucketScratch {
     int32_t *cnt;             // [n_ops*kCntStride] invocations per op: zero when a call starts

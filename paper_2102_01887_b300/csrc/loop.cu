@@ -3,6 +3,8 @@
 // (Section 4.4).  The host only writes requests into a page-locked ring,
 // launches ticks (k_loop_tick, kernels.cu) and reads result records from a
 // second page-locked ring; every queue, sum and slot lives on the device.
+#include <nvtx3/nvToolsExt.h>
+
 #include <atomic>
 #include <cstring>
 #include <new>
@@ -213,8 +215,10 @@ extern "C" int llama_loop_tick(llama_loop *lp, int64_t now_us, const int32_t *di
         if (a.dispatch[h] < 0) return loop_fail(lp, LLAMA_EINVAL, "tick: negative dispatch count");
     }
     CurrentDevice guard(lp->device);
+    nvtxRangePushA("llama:loop_tick");
     std::atomic_thread_fence(std::memory_order_seq_cst);
     const cudaError_t e = enqueue_loop_tick(lp->P, lp->L, a, lp->stream);
+    nvtxRangePop();
     if (e != cudaSuccess) return loop_cuda(lp, e, "tick launch");
     return LLAMA_OK;
 }

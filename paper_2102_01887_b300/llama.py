@@ -17,6 +17,9 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libllama.so")
+# the -DLLAMA_CHECK build (bounds checks that set bits instead of trapping); a
+# process selects it with LLAMA_LIB=check before the first load
+CHECK_LIB_PATH = os.path.join(_HERE, "libllama_check.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ENOTREADY, ETIMEOUT = 0, -1, -2, -3, -4, -5
 MODE_COST_FIRST, MODE_ALPHA = 0, 1
@@ -42,7 +45,8 @@ EXPORTS = ("llama_create", "llama_destroy", "llama_set_dags", "llama_set_profile
            "llama_server_create", "llama_server_destroy", "llama_server_submit", "llama_server_poll",
            "llama_server_drain", "llama_server_stats_get", "llama_queue_time", "llama_feedback",
            "llama_get_profiles", "llama_backend_objectives", "llama_commit_order",
-           "llama_static_status", "llama_set_wait_limit", "llama_alu_peak",
+           "llama_static_status", "llama_set_wait_limit", "llama_alu_peak", "llama_set_stats_file",
+           "llama_check_build", "llama_check_word",
            "llama_loop_create", "llama_loop_destroy", "llama_loop_submit", "llama_loop_tick", "llama_loop_poll",
            "llama_loop_sync", "llama_loop_state_get", "llama_loop_refresh", "llama_loop_ticks_done")
 TRACE_EVENTS = 3
@@ -85,9 +89,12 @@ _lib = None
 _lock = threading.Lock()
 
 
-def load(path: str = LIB_PATH) -> ctypes.CDLL:
-    """Load the CUDA library; raises if it has not been built."""
+def load(path: str = None) -> ctypes.CDLL:
+    """Load the CUDA library (the checked build when LLAMA_LIB=check); raises if
+    it has not been built."""
     global _lib
+    if path is None:
+        path = CHECK_LIB_PATH if os.environ.get("LLAMA_LIB") == "check" else LIB_PATH
     with _lock:
         if _lib is not None:
             return _lib
@@ -149,6 +156,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "llama_static_status": ([vp, vp, vp, vp], ctypes.c_int),
             "llama_set_wait_limit": ([vp, i32], ctypes.c_int),
             "llama_alu_peak": ([i32, i32, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+            "llama_set_stats_file": ([vp, ctypes.c_char_p], ctypes.c_int),
+            "llama_check_build": ([], ctypes.c_int),
+            "llama_check_word": ([vp, vp, i32], ctypes.c_int),
             "llama_loop_create": ([vp, ctypes.POINTER(llama_loop_opts), ctypes.POINTER(vp)], ctypes.c_int),
             "llama_loop_destroy": ([vp], None),
             "llama_loop_submit": ([vp, vp, i64], ctypes.c_int),
@@ -483,6 +493,18 @@ def llama_static_status(ctx, stream=None) -> tuple[int, int]:
     _check(ctx, load().llama_static_status(ctx, ctypes.c_void_p(stream.cuda_stream), ctypes.byref(inv),
                                            ctypes.byref(tmo)))
     return inv.value, tmo.value
+
+
+def llama_check_word(ctx, clear: bool = True) -> int:
+    """Violation bits of the checked build (LLAMA_CHECK_*; 0 in a normal build)."""
+    w = ctypes.c_uint32()
+    _check(ctx, load().llama_check_word(ctx, ctypes.byref(w), 1 if clear else 0))
+    return w.value
+
+
+def llama_set_stats_file(ctx, path) -> None:
+    """Append one JSON line per blocking llama_schedule call to path (None closes it)."""
+    _check(ctx, load().llama_set_stats_file(ctx, None if path is None else str(path).encode()))
 
 
 def llama_set_wait_limit(ctx, tries: int) -> None:

@@ -1,0 +1,66 @@
+"""Auxiliary subsystems on the GPU: per-call statistics (JSONL), the
+bounds-checked build (-DLLAMA_CHECK) on the parity workloads, and NVTX ranges
+compiled into the library."""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+from paper_2102_01887_b300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.mark.gpu
+def test_stats_file_records_every_blocking_call(cuda_device, tmp_path):
+    from paper_2102_01887_b300 import build, llama as L
+    build.build()
+    p, inv = W.medium(n_inv=5000)
+    bad = W.Invocations(np.where(np.arange(inv.n) % 50 == 0, -1, inv.dag).astype(np.int32), inv.op_local,
+                        inv.start_us, inv.now_us)
+    path = tmp_path / "calls.jsonl"
+    with L.Scheduler(p, use_graph=True) as s:
+        L.llama_set_stats_file(s.ctx, path)
+        s.schedule(inv)
+        s.schedule(bad)
+        s.schedule(inv)
+        L.llama_set_stats_file(s.ctx, None)
+        s.schedule(inv)  # not recorded
+    rows = [json.loads(line) for line in open(path)]
+    assert [r["call"] for r in rows] == [0, 1, 2]
+    assert all(r["n_inv"] == inv.n and r["launches"] >= 2 and r["device_us"] > 0 and r["host_us"] > 0
+               for r in rows)
+    assert [r["invalid"] for r in rows] == [0, int((bad.dag < 0).sum()), 0]
+    assert not any(r["timeout"] for r in rows) and rows[0]["graph"] is True
+
+
+@pytest.mark.gpu
+def test_checked_build_parity(cuda_device):
+    from paper_2102_01887_b300 import build
+    build.build_check()
+    env = dict(os.environ, LLAMA_LIB="check")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "tests", "checked_build_parity.py")], env=env,
+                       capture_output=True, text=True, timeout=1200)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-4000:]
+    assert "no bounds check failed" in r.stdout
+
+
+def test_checked_build_compiles_and_says_so():
+    import ctypes
+    from paper_2102_01887_b300 import build
+    so = build.build_check()
+    assert ctypes.CDLL(so).llama_check_build() == 1
+    assert ctypes.CDLL(build.build()).llama_check_build() == 0
+
+
+def test_nvtx_ranges_are_compiled_in():
+    from paper_2102_01887_b300 import build
+    so = build.build()
+    text = open(so, "rb").read()
+    # the range names (distinct from every exported symbol name)
+    for name in (b"llama:schedule\0", b"llama:schedule_async\0", b"llama:set_profiles\0", b"llama:feedback\0",
+                 b"llama:loop_tick\0"):
+        assert name in text, name
