@@ -86,6 +86,41 @@ def test_dags_of_every_size(L, mode, alpha, method):
     assert_same(got, exp)
 
 
+@pytest.mark.parametrize("shape", ["chain", "branching"])
+def test_slack_division_at_its_extremes(L, shape, method):
+    """Algorithm 1's division floor(ref * R / cp) at the edge of its range:
+    reference latencies and remaining times within a few thousand of 2^31
+    (ref * R just below 2^62) over long paths (cp up to about 2^40), so the
+    multiply-high by floor((2^64 - 1) / cp) and its one correction are checked
+    where they are tightest; slack, critical path and decisions bit-exact."""
+    rng = np.random.default_rng(7 if shape == "chain" else 8)
+    n = 600
+    top = 2**31 - 2
+    if shape == "chain":
+        succ = [[v + 1] for v in range(n - 1)] + [[]]
+        ref = (top - rng.integers(0, 5000, n)).tolist()
+    else:  # random branching over later ops, reference latencies spread over [2^20, 2^31)
+        succ = [sorted({int(x) for x in rng.integers(v + 1, n, rng.integers(1, 4))}) if v < n - 1 else []
+                for v in range(n)]
+        ref = np.minimum(top, np.exp(rng.uniform(np.log(2.0**20), np.log(2.0**31), n))).astype(np.int64).tolist()
+    extra = [[(int(rng.integers(0, 3)), int(rng.integers(1, top)), int(rng.integers(0, 2**40)))
+              for _ in range(int(rng.integers(1, 6)))] for _ in range(n)]
+    p = single_table_problem(succ, ref, slo=2**31 - 1, q=(0, 7, 123_456), extra=extra)
+    m = 4000
+    ops = rng.integers(0, n, m).astype(np.int32)
+    now = 10**12
+    start = now - rng.integers(0, 3000, m)
+    start[::50] = now - rng.integers(0, 2**31 - 1, start[::50].shape[0])  # some far into their target
+    inv = W.Invocations(np.zeros(m, np.int32), ops, start.astype(np.int64), now)
+    cp = oracle.critical_path(p)
+    assert cp.max() > 2**38
+    with L.Scheduler(p, method=method) as s:
+        assert np.array_equal(s.critical_path(), cp)
+        assert np.array_equal(s.slack(inv).astype(np.int64), oracle.slacks(p, inv))
+    got, exp = run_both(L, p, inv, method=method)
+    assert_same(got, exp, shape)
+
+
 @pytest.mark.parametrize("seed", range(20))
 def test_slack_random_small(L, seed):
     p, inv = W.random_small(seed)
