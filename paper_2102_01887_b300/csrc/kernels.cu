@@ -844,15 +844,48 @@ __device__ __forceinline__ int32_t slack_at(const BucketScratch &S, const TileSt
 
 // Counts c(u, h) of distinct latencies below the slack of invocation u for
 // backend h, into cg[u * H + h], from the sorted list dl (shared memory: the
-// lanes of a group share the bisections).
+// lanes of a group share the bisections).  A lane advances its searches in
+// lockstep, up to four at a time, so their dependent shared-memory loads
+// overlap instead of following one another.
 template <int IPT>
 __device__ __forceinline__ void counts_from_shared(const BucketScratch &S, const TileState<IPT> &T,
                                                    const TileConst &tc, int H, const int32_t *dl, uint16_t *cg) {
     if (!T.any) return;
-    for (int t = T.s; t < IPT * H; t += T.L) {
-        const int u = t / H, h = t - u * H;
-        const int32_t iu = inv_at(T, u);
-        cg[t] = iu >= 0 ? (uint16_t)count_below(dl, T.dn, slack_at(S, T, tc, u, h)) : 0;
+    constexpr int kLock = 4;
+    const int nt = IPT * H;
+    for (int t0 = T.s; t0 < nt; t0 += kLock * T.L) {
+        int32_t lo[kLock], hi[kLock], sl[kLock];
+#pragma unroll
+        for (int j = 0; j < kLock; ++j) {
+            const int t = t0 + j * T.L;
+            const int u = t / H;
+            const bool act = t < nt && inv_at(T, u) >= 0;
+            sl[j] = act ? slack_at(S, T, tc, u, t - u * H) : 0;
+            lo[j] = 0;
+            hi[j] = act ? T.dn : 0;
+        }
+        for (;;) {
+            int32_t val[kLock];
+            bool more = false;
+#pragma unroll
+            for (int j = 0; j < kLock; ++j) {  // every probe's load first
+                const bool a = lo[j] < hi[j];
+                more |= a;
+                val[j] = a ? dl[(lo[j] + hi[j]) >> 1] : 0;
+            }
+            if (!more) break;
+#pragma unroll
+            for (int j = 0; j < kLock; ++j) {
+                if (lo[j] >= hi[j]) continue;
+                const int32_t mid = (lo[j] + hi[j]) >> 1;
+                if (val[j] < sl[j]) lo[j] = mid + 1; else hi[j] = mid;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kLock; ++j) {
+            const int t = t0 + j * T.L;
+            if (t < nt) cg[t] = (uint16_t)lo[j];  // 0 for a group slot without an invocation
+        }
     }
 }
 

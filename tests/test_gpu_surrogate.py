@@ -189,6 +189,44 @@ def test_layer1_configuration_part_is_kept_while_valid(L, world):
             assert np.array_equal(sg.schedule(cfg_x, sub, content), fresh())
 
 
+def test_decisions_are_the_same_alone_and_in_any_mix(L, world):
+    """Serving batches whatever has arrived: an invocation's surrogate decision
+    must not depend on the batch it lands in.  Every pair row is computed on its
+    own (its own inputs, the same weights and summation order) and the
+    per-invocation minimum is order-free, so decisions are bit-identical alone,
+    in one batch, and in a shuffled batch with other invocations."""
+    from paper_2102_01887_b300 import surrogate as S
+    p, inv, cw = world
+    sub = inv.subset(np.arange(0, inv.n, 1024))  # 64 invocations
+    content = W.invocation_content(4, sub.n)
+    with L.Scheduler(p) as s, L.MLP(max_batch=1024) as net:
+        net.set_params(M.pack(perturbed_params(31)).astype(np.float32))
+        cfg_x = S.config_inputs(p, cw)
+        with S.SurrogateScheduler(s, net, max_inv=4096, max_pairs=1 << 20) as sg:
+            sg.set_margin(0.02)
+            together = sg.schedule(cfg_x, sub, content)
+            alone = np.concatenate([sg.schedule(cfg_x, sub.subset(np.asarray([i])),
+                                                W.Content(content.n_obj[i:i + 1], content.motion[i:i + 1],
+                                                          content.in_res[i:i + 1]))
+                                    for i in range(sub.n)])
+            rng = np.random.default_rng(2)
+            other = inv.subset(rng.integers(0, inv.n, 500))
+            oc = W.invocation_content(5, other.n)
+            mix_idx = rng.permutation(sub.n + other.n)
+            dag = np.concatenate([sub.dag, other.dag])[mix_idx]
+            opl = np.concatenate([sub.op_local, other.op_local])[mix_idx]
+            st = np.concatenate([sub.start_us, other.start_us])[mix_idx]
+            mc = W.Content(*(np.concatenate([getattr(content, k), getattr(oc, k)])[mix_idx]
+                             for k in ("n_obj", "motion", "in_res")))
+            mixed = sg.schedule(cfg_x, W.Invocations(dag, opl, st, sub.now_us), mc)
+            back = np.empty(sub.n, dtype=mixed.dtype)
+            pos = np.argsort(mix_idx)[:sub.n]  # where each of sub's invocations went
+            back[:] = mixed[pos]
+    for k in ("cfg", "lat", "cost", "slack", "flags"):
+        assert np.array_equal(together[k], alone[k]), k
+        assert np.array_equal(together[k], back[k]), k
+
+
 @pytest.mark.slow
 def test_edge_cases(L, world):
     """A single invocation; a call in which every invocation is invalid (no pair
