@@ -779,6 +779,7 @@ struct TileState {
     int32_t cbase;  // cfg_off of the op
     int64_t p0;
     int32_t inv[IPT];
+    int32_t rem[IPT];  // remaining time before queueing of each invocation (its bucket entry)
     uint32_t best[IPT];
     bool any;
     // the op's reference latency, critical path and floor((2^64-1) / critical
@@ -812,9 +813,9 @@ __device__ __forceinline__ void tile_begin(const DevProblem &P, const BucketScra
 #pragma unroll
     for (int u = 0; u < IPT; ++u) {
         const int32_t j = T.g * IPT + u;
-        T.inv[u] = j < T.m && LLAMA_IN_BOUNDS(P, tile.y + j >= 0 && tile.y + j < S.n_inv, LLAMA_CHECK_TILE)
-                       ? S.b_inv[tile.y + j]
-                       : -1;
+        const bool in = j < T.m && LLAMA_IN_BOUNDS(P, tile.y + j >= 0 && tile.y + j < S.n_inv, LLAMA_CHECK_TILE);
+        T.inv[u] = in ? S.b_inv[tile.y + j] : -1;
+        T.rem[u] = in ? S.b_rem[tile.y + j] : 0;
         if (!LLAMA_IN_BOUNDS(P, T.inv[u] < S.n_inv, LLAMA_CHECK_TILE)) T.inv[u] = -1;
         T.any |= T.inv[u] >= 0;
         T.best[u] = 0xFFFFFFFFu;
@@ -824,7 +825,7 @@ __device__ __forceinline__ void tile_begin(const DevProblem &P, const BucketScra
     T.mg = P.cp_magic[T.v];
 }
 
-// inv[u] for a runtime u, without a runtime index into registers.
+// inv[u] and rem[u] for a runtime u, without a runtime index into registers.
 template <int IPT>
 __device__ __forceinline__ int32_t inv_at(const TileState<IPT> &T, int u) {
     int32_t iu = T.inv[0];
@@ -833,13 +834,22 @@ __device__ __forceinline__ int32_t inv_at(const TileState<IPT> &T, int u) {
     return iu;
 }
 
+template <int IPT>
+__device__ __forceinline__ int32_t rem_at(const TileState<IPT> &T, int u) {
+    int32_t r = T.rem[0];
+#pragma unroll
+    for (int w = 1; w < IPT; ++w) r = u == w ? T.rem[w] : r;
+    return r;
+}
+
 // Slack of the tile's invocation u for backend h: Algorithm 1 through the
 // critical path, floor(ref * (rem - Q[h]) / cp), 0 once the target has passed,
-// rem being the invocation's remaining time stored beside its bucket entry.
+// rem being the invocation's remaining time stored beside its bucket entry
+// (loaded with the tile's invocation indices).
 template <int IPT>
 __device__ __forceinline__ int32_t slack_at(const BucketScratch &S, const TileState<IPT> &T, const TileConst &tc,
                                             int u, int h) {
-    return slack_of(T.ref, T.cp, T.mg, (int64_t)S.b_rem[T.pos0 + u] - tc.q[h]);
+    return slack_of(T.ref, T.cp, T.mg, (int64_t)rem_at(T, u) - tc.q[h]);
 }
 
 // Counts c(u, h) of distinct latencies below the slack of invocation u for
