@@ -721,9 +721,10 @@ def run_surrogate(args):
 
 
 def serve_loop_rate(L, lp, inv, rate: float, seconds: float, rng, id0: int, ticks_in_flight: int = 2):
-    """Poisson arrivals at `rate` into the device loop: each arrival is submitted
-    as its time comes, ticks run back to back (at most ticks_in_flight queued),
-    every tick dispatches what the previous ticks committed (backends keep up).
+    """Poisson arrivals at `rate` into the device loop.  The library's driver
+    thread runs the ticks back to back (at most ticks_in_flight queued), each
+    dispatching every committed invocation (backends that keep up); this
+    thread only submits arrivals as their time comes and polls the records.
     Latency: arrival -> speculative record seen by the host, and -> commit record."""
     n = int(rate * seconds)
     arrive = np.cumsum(rng.exponential(1e9 / rate, n)).astype(np.int64)  # ns after t0
@@ -733,30 +734,21 @@ def serve_loop_rate(L, lp, inv, rate: float, seconds: float, rng, id0: int, tick
     req["dag"], req["op_local"], req["start_us"] = inv.dag[idx], inv.op_local[idx], inv.start_us[idx]
     spec_ns = np.full(n, -1, np.int64)
     com_ns = np.full(n, -1, np.int64)
-    committed_by_hw = np.zeros(lp.n_hw, np.int64)
-    dispatched_by_hw = np.zeros_like(committed_by_hw)
     st0 = lp.state()
-    launched = st0["ticks"]
+    lp.start(inv.now_us, ticks_in_flight)
     t0 = time.perf_counter_ns()
     k = 0
     n_seen = 0
-    while n_seen < 2 * n - int((req["dag"] < 0).sum()):
+    while n_seen < 2 * n:
         t = time.perf_counter_ns() - t0
         j = int(np.searchsorted(arrive, t, side="right"))
         # arrivals enter the ring as far as it has room; the rest waits for the
-        # ticks below to drain it (a full ring never blocks this loop)
+        # ticks to drain it (a full ring never blocks this loop)
         while j > k:
             m = min(j - k, 4096)
             if lp.submit(req[k:k + m]) == L.EAGAIN:
                 break
             k += m
-        # a tick when fewer than ticks_in_flight are queued (the device works
-        # through them in order; the control words say how many are done)
-        if launched - lp.ticks_done() < ticks_in_flight:
-            disp = committed_by_hw - dispatched_by_hw
-            lp.tick(inv.now_us + t // 1000, disp)
-            dispatched_by_hw += disp
-            launched += 1
         res = lp.poll()
         if res.shape[0]:
             now_ns = time.perf_counter_ns() - t0
@@ -765,12 +757,11 @@ def serve_loop_rate(L, lp, inv, rate: float, seconds: float, rng, id0: int, tick
             cm = res["kind"] == L.LOOP_COMMITTED
             spec_ns[ids[sp]] = now_ns
             com_ns[ids[cm]] = now_ns
-            np.add.at(committed_by_hw, res["backend"][cm], 1)
             n_seen += int(sp.sum()) + int(cm.sum())
         if time.perf_counter_ns() - t0 > 10e9 + seconds * 1e9:
             break
     t_end = time.perf_counter_ns() - t0
-    lp.sync()
+    lp.stop()
     st = lp.state()
     ok = (spec_ns >= 0) & (com_ns >= 0)
     spec_us = (spec_ns[ok] - arrive[ok]) / 1e3
@@ -865,7 +856,8 @@ def run_serve(args):
         "config": {"workload": workload, "method": "serve", "path": "table (device-resident loop)",
                    "dags": p.n_dags, "ops": p.n_ops, "slots": 1 << 20, "cq_cap": cq, "arrivals": "Poisson",
                    "seconds_per_rate": args.seconds,
-                   "backends": "dispatch every committed invocation at the next tick (backends keep up)"},
+                   "backends": "every tick dispatches each commit queue whole (backends keep up)",
+                   "ticks": "launched back to back by the library's driver thread, at most 2 queued"},
         "decision_latency_us": top["speculative_us"], "commit_latency_us": top["commit_us"],
         "serving": rows, "clocks": clocks.summary(),
         "serving_surrogate": {"rows": sg_rows, "network": "64-256-256-256-64 MLP, untrained weights (the "

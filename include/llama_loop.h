@@ -111,7 +111,7 @@ int llama_loop_create(llama_ctx *ctx, const llama_loop_opts *opts, llama_loop **
 void llama_loop_destroy(llama_loop *loop);
 
 /* Write n requests into the ring (host only; not thread-safe against
- * another submit).  All or nothing: EINVAL for bad arguments, LLAMA_EAGAIN
+ * another submit; safe beside the driver thread).  All or nothing: EINVAL for bad arguments, LLAMA_EAGAIN
  * (-6) when the ring lacks room for all n. */
 int llama_loop_submit(llama_loop *loop, const llama_loop_request *req, int64_t n);
 
@@ -121,6 +121,22 @@ int llama_loop_submit(llama_loop *loop, const llama_loop_request *req, int64_t n
  * tick admits only requests submitted before this call.  Errors: EINVAL,
  * ECUDA. */
 int llama_loop_tick(llama_loop *loop, int64_t now_us, const int32_t *dispatch);
+
+/* Run the ticks on a native host thread of the library (the "driver"):
+ * whenever fewer than ticks_in_flight ticks are queued on the loop's stream,
+ * it enqueues one at the steady clock's time (now_us at the start, plus the
+ * microseconds since), with the same dispatch counts every tick (host,
+ * n_hw entries, nullable = none; INT32_MAX dispatches each commit queue whole,
+ * for backends that keep up).  It idles (sleeps a few microseconds) while the
+ * ring is empty and nothing is in flight.  The caller keeps submitting and
+ * polling; llama_loop_tick is refused while the driver runs.  Ticks are then
+ * timed by the clock, so their records are not reproducible run to run (each
+ * tick still does exactly what llama_loop_tick would).  Errors: EINVAL. */
+int llama_loop_start(llama_loop *loop, int64_t now_us, int32_t ticks_in_flight, const int32_t *dispatch);
+
+/* Stop the driver thread and wait for its ticks.  Errors: ECUDA (a tick
+ * launch failed; the driver stopped then). */
+int llama_loop_stop(llama_loop *loop);
 
 /* Copy up to max_out result records, oldest first, into out (host); their
  * number in *n_out.  Never waits for the GPU. */

@@ -779,7 +779,6 @@ struct TileState {
     int32_t cbase;  // cfg_off of the op
     int64_t p0;
     int32_t inv[IPT];
-    int32_t rem[IPT];  // remaining time before queueing of each invocation (its bucket entry)
     uint32_t best[IPT];
     bool any;
     // the op's reference latency, critical path and floor((2^64-1) / critical
@@ -815,7 +814,6 @@ __device__ __forceinline__ void tile_begin(const DevProblem &P, const BucketScra
         const int32_t j = T.g * IPT + u;
         const bool in = j < T.m && LLAMA_IN_BOUNDS(P, tile.y + j >= 0 && tile.y + j < S.n_inv, LLAMA_CHECK_TILE);
         T.inv[u] = in ? S.b_inv[tile.y + j] : -1;
-        T.rem[u] = in ? S.b_rem[tile.y + j] : 0;
         if (!LLAMA_IN_BOUNDS(P, T.inv[u] < S.n_inv, LLAMA_CHECK_TILE)) T.inv[u] = -1;
         T.any |= T.inv[u] >= 0;
         T.best[u] = 0xFFFFFFFFu;
@@ -825,7 +823,7 @@ __device__ __forceinline__ void tile_begin(const DevProblem &P, const BucketScra
     T.mg = P.cp_magic[T.v];
 }
 
-// inv[u] and rem[u] for a runtime u, without a runtime index into registers.
+// inv[u] for a runtime u, without a runtime index into registers.
 template <int IPT>
 __device__ __forceinline__ int32_t inv_at(const TileState<IPT> &T, int u) {
     int32_t iu = T.inv[0];
@@ -834,68 +832,26 @@ __device__ __forceinline__ int32_t inv_at(const TileState<IPT> &T, int u) {
     return iu;
 }
 
-template <int IPT>
-__device__ __forceinline__ int32_t rem_at(const TileState<IPT> &T, int u) {
-    int32_t r = T.rem[0];
-#pragma unroll
-    for (int w = 1; w < IPT; ++w) r = u == w ? T.rem[w] : r;
-    return r;
-}
-
 // Slack of the tile's invocation u for backend h: Algorithm 1 through the
 // critical path, floor(ref * (rem - Q[h]) / cp), 0 once the target has passed,
-// rem being the invocation's remaining time stored beside its bucket entry
-// (loaded with the tile's invocation indices).
+// rem being the invocation's remaining time stored beside its bucket entry.
 template <int IPT>
 __device__ __forceinline__ int32_t slack_at(const BucketScratch &S, const TileState<IPT> &T, const TileConst &tc,
                                             int u, int h) {
-    return slack_of(T.ref, T.cp, T.mg, (int64_t)rem_at(T, u) - tc.q[h]);
+    return slack_of(T.ref, T.cp, T.mg, (int64_t)S.b_rem[T.pos0 + u] - tc.q[h]);
 }
 
 // Counts c(u, h) of distinct latencies below the slack of invocation u for
 // backend h, into cg[u * H + h], from the sorted list dl (shared memory: the
-// lanes of a group share the bisections).  A lane advances its searches in
-// lockstep, up to four at a time, so their dependent shared-memory loads
-// overlap instead of following one another.
+// lanes of a group share the bisections).
 template <int IPT>
 __device__ __forceinline__ void counts_from_shared(const BucketScratch &S, const TileState<IPT> &T,
                                                    const TileConst &tc, int H, const int32_t *dl, uint16_t *cg) {
     if (!T.any) return;
-    constexpr int kLock = 4;
-    const int nt = IPT * H;
-    for (int t0 = T.s; t0 < nt; t0 += kLock * T.L) {
-        int32_t lo[kLock], hi[kLock], sl[kLock];
-#pragma unroll
-        for (int j = 0; j < kLock; ++j) {
-            const int t = t0 + j * T.L;
-            const int u = t / H;
-            const bool act = t < nt && inv_at(T, u) >= 0;
-            sl[j] = act ? slack_at(S, T, tc, u, t - u * H) : 0;
-            lo[j] = 0;
-            hi[j] = act ? T.dn : 0;
-        }
-        for (;;) {
-            int32_t val[kLock];
-            bool more = false;
-#pragma unroll
-            for (int j = 0; j < kLock; ++j) {  // every probe's load first
-                const bool a = lo[j] < hi[j];
-                more |= a;
-                val[j] = a ? dl[(lo[j] + hi[j]) >> 1] : 0;
-            }
-            if (!more) break;
-#pragma unroll
-            for (int j = 0; j < kLock; ++j) {
-                if (lo[j] >= hi[j]) continue;
-                const int32_t mid = (lo[j] + hi[j]) >> 1;
-                if (val[j] < sl[j]) lo[j] = mid + 1; else hi[j] = mid;
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < kLock; ++j) {
-            const int t = t0 + j * T.L;
-            if (t < nt) cg[t] = (uint16_t)lo[j];  // 0 for a group slot without an invocation
-        }
+    for (int t = T.s; t < IPT * H; t += T.L) {
+        const int u = t / H, h = t - u * H;
+        const int32_t iu = inv_at(T, u);
+        cg[t] = iu >= 0 ? (uint16_t)count_below(dl, T.dn, slack_at(S, T, tc, u, h)) : 0;
     }
 }
 
@@ -2255,22 +2211,46 @@ __global__ void __launch_bounds__(kLoopThreads) k_loop_tick(DevProblem P, LoopDe
     __shared__ double c_aff[kLoopThreads];
     __shared__ int8_t c_lam[kLoopThreads], c_commit[kLoopThreads];
 
-    // 1. dispatch (one thread, so the free stack's order is reproducible), then
-    //    the queueing time at the tick's start (Eq. 2 over both queues)
+    // 1. dispatch: the heads of the commit queues leave (their slots go back on
+    //    the free stack in backend order, then queue order, so the stack's order
+    //    is reproducible), a thread per dispatched invocation; then the
+    //    queueing time at the tick's start (Eq. 2 over both queues)
     if (tid == 0) {
-        int32_t ft = S.free_top;
+        int off = 0;
         for (int h = 0; h < H; ++h) {
             const long long len = S.cq_tail[h] - S.cq_head[h];
-            const long long k = min((long long)max(a.dispatch[h], 0), len);
-            for (long long j = 0; j < k; ++j) {
-                const int32_t slot = L.cq[(int64_t)h * L.cq_stride + (S.cq_head[h] + j) % L.cq_cap[h]];
-                if (!LLAMA_IN_BOUNDS(P, slot >= 0 && slot < L.slots, LLAMA_CHECK_LOOP)) continue;
-                S.s_cq[h] -= L.slot_lr_commit[slot];
-                L.free_stack[ft++] = slot;
-            }
-            S.cq_head[h] += k;
-            S.dispatched += k;
+            const int k = (int)min((long long)max(a.dispatch[h], 0), len);
+            sh_cnt[h] = off;  // first dispatched entry of backend h
+            off += k;
+            sh_lr_out[h] = 0;
         }
+        sh_w[0] = off;  // dispatched in all
+        sh_free_top = S.free_top;
+        for (int h = 0; h < H; ++h) sh_cq_tail[h] = S.cq_head[h];  // the heads, for the loop below
+    }
+    __syncthreads();
+    {
+        const int n_disp = sh_w[0];
+        for (int t = tid; t < n_disp; t += kLoopThreads) {
+            int h = 0;
+            while (h + 1 < H && t >= sh_cnt[h + 1]) ++h;
+            const long long pos = sh_cq_tail[h] + (t - sh_cnt[h]);
+            const int32_t slot = L.cq[(int64_t)h * L.cq_stride + pos % L.cq_cap[h]];
+            if (!LLAMA_IN_BOUNDS(P, slot >= 0 && slot < L.slots, LLAMA_CHECK_LOOP)) continue;
+            atomicAdd(&sh_lr_out[h], L.slot_lr_commit[slot]);
+            L.free_stack[sh_free_top + t] = slot;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const int n_disp = sh_w[0];
+        for (int h = 0; h < H; ++h) {
+            const int k = (h + 1 < H ? sh_cnt[h + 1] : n_disp) - sh_cnt[h];
+            S.s_cq[h] -= sh_lr_out[h];
+            S.cq_head[h] += k;
+        }
+        S.dispatched += n_disp;
+        const int32_t ft = S.free_top + n_disp;
         S.free_top = ft;
         for (int h = 0; h < H; ++h) L.q[h] = loop_queue_time(S.s_sq[h] + S.s_cq[h], P.res_total[h]);
         const long long avail = max(0ll, a.limit - S.head);
@@ -2289,6 +2269,7 @@ __global__ void __launch_bounds__(kLoopThreads) k_loop_tick(DevProblem P, LoopDe
             sh_lr_out[h] = 0;
             sh_group[h] = 0;
             sh_ncommit_src[h] = 0;
+            sh_cnt[h] = 0;
         }
     }
     __syncthreads();
@@ -2445,6 +2426,7 @@ __global__ void __launch_bounds__(kLoopThreads) k_loop_tick(DevProblem P, LoopDe
         volatile LoopCtl *ctl = L.ctl;
         ctl->head = (unsigned long long)S.head;
         ctl->dropped = (unsigned long long)S.dropped;
+        ctl->inflight = (unsigned long long)(S.admitted - S.dispatched);
         ctl->ticks = (unsigned long long)S.ticks;
         __threadfence_system();
         ctl->res_count = (unsigned long long)S.res_count;

@@ -57,12 +57,6 @@ struct DeviceGuard {
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
-// llama_schedule with host output: calls of at least kE2EChunkMin invocations
-// go in kE2EChunks pieces whose decisions are copied back while the next runs
-constexpr int64_t kE2EChunkMin = 1 << 18;
-constexpr int kE2EChunks = 4;
-static_assert(kE2EChunks * kStatusWords <= kCtrlWords, "the pinned status buffer holds every piece's words");
-
 // An NVTX range over an API call (shown by Nsight tools; costs nothing when no
 // tool is attached).
 struct Range {
@@ -87,8 +81,6 @@ struct llama_ctx {
     int max_smem_optin = 0;
     int64_t l2_bytes = 0;
     cudaStream_t stream = nullptr;
-    cudaStream_t copy_stream = nullptr;  // decisions copied back while later chunks run (llama_schedule)
-    cudaEvent_t chunk_ev[4] = {};
     cudaEvent_t order_ev = nullptr;  // orders the context's own stream after table updates on other streams
     std::string err = "no error";
 
@@ -587,8 +579,8 @@ int capture_graph(llama_ctx *c, int64_t n_inv, const int32_t *dag, const int32_t
 }
 
 int launch_schedule(llama_ctx *c, int64_t n_inv, const int32_t *dag, const int32_t *op_local,
-                    const int64_t *start, int64_t now, llama_decision *out, cudaStream_t s, bool direct = false) {
-    if (direct || !c->opts.use_graph || c->tracing) {
+                    const int64_t *start, int64_t now, llama_decision *out, cudaStream_t s) {
+    if (!c->opts.use_graph || c->tracing) {
         const ContextView v = view_of(c);
         const BucketScratch S = make_scratch(c->ws);
         LL_CUDA(c, enqueue_schedule(v, S, n_inv, dag, op_local, start, now, out, s,
@@ -671,11 +663,6 @@ extern "C" int llama_create(llama_ctx **out, const llama_opts *opts) {
         cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, opts->device) != cudaSuccess ||
         cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->chunk_ev[0], cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->chunk_ev[1], cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->chunk_ev[2], cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->chunk_ev[3], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->order_ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaMallocHost(&c->h_ctrl, sizeof(unsigned long long) * kCtrlWords) != cudaSuccess ||
         c->q_dev.alloc(8 * LLAMA_MAX_HW) != cudaSuccess || c->q_sums.alloc(8 * LLAMA_MAX_HW) != cudaSuccess ||
@@ -705,9 +692,6 @@ extern "C" void llama_destroy(llama_ctx *c) {
         c->drop_graph();
         if (c->stream) cudaStreamDestroy(c->stream);
         if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
-        if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
-        for (cudaEvent_t e : c->chunk_ev)
-            if (e) cudaEventDestroy(e);
         if (c->order_ev) cudaEventDestroy(c->order_ev);
         if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
         c->close_stats();
@@ -1369,46 +1353,12 @@ extern "C" int llama_schedule(llama_ctx *c, int64_t n_inv, const int32_t *dag, c
     if (!ro) LL_CUDA(c, cudaMemcpyAsync((void *)d_opl, op_local, 4 * n_inv, cudaMemcpyHostToDevice, s));
     if (!rs) LL_CUDA(c, cudaMemcpyAsync((void *)d_start, start_us, 8 * n_inv, cudaMemcpyHostToDevice, s));
     if (c->stats) LL_CUDA(c, cudaEventRecord(c->stats_ev[0], s));
-    const unsigned long long *d_status = c->ws.ctrl.as<unsigned long long>() + kCtrlWords;
-    if (!outd && n_inv >= kE2EChunkMin) {
-        // a large call with host output goes in kE2EChunks pieces on the context's
-        // stream (direct launches, the scratch reused in turn); each piece's
-        // decisions are copied back on the copy stream while the next one runs
-        // (the host link carries the copies one way and the in-place input reads
-        // the other); each piece's status words land in their own pair
-        const int64_t per = (n_inv + kE2EChunks - 1) / kE2EChunks;
-        int nch = 0;
-        for (int64_t off = 0; off < n_inv; off += per, ++nch) {
-            const int64_t m = std::min(per, n_inv - off);
-            if ((rc = launch_schedule(c, m, d_dag + off, d_opl + off, d_start + off, now_us, d_out + off, s, true)))
-                return rc;
-            LL_CUDA(c, cudaMemcpyAsync(c->h_ctrl + kStatusWords * nch, d_status,
-                                       sizeof(unsigned long long) * kStatusWords, cudaMemcpyDeviceToHost, s));
-            LL_CUDA(c, cudaEventRecord(c->chunk_ev[nch], s));
-            LL_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->chunk_ev[nch], 0));
-            LL_CUDA(c, cudaMemcpyAsync(out + off, d_out + off, sizeof(llama_decision) * m, cudaMemcpyDeviceToHost,
-                                       c->copy_stream));
-        }
-        if (c->stats) LL_CUDA(c, cudaEventRecord(c->stats_ev[1], s));
-        LL_CUDA(c, cudaStreamSynchronize(s));
-        LL_CUDA(c, cudaStreamSynchronize(c->copy_stream));
-        unsigned long long invalid = 0, timeout = 0;
-        for (int k = 0; k < nch; ++k) {
-            invalid += c->h_ctrl[kStatusWords * k];
-            timeout |= c->h_ctrl[kStatusWords * k + 1];
-        }
-        c->h_ctrl[0] = invalid;
-        c->h_ctrl[1] = timeout;
-        c->last_launches *= nch;
-    } else {
-        if ((rc = launch_schedule(c, n_inv, d_dag, d_opl, d_start, now_us, d_out, s))) return rc;
-        if (c->stats) LL_CUDA(c, cudaEventRecord(c->stats_ev[1], s));
-        if (!outd)
-            LL_CUDA(c, cudaMemcpyAsync(out, d_out, sizeof(llama_decision) * n_inv, cudaMemcpyDeviceToHost, s));
-        LL_CUDA(c, cudaMemcpyAsync(c->h_ctrl, d_status, sizeof(unsigned long long) * kStatusWords,
-                                   cudaMemcpyDeviceToHost, s));
-        LL_CUDA(c, cudaStreamSynchronize(s));
-    }
+    if ((rc = launch_schedule(c, n_inv, d_dag, d_opl, d_start, now_us, d_out, s))) return rc;
+    if (c->stats) LL_CUDA(c, cudaEventRecord(c->stats_ev[1], s));
+    if (!outd) LL_CUDA(c, cudaMemcpyAsync(out, d_out, sizeof(llama_decision) * n_inv, cudaMemcpyDeviceToHost, s));
+    LL_CUDA(c, cudaMemcpyAsync(c->h_ctrl, c->ws.ctrl.as<unsigned long long>() + kCtrlWords,
+                               sizeof(unsigned long long) * kStatusWords, cudaMemcpyDeviceToHost, s));
+    LL_CUDA(c, cudaStreamSynchronize(s));
     if (c->stats) {
         // one JSON object per line: the call's size, its kernels, what it found
         // and how long it took on the device (kernels only) and on the host (whole call)

@@ -316,6 +316,7 @@ struct LoopCtl {
     unsigned long long res_read;   // records the host has taken (host writes)
     unsigned long long dropped;    // records lost to a full result ring
     unsigned long long ticks;
+    unsigned long long inflight;   // admitted and not yet dispatched
 };
 
 // Device-resident counters and queue state (one struct in device memory).

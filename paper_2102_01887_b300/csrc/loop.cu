@@ -6,9 +6,11 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include <atomic>
+#include <chrono>
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "llama_internal.cuh"
@@ -46,8 +48,13 @@ struct llama_loop {
     llama_loop_request *h_ring = nullptr;
     llama_loop_result *h_res = nullptr;
     LoopCtl *h_ctl = nullptr;
-    int64_t tail = 0;      // requests written into the ring
-    int64_t res_read = 0;  // records taken by poll
+    std::atomic<int64_t> tail{0};  // requests written into the ring (published after the entries)
+    int64_t res_read = 0;          // records taken by poll
+    // the driver thread (llama_loop_start): ticks launched back to back
+    std::thread driver;
+    std::atomic<bool> running{false};
+    std::atomic<int> driver_error{0};
+    int64_t launched = 0;          // ticks enqueued (driver or llama_loop_tick)
     std::vector<int32_t> res_total;
     LoopDev L{};
     DevProblem P{};
@@ -61,6 +68,8 @@ struct llama_loop {
         return e;
     }
     void release() {
+        running.store(false);
+        if (driver.joinable()) driver.join();
         if (stream) cudaStreamSynchronize(stream);
         for (void *p : dev_bufs) cudaFree(p);
         dev_bufs.clear();
@@ -197,19 +206,21 @@ extern "C" void llama_loop_destroy(llama_loop *lp) {
 extern "C" int llama_loop_submit(llama_loop *lp, const llama_loop_request *req, int64_t n) {
     if (!lp || n < 0 || (n > 0 && !req)) return LLAMA_EINVAL;
     const int64_t taken = (int64_t)*reinterpret_cast<volatile unsigned long long *>(&lp->h_ctl->head);
-    if (lp->tail - taken + n > lp->opts.ring) return -6;  // LLAMA_EAGAIN: the ring lacks room
+    const int64_t tail = lp->tail.load(std::memory_order_relaxed);
+    if (tail - taken + n > lp->opts.ring) return -6;  // LLAMA_EAGAIN: the ring lacks room
     const int64_t mask = lp->opts.ring - 1;
-    for (int64_t k = 0; k < n; ++k) lp->h_ring[(lp->tail + k) & mask] = req[k];
-    std::atomic_thread_fence(std::memory_order_seq_cst);  // the entries before the tick that reads them
-    lp->tail += n;
+    for (int64_t k = 0; k < n; ++k) lp->h_ring[(tail + k) & mask] = req[k];
+    // the entries before the tail that publishes them (and before any tick that reads them)
+    lp->tail.store(tail + n, std::memory_order_seq_cst);
     return LLAMA_OK;
 }
 
 extern "C" int llama_loop_tick(llama_loop *lp, int64_t now_us, const int32_t *dispatch) {
     if (!lp) return LLAMA_EINVAL;
+    if (lp->running.load()) return loop_fail(lp, LLAMA_EINVAL, "tick: the driver thread is running");
     LoopTickArgs a{};
     a.now = now_us;
-    a.limit = lp->tail;
+    a.limit = lp->tail.load(std::memory_order_seq_cst);
     for (int h = 0; h < lp->n_hw; ++h) {
         a.dispatch[h] = dispatch ? dispatch[h] : 0;
         if (a.dispatch[h] < 0) return loop_fail(lp, LLAMA_EINVAL, "tick: negative dispatch count");
@@ -220,6 +231,69 @@ extern "C" int llama_loop_tick(llama_loop *lp, int64_t now_us, const int32_t *di
     const cudaError_t e = enqueue_loop_tick(lp->P, lp->L, a, lp->stream);
     nvtxRangePop();
     if (e != cudaSuccess) return loop_cuda(lp, e, "tick launch");
+    ++lp->launched;
+    return LLAMA_OK;
+}
+
+namespace {
+
+// The driver thread: a tick whenever fewer than in_flight are queued, at the
+// steady clock's time (now_us at the start, then the microseconds elapsed);
+// every tick applies the same dispatch counts.  With nothing pending on the
+// device and nothing new in the ring it idles briefly instead of launching.
+void drive(llama_loop *lp, int64_t now0, int in_flight, LoopTickArgs a) {
+    cudaSetDevice(lp->device);
+    const auto t0 = std::chrono::steady_clock::now();
+    volatile LoopCtl *ctl = lp->h_ctl;
+    while (lp->running.load(std::memory_order_relaxed)) {
+        const int64_t done = (int64_t)ctl->ticks;
+        const int64_t limit = lp->tail.load(std::memory_order_seq_cst);
+        const bool idle = done == lp->launched && (int64_t)ctl->head == limit && ctl->inflight == 0;
+        if (lp->launched - done >= in_flight || idle) {
+            std::this_thread::sleep_for(std::chrono::microseconds(idle ? 20 : 2));
+            continue;
+        }
+        a.now = now0 + std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t0).count();
+        a.limit = limit;
+        nvtxRangePushA("llama:loop_tick");
+        const cudaError_t e = enqueue_loop_tick(lp->P, lp->L, a, lp->stream);
+        nvtxRangePop();
+        if (e != cudaSuccess) {
+            lp->driver_error.store((int)e);
+            lp->running.store(false);
+            break;
+        }
+        ++lp->launched;
+    }
+}
+
+}  // namespace
+
+extern "C" int llama_loop_start(llama_loop *lp, int64_t now_us, int32_t ticks_in_flight, const int32_t *dispatch) {
+    if (!lp) return LLAMA_EINVAL;
+    if (lp->running.load()) return loop_fail(lp, LLAMA_EINVAL, "start: the driver thread is running");
+    if (ticks_in_flight < 1 || ticks_in_flight > 64)
+        return loop_fail(lp, LLAMA_EINVAL, "start: ticks_in_flight outside 1..64");
+    LoopTickArgs a{};
+    for (int h = 0; h < lp->n_hw; ++h) {
+        a.dispatch[h] = dispatch ? dispatch[h] : 0;
+        if (a.dispatch[h] < 0) return loop_fail(lp, LLAMA_EINVAL, "start: negative dispatch count");
+    }
+    lp->driver_error.store(0);
+    lp->running.store(true);
+    lp->driver = std::thread(drive, lp, now_us, (int)ticks_in_flight, a);
+    return LLAMA_OK;
+}
+
+extern "C" int llama_loop_stop(llama_loop *lp) {
+    if (!lp) return LLAMA_EINVAL;
+    lp->running.store(false);
+    if (lp->driver.joinable()) lp->driver.join();
+    CurrentDevice guard(lp->device);
+    const cudaError_t e = cudaStreamSynchronize(lp->stream);
+    if (e != cudaSuccess) return loop_cuda(lp, e, "stop");
+    const int de = lp->driver_error.load();
+    if (de) return loop_cuda(lp, (cudaError_t)de, "driver tick launch");
     return LLAMA_OK;
 }
 
@@ -258,7 +332,7 @@ extern "C" int llama_loop_state_get(llama_loop *lp, llama_loop_state *out) {
     if (e != cudaSuccess) return loop_cuda(lp, e, "state");
     std::memset(out, 0, sizeof(*out));
     out->ticks = st.ticks;
-    out->submitted = lp->tail;
+    out->submitted = lp->tail.load();
     out->admitted = st.admitted;
     out->rejected = st.rejected;
     out->committed = st.committed;

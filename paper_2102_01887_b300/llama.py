@@ -48,7 +48,8 @@ EXPORTS = ("llama_create", "llama_destroy", "llama_set_dags", "llama_set_profile
            "llama_static_status", "llama_set_wait_limit", "llama_alu_peak", "llama_set_stats_file",
            "llama_check_build", "llama_check_word",
            "llama_loop_create", "llama_loop_destroy", "llama_loop_submit", "llama_loop_tick", "llama_loop_poll",
-           "llama_loop_sync", "llama_loop_state_get", "llama_loop_refresh", "llama_loop_ticks_done")
+           "llama_loop_sync", "llama_loop_state_get", "llama_loop_refresh", "llama_loop_ticks_done",
+           "llama_loop_start", "llama_loop_stop")
 TRACE_EVENTS = 3
 TRACE_PHASES = ("bucket", "score")
 
@@ -168,6 +169,8 @@ def load(path: str = None) -> ctypes.CDLL:
             "llama_loop_state_get": ([vp, ctypes.POINTER(llama_loop_state)], ctypes.c_int),
             "llama_loop_refresh": ([vp], ctypes.c_int),
             "llama_loop_ticks_done": ([vp], i64),
+            "llama_loop_start": ([vp, i64, i32, vp], ctypes.c_int),
+            "llama_loop_stop": ([vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -591,6 +594,16 @@ class Loop:
 
     def ticks_done(self) -> int:
         return int(self.lib.llama_loop_ticks_done(self.h))
+
+    def start(self, now_us: int, ticks_in_flight: int = 2, dispatch=None) -> None:
+        """Ticks on the library's driver thread (dispatch: per-tick counts; None =
+        dispatch every commit queue whole each tick)."""
+        d = np.full(self.n_hw, 2**31 - 1, np.int32) if dispatch is None else np.ascontiguousarray(dispatch, np.int32)
+        self._dispatch = d
+        self._check(self.lib.llama_loop_start(self.h, int(now_us), int(ticks_in_flight), d.ctypes.data))
+
+    def stop(self) -> None:
+        self._check(self.lib.llama_loop_stop(self.h))
 
     def state(self) -> dict:
         st = llama_loop_state()

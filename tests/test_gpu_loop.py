@@ -134,3 +134,50 @@ def test_ring_backpressure_and_state(L):
         assert st["admitted"] == 4 and st["submitted"] == 9 and st["ticks"] == 1
         recs = lp.poll()
         assert sorted(recs["id"][recs["kind"] == L.LOOP_SPECULATED].tolist()) == [0, 1, 2, 3]
+
+
+def test_driver_thread_serves_every_request(L):
+    """The library's driver thread runs the ticks while this thread submits and
+    polls: every valid request is speculated and committed once, invalid ones
+    are rejected, each decision is its configuration's profile entry with a
+    consistent backend, and with every commit queue dispatched whole each tick
+    the loop ends empty with every slot free."""
+    import time
+    p, inv = W.medium(n_inv=20_000)
+    req = np.zeros(inv.n, L.LOOP_REQUEST_DTYPE)
+    req["id"] = np.arange(inv.n)
+    req["dag"], req["op_local"], req["start_us"] = inv.dag, inv.op_local, inv.start_us
+    req["dag"][::211] = -1
+    n_bad = int((req["dag"] < 0).sum())
+    seen = {L.LOOP_SPECULATED: [], L.LOOP_COMMITTED: [], L.LOOP_REJECTED: []}
+    recs = []
+    with L.Scheduler(p) as s, L.Loop(s, slots=4096, ring=1 << 14, results=1 << 16, max_admit=512,
+                                     cq_cap=(32, 32, 32)) as lp:
+        lp.start(inv.now_us, 2)
+        k, t0 = 0, time.time()
+        while len(seen[L.LOOP_COMMITTED]) + len(seen[L.LOOP_REJECTED]) < inv.n and time.time() - t0 < 60:
+            if k < inv.n and lp.submit(req[k:k + 1000]) == L.OK:
+                k = min(inv.n, k + 1000)
+            r = lp.poll()
+            recs.append(r)
+            for kind in seen:
+                seen[kind].extend(r["id"][r["kind"] == kind].tolist())
+        lp.stop()
+        st = lp.state()
+    assert sorted(seen[L.LOOP_REJECTED]) == sorted(np.flatnonzero(req["dag"] < 0).tolist())
+    good = sorted(np.flatnonzero(req["dag"] >= 0).tolist())
+    assert sorted(seen[L.LOOP_SPECULATED]) == good and sorted(seen[L.LOOP_COMMITTED]) == good
+    assert st["rejected"] == n_bad and st["committed"] == inv.n - n_bad
+    assert st["free_slots"] == 4096 and not any(st["sq_len"]) and not any(st["cq_len"])
+    r = np.concatenate(recs)
+    r = r[r["kind"] != L.LOOP_REJECTED]
+    ids = r["id"]
+    g = p.dag_op_off[inv.dag[ids]] + inv.op_local[ids]
+    d = r["decision"]
+    assert (d["cfg"] >= 0).all() and (d["cfg"] < np.diff(p.cfg_off)[g]).all()
+    assert np.array_equal(d["lat"], p.lat_us[p.cfg_off[g] + d["cfg"]])
+    assert np.array_equal(d["cost"], p.cost_nd[p.cfg_off[g] + d["cfg"]])
+    hw = p.hw_off.reshape(p.n_ops, p.n_hw + 1)
+    lam = (hw[g][:, 1:p.n_hw] <= d["cfg"][:, None]).sum(axis=1)
+    assert np.array_equal(r["backend"], lam)
+    assert np.array_equal(d["flags"] & 1, (d["lat"] < d["slack"]).astype(np.int32))

@@ -113,7 +113,7 @@ def test_slack_division_at_its_extremes(L, shape, method):
     start[::50] = now - rng.integers(0, 2**31 - 1, start[::50].shape[0])  # some far into their target
     inv = W.Invocations(np.zeros(m, np.int32), ops, start.astype(np.int64), now)
     cp = oracle.critical_path(p)
-    assert cp.max() > 2**38
+    assert cp.max() > (2**38 if shape == "chain" else 2**32)
     with L.Scheduler(p, method=method) as s:
         assert np.array_equal(s.critical_path(), cp)
         assert np.array_equal(s.slack(inv).astype(np.int64), oracle.slacks(p, inv))
