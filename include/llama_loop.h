@@ -100,9 +100,10 @@ typedef struct llama_loop llama_loop;
 
 /* A loop over a ready context: DAGs and profiles set, with batch, res and
  * res_total (Eq. 2 and Eq. 3 need B(x), R(x) and R_total).  Builds the
- * staircase tables for the current profiles (if the context has none) and
- * computes the critical paths; Eq. 3's per-backend minima are taken per commit
- * candidate over its operation's configurations (a warp each).  Call
+ * staircase tables for the current profiles (if the context has none), the
+ * loop's tables of Eq. 3's per-backend minima (per op, backend and count of
+ * distinct latencies below the slack: 8 B per configuration and backend) and
+ * the critical paths.  Call
  * llama_loop_refresh after the context's tables change (feedback); a new
  * llama_set_profiles needs a new loop.  The loop owns a CUDA stream, device
  * state sized by opts, and two page-locked rings.  Errors: EINVAL, ENOTREADY,

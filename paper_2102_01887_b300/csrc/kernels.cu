@@ -1419,13 +1419,18 @@ template __global__ void k_counts<LLAMA_MAX_HW>(DevProblem, BucketScratch, int32
 // The staircase decision of one valid invocation of global op g whose
 // remaining time before queueing is rbase = SLO - elapsed (Algorithm 1 with
 // the queueing times P.q, Eq. 1 through the staircase tables): the decision,
-// and its backend in *lam.
-__device__ llama_decision stair_decide(const DevProblem &P, int32_t g, int64_t rbase, int *lam_out) {
+// and its backend in *lam; with cnt_out, also the count per backend of the
+// op's distinct latencies below the slack on it.
+__device__ llama_decision stair_decide(const DevProblem &P, int32_t g, int64_t rbase, int *lam_out,
+                                       int32_t *cnt_out = nullptr) {
     const int H = P.n_hw;
     const int64_t ref = P.ref[g], cp = P.cp[g];
     const uint64_t mg = P.cp_magic[g];
     int32_t lo[LLAMA_MAX_HW];
     counts_all_backends<LLAMA_MAX_HW, false>(P, g, ref, cp, mg, rbase, lo);
+    if (cnt_out)
+#pragma unroll
+        for (int h = 0; h < LLAMA_MAX_HW; ++h) cnt_out[h] = lo[h];
     const uint16_t *sg = P.stair + P.stair_off[g];
     const int64_t stride = P.cfg_off[g + 1] - P.cfg_off[g] + 1;
     uint32_t key = 0xFFFFu;
@@ -1477,32 +1482,34 @@ __global__ void __launch_bounds__(256) k_stair(DevProblem P, int64_t n_inv, cons
 
 // Inclusive minimum scan of a[0..n) in shared memory by the whole block, from
 // the front (reverse = false) or from the back; part[] holds 32 words.
-__device__ void block_min_scan(int32_t *a, int n, bool reverse, int32_t *part) {
-    const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int per = (n + T - 1) / T;
+template <typename T>
+__device__ void block_min_scan(T *a, int n, bool reverse, T *part) {
+    const T kTop = sizeof(T) == 8 ? (T)LLONG_MAX : (T)INT32_MAX;  // int32_t or long long
+    const int NT = blockDim.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int per = (n + NT - 1) / NT;
     const int b = min(n, tid * per), e = min(n, b + per);
-    auto at = [&](int k) -> int32_t & { return a[reverse ? n - 1 - k : k]; };
-    int32_t run = INT32_MAX;
+    auto at = [&](int k) -> T & { return a[reverse ? n - 1 - k : k]; };
+    T run = kTop;
     for (int k = b; k < e; ++k) run = min(run, at(k));
-    int32_t inc = run;
+    T inc = run;
     for (int o = 1; o < 32; o <<= 1) {
-        const int32_t u = __shfl_up_sync(0xffffffffu, inc, o);
+        const T u = __shfl_up_sync(0xffffffffu, inc, o);
         if (lane >= o) inc = min(inc, u);
     }
     if (lane == 31) part[wid] = inc;
     __syncthreads();
     if (wid == 0) {
-        int32_t w = lane < (T >> 5) ? part[lane] : INT32_MAX;
+        T w = lane < (NT >> 5) ? part[lane] : kTop;
         for (int o = 1; o < 32; o <<= 1) {
-            const int32_t u = __shfl_up_sync(0xffffffffu, w, o);
+            const T u = __shfl_up_sync(0xffffffffu, w, o);
             if (lane >= o) w = min(w, u);
         }
-        if (lane < (T >> 5)) part[lane] = w;
+        if (lane < (NT >> 5)) part[lane] = w;
     }
     __syncthreads();
     // minimum of everything before this thread's run
-    int32_t before = __shfl_up_sync(0xffffffffu, inc, 1);
-    if (lane == 0) before = INT32_MAX;
+    T before = __shfl_up_sync(0xffffffffu, inc, 1);
+    if (lane == 0) before = kTop;
     if (wid > 0) before = min(before, part[wid - 1]);
     for (int k = b; k < e; ++k) {
         before = min(before, at(k));
@@ -1550,6 +1557,66 @@ __global__ void k_encode_stair(DevProblem P, uint16_t *stair) {
             out[(int64_t)h * stride + k] = (uint16_t)(alpha ? min(pre[k], suf[k]) : pre[k]);
         __syncthreads();
     }
+}
+
+// Eq. 1's infeasible branch in unsigned 64-bit: alpha_num*L*R < 2^63 and
+// alpha_den*B*R_total < 2^63 by the validated bounds; the sum saturates.
+__device__ __forceinline__ uint64_t alpha_infeasible_objective(const DevProblem &P, int64_t g, int h) {
+    const uint64_t num = (uint64_t)P.alpha_num * (uint64_t)P.lat[g] * (uint64_t)P.res[g];
+    const uint64_t den = (uint64_t)P.alpha_den * (uint64_t)P.batch[g] * (uint64_t)P.res_total[h];
+    const uint64_t obj = (uint64_t)P.cost[g] + num / den;
+    return obj > (uint64_t)LLONG_MAX ? (uint64_t)LLONG_MAX : obj;
+}
+
+// Eq. 3's per-backend minima as tables, one CTA per op (used where the
+// minima of single invocations are needed fast: the serving loop's commit).
+// For segment h and a count k of the op's distinct latencies below the
+// slack on h, a configuration of h is feasible exactly when its latency rank
+// is below k, so the least Eq. 1 objective on h is
+//   min(least C among ranks < k, least C + floor(a L R / (b B R_total)) among ranks >= k),
+// a prefix minimum and a suffix minimum over the ranks; at
+// objmin[stair_off[v] + h*(n_cfg(v)+1) + k] for k = 0..dn (INT64_MAX for an
+// empty segment), the staircase tables' indexing.
+__global__ void k_encode_objmin(DevProblem P, int64_t *objmin) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ long long part[32];
+    const int v = blockIdx.x, H = P.n_hw, T = blockDim.x, tid = threadIdx.x;
+    const int32_t dn = P.dlat_n[v], m = dn + 1;
+    long long *pre = reinterpret_cast<long long *>(smem_raw);
+    long long *suf = pre + m;
+    const int64_t p0 = P.pad_off[v], c0 = P.cfg_off[v];
+    const int32_t *hw = P.hw_off + (int64_t)v * (H + 1);
+    const int32_t *sp = P.seg_pad + (int64_t)v * (H + 1);
+    int64_t *out = objmin + P.stair_off[v];
+    const int64_t stride = P.cfg_off[v + 1] - c0 + 1;
+    for (int h = 0; h < H; ++h) {
+        for (int k = tid; k < m; k += T) {
+            pre[k] = LLONG_MAX;
+            suf[k] = LLONG_MAX;
+        }
+        __syncthreads();
+        const int n_h = hw[h + 1] - hw[h];
+        for (int j = tid; j < n_h; j += T) {
+            const int32_t r = (int32_t)P.lrb[p0 + sp[h] + j] - kLatRankBias;
+            const int64_t g = c0 + hw[h] + j;
+            atomicMin(&pre[r + 1], (long long)P.cost[g]);
+            atomicMin(&suf[r], (long long)alpha_infeasible_objective(P, g, h));
+        }
+        __syncthreads();
+        block_min_scan(pre, m, false, part);
+        block_min_scan(suf, m, true, part);
+        for (int k = tid; k < m; k += T) out[(int64_t)h * stride + k] = min(pre[k], suf[k]);
+        __syncthreads();
+    }
+}
+
+cudaError_t enqueue_encode_objmin(const ContextView &v, int64_t *objmin, cudaStream_t s) {
+    // distinct latencies of an op <= its configurations
+    const size_t smem = 2 * sizeof(long long) * (size_t)(v.max_ncfg + 1);
+    cudaError_t e = cudaFuncSetAttribute(k_encode_objmin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (v.n_ops > 0) k_encode_objmin<<<v.n_ops, 1024, smem, s>>>(v.P, objmin);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -1736,15 +1803,6 @@ __global__ void k_encode_pad(DevProblem P, uint16_t *lrb, uint16_t *rf, uint16_t
         for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
         if (threadIdx.x == 0) fast[v] = (int32_t)(best & 0xFFFF);
     }
-}
-
-// Eq. 1's infeasible branch in unsigned 64-bit: alpha_num*L*R < 2^63 and
-// alpha_den*B*R_total < 2^63 by the validated bounds; the sum saturates.
-__device__ __forceinline__ uint64_t alpha_infeasible_objective(const DevProblem &P, int64_t g, int h) {
-    const uint64_t num = (uint64_t)P.alpha_num * (uint64_t)P.lat[g] * (uint64_t)P.res[g];
-    const uint64_t den = (uint64_t)P.alpha_den * (uint64_t)P.batch[g] * (uint64_t)P.res_total[h];
-    const uint64_t obj = (uint64_t)P.cost[g] + num / den;
-    return obj > (uint64_t)LLONG_MAX ? (uint64_t)LLONG_MAX : obj;
 }
 
 // One CTA per op: sort the op's (objective, tag) pairs in shared memory with a
@@ -2197,7 +2255,7 @@ __device__ __forceinline__ void loop_record(const LoopDev &L, long long pos, lon
 }
 
 __global__ void __launch_bounds__(kLoopThreads) k_loop_tick(DevProblem P, LoopDev L, LoopTickArgs a) {
-    const int H = P.n_hw, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int H = P.n_hw, tid = threadIdx.x;
     LoopState &S = *L.st;
     __shared__ int wsum[32];
     __shared__ int sh_n_adm, sh_free_top, sh_tick;
@@ -2206,8 +2264,6 @@ __global__ void __launch_bounds__(kLoopThreads) k_loop_tick(DevProblem P, LoopDe
     __shared__ int sh_room[LLAMA_MAX_HW], sh_cnt[LLAMA_MAX_HW], sh_w[LLAMA_MAX_HW + 1], sh_group[LLAMA_MAX_HW],
         sh_ncommit_src[LLAMA_MAX_HW];
     __shared__ unsigned long long sh_lr_in[LLAMA_MAX_HW], sh_lr_out[LLAMA_MAX_HW];
-    __shared__ int32_t c_g[kLoopThreads];
-    __shared__ long long c_rbase[kLoopThreads];
     __shared__ double c_aff[kLoopThreads];
     __shared__ int8_t c_lam[kLoopThreads], c_commit[kLoopThreads];
 
@@ -2357,23 +2413,17 @@ __global__ void __launch_bounds__(kLoopThreads) k_loop_tick(DevProblem P, LoopDe
         const int32_t d = L.slot_dag[slot];
         g2 = P.dag_op_off[d] + L.slot_opl[slot];
         const long long rb = P.slo[d] - (a.now - L.slot_start[slot]);
-        d2 = stair_decide(P, g2, rb, &lam2);
-        c_g[tid] = g2;
-        c_rbase[tid] = rb;
-        c_lam[tid] = (int8_t)lam2;
-    }
-    __syncthreads();
-    // Eq. 3: the least objective per backend of each candidate (a warp each)
-    for (int c = wid; c < C; c += kLoopThreads / 32) {
-        const int32_t g = c_g[c];
-        const long long rb = c_rbase[c];
-        int32_t sl[LLAMA_MAX_HW];
-#pragma unroll
-        for (int h = 0; h < LLAMA_MAX_HW; ++h)
-            sl[h] = h < H ? slack_of(P.ref[g], P.cp[g], P.cp_magic[g], rb - P.q[h]) : 0;
+        int32_t cnt[LLAMA_MAX_HW];
+        d2 = stair_decide(P, g2, rb, &lam2, cnt);
+        // Eq. 3: the least objective per backend under the same slacks, from
+        // the minima tables at the counts the decision searched
+        const int64_t *om = L.objmin + P.stair_off[g2];
+        const int64_t stride = P.cfg_off[g2 + 1] - P.cfg_off[g2] + 1;
         int64_t best[LLAMA_MAX_HW];
-        warp_backend_minima(P, g, sl, best);
-        if (lane == 0) c_aff[c] = affinity_of(best, H, c_lam[c]);
+#pragma unroll
+        for (int h = 0; h < LLAMA_MAX_HW; ++h) best[h] = h < H ? __ldg(om + h * stride + cnt[h]) : INT64_MAX;
+        c_aff[tid] = affinity_of(best, H, lam2);
+        c_lam[tid] = (int8_t)lam2;
     }
     __syncthreads();
     // the commit order: by backend, descending affinity, then candidate order

@@ -305,6 +305,7 @@ ContextView view_of(const llama_ctx *c) {
     v.score_chunk = c->score_chunk;
     v.dlat_cap = c->dlat_cap;
     v.score_smem = c->score_smem;
+    v.max_ncfg = c->max_ncfg;
     // the count pass: where some op may have more distinct latencies than the
     // scoring kernel stages, if asked for, or by default when such ops are at
     // least half of them (few invocations per table: the scoring kernel's own

@@ -213,6 +213,7 @@ struct ContextView {
     int32_t dlat_cap;     // distinct latencies the scoring kernel stages (a multiple of 4)
     size_t score_smem;    // dynamic shared memory of the scoring kernel
     bool need_counts;     // some op may have more distinct latencies than dlat_cap
+    int32_t max_ncfg;     // configurations of the largest op
 };
 int context_view(llama_ctx *c, ContextView *v);  // LLAMA_OK or the readiness error
 int context_fail(llama_ctx *c, int code, const char *msg);
@@ -340,6 +341,9 @@ struct LoopDev {
     int32_t *sq;                        // [n_hw][slots] speculative queues (rings of slot ids)
     int32_t *cq;                        // [n_hw][cq_stride] commit queues
     int64_t *q;                         // [LLAMA_MAX_HW] the tick's queueing time (P.q points here)
+    // Eq. 3's per-backend minima per op, backend and count of distinct latencies
+    // below the slack (k_encode_objmin; the staircase tables' indexing)
+    int64_t *objmin;
     int32_t slots, cq_stride, max_admit;
     int32_t cq_cap[LLAMA_MAX_HW];
 };
@@ -354,5 +358,8 @@ cudaError_t enqueue_loop_tick(const DevProblem &P, const LoopDev &L, const LoopT
 // Critical paths of every DAG (a1), on s.
 cudaError_t enqueue_critical_paths(const ContextView &v, cudaStream_t s);
 int context_ensure_stair(llama_ctx *c);  // staircase tables for the current profiles
+// Eq. 3's minima tables of the current profiles into objmin (as many elements
+// as the staircase tables, H * (n_cfg + n_ops)), on s.
+cudaError_t enqueue_encode_objmin(const ContextView &v, int64_t *objmin, cudaStream_t s);
 
 }  // namespace llama

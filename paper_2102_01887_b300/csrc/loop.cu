@@ -95,17 +95,25 @@ int loop_cuda(llama_loop *lp, cudaError_t e, const char *what) {
                      std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-// The context's current tables (staircase included), critical paths computed
-// on the loop's stream, and the problem view the ticks use (P.q = the loop's
-// queueing-time array).
+// The context's current tables (staircase included), Eq. 3's minima tables and
+// the critical paths computed on the loop's stream, and the problem view the
+// ticks use (P.q = the loop's queueing-time array).
 int loop_tables(llama_loop *lp) {
     int rc = context_ensure_stair(lp->ctx);
     if (rc) return rc;
     ContextView v;
     if ((rc = context_view(lp->ctx, &v))) return rc;
-    cudaError_t e = enqueue_critical_paths(v, lp->stream);
+    cudaError_t e = cudaSuccess;
+    if (!lp->L.objmin) {  // sized by the profiles, which a loop keeps
+        int64_t *om = nullptr;
+        if ((e = lp->dalloc(&om, (size_t)v.n_hw * (size_t)(v.P.n_cfg + v.n_ops))) != cudaSuccess)
+            return loop_cuda(lp, e, "Eq. 3 minima tables");
+        lp->L.objmin = om;
+    }
+    e = enqueue_encode_objmin(v, lp->L.objmin, lp->stream);
+    if (e == cudaSuccess) e = enqueue_critical_paths(v, lp->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(lp->stream);
-    if (e != cudaSuccess) return loop_cuda(lp, e, "critical paths");
+    if (e != cudaSuccess) return loop_cuda(lp, e, "Eq. 3 minima tables and critical paths");
     lp->P = v.P;
     lp->P.q = lp->L.q;
     return LLAMA_OK;

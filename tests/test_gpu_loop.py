@@ -141,7 +141,8 @@ def test_driver_thread_serves_every_request(L):
     polls: every valid request is speculated and committed once, invalid ones
     are rejected, each decision is its configuration's profile entry with a
     consistent backend, and with every commit queue dispatched whole each tick
-    the loop ends empty with every slot free."""
+    the loop ends empty with every slot free (one more tick after the driver
+    stops dispatches the commits of its last tick)."""
     import time
     p, inv = W.medium(n_inv=20_000)
     req = np.zeros(inv.n, L.LOOP_REQUEST_DTYPE)
@@ -163,6 +164,8 @@ def test_driver_thread_serves_every_request(L):
             for kind in seen:
                 seen[kind].extend(r["id"][r["kind"] == kind].tolist())
         lp.stop()
+        lp.tick(inv.now_us + 10**7, [2**31 - 1] * p.n_hw)
+        lp.sync()
         st = lp.state()
     assert sorted(seen[L.LOOP_REJECTED]) == sorted(np.flatnonzero(req["dag"] < 0).tolist())
     good = sorted(np.flatnonzero(req["dag"] >= 0).tolist())
