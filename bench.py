@@ -85,9 +85,9 @@ def parse():
                     help="selection method: score every configuration, the staircase tables, or the "
                          "learned latency surrogate (trained first, untimed)")
     ap.add_argument("--cpu-seconds", type=float, default=8.0, help="CPU-baseline budget per leg (all cores, one core)")
-    ap.add_argument("--hbm-dags", type=int, default=192,
+    ap.add_argument("--hbm-dags", type=int, default=512,
                     help="DAGs of the HBM-streaming line (8,192 configurations per op, 64 invocations "
-                         "per DAG; 0: no such line)")
+                         "per DAG; 512: about 1.6 GB of caller tables; 0: no such line)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the tiny-call latency, host-link and ALU-peak measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")

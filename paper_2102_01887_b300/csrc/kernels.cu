@@ -219,12 +219,27 @@ __device__ __forceinline__ int tail_lanes_log2(int32_t m, int lg, int ipt, int32
     return lg;
 }
 
+// The warp tiles of op v (ck invocations from bucket position pos, tile
+// descriptor tx) at tile indices tt, tt + 1, ...: 32 * ipt invocations each
+// (lane l of the scoring warp takes its ipt consecutive ones), the last one
+// the rest.  Returns the next tile index.
+__device__ __forceinline__ int32_t write_warp_tiles(const BucketScratch &S, int32_t v, int32_t pos, int32_t ck,
+                                                    int32_t ipt, const int4 &tx, int32_t tt) {
+    for (int32_t j = 0; j < ck; j += 32 * ipt, ++tt) {
+        S.tiles[2 * tt] = make_int4(v, pos + j, min(32 * ipt, ck - j), 0);
+        S.tiles[2 * tt + 1] = tx;
+    }
+    return tt;
+}
+
 // Bucket and tile layout once the counts are final, spread over the counting
 // blocks.  Block b of nb owns a contiguous run of ops in the order P.op_order
 // (largest tables first); each thread a contiguous run of those.  Positions are
 // exclusive prefixes, in that order, of the bucket sizes, of the full tiles and
 // of the tail tiles; every op's full tiles come first in the tile list, the
-// tails after them.
+// tails after them.  The warp tiles of the ops from P.n_cta_ops on count as
+// tails, so they end the list; the thread that lays out op P.n_cta_ops
+// publishes where they start (kCtrlCtaTiles).
 struct LayoutRun {
     int32_t kb, ke;          // this thread's ops: op_order[kb .. ke)
     int4 ki[kKeepOps];       // the first kKeepOps of them stay in registers
@@ -233,8 +248,16 @@ struct LayoutRun {
     int32_t excl[3];         // their exclusive prefixes inside the block
 };
 
-__device__ __forceinline__ void op_tiles(int32_t ck, int32_t nvec, int32_t min_vpl, int32_t ipt,
+// The tiles of an op (bucket-order position k) with ck invocations: full and
+// tail tiles of whole CTAs, or, from position P.n_cta_ops on, warp tiles of
+// 32 * ipt invocations (counted with the tails: they end the tile list).
+__device__ __forceinline__ void op_tiles(int32_t ck, int32_t nvec, int32_t min_vpl, int32_t ipt, bool warp,
                                          int32_t &full, int32_t &tail) {
+    if (warp) {
+        full = 0;
+        tail = (ck + 32 * ipt - 1) / (32 * ipt);
+        return;
+    }
     const int lg = lanes_log2_for(nvec, min_vpl);
     full = full_tiles(ck, lg, ipt);
     tail = ck > full * ((kScoreThreads >> lg) * ipt) ? 1 : 0;
@@ -294,7 +317,7 @@ __device__ void layout_sums(const DevProblem &P, const BucketScratch &S, int32_t
     for (int j = 0; j < kKeepOps; ++j) {
         if (R.kb + j >= R.ke) break;
         int32_t f, t;
-        op_tiles(R.kc[j], R.ki[j].y, min_vpl, ipt, f, t);
+        op_tiles(R.kc[j], R.ki[j].y, min_vpl, ipt, R.kb + j >= P.n_cta_ops, f, t);
         R.loc[0] += R.kc[j];
         R.loc[1] += f;
         R.loc[2] += t;
@@ -303,7 +326,7 @@ __device__ void layout_sums(const DevProblem &P, const BucketScratch &S, int32_t
         const int4 oi = P.ord_info[k];
         const int32_t ck = __ldcg(&S.cnt[(int64_t)oi.x * kCntStride]);
         int32_t f, t;
-        op_tiles(ck, oi.y, min_vpl, ipt, f, t);
+        op_tiles(ck, oi.y, min_vpl, ipt, k >= P.n_cta_ops, f, t);
         R.loc[0] += ck;
         R.loc[1] += f;
         R.loc[2] += t;
@@ -351,11 +374,17 @@ __device__ void layout_write(const DevProblem &P, const BucketScratch &S, int32_
             ck = __ldcg(&S.cnt[(int64_t)oi.x * kCntStride]);
         }
         const int32_t v = oi.x, nvec = oi.y;
-        const int lg = lanes_log2_for(nvec, min_vpl);
-        const int32_t per_tile = (kScoreThreads >> lg) * ipt;
         // {padded entries, distinct latencies, padded offset, first configuration}
         const int4 tx = make_int4(nvec * kVec, oi.w, oi.z, __ldg(P.ord_cbase + k));
         S.op_start[v] = pos;
+        if (k >= P.n_cta_ops) {
+            if (k == P.n_cta_ops) S.ctrl[kCtrlCtaTiles] = (unsigned long long)tt;
+            tt = write_warp_tiles(S, v, pos, ck, ipt, tx, tt);
+            pos += ck;
+            continue;
+        }
+        const int lg = lanes_log2_for(nvec, min_vpl);
+        const int32_t per_tile = (kScoreThreads >> lg) * ipt;
         int32_t j = 0;
         for (; j + per_tile <= ck; j += per_tile, ++tf) {
             S.tiles[2 * tf] = make_int4(v, pos + j, per_tile, lg);
@@ -400,7 +429,7 @@ __device__ void layout_whole(const DevProblem &P, const BucketScratch &S, int32_
     for (int j = 0; j < kW; ++j) {
         if (kb + j >= ke) continue;
         int32_t f, t;
-        op_tiles(ck[j], oi[j].y, min_vpl, ipt, f, t);
+        op_tiles(ck[j], oi[j].y, min_vpl, ipt, kb + j >= P.n_cta_ops, f, t);
         loc[0] += ck[j];
         loc[1] += f;
         loc[2] += t;
@@ -415,10 +444,21 @@ __device__ void layout_whole(const DevProblem &P, const BucketScratch &S, int32_
         const int k = kb + j;
         if (k >= ke) continue;
         const int32_t v = oi[j].x, nvec = oi[j].y, c = ck[j];
+        op_start_s[v] = pos;
+        if (k >= P.n_cta_ops) {
+            if (k >= t0 && k < t1) {
+                S.op_start[v] = pos;
+                if (k == P.n_cta_ops) S.ctrl[kCtrlCtaTiles] = (unsigned long long)tt;
+                write_warp_tiles(S, v, pos, c, ipt, make_int4(nvec * kVec, oi[j].w, oi[j].z, __ldg(P.ord_cbase + k)),
+                                 tt);
+            }
+            tt += (c + 32 * ipt - 1) / (32 * ipt);
+            pos += c;
+            continue;
+        }
         const int lg = lanes_log2_for(nvec, min_vpl);
         const int32_t per_tile = (kScoreThreads >> lg) * ipt;
         const int32_t full = full_tiles(c, lg, ipt), rest = c - full * per_tile;
-        op_start_s[v] = pos;
         if (k >= t0 && k < t1) {
             S.op_start[v] = pos;  // for the count pass
             // {padded entries, distinct latencies, padded offset, first configuration}
@@ -952,6 +992,27 @@ __device__ __forceinline__ void scan_chunk(const DevProblem &P, TileState<IPT> &
     }
 }
 
+// The decision of one invocation of op v (first configuration cbase) from its
+// least key, and its slack on the chosen backend (Algorithm 1 from the
+// remaining time rem), into *dst.
+template <int MODE>
+__device__ __forceinline__ void decode_into(const DevProblem &P, int32_t v, int32_t cbase, uint32_t key,
+                                            int64_t ref, int64_t cp, uint64_t mg, int64_t rem,
+                                            const TileConst &tc, llama_decision *dst) {
+    if (!LLAMA_IN_BOUNDS(P, decode_key_ok(P, v, key, MODE), LLAMA_CHECK_DECODE)) return;
+    int4 d;
+    if (MODE == LLAMA_MODE_ALPHA) d = P.dec[2 * (int64_t)cbase + key];
+    else d = key < 0x8000u ? P.dec[(int64_t)cbase + key] : P.dfast[v];
+    const int32_t sl = slack_of(ref, cp, mg, rem - tc.q[d.x >> 16]);
+    llama_decision dsn;
+    dsn.cfg = d.x & 0xFFFF;
+    dsn.lat = d.y;
+    dsn.cost = (int64_t)(((uint64_t)(uint32_t)d.w << 32) | (uint32_t)d.z);
+    dsn.slack = sl;
+    dsn.flags = d.y < sl ? LLAMA_FLAG_FEASIBLE : 0;
+    *dst = dsn;
+}
+
 // Reduce each group's keys and decode them into decisions.  Every thread of
 // the CTA must call this (a block barrier when groups span several warps).
 template <int MODE, int IPT>
@@ -979,19 +1040,8 @@ __device__ __forceinline__ void finish_tile(const DevProblem &P, const BucketScr
 #pragma unroll
     for (int u = 0; u < IPT; ++u) {
         if (T.s != (u & (T.L - 1)) || T.inv[u] < 0) continue;
-        const int32_t i = T.inv[u];
-        int4 d;
-        if (!LLAMA_IN_BOUNDS(P, decode_key_ok(P, T.v, key[u], MODE), LLAMA_CHECK_DECODE)) continue;
-        if (MODE == LLAMA_MODE_ALPHA) d = P.dec[2 * (int64_t)T.cbase + key[u]];
-        else d = key[u] < 0x8000u ? P.dec[(int64_t)T.cbase + key[u]] : P.dfast[T.v];
-        const int32_t sl = slack_at(S, T, tc, u, d.x >> 16);
-        llama_decision dsn;
-        dsn.cfg = d.x & 0xFFFF;
-        dsn.lat = d.y;
-        dsn.cost = (int64_t)(((uint64_t)(uint32_t)d.w << 32) | (uint32_t)d.z);
-        dsn.slack = sl;
-        dsn.flags = d.y < sl ? LLAMA_FLAG_FEASIBLE : 0;
-        out[i] = dsn;
+        decode_into<MODE>(P, T.v, T.cbase, key[u], T.ref, T.cp, T.mg, (int64_t)S.b_rem[T.pos0 + u], tc,
+                          out + T.inv[u]);
     }
 }
 
@@ -1028,6 +1078,101 @@ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(
 __device__ __forceinline__ void prefetch_l2(const void *src, uint32_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<uint64_t>(src)), "r"(bytes)
                  : "memory");
+}
+
+// The warp tiles [n_cta, n_tiles), after the CTA's last whole-CTA tile: each
+// warp takes them one at a time from a counter (the next claim in flight
+// while a tile is scored), with no block barrier, so up to kScoreWarps tiles
+// per CTA progress independently.  A warp copies the op's rank vectors and
+// distinct latencies into its own kWarpSlice bytes of shared memory with
+// 16-byte loads; lane l takes the tile's invocations l * IPT + u (u < IPT,
+// below m).  Per backend segment, each lane counts the distinct latencies
+// below each of its slacks (a bisection of the staged list), then every lane
+// scans the same vectors of the segment (broadcast reads), as scan_chunk does
+// with one lane per group; each lane then decodes its invocations.  Every
+// thread of the CTA calls this after a block barrier (the whole-CTA staging
+// buffers are free: no copy in flight).
+template <int MODE, int IPT>
+__device__ __forceinline__ void warp_tiles(const DevProblem &P, const BucketScratch &S, llama_decision *out,
+                                           unsigned char *smem_raw, long long n_cta, long long n_tiles,
+                                           const TileConst &tc) {
+    constexpr int kTb = MODE == LLAMA_MODE_ALPHA ? 6 : 4;  // staged bytes per table entry
+    const int H = P.n_hw, lane = threadIdx.x & 31;
+    unsigned char *slice = smem_raw + (size_t)(threadIdx.x >> 5) * kWarpSlice;
+    unsigned long long claim = 0;
+    if (lane == 0) claim = atomicAdd(&S.ctrl[kCtrlNextWarpTile], 1ull);
+    long long wt = n_cta + (long long)__shfl_sync(0xffffffffu, claim, 0);
+    while (wt < n_tiles) {
+        if (lane == 0) claim = atomicAdd(&S.ctrl[kCtrlNextWarpTile], 1ull);  // the tile after this one
+        const int4 tile = S.tiles[2 * wt], tx = S.tiles[2 * wt + 1];
+        const int32_t v = tile.x, m = tile.z, npad = tx.x, dn = tx.y, cbase = tx.w;
+        const int64_t p0 = tx.z;
+        // tables at padded offsets (multiples of 8 entries: 16-byte aligned);
+        // the distinct latencies after the table (npad * kTb is a multiple of 16)
+        const bool fits = LLAMA_IN_BOUNDS(P, p0 >= 0 && p0 + npad <= P.n_pad && (size_t)npad * (kTb + 4) <= kWarpSlice &&
+                                                 dn <= npad && tile.y >= 0 && tile.y + m <= S.n_inv,
+                                          LLAMA_CHECK_TILE);
+        uint4 *lr4 = reinterpret_cast<uint4 *>(slice);
+        uint4 *rf4 = lr4 + npad / kVec;
+        uint4 *df4 = rf4 + npad / kVec;
+        int32_t *dl_s = reinterpret_cast<int32_t *>(slice + (size_t)npad * kTb);
+        if (fits) {
+            const uint4 *glr = reinterpret_cast<const uint4 *>(P.lrb + p0);
+            const uint4 *grf = reinterpret_cast<const uint4 *>(P.rf + p0);
+            const uint4 *gdf = reinterpret_cast<const uint4 *>(P.df + p0);
+            for (int k = lane; k < npad / kVec; k += 32) {
+                lr4[k] = __ldg(glr + k);
+                rf4[k] = __ldg(grf + k);
+                if (MODE == LLAMA_MODE_ALPHA) df4[k] = __ldg(gdf + k);
+            }
+            const int4 *gdl = reinterpret_cast<const int4 *>(P.dlat + p0);
+            for (int k = lane; k < (dn + 3) / 4; k += 32) reinterpret_cast<int4 *>(dl_s)[k] = __ldg(gdl + k);
+        }
+        int32_t inv[IPT];
+        int64_t rem[IPT];
+        uint32_t best[IPT];
+#pragma unroll
+        for (int u = 0; u < IPT; ++u) {
+            const int32_t j = lane * IPT + u;
+            const bool in = fits && j < m;
+            inv[u] = in ? S.b_inv[tile.y + j] : -1;
+            if (!LLAMA_IN_BOUNDS(P, inv[u] < S.n_inv, LLAMA_CHECK_TILE)) inv[u] = -1;
+            rem[u] = in ? (int64_t)S.b_rem[tile.y + j] : 0;
+            best[u] = 0xFFFFFFFFu;
+        }
+        const int64_t ref = P.ref[v], cp = P.cp[v];
+        const uint64_t mg = P.cp_magic[v];
+        const int32_t *sp = P.seg_pad + (int64_t)v * (H + 1);
+        __syncwarp();
+        for (int h = 0; fits && h < H; ++h) {
+            const int a = __ldg(sp + h) / kVec, b = __ldg(sp + h + 1) / kVec;
+            if (a >= b) continue;
+            uint32_t c2[IPT];
+#pragma unroll
+            for (int u = 0; u < IPT; ++u)
+                c2[u] = inv[u] >= 0 ? (uint32_t)count_below(dl_s, dn, slack_of(ref, cp, mg, rem[u] - tc.q[h])) *
+                                          0x00010001u
+                                    : 0u;
+            for (int q = a; q < b; ++q) {
+                const uint4 lk = lr4[q], rk = rf4[q];
+                if (MODE == LLAMA_MODE_ALPHA) {
+                    const uint4 dk = df4[q];
+#pragma unroll
+                    for (int u = 0; u < IPT; ++u) best[u] = scan8_alpha(best[u], c2[u], lk, rk, dk);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < IPT; ++u) best[u] = scan8_cost_first(best[u], c2[u], lk, rk);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < IPT; ++u)
+            if (inv[u] >= 0)
+                decode_into<MODE>(P, v, cbase, min(best[u] & 0xFFFFu, best[u] >> 16), ref, cp, mg, rem[u], tc,
+                                  out + inv[u]);
+        __syncwarp();  // every lane is done with the slice before the next tile is copied in
+        wt = n_cta + (long long)__shfl_sync(0xffffffffu, claim, 0);
+    }
 }
 
 // One staging buffer.  Persistent CTAs take tiles from the tile list: first
@@ -1069,17 +1214,20 @@ __device__ __forceinline__ void score_body(const DevProblem &P, const BucketScra
     if (tid < H) tc.q[tid] = P.q[tid];
     // after a bucketing barrier gave up, no tile list or bucket entry is read
     const long long n_tiles = call_timed_out(S) ? 0 : (long long)S.ctrl[kCtrlTiles];
+    // the whole-CTA tiles come first; the warp tiles after them
+    const long long n_cta =
+        P.n_cta_ops < P.n_ops ? min((long long)S.ctrl[kCtrlCtaTiles], n_tiles) : n_tiles;
     long long ti = blockIdx.x;
     // the first chunk of a tile, from the tile's descriptor tx = {npad, dn, p0}
     // (every op has at least one configuration: npad > 0)
     const auto first_chunk = [&](const int4 &tx) {
         stage_chunk<MODE>(P, (int64_t)tx.z, 0, min(chunk, tx.x), tx.y <= dl_cap, tx.y, lr_s, rf_s, df_s, dl_s, bar);
     };
-    if (ti < n_tiles && tid == 0) first_chunk(S.tiles[2 * ti + 1]);
-    bool pending = ti < n_tiles;  // a copy into the buffer is in flight
+    if (ti < n_cta && tid == 0) first_chunk(S.tiles[2 * ti + 1]);
+    bool pending = ti < n_cta;  // a copy into the buffer is in flight
     __syncthreads();
     TileState<IPT> T;
-    while (ti < n_tiles) {
+    while (ti < n_cta) {
         unsigned long long claim = 0;
         if (tid == 0) claim = atomicAdd(&S.ctrl[kCtrlNextTile], 1ull);  // the tile after this one
         tile_begin(P, S, ti, tc, T);
@@ -1108,7 +1256,7 @@ __device__ __forceinline__ void score_body(const DevProblem &P, const BucketScra
                 if (tid == 0) {
                     const long long tn = (long long)(claim + gridDim.x);
                     next_tile = tn;
-                    if (tn < n_tiles) {
+                    if (tn < n_cta) {
                         // the next tile's first chunk goes to L2 while this one is scored
                         txn = S.tiles[2 * tn + 1];
                         const uint32_t pb = 2u * (uint32_t)min(chunk, txn.x);
@@ -1127,7 +1275,7 @@ __device__ __forceinline__ void score_body(const DevProblem &P, const BucketScra
         if (!ok) break;
         __syncthreads();  // the scan is done with the buffer; next_tile is published
         const long long tn = next_tile;
-        if (tn < n_tiles) {
+        if (tn < n_cta) {
             if (tid == 0) first_chunk(txn);
             pending = true;
         }
@@ -1139,6 +1287,10 @@ __device__ __forceinline__ void score_body(const DevProblem &P, const BucketScra
         // to land so no transfer targets this CTA's shared memory after exit
         if (!ok && tid == 0) atomicOr(&S.ctrl[kCtrlTimeout], 1ull);
         mbar_wait(bar, phase);
+    }
+    if (ok && n_cta < n_tiles) {
+        __syncthreads();  // every thread is done with the staging buffer
+        warp_tiles<MODE, IPT>(P, S, out, smem_raw, n_cta, n_tiles, tc);
     }
     finish_call(S, out, true);
 }
@@ -1184,9 +1336,12 @@ __device__ __forceinline__ void score_body_pipe(const DevProblem &P, const Bucke
     if (tid < H) tc.q[tid] = P.q[tid];
     // after a bucketing barrier gave up, no tile list or bucket entry is read
     const long long n_tiles = call_timed_out(S) ? 0 : (long long)S.ctrl[kCtrlTiles];
+    // the whole-CTA tiles come first; the warp tiles after them
+    const long long n_cta =
+        P.n_cta_ops < P.n_ops ? min((long long)S.ctrl[kCtrlCtaTiles], n_tiles) : n_tiles;
     long long ti = blockIdx.x, tn;
     if (tid == 0) next_tile = (long long)atomicAdd(&S.ctrl[kCtrlNextTile], 1ull) + gridDim.x;
-    if (ti < n_tiles) {
+    if (ti < n_cta) {
         if (tid == 0) issue(0, S.tiles[2 * ti + 1], 0);
         pending = 1u;
     }
@@ -1194,10 +1349,10 @@ __device__ __forceinline__ void score_body_pipe(const DevProblem &P, const Bucke
     tn = next_tile;
     int st = 0;
     TileState<IPT> T;
-    while (ti < n_tiles) {
+    while (ti < n_cta) {
         unsigned long long claim = 0;
         if (tid == 0) claim = atomicAdd(&S.ctrl[kCtrlNextTile], 1ull);  // the tile after tn
-        const int4 txn = tn < n_tiles ? S.tiles[2 * tn + 1] : make_int4(0, 0, 0, 0);
+        const int4 txn = tn < n_cta ? S.tiles[2 * tn + 1] : make_int4(0, 0, 0, 0);
         tile_begin(P, S, ti, tc, T);
         const bool dl_staged = T.dn <= dl_cap;
         uint16_t *cg = c_s + T.g * IPT * H;
@@ -1205,7 +1360,7 @@ __device__ __forceinline__ void score_body_pipe(const DevProblem &P, const Bucke
             const int32_t cn = min(chunk, T.npad - c0);
             __syncthreads();  // every thread is done with the other stage and with cg
             // the item after this one: the next chunk, or the next tile's first
-            if (c0 + chunk < T.npad || tn < n_tiles) {
+            if (c0 + chunk < T.npad || tn < n_cta) {
                 if (tid == 0) {
                     if (c0 + chunk < T.npad) issue(st ^ 1, make_int4(T.npad, T.dn, (int32_t)T.p0, 0), c0 + chunk);
                     else issue(st ^ 1, txn, 0);
@@ -1242,6 +1397,10 @@ __device__ __forceinline__ void score_body_pipe(const DevProblem &P, const Bucke
         if (tid == 0) atomicOr(&S.ctrl[kCtrlTimeout], 1ull);
         for (int k = 0; k < 2; ++k)
             if (pending & (1u << k)) mbar_wait(bar0 + 8 * k, (phases >> k) & 1u);
+    }
+    if (ok && n_cta < n_tiles) {
+        __syncthreads();  // every thread is done with the staging buffers
+        warp_tiles<MODE, IPT>(P, S, out, smem_raw, n_cta, n_tiles, tc);
     }
     finish_call(S, out, true);
 }

@@ -132,6 +132,7 @@ struct llama_ctx {
     int last_launches = 0;
     int32_t max_ncfg = 0;  // configurations of the largest op
     int32_t n_big_ops = 0;  // ops with more padded entries than dlat_cap
+    int32_t n_cta_ops = 0;  // ops (bucket order) scored by whole CTAs; the rest by warp tiles
     int32_t count_pass = LLAMA_COUNT_PASS_AUTO;
     int32_t wait_tries = kMaxWaitTries;  // polls of a bucketing grid barrier (llama_set_wait_limit)
     cudaEvent_t trace[LLAMA_TRACE_EVENTS] = {};
@@ -219,6 +220,7 @@ DevProblem make_problem(const llama_ctx *c) {
     P.op_order = c->op_order.as<int32_t>();
     P.max_npad = c->max_npad;
     P.n_big_ops = c->n_big_ops;
+    P.n_cta_ops = c->n_cta_ops;
     // prefetch the encoded tables into L2 when they take at most half of it
     const int64_t tbl_bytes = (int64_t)(c->opts.mode == LLAMA_MODE_ALPHA ? 10 : 8) * c->n_pad;
     const bool pf = c->n_pad > 0 && tbl_bytes <= c->l2_bytes / 2;
@@ -498,7 +500,9 @@ int grid_for(const llama_ctx *c, int64_t n, int threads) {
 size_t score_smem_bytes(const llama_ctx *c) {
     const size_t tbl = ((size_t)c->score_chunk * (c->opts.mode == LLAMA_MODE_ALPHA ? 6 : 4) + 15) / 16 * 16;
     const size_t counts = (size_t)kScoreThreads * c->ipt * c->opts.n_hw * 2;
-    return (size_t)c->stages * (tbl + 4 * (size_t)c->dlat_cap) + counts;
+    const size_t cta = (size_t)c->stages * (tbl + 4 * (size_t)c->dlat_cap) + counts;
+    // the warp phase reuses the same memory: one slice per warp
+    return c->n_cta_ops < c->n_ops ? std::max(cta, (size_t)kScoreWarps * kWarpSlice) : cta;
 }
 
 // Default staging chunk: the largest padded table split into the fewest pieces
@@ -979,6 +983,10 @@ extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cf
         c->dlat_cap = (cap + 3) / 4 * 4;
         c->n_big_ops = 0;
         for (int32_t v = 0; v < n_ops; ++v) c->n_big_ops += pad_off[v + 1] - pad_off[v] > c->dlat_cap;
+        // ops whose padded table fits a warp's slice are scored by warp tiles:
+        // the end of the bucket order (largest tables first)
+        c->n_cta_ops = 0;
+        for (int32_t v = 0; v < n_ops; ++v) c->n_cta_ops += pad_off[v + 1] - pad_off[v] > warp_pad_of(c->opts.mode);
         c->h_dn = std::move(dn);
     }
     c->stair_ready = false;

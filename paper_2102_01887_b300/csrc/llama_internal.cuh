@@ -38,6 +38,16 @@ constexpr uint16_t kLatRankPad = 0xBFFF;   // at pads: above any count of distin
 constexpr int kScoreThreads = 256;
 constexpr int kScoreThreadsLog2 = 8;
 constexpr int kMaxChunk = 4096;        // table entries staged at a time by the scoring kernel
+// Warp tiles: an op whose padded table and distinct latencies fit one warp's
+// slice of the scoring kernel's shared memory is scored by single warps, each
+// taking 32 * IPT of its invocations, with no block barrier
+constexpr int kScoreWarps = kScoreThreads / 32;
+constexpr int kWarpSlice = 4608;       // bytes of shared memory per warp in the warp phase
+// largest padded table scored by warp tiles: table (4 B per entry, 6 in alpha
+// mode) and distinct latencies (at most one 4-byte value per entry) in a slice
+__host__ __device__ constexpr int32_t warp_pad_of(int mode) {
+    return kWarpSlice / (mode == LLAMA_MODE_ALPHA ? 10 : 8) / kVec * kVec;
+}
 constexpr int kMaxWaitTries = LLAMA_WAIT_LIMIT_DEFAULT;  // bounded waits (mbarrier, grid barrier)
 constexpr int kKeep = 4;               // invocations a counting thread keeps in registers
 constexpr int kKeepOps = 2;            // ops the layout keeps in registers per thread
@@ -53,7 +63,9 @@ constexpr int kCtrlTimeout = 4;    // nonzero: a bounded device wait gave up
 constexpr int kCtrlNextTile = 5;   // dynamic tile counter of the scoring kernel
 constexpr int kCtrlBarrier = 6;    // grid barrier of k_bucket
 constexpr int kCtrlDone = 7;       // CTAs of the scoring kernel that have finished
-constexpr int kCtrlWords = 8;
+constexpr int kCtrlNextWarpTile = 8;  // dynamic warp-tile counter of the scoring kernel
+constexpr int kCtrlCtaTiles = 9;   // tiles scored by whole CTAs (the warp tiles follow them)
+constexpr int kCtrlWords = 10;
 // Status of the last completed call, after the control words: {invalid
 // invocations, nonzero if a bounded device wait gave up}
 constexpr int kStatusWords = 2;
@@ -98,6 +110,9 @@ struct DevProblem {
     const int32_t *fast;
     const int32_t *op_order;  // ops by padded table size, largest first (bucket order)
     int32_t max_npad;  // largest padded op table (entries)
+    // ops in bucket order scored by whole CTAs; the rest (padded tables of at
+    // most warp_pad entries, the end of the bucket order) by single warps
+    int32_t n_cta_ops;
     // ops whose padded tables exceed the distinct latencies the scoring kernel
     // stages: the first n_big_ops of op_order, so their bucket positions come first
     int32_t n_big_ops;
