@@ -99,8 +99,9 @@ def parse():
     ap.add_argument("--train-epochs", type=int, default=11,
                     help="surrogate: training epochs before the timed calls (0: untrained network, for profiling)")
     ap.add_argument("--tuning", default=None,
-                    help="fixed scoring schedule 'lanes_min_vectors,inv_per_thread,chunk,stages[,count_pass]' "
-                         "(no autotuning; count_pass 0 auto, 1 on, 2 off)")
+                    help="fixed scoring schedule 'lanes_min_vectors,inv_per_thread,chunk,stages"
+                         "[,count_pass[,ctas_per_sm]]' (no autotuning; count_pass 0 auto, 1 on, 2 off; "
+                         "ctas_per_sm 0 = as many as fit)")
     return ap.parse_args()
 
 
@@ -915,11 +916,14 @@ def main():
 
     tuning = None
     if args.tuning:
-        lmv, ipt, chunk, stages, *cpass = (int(x) for x in args.tuning.split(","))
+        lmv, ipt, chunk, stages, *rest = (int(x) for x in args.tuning.split(","))
+        cpass = rest[0] if rest else L.COUNT_PASS_AUTO
+        per_sm = rest[1] if len(rest) > 1 else 0
         L.llama_set_tuning(ctx, lmv, ipt, chunk, stages)
-        L.llama_set_count_pass(ctx, cpass[0] if cpass else L.COUNT_PASS_AUTO)
+        L.llama_set_count_pass(ctx, cpass)
+        L.llama_set_score_occupancy(ctx, per_sm)
         tuning = {"best": {"lanes_min_vectors": lmv, "inv_per_thread": ipt, "chunk": chunk, "stages": stages,
-                           "count_pass": cpass[0] if cpass else L.COUNT_PASS_AUTO},
+                           "count_pass": cpass, "ctas_per_sm": per_sm},
                   "trials": []}
     elif not args.no_autotune and args.method == "scan":
         # choose the scoring schedule on this batch before anything is timed;
@@ -1139,7 +1143,7 @@ def main():
         "roofline": roofline,
         "rooflines": rooflines,
         "schedule_trials": ([{k: t[k] for k in ("lanes_min_vectors", "inv_per_thread", "chunk", "stages",
-                                                "count_pass", "ms") if k in t}
+                                                "count_pass", "ctas_per_sm", "ms") if k in t}
                              for t in tuning["trials"]] if tuning and tuning["trials"] else None),
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
         "parity_vs_oracle": parity, "set_profiles_ms": set_profiles_ms, **extras,

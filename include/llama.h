@@ -297,6 +297,15 @@ int llama_static_status(llama_ctx *ctx, void *stream, int64_t *invalid, int32_t 
 int llama_set_tuning(llama_ctx *ctx, int32_t lanes_min_vectors, int32_t inv_per_thread,
                      int32_t chunk_entries, int32_t stages);
 
+/* Persistent CTAs of the scoring kernel per SM (no counterpart in the paper;
+ * changes speed, never results): 0 (default) as many as its registers and
+ * shared memory allow, else at most ctas_per_sm (1..32).  Fewer, larger
+ * shares of the SM can be faster where staging and scanning contend; more
+ * CTAs keep more table copies in flight where tables stream from DRAM.
+ * Call after llama_set_profiles (which resets it to 0).  Errors: EINVAL,
+ * ENOTREADY (no profiles), ECUDA. */
+int llama_set_score_occupancy(llama_ctx *ctx, int32_t ctas_per_sm);
+
 /* Count pass of the scan method (no counterpart in the paper; changes speed,
  * never results).  Operations with more distinct latencies than the scoring
  * kernel stages in shared memory need, per invocation and backend, the number

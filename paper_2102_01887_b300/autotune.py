@@ -1,8 +1,9 @@
 """Autotuner of the scoring kernel's launch schedule.
 
 The schedule (lanes sharing one invocation, invocations per thread, staging
-chunk, staging buffers, and whether a count pass precedes the scoring kernel)
-changes speed, never results (tests check the latter).  For a given
+chunk, staging buffers, whether a count pass precedes the scoring kernel, and
+how many scoring CTAs share an SM) changes speed, never results (tests check
+the latter).  For a given
 context and a batch of device-resident invocations, the tuner times every
 candidate on that batch -- whole scheduling calls replayed as the caller
 would replay them, the L2 cache flushed before each call -- and keeps the
@@ -18,6 +19,7 @@ from . import llama as L
 DEFAULT_LANES_MIN_VECTORS = (4, 8, 16, 32, 64)
 DEFAULT_INV_PER_THREAD = (1, 2, 4)
 DEFAULT_STAGES = (1, 2)
+DEFAULT_CTAS_PER_SM = (0, 4, 3)  # 0: as many as fit
 
 
 def time_call(ctx, dag, op_local, start, now: int, out, stream, flush, reps: int = 5) -> float:
@@ -42,11 +44,13 @@ def time_call(ctx, dag, op_local, start, now: int, out, stream, flush, reps: int
 def autotune(ctx, dag, op_local, start, now: int, out, stream=None, flush=None,
              lanes: Iterable[int] = DEFAULT_LANES_MIN_VECTORS,
              ipts: Iterable[int] = DEFAULT_INV_PER_THREAD, chunks: Iterable[int] = (0,),
-             stages: Iterable[int] = DEFAULT_STAGES, reps: int = 5) -> dict:
+             stages: Iterable[int] = DEFAULT_STAGES, ctas_per_sm: Iterable[int] = DEFAULT_CTAS_PER_SM,
+             reps: int = 5) -> dict:
     """Sweep the candidates, apply the fastest, return {"best": ..., "trials": [...]}.
 
     ``chunks``: staging chunk sizes in configurations (0 = the library default);
-    ``stages``: staging buffers per CTA (1 or 2).
+    ``stages``: staging buffers per CTA (1 or 2); ``ctas_per_sm``: caps on the
+    scoring CTAs per SM, tried for the fastest schedule (0 = as many as fit).
     """
     import torch
     if stream is None:
@@ -55,6 +59,7 @@ def autotune(ctx, dag, op_local, start, now: int, out, stream=None, flush=None,
         flush = torch.empty(256 << 20, dtype=torch.uint8, device=dag.device)
     trials = []
     L.llama_set_count_pass(ctx, L.COUNT_PASS_AUTO)
+    L.llama_set_score_occupancy(ctx, 0)
     for st, chunk, lmv, ipt in itertools.product(stages, chunks, lanes, ipts):
         L.llama_set_tuning(ctx, lmv, ipt, chunk, st)
         ms = time_call(ctx, dag, op_local, start, now, out, stream, flush, reps)
@@ -74,4 +79,15 @@ def autotune(ctx, dag, op_local, start, now: int, out, stream=None, flush=None,
         if ms < best["ms"]:
             best = trials[-1]
     L.llama_set_count_pass(ctx, best["count_pass"])
+    # the CTAs per SM for that schedule
+    best = dict(best, ctas_per_sm=0)
+    for cap in ctas_per_sm:
+        if cap == 0:
+            continue
+        L.llama_set_score_occupancy(ctx, cap)
+        ms = time_call(ctx, dag, op_local, start, now, out, stream, flush, reps)
+        trials.append(dict(best, ctas_per_sm=cap, ms=ms))
+        if ms < best["ms"]:
+            best = trials[-1]
+    L.llama_set_score_occupancy(ctx, best["ctas_per_sm"])
     return {"best": best, "trials": trials}

@@ -1182,7 +1182,7 @@ __device__ __forceinline__ void warp_tiles(const DevProblem &P, const BucketScra
 // tile starts and its descriptor read while the tile's copy lands, so its
 // first chunk is copied as soon as the scan is done with the buffer, while
 // this tile's decisions are decoded.
-template <int MODE, int IPT>
+template <int MODE, int IPT, bool WARP>
 __device__ __forceinline__ void score_body(const DevProblem &P, const BucketScratch &S,
                                            llama_decision *out, int32_t chunk, int32_t dl_cap) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1214,9 +1214,11 @@ __device__ __forceinline__ void score_body(const DevProblem &P, const BucketScra
     if (tid < H) tc.q[tid] = P.q[tid];
     // after a bucketing barrier gave up, no tile list or bucket entry is read
     const long long n_tiles = call_timed_out(S) ? 0 : (long long)S.ctrl[kCtrlTiles];
-    // the whole-CTA tiles come first; the warp tiles after them
+    // the whole-CTA tiles come first; the warp tiles after them (a kernel
+    // without the warp phase scores any warp tile as a CTA tile of one lane
+    // per invocation, with the same result)
     const long long n_cta =
-        P.n_cta_ops < P.n_ops ? min((long long)S.ctrl[kCtrlCtaTiles], n_tiles) : n_tiles;
+        WARP && P.n_cta_ops < P.n_ops ? min((long long)S.ctrl[kCtrlCtaTiles], n_tiles) : n_tiles;
     long long ti = blockIdx.x;
     // the first chunk of a tile, from the tile's descriptor tx = {npad, dn, p0}
     // (every op has at least one configuration: npad > 0)
@@ -1288,7 +1290,7 @@ __device__ __forceinline__ void score_body(const DevProblem &P, const BucketScra
         if (!ok && tid == 0) atomicOr(&S.ctrl[kCtrlTimeout], 1ull);
         mbar_wait(bar, phase);
     }
-    if (ok && n_cta < n_tiles) {
+    if (WARP && ok && n_cta < n_tiles) {
         __syncthreads();  // every thread is done with the staging buffer
         warp_tiles<MODE, IPT>(P, S, out, smem_raw, n_cta, n_tiles, tc);
     }
@@ -1300,7 +1302,7 @@ __device__ __forceinline__ void score_body(const DevProblem &P, const BucketScra
 // claimed from the counter one tile ahead: while tile k is scored the CTA
 // already knows tile k + 1 (its first chunk is staged during tile k) and the
 // claim of tile k + 2 is in flight.
-template <int MODE, int IPT>
+template <int MODE, int IPT, bool WARP>
 __device__ __forceinline__ void score_body_pipe(const DevProblem &P, const BucketScratch &S,
                                                 llama_decision *out, int32_t chunk, int32_t dl_cap) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1336,9 +1338,11 @@ __device__ __forceinline__ void score_body_pipe(const DevProblem &P, const Bucke
     if (tid < H) tc.q[tid] = P.q[tid];
     // after a bucketing barrier gave up, no tile list or bucket entry is read
     const long long n_tiles = call_timed_out(S) ? 0 : (long long)S.ctrl[kCtrlTiles];
-    // the whole-CTA tiles come first; the warp tiles after them
+    // the whole-CTA tiles come first; the warp tiles after them (a kernel
+    // without the warp phase scores any warp tile as a CTA tile of one lane
+    // per invocation, with the same result)
     const long long n_cta =
-        P.n_cta_ops < P.n_ops ? min((long long)S.ctrl[kCtrlCtaTiles], n_tiles) : n_tiles;
+        WARP && P.n_cta_ops < P.n_ops ? min((long long)S.ctrl[kCtrlCtaTiles], n_tiles) : n_tiles;
     long long ti = blockIdx.x, tn;
     if (tid == 0) next_tile = (long long)atomicAdd(&S.ctrl[kCtrlNextTile], 1ull) + gridDim.x;
     if (ti < n_cta) {
@@ -1398,40 +1402,51 @@ __device__ __forceinline__ void score_body_pipe(const DevProblem &P, const Bucke
         for (int k = 0; k < 2; ++k)
             if (pending & (1u << k)) mbar_wait(bar0 + 8 * k, (phases >> k) & 1u);
     }
-    if (ok && n_cta < n_tiles) {
+    if (WARP && ok && n_cta < n_tiles) {
         __syncthreads();  // every thread is done with the staging buffers
         warp_tiles<MODE, IPT>(P, S, out, smem_raw, n_cta, n_tiles, tc);
     }
     finish_call(S, out, true);
 }
 
-#define LLAMA_SCORE_KERNEL(name, MODE, IPT, BODY)                                                \
+// Every (objective mode, invocations per thread, staging buffers) twice: with
+// the warp phase (suffix w, for profiles with ops scored by warp tiles) and
+// without it (fewer registers: more CTAs per SM where no op needs it).
+#define LLAMA_SCORE_KERNEL(name, MODE, IPT, BODY, WARP)                                         \
     __global__ void __launch_bounds__(kScoreThreads)                                            \
         name(DevProblem P, BucketScratch S, llama_decision *out, int32_t chunk, int32_t dl_cap) { \
-        BODY<MODE, IPT>(P, S, out, chunk, dl_cap);                                                \
+        BODY<MODE, IPT, WARP>(P, S, out, chunk, dl_cap);                                          \
     }
-LLAMA_SCORE_KERNEL(k_score_cf1, LLAMA_MODE_COST_FIRST, 1, score_body)
-LLAMA_SCORE_KERNEL(k_score_cf2, LLAMA_MODE_COST_FIRST, 2, score_body)
-LLAMA_SCORE_KERNEL(k_score_cf4, LLAMA_MODE_COST_FIRST, 4, score_body)
-LLAMA_SCORE_KERNEL(k_score_al1, LLAMA_MODE_ALPHA, 1, score_body)
-LLAMA_SCORE_KERNEL(k_score_al2, LLAMA_MODE_ALPHA, 2, score_body)
-LLAMA_SCORE_KERNEL(k_score_al4, LLAMA_MODE_ALPHA, 4, score_body)
-LLAMA_SCORE_KERNEL(k_score2_cf1, LLAMA_MODE_COST_FIRST, 1, score_body_pipe)
-LLAMA_SCORE_KERNEL(k_score2_cf2, LLAMA_MODE_COST_FIRST, 2, score_body_pipe)
-LLAMA_SCORE_KERNEL(k_score2_cf4, LLAMA_MODE_COST_FIRST, 4, score_body_pipe)
-LLAMA_SCORE_KERNEL(k_score2_al1, LLAMA_MODE_ALPHA, 1, score_body_pipe)
-LLAMA_SCORE_KERNEL(k_score2_al2, LLAMA_MODE_ALPHA, 2, score_body_pipe)
-LLAMA_SCORE_KERNEL(k_score2_al4, LLAMA_MODE_ALPHA, 4, score_body_pipe)
+#define LLAMA_SCORE_KERNELS(name, MODE, IPT, BODY)  \
+    LLAMA_SCORE_KERNEL(name, MODE, IPT, BODY, false) \
+    LLAMA_SCORE_KERNEL(name##w, MODE, IPT, BODY, true)
+LLAMA_SCORE_KERNELS(k_score_cf1, LLAMA_MODE_COST_FIRST, 1, score_body)
+LLAMA_SCORE_KERNELS(k_score_cf2, LLAMA_MODE_COST_FIRST, 2, score_body)
+LLAMA_SCORE_KERNELS(k_score_cf4, LLAMA_MODE_COST_FIRST, 4, score_body)
+LLAMA_SCORE_KERNELS(k_score_al1, LLAMA_MODE_ALPHA, 1, score_body)
+LLAMA_SCORE_KERNELS(k_score_al2, LLAMA_MODE_ALPHA, 2, score_body)
+LLAMA_SCORE_KERNELS(k_score_al4, LLAMA_MODE_ALPHA, 4, score_body)
+LLAMA_SCORE_KERNELS(k_score2_cf1, LLAMA_MODE_COST_FIRST, 1, score_body_pipe)
+LLAMA_SCORE_KERNELS(k_score2_cf2, LLAMA_MODE_COST_FIRST, 2, score_body_pipe)
+LLAMA_SCORE_KERNELS(k_score2_cf4, LLAMA_MODE_COST_FIRST, 4, score_body_pipe)
+LLAMA_SCORE_KERNELS(k_score2_al1, LLAMA_MODE_ALPHA, 1, score_body_pipe)
+LLAMA_SCORE_KERNELS(k_score2_al2, LLAMA_MODE_ALPHA, 2, score_body_pipe)
+LLAMA_SCORE_KERNELS(k_score2_al4, LLAMA_MODE_ALPHA, 4, score_body_pipe)
+#undef LLAMA_SCORE_KERNELS
 #undef LLAMA_SCORE_KERNEL
 
-const void *score_kernel(int mode, int ipt, int stages) {
-    const bool al = mode == LLAMA_MODE_ALPHA;
-    if (stages >= 2) {
-        if (al) return ipt >= 4 ? (const void *)k_score2_al4 : ipt == 2 ? (const void *)k_score2_al2 : (const void *)k_score2_al1;
-        return ipt >= 4 ? (const void *)k_score2_cf4 : ipt == 2 ? (const void *)k_score2_cf2 : (const void *)k_score2_cf1;
-    }
-    if (al) return ipt >= 4 ? (const void *)k_score_al4 : ipt == 2 ? (const void *)k_score_al2 : (const void *)k_score_al1;
-    return ipt >= 4 ? (const void *)k_score_cf4 : ipt == 2 ? (const void *)k_score_cf2 : (const void *)k_score_cf1;
+const void *score_kernel(int mode, int ipt, int stages, bool warp) {
+    // [warp][alpha][two stages][log2 ipt]
+    static const void *const fn[2][2][2][3] = {
+        {{{(const void *)k_score_cf1, (const void *)k_score_cf2, (const void *)k_score_cf4},
+          {(const void *)k_score2_cf1, (const void *)k_score2_cf2, (const void *)k_score2_cf4}},
+         {{(const void *)k_score_al1, (const void *)k_score_al2, (const void *)k_score_al4},
+          {(const void *)k_score2_al1, (const void *)k_score2_al2, (const void *)k_score2_al4}}},
+        {{{(const void *)k_score_cf1w, (const void *)k_score_cf2w, (const void *)k_score_cf4w},
+          {(const void *)k_score2_cf1w, (const void *)k_score2_cf2w, (const void *)k_score2_cf4w}},
+         {{(const void *)k_score_al1w, (const void *)k_score_al2w, (const void *)k_score_al4w},
+          {(const void *)k_score2_al1w, (const void *)k_score2_al2w, (const void *)k_score2_al4w}}}};
+    return fn[warp ? 1 : 0][mode == LLAMA_MODE_ALPHA ? 1 : 0][stages >= 2 ? 1 : 0][ipt >= 4 ? 2 : ipt == 2 ? 1 : 0];
 }
 
 // ---------------------------------------------------------------------------
@@ -1918,7 +1933,7 @@ static cudaError_t enqueue_schedule_impl(const ContextView &v, const BucketScrat
     DevProblem P = v.P;
     int32_t chunk = v.score_chunk, dl_cap = v.dlat_cap;
     void *args[] = {&P, &Sc, &out, &chunk, &dl_cap};
-    e = cudaLaunchKernelExC(&cfg, score_kernel(v.mode, v.ipt, v.stages), args);
+    e = cudaLaunchKernelExC(&cfg, score_kernel(v.mode, v.ipt, v.stages, v.warp_tiles), args);
     if (e != cudaSuccess) return e;
     mark(2);
     return cudaGetLastError();

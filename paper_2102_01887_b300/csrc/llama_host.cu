@@ -122,6 +122,7 @@ struct llama_ctx {
     Workspace ws;  // the context's own scratch (llama_schedule, llama_schedule_async)
     // scoring kernel geometry (set by llama_set_profiles)
     int32_t min_vpl = 16, ipt = 2, stages = 1, score_grid = 0, score_chunk = 0, bucket_max_blocks = 0, dlat_cap = 0;
+    int32_t score_per_sm = 0;  // persistent scoring CTAs per SM: 0 = as many as fit
     size_t score_smem = 0;
 
     // staging for host-memory arguments of the blocking calls
@@ -308,6 +309,7 @@ ContextView view_of(const llama_ctx *c) {
     v.dlat_cap = c->dlat_cap;
     v.score_smem = c->score_smem;
     v.max_ncfg = c->max_ncfg;
+    v.warp_tiles = c->n_cta_ops < c->n_ops;
     // the count pass: where some op may have more distinct latencies than the
     // scoring kernel stages, if asked for, or by default when such ops are at
     // least half of them (few invocations per table: the scoring kernel's own
@@ -519,10 +521,11 @@ int32_t default_chunk(int32_t max_npad) {
 // Dynamic shared memory and persistent grid of the scoring kernel for the
 // current profiles and tuning.
 int configure_score(llama_ctx *c) {
-    const void *fn = score_kernel(c->opts.mode, c->ipt, c->stages);
+    const void *fn = score_kernel(c->opts.mode, c->ipt, c->stages, c->n_cta_ops < c->n_ops);
     LL_CUDA(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->score_smem));
     int nb = 0;
     LL_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kScoreThreads, c->score_smem));
+    if (c->score_per_sm > 0) nb = std::min(nb, c->score_per_sm);
     c->score_grid = c->num_sms * std::max(1, nb);
     return LLAMA_OK;
 }
@@ -994,6 +997,7 @@ extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cf
     // scoring kernel: stage tables in chunks of at most kMaxChunk entries, one
     // persistent CTA per resident slot
     c->score_chunk = default_chunk(max_npad);
+    c->score_per_sm = 0;
     c->score_smem = score_smem_bytes(c);
     const int rc = configure_score(c);
     if (rc) return rc;
@@ -1057,6 +1061,17 @@ extern "C" int llama_set_tuning(llama_ctx *c, int32_t lanes_min_vectors, int32_t
     c->stages = stages;
     c->score_chunk = chunk_entries ? std::min<int32_t>(chunk_entries, c->max_npad) : default_chunk(c->max_npad);
     c->score_smem = score_smem_bytes(c);
+    return configure_score(c);
+}
+
+extern "C" int llama_set_score_occupancy(llama_ctx *c, int32_t ctas_per_sm) {
+    if (!c) return LLAMA_EINVAL;
+    if (ctas_per_sm < 0 || ctas_per_sm > 32)
+        return c->fail(LLAMA_EINVAL, "set_score_occupancy: ctas_per_sm out of 0..32");
+    if (!c->prof_set) return c->fail(LLAMA_ENOTREADY, "set_score_occupancy: set the profiles first");
+    DeviceGuard g(c->opts.device);
+    c->drop_graph();
+    c->score_per_sm = ctas_per_sm;
     return configure_score(c);
 }
 

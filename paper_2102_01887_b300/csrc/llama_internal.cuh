@@ -229,6 +229,7 @@ struct ContextView {
     size_t score_smem;    // dynamic shared memory of the scoring kernel
     bool need_counts;     // some op may have more distinct latencies than dlat_cap
     int32_t max_ncfg;     // configurations of the largest op
+    bool warp_tiles;      // some op is scored by warp tiles (the scoring kernel with the warp phase)
 };
 int context_view(llama_ctx *c, ContextView *v);  // LLAMA_OK or the readiness error
 int context_fail(llama_ctx *c, int code, const char *msg);
@@ -243,9 +244,11 @@ __global__ void k_bucket(DevProblem P, int64_t n_inv, const int32_t *dag, const 
                          int32_t min_vpl, int32_t ipt, int32_t n_cp);
 // Scoring kernels: objective mode x invocations per thread (1, 2 or 4) x
 // staging buffers (k_score: one, tiles claimed dynamically; k_score2: two,
-// tiles round-robin).
+// tiles round-robin) x the warp phase (suffix w: after the whole-CTA tiles,
+// the warp tiles of ops whose tables fit a warp's slice).
 #define LLAMA_DECLARE_SCORE(name) \
-    __global__ void name(DevProblem P, BucketScratch S, llama_decision *out, int32_t chunk, int32_t dl_cap);
+    __global__ void name(DevProblem P, BucketScratch S, llama_decision *out, int32_t chunk, int32_t dl_cap); \
+    __global__ void name##w(DevProblem P, BucketScratch S, llama_decision *out, int32_t chunk, int32_t dl_cap);
 LLAMA_DECLARE_SCORE(k_score_cf1)
 LLAMA_DECLARE_SCORE(k_score_cf2)
 LLAMA_DECLARE_SCORE(k_score_cf4)
@@ -259,7 +262,7 @@ LLAMA_DECLARE_SCORE(k_score2_al1)
 LLAMA_DECLARE_SCORE(k_score2_al2)
 LLAMA_DECLARE_SCORE(k_score2_al4)
 #undef LLAMA_DECLARE_SCORE
-const void *score_kernel(int mode, int ipt, int stages);
+const void *score_kernel(int mode, int ipt, int stages, bool warp);
 
 // Scoring tiles a call may lay out (each op: full tiles plus one tail).
 int64_t max_tiles(int64_t n_inv, int32_t n_ops);

@@ -375,10 +375,17 @@ def test_errors(L):
         with pytest.raises(L.LlamaError) as e:  # tuning before the profiles
             L.llama_set_tuning(ctx, 16, 2, 0, 1)
         assert e.value.code == L.ENOTREADY
+        with pytest.raises(L.LlamaError) as e:
+            L.llama_set_score_occupancy(ctx, 4)
+        assert e.value.code == L.ENOTREADY
         for bad in ((0, 2, 0, 1), (2048, 2, 0, 1), (16, 3, 0, 1), (16, 2, 12, 1), (16, 2, 8264, 1),
                     (16, 2, 0, 3), (16, 2, 0, 0)):
             with pytest.raises(L.LlamaError) as e:
                 L.llama_set_tuning(ctx, *bad)
+            assert e.value.code == L.EINVAL, bad
+        for bad in (-1, 33):
+            with pytest.raises(L.LlamaError) as e:
+                L.llama_set_score_occupancy(ctx, bad)
             assert e.value.code == L.EINVAL, bad
     finally:
         L.llama_destroy(ctx)
@@ -475,6 +482,29 @@ def test_tunings_change_no_result(L, tuning):
                     got, rc = s.schedule(case)
                 assert rc == L.OK
                 assert_same(got, exp, f"tuning {tuning} mode {mode} count pass {cp}")
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["cost_first", "alpha"])
+def test_warp_tiles_and_occupancy_change_no_result(L, mode):
+    # ops of 1..700 configurations on 3 backends: padded tables on both sides
+    # of the size a warp scores alone (576 entries cost-first, 456 alpha), so
+    # whole-CTA tiles and warp tiles in one call; 108 to 151 invocations per op
+    # (ragged warp tiles); every invocations per thread, one and two staging
+    # buffers, and 1 to 4 scoring CTAs per SM
+    p, inv = W.random_small(5, max_dags=6, max_ops=12, max_cfg=700, n_inv=5000, value_range=400)
+    npad = np.diff(p.hw_off.reshape(p.n_ops, p.n_hw + 1), axis=1)
+    npad = ((npad + 7) // 8 * 8).sum(axis=1)
+    limit = 576 if mode == 0 else 456
+    assert (npad <= limit).any() and (npad > limit).any()
+    exp, _ = oracle.schedule(p, inv, mode=mode, alpha=(2, 3))
+    with L.Scheduler(p, mode=mode, alpha=(2, 3)) as s:
+        for tuning, per_sm in (((16, 1, 0, 1), 0), ((16, 2, 0, 1), 0), ((16, 4, 0, 1), 0), ((4, 2, 0, 1), 1),
+                               ((64, 2, 0, 1), 2), ((8, 4, 0, 2), 3), ((16, 1, 0, 2), 4), ((16, 2, 64, 1), 0)):
+            L.llama_set_tuning(s.ctx, *tuning)
+            L.llama_set_score_occupancy(s.ctx, per_sm)
+            got, rc = s.schedule(inv)
+            assert rc == L.OK
+            assert_same(got, exp, f"tuning {tuning} ctas per sm {per_sm}")
 
 
 @pytest.mark.parametrize("mode", [0, 1], ids=["cost_first", "alpha"])
