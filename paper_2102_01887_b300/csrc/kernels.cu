@@ -556,8 +556,7 @@ __device__ __forceinline__ void scatter_invocation(const DevProblem &P, const Bu
                                                    int64_t rbase) {
     const int64_t pos = (int64_t)op_start[g] + slot;
     if (!LLAMA_IN_BOUNDS(P, pos >= 0 && pos < S.n_inv, LLAMA_CHECK_SCATTER)) return;
-    S.b_inv[pos] = (int32_t)i;
-    S.b_rem[pos] = (int32_t)max(rbase, (int64_t)0);
+    S.b_ent[pos] = make_int2((int32_t)i, (int32_t)max(rbase, (int64_t)0));
 }
 
 // The bucketing step of a call, one cooperative launch (all blocks resident):
@@ -853,7 +852,7 @@ __device__ __forceinline__ void tile_begin(const DevProblem &P, const BucketScra
     for (int u = 0; u < IPT; ++u) {
         const int32_t j = T.g * IPT + u;
         const bool in = j < T.m && LLAMA_IN_BOUNDS(P, tile.y + j >= 0 && tile.y + j < S.n_inv, LLAMA_CHECK_TILE);
-        T.inv[u] = in ? S.b_inv[tile.y + j] : -1;
+        T.inv[u] = in ? S.b_ent[tile.y + j].x : -1;
         if (!LLAMA_IN_BOUNDS(P, T.inv[u] < S.n_inv, LLAMA_CHECK_TILE)) T.inv[u] = -1;
         T.any |= T.inv[u] >= 0;
         T.best[u] = 0xFFFFFFFFu;
@@ -878,7 +877,7 @@ __device__ __forceinline__ int32_t inv_at(const TileState<IPT> &T, int u) {
 template <int IPT>
 __device__ __forceinline__ int32_t slack_at(const BucketScratch &S, const TileState<IPT> &T, const TileConst &tc,
                                             int u, int h) {
-    return slack_of(T.ref, T.cp, T.mg, (int64_t)S.b_rem[T.pos0 + u] - tc.q[h]);
+    return slack_of(T.ref, T.cp, T.mg, (int64_t)S.b_ent[T.pos0 + u].y - tc.q[h]);
 }
 
 // Counts c(u, h) of distinct latencies below the slack of invocation u for
@@ -1040,7 +1039,7 @@ __device__ __forceinline__ void finish_tile(const DevProblem &P, const BucketScr
 #pragma unroll
     for (int u = 0; u < IPT; ++u) {
         if (T.s != (u & (T.L - 1)) || T.inv[u] < 0) continue;
-        decode_into<MODE>(P, T.v, T.cbase, key[u], T.ref, T.cp, T.mg, (int64_t)S.b_rem[T.pos0 + u], tc,
+        decode_into<MODE>(P, T.v, T.cbase, key[u], T.ref, T.cp, T.mg, (int64_t)S.b_ent[T.pos0 + u].y, tc,
                           out + T.inv[u]);
     }
 }
@@ -1135,9 +1134,10 @@ __device__ __forceinline__ void warp_tiles(const DevProblem &P, const BucketScra
         for (int u = 0; u < IPT; ++u) {
             const int32_t j = lane * IPT + u;
             const bool in = fits && j < m;
-            inv[u] = in ? S.b_inv[tile.y + j] : -1;
+            const int2 e = in ? S.b_ent[tile.y + j] : make_int2(-1, 0);
+            inv[u] = e.x;
             if (!LLAMA_IN_BOUNDS(P, inv[u] < S.n_inv, LLAMA_CHECK_TILE)) inv[u] = -1;
-            rem[u] = in ? (int64_t)S.b_rem[tile.y + j] : 0;
+            rem[u] = e.y;
             best[u] = 0xFFFFFFFFu;
         }
         const int64_t ref = P.ref[v], cp = P.cp[v];
@@ -1574,13 +1574,14 @@ __global__ void __launch_bounds__(256, 4) k_counts(DevProblem P, BucketScratch S
                                                   : (int64_t)S.ctrl[kCtrlPositions];
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n_pos;
          p += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t bi = S.b_inv[p];
+        const int2 e = S.b_ent[p];
+        const int32_t bi = e.x;
         if (!LLAMA_IN_BOUNDS(P, bi >= 0 && bi < S.n_inv, LLAMA_CHECK_COUNTS)) continue;
         const int32_t g = S.gop[bi];
         if (!LLAMA_IN_BOUNDS(P, g >= 0 && g < P.n_ops, LLAMA_CHECK_COUNTS)) continue;
         if (P.dlat_n[g] <= dl_cap) continue;
         int32_t lo[MAXH];
-        counts_all_backends<MAXH, true>(P, g, P.ref[g], P.cp[g], P.cp_magic[g], (int64_t)S.b_rem[p], lo);
+        counts_all_backends<MAXH, true>(P, g, P.ref[g], P.cp[g], P.cp_magic[g], (int64_t)e.y, lo);
 #pragma unroll
         for (int h = 0; h < MAXH; ++h)
             if (h < H) S.b_cnt[p * H + h] = (uint16_t)lo[h];

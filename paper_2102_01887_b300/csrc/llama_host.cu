@@ -70,7 +70,7 @@ struct Range {
 // starts, per-invocation bucket entries, the tile list and the control and
 // status words.  Counters and control words are zero between calls.
 struct Workspace {
-    DevBuf cnt, ctrl, op_start, gop, slot, b_inv, b_rem, rbase, tiles, b_cnt;
+    DevBuf cnt, ctrl, op_start, gop, slot, b_ent, rbase, tiles, b_cnt;
     int64_t cap_inv = 0, cap_tiles = 0;
     int32_t cap_ops = 0;
 };
@@ -279,8 +279,7 @@ BucketScratch make_scratch(const Workspace &w) {
     S.op_start = w.op_start.as<int32_t>();
     S.gop = w.gop.as<int32_t>();
     S.slot = w.slot.as<int32_t>();
-    S.b_inv = w.b_inv.as<int32_t>();
-    S.b_rem = w.b_rem.as<int32_t>();
+    S.b_ent = w.b_ent.as<int2>();
     S.rbase = w.rbase.as<int64_t>();
     S.tiles = w.tiles.as<int4>();
     S.b_cnt = w.b_cnt.p ? w.b_cnt.as<uint16_t>() : nullptr;
@@ -433,8 +432,7 @@ int ensure_ws(llama_ctx *c, Workspace &w, int64_t n_inv) {
         const int64_t n = std::max<int64_t>(n_inv, 1024);
         LL_CUDA(c, w.gop.alloc(sizeof(int32_t) * n));
         LL_CUDA(c, w.slot.alloc(sizeof(int32_t) * n));
-        LL_CUDA(c, w.b_inv.alloc(sizeof(int32_t) * n));
-        LL_CUDA(c, w.b_rem.alloc(sizeof(int32_t) * n));
+        LL_CUDA(c, w.b_ent.alloc(sizeof(int2) * n));
         LL_CUDA(c, w.rbase.alloc(sizeof(int64_t) * n));
         LL_CUDA(c, w.b_cnt.alloc(sizeof(uint16_t) * LLAMA_MAX_HW * n));
         w.cap_inv = n;

@@ -181,9 +181,9 @@ struct BucketScratch {
     int32_t *op_start;        // [n_ops]     first bucket position of each op
     int32_t *gop;             // [n_inv]     global op of each invocation, -1 if invalid
     int32_t *slot;            // [n_inv]     rank of the invocation inside its op's bucket
-    int32_t *b_inv;           // [n_inv]     invocation at each bucket position
-    int32_t *b_rem;           // [n_inv]     remaining time before queueing, max(0, SLO - elapsed), of the
-                              //             invocation at each bucket position
+    int2 *b_ent;              // [n_inv]     at each bucket position, {invocation, its remaining time
+                              //             before queueing, max(0, SLO - elapsed)}: one 8-byte
+                              //             store per invocation from the scatter
     int64_t *rbase;           // [n_inv]     target - elapsed time of each invocation
     int4 *tiles;              // [2*max_tiles] scoring tiles: {op, first bucket position, m, lanes_log2},
                               // {padded entries, distinct latencies, padded offset, 0}

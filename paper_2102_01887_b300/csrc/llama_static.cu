@@ -47,9 +47,8 @@ constexpr size_t kCtrlOff = align256(kCntOff + 4 * (size_t)kCntStride * LLAMA_ST
 constexpr size_t kOpStartOff = align256(kCtrlOff + 8 * (size_t)(kCtrlWords + kStatusWords) + 16 * (size_t)kMaxBucketBlocks);
 constexpr size_t kGopOff = align256(kOpStartOff + 4 * (size_t)(LLAMA_STATIC_MAX_OPS + 1));
 constexpr size_t kSlotOff = align256(kGopOff + 4 * (size_t)LLAMA_STATIC_MAX_INV);
-constexpr size_t kBInvOff = align256(kSlotOff + 4 * (size_t)LLAMA_STATIC_MAX_INV);
-constexpr size_t kBRemOff = align256(kBInvOff + 4 * (size_t)LLAMA_STATIC_MAX_INV);
-constexpr size_t kRbaseOff = align256(kBRemOff + 4 * (size_t)LLAMA_STATIC_MAX_INV);
+constexpr size_t kBEntOff = align256(kSlotOff + 4 * (size_t)LLAMA_STATIC_MAX_INV);
+constexpr size_t kRbaseOff = align256(kBEntOff + 8 * (size_t)LLAMA_STATIC_MAX_INV);
 constexpr size_t kTilesOff = align256(kRbaseOff + 8 * (size_t)LLAMA_STATIC_MAX_INV);
 constexpr size_t kScratchBytes = align256(kTilesOff + 32 * kMaxTiles);
 
@@ -130,8 +129,7 @@ extern "C" int llama_schedule_static(llama_ctx *c, int64_t n_inv, const int32_t 
     S.op_start = reinterpret_cast<int32_t *>(base + kOpStartOff);
     S.gop = reinterpret_cast<int32_t *>(base + kGopOff);
     S.slot = reinterpret_cast<int32_t *>(base + kSlotOff);
-    S.b_inv = reinterpret_cast<int32_t *>(base + kBInvOff);
-    S.b_rem = reinterpret_cast<int32_t *>(base + kBRemOff);
+    S.b_ent = reinterpret_cast<int2 *>(base + kBEntOff);
     S.rbase = reinterpret_cast<int64_t *>(base + kRbaseOff);
     S.tiles = reinterpret_cast<int4 *>(base + kTilesOff);
 
