@@ -42,24 +42,28 @@ SCAN_BYTES_PER_SCORE = 12  # int32 latency + int64 cost per scored configuration
 # (profiles/ holds the summaries and the commands); reported as null as soon as
 # the sources differ.  Keys: workload/objective.
 MEASURED_TRAFFIC = {
-    "digest": "53f1672b257b1d72",
-    # profiles/k_bucket_medium.md, profiles/k_score_medium.md
-    "k_bucket:medium/cost_first": 6.807040e6,
-    "k_score:medium/cost_first": 2.674432e6,
-    # profiles/k_score_batched_large_192dags.md and k_counts_batched_large_192dags.md:
-    # the scoring pass (count pass + scoring kernel, the bench's timed region for
-    # this kernel) measured at 192 DAGs, 184.65 MB, scaled to the full launch by
-    # its algorithmic bytes (459.50 / 172.25 MB)
-    "k_score:batched_large/cost_first": 492.58e6,
+    "digest": "8061884340673808",
+    # profiles/k_bucket_batched.md, profiles/k_score_batched.md
+    "k_bucket:batched/cost_first": 70.84e6,
+    "k_score:batched/cost_first": 83.66e6,
+    # profiles/scoring_pass_batched_large_192dags.md: the scoring pass (count pass
+    # + scoring kernel) measured at 192 DAGs, 180.46 MB, scaled to the 512-DAG
+    # launch by its algorithmic bytes (459.50 / 172.25 MB)
+    "k_score:batched_large_512/cost_first": 481.4e6,
 }
 
 
 def kernel_digest() -> str:
+    """Digest of the scheduling call's kernel sources: kernels.cu up to the
+    serving loop's section (the tick kernel is not among the captured ones)
+    and the shared header."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("kernels.cu", "llama_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_2102_01887_b300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    with open(os.path.join(ROOT, "paper_2102_01887_b300", "csrc", "kernels.cu"), "rb") as fh:
+        src = fh.read()
+    h.update(src[:src.index(b"// Serving loop: one tick of early speculation")])
+    with open(os.path.join(ROOT, "paper_2102_01887_b300", "csrc", "llama_internal.cuh"), "rb") as fh:
+        h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -416,6 +420,7 @@ def hbm_streaming_line(args, peaks, peak_src, dev, flush):
             "bound": "hbm", "kernel": "k_counts + k_score" if per_call == 3 else "k_score",
             "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
             "peak_source": f"{peak_src} HBM copy bandwidth", "algorithmic_bytes": algo, "ms": score_ms,
+            "traffic": measured_traffic("k_score", f"batched_large_{p.n_dags}", "cost_first"),
             "bytes_note": "4 B per padded table entry (16-bit latency rank + 16-bit objective rank) of each "
                           "op with invocations, read once, plus 40 B per invocation"},
         "scan_12B_per_config": {"gbs": per12, "frac": per12 / hbm,

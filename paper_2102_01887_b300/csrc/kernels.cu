@@ -2413,10 +2413,11 @@ __device__ __forceinline__ unsigned long long decision_lr(const DevProblem &P, i
     return (unsigned long long)(uint32_t)d.lat * (unsigned long long)(uint32_t)P.res[P.cfg_off[g] + d.cfg];
 }
 
-__device__ __forceinline__ void loop_record(const LoopDev &L, long long pos, long long res_read, int64_t id,
-                                            int32_t kind, int32_t tick, const llama_decision &d, int32_t lam) {
+__device__ __forceinline__ void loop_record(const LoopDev &L, long long *dropped, long long pos, long long res_read,
+                                            int64_t id, int32_t kind, int32_t tick, const llama_decision &d,
+                                            int32_t lam) {
     if (pos - res_read >= L.res_cap) {  // the host has not taken enough records: drop, count
-        atomicAdd(reinterpret_cast<unsigned long long *>(&L.st->dropped), 1ull);
+        atomicAdd(reinterpret_cast<unsigned long long *>(dropped), 1ull);
         return;
     }
     llama_loop_result rec;
@@ -2431,16 +2432,35 @@ __device__ __forceinline__ void loop_record(const LoopDev &L, long long pos, lon
 
 __global__ void __launch_bounds__(kLoopThreads) k_loop_tick(DevProblem P, LoopDev L, LoopTickArgs a) {
     const int H = P.n_hw, tid = threadIdx.x;
-    LoopState &S = *L.st;
+    // the loop's state is worked on in shared memory (the serial steps below
+    // then touch no device memory) and written back at the end of the tick
+    __shared__ __align__(16) LoopState S;
+    constexpr int kStateWords = (int)(sizeof(LoopState) / 8);
+    static_assert(sizeof(LoopState) % 8 == 0, "state copied in 8-byte words");
+    for (int k = tid; k < kStateWords; k += kLoopThreads)
+        reinterpret_cast<unsigned long long *>(&S)[k] = reinterpret_cast<const unsigned long long *>(L.st)[k];
+    // the requests this tick may admit (at most max_admit of those submitted
+    // before it), read from the mapped ring now so the host link's latency
+    // overlaps the dispatch step; admission takes a prefix of them
+    llama_loop_request r;
+    r.id = 0;
+    {
+        const long long head = L.st->head;
+        if (tid < L.max_admit && head + tid < a.limit) r = L.ring[(head + tid) & L.ring_mask];
+    }
     __shared__ int wsum[32];
     __shared__ int sh_n_adm, sh_free_top, sh_tick;
-    __shared__ long long sh_head, sh_res, sh_res_read;
+    __shared__ long long sh_res, sh_res_read;
     __shared__ long long sh_sq_head[LLAMA_MAX_HW], sh_sq_tail[LLAMA_MAX_HW], sh_cq_tail[LLAMA_MAX_HW];
     __shared__ int sh_room[LLAMA_MAX_HW], sh_cnt[LLAMA_MAX_HW], sh_w[LLAMA_MAX_HW + 1], sh_group[LLAMA_MAX_HW],
         sh_ncommit_src[LLAMA_MAX_HW];
     __shared__ unsigned long long sh_lr_in[LLAMA_MAX_HW], sh_lr_out[LLAMA_MAX_HW];
     __shared__ double c_aff[kLoopThreads];
     __shared__ int8_t c_lam[kLoopThreads], c_commit[kLoopThreads];
+    // records the host has taken (mapped memory), read by the thread that uses it
+    long long res_read = 0;
+    if (tid == 0) res_read = (long long)*reinterpret_cast<volatile unsigned long long *>(&L.ctl->res_read);
+    __syncthreads();  // the state copy is complete
 
     // 1. dispatch: the heads of the commit queues leave (their slots go back on
     //    the free stack in backend order, then queue order, so the stack's order
@@ -2487,10 +2507,9 @@ __global__ void __launch_bounds__(kLoopThreads) k_loop_tick(DevProblem P, LoopDe
         const long long avail = max(0ll, a.limit - S.head);
         sh_n_adm = (int)min(avail, (long long)min(ft, L.max_admit));
         sh_free_top = ft;
-        sh_head = S.head;
         sh_res = S.res_count;
         sh_tick = (int)S.ticks;
-        sh_res_read = (long long)*reinterpret_cast<volatile unsigned long long *>(&L.ctl->res_read);
+        sh_res_read = res_read;
         for (int h = 0; h < H; ++h) {
             sh_sq_head[h] = S.sq_head[h];
             sh_sq_tail[h] = S.sq_tail[h];
@@ -2517,10 +2536,7 @@ __global__ void __launch_bounds__(kLoopThreads) k_loop_tick(DevProblem P, LoopDe
     dsn.slack = 0;
     dsn.flags = LLAMA_FLAG_INVALID;
     unsigned long long lr = 0;
-    llama_loop_request r;
-    r.id = 0;
     if (tid < n_adm) {
-        r = L.ring[(sh_head + tid) & L.ring_mask];
         if (invocation_valid(P, r.dag, r.op_local, r.start_us, a.now)) {
             valid = true;
             const int32_t g = P.dag_op_off[r.dag] + r.op_local;
@@ -2548,8 +2564,8 @@ __global__ void __launch_bounds__(kLoopThreads) k_loop_tick(DevProblem P, LoopDe
         atomicAdd(&sh_lr_in[lam], lr);
     }
     if (tid < n_adm)
-        loop_record(L, sh_res + tid, sh_res_read, r.id, valid ? LLAMA_LOOP_SPECULATED : LLAMA_LOOP_REJECTED, sh_tick,
-                    dsn, lam);
+        loop_record(L, &S.dropped, sh_res + tid, sh_res_read, r.id, valid ? LLAMA_LOOP_SPECULATED : LLAMA_LOOP_REJECTED,
+                    sh_tick, dsn, lam);
     __syncthreads();
     if (tid == 0) {
         for (int h = 0; h < H; ++h) {
@@ -2624,7 +2640,8 @@ __global__ void __launch_bounds__(kLoopThreads) k_loop_tick(DevProblem P, LoopDe
         atomicAdd(&sh_lr_in[lam2], lr2);
         atomicAdd(&sh_lr_out[src], L.slot_lr_spec[slot]);
         atomicAdd(&sh_ncommit_src[src], 1);
-        loop_record(L, sh_res + before + rank, sh_res_read, L.slot_id[slot], LLAMA_LOOP_COMMITTED, sh_tick, d2, lam2);
+        loop_record(L, &S.dropped, sh_res + before + rank, sh_res_read, L.slot_id[slot], LLAMA_LOOP_COMMITTED, sh_tick,
+                    d2, lam2);
     }
     __syncthreads();
     if (tid < C && !commit) {
@@ -2656,6 +2673,9 @@ __global__ void __launch_bounds__(kLoopThreads) k_loop_tick(DevProblem P, LoopDe
         __threadfence_system();
         ctl->res_count = (unsigned long long)S.res_count;
     }
+    __syncthreads();
+    for (int k = tid; k < kStateWords; k += kLoopThreads)
+        reinterpret_cast<unsigned long long *>(L.st)[k] = reinterpret_cast<const unsigned long long *>(&S)[k];
 }
 
 cudaError_t enqueue_loop_tick(const DevProblem &P, const LoopDev &L, const LoopTickArgs &a, cudaStream_t s) {
