@@ -22,6 +22,7 @@ import statistics
 import subprocess
 import sys
 import time
+from typing import Optional
 
 import numpy as np
 
@@ -38,19 +39,22 @@ ALU_OPS_PER_SCORE = {"cost_first": 1.0, "alpha": 1.5}
 ALU_LANES_PER_SM = 64  # integer ALU pipe: 16 lanes per SM sub-partition, 4 per SM
 SCAN_BYTES_PER_SCORE = 12  # int32 latency + int64 cost per scored configuration
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of each
-# kernel, from ncu captures of the kernel sources whose digest is "digest"
-# (profiles/ holds the summaries and the commands); reported as null as soon as
-# the sources differ.  Keys: workload/objective.
+# kernel, from ncu captures of the kernel sources whose digest is "digest", each
+# with the launch schedule it was captured under (lanes_min_vectors,
+# inv_per_thread, chunk, stages, count_pass, ctas_per_sm, dlat_stage);
+# profiles/ holds the summaries and the commands.  Reported as null as soon as
+# the sources or the schedule differ.  Keys: workload/objective.
 MEASURED_TRAFFIC = {
     "digest": "8061884340673808",
     # profiles/k_bucket_batched.md, profiles/k_score_batched.md
-    "k_bucket:batched/cost_first": 70.84e6,
-    "k_score:batched/cost_first": 83.66e6,
+    "k_bucket:batched/cost_first": (70.84e6, (64, 2, 0, 1, 0, 0, 4096)),
+    "k_score:batched/cost_first": (83.66e6, (64, 2, 0, 1, 0, 0, 4096)),
     # profiles/scoring_pass_batched_large_192dags.md: the scoring pass (count pass
     # + scoring kernel) measured at 192 DAGs, 180.46 MB, scaled to the 512-DAG
     # launch by its algorithmic bytes (459.50 / 172.25 MB)
-    "k_score:batched_large_512/cost_first": 481.4e6,
+    "k_score:batched_large_512/cost_first": (481.4e6, (32, 1, 8256, 1, 0, 0, 4096)),
 }
+SCHEDULE_KEYS = ("lanes_min_vectors", "inv_per_thread", "chunk", "stages", "count_pass", "ctas_per_sm", "dlat_stage")
 
 
 def kernel_digest() -> str:
@@ -67,10 +71,16 @@ def kernel_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic(kernel: str, workload: str, mode: str):
-    if MEASURED_TRAFFIC.get("digest") != kernel_digest():
+def measured_traffic(kernel: str, workload: str, mode: str, schedule) -> Optional[float]:
+    """The captured traffic of `kernel`, if its sources and `schedule` (the
+    bench's applied schedule dict) are those of the capture."""
+    if MEASURED_TRAFFIC.get("digest") != kernel_digest() or not isinstance(schedule, dict):
         return None
-    return MEASURED_TRAFFIC.get(f"{kernel}:{workload}/{mode}")
+    entry = MEASURED_TRAFFIC.get(f"{kernel}:{workload}/{mode}")
+    if entry is None:
+        return None
+    value, sched = entry
+    return value if tuple(int(schedule.get(k, -1)) for k in SCHEDULE_KEYS) == sched else None
 
 
 def parse():
@@ -104,8 +114,9 @@ def parse():
                     help="surrogate: training epochs before the timed calls (0: untrained network, for profiling)")
     ap.add_argument("--tuning", default=None,
                     help="fixed scoring schedule 'lanes_min_vectors,inv_per_thread,chunk,stages"
-                         "[,count_pass[,ctas_per_sm]]' (no autotuning; count_pass 0 auto, 1 on, 2 off; "
-                         "ctas_per_sm 0 = as many as fit)")
+                         "[,count_pass[,ctas_per_sm[,dlat_stage]]]' (no autotuning; count_pass 0 auto, 1 on, "
+                         "2 off; ctas_per_sm 0 = as many as fit; dlat_stage: distinct latencies staged per op, "
+                         "default 4096)")
     return ap.parse_args()
 
 
@@ -420,7 +431,7 @@ def hbm_streaming_line(args, peaks, peak_src, dev, flush):
             "bound": "hbm", "kernel": "k_counts + k_score" if per_call == 3 else "k_score",
             "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
             "peak_source": f"{peak_src} HBM copy bandwidth", "algorithmic_bytes": algo, "ms": score_ms,
-            "traffic": measured_traffic("k_score", f"batched_large_{p.n_dags}", "cost_first"),
+            "traffic": measured_traffic("k_score", f"batched_large_{p.n_dags}", "cost_first", tuning["best"]),
             "bytes_note": "4 B per padded table entry (16-bit latency rank + 16-bit objective rank) of each "
                           "op with invocations, read once, plus 40 B per invocation"},
         "scan_12B_per_config": {"gbs": per12, "frac": per12 / hbm,
@@ -924,11 +935,13 @@ def main():
         lmv, ipt, chunk, stages, *rest = (int(x) for x in args.tuning.split(","))
         cpass = rest[0] if rest else L.COUNT_PASS_AUTO
         per_sm = rest[1] if len(rest) > 1 else 0
+        dstage = rest[2] if len(rest) > 2 else L.DLAT_STAGE_DEFAULT
         L.llama_set_tuning(ctx, lmv, ipt, chunk, stages)
         L.llama_set_count_pass(ctx, cpass)
         L.llama_set_score_occupancy(ctx, per_sm)
+        L.llama_set_dlat_stage(ctx, dstage)
         tuning = {"best": {"lanes_min_vectors": lmv, "inv_per_thread": ipt, "chunk": chunk, "stages": stages,
-                           "count_pass": cpass, "ctas_per_sm": per_sm},
+                           "count_pass": cpass, "ctas_per_sm": per_sm, "dlat_stage": dstage},
                   "trials": []}
     elif not args.no_autotune and args.method == "scan":
         # choose the scoring schedule on this batch before anything is timed;
@@ -1057,6 +1070,7 @@ def main():
     tbl_per_entry = 6 if args.mode == "alpha" else 4
     kms = {n: float(phase_ms[:, j].mean()) for j, n in enumerate(L.TRACE_PHASES)}
     rooflines = {}
+    sched = tuning["best"] if tuning else None  # the schedule the timed calls ran with
     if args.method == "staircase":
         # one thread per invocation: 16 B in, 24 B out; the searches and lookups
         # are dependent loads into per-op arrays (latency, not bandwidth)
@@ -1064,7 +1078,7 @@ def main():
         s_ach = s_bytes / (kms["score"] / 1e3) / 1e9
         rooflines["k_stair"] = {
             "bound": "hbm", "kernel": "k_stair", "achieved": s_ach, "peak": hbm, "unit": "GB/s",
-            "frac": s_ach / hbm, "traffic": measured_traffic("k_stair", args.workload, args.mode),
+            "frac": s_ach / hbm, "traffic": measured_traffic("k_stair", args.workload, args.mode, sched),
             "peak_source": f"{peak_src} HBM copy bandwidth", "algorithmic_bytes": s_bytes,
             "bytes_note": "16 B in and 24 B out per invocation"}
         c_bytes = 16 * p.n_ops
@@ -1080,7 +1094,7 @@ def main():
         achieved = algo_bytes / (kms["score"] / 1e3) / 1e9
         rooflines["k_score"] = {
             "bound": "hbm", "kernel": "k_score", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": measured_traffic("k_score", args.workload, args.mode),
+            "frac": achieved / hbm, "traffic": measured_traffic("k_score", args.workload, args.mode, sched),
             "peak_source": f"{peak_src} HBM copy bandwidth", "algorithmic_bytes": algo_bytes,
             "bytes_note": f"{tbl_per_entry} B per padded table entry of each op with invocations "
                           "(latency rank + objective rank(s)), once, plus 40 B per invocation",
@@ -1095,7 +1109,7 @@ def main():
         rooflines["k_score"] = {
             "bound": "alu", "kernel": "k_score", "achieved": achieved, "peak": peak_tops,
             "unit": "T ALU-ops/s", "frac": achieved / peak_tops,
-            "traffic": measured_traffic("k_score", args.workload, args.mode),
+            "traffic": measured_traffic("k_score", args.workload, args.mode, sched),
             "peak_source": "measured: llama_alu_peak, the scan's per-two-configuration instruction mix "
                            "(packed subtract, LOP3, 16-bit min" + (", PRMT" if args.mode == "alpha" else "")
                            + ") from registers on every SM",
@@ -1108,7 +1122,7 @@ def main():
         b_ach = b_bytes / (kms["bucket"] / 1e3) / 1e9
         rooflines["k_bucket"] = {
             "bound": "hbm", "kernel": "k_bucket", "achieved": b_ach, "peak": hbm, "unit": "GB/s",
-            "frac": b_ach / hbm, "traffic": measured_traffic("k_bucket", args.workload, args.mode),
+            "frac": b_ach / hbm, "traffic": measured_traffic("k_bucket", args.workload, args.mode, sched),
             "peak_source": f"{peak_src} HBM copy bandwidth", "algorithmic_bytes": b_bytes,
             "bytes_note": "16 B in and 8 B of bucket entry (index, remaining time) out per invocation; "
                           "time includes its launch (trace events around it)"}
@@ -1148,7 +1162,7 @@ def main():
         "roofline": roofline,
         "rooflines": rooflines,
         "schedule_trials": ([{k: t[k] for k in ("lanes_min_vectors", "inv_per_thread", "chunk", "stages",
-                                                "count_pass", "ctas_per_sm", "ms") if k in t}
+                                                "count_pass", "ctas_per_sm", "dlat_stage", "ms") if k in t}
                              for t in tuning["trials"]] if tuning and tuning["trials"] else None),
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
         "parity_vs_oracle": parity, "set_profiles_ms": set_profiles_ms, **extras,

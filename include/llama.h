@@ -297,6 +297,17 @@ int llama_static_status(llama_ctx *ctx, void *stream, int64_t *invalid, int32_t 
 int llama_set_tuning(llama_ctx *ctx, int32_t lanes_min_vectors, int32_t inv_per_thread,
                      int32_t chunk_entries, int32_t stages);
 
+/* Distinct latencies of an operation staged in shared memory by the scoring
+ * kernel (no counterpart in the paper; changes speed, never results): an op
+ * with at most max_entries of them (1..LLAMA_MAX_CFG; default 4096) has its
+ * sorted list copied beside its table and searched there; an op with more is
+ * counted by the count pass or searched in global memory.  Staging a list
+ * costs 4 B per distinct latency per tile: worth it where an op's table serves
+ * many invocations, not where tables stream from DRAM for a few each.  Call
+ * after llama_set_profiles (which resets it to 4096).  Errors: EINVAL,
+ * ENOTREADY (no profiles), ECUDA. */
+int llama_set_dlat_stage(llama_ctx *ctx, int32_t max_entries);
+
 /* Persistent CTAs of the scoring kernel per SM (no counterpart in the paper;
  * changes speed, never results): 0 (default) as many as its registers and
  * shared memory allow, else at most ctas_per_sm (1..32).  Fewer, larger
@@ -316,8 +327,9 @@ int llama_set_score_occupancy(llama_ctx *ctx, int32_t ctas_per_sm);
  * itself, a warp-wide search per (invocation, backend), overlapped with the
  * staging of the table.  AUTO (default): ON when at least half of the
  * operations have padded tables larger than the staged distinct latencies.
- * The pass is never launched when no operation needs it, nor by
- * llama_schedule_static.  Errors: EINVAL. */
+ * The pass is launched only while some operation can have more distinct
+ * latencies than are staged (they are at most its configurations, which
+ * feedback can reach), never by llama_schedule_static.  Errors: EINVAL. */
 #define LLAMA_COUNT_PASS_AUTO 0
 #define LLAMA_COUNT_PASS_ON 1
 #define LLAMA_COUNT_PASS_OFF 2

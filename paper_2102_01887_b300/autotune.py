@@ -1,9 +1,10 @@
 """Autotuner of the scoring kernel's launch schedule.
 
 The schedule (lanes sharing one invocation, invocations per thread, staging
-chunk, staging buffers, whether a count pass precedes the scoring kernel, and
-how many scoring CTAs share an SM) changes speed, never results (tests check
-the latter).  For a given
+chunk, staging buffers, whether a count pass precedes the scoring kernel, how
+many scoring CTAs share an SM, and how many distinct latencies of an op are
+staged beside its table) changes speed, never results (tests check the
+latter).  For a given
 context and a batch of device-resident invocations, the tuner times every
 candidate on that batch -- whole scheduling calls replayed as the caller
 would replay them, the L2 cache flushed before each call -- and keeps the
@@ -20,6 +21,7 @@ DEFAULT_LANES_MIN_VECTORS = (4, 8, 16, 32, 64)
 DEFAULT_INV_PER_THREAD = (1, 2, 4)
 DEFAULT_STAGES = (1, 2)
 DEFAULT_CTAS_PER_SM = (0, 4, 3)  # 0: as many as fit
+DEFAULT_DLAT_STAGE = (4096, 8192)  # the first is the library default
 
 
 def time_call(ctx, dag, op_local, start, now: int, out, stream, flush, reps: int = 5) -> float:
@@ -45,12 +47,14 @@ def autotune(ctx, dag, op_local, start, now: int, out, stream=None, flush=None,
              lanes: Iterable[int] = DEFAULT_LANES_MIN_VECTORS,
              ipts: Iterable[int] = DEFAULT_INV_PER_THREAD, chunks: Iterable[int] = (0,),
              stages: Iterable[int] = DEFAULT_STAGES, ctas_per_sm: Iterable[int] = DEFAULT_CTAS_PER_SM,
-             reps: int = 5) -> dict:
+             dlat_stage: Iterable[int] = DEFAULT_DLAT_STAGE, reps: int = 5) -> dict:
     """Sweep the candidates, apply the fastest, return {"best": ..., "trials": [...]}.
 
     ``chunks``: staging chunk sizes in configurations (0 = the library default);
     ``stages``: staging buffers per CTA (1 or 2); ``ctas_per_sm``: caps on the
-    scoring CTAs per SM, tried for the fastest schedule (0 = as many as fit).
+    scoring CTAs per SM, tried for the fastest schedule (0 = as many as fit);
+    ``dlat_stage``: most distinct latencies staged per op, the first used for
+    the sweep, the others tried last.
     """
     import torch
     if stream is None:
@@ -58,8 +62,10 @@ def autotune(ctx, dag, op_local, start, now: int, out, stream=None, flush=None,
     if flush is None:
         flush = torch.empty(256 << 20, dtype=torch.uint8, device=dag.device)
     trials = []
+    dlat_stage = list(dlat_stage)
     L.llama_set_count_pass(ctx, L.COUNT_PASS_AUTO)
     L.llama_set_score_occupancy(ctx, 0)
+    L.llama_set_dlat_stage(ctx, dlat_stage[0])
     for st, chunk, lmv, ipt in itertools.product(stages, chunks, lanes, ipts):
         L.llama_set_tuning(ctx, lmv, ipt, chunk, st)
         ms = time_call(ctx, dag, op_local, start, now, out, stream, flush, reps)
@@ -90,4 +96,14 @@ def autotune(ctx, dag, op_local, start, now: int, out, stream=None, flush=None,
         if ms < best["ms"]:
             best = trials[-1]
     L.llama_set_score_occupancy(ctx, best["ctas_per_sm"])
+    # the distinct latencies staged per op, for that schedule (the count pass
+    # as chosen above; it is not launched where no op needs it)
+    best = dict(best, dlat_stage=dlat_stage[0])
+    for cap in dlat_stage[1:]:
+        L.llama_set_dlat_stage(ctx, cap)
+        ms = time_call(ctx, dag, op_local, start, now, out, stream, flush, reps)
+        trials.append(dict(best, dlat_stage=cap, ms=ms))
+        if ms < best["ms"]:
+            best = trials[-1]
+    L.llama_set_dlat_stage(ctx, best["dlat_stage"])
     return {"best": best, "trials": trials}

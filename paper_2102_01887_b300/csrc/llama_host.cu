@@ -97,6 +97,7 @@ struct llama_ctx {
     bool stair_ready = false;
     DevBuf stair, stair_off;
     std::vector<int32_t> h_dn;     // distinct latencies per op (as set; feedback changes them on the device)
+    std::vector<int32_t> h_npad;   // padded table entries per op
     std::vector<int32_t> h_ncfg;   // configurations per op
     int32_t max_n = 0, sort_cap = 1;
     size_t sort_smem = 0, lat_smem = 0;
@@ -123,6 +124,7 @@ struct llama_ctx {
     // scoring kernel geometry (set by llama_set_profiles)
     int32_t min_vpl = 16, ipt = 2, stages = 1, score_grid = 0, score_chunk = 0, bucket_max_blocks = 0, dlat_cap = 0;
     int32_t score_per_sm = 0;  // persistent scoring CTAs per SM: 0 = as many as fit
+    int32_t dlat_stage = kMaxDlatSmem;  // most distinct latencies of an op the scoring kernel stages
     size_t score_smem = 0;
 
     // staging for host-memory arguments of the blocking calls
@@ -497,6 +499,19 @@ int grid_for(const llama_ctx *c, int64_t n, int threads) {
 // ranks and objective ranks (plus rank differences in alpha mode) and the op's
 // distinct latencies; then one count per (invocation, backend) for every group
 // of the CTA (at most one group per thread).
+// Shared-memory room for the distinct latencies of the largest op whose list
+// has at most dlat_stage entries (none: every op is counted by the count pass
+// or searched in global memory), and the ops whose padded tables exceed it
+// (a prefix of the bucket order: they may need counts).
+void apply_dlat_stage(llama_ctx *c) {
+    int32_t cap = 0;
+    for (int32_t v = 0; v < c->n_ops; ++v)
+        if (c->h_dn[v] <= c->dlat_stage) cap = std::max(cap, c->h_dn[v]);
+    c->dlat_cap = (cap + 3) / 4 * 4;
+    c->n_big_ops = 0;
+    for (int32_t v = 0; v < c->n_ops; ++v) c->n_big_ops += c->h_npad[v] > c->dlat_cap;
+}
+
 size_t score_smem_bytes(const llama_ctx *c) {
     const size_t tbl = ((size_t)c->score_chunk * (c->opts.mode == LLAMA_MODE_ALPHA ? 6 : 4) + 15) / 16 * 16;
     const size_t counts = (size_t)kScoreThreads * c->ipt * c->opts.n_hw * 2;
@@ -976,19 +991,15 @@ extern "C" int llama_set_profiles(llama_ctx *c, int32_t n_ops, const int64_t *cf
         LL_CUDA(c, cudaMemcpy(c->ord_pos.p, pos.data(), 4 * (size_t)n_ops, cudaMemcpyHostToDevice));
         c->h_ncfg.resize(n_ops);
         for (int32_t v = 0; v < n_ops; ++v) c->h_ncfg[v] = (int32_t)(cfg_off[v + 1] - cfg_off[v]);
-        // shared-memory room for the distinct latencies of the largest op whose
-        // list fits kMaxDlatSmem entries (none: every op searches global memory)
-        int32_t cap = 0;
-        for (int32_t v = 0; v < n_ops; ++v)
-            if (dn[v] <= kMaxDlatSmem) cap = std::max(cap, dn[v]);
-        c->dlat_cap = (cap + 3) / 4 * 4;
-        c->n_big_ops = 0;
-        for (int32_t v = 0; v < n_ops; ++v) c->n_big_ops += pad_off[v + 1] - pad_off[v] > c->dlat_cap;
         // ops whose padded table fits a warp's slice are scored by warp tiles:
         // the end of the bucket order (largest tables first)
         c->n_cta_ops = 0;
         for (int32_t v = 0; v < n_ops; ++v) c->n_cta_ops += pad_off[v + 1] - pad_off[v] > warp_pad_of(c->opts.mode);
         c->h_dn = std::move(dn);
+        c->h_npad.resize(n_ops);
+        for (int32_t v = 0; v < n_ops; ++v) c->h_npad[v] = (int32_t)(pad_off[v + 1] - pad_off[v]);
+        c->dlat_stage = kMaxDlatSmem;
+        apply_dlat_stage(c);
     }
     c->stair_ready = false;
 
@@ -1058,6 +1069,19 @@ extern "C" int llama_set_tuning(llama_ctx *c, int32_t lanes_min_vectors, int32_t
     c->ipt = inv_per_thread;
     c->stages = stages;
     c->score_chunk = chunk_entries ? std::min<int32_t>(chunk_entries, c->max_npad) : default_chunk(c->max_npad);
+    c->score_smem = score_smem_bytes(c);
+    return configure_score(c);
+}
+
+extern "C" int llama_set_dlat_stage(llama_ctx *c, int32_t max_entries) {
+    if (!c) return LLAMA_EINVAL;
+    if (max_entries < 1 || max_entries > LLAMA_MAX_CFG)
+        return c->fail(LLAMA_EINVAL, "set_dlat_stage: max_entries out of 1..8192");
+    if (!c->prof_set) return c->fail(LLAMA_ENOTREADY, "set_dlat_stage: set the profiles first");
+    DeviceGuard g(c->opts.device);
+    c->drop_graph();
+    c->dlat_stage = max_entries;
+    apply_dlat_stage(c);
     c->score_smem = score_smem_bytes(c);
     return configure_score(c);
 }

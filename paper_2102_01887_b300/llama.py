@@ -34,7 +34,7 @@ assert DECISION_DTYPE.itemsize == 24
 
 EXPORTS = ("llama_create", "llama_destroy", "llama_set_dags", "llama_set_profiles",
            "llama_set_queue", "llama_schedule", "llama_schedule_async", "llama_schedule_static",
-           "llama_set_tuning", "llama_set_count_pass", "llama_set_score_occupancy", "llama_set_method", "llama_reserve",
+           "llama_set_tuning", "llama_set_count_pass", "llama_set_score_occupancy", "llama_set_dlat_stage", "llama_set_method", "llama_reserve",
            "llama_critical_path", "llama_slack", "llama_set_trace_events", "llama_last_launch_count",
            "llama_last_error", "llama_gemm_bf16", "llama_gemm_error",
            "llama_mlp_create", "llama_mlp_destroy", "llama_mlp_set_params", "llama_mlp_get_params",
@@ -115,6 +115,7 @@ def load(path: str = None) -> ctypes.CDLL:
             "llama_set_tuning": ([vp, i32, i32, i32, i32], ctypes.c_int),
             "llama_set_count_pass": ([vp, i32], ctypes.c_int),
             "llama_set_score_occupancy": ([vp, i32], ctypes.c_int),
+            "llama_set_dlat_stage": ([vp, i32], ctypes.c_int),
             "llama_set_method": ([vp, i32], ctypes.c_int),
             "llama_reserve": ([vp, i64], ctypes.c_int),
             "llama_critical_path": ([vp, vp], ctypes.c_int),
@@ -255,6 +256,13 @@ def llama_set_count_pass(ctx, mode: int) -> None:
 
 def llama_set_score_occupancy(ctx, ctas_per_sm: int) -> None:
     _check(ctx, load().llama_set_score_occupancy(ctx, int(ctas_per_sm)))
+
+
+DLAT_STAGE_DEFAULT = 4096
+
+
+def llama_set_dlat_stage(ctx, max_entries: int) -> None:
+    _check(ctx, load().llama_set_dlat_stage(ctx, int(max_entries)))
 
 
 GEMM_RELU = 1

@@ -23,11 +23,12 @@ def test_autotune_picks_a_schedule_and_results_stay_exact(cuda_device):
         st = torch.from_numpy(sub.start_us).to(dev)
         out = torch.zeros(sub.n * 24, dtype=torch.uint8, device=dev)
         res = autotune(s.ctx, dag, opl, st, sub.now_us, out, lanes=(8, 32), ipts=(1, 2), reps=2)
-        # 2 lanes x 2 ipt x 2 stagings, then 4 and 3 scoring CTAs per SM for the
-        # fastest; no count-pass trials: every op's distinct latencies are
-        # staged by the scoring kernel
-        assert len(res["trials"]) == 10 and res["best"]["ms"] > 0
-        assert [t.get("ctas_per_sm") for t in res["trials"][8:]] == [4, 3]
+        # 2 lanes x 2 ipt x 2 stagings, then 4 and 3 scoring CTAs per SM and
+        # 8,192 staged distinct latencies for the fastest; no count-pass
+        # trials: every op's distinct latencies are staged by the scoring kernel
+        assert len(res["trials"]) == 11 and res["best"]["ms"] > 0
+        assert [t.get("ctas_per_sm") for t in res["trials"][8:10]] == [4, 3]
+        assert res["trials"][10]["dlat_stage"] == 8192 and res["best"]["dlat_stage"] in (4096, 8192)
         assert res["best"]["count_pass"] == L.COUNT_PASS_AUTO
         assert res["best"]["ctas_per_sm"] in (0, 4, 3)
         out.zero_()
@@ -53,7 +54,7 @@ def test_autotune_chooses_the_count_pass_and_results_stay_exact(cuda_device):
         st = torch.from_numpy(inv.start_us).to(dev)
         out = torch.zeros(inv.n * 24, dtype=torch.uint8, device=dev)
         res = autotune(s.ctx, dag, opl, st, inv.now_us, out, lanes=(32,), ipts=(1,), stages=(1,), ctas_per_sm=(0,),
-                       reps=2)
+                       dlat_stage=(4096,), reps=2)
         assert [t.get("count_pass") for t in res["trials"]] == [None, L.COUNT_PASS_ON, L.COUNT_PASS_OFF]
         assert res["best"]["ms"] == min(t["ms"] for t in res["trials"])
         out.zero_()

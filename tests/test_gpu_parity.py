@@ -378,6 +378,9 @@ def test_errors(L):
         with pytest.raises(L.LlamaError) as e:
             L.llama_set_score_occupancy(ctx, 4)
         assert e.value.code == L.ENOTREADY
+        with pytest.raises(L.LlamaError) as e:
+            L.llama_set_dlat_stage(ctx, 4096)
+        assert e.value.code == L.ENOTREADY
         for bad in ((0, 2, 0, 1), (2048, 2, 0, 1), (16, 3, 0, 1), (16, 2, 12, 1), (16, 2, 8264, 1),
                     (16, 2, 0, 3), (16, 2, 0, 0)):
             with pytest.raises(L.LlamaError) as e:
@@ -386,6 +389,10 @@ def test_errors(L):
         for bad in (-1, 33):
             with pytest.raises(L.LlamaError) as e:
                 L.llama_set_score_occupancy(ctx, bad)
+            assert e.value.code == L.EINVAL, bad
+        for bad in (0, 8193):
+            with pytest.raises(L.LlamaError) as e:
+                L.llama_set_dlat_stage(ctx, bad)
             assert e.value.code == L.EINVAL, bad
     finally:
         L.llama_destroy(ctx)
@@ -524,6 +531,36 @@ def test_count_pass_changes_no_result(L, mode):
                 assert rc == L.OK
                 assert L.llama_last_launch_count(s.ctx) == launches, cp
                 assert_same(got, exp, f"count pass {cp}")
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["cost_first", "alpha"])
+def test_dlat_stage_changes_no_result(L, mode):
+    # the distinct latencies staged per op from 1 (almost every op counted by
+    # the count pass or searched in global memory) to 8,192 (every op staged),
+    # with the pass forced on (launched while some op could have more distinct
+    # latencies than are staged, after feedback too) and off, on Zipf-sized
+    # and on 8,192-configuration tables
+    cases = (W.batched(n_inv=65536), W.batched_large(n_dags=24, n_inv=6000))
+    for prob, case in cases:
+        exp, _ = oracle.schedule(prob, case, mode=mode, alpha=(2, 3))
+        sizes = np.diff(prob.cfg_off)
+        dn = np.asarray([np.unique(prob.lat_us[prob.cfg_off[v]:prob.cfg_off[v + 1]]).size
+                         for v in range(prob.n_ops)])
+        with L.Scheduler(prob, mode=mode, alpha=(2, 3)) as s:
+            for stage in (1, 64, 4096, 8192):
+                L.llama_set_dlat_stage(s.ctx, stage)
+                # staged room: the largest list of at most `stage` entries; the
+                # pass is launched (forced on) while some op's configurations
+                # exceed it
+                staged = dn[dn <= stage]
+                cap = (int(staged.max()) + 3) // 4 * 4 if staged.size else 0
+                for cp in (L.COUNT_PASS_ON, L.COUNT_PASS_OFF):
+                    L.llama_set_count_pass(s.ctx, cp)
+                    got, rc = s.schedule(case)
+                    assert rc == L.OK
+                    launches = 3 if cp == L.COUNT_PASS_ON and sizes.max() > cap else 2
+                    assert L.llama_last_launch_count(s.ctx) == launches, (stage, cp)
+                    assert_same(got, exp, f"dlat stage {stage} count pass {cp}")
 
 
 @pytest.fixture(scope="module")
