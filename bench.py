@@ -1070,7 +1070,7 @@ def main():
     tbl_per_entry = 6 if args.mode == "alpha" else 4
     kms = {n: float(phase_ms[:, j].mean()) for j, n in enumerate(L.TRACE_PHASES)}
     rooflines = {}
-    sched = tuning["best"] if tuning else None  # the schedule the timed calls ran with
+    applied = tuning["best"] if tuning else None  # the schedule the timed calls ran with
     if args.method == "staircase":
         # one thread per invocation: 16 B in, 24 B out; the searches and lookups
         # are dependent loads into per-op arrays (latency, not bandwidth)
@@ -1078,7 +1078,7 @@ def main():
         s_ach = s_bytes / (kms["score"] / 1e3) / 1e9
         rooflines["k_stair"] = {
             "bound": "hbm", "kernel": "k_stair", "achieved": s_ach, "peak": hbm, "unit": "GB/s",
-            "frac": s_ach / hbm, "traffic": measured_traffic("k_stair", args.workload, args.mode, sched),
+            "frac": s_ach / hbm, "traffic": measured_traffic("k_stair", args.workload, args.mode, applied),
             "peak_source": f"{peak_src} HBM copy bandwidth", "algorithmic_bytes": s_bytes,
             "bytes_note": "16 B in and 24 B out per invocation"}
         c_bytes = 16 * p.n_ops
@@ -1094,7 +1094,7 @@ def main():
         achieved = algo_bytes / (kms["score"] / 1e3) / 1e9
         rooflines["k_score"] = {
             "bound": "hbm", "kernel": "k_score", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": measured_traffic("k_score", args.workload, args.mode, sched),
+            "frac": achieved / hbm, "traffic": measured_traffic("k_score", args.workload, args.mode, applied),
             "peak_source": f"{peak_src} HBM copy bandwidth", "algorithmic_bytes": algo_bytes,
             "bytes_note": f"{tbl_per_entry} B per padded table entry of each op with invocations "
                           "(latency rank + objective rank(s)), once, plus 40 B per invocation",
@@ -1109,7 +1109,7 @@ def main():
         rooflines["k_score"] = {
             "bound": "alu", "kernel": "k_score", "achieved": achieved, "peak": peak_tops,
             "unit": "T ALU-ops/s", "frac": achieved / peak_tops,
-            "traffic": measured_traffic("k_score", args.workload, args.mode, sched),
+            "traffic": measured_traffic("k_score", args.workload, args.mode, applied),
             "peak_source": "measured: llama_alu_peak, the scan's per-two-configuration instruction mix "
                            "(packed subtract, LOP3, 16-bit min" + (", PRMT" if args.mode == "alpha" else "")
                            + ") from registers on every SM",
@@ -1122,7 +1122,7 @@ def main():
         b_ach = b_bytes / (kms["bucket"] / 1e3) / 1e9
         rooflines["k_bucket"] = {
             "bound": "hbm", "kernel": "k_bucket", "achieved": b_ach, "peak": hbm, "unit": "GB/s",
-            "frac": b_ach / hbm, "traffic": measured_traffic("k_bucket", args.workload, args.mode, sched),
+            "frac": b_ach / hbm, "traffic": measured_traffic("k_bucket", args.workload, args.mode, applied),
             "peak_source": f"{peak_src} HBM copy bandwidth", "algorithmic_bytes": b_bytes,
             "bytes_note": "16 B in and 8 B of bucket entry (index, remaining time) out per invocation; "
                           "time includes its launch (trace events around it)"}

@@ -75,6 +75,19 @@ __device__ __forceinline__ bool invocation_valid(const DevProblem &P, int32_t d,
     return s >= 0 && s <= now;
 }
 
+// invocation_valid from the DAG's record (one 16-byte load: op range and SLO);
+// for a valid invocation also its global op g and its remaining time before
+// queueing, rbase = SLO - elapsed (Algorithm 1).
+__device__ __forceinline__ bool invocation_op(const DevProblem &P, int32_t d, int32_t o, int64_t s, int64_t now,
+                                              int32_t &g, int64_t &rbase) {
+    if (d < 0 || d >= P.n_dags) return false;
+    const int4 di = __ldg(P.dag_info + d);
+    if (o < 0 || o >= di.y - di.x || s < 0 || s > now) return false;
+    g = di.x + o;
+    rbase = (int64_t)(((uint64_t)(uint32_t)di.w << 32) | (uint32_t)di.z) - (now - s);
+    return true;
+}
+
 // Longest remaining reference-latency path of every op of DAG d, op included
 // (Algorithm 1's RemainingPathLatency maximised over the paths through op).
 // Levels hold the ops of equal height above the sinks (height 0 first), so
@@ -525,7 +538,7 @@ __device__ __forceinline__ void count_invocation(const DevProblem &P, int64_t i,
                                                  int64_t &rbase) {
     const int32_t d = dag[i], o = op_local[i];
     const int64_t st = start[i];
-    if (!invocation_valid(P, d, o, st, now)) {
+    if (!invocation_op(P, d, o, st, now, g, rbase)) {
         g = -1;
         S.gop[i] = -1;
         llama_decision bad;
@@ -538,8 +551,6 @@ __device__ __forceinline__ void count_invocation(const DevProblem &P, int64_t i,
         atomicAdd(&S.ctrl[kCtrlInvalid], 1ull);
         return;
     }
-    g = P.dag_op_off[d] + o;
-    rbase = P.slo[d] - (now - st);
     slot = atomicAdd(&S.cnt[(int64_t)g * kCntStride], 1);
     S.gop[i] = g;
     S.slot[i] = slot;
@@ -1637,9 +1648,9 @@ __global__ void __launch_bounds__(256) k_stair(DevProblem P, int64_t n_inv, cons
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n_inv) {
-        const int32_t d = dag[i], o = op_local[i];
-        const int64_t st = start[i];
-        if (!invocation_valid(P, d, o, st, now)) {
+        int32_t g;
+        int64_t rbase;
+        if (!invocation_op(P, dag[i], op_local[i], start[i], now, g, rbase)) {
             llama_decision bad;
             bad.cfg = -1;
             bad.lat = 0;
@@ -1649,7 +1660,7 @@ __global__ void __launch_bounds__(256) k_stair(DevProblem P, int64_t n_inv, cons
             out[i] = bad;
             atomicAdd(&S.ctrl[kCtrlInvalid], 1ull);
         } else {
-            out[i] = stair_decide(P, P.dag_op_off[d] + o, P.slo[d] - (now - st), nullptr);
+            out[i] = stair_decide(P, g, rbase, nullptr);
         }
     }
     finish_call(S, out, false);
@@ -2383,22 +2394,38 @@ __global__ void k_refresh_order(DevProblem P, const int32_t *ord_pos, int4 *ord_
 // state lives in device memory (LoopState, the slot arrays and the queues).
 // ---------------------------------------------------------------------------
 
-// For each thread, how many threads before it have their flag set; *total is
-// the block's count.  Every thread must call it (two barriers).
-__device__ __forceinline__ int block_excl_count(bool f, int *total, int *wsum) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const unsigned b = __ballot_sync(0xffffffffu, f);
-    if (lane == 0) wsum[wid] = __popc(b);
-    __syncthreads();
-    int before = 0, tot = 0;
-    for (int w = 0; w < nw; ++w) {
-        const int c = wsum[w];
-        tot += c;
-        if (w < wid) before += c;
+// Arrival-order ranks of one tick's admissions, in one pass (two barriers):
+// for each thread, how many threads before it are valid (*vrank) and how many
+// before it are valid and speculated onto its own backend lam (*hrank);
+// tot[0] = valid ones, tot[1 + h] = those onto backend h.  cnt and pre hold
+// (LLAMA_MAX_HW + 1) x 32 words; one warp per category scans the per-warp
+// counts.  Every thread of the (1024-thread) block must call it.
+__device__ __forceinline__ void block_admission_ranks(bool valid, int lam, int H, int *vrank, int *hrank,
+                                                      int (*cnt)[32], int (*pre)[32], int *tot) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned below = (1u << lane) - 1u;
+    const unsigned bv = __ballot_sync(0xffffffffu, valid);
+    if (lane == 0) cnt[0][wid] = __popc(bv);
+    unsigned mine = 0;
+    for (int h = 0; h < H; ++h) {
+        const unsigned b = __ballot_sync(0xffffffffu, valid && lam == h);
+        if (lane == 0) cnt[1 + h][wid] = __popc(b);
+        if (lam == h) mine = b;
     }
-    __syncthreads();  // wsum is reused by the next call
-    *total = tot;
-    return before + __popc(b & ((1u << lane) - 1u));
+    __syncthreads();
+    if (wid <= H) {  // warp k scans category k over the 32 warps
+        const int c = cnt[wid][lane];
+        int inc = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += u;
+        }
+        pre[wid][lane] = inc - c;
+        if (lane == 31) tot[wid] = inc;
+    }
+    __syncthreads();
+    *vrank = pre[0][wid] + __popc(bv & below);
+    *hrank = lam >= 0 ? pre[1 + lam][wid] + __popc(mine & below) : 0;
 }
 
 // Eq. 2 over both queues: floor(s / R_total), clamped at INT32_MAX (every sum
@@ -2448,18 +2475,24 @@ __global__ void __launch_bounds__(kLoopThreads) k_loop_tick(DevProblem P, LoopDe
         const long long head = L.st->head;
         if (tid < L.max_admit && head + tid < a.limit) r = L.ring[(head + tid) & L.ring_mask];
     }
-    __shared__ int wsum[32];
+    __shared__ int adm_cnt[LLAMA_MAX_HW + 1][32], adm_pre[LLAMA_MAX_HW + 1][32], adm_tot[LLAMA_MAX_HW + 1];
+    __shared__ int32_t sh_disp[LLAMA_MAX_HW];
     __shared__ int sh_n_adm, sh_free_top, sh_tick;
     __shared__ long long sh_res, sh_res_read;
     __shared__ long long sh_sq_head[LLAMA_MAX_HW], sh_sq_tail[LLAMA_MAX_HW], sh_cq_tail[LLAMA_MAX_HW];
     __shared__ int sh_room[LLAMA_MAX_HW], sh_cnt[LLAMA_MAX_HW], sh_w[LLAMA_MAX_HW + 1], sh_group[LLAMA_MAX_HW],
         sh_ncommit_src[LLAMA_MAX_HW];
     __shared__ unsigned long long sh_lr_in[LLAMA_MAX_HW], sh_lr_out[LLAMA_MAX_HW];
-    __shared__ double c_aff[kLoopThreads];
+    // Eq. 3 affinities as order-preserving integer keys: non-negative doubles
+    // (+inf included) compare as their bit patterns read as unsigned integers
+    __shared__ unsigned long long c_aff[kLoopThreads];
     __shared__ int8_t c_lam[kLoopThreads], c_commit[kLoopThreads];
     // records the host has taken (mapped memory), read by the thread that uses it
     long long res_read = 0;
     if (tid == 0) res_read = (long long)*reinterpret_cast<volatile unsigned long long *>(&L.ctl->res_read);
+#pragma unroll
+    for (int h = 0; h < LLAMA_MAX_HW; ++h)  // constant indices into the argument
+        if (tid == h) sh_disp[h] = a.dispatch[h];
     __syncthreads();  // the state copy is complete
 
     // 1. dispatch: the heads of the commit queues leave (their slots go back on
@@ -2470,7 +2503,7 @@ __global__ void __launch_bounds__(kLoopThreads) k_loop_tick(DevProblem P, LoopDe
         int off = 0;
         for (int h = 0; h < H; ++h) {
             const long long len = S.cq_tail[h] - S.cq_head[h];
-            const int k = (int)min((long long)max(a.dispatch[h], 0), len);
+            const int k = (int)min((long long)max(sh_disp[h], 0), len);
             sh_cnt[h] = off;  // first dispatched entry of backend h
             off += k;
             sh_lr_out[h] = 0;
@@ -2537,22 +2570,20 @@ __global__ void __launch_bounds__(kLoopThreads) k_loop_tick(DevProblem P, LoopDe
     dsn.flags = LLAMA_FLAG_INVALID;
     unsigned long long lr = 0;
     if (tid < n_adm) {
-        if (invocation_valid(P, r.dag, r.op_local, r.start_us, a.now)) {
+        int32_t g;
+        int64_t rbase;
+        if (invocation_op(P, r.dag, r.op_local, r.start_us, a.now, g, rbase)) {
             valid = true;
-            const int32_t g = P.dag_op_off[r.dag] + r.op_local;
-            dsn = stair_decide(P, g, P.slo[r.dag] - (a.now - r.start_us), &lam);
+            dsn = stair_decide(P, g, rbase, &lam);
             lr = decision_lr(P, g, dsn);
         }
     }
-    int n_valid;
-    const int vrank = block_excl_count(valid, &n_valid, wsum);
-    int hrank = 0;
-    for (int h = 0; h < H; ++h) {  // rank among this tick's admissions speculated onto backend h
-        int tot;
-        const int rk = block_excl_count(valid && lam == h, &tot, wsum);
-        if (lam == h) hrank = rk;
-        if (tid == 0) sh_cnt[h] = tot;
-    }
+    // ranks among this tick's valid admissions, and among those speculated onto
+    // the same backend
+    int vrank, hrank;
+    block_admission_ranks(valid, valid ? lam : -1, H, &vrank, &hrank, adm_cnt, adm_pre, adm_tot);
+    const int n_valid = adm_tot[0];
+    if (tid < H) sh_cnt[tid] = adm_tot[1 + tid];
     if (valid) {
         const int32_t slot = L.free_stack[sh_free_top - 1 - vrank];
         L.slot_id[slot] = r.id;
@@ -2613,17 +2644,17 @@ __global__ void __launch_bounds__(kLoopThreads) k_loop_tick(DevProblem P, LoopDe
         int64_t best[LLAMA_MAX_HW];
 #pragma unroll
         for (int h = 0; h < LLAMA_MAX_HW; ++h) best[h] = h < H ? __ldg(om + h * stride + cnt[h]) : INT64_MAX;
-        c_aff[tid] = affinity_of(best, H, lam2);
+        c_aff[tid] = (unsigned long long)__double_as_longlong(affinity_of(best, H, lam2));
         c_lam[tid] = (int8_t)lam2;
     }
     __syncthreads();
     // the commit order: by backend, descending affinity, then candidate order
     int rank = 0;
     if (tid < C) {
-        const double my = c_aff[tid];
+        const unsigned long long my = c_aff[tid];
         for (int k = 0; k < C; ++k) {
             if (c_lam[k] != lam2) continue;
-            const double o = c_aff[k];
+            const unsigned long long o = c_aff[k];
             rank += (o > my) || (o == my && k < tid);
         }
         atomicAdd(&sh_group[lam2], 1);

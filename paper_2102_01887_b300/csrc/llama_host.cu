@@ -87,7 +87,7 @@ struct llama_ctx {
     // DAGs
     bool dags_set = false;
     int32_t n_dags = 0, n_ops_dag = 0;
-    DevBuf dag_op_off, row_ptr, col, slo, topo, lvl_off, dag_lvl;
+    DevBuf dag_op_off, row_ptr, col, slo, dag_info, topo, lvl_off, dag_lvl;
     // host copies of the DAG structure (for the packed per-DAG layout)
     std::vector<int32_t> h_dag_op_off, h_row_ptr, h_col, h_topo, h_lvl_off, h_dag_lvl;
     std::vector<int64_t> h_ref_gidx;
@@ -201,6 +201,7 @@ DevProblem make_problem(const llama_ctx *c) {
     P.row_ptr = c->row_ptr.as<int32_t>();
     P.col = c->col.as<int32_t>();
     P.slo = c->slo.as<int64_t>();
+    P.dag_info = c->dag_info.as<int4>();
     P.cfg_off = c->cfg_off.as<int64_t>();
     P.hw_off = c->hw_off.as<int32_t>();
     P.lat = c->lat.as<int32_t>();
@@ -809,8 +810,16 @@ extern "C" int llama_set_dags(llama_ctx *c, int32_t n_dags, const int32_t *dag_o
         if (e != cudaSuccess || bytes == 0) return e;
         return cudaMemcpy(b.p, h, bytes, cudaMemcpyHostToDevice);
     };
+    std::vector<int32_t> info(4 * (size_t)n_dags);
+    for (int32_t d = 0; d < n_dags; ++d) {
+        info[4 * (size_t)d + 0] = dag_op_off[d];
+        info[4 * (size_t)d + 1] = dag_op_off[d + 1];
+        info[4 * (size_t)d + 2] = (int32_t)(uint32_t)((uint64_t)slo_us[d] & 0xFFFFFFFFu);
+        info[4 * (size_t)d + 3] = (int32_t)(uint32_t)((uint64_t)slo_us[d] >> 32);
+    }
     cudaError_t e;
     if ((e = up(c->dag_op_off, dag_op_off, 4 * (size_t)(n_dags + 1))) != cudaSuccess ||
+        (e = up(c->dag_info, info.data(), 16 * (size_t)n_dags)) != cudaSuccess ||
         (e = up(c->row_ptr, row_ptr, 4 * (size_t)(n_ops + 1))) != cudaSuccess ||
         (e = up(c->col, col, 4 * (size_t)n_edges)) != cudaSuccess ||
         (e = up(c->slo, slo_us, 8 * (size_t)n_dags)) != cudaSuccess ||

@@ -87,6 +87,9 @@ struct DevProblem {
     int32_t n_dags, n_ops, n_hw, mode;
     const int32_t *dag_op_off, *row_ptr, *col;
     const int64_t *slo;
+    // [n_dags] per DAG {first op, end of its ops, SLO low 32 bits, SLO high 32
+    // bits}: what validating and counting an invocation needs, in one 16-byte load
+    const int4 *dag_info;
     const int64_t *cfg_off;
     const int32_t *hw_off;
     const int32_t *lat;
