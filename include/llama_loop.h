@@ -128,8 +128,9 @@ int llama_loop_tick(llama_loop *loop, int64_t now_us, const int32_t *dispatch);
  * it enqueues one at the steady clock's time (now_us at the start, plus the
  * microseconds since), with the same dispatch counts every tick (host,
  * n_hw entries, nullable = none; INT32_MAX dispatches each commit queue whole,
- * for backends that keep up).  It idles (sleeps a few microseconds) while the
- * ring is empty and nothing is in flight.  The caller keeps submitting and
+ * for backends that keep up).  The driver spins on the control words (it
+ * keeps one host core busy) while ticks are queued; once the ring is empty and
+ * nothing is in flight it spins a while longer, then sleeps 20 us between polls.  The caller keeps submitting and
  * polling; llama_loop_tick is refused while the driver runs.  Ticks are then
  * timed by the clock, so their records are not reproducible run to run (each
  * tick still does exactly what llama_loop_tick would).  Errors: EINVAL. */

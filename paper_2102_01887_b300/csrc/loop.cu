@@ -245,22 +245,38 @@ extern "C" int llama_loop_tick(llama_loop *lp, int64_t now_us, const int32_t *di
 
 namespace {
 
+// One pause of a waiting loop (the core's spin-wait hint where there is one).
+inline void cpu_relax() {
+#if defined(__x86_64__) || defined(__i386__)
+    __builtin_ia32_pause();
+#else
+    std::this_thread::yield();
+#endif
+}
+
 // The driver thread: a tick whenever fewer than in_flight are queued, at the
 // steady clock's time (now_us at the start, then the microseconds elapsed);
-// every tick applies the same dispatch counts.  With nothing pending on the
-// device and nothing new in the ring it idles briefly instead of launching.
+// every tick applies the same dispatch counts.  It spins (a pause per poll of
+// the mapped control words) while ticks are queued, since a sleep of a few
+// microseconds lasts tens on a general-purpose kernel and would let the queue
+// run dry; with nothing pending on the device and nothing new in the ring it
+// keeps spinning for a while, then sleeps between polls.
 void drive(llama_loop *lp, int64_t now0, int in_flight, LoopTickArgs a) {
     cudaSetDevice(lp->device);
     const auto t0 = std::chrono::steady_clock::now();
     volatile LoopCtl *ctl = lp->h_ctl;
+    constexpr int kIdleSpins = 1 << 16;  // polls before an idle loop starts to sleep
+    int idle_spins = 0;
     while (lp->running.load(std::memory_order_relaxed)) {
         const int64_t done = (int64_t)ctl->ticks;
         const int64_t limit = lp->tail.load(std::memory_order_seq_cst);
         const bool idle = done == lp->launched && (int64_t)ctl->head == limit && ctl->inflight == 0;
         if (lp->launched - done >= in_flight || idle) {
-            std::this_thread::sleep_for(std::chrono::microseconds(idle ? 20 : 2));
+            if (idle && ++idle_spins > kIdleSpins) std::this_thread::sleep_for(std::chrono::microseconds(20));
+            else cpu_relax();
             continue;
         }
+        idle_spins = 0;
         a.now = now0 + std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t0).count();
         a.limit = limit;
         nvtxRangePushA("llama:loop_tick");
