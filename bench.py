@@ -511,6 +511,57 @@ class HugePinned:
             self.ok = False
 
 
+def e2e_pipelined(L, ctx, dev, inv, np_dag, np_opl, np_st, flush, steps: int, warmup: int, depth: int = 2,
+                  inputs: int = 0):
+    """End to end through llama_schedule_ws_async with page-locked host arrays,
+    `depth` calls in flight on as many streams (a workspace and a host output
+    each): every step reads its inputs in place over the host link and copies
+    its decisions back to the host, the next step's reads overlapping that copy
+    (inputs = WS_INPUTS_COPY: the inputs copied by the copy engine first).
+    Returns (seconds for `steps` steps, host outputs) -- the whole run timed,
+    each step's L2 flush enqueued on its own stream."""
+    import ctypes
+
+    import torch
+    lib = L.load()
+    ws = [ctypes.c_void_p() for _ in range(depth)]
+    outs = [torch.zeros(inv.n * 24, dtype=torch.uint8).pin_memory() for _ in range(depth)]
+    streams = [torch.cuda.Stream(device=dev) for _ in range(depth)]
+    try:
+        for w in ws:
+            rc = lib.llama_ws_create(ctx, inv.n, ctypes.byref(w))
+            if rc != L.OK:
+                raise L.LlamaError(rc, "ws_create")
+            lib.llama_ws_set_inputs(w, inputs)
+
+        def call(k):
+            slot = k % depth
+            with torch.cuda.stream(streams[slot]):
+                flush.fill_(k & 0xFF)
+            rc = lib.llama_schedule_ws_async(ctx, ws[slot], inv.n, np_dag.ctypes.data, np_opl.ctypes.data,
+                                             np_st.ctypes.data, inv.now_us, outs[slot].data_ptr(),
+                                             streams[slot].cuda_stream)
+            if rc != L.OK:
+                raise L.LlamaError(rc, "schedule_ws_async")
+
+        for k in range(warmup):
+            call(k)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(steps):
+            if k >= depth:
+                streams[k % depth].synchronize()  # that slot's previous decisions are on the host
+            call(k)
+        for st in streams:
+            st.synchronize()
+        wall = time.perf_counter() - t0
+    finally:
+        for w in ws:
+            if w.value:
+                lib.llama_ws_destroy(w)
+    return wall, [o.numpy().view(L.DECISION_DTYPE) for o in outs]
+
+
 def host_link(dev):
     """Page-locked host <-> device copy rates at several sizes (copy engine,
     CUDA events), the transfers an end-to-end call makes: torch's pinned
@@ -1022,6 +1073,23 @@ def main():
                 np_dag[:], np_opl[:], np_st[:] = inv.dag, inv.op_local, inv.start_us
                 h_out = hps[3].t[:inv.n * 24]
             np_out = h_out.numpy().view(L.DECISION_DTYPE)
+            if kind == "huge_pages":
+                # two calls in flight (a workspace and a stream each), inputs read
+                # in place or copied by the copy engine
+                for name, mode, how in (("pipelined", L.WS_INPUTS_IN_PLACE, "read in place from"),
+                                        ("pipelined_copy", L.WS_INPUTS_COPY, "copied by the copy engine from")):
+                    pw, pouts = e2e_pipelined(L, ctx, dev, inv, np_dag, np_opl, np_st, flush, args.steps,
+                                              args.warmup, inputs=mode)
+                    assert all((o["cfg"] == got["cfg"]).all() for o in pouts)
+                    pw = max_over_ranks(pw, world, dev)
+                    variants[name] = {
+                        "value": job_throughput(world, inv.n, args.steps, pw), "unit": UNIT,
+                        "h2d_bytes_per_step": int(inv.n * (4 + 4 + 8)), "d2h_bytes_per_step": int(inv.n * 24),
+                        "memory": "huge_pages",
+                        "transfer": f"two calls in flight on two streams (llama_schedule_ws_async, a workspace "
+                                    f"each): inputs {how} page-locked host memory, decisions copied back on "
+                                    f"the call's stream",
+                        "p50_call_us": 1e6 * pw / args.steps, "p99_call_us": None}
             for _ in range(args.warmup):
                 L.llama_schedule(ctx, np_dag, np_opl, np_st, inv.now_us, np_out)
             wall = []

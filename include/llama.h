@@ -225,10 +225,30 @@ typedef struct llama_ws llama_ws;
 int llama_ws_create(llama_ctx *ctx, int64_t max_inv, llama_ws **out);
 void llama_ws_destroy(llama_ws *ws);
 
-/* llama_schedule_async with the workspace ws (direct launches, no graph). */
+/* llama_schedule_async with the workspace ws (direct launches, no graph).
+ * Each pointer may be device memory or page-locked host memory: host inputs
+ * are read in place by the kernels over the host link; for a host `out` the
+ * decisions go to a device buffer of the workspace (allocated by the first
+ * such call, max_inv records) and are copied back on `stream`.  So a caller
+ * holding host arrays can keep several calls in flight on several streams
+ * (one workspace each), one call's copy back overlapping the next one's reads.
+ * Pageable host memory is refused (EINVAL).  Host arrays must stay valid and
+ * unchanged until the stream passes the call. */
 int llama_schedule_ws_async(llama_ctx *ctx, llama_ws *ws, int64_t n_inv, const int32_t *dag,
                             const int32_t *op_local, const int64_t *start_us, int64_t now_us,
                             llama_decision *out, void *stream);
+
+/* How the workspace's calls take inputs in page-locked host memory: read in
+ * place by the kernels over the host link (LLAMA_WS_INPUTS_IN_PLACE, the
+ * default; the fastest for a call alone) or copied into the workspace by the
+ * copy engine on the call's stream first (LLAMA_WS_INPUTS_COPY: the kernels
+ * then do not wait on the link, so with calls in flight on several streams
+ * one call's inputs, another's kernels and a third's decisions can move at
+ * once).  The copy buffers (16 B per invocation of max_inv) are allocated by
+ * the first call that needs them.  Errors: EINVAL. */
+#define LLAMA_WS_INPUTS_IN_PLACE 0
+#define LLAMA_WS_INPUTS_COPY 1
+int llama_ws_set_inputs(llama_ws *ws, int32_t mode);
 
 /* Status of the workspace's last completed call (read once the stream has
  * passed it; blocking): the number of invalid invocations, and whether a

@@ -51,10 +51,10 @@ def autotune(ctx, dag, op_local, start, now: int, out, stream=None, flush=None,
     """Sweep the candidates, apply the fastest, return {"best": ..., "trials": [...]}.
 
     ``chunks``: staging chunk sizes in configurations (0 = the library default);
-    ``stages``: staging buffers per CTA (1 or 2); ``ctas_per_sm``: caps on the
-    scoring CTAs per SM, tried for the fastest schedule (0 = as many as fit);
-    ``dlat_stage``: most distinct latencies staged per op, the first used for
-    the sweep, the others tried last.
+    ``stages``: staging buffers per CTA (1 or 2); ``dlat_stage``: most distinct
+    latencies staged per op, each with the whole grid of the above (the best
+    chunk depends on it); ``ctas_per_sm``: caps on the scoring CTAs per SM,
+    tried for the fastest schedule (0 = as many as fit).
     """
     import torch
     if stream is None:
@@ -62,16 +62,17 @@ def autotune(ctx, dag, op_local, start, now: int, out, stream=None, flush=None,
     if flush is None:
         flush = torch.empty(256 << 20, dtype=torch.uint8, device=dag.device)
     trials = []
-    dlat_stage = list(dlat_stage)
     L.llama_set_count_pass(ctx, L.COUNT_PASS_AUTO)
     L.llama_set_score_occupancy(ctx, 0)
-    L.llama_set_dlat_stage(ctx, dlat_stage[0])
-    for st, chunk, lmv, ipt in itertools.product(stages, chunks, lanes, ipts):
-        L.llama_set_tuning(ctx, lmv, ipt, chunk, st)
-        ms = time_call(ctx, dag, op_local, start, now, out, stream, flush, reps)
-        trials.append({"lanes_min_vectors": lmv, "inv_per_thread": ipt, "chunk": chunk, "stages": st,
-                       "ms": ms})
+    for dls in dlat_stage:
+        L.llama_set_dlat_stage(ctx, dls)
+        for st, chunk, lmv, ipt in itertools.product(stages, chunks, lanes, ipts):
+            L.llama_set_tuning(ctx, lmv, ipt, chunk, st)
+            ms = time_call(ctx, dag, op_local, start, now, out, stream, flush, reps)
+            trials.append({"lanes_min_vectors": lmv, "inv_per_thread": ipt, "chunk": chunk, "stages": st,
+                           "dlat_stage": dls, "ms": ms})
     best = min(trials, key=lambda t: t["ms"])
+    L.llama_set_dlat_stage(ctx, best["dlat_stage"])
     L.llama_set_tuning(ctx, best["lanes_min_vectors"], best["inv_per_thread"], best["chunk"], best["stages"])
     # the count pass, forced on and off, against the default for the best
     # schedule -- where it can run at all (forced on, a call launches it)
@@ -96,14 +97,4 @@ def autotune(ctx, dag, op_local, start, now: int, out, stream=None, flush=None,
         if ms < best["ms"]:
             best = trials[-1]
     L.llama_set_score_occupancy(ctx, best["ctas_per_sm"])
-    # the distinct latencies staged per op, for that schedule (the count pass
-    # as chosen above; it is not launched where no op needs it)
-    best = dict(best, dlat_stage=dlat_stage[0])
-    for cap in dlat_stage[1:]:
-        L.llama_set_dlat_stage(ctx, cap)
-        ms = time_call(ctx, dag, op_local, start, now, out, stream, flush, reps)
-        trials.append(dict(best, dlat_stage=cap, ms=ms))
-        if ms < best["ms"]:
-            best = trials[-1]
-    L.llama_set_dlat_stage(ctx, best["dlat_stage"])
     return {"best": best, "trials": trials}

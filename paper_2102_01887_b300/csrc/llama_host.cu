@@ -1309,6 +1309,9 @@ struct llama_ws {
     Workspace w;
     llama_ctx *ctx = nullptr;
     int device = 0;
+    DevBuf out_stage;  // decisions of a call whose output is page-locked host memory
+    int32_t inputs = LLAMA_WS_INPUTS_IN_PLACE;
+    DevBuf in_dag, in_opl, in_start;  // copies of page-locked host inputs (LLAMA_WS_INPUTS_COPY)
 };
 
 extern "C" int llama_ws_create(llama_ctx *c, int64_t max_inv, llama_ws **out) {
@@ -1348,9 +1351,50 @@ extern "C" int llama_schedule_ws_async(llama_ctx *c, llama_ws *ws, int64_t n_inv
     if (ws->w.cap_ops < c->n_ops + 1 || ws->w.cap_tiles < max_tiles(n_inv, c->n_ops))
         return c->fail(LLAMA_EINVAL, "schedule_ws: workspace sized for fewer operations (profiles changed)");
     DeviceGuard g(c->opts.device);
+    // device or page-locked host memory: inputs read in place, decisions for a
+    // host output written to the workspace's staging buffer and copied back
+    // on the stream
+    const void *rd = kernel_readable(dag), *ro = kernel_readable(op_local), *rs = kernel_readable(start_us);
+    if (!rd || !ro || !rs)
+        return c->fail(LLAMA_EINVAL, "schedule_ws: inputs must be device or page-locked host memory");
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (ws->inputs == LLAMA_WS_INPUTS_COPY) {
+        // host inputs copied into the workspace by the copy engine on the stream
+        const int64_t cap = ws->w.cap_inv;
+        struct In {
+            const void *src, **dst;
+            DevBuf *buf;
+            size_t elem;
+        } ins[3] = {{dag, &rd, &ws->in_dag, 4}, {op_local, &ro, &ws->in_opl, 4}, {start_us, &rs, &ws->in_start, 8}};
+        for (In &in : ins) {
+            if (is_device_ptr(in.src)) continue;
+            if (in.buf->bytes < in.elem * (size_t)cap) LL_CUDA(c, in.buf->alloc(in.elem * (size_t)cap));
+            LL_CUDA(c, cudaMemcpyAsync(in.buf->p, in.src, in.elem * (size_t)n_inv, cudaMemcpyHostToDevice, s));
+            *in.dst = in.buf->p;
+        }
+    }
+    const bool outd = is_device_ptr(out);
+    if (!outd) {
+        cudaPointerAttributes a{};
+        if (cudaPointerGetAttributes(&a, out) != cudaSuccess || a.type != cudaMemoryTypeHost) {
+            cudaGetLastError();
+            return c->fail(LLAMA_EINVAL, "schedule_ws: out must be device or page-locked host memory");
+        }
+        if (ws->out_stage.bytes < sizeof(llama_decision) * (size_t)ws->w.cap_inv)
+            LL_CUDA(c, ws->out_stage.alloc(sizeof(llama_decision) * (size_t)ws->w.cap_inv));
+    }
+    llama_decision *d_out = outd ? out : ws->out_stage.as<llama_decision>();
     const ContextView v = view_of(c);
-    LL_CUDA(c, enqueue_schedule(v, make_scratch(ws->w), n_inv, dag, op_local, start_us, now_us, out,
-                                static_cast<cudaStream_t>(stream), nullptr));
+    LL_CUDA(c, enqueue_schedule(v, make_scratch(ws->w), n_inv, static_cast<const int32_t *>(rd),
+                                static_cast<const int32_t *>(ro), static_cast<const int64_t *>(rs), now_us, d_out,
+                                s, nullptr));
+    if (!outd) LL_CUDA(c, cudaMemcpyAsync(out, d_out, sizeof(llama_decision) * n_inv, cudaMemcpyDeviceToHost, s));
+    return LLAMA_OK;
+}
+
+extern "C" int llama_ws_set_inputs(llama_ws *ws, int32_t mode) {
+    if (!ws || (mode != LLAMA_WS_INPUTS_IN_PLACE && mode != LLAMA_WS_INPUTS_COPY)) return LLAMA_EINVAL;
+    ws->inputs = mode;
     return LLAMA_OK;
 }
 

@@ -41,7 +41,7 @@ EXPORTS = ("llama_create", "llama_destroy", "llama_set_dags", "llama_set_profile
            "llama_mlp_forward", "llama_mlp_gradients", "llama_mlp_train_step", "llama_mlp_last_error",
            "llama_sg_create", "llama_sg_destroy", "llama_sg_schedule", "llama_sg_last_pairs",
            "llama_sg_predictions", "llama_sg_last_error", "llama_sg_set_margin", "llama_sg_invalidate",
-           "llama_ws_create", "llama_ws_destroy", "llama_schedule_ws_async", "llama_ws_status",
+           "llama_ws_create", "llama_ws_destroy", "llama_schedule_ws_async", "llama_ws_status", "llama_ws_set_inputs",
            "llama_server_create", "llama_server_destroy", "llama_server_submit", "llama_server_poll",
            "llama_server_drain", "llama_server_stats_get", "llama_queue_time", "llama_feedback",
            "llama_get_profiles", "llama_backend_objectives", "llama_commit_order",
@@ -144,6 +144,7 @@ def load(path: str = None) -> ctypes.CDLL:
             "llama_ws_create": ([vp, i64, ctypes.POINTER(vp)], ctypes.c_int),
             "llama_ws_destroy": ([vp], None),
             "llama_schedule_ws_async": ([vp, vp, i64, vp, vp, vp, i64, vp, vp], ctypes.c_int),
+            "llama_ws_set_inputs": ([vp, ctypes.c_int32], ctypes.c_int),
             "llama_ws_status": ([vp, vp, vp], ctypes.c_int),
             "llama_server_create": ([vp, vp, ctypes.POINTER(vp)], ctypes.c_int),
             "llama_server_destroy": ([vp], None),
@@ -259,6 +260,8 @@ def llama_set_score_occupancy(ctx, ctas_per_sm: int) -> None:
 
 
 DLAT_STAGE_DEFAULT = 4096
+WS_INPUTS_IN_PLACE = 0
+WS_INPUTS_COPY = 1
 
 
 def llama_set_dlat_stage(ctx, max_entries: int) -> None:

@@ -23,12 +23,14 @@ def test_autotune_picks_a_schedule_and_results_stay_exact(cuda_device):
         st = torch.from_numpy(sub.start_us).to(dev)
         out = torch.zeros(sub.n * 24, dtype=torch.uint8, device=dev)
         res = autotune(s.ctx, dag, opl, st, sub.now_us, out, lanes=(8, 32), ipts=(1, 2), reps=2)
-        # 2 lanes x 2 ipt x 2 stagings, then 4 and 3 scoring CTAs per SM and
-        # 8,192 staged distinct latencies for the fastest; no count-pass
-        # trials: every op's distinct latencies are staged by the scoring kernel
-        assert len(res["trials"]) == 11 and res["best"]["ms"] > 0
-        assert [t.get("ctas_per_sm") for t in res["trials"][8:10]] == [4, 3]
-        assert res["trials"][10]["dlat_stage"] == 8192 and res["best"]["dlat_stage"] in (4096, 8192)
+        # 2 lanes x 2 ipt x 2 stagings for each of 4,096 and 8,192 staged
+        # distinct latencies, then 4 and 3 scoring CTAs per SM for the fastest;
+        # no count-pass trials: every op's distinct latencies are staged by the
+        # scoring kernel
+        assert len(res["trials"]) == 18 and res["best"]["ms"] > 0
+        assert [t["dlat_stage"] for t in res["trials"][:16]] == [4096] * 8 + [8192] * 8
+        assert [t.get("ctas_per_sm") for t in res["trials"][16:]] == [4, 3]
+        assert res["best"]["dlat_stage"] in (4096, 8192)
         assert res["best"]["count_pass"] == L.COUNT_PASS_AUTO
         assert res["best"]["ctas_per_sm"] in (0, 4, 3)
         out.zero_()
