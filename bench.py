@@ -1035,6 +1035,9 @@ def main():
                 step()
             L.llama_set_trace_events(ctx, [])
         torch.cuda.synchronize()
+        # the ceiling of the scan's instruction mix, measured while the GPU is
+        # still under the timed load (its clocks are in the same samples)
+        mix_scores = L.llama_alu_peak(local, mode) if args.method == "scan" else None
     step_ms = np.asarray([s.elapsed_time(e) for s, e in zip(starts, ends)])
     phase_ms = np.asarray([[t[j].elapsed_time(t[j + 1]) for j in range(len(L.TRACE_PHASES))]
                            for t in traces])
@@ -1170,8 +1173,8 @@ def main():
     else:
         nominal_tops = sm_count * ALU_LANES_PER_SM * sm_mhz * 1e6 / 1e12
         ops_per_score = ALU_OPS_PER_SCORE[args.mode]
-        # the measured ceiling of the scan's own instruction mix (llama_alu_peak)
-        mix_scores = L.llama_alu_peak(local, mode)
+        # mix_scores: the measured ceiling of the scan's own instruction mix
+        # (llama_alu_peak, right after the timed steps)
         peak_tops = mix_scores * ops_per_score / 1e12
         achieved = ops_per_score * scores / (kms["score"] / 1e3) / 1e12
         rooflines["k_score"] = {

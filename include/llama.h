@@ -444,7 +444,8 @@ int llama_last_launch_count(llama_ctx *ctx);
  * packed subtract of latency ranks, one LOP3, one per-half 16-bit minimum
  * (LLAMA_MODE_COST_FIRST), plus one PRMT (LLAMA_MODE_ALPHA) -- on operands
  * already in registers, on every SM.  *scores_per_s receives configurations
- * per second (best of five timed launches after one warm-up).  Allocates a
+ * per second: the best of 20 timed launches after 40 untimed ones (about
+ * 25 ms of full load, so the SM clock has left any idle state).  Allocates a
  * 16-byte buffer for the duration of the call.  Errors: EINVAL, ECUDA. */
 int llama_alu_peak(int32_t device, int32_t mode, double *scores_per_s);
 

@@ -79,15 +79,20 @@ extern "C" int llama_alu_peak(int32_t device, int32_t mode, double *scores_per_s
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) goto done;
     {
         const int blocks = sms * std::max(1, per_sm);
-        for (int rep = 0; rep < 6; ++rep) {
-            cudaEventRecord(e0, s);
+        // kWarm back-to-back launches (tens of ms of full load) bring the SM
+        // clock up from whatever the GPU was doing before; then the best of
+        // kTimed single launches
+        constexpr int kWarm = 40, kTimed = 20;
+        for (int rep = 0; rep < kWarm + kTimed; ++rep) {
+            if (rep >= kWarm) cudaEventRecord(e0, s);
             if (mode == LLAMA_MODE_ALPHA) k_alu_peak<true><<<blocks, kThreads, 0, s>>>(sink, iters, rep);
             else k_alu_peak<false><<<blocks, kThreads, 0, s>>>(sink, iters, rep);
+            if (rep < kWarm) continue;
             cudaEventRecord(e1, s);
             if (cudaEventSynchronize(e1) != cudaSuccess) goto done;
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
-            if (rep > 0) best_ms = std::min(best_ms, ms);  // the first launch warms up
+            best_ms = std::min(best_ms, ms);
         }
         // two configurations per chain step
         *scores_per_s = 2.0 * kChains * (double)iters * blocks * kThreads / (best_ms * 1e-3);
