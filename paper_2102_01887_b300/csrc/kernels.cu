@@ -528,35 +528,6 @@ __device__ __forceinline__ bool call_timed_out(const BucketScratch &S) {
     return *reinterpret_cast<volatile unsigned long long *>(&S.ctrl[kCtrlTimeout]) != 0ull;
 }
 
-// Validate invocation i and count it for its op: g = global op (-1 if invalid,
-// then its decision is written here), slot = its rank in the op's bucket,
-// rbase = target - elapsed time (Algorithm 1 before the queueing time).
-__device__ __forceinline__ void count_invocation(const DevProblem &P, int64_t i, const int32_t *dag,
-                                                 const int32_t *op_local, const int64_t *start,
-                                                 int64_t now, const BucketScratch &S,
-                                                 llama_decision *out, int32_t &g, int32_t &slot,
-                                                 int64_t &rbase) {
-    const int32_t d = dag[i], o = op_local[i];
-    const int64_t st = start[i];
-    if (!invocation_op(P, d, o, st, now, g, rbase)) {
-        g = -1;
-        S.gop[i] = -1;
-        llama_decision bad;
-        bad.cfg = -1;
-        bad.lat = 0;
-        bad.cost = 0;
-        bad.slack = 0;
-        bad.flags = LLAMA_FLAG_INVALID;
-        out[i] = bad;
-        atomicAdd(&S.ctrl[kCtrlInvalid], 1ull);
-        return;
-    }
-    slot = atomicAdd(&S.cnt[(int64_t)g * kCntStride], 1);
-    S.gop[i] = g;
-    S.slot[i] = slot;
-    S.rbase[i] = rbase;
-}
-
 // Place invocation i in its op's bucket (op_start: first bucket position of
 // every op) with its remaining time before queueing, max(0, SLO - elapsed)
 // <= SLO < 2^31.  The scoring kernel turns it into the slack per backend
@@ -570,11 +541,103 @@ __device__ __forceinline__ void scatter_invocation(const DevProblem &P, const Bu
     S.b_ent[pos] = make_int2((int32_t)i, (int32_t)max(rbase, (int64_t)0));
 }
 
-// The bucketing step of a call, one cooperative launch (all blocks resident):
+// Validate and count a round of B invocations, i = i0 + j * stride for j < B
+// (every load of the round is issued before any of its results is used, so a
+// thread has B dependent chains in flight): g[j] = the global op (-1 if invalid,
+// then its decision is written here, or if i >= n_inv), slot[j] = its rank in
+// the op's bucket (one counter per 128-byte line, so concurrent atomics on
+// different ops never share a line), rb[j] = target - elapsed time (Algorithm 1
+// before the queueing time).  S.gop[i] is written for every invocation of the
+// call; slot and rb also go to S.slot and S.rbase when store_rest (the caller
+// does not keep them in registers).
+template <int B>
+__device__ __forceinline__ void count_round(const DevProblem &P, int64_t i0, int64_t stride, int64_t n_inv,
+                                            const int32_t *dag, const int32_t *op_local, const int64_t *start,
+                                            int64_t now, const BucketScratch &S, llama_decision *out,
+                                            bool store_rest, int32_t (&g)[B], int32_t (&slot)[B],
+                                            int64_t (&rb)[B]) {
+    int32_t d[B], o[B];
+    int64_t st[B];
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+        const int64_t i = i0 + j * stride;
+        const bool in = i < n_inv;
+        d[j] = in ? dag[i] : -1;
+        o[j] = in ? op_local[i] : 0;
+        st[j] = in ? start[i] : 0;
+    }
+    // the checks of invocation_op, on each invocation's DAG record
+    int4 di[B];
+#pragma unroll
+    for (int j = 0; j < B; ++j)
+        di[j] = (d[j] >= 0 && d[j] < P.n_dags) ? __ldg(P.dag_info + d[j]) : make_int4(0, 0, 0, 0);
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+        const bool ok = d[j] >= 0 && d[j] < P.n_dags && o[j] >= 0 && o[j] < di[j].y - di[j].x && st[j] >= 0 &&
+                        st[j] <= now;
+        g[j] = ok ? di[j].x + o[j] : -1;
+        rb[j] = (int64_t)(((uint64_t)(uint32_t)di[j].w << 32) | (uint32_t)di[j].z) - (now - st[j]);
+        slot[j] = ok ? atomicAdd(&S.cnt[(int64_t)g[j] * kCntStride], 1) : 0;
+    }
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+        const int64_t i = i0 + j * stride;
+        if (i >= n_inv) continue;
+        S.gop[i] = g[j];
+        if (g[j] < 0) {
+            llama_decision bad;
+            bad.cfg = -1;
+            bad.lat = 0;
+            bad.cost = 0;
+            bad.slack = 0;
+            bad.flags = LLAMA_FLAG_INVALID;
+            out[i] = bad;
+            atomicAdd(&S.ctrl[kCtrlInvalid], 1ull);
+        } else if (store_rest) {
+            S.slot[i] = slot[j];
+            S.rbase[i] = rb[j];
+        }
+    }
+}
+
+// Place a round of B invocations counted by count_round with store_rest (not
+// kept in registers): their ops, slots and times loaded first, then the
+// bucket starts, then the stores.
+template <int B>
+__device__ __forceinline__ void scatter_round(const DevProblem &P, const BucketScratch &S, const int32_t *op_start,
+                                              int64_t i0, int64_t stride, int64_t n_inv) {
+    int32_t g[B], sl[B];
+    int64_t rb[B];
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+        const int64_t i = i0 + j * stride;
+        g[j] = i < n_inv ? S.gop[i] : -1;
+    }
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+        const int64_t i = i0 + j * stride;
+        sl[j] = g[j] >= 0 ? S.slot[i] : 0;
+        rb[j] = g[j] >= 0 ? S.rbase[i] : 0;
+    }
+    int32_t os[B];
+#pragma unroll
+    for (int j = 0; j < B; ++j) os[j] = g[j] >= 0 ? op_start[g[j]] : 0;
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+        if (g[j] < 0) continue;
+        const int64_t pos = (int64_t)os[j] + sl[j];
+        if (!LLAMA_IN_BOUNDS(P, pos >= 0 && pos < S.n_inv, LLAMA_CHECK_SCATTER)) continue;
+        S.b_ent[pos] = make_int2((int32_t)(i0 + j * stride), (int32_t)max(rb[j], (int64_t)0));
+    }
+}
+
+// The bucketing step of a call, one cooperative launch (all blocks resident,
+// four per SM at 64 registers):
 //  1. blocks [0, n_cp) compute the critical paths (a warp per small DAG); the
 //     other blocks validate invocations, count them per op (one counter per
 //     128-byte line, so concurrent atomics on different ops never share a
-//     line) and prefetch the encoded tables into L2;
+//     line), in rounds of kRound per thread after the first kKeep, and
+//     prefetch the encoded tables into L2;
 //  2. the counting blocks lay out the buckets and the scoring tiles, ops in
 //     the order P.op_order (largest tables first), every op's full tiles
 //     first, then the tails: per-block sums, a barrier of the counting
@@ -583,7 +646,7 @@ __device__ __forceinline__ void scatter_invocation(const DevProblem &P, const Bu
 //  4. the counting blocks place their invocations in their buckets, each with
 //     its remaining time (the scoring kernel turns it into the slack per
 //     backend, Algorithm 1 through the critical path).
-__global__ void __launch_bounds__(256) k_bucket(DevProblem P, int64_t n_inv, const int32_t *dag,
+__global__ void __launch_bounds__(256, 4) k_bucket(DevProblem P, int64_t n_inv, const int32_t *dag,
                                                 const int32_t *op_local, const int64_t *start,
                                                 int64_t now, BucketScratch S, llama_decision *out,
                                                 const int32_t *topo, const int32_t *lvl_off,
@@ -617,16 +680,11 @@ __global__ void __launch_bounds__(256) k_bucket(DevProblem P, int64_t n_inv, con
     const int64_t base = (blockIdx.x - n_cp) * (int64_t)blockDim.x + threadIdx.x;
     int32_t kg[kKeep], ks[kKeep];
     int64_t kr[kKeep];
-#pragma unroll
-    for (int j = 0; j < kKeep; ++j) {
-        kg[j] = -1;
-        const int64_t i = base + j * stride;
-        if (i < n_inv) count_invocation(P, i, dag, op_local, start, now, S, out, kg[j], ks[j], kr[j]);
-    }
-    for (int64_t i = base + kKeep * stride; i < n_inv; i += stride) {
-        int32_t g, sl;
-        int64_t rb;
-        count_invocation(P, i, dag, op_local, start, now, S, out, g, sl, rb);
+    count_round<kKeep>(P, base, stride, n_inv, dag, op_local, start, now, S, out, false, kg, ks, kr);
+    for (int64_t i0 = base + kKeep * stride; i0 < n_inv; i0 += kRound * stride) {
+        int32_t g[kRound], sl[kRound];
+        int64_t rb[kRound];
+        count_round<kRound>(P, i0, stride, n_inv, dag, op_local, start, now, S, out, true, g, sl, rb);
     }
     // Pull the encoded tables into L2 while the buckets are laid out, so the
     // scoring kernel's staging does not wait on DRAM.
@@ -673,10 +731,8 @@ __global__ void __launch_bounds__(256) k_bucket(DevProblem P, int64_t n_inv, con
 #pragma unroll
     for (int j = 0; j < kKeep; ++j)
         if (kg[j] >= 0) scatter_invocation(P, S, op_start, base + j * stride, kg[j], ks[j], kr[j]);
-    for (int64_t i = base + kKeep * stride; i < n_inv; i += stride) {
-        const int32_t g = S.gop[i];
-        if (g >= 0) scatter_invocation(P, S, op_start, i, g, S.slot[i], S.rbase[i]);
-    }
+    for (int64_t i0 = base + kKeep * stride; i0 < n_inv; i0 += kRound * stride)
+        scatter_round<kRound>(P, S, op_start, i0, stride, n_inv);
 }
 
 // Slack of every invocation for every backend, without bucketing.

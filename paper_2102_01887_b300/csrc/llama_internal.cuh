@@ -50,6 +50,7 @@ __host__ __device__ constexpr int32_t warp_pad_of(int mode) {
 }
 constexpr int kMaxWaitTries = LLAMA_WAIT_LIMIT_DEFAULT;  // bounded waits (mbarrier, grid barrier)
 constexpr int kKeep = 4;               // invocations a counting thread keeps in registers
+constexpr int kRound = 4;              // invocations a counting thread takes per round after those
 constexpr int kKeepOps = 2;            // ops the layout keeps in registers per thread
 constexpr int kMaxDlatSmem = 4096;     // distinct latencies staged per op (else searched in L2)
 constexpr int kPfArrays = 20;          // arrays k_bucket prefetches into L2 at its start
