@@ -45,14 +45,14 @@ SCAN_BYTES_PER_SCORE = 12  # int32 latency + int64 cost per scored configuration
 # profiles/ holds the summaries and the commands.  Reported as null as soon as
 # the sources or the schedule differ.  Keys: workload/objective.
 MEASURED_TRAFFIC = {
-    "digest": "9fb0adeecd414c1b",
+    "digest": "0eeff0ab32242e36",
     # profiles/k_bucket_batched.md, profiles/k_score_batched.md
-    "k_bucket:batched/cost_first": (71.23e6, (64, 2, 0, 1, 0, 0, 8192)),
-    "k_score:batched/cost_first": (86.80e6, (64, 2, 0, 1, 0, 0, 8192)),
+    "k_bucket:batched/cost_first": (68.77e6, (64, 2, 0, 1, 0, 0, 8192)),
+    "k_score:batched/cost_first": (86.42e6, (64, 2, 0, 1, 0, 0, 8192)),
     # profiles/scoring_pass_batched_large_192dags.md: the scoring pass (count pass
-    # + scoring kernel) measured at 192 DAGs, 180.40 MB, scaled to the 512-DAG
+    # + scoring kernel) measured at 192 DAGs, 180.41 MB, scaled to the 512-DAG
     # launch by its algorithmic bytes (459.50 / 172.25 MB)
-    "k_score:batched_large_512/cost_first": (481.2e6, (32, 1, 8256, 1, 0, 0, 4096)),
+    "k_score:batched_large_512/cost_first": (481.3e6, (32, 1, 8256, 1, 0, 0, 4096)),
 }
 SCHEDULE_KEYS = ("lanes_min_vectors", "inv_per_thread", "chunk", "stages", "count_pass", "ctas_per_sm", "dlat_stage")
 
