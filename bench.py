@@ -41,20 +41,21 @@ SCAN_BYTES_PER_SCORE = 12  # int32 latency + int64 cost per scored configuration
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of each
 # kernel, from ncu captures of the kernel sources whose digest is "digest", each
 # with the launch schedule it was captured under (lanes_min_vectors,
-# inv_per_thread, chunk, stages, count_pass, ctas_per_sm, dlat_stage);
+# inv_per_thread, chunk, stages, ctas_per_sm, dlat_stage) and whether the count
+# pass ran (the count-pass setting itself may be on, off or automatic);
 # profiles/ holds the summaries and the commands.  Reported as null as soon as
 # the sources or the schedule differ.  Keys: workload/objective.
 MEASURED_TRAFFIC = {
     "digest": "0eeff0ab32242e36",
     # profiles/k_bucket_batched.md, profiles/k_score_batched.md
-    "k_bucket:batched/cost_first": (68.77e6, (64, 2, 0, 1, 0, 0, 8192)),
-    "k_score:batched/cost_first": (86.42e6, (64, 2, 0, 1, 0, 0, 8192)),
+    "k_bucket:batched/cost_first": (68.77e6, (64, 2, 0, 1, 0, 8192), False),
+    "k_score:batched/cost_first": (86.42e6, (64, 2, 0, 1, 0, 8192), False),
     # profiles/scoring_pass_batched_large_192dags.md: the scoring pass (count pass
     # + scoring kernel) measured at 192 DAGs, 180.41 MB, scaled to the 512-DAG
     # launch by its algorithmic bytes (459.50 / 172.25 MB)
-    "k_score:batched_large_512/cost_first": (481.3e6, (32, 1, 8256, 1, 0, 0, 4096)),
+    "k_score:batched_large_512/cost_first": (481.3e6, (32, 1, 8256, 1, 0, 4096), True),
 }
-SCHEDULE_KEYS = ("lanes_min_vectors", "inv_per_thread", "chunk", "stages", "count_pass", "ctas_per_sm", "dlat_stage")
+SCHEDULE_KEYS = ("lanes_min_vectors", "inv_per_thread", "chunk", "stages", "ctas_per_sm", "dlat_stage")
 
 
 def kernel_digest() -> str:
@@ -71,16 +72,18 @@ def kernel_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic(kernel: str, workload: str, mode: str, schedule) -> Optional[float]:
-    """The captured traffic of `kernel`, if its sources and `schedule` (the
-    bench's applied schedule dict) are those of the capture."""
+def measured_traffic(kernel: str, workload: str, mode: str, schedule, count_pass_ran: bool) -> Optional[float]:
+    """The captured traffic of `kernel`, if its sources, `schedule` (the bench's
+    applied schedule dict) and whether the count pass ran are those of the
+    capture."""
     if MEASURED_TRAFFIC.get("digest") != kernel_digest() or not isinstance(schedule, dict):
         return None
     entry = MEASURED_TRAFFIC.get(f"{kernel}:{workload}/{mode}")
     if entry is None:
         return None
-    value, sched = entry
-    return value if tuple(int(schedule.get(k, -1)) for k in SCHEDULE_KEYS) == sched else None
+    value, sched, ran = entry
+    same = tuple(int(schedule.get(k, -1)) for k in SCHEDULE_KEYS) == sched and bool(count_pass_ran) == ran
+    return value if same else None
 
 
 def parse():
@@ -431,7 +434,8 @@ def hbm_streaming_line(args, peaks, peak_src, dev, flush):
             "bound": "hbm", "kernel": "k_counts + k_score" if per_call == 3 else "k_score",
             "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
             "peak_source": f"{peak_src} HBM copy bandwidth", "algorithmic_bytes": algo, "ms": score_ms,
-            "traffic": measured_traffic("k_score", f"batched_large_{p.n_dags}", "cost_first", tuning["best"]),
+            "traffic": measured_traffic("k_score", f"batched_large_{p.n_dags}", "cost_first", tuning["best"],
+                                        per_call == 3),
             "bytes_note": "4 B per padded table entry (16-bit latency rank + 16-bit objective rank) of each "
                           "op with invocations, read once, plus 40 B per invocation"},
         "scan_12B_per_config": {"gbs": per12, "frac": per12 / hbm,
@@ -962,6 +966,9 @@ def main():
     p, inv = make_workload(args.workload, rank, args.n_dags, args.n_inv)
     mode = L.MODE_ALPHA if args.mode == "alpha" else L.MODE_COST_FIRST
     method = L.METHOD_STAIRCASE if args.method == "staircase" else L.METHOD_SCAN
+    # the floor of the bucketing kernel's counting: its count atomics alone, on
+    # the fresh context before anything else runs
+    count_floor = L.llama_count_rate(local, inv.n, p.n_ops) if args.method == "scan" else None
     torch.cuda.synchronize()
     t_set = time.perf_counter()
     sched = L.Scheduler(p, mode=mode, alpha=(3, 2), device=local, use_graph=not args.no_graph, method=method)
@@ -1149,7 +1156,7 @@ def main():
         s_ach = s_bytes / (kms["score"] / 1e3) / 1e9
         rooflines["k_stair"] = {
             "bound": "hbm", "kernel": "k_stair", "achieved": s_ach, "peak": hbm, "unit": "GB/s",
-            "frac": s_ach / hbm, "traffic": measured_traffic("k_stair", args.workload, args.mode, applied),
+            "frac": s_ach / hbm, "traffic": measured_traffic("k_stair", args.workload, args.mode, applied, False),
             "peak_source": f"{peak_src} HBM copy bandwidth", "algorithmic_bytes": s_bytes,
             "bytes_note": "16 B in and 24 B out per invocation"}
         c_bytes = 16 * p.n_ops
@@ -1165,7 +1172,7 @@ def main():
         achieved = algo_bytes / (kms["score"] / 1e3) / 1e9
         rooflines["k_score"] = {
             "bound": "hbm", "kernel": "k_score", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": measured_traffic("k_score", args.workload, args.mode, applied),
+            "frac": achieved / hbm, "traffic": measured_traffic("k_score", args.workload, args.mode, applied, count_pass),
             "peak_source": f"{peak_src} HBM copy bandwidth", "algorithmic_bytes": algo_bytes,
             "bytes_note": f"{tbl_per_entry} B per padded table entry of each op with invocations "
                           "(latency rank + objective rank(s)), once, plus 40 B per invocation",
@@ -1180,7 +1187,7 @@ def main():
         rooflines["k_score"] = {
             "bound": "alu", "kernel": "k_score", "achieved": achieved, "peak": peak_tops,
             "unit": "T ALU-ops/s", "frac": achieved / peak_tops,
-            "traffic": measured_traffic("k_score", args.workload, args.mode, applied),
+            "traffic": measured_traffic("k_score", args.workload, args.mode, applied, count_pass),
             "peak_source": "measured: llama_alu_peak, the scan's per-two-configuration instruction mix "
                            "(packed subtract, LOP3, 16-bit min" + (", PRMT" if args.mode == "alpha" else "")
                            + ") from registers on every SM",
@@ -1193,10 +1200,17 @@ def main():
         b_ach = b_bytes / (kms["bucket"] / 1e3) / 1e9
         rooflines["k_bucket"] = {
             "bound": "hbm", "kernel": "k_bucket", "achieved": b_ach, "peak": hbm, "unit": "GB/s",
-            "frac": b_ach / hbm, "traffic": measured_traffic("k_bucket", args.workload, args.mode, applied),
+            "frac": b_ach / hbm, "traffic": measured_traffic("k_bucket", args.workload, args.mode, applied, count_pass),
             "peak_source": f"{peak_src} HBM copy bandwidth", "algorithmic_bytes": b_bytes,
             "bytes_note": "16 B in and 8 B of bucket entry (index, remaining time) out per invocation; "
-                          "time includes its launch (trace events around it)"}
+                          "time includes its launch (trace events around it)",
+            "count_atomics": {
+                "us": count_floor[0], "stream_us": count_floor[1], "n": inv.n, "counters": p.n_ops,
+                "share_of_kernel": count_floor[0] / (1e3 * kms["bucket"]),
+                "note": "llama_count_rate, on the fresh context before the workload runs: the kernel's "
+                        "counting pattern alone (one returning atomic per invocation on per-op counters a "
+                        "128-byte line apart, four in flight per thread, four blocks per SM), as a kernel of "
+                        "its own; stream_us: the same loads and stores without the atomics"}}
         dominant = max(rooflines, key=lambda k: kms["score" if k == "k_score" else "bucket"])
         roofline = rooflines[dominant]
     value = job_throughput(world, inv.n, args.steps, total_s)

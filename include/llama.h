@@ -449,6 +449,18 @@ int llama_last_launch_count(llama_ctx *ctx);
  * 16-byte buffer for the duration of the call.  Errors: EINVAL, ECUDA. */
 int llama_alu_peak(int32_t device, int32_t mode, double *scores_per_s);
 
+/* Measured floor of the bucketing step's per-op counting (no counterpart in the
+ * paper; reported beside the bucketing kernel's roofline): n operation indices
+ * spread by a hash over n_counters counters one 128-byte line apart, loaded
+ * coalesced, counted with returning atomic adds, four in flight per thread, on
+ * as many blocks as the bucketing kernel runs (four per SM), every rank stored
+ * -- the counting pattern of the bucketing kernel, alone.  *atomic_us receives
+ * the best time of that kernel, *stream_us the best time of the same loads and
+ * stores without the atomics (10 timed launches each, after warm-up ones).
+ * Allocates 8 * n + 128 * n_counters bytes for the duration of the call.
+ * n in 1..LLAMA_MAX_INV, n_counters >= 1.  Errors: EINVAL, ECUDA. */
+int llama_count_rate(int32_t device, int64_t n, int32_t n_counters, double *atomic_us, double *stream_us);
+
 /* One-line description of the last error on ctx (never NULL). */
 const char *llama_last_error(llama_ctx *ctx);
 

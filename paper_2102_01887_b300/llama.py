@@ -45,7 +45,7 @@ EXPORTS = ("llama_create", "llama_destroy", "llama_set_dags", "llama_set_profile
            "llama_server_create", "llama_server_destroy", "llama_server_submit", "llama_server_poll",
            "llama_server_drain", "llama_server_stats_get", "llama_queue_time", "llama_feedback",
            "llama_get_profiles", "llama_backend_objectives", "llama_commit_order",
-           "llama_static_status", "llama_set_wait_limit", "llama_alu_peak", "llama_set_stats_file",
+           "llama_static_status", "llama_set_wait_limit", "llama_alu_peak", "llama_count_rate", "llama_set_stats_file",
            "llama_check_build", "llama_check_word",
            "llama_loop_create", "llama_loop_destroy", "llama_loop_submit", "llama_loop_tick", "llama_loop_poll",
            "llama_loop_sync", "llama_loop_state_get", "llama_loop_refresh", "llama_loop_ticks_done",
@@ -160,6 +160,8 @@ def load(path: str = None) -> ctypes.CDLL:
             "llama_static_status": ([vp, vp, vp, vp], ctypes.c_int),
             "llama_set_wait_limit": ([vp, i32], ctypes.c_int),
             "llama_alu_peak": ([i32, i32, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+            "llama_count_rate": ([i32, i64, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+                                 ctypes.c_int),
             "llama_set_stats_file": ([vp, ctypes.c_char_p], ctypes.c_int),
             "llama_check_build": ([], ctypes.c_int),
             "llama_check_word": ([vp, vp, i32], ctypes.c_int),
@@ -529,6 +531,17 @@ def llama_set_stats_file(ctx, path) -> None:
 def llama_set_wait_limit(ctx, tries: int) -> None:
     """Polls of a bucketing grid barrier before it gives up (WAIT_LIMIT_DEFAULT; 0 gives up at once)."""
     _check(ctx, load().llama_set_wait_limit(ctx, int(tries)))
+
+
+def llama_count_rate(device: int, n: int, n_counters: int) -> tuple:
+    """(atomic_us, stream_us): the best time of n returning count atomics on
+    n_counters counters (the bucketing kernel's counting pattern, alone) and of
+    the same loads and stores without them."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    rc = load().llama_count_rate(int(device), int(n), int(n_counters), ctypes.byref(a), ctypes.byref(b))
+    if rc != OK:
+        raise LlamaError(rc, "llama_count_rate failed")
+    return a.value, b.value
 
 
 def llama_alu_peak(device: int = 0, mode: int = MODE_COST_FIRST) -> float:

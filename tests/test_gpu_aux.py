@@ -64,3 +64,23 @@ def test_nvtx_ranges_are_compiled_in():
     for name in (b"llama:schedule\0", b"llama:schedule_async\0", b"llama:set_profiles\0", b"llama:feedback\0",
                  b"llama:loop_tick\0"):
         assert name in text, name
+
+
+@pytest.mark.gpu
+def test_measured_ceilings_run_and_are_plausible(cuda_device):
+    """The micro-benchmarks behind the bench line's denominators: the scan's
+    instruction mix runs below one configuration per integer ALU lane per clock
+    on every SM, and the bucketing kernel's count atomics alone take longer than
+    the same loads and stores without them."""
+    import torch
+    from paper_2102_01887_b300 import build, llama as L
+    build.build()
+    sms = torch.cuda.get_device_properties(cuda_device).multi_processor_count
+    lane_rate = sms * 64 * 2.2e9  # integer ALU lanes x a clock above the maximum
+    for mode in (L.MODE_COST_FIRST, L.MODE_ALPHA):
+        sps = L.llama_alu_peak(cuda_device, mode)
+        assert 0.1 * lane_rate < sps < lane_rate, (mode, sps)
+    atomic_us, stream_us = L.llama_count_rate(cuda_device, 1 << 20, 8368)
+    assert 0 < stream_us < atomic_us < 1e4, (atomic_us, stream_us)
+    with pytest.raises(L.LlamaError):
+        L.llama_count_rate(cuda_device, 0, 8368)
