@@ -189,6 +189,35 @@ def test_invalid_invocations_mixed_with_valid(L, method):
     assert d["cfg"].tolist() == [5, -1, -1, -1, -1, -1]
 
 
+def _with_invalid(inv, every: int):
+    """inv with every `every`-th invocation made invalid, by turns: no such DAG,
+    an op index past its DAG, a start after now."""
+    dag, opl, st = inv.dag.copy(), inv.op_local.copy(), inv.start_us.copy()
+    idx = np.arange(0, inv.n, every)
+    kind = (idx // every) % 3
+    dag[idx[kind == 0]] = -1
+    opl[idx[kind == 1]] = 10_000
+    st[idx[kind == 2]] = inv.now_us + 1
+    return W.Invocations(dag, opl, st, inv.now_us)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("shape", ["medium_600k", "batched"])
+def test_invalid_invocations_in_every_counting_round(L, shape):
+    """Enough invocations that every counting thread of the bucketing kernel
+    takes rounds beyond the ones it keeps in registers -- on the one-barrier
+    layout (medium: at most 1,024 ops) and the three-barrier one (batched) --
+    with invalid invocations spread over all of them: every decision equal to
+    the oracle's, the invalid ones flagged, the call's status EINVAL."""
+    p, inv = W.medium(n_inv=600_000) if shape == "medium_600k" else W.batched()
+    bad = _with_invalid(inv, 37)
+    got, exp = run_both(L, p, bad)
+    assert_same(got, exp)
+    n_bad = len(range(0, inv.n, 37))
+    assert int((got["flags"] & L.FLAG_INVALID != 0).sum()) == n_bad
+    assert (got["cfg"][::37] == -1).all()
+
+
 def test_all_targets_passed(L, method):
     p, inv = W.medium()
     late = W.Invocations(inv.dag, inv.op_local, np.zeros(inv.n, np.int64), inv.now_us)
