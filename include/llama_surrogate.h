@@ -88,6 +88,18 @@ int llama_mlp_gradients(llama_mlp *net, const void *x, const float *t, int64_t n
 int llama_mlp_train_step(llama_mlp *net, const void *x, const float *t, int64_t n, float w_fan, float lr,
                          float *loss, void *stream);
 
+/* An epoch of Adam steps without a host round trip per step: for b <
+ * n_batches, the rows perm[b*batch .. (b+1)*batch) of x (BF16 [n_rows x 64],
+ * device, 16-byte aligned) and t (FP32 [n_rows x 2], device) are gathered on
+ * the device into the network's own batch buffers, then llama_mlp_train_step's
+ * step is taken on them.  batch: a multiple of 128, at most max_batch; perm
+ * (int32 [n_batches*batch], device): row indices, an index outside
+ * 0..n_rows-1 giving a zero row.  The batches' losses (each before its step)
+ * are added to *loss_sum (device) unless NULL.  The result equals the same
+ * batches taken one llama_mlp_train_step at a time.  Errors: EINVAL, ECUDA. */
+int llama_mlp_train_epoch(llama_mlp *net, const void *x, const float *t, int64_t n_rows, const int32_t *perm,
+                          int64_t n_batches, int64_t batch, float w_fan, float lr, float *loss_sum, void *stream);
+
 /* One-line description of the network's last failure. */
 const char *llama_mlp_last_error(llama_mlp *net);
 

@@ -110,7 +110,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ int issued, consumed, failed;
     const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN, nk = K / kBK;
+    // split K (gridDim.z > 1): CTA z takes K blocks [z * nk, (z + 1) * nk) and
+    // writes its FP32 partial product to slice z of c32 (M x ldc each)
+    const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN, nk = K / kBK / (int)gridDim.z;
+    const int kb0 = (int)blockIdx.z * nk;
+    if (c32) c32 += (int64_t)blockIdx.z * M * ldc;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(smem_u32(&full[s]), 1);
@@ -141,8 +145,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             const uint32_t a = base + s * STAGE, b = a + A_BYTES, bar = smem_u32(&full[s]);
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(STAGE) : "memory");
-            tma_load_2d(a, &tmA, kb * kBK, m0, bar);
-            tma_load_2d(b, &tmB, kb * kBK, n0, bar);
+            tma_load_2d(a, &tmA, (kb0 + kb) * kBK, m0, bar);
+            tma_load_2d(b, &tmB, (kb0 + kb) * kBK, n0, bar);
         }
         issued = kb;
     } else if (warp == 1 && lane == 0) {
@@ -681,7 +685,7 @@ int make_store_map(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols
 
 template <int BN>
 cudaError_t launch_gemm(const CUtensorMap &ta, const CUtensorMap &tb, int64_t M, int N, int K, const float *bias,
-                        int flags, void *c16, float *c32, int ldc, int *err, cudaStream_t s) {
+                        int flags, void *c16, float *c32, int ldc, int *err, cudaStream_t s, int splits = 1) {
     constexpr int smem = kStages * (kBM + BN) * kBK * 2 + 1024;
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
@@ -689,7 +693,7 @@ cudaError_t launch_gemm(const CUtensorMap &ta, const CUtensorMap &tb, int64_t M,
         attr = cudaFuncSetAttribute(k_gemm_bf16<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     });
     if (attr != cudaSuccess) return attr;
-    const dim3 grid((unsigned)((M + kBM - 1) / kBM), (unsigned)(N / BN));
+    const dim3 grid((unsigned)((M + kBM - 1) / kBM), (unsigned)(N / BN), (unsigned)splits);
     k_gemm_bf16<BN><<<grid, kThreads, smem, s>>>(ta, tb, (int)M, N, K, bias, flags,
                                                   static_cast<__nv_bfloat16 *>(c16), c32, ldc, err);
     return cudaGetLastError();
@@ -715,7 +719,12 @@ int gemm(const void *a, const void *b, const float *bias, void *c16, float *c32,
     if ((reinterpret_cast<uintptr_t>(c16) | reinterpret_cast<uintptr_t>(c32)) & 15) return LLAMA_EINVAL;
     int *err = error_word();
     if (!err) return LLAMA_ENOMEM;
-    const int bn = n == 64 ? 64 : n % 256 == 0 ? 256 : 128;
+    // 256 columns per tile, unless that leaves SMs without a tile: then 128
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return LLAMA_ECUDA;
+    const int64_t row_tiles = (m + kBM - 1) / kBM;
+    const int bn = n == 64 ? 64 : n % 256 == 0 && row_tiles * (n / 256) >= sms ? 256 : 128;
     CUtensorMap ta, tb;
     if (make_map(&ta, a, m, k, kBM) != LLAMA_OK || make_map(&tb, b, n, k, bn) != LLAMA_OK) return LLAMA_EINVAL;
     cudaError_t e;
@@ -723,6 +732,71 @@ int gemm(const void *a, const void *b, const float *bias, void *c16, float *c32,
     else if (bn == 128) e = launch_gemm<128>(ta, tb, m, n, k, bias, flags, c16, c32, n, err, s);
     else e = launch_gemm<256>(ta, tb, m, n, k, bias, flags, c16, c32, n, err, s);
     return e == cudaSuccess ? LLAMA_OK : LLAMA_ECUDA;
+}
+
+namespace {
+
+__device__ __forceinline__ void add4(float4 &a, const float4 &v) {
+    a.x += v.x;
+    a.y += v.y;
+    a.z += v.z;
+    a.w += v.w;
+}
+
+// c[i] = sum over z < splits of part[z * count + i], added in order of z;
+// eight partials' loads in flight at a time.
+__global__ void k_sum_splits(const float4 *__restrict__ part, int64_t count4, int splits, float4 *__restrict__ c) {
+    constexpr int kBatch = 8;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count4;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float4 acc = part[i];
+        int z = 1;
+        for (; z + kBatch <= splits; z += kBatch) {
+            float4 v[kBatch];
+#pragma unroll
+            for (int j = 0; j < kBatch; ++j) v[j] = part[(z + j) * count4 + i];
+#pragma unroll
+            for (int j = 0; j < kBatch; ++j) add4(acc, v[j]);
+        }
+        for (; z < splits; ++z) add4(acc, part[z * count4 + i]);
+        c[i] = acc;
+    }
+}
+
+}  // namespace
+
+int splits_for(int64_t m, int n, int k, int sms) {
+    const int64_t tiles = ((m + kBM - 1) / kBM) * (n == 64 ? 1 : n / 128);
+    int splits = 1;
+    // double the splits while the grid stays within one CTA per SM and every
+    // split keeps at least kMinSplitBlocks K blocks
+    while (tiles * splits * 2 <= sms && (k / kBK) % (splits * 2) == 0 && k / kBK / (splits * 2) >= kMinSplitBlocks)
+        splits *= 2;
+    return splits;
+}
+
+int gemm_split_k(const void *a, const void *b, float *c32, int64_t m, int n, int k, int splits, float *part,
+                 size_t part_bytes, cudaStream_t s) {
+    if (!a || !b || !c32 || !part || splits < 1) return LLAMA_EINVAL;
+    if (m < 1 || m > (1 << 30) || k < kBK || k % kBK || k > (1 << 24)) return LLAMA_EINVAL;
+    if (n != 64 && n % 128) return LLAMA_EINVAL;
+    if ((k / kBK) % splits || (size_t)splits * (size_t)m * (size_t)n * sizeof(float) > part_bytes) return LLAMA_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b) | reinterpret_cast<uintptr_t>(c32) |
+         reinterpret_cast<uintptr_t>(part)) & 15)
+        return LLAMA_EINVAL;
+    if (splits == 1) return gemm(a, b, nullptr, nullptr, c32, m, n, k, 0, s);
+    int *err = error_word();
+    if (!err) return LLAMA_ENOMEM;
+    const int bn = n == 64 ? 64 : 128;
+    CUtensorMap ta, tb;
+    if (make_map(&ta, a, m, k, kBM) != LLAMA_OK || make_map(&tb, b, n, k, bn) != LLAMA_OK) return LLAMA_EINVAL;
+    const cudaError_t e = bn == 64 ? launch_gemm<64>(ta, tb, m, n, k, nullptr, 0, nullptr, part, n, err, s, splits)
+                                   : launch_gemm<128>(ta, tb, m, n, k, nullptr, 0, nullptr, part, n, err, s, splits);
+    if (e != cudaSuccess) return LLAMA_ECUDA;
+    const int64_t count4 = m * n / 4;  // n is a multiple of 64
+    k_sum_splits<<<(unsigned)std::min<int64_t>((count4 + 255) / 256, 1024), 256, 0, s>>>(
+        reinterpret_cast<const float4 *>(part), count4, splits, reinterpret_cast<float4 *>(c32));
+    return cudaGetLastError() == cudaSuccess ? LLAMA_OK : LLAMA_ECUDA;
 }
 
 // The persistent pair layer (see k_mlp_layer) over m rows: a, BF16 with 256

@@ -23,6 +23,16 @@ struct SelectArgs {
 // C = A . B^T on the tensor cores; see llama_gemm_bf16 for shapes and limits.
 int gemm(const void *a, const void *b, const float *bias, void *c16, float *c32, int64_t m, int n, int k,
          int flags, cudaStream_t s);
+// The same product into FP32 c32 [m x n] (no bias, no activation) with K split
+// over `splits` CTAs per output tile (a power of two dividing k / 64): each
+// writes its partial product to part (splits * m * n floats, at most part_bytes),
+// then one pass sums the partials in a fixed order, so the result does not
+// depend on scheduling.  For products with few output tiles and a long K
+// (weight gradients: K = the batch).
+constexpr int kMinSplitBlocks = 4;  // K blocks of 64 per split at least
+int splits_for(int64_t m, int n, int k, int sms);
+int gemm_split_k(const void *a, const void *b, float *c32, int64_t m, int n, int k, int splits, float *part,
+                 size_t part_bytes, cudaStream_t s);
 struct llama_mlp_view {
     const float *params;       // FP32 master parameters (flat layout above)
     const void *w16[4];        // BF16 W1..W4 [out x in]

@@ -75,10 +75,8 @@ __global__ void k_loss_grad(const float *__restrict__ y, const float *__restrict
         l = 0.5f * (e0 * e0 + w_fan * e1 * e1) * inv;
         g0 = e0 * inv;
         g1 = w_fan * e1 * inv;
-        bf16 *row = dy + r * kOut;
-        row[0] = __float2bfloat16(g0);
-        row[1] = __float2bfloat16(g1);
-        for (int c = 2; c < kOut; ++c) row[c] = __float2bfloat16(0.f);
+        // columns 2..kOut-1 of dy stay zero (cleared when the network is created)
+        *reinterpret_cast<__nv_bfloat162 *>(dy + r * kOut) = __floats2bfloat162_rn(g0, g1);
     }
     for (int o = 16; o > 0; o >>= 1) {
         l += __shfl_xor_sync(0xffffffffu, l, o);
@@ -134,17 +132,36 @@ __global__ void k_relu_back(const float *__restrict__ dh, const bf16 *__restrict
     }
 }
 
-// Adam (Kingma and Ba, 2015), bias-corrected, over the flat FP32 parameters.
-__global__ void k_adam(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m,
-                       float *__restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float c1,
-                       float c2) {
+// Where the BF16 copies of the four weight matrices go (W_l and W_l^T).
+struct PackTargets {
+    bf16 *wb[4], *wt[4];
+};
+
+// Adam (Kingma and Ba, 2015), bias-corrected, over the flat FP32 parameters;
+// for an element of a weight matrix, its BF16 copies in W and W^T (what k_pack
+// writes) in the same pass.
+__global__ void k_adam_pack(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m,
+                            float *__restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float c1,
+                            float c2, PackTargets pk) {
+    const int64_t off[4] = {kOffW1, kOffW2, kOffW3, kOffW4};
+    const int rows[4] = {kHid, kHid, kHid, kOut}, cols[4] = {kIn, kHid, kHid, kHid};
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const float gi = g[i];
         const float mi = b1 * m[i] + (1.f - b1) * gi;
         const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
         m[i] = mi;
         v[i] = vi;
-        w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        w[i] = wi;
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            const int64_t j = i - off[l];
+            if (j >= 0 && j < (int64_t)rows[l] * cols[l]) {
+                const bf16 b = __float2bfloat16(wi);
+                pk.wb[l][j] = b;
+                pk.wt[l][(j % cols[l]) * rows[l] + j / cols[l]] = b;
+            }
+        }
     }
 }
 
@@ -167,6 +184,23 @@ __global__ void k_take2(const float *__restrict__ y, int64_t n, float *__restric
     }
 }
 
+// Rows idx[r] of x (BF16, kIn per row) and t (FP32, 2 per row) into rows r of
+// xb and tb, r < n; an index outside 0..n_rows-1 gives a zero row.
+__global__ void k_gather_rows(const uint4 *__restrict__ x, const float2 *__restrict__ t, int64_t n_rows,
+                              const int32_t *__restrict__ idx, int64_t n, uint4 *__restrict__ xb,
+                              float2 *__restrict__ tb) {
+    constexpr int kChunks = kIn * 2 / 16;  // 16-byte chunks per input row
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n * kChunks;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = q / kChunks;
+        const int c = (int)(q - r * kChunks);
+        const int64_t src = idx[r];
+        const bool in = src >= 0 && src < n_rows;
+        xb[q] = in ? x[src * kChunks + c] : make_uint4(0, 0, 0, 0);
+        if (c == 0) tb[r] = in ? t[src] : make_float2(0.f, 0.f);
+    }
+}
+
 }  // namespace
 
 struct llama_mlp {
@@ -178,12 +212,26 @@ struct llama_mlp {
     Buf wb[4], wt[4];     // BF16 W_l and W_l^T
     Buf h1, h2, h3, y;    // activations (BF16) and outputs (FP32, 64 per row)
     Buf h0t, h1t, h2t, h3t, dy, dyt, dh, dz, dzt;
+    Buf part;             // FP32 partial products of the split-K weight gradients
+    Buf xb, tb;           // one gathered mini-batch of inputs (BF16) and targets (FP32)
+    int sms = 0;          // SMs of the device (sets the split of the weight gradients)
     std::string err;
 };
 
 namespace {
 
 const int kRows[4] = {kHid, kHid, kHid, kOut}, kCols[4] = {kIn, kHid, kHid, kHid};
+// the split-K partials of one weight gradient: up to 64 splits of a 256 x 256 product
+constexpr size_t kPartBytes = 64 * sizeof(float) * kHid * kHid;
+
+// dW = dz^T h (FP32 [rows x cols] into g), K = the batch: with so few output
+// tiles the product is split over K (deterministic partial sums).
+int weight_gradient(llama_mlp *m, const void *dzt, const void *ht, float *g, int rows, int cols, int64_t n,
+                    cudaStream_t s) {
+    int splits = splits_for(rows, cols, (int)n, m->sms);
+    while (splits > 1 && (size_t)splits * rows * cols * sizeof(float) > kPartBytes) splits /= 2;
+    return gemm_split_k(dzt, ht, g, rows, cols, (int)n, splits, m->part.as<float>(), kPartBytes, s);
+}
 const int64_t kOffW[4] = {kOffW1, kOffW2, kOffW3, kOffW4}, kOffB[4] = {kOffB1, kOffB2, kOffB3, kOffB4};
 
 struct Guard {
@@ -256,7 +304,7 @@ int backward(llama_mlp *m, const void *x, const float *t, int64_t n, float w_fan
     transpose(m->h3.as<bf16>(), m->h3t.as<bf16>(), n, kHid, s);
     MLP_CUDA(m, cudaGetLastError());
     // layer 4 (linear): dW4 = dy^T h3, dh3 = dy W4
-    MLP_RC(gemm(m->dyt.p, m->h3t.p, nullptr, nullptr, g + kOffW4, kOut, kHid, (int)n, 0, s));
+    MLP_RC(weight_gradient(m, m->dyt.p, m->h3t.p, g + kOffW4, kOut, kHid, n, s));
     MLP_RC(gemm(m->dy.p, m->wt[3].p, nullptr, nullptr, m->dh.as<float>(), n, kHid, kOut, 0, s));
     const bf16 *hs[3] = {m->h1.as<bf16>(), m->h2.as<bf16>(), m->h3.as<bf16>()};
     const void *hts[4] = {m->h0t.p, m->h1t.p, m->h2t.p, m->h3t.p};
@@ -266,9 +314,24 @@ int backward(llama_mlp *m, const void *x, const float *t, int64_t n, float w_fan
         k_relu_back<<<rgrid, dim3(32, 8), 0, s>>>(m->dh.as<float>(), hs[l], n, m->dz.as<bf16>(),
                                                  m->dzt.as<bf16>(), g + kOffB[l]);
         MLP_CUDA(m, cudaGetLastError());
-        MLP_RC(gemm(m->dzt.p, hts[l], nullptr, nullptr, g + kOffW[l], kHid, kCols[l], (int)n, 0, s));
+        MLP_RC(weight_gradient(m, m->dzt.p, hts[l], g + kOffW[l], kHid, kCols[l], n, s));
         if (l > 0) MLP_RC(gemm(m->dz.p, m->wt[l].p, nullptr, nullptr, m->dh.as<float>(), n, kHid, kHid, 0, s));
     }
+    return LLAMA_OK;
+}
+
+// One Adam step (bias-corrected) on m->g at learning rate lr, with the BF16
+// copies of the weights written in the same pass.
+int adam_step(llama_mlp *m, float lr, cudaStream_t s) {
+    const int64_t step = ++m->steps;
+    ++m->version;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - (float)std::pow((double)b1, (double)step), c2 = 1.f - (float)std::pow((double)b2, (double)step);
+    PackTargets pk;
+    for (int l = 0; l < 4; ++l) pk.wb[l] = m->wb[l].as<bf16>(), pk.wt[l] = m->wt[l].as<bf16>();
+    k_adam_pack<<<592, 256, 0, s>>>(m->w.as<float>(), m->g.as<float>(), m->m.as<float>(), m->v.as<float>(),
+                                    kParams, lr, b1, b2, 1e-8f, c1, c2, pk);
+    MLP_CUDA(m, cudaGetLastError());
     return LLAMA_OK;
 }
 
@@ -299,6 +362,10 @@ extern "C" int llama_mlp_create(llama_mlp **out, int32_t device, int64_t max_bat
     A(m->h0t, 2 * c * kIn), A(m->h1t, 2 * c * kHid), A(m->h2t, 2 * c * kHid), A(m->h3t, 2 * c * kHid);
     A(m->dy, 2 * c * kOut), A(m->dyt, 2 * c * kOut), A(m->dh, 4 * c * kHid), A(m->dz, 2 * c * kHid);
     A(m->dzt, 2 * c * kHid);
+    A(m->part, kPartBytes);
+    A(m->xb, 2 * c * kIn), A(m->tb, 4 * c * 2);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&m->sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaMemset(m->dy.p, 0, 2 * c * kOut);  // the loss writes columns 0 and 1 only
     if (e == cudaSuccess) e = cudaMemset(m->w.p, 0, 4 * kParams);
     if (e == cudaSuccess) e = cudaMemset(m->m.p, 0, 4 * kParams);
     if (e == cudaSuccess) e = cudaMemset(m->v.p, 0, 4 * kParams);
@@ -379,14 +446,30 @@ extern "C" int llama_mlp_train_step(llama_mlp *m, const void *x, const float *t,
     if (loss) MLP_CUDA(m, cudaMemsetAsync(loss, 0, sizeof(float), s));
     MLP_RC(forward(m, x, n, s));
     MLP_RC(backward(m, x, t, n, w_fan, loss, s));
-    const int64_t step = ++m->steps;
-    ++m->version;
-    const float b1 = 0.9f, b2 = 0.999f;
-    const float c1 = 1.f - (float)std::pow((double)b1, (double)step), c2 = 1.f - (float)std::pow((double)b2, (double)step);
-    k_adam<<<592, 256, 0, s>>>(m->w.as<float>(), m->g.as<float>(), m->m.as<float>(), m->v.as<float>(), kParams,
-                               lr, b1, b2, 1e-8f, c1, c2);
-    MLP_CUDA(m, cudaGetLastError());
-    MLP_RC(pack_weights(m, s));
+    return adam_step(m, lr, s);
+}
+
+extern "C" int llama_mlp_train_epoch(llama_mlp *m, const void *x, const float *t, int64_t n_rows,
+                                     const int32_t *perm, int64_t n_batches, int64_t batch, float w_fan, float lr,
+                                     float *loss_sum, void *stream) {
+    if (!m) return LLAMA_EINVAL;
+    if (!x || !t || !perm || n_rows < 1 || n_batches < 0) return fail(m, LLAMA_EINVAL, "train_epoch: bad arguments");
+    if (batch < 128 || batch > m->cap || batch % 128) return fail(m, LLAMA_EINVAL, "train_epoch: bad batch size");
+    if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(t)) & 15)
+        return fail(m, LLAMA_EINVAL, "train_epoch: inputs not 16-byte aligned");
+    if (!(lr > 0.f) || lr > 1.f) return fail(m, LLAMA_EINVAL, "train_epoch: learning rate outside (0, 1]");
+    Guard gd(m->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t chunks = batch * (kIn * 2 / 16);
+    const unsigned grid = (unsigned)std::min<int64_t>((chunks + 255) / 256, 4096);
+    for (int64_t b = 0; b < n_batches; ++b) {
+        k_gather_rows<<<grid, 256, 0, s>>>(static_cast<const uint4 *>(x), reinterpret_cast<const float2 *>(t), n_rows,
+                                           perm + b * batch, batch, m->xb.as<uint4>(), m->tb.as<float2>());
+        MLP_CUDA(m, cudaGetLastError());
+        MLP_RC(forward(m, m->xb.p, batch, s));
+        MLP_RC(backward(m, m->xb.p, m->tb.as<float>(), batch, w_fan, loss_sum, s));
+        MLP_RC(adam_step(m, lr, s));
+    }
     return LLAMA_OK;
 }
 

@@ -38,7 +38,7 @@ EXPORTS = ("llama_create", "llama_destroy", "llama_set_dags", "llama_set_profile
            "llama_critical_path", "llama_slack", "llama_set_trace_events", "llama_last_launch_count",
            "llama_last_error", "llama_gemm_bf16", "llama_gemm_error",
            "llama_mlp_create", "llama_mlp_destroy", "llama_mlp_set_params", "llama_mlp_get_params",
-           "llama_mlp_forward", "llama_mlp_gradients", "llama_mlp_train_step", "llama_mlp_last_error",
+           "llama_mlp_forward", "llama_mlp_gradients", "llama_mlp_train_step", "llama_mlp_train_epoch", "llama_mlp_last_error",
            "llama_sg_create", "llama_sg_destroy", "llama_sg_schedule", "llama_sg_last_pairs",
            "llama_sg_predictions", "llama_sg_last_error", "llama_sg_set_margin", "llama_sg_invalidate",
            "llama_ws_create", "llama_ws_destroy", "llama_schedule_ws_async", "llama_ws_status", "llama_ws_set_inputs",
@@ -132,6 +132,8 @@ def load(path: str = None) -> ctypes.CDLL:
             "llama_mlp_forward": ([vp, vp, i64, vp, vp], ctypes.c_int),
             "llama_mlp_gradients": ([vp, vp, vp, i64, ctypes.c_float, vp, vp, vp], ctypes.c_int),
             "llama_mlp_train_step": ([vp, vp, vp, i64, ctypes.c_float, ctypes.c_float, vp, vp], ctypes.c_int),
+            "llama_mlp_train_epoch": ([vp, vp, vp, i64, vp, i64, i64, ctypes.c_float, ctypes.c_float, vp, vp],
+                                      ctypes.c_int),
             "llama_mlp_last_error": ([vp], ctypes.c_char_p),
             "llama_sg_create": ([ctypes.POINTER(vp), vp, vp, i64, i64], ctypes.c_int),
             "llama_sg_destroy": ([vp], None),
@@ -339,6 +341,15 @@ class MLP:
         p = lambda v: None if v is None else ctypes.c_void_p(v.data_ptr())
         self._check(load().llama_mlp_train_step(self.h, p(x), p(t), x.shape[0], float(w_fan), float(lr), p(loss),
                                                 _stream_ptr(stream)))
+
+    def train_epoch(self, x, t, perm, batch: int, w_fan: float, lr: float, loss_sum=None, stream=None) -> None:
+        """Adam steps over the batches perm[b*batch:(b+1)*batch] of x and t
+        (perm: int32 device tensor), gathered on the device."""
+        p = lambda v: None if v is None else ctypes.c_void_p(v.data_ptr())
+        assert perm.dtype.itemsize == 4 and perm.shape[0] % batch == 0
+        self._check(load().llama_mlp_train_epoch(self.h, p(x), p(t), x.shape[0], p(perm), perm.shape[0] // batch,
+                                                 int(batch), float(w_fan), float(lr), p(loss_sum),
+                                                 _stream_ptr(stream)))
 
     def close(self) -> None:
         if self.h:

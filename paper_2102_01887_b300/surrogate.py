@@ -7,6 +7,7 @@ profiler's samples (``workloads.surrogate_training_set``).
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 
 import numpy as np
@@ -47,17 +48,16 @@ def train(net, x, t, epochs: int, batch: int = 8192, lr: float = 1e-3, w_fan: fl
     import torch
     n = x.shape[0] // batch * batch
     g = torch.Generator(device="cpu").manual_seed(seed)
-    loss = torch.zeros(1, dtype=torch.float32, device=x.device)
     acc = torch.zeros(1, dtype=torch.float32, device=x.device)
     history = []
     for _ in range(epochs):
-        perm = torch.randperm(x.shape[0], generator=g)[:n].to(x.device)
-        acc.zero_()
-        for b in range(n // batch):
-            idx = perm[b * batch:(b + 1) * batch]
-            net.train_step(x[idx].contiguous(), t[idx].contiguous(), w_fan, lr, loss, stream)
-            acc += loss
-        history.append(float(acc.item()) / (n // batch))
+        # the permutation, the loss sum and the epoch on one stream
+        with torch.cuda.stream(stream) if stream is not None else contextlib.nullcontext():
+            perm = torch.randperm(x.shape[0], generator=g)[:n].to(device=x.device, dtype=torch.int32)
+            acc.zero_()
+            # every batch of the epoch in one library call: gathered on the device
+            net.train_epoch(x, t, perm, batch, w_fan, lr, acc, stream)
+            history.append(float(acc.item()) / (n // batch))
     return history
 
 

@@ -159,3 +159,48 @@ def test_training_reduces_the_loss(L, world):
     r2 = 1 - np.mean((pred[:, 0] - tv[:, 0]) ** 2) / np.var(tv[:, 0])
     assert r2 > 0.85, r2
     assert float(loss.item()) < 0.3 * first
+
+
+def test_train_epoch_equals_the_same_steps_one_at_a_time(L, world):
+    """llama_mlp_train_epoch (batches gathered on the device, no host round
+    trip per step) leaves the parameters equal to those of the same batches
+    taken one llama_mlp_train_step at a time, and sums the same batch losses;
+    an out-of-range index gives a zero row.  Equal up to the order of the
+    bias gradients' atomic sums: nearly every parameter to the last bits, and
+    none further apart than the steps' learning rate can move it."""
+    import torch
+    _, _, x, t = world
+    n_rows, batch, n_batches = 40_000, 1024, 6
+    xd, td = to_device_x(x[:n_rows]), torch.from_numpy(t[:n_rows]).cuda()
+    perm = torch.from_numpy(np.random.default_rng(5).permutation(n_rows)[:batch * n_batches].astype(np.int32)).cuda()
+    start = M.pack(perturbed_params(9)).astype(np.float32)
+    with L.MLP(max_batch=batch) as a, L.MLP(max_batch=batch) as b:
+        a.set_params(start)
+        b.set_params(start)
+        la = torch.zeros(1, dtype=torch.float32, device="cuda")
+        a.train_epoch(xd, td, perm, batch, 0.5, 1e-3, la)
+        lb, one = torch.zeros(1, dtype=torch.float32, device="cuda"), torch.zeros(1, dtype=torch.float32, device="cuda")
+        for k in range(n_batches):
+            idx = perm[k * batch:(k + 1) * batch].long()
+            b.train_step(xd[idx].contiguous(), td[idx].contiguous(), 0.5, 1e-3, one)
+            lb += one
+        def assert_close(pa, pb, steps):
+            d = np.abs(pa.astype(np.float64) - pb)
+            assert np.mean(d <= 1e-6 * np.abs(pb) + 1e-9) > 0.999, float(d.max())
+            assert d.max() <= 2 * 1e-3 * steps
+        assert_close(a.get_params(), b.get_params(), n_batches)
+        assert abs(float(la.item()) - float(lb.item())) <= 1e-5 * abs(float(lb.item()))
+        # a zero row for an index outside the rows: same as a batch with that row zeroed
+        bad = perm[:batch].clone()
+        bad[7] = n_rows + 3
+        a.set_params(start)
+        b.set_params(start)
+        a.train_epoch(xd, td, bad, batch, 0.5, 1e-3)
+        idx = bad.long().clamp(max=n_rows - 1)
+        xz, tz = xd[idx].contiguous(), td[idx].contiguous()
+        xz[7].zero_()
+        tz[7].zero_()
+        b.train_step(xz, tz, 0.5, 1e-3)
+        assert_close(a.get_params(), b.get_params(), 1)
+        with pytest.raises(L.LlamaError):
+            a.train_epoch(xd, td, perm[:2000], 1000, 0.5, 1e-3)  # not a multiple of 128
