@@ -44,22 +44,34 @@ struct Buf {
 
 using bf16 = __nv_bfloat16;
 
-// Transpose a row-major BF16 matrix [rows x cols] into [cols x rows] through
-// 32 x 32 shared-memory tiles (coalesced reads and writes).
+// dst [cols x rows] = src [rows x cols]^T (BF16; cols a multiple of 64), in
+// 64 x 64 tiles: pairs of elements loaded and stored as 4-byte words, so a
+// warp reads and writes 128 contiguous bytes.
+constexpr int kTT = 64;  // tile side of the transposes
 __global__ void k_transpose(const bf16 *__restrict__ src, bf16 *__restrict__ dst, int64_t rows, int cols) {
-    __shared__ bf16 tile[32][33];
-    const int64_t r0 = blockIdx.y * 32ll;
-    const int c0 = blockIdx.x * 32;
-    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    __shared__ bf16 tile[kTT][kTT + 2];
+    const int64_t r0 = blockIdx.y * (int64_t)kTT;
+    const int c0 = blockIdx.x * kTT, tx = threadIdx.x;
+    for (int j = threadIdx.y; j < kTT; j += blockDim.y) {
         const int64_t r = r0 + j;
-        const int c = c0 + threadIdx.x;
-        tile[j][threadIdx.x] = (r < rows && c < cols) ? src[r * cols + c] : __float2bfloat16(0.f);
+        const __nv_bfloat162 v = r < rows ? *reinterpret_cast<const __nv_bfloat162 *>(src + r * cols + c0 + 2 * tx)
+                                          : __floats2bfloat162_rn(0.f, 0.f);
+        tile[j][2 * tx] = v.x;
+        tile[j][2 * tx + 1] = v.y;
     }
     __syncthreads();
-    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
-        const int c = c0 + j;
-        const int64_t r = r0 + threadIdx.x;
-        if (c < cols && r < rows) dst[(int64_t)c * rows + r] = tile[threadIdx.x][j];
+    const int64_t r = r0 + 2 * tx;
+    for (int j = threadIdx.y; j < kTT; j += blockDim.y) {
+        bf16 *d = dst + (int64_t)(c0 + j) * rows + r;
+        if (r + 1 < rows) {
+            __nv_bfloat162 v;
+            v.x = tile[2 * tx][j];
+            v.y = tile[2 * tx + 1][j];
+            if ((rows & 1) == 0) *reinterpret_cast<__nv_bfloat162 *>(d) = v;  // 4-byte aligned
+            else d[0] = v.x, d[1] = v.y;
+        } else if (r < rows) {
+            d[0] = tile[2 * tx][j];
+        }
     }
 }
 
@@ -99,36 +111,54 @@ __global__ void k_loss_grad(const float *__restrict__ y, const float *__restrict
 }
 
 // Through a ReLU: dz = dh where the layer's output h was positive; dz is
-// written row-major and transposed (32 x 32 tiles), and its column sums
-// (the bias gradient) are accumulated.
+// written row-major and transposed, and its column sums (the bias gradient)
+// are accumulated.  64 x 64 tiles of the kHid columns, pairs of elements per
+// thread (8-byte loads of dh, 4-byte loads and stores of BF16).
 __global__ void k_relu_back(const float *__restrict__ dh, const bf16 *__restrict__ h, int64_t n,
                             bf16 *__restrict__ dz, bf16 *__restrict__ dzt, float *__restrict__ db) {
-    __shared__ bf16 tile[32][33];
-    __shared__ float colsum[32][33];
-    const int64_t r0 = blockIdx.y * 32ll;
-    const int c0 = blockIdx.x * 32;
-    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    __shared__ bf16 tile[kTT][kTT + 2];
+    __shared__ float colsum[8][kTT];
+    const int64_t r0 = blockIdx.y * (int64_t)kTT;
+    const int c0 = blockIdx.x * kTT, tx = threadIdx.x;
+    float s0 = 0.f, s1 = 0.f;
+    for (int j = threadIdx.y; j < kTT; j += blockDim.y) {
         const int64_t r = r0 + j;
-        const int c = c0 + threadIdx.x;
-        float v = 0.f;
+        float2 v = make_float2(0.f, 0.f);
         if (r < n) {
-            const int64_t o = r * kHid + c;
-            v = __bfloat162float(h[o]) > 0.f ? dh[o] : 0.f;
-            dz[o] = __float2bfloat16(v);
+            const int64_t o = r * kHid + c0 + 2 * tx;
+            const float2 d = *reinterpret_cast<const float2 *>(dh + o);
+            const __nv_bfloat162 hv = *reinterpret_cast<const __nv_bfloat162 *>(h + o);
+            v.x = __bfloat162float(hv.x) > 0.f ? d.x : 0.f;
+            v.y = __bfloat162float(hv.y) > 0.f ? d.y : 0.f;
+            *reinterpret_cast<__nv_bfloat162 *>(dz + o) = __floats2bfloat162_rn(v.x, v.y);
         }
-        tile[j][threadIdx.x] = __float2bfloat16(v);
-        colsum[j][threadIdx.x] = v;
+        tile[j][2 * tx] = __float2bfloat16(v.x);
+        tile[j][2 * tx + 1] = __float2bfloat16(v.y);
+        s0 += v.x;
+        s1 += v.y;
     }
+    colsum[threadIdx.y][2 * tx] = s0;
+    colsum[threadIdx.y][2 * tx + 1] = s1;
     __syncthreads();
-    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
-        const int c = c0 + j;
-        const int64_t r = r0 + threadIdx.x;
-        if (r < n) dzt[(int64_t)c * n + r] = tile[threadIdx.x][j];
+    const int64_t r = r0 + 2 * tx;
+    for (int j = threadIdx.y; j < kTT; j += blockDim.y) {
+        bf16 *d = dzt + (int64_t)(c0 + j) * n + r;
+        if (r + 1 < n) {
+            __nv_bfloat162 v;
+            v.x = tile[2 * tx][j];
+            v.y = tile[2 * tx + 1][j];
+            if ((n & 1) == 0) *reinterpret_cast<__nv_bfloat162 *>(d) = v;  // 4-byte aligned
+            else d[0] = v.x, d[1] = v.y;
+        } else if (r < n) {
+            d[0] = tile[2 * tx][j];
+        }
     }
     if (threadIdx.y == 0) {
-        float s = 0.f;
-        for (int j = 0; j < 32; ++j) s += colsum[j][threadIdx.x];
-        atomicAdd(db + c0 + threadIdx.x, s);
+        for (int q = 0; q < 2; ++q) {
+            float t = 0.f;
+            for (int k = 0; k < 8; ++k) t += colsum[k][2 * tx + q];
+            atomicAdd(db + c0 + 2 * tx + q, t);
+        }
     }
 }
 
@@ -277,7 +307,7 @@ int pack_weights(llama_mlp *m, cudaStream_t s) {
 }
 
 void transpose(const bf16 *src, bf16 *dst, int64_t rows, int cols, cudaStream_t s) {
-    const dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+    const dim3 grid((unsigned)(cols / kTT), (unsigned)((rows + kTT - 1) / kTT));  // cols: 64 or 256
     k_transpose<<<grid, dim3(32, 8), 0, s>>>(src, dst, rows, cols);
 }
 
@@ -308,7 +338,7 @@ int backward(llama_mlp *m, const void *x, const float *t, int64_t n, float w_fan
     MLP_RC(gemm(m->dy.p, m->wt[3].p, nullptr, nullptr, m->dh.as<float>(), n, kHid, kOut, 0, s));
     const bf16 *hs[3] = {m->h1.as<bf16>(), m->h2.as<bf16>(), m->h3.as<bf16>()};
     const void *hts[4] = {m->h0t.p, m->h1t.p, m->h2t.p, m->h3t.p};
-    const dim3 rgrid(kHid / 32, (unsigned)((n + 31) / 32));
+    const dim3 rgrid(kHid / kTT, (unsigned)((n + kTT - 1) / kTT));
     for (int l = 2; l >= 0; --l) {
         // through the ReLU of layer l+1, then dW = dz^T h_l and (below layer 1) dh_l = dz W
         k_relu_back<<<rgrid, dim3(32, 8), 0, s>>>(m->dh.as<float>(), hs[l], n, m->dz.as<bf16>(),
