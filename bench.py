@@ -1086,19 +1086,22 @@ def main():
             if kind == "huge_pages":
                 # two calls in flight (a workspace and a stream each), inputs read
                 # in place or copied by the copy engine
-                for name, mode, how in (("pipelined", L.WS_INPUTS_IN_PLACE, "read in place from"),
-                                        ("pipelined_copy", L.WS_INPUTS_COPY, "copied by the copy engine from")):
+                for name, mode, how, depth in (
+                        ("pipelined", L.WS_INPUTS_IN_PLACE, "read in place from", 2),
+                        ("pipelined_copy", L.WS_INPUTS_COPY, "copied by the copy engine from", 2),
+                        ("pipelined_copy_3", L.WS_INPUTS_COPY, "copied by the copy engine from", 3),
+                        ("pipelined_copy_4", L.WS_INPUTS_COPY, "copied by the copy engine from", 4)):
                     pw, pouts = e2e_pipelined(L, ctx, dev, inv, np_dag, np_opl, np_st, flush, args.steps,
-                                              args.warmup, inputs=mode)
+                                              args.warmup, depth=depth, inputs=mode)
                     assert all((o["cfg"] == got["cfg"]).all() for o in pouts)
                     pw = max_over_ranks(pw, world, dev)
                     variants[name] = {
                         "value": job_throughput(world, inv.n, args.steps, pw), "unit": UNIT,
                         "h2d_bytes_per_step": int(inv.n * (4 + 4 + 8)), "d2h_bytes_per_step": int(inv.n * 24),
                         "memory": "huge_pages",
-                        "transfer": f"two calls in flight on two streams (llama_schedule_ws_async, a workspace "
-                                    f"each): inputs {how} page-locked host memory, decisions copied back on "
-                                    f"the call's stream",
+                        "transfer": f"{depth} calls in flight on {depth} streams (llama_schedule_ws_async, a "
+                                    f"workspace each): inputs {how} page-locked host memory, decisions copied "
+                                    f"back on the call's stream",
                         "p50_call_us": 1e6 * pw / args.steps, "p99_call_us": None}
             for _ in range(args.warmup):
                 L.llama_schedule(ctx, np_dag, np_opl, np_st, inv.now_us, np_out)
