@@ -218,6 +218,20 @@ def test_invalid_invocations_in_every_counting_round(L, shape):
     assert (got["cfg"][::37] == -1).all()
 
 
+@pytest.mark.parametrize("q", [(0, 7000, 7000), (3000, 0, 3000), (5000, 5000, 5000), (0, 0, 9000)],
+                         ids=["last-two", "first-last", "all-equal", "first-two"])
+@pytest.mark.parametrize("shape", ["medium", "batched"])
+def test_backends_sharing_a_queueing_time(L, shape, q):
+    """Queueing times equal on some backends and not on others (equal ones give
+    an invocation equal slacks on those backends): every grouping of three
+    backends, on whole-CTA tiles (medium) and on warp tiles too (batched),
+    against the oracle."""
+    p, inv = W.medium(n_inv=20_000) if shape == "medium" else W.batched(n_inv=200_000)
+    p.q_us = np.asarray(q, np.int64)
+    got, exp = run_both(L, p, inv)
+    assert_same(got, exp)
+
+
 def test_all_targets_passed(L, method):
     p, inv = W.medium()
     late = W.Invocations(inv.dag, inv.op_local, np.zeros(inv.n, np.int64), inv.now_us)
