@@ -438,6 +438,26 @@ int llama_check_word(llama_ctx *ctx, uint32_t *bits, int32_t clear);
 /* Kernel launches issued by the last scheduling call (for accounting). */
 int llama_last_launch_count(llama_ctx *ctx);
 
+/* Stragglers and failures (Section 3.4, "Handling stragglers and invocation
+ * failures"; time-out of Section 5): which of n invocations, decided at now_us
+ * with decisions dec[i], get a duplicate invocation, and when the duplicate is
+ * handed back to slack allotment and configuration.  Invocation i ran for
+ * obs_us[i] >= 0 microseconds after now_us and then completed, or then
+ * reported an error (failed[i] != 0; failed may be NULL: no errors).  Its
+ * time-out is ceil(timeout_num * dec[i].lat / timeout_den) us (3/2 in the
+ * paper).  A duplicate is made when the error arrives no later than the
+ * time-out, or when the invocation is still running at the time-out; it is
+ * handed back at the first multiple of tick_us (the Manager's check period) at
+ * or after now_us + that moment.  Undecided invocations (cfg < 0) get none.
+ * Writes the duplicates' indices to dup_idx and their hand-back times to
+ * resubmit_us (each at most n long, host), their number to *n_dup.  Rescheduled
+ * with the invocation's own start time at the later now, a duplicate gets no
+ * more slack on any backend than the original (Algorithm 1: less of the target
+ * is left).  Host memory and host code only.  Errors: EINVAL. */
+int llama_stragglers(int64_t n, const llama_decision *dec, const int64_t *obs_us, const uint8_t *failed,
+                     int64_t now_us, int32_t timeout_num, int32_t timeout_den, int64_t tick_us,
+                     int64_t *dup_idx, int64_t *resubmit_us, int64_t *n_dup);
+
 /* Measured ceiling of the scan's inner loop (no counterpart in the paper; the
  * denominator of the scoring kernel's ALU roofline): the rate at which the
  * device issues the scan's instruction mix for two configurations -- one

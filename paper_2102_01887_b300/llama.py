@@ -45,7 +45,7 @@ EXPORTS = ("llama_create", "llama_destroy", "llama_set_dags", "llama_set_profile
            "llama_server_create", "llama_server_destroy", "llama_server_submit", "llama_server_poll",
            "llama_server_drain", "llama_server_stats_get", "llama_queue_time", "llama_feedback",
            "llama_get_profiles", "llama_backend_objectives", "llama_commit_order",
-           "llama_static_status", "llama_set_wait_limit", "llama_alu_peak", "llama_count_rate", "llama_set_stats_file",
+           "llama_static_status", "llama_set_wait_limit", "llama_alu_peak", "llama_count_rate", "llama_stragglers", "llama_set_stats_file",
            "llama_check_build", "llama_check_word",
            "llama_loop_create", "llama_loop_destroy", "llama_loop_submit", "llama_loop_tick", "llama_loop_poll",
            "llama_loop_sync", "llama_loop_state_get", "llama_loop_refresh", "llama_loop_ticks_done",
@@ -164,6 +164,7 @@ def load(path: str = None) -> ctypes.CDLL:
             "llama_alu_peak": ([i32, i32, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
             "llama_count_rate": ([i32, i64, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
                                  ctypes.c_int),
+            "llama_stragglers": ([i64, vp, vp, vp, i64, i32, i32, i64, vp, vp, ctypes.POINTER(i64)], ctypes.c_int),
             "llama_set_stats_file": ([vp, ctypes.c_char_p], ctypes.c_int),
             "llama_check_build": ([], ctypes.c_int),
             "llama_check_word": ([vp, vp, i32], ctypes.c_int),
@@ -542,6 +543,26 @@ def llama_set_stats_file(ctx, path) -> None:
 def llama_set_wait_limit(ctx, tries: int) -> None:
     """Polls of a bucketing grid barrier before it gives up (WAIT_LIMIT_DEFAULT; 0 gives up at once)."""
     _check(ctx, load().llama_set_wait_limit(ctx, int(tries)))
+
+
+def llama_stragglers(dec: np.ndarray, obs_us, failed, now_us: int, timeout=(3, 2), tick_us: int = 1) -> tuple:
+    """(indices, hand-back times) of the invocations that get a duplicate: an
+    error before the time-out or still running at it (timeout = num/den times
+    the decided latency), handed back at the first tick at or after the event."""
+    dec = np.ascontiguousarray(dec)
+    assert dec.dtype == DECISION_DTYPE
+    n = dec.shape[0]
+    obs = np.ascontiguousarray(obs_us, np.int64)
+    fl = None if failed is None else np.ascontiguousarray(failed, np.uint8)
+    idx = np.empty(max(n, 1), np.int64)
+    when = np.empty(max(n, 1), np.int64)
+    k = ctypes.c_int64()
+    rc = load().llama_stragglers(n, dec.ctypes.data, obs.ctypes.data, None if fl is None else fl.ctypes.data,
+                                 int(now_us), int(timeout[0]), int(timeout[1]), int(tick_us), idx.ctypes.data,
+                                 when.ctypes.data, ctypes.byref(k))
+    if rc != OK:
+        raise LlamaError(rc, "llama_stragglers failed")
+    return idx[:k.value].copy(), when[:k.value].copy()
 
 
 def llama_count_rate(device: int, n: int, n_counters: int) -> tuple:
