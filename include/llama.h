@@ -413,8 +413,12 @@ int llama_set_trace_events(llama_ctx *ctx, void *const *events, int32_t n_events
  * (opened for appending; NULL or "" closes it): the call's index, n_inv,
  * now_us, method, kernel launches, whether a CUDA graph was replayed, the
  * invalid count, whether a bounded wait gave up, the device time of its
- * kernels (events around them) and the host time of the whole call.  Errors:
- * EINVAL (the file cannot be opened), ECUDA. */
+ * kernels (events around them), the host time of the whole call, invocations
+ * per second of device time, and -- when the decisions are written to host
+ * memory -- how many were feasible (met their target) and, with the
+ * invocations in host memory too, how many configurations the decided ones
+ * scored and per second of device time (null otherwise).  Errors: EINVAL (the
+ * file cannot be opened), ECUDA. */
 int llama_set_stats_file(llama_ctx *ctx, const char *path);
 
 /* Checked build (no counterpart in the paper).  A library compiled with

@@ -1465,14 +1465,31 @@ extern "C" int llama_schedule(llama_ctx *c, int64_t n_inv, const int32_t *dag, c
         cudaEventElapsedTime(&dev_ms, c->stats_ev[0], c->stats_ev[1]);
         const double host_us =
             std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t_call).count();
+        // with the decisions (and the invocations) in host memory: how many met
+        // their target, and how many configurations the decided ones scored
+        char feas[32] = "null", scored[32] = "null", cps[32] = "null";
+        if (!outd) {
+            int64_t nf = 0;
+            for (int64_t i = 0; i < n_inv; ++i) nf += (out[i].flags & LLAMA_FLAG_FEASIBLE) != 0;
+            snprintf(feas, sizeof feas, "%lld", (long long)nf);
+            if (!is_device_ptr(dag) && !is_device_ptr(op_local)) {
+                int64_t nc = 0;
+                for (int64_t i = 0; i < n_inv; ++i)
+                    if (out[i].cfg >= 0) nc += c->h_ncfg[c->h_dag_op_off[dag[i]] + op_local[i]];
+                snprintf(scored, sizeof scored, "%lld", (long long)nc);
+                if (dev_ms > 0.f) snprintf(cps, sizeof cps, "%.6g", (double)nc / (1e-3 * dev_ms));
+            }
+        }
         fprintf(c->stats,
                 "{\"call\": %lld, \"n_inv\": %lld, \"now_us\": %lld, \"method\": \"%s\", \"launches\": %d, "
                 "\"graph\": %s, \"invalid\": %llu, \"timeout\": %s, \"device_us\": %.3f, \"host_us\": %.3f, "
-                "\"inputs\": \"%s\"}\n",
+                "\"inputs\": \"%s\", \"inv_per_s\": %.6g, \"feasible\": %s, \"configs_scored\": %s, "
+                "\"configs_per_s\": %s}\n",
                 (long long)c->stats_calls++, (long long)n_inv, (long long)now_us,
                 c->method == LLAMA_METHOD_STAIRCASE ? "staircase" : "scan", c->last_launches,
                 c->opts.use_graph && !c->tracing ? "true" : "false", c->h_ctrl[0], c->h_ctrl[1] ? "true" : "false",
-                1e3 * dev_ms, host_us, rd && ro && rs ? "read in place" : "copied");
+                1e3 * dev_ms, host_us, rd && ro && rs ? "read in place" : "copied",
+                dev_ms > 0.f ? (double)n_inv / (1e-3 * dev_ms) : 0.0, feas, scored, cps);
         fflush(c->stats);
     }
     if (c->h_ctrl[1])

@@ -35,6 +35,15 @@ def test_stats_file_records_every_blocking_call(cuda_device, tmp_path):
                for r in rows)
     assert [r["invalid"] for r in rows] == [0, int((bad.dag < 0).sum()), 0]
     assert not any(r["timeout"] for r in rows) and rows[0]["graph"] is True
+    # what the decisions say, counted on the host: feasible ones, configurations scored
+    with L.Scheduler(p, use_graph=True) as s:
+        d, _ = s.schedule(inv)
+    ncfg = np.diff(p.cfg_off)[p.dag_op_off[inv.dag] + inv.op_local]
+    assert rows[0]["feasible"] == int((d["flags"] & L.FLAG_FEASIBLE != 0).sum())
+    assert rows[0]["configs_scored"] == int(ncfg.sum())
+    valid = bad.dag >= 0
+    assert rows[1]["configs_scored"] == int(ncfg[valid].sum())
+    assert rows[0]["inv_per_s"] > 0 and rows[0]["configs_per_s"] > 0
 
 
 @pytest.mark.gpu
