@@ -167,6 +167,15 @@ def test_batched_full(L, method):
     assert_same(got, exp)
 
 
+@pytest.mark.slow
+def test_batched_full_alpha(L, method):
+    """The headline workload in alpha mode (Eq. 1's penalty for missing the
+    target, alpha = 3/2), every decision of all 1,048,576 invocations."""
+    p, inv = W.batched()
+    got, exp = run_both(L, p, inv, mode=1, alpha=(3, 2), method=method)
+    assert_same(got, exp)
+
+
 # ------------------------------------------------------------ edge cases ---
 
 def test_empty_call(L, method):
