@@ -795,8 +795,9 @@ def run_surrogate(args):
 def serve_loop_rate(L, lp, inv, rate: float, seconds: float, rng, id0: int, ticks_in_flight: int = 2):
     """Poisson arrivals at `rate` into the device loop.  The library's driver
     thread runs the ticks back to back (at most ticks_in_flight queued), each
-    dispatching every committed invocation (backends that keep up); this
-    thread only submits arrivals as their time comes and polls the records.
+    dispatching every committed invocation (backends that keep up); the
+    library's arrival process (llama_loop_run_arrivals, on this thread) submits
+    arrivals as their time comes and polls the records.
     Latency: arrival -> speculative record seen by the host, and -> commit record."""
     n = int(rate * seconds)
     arrive = np.cumsum(rng.exponential(1e9 / rate, n)).astype(np.int64)  # ns after t0
@@ -804,34 +805,12 @@ def serve_loop_rate(L, lp, inv, rate: float, seconds: float, rng, id0: int, tick
     req = np.zeros(n, L.LOOP_REQUEST_DTYPE)
     req["id"] = id0 + np.arange(n)
     req["dag"], req["op_local"], req["start_us"] = inv.dag[idx], inv.op_local[idx], inv.start_us[idx]
-    spec_ns = np.full(n, -1, np.int64)
-    com_ns = np.full(n, -1, np.int64)
     st0 = lp.state()
     lp.start(inv.now_us, ticks_in_flight)
     t0 = time.perf_counter_ns()
-    k = 0
-    n_seen = 0
-    while n_seen < 2 * n:
-        t = time.perf_counter_ns() - t0
-        j = int(np.searchsorted(arrive, t, side="right"))
-        # arrivals enter the ring as far as it has room; the rest waits for the
-        # ticks to drain it (a full ring never blocks this loop)
-        while j > k:
-            m = min(j - k, 4096)
-            if lp.submit(req[k:k + m]) == L.EAGAIN:
-                break
-            k += m
-        res = lp.poll()
-        if res.shape[0]:
-            now_ns = time.perf_counter_ns() - t0
-            ids = res["id"] - id0
-            sp = res["kind"] == L.LOOP_SPECULATED
-            cm = res["kind"] == L.LOOP_COMMITTED
-            spec_ns[ids[sp]] = now_ns
-            com_ns[ids[cm]] = now_ns
-            n_seen += int(sp.sum()) + int(cm.sum())
-        if time.perf_counter_ns() - t0 > 10e9 + seconds * 1e9:
-            break
+    # the arrivals submitted and the records polled by the library on this
+    # thread, in native code (no interpreter pauses in the timestamps)
+    spec_ns, com_ns = lp.run_arrivals(req, arrive, timeout_s=10.0 + seconds)
     t_end = time.perf_counter_ns() - t0
     lp.stop()
     st = lp.state()

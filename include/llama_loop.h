@@ -144,6 +144,19 @@ int llama_loop_stop(llama_loop *loop);
  * number in *n_out.  Never waits for the GPU. */
 int llama_loop_poll(llama_loop *loop, llama_loop_result *out, int64_t max_out, int64_t *n_out);
 
+/* A native arrival process (no counterpart in the paper): on the calling host
+ * thread, submit req[k] (whose ids must be id0 + k) once arrive_ns[k]
+ * (non-decreasing, nanoseconds after this call starts) has passed -- as many
+ * as the ring takes, the rest at the next pass -- and poll the records, until
+ * every request's speculative and commit records are seen or timeout_ns has
+ * passed; spec_ns[k] and commit_ns[k] (host, n each) receive when each record
+ * was seen (ns after the start; -1 if not seen; a rejected request gets both
+ * at its rejection).  The driver thread (llama_loop_start) must run the ticks.
+ * Spins on one host core; nothing is allocated on the device.  Errors:
+ * EINVAL, and any error of llama_loop_submit or llama_loop_poll. */
+int llama_loop_run_arrivals(llama_loop *loop, const llama_loop_request *req, const int64_t *arrive_ns, int64_t n,
+                            int64_t id0, int64_t timeout_ns, int64_t *spec_ns, int64_t *commit_ns);
+
 /* Ticks completed so far (read from the page-locked control words the last
  * tick published; never waits), or -1 for a null loop. */
 int64_t llama_loop_ticks_done(llama_loop *loop);

@@ -19,7 +19,7 @@ ROOT = os.path.dirname(PKG)
 LIB = os.path.join(PKG, "libllama.so")
 CHECK_LIB = os.path.join(PKG, "libllama_check.so")  # bounds checks that set bits (-DLLAMA_CHECK)
 OBJ_DIR = os.path.join(ROOT, "_build")
-SOURCES = [os.path.join(PKG, "csrc", f) for f in ("kernels.cu", "llama_host.cu", "llama_static.cu", "sg_gemm.cu", "sg_mlp.cu", "sg_score.cu", "server.cpp", "alu_peak.cu", "count_rate.cu", "loop.cu", "stragglers.cpp")]
+SOURCES = [os.path.join(PKG, "csrc", f) for f in ("kernels.cu", "llama_host.cu", "llama_static.cu", "sg_gemm.cu", "sg_mlp.cu", "sg_score.cu", "server.cpp", "alu_peak.cu", "count_rate.cu", "loop.cu", "loop_arrivals.cpp", "stragglers.cpp")]
 HEADERS = glob.glob(os.path.join(PKG, "csrc", "*.cuh")) + glob.glob(os.path.join(PKG, "csrc", "*.h")) + \
     glob.glob(os.path.join(ROOT, "include", "*.h"))
 DEPS = SOURCES + HEADERS

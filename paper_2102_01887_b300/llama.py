@@ -48,6 +48,7 @@ EXPORTS = ("llama_create", "llama_destroy", "llama_set_dags", "llama_set_profile
            "llama_static_status", "llama_set_wait_limit", "llama_alu_peak", "llama_count_rate", "llama_stragglers", "llama_set_stats_file",
            "llama_check_build", "llama_check_word",
            "llama_loop_create", "llama_loop_destroy", "llama_loop_submit", "llama_loop_tick", "llama_loop_poll",
+           "llama_loop_run_arrivals",
            "llama_loop_sync", "llama_loop_state_get", "llama_loop_refresh", "llama_loop_ticks_done",
            "llama_loop_start", "llama_loop_stop")
 TRACE_EVENTS = 3
@@ -173,6 +174,7 @@ def load(path: str = None) -> ctypes.CDLL:
             "llama_loop_submit": ([vp, vp, i64], ctypes.c_int),
             "llama_loop_tick": ([vp, i64, vp], ctypes.c_int),
             "llama_loop_poll": ([vp, vp, i64, ctypes.POINTER(i64)], ctypes.c_int),
+            "llama_loop_run_arrivals": ([vp, vp, vp, i64, i64, i64, vp, vp], ctypes.c_int),
             "llama_loop_sync": ([vp], ctypes.c_int),
             "llama_loop_state_get": ([vp, ctypes.POINTER(llama_loop_state)], ctypes.c_int),
             "llama_loop_refresh": ([vp], ctypes.c_int),
@@ -665,6 +667,20 @@ class Loop:
 
     def stop(self) -> None:
         self._check(self.lib.llama_loop_stop(self.h))
+
+    def run_arrivals(self, req: np.ndarray, arrive_ns: np.ndarray, timeout_s: float = 10.0) -> tuple:
+        """Submit req[k] at arrive_ns[k] (ns after the call starts) and poll, on a
+        native host thread (the driver must run): (spec_ns, commit_ns), when each
+        request's records were seen (-1 if not)."""
+        req = np.ascontiguousarray(req, LOOP_REQUEST_DTYPE)
+        t = np.ascontiguousarray(arrive_ns, np.int64)
+        n = req.shape[0]
+        spec = np.empty(max(n, 1), np.int64)
+        com = np.empty(max(n, 1), np.int64)
+        id0 = int(req["id"][0]) if n else 0
+        self._check(self.lib.llama_loop_run_arrivals(self.h, req.ctypes.data, t.ctypes.data, n, id0,
+                                                     int(timeout_s * 1e9), spec.ctypes.data, com.ctypes.data))
+        return spec[:n], com[:n]
 
     def state(self) -> dict:
         st = llama_loop_state()

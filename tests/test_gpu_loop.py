@@ -184,3 +184,40 @@ def test_driver_thread_serves_every_request(L):
     lam = (hw[g][:, 1:p.n_hw] <= d["cfg"][:, None]).sum(axis=1)
     assert np.array_equal(r["backend"], lam)
     assert np.array_equal(d["flags"] & 1, (d["lat"] < d["slack"]).astype(np.int32))
+
+
+def test_native_arrival_process_sees_every_record(L):
+    """llama_loop_run_arrivals submits requests as their arrival times come and
+    polls on the calling thread: every valid request's speculative record comes
+    no earlier than its arrival and its commit record no earlier than that, an
+    invalid one is rejected (both times at once), the loop ends with every
+    slot back; ids that are not id0 + k are refused."""
+    p, inv = W.medium(n_inv=5_000)
+    n = inv.n
+    req = np.zeros(n, L.LOOP_REQUEST_DTYPE)
+    req["id"] = 1000 + np.arange(n)
+    req["dag"], req["op_local"], req["start_us"] = inv.dag, inv.op_local, inv.start_us
+    req["dag"][::97] = -1
+    arrive = np.cumsum(np.random.default_rng(4).exponential(1e9 / 2e5, n)).astype(np.int64)  # 2e5 per second
+    with L.Scheduler(p) as s, L.Loop(s, slots=4096, ring=1 << 14, results=1 << 16, max_admit=512,
+                                     cq_cap=(32, 32, 32)) as lp:
+        lp.start(inv.now_us, 2)
+        spec, com = lp.run_arrivals(req, arrive, timeout_s=30.0)
+        lp.stop()
+        lp.tick(inv.now_us + 10**7, [2**31 - 1] * p.n_hw)
+        lp.sync()
+        st = lp.state()
+        bad = req.copy()
+        bad["id"][3] += 1
+        with pytest.raises(L.LlamaError):
+            lp.start(inv.now_us, 2)
+            try:
+                lp.run_arrivals(bad, arrive)
+            finally:
+                lp.stop()
+    assert (spec >= 0).all() and (com >= spec).all()
+    assert (spec >= arrive).all()
+    rej = req["dag"] < 0
+    assert (spec[rej] == com[rej]).all()
+    assert st["rejected"] == int(rej.sum()) and st["committed"] == n - int(rej.sum())
+    assert st["free_slots"] == 4096
