@@ -829,7 +829,9 @@ def serve_loop_rate(L, lp, inv, rate: float, seconds: float, rng, id0: int, tick
 def serve_surrogate_rate(sg, cfg_x, inv, content_x, rate: float, seconds: float, rng, max_batch: int = 4096):
     """The learned-surrogate path under Poisson arrivals: continuous batching --
     each call takes every request that arrived while the previous call ran (up
-    to max_batch); latency = arrival -> the call's decisions are back on the host."""
+    to max_batch), on the library's native arrival process
+    (llama_sg_run_arrivals); latency = arrival -> the call's decisions are back
+    on the host."""
     import torch
     n = int(rate * seconds)
     arrive = np.cumsum(rng.exponential(1e9 / rate, n)).astype(np.int64)
@@ -839,30 +841,15 @@ def serve_surrogate_rate(sg, cfg_x, inv, content_x, rate: float, seconds: float,
     opl = torch.from_numpy(inv.op_local[idx]).to(dev)
     st = torch.from_numpy(inv.start_us[idx]).to(dev)
     cx = content_x[torch.from_numpy(idx % content_x.shape[0]).to(dev)].contiguous()
-    out = torch.zeros(max_batch * 24, dtype=torch.uint8, device=dev)
-    host = torch.zeros(max_batch * 24, dtype=torch.uint8).pin_memory()
-    stream = torch.cuda.current_stream()
-    done_ns = np.full(n, -1, np.int64)
-    sizes = []
+    torch.cuda.synchronize()
     t0 = time.perf_counter_ns()
-    k = 0
-    while k < n:
-        t = time.perf_counter_ns() - t0
-        j = min(int(np.searchsorted(arrive, t, side="right")), k + max_batch)
-        if j == k:
-            continue
-        sg.schedule_device(cfg_x, cx[k:j], dag[k:j], opl[k:j], st[k:j], inv.now_us + t // 1000,
-                           out[:24 * (j - k)], stream)
-        host[:24 * (j - k)].copy_(out[:24 * (j - k)], non_blocking=True)
-        stream.synchronize()
-        done_ns[k:j] = time.perf_counter_ns() - t0
-        sizes.append(j - k)
-        k = j
+    done_ns = sg.run_arrivals(cfg_x, cx, dag, opl, st, arrive, inv.now_us, max_batch)
     t_end = time.perf_counter_ns() - t0
     lat_us = (done_ns - arrive) / 1e3
+    calls = int(np.unique(done_ns).size)
     return {"offered_per_s": rate, "requests": n, "throughput_per_s": n / (t_end / 1e9),
             "decision_us": {"p50": float(np.percentile(lat_us, 50)), "p99": float(np.percentile(lat_us, 99))},
-            "calls": len(sizes), "mean_batch": float(np.mean(sizes))}
+            "calls": calls, "mean_batch": n / max(calls, 1)}
 
 
 def run_serve(args):

@@ -111,9 +111,14 @@ const char *llama_mlp_last_error(llama_mlp *net);
  * profile tables; `net` the weights (not copied: later training is seen).  A
  * prediction that is not finite falls back to the profiled value.  Decisions
  * report the predicted latency and cost of the chosen configuration and the
- * slack of its backend; FEASIBLE means predicted latency < slack.  Scratch
- * grows with the calls; at most max_inv invocations and max_pairs
- * (invocation, configuration) pairs per call.  Errors: EINVAL. */
+ * slack of its backend; FEASIBLE means predicted latency < slack.  At most
+ * max_inv invocations and max_pairs (invocation, configuration) pairs per
+ * call.  The scratch of a call is allocated here -- for max_inv invocations,
+ * and pair rows (whole 128-row tiles per invocation, about 550 B per row) for
+ * max_pairs pairs and the padding of up to 4,096 invocations -- so a call
+ * allocates nothing but, once per profile, layer 1's configuration part, and,
+ * when it needs more pair rows than any call before, their growth (to twice the
+ * rows held at least).  Errors: EINVAL, ENOMEM, ECUDA. */
 typedef struct llama_sg llama_sg;
 int llama_sg_create(llama_sg **out, llama_ctx *ctx, llama_mlp *net, int64_t max_inv, int64_t max_pairs);
 void llama_sg_destroy(llama_sg *sg);
@@ -136,6 +141,21 @@ int llama_sg_schedule(llama_sg *sg, const void *cfg_x, const void *inv_x, int64_
  * (one stream, or an event).  After changing cfg_x's contents in place, call
  * llama_sg_invalidate.  No counterpart in the paper.  Errors: EINVAL. */
 int llama_sg_invalidate(llama_sg *sg);
+
+/* A native arrival process for the surrogate's path (no counterpart in the
+ * paper), on the calling host thread: continuous batching -- each call of
+ * llama_sg_schedule (at time now_us plus the microseconds since this call
+ * started) takes every request k whose arrive_ns[k] (non-decreasing, ns after
+ * the start) has passed, at most max_batch, then copies the decisions to
+ * host_out (page-locked, max_batch entries) on `stream` and waits for them;
+ * done_ns[k] (host, n) receives when request k's decision was on the host.
+ * inv_x, dag, op_local, start_us: device, per request (inv_x rows as for
+ * llama_sg_schedule); out: device, max_batch entries.  Errors: EINVAL, ECUDA,
+ * and those of llama_sg_schedule. */
+int llama_sg_run_arrivals(llama_sg *sg, const void *cfg_x, const void *inv_x, const int32_t *dag,
+                          const int32_t *op_local, const int64_t *start_us, int64_t n, const int64_t *arrive_ns,
+                          int64_t now_us, int64_t max_batch, llama_decision *out, llama_decision *host_out,
+                          void *stream, int64_t *done_ns);
 
 /* Safety margin in log units (0 .. 1, default 0): the selection uses
  * e^(y0 + margin) times the profiled latency and cost, an upper quantile of the

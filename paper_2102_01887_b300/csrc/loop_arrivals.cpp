@@ -1,15 +1,19 @@
-// loop_arrivals.cpp -- a native arrival process for the serving loop (no
-// counterpart in the paper): requests are submitted to the loop's ring as their
-// arrival times come and the records are polled, on the calling host thread,
-// each request's speculative and commit records timed by the steady clock.
-// The driver thread (llama_loop_start) must be running.  Host code only.
+// loop_arrivals.cpp -- native arrival processes for serving (no counterpart in
+// the paper), on the calling host thread, timed by the steady clock:
+//  * the device-resident loop: requests submitted to its ring as their arrival
+//    times come, its records polled (the driver thread runs the ticks);
+//  * the learned surrogate's path: continuous batching, each call taking every
+//    request that arrived while the previous one ran.
+// Host code only (the surrogate's calls enqueue its kernels).
+#include <cuda_runtime.h>
+
 #include <chrono>
 #include <cstdint>
-#include <thread>
 #include <vector>
 
 #include "../../include/llama_loop.h"
 #include "../../include/llama_server.h"
+#include "../../include/llama_surrogate.h"
 
 extern "C" int llama_loop_run_arrivals(llama_loop *loop, const llama_loop_request *req, const int64_t *arrive_ns,
                                        int64_t n, int64_t id0, int64_t timeout_ns, int64_t *spec_ns,
@@ -55,6 +59,42 @@ extern "C" int llama_loop_run_arrivals(llama_loop *loop, const llama_loop_reques
             }
         }
         if (since() > timeout_ns) break;  // records not seen by then stay -1
+    }
+    return LLAMA_OK;
+}
+
+extern "C" int llama_sg_run_arrivals(llama_sg *sg, const void *cfg_x, const void *inv_x, const int32_t *dag,
+                                     const int32_t *op_local, const int64_t *start_us, int64_t n,
+                                     const int64_t *arrive_ns, int64_t now_us, int64_t max_batch,
+                                     llama_decision *out, llama_decision *host_out, void *stream, int64_t *done_ns) {
+    if (!sg || n < 0 || max_batch < 1) return LLAMA_EINVAL;
+    if (n > 0 && (!cfg_x || !inv_x || !dag || !op_local || !start_us || !arrive_ns || !out || !host_out || !done_ns))
+        return LLAMA_EINVAL;
+    for (int64_t k = 1; k < n; ++k)
+        if (arrive_ns[k] < arrive_ns[k - 1]) return LLAMA_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const auto t0 = std::chrono::steady_clock::now();
+    const auto since = [&] {
+        return (int64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now() - t0)
+            .count();
+    };
+    constexpr int64_t kRow = 64 * 2;  // bytes of one BF16 feature row
+    int64_t k = 0;
+    while (k < n) {
+        const int64_t t = since();
+        int64_t j = k;
+        while (j < n && j - k < max_batch && arrive_ns[j] <= t) ++j;
+        if (j == k) continue;  // nothing has arrived yet
+        const int64_t m = j - k;
+        int rc = llama_sg_schedule(sg, cfg_x, static_cast<const char *>(inv_x) + k * kRow, m, dag + k,
+                                   op_local + k, start_us + k, now_us + t / 1000, out, stream);
+        if (rc != LLAMA_OK) return rc;
+        if (cudaMemcpyAsync(host_out, out, sizeof(llama_decision) * m, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return LLAMA_ECUDA;
+        const int64_t now = since();
+        for (int64_t q = k; q < j; ++q) done_ns[q] = now;
+        k = j;
     }
     return LLAMA_OK;
 }

@@ -183,6 +183,7 @@ struct llama_sg {
     const int32_t *a_hw_off = nullptr;
     int64_t a_ncfg = -1, a_version = -1;
     std::string err;
+    size_t cap_rows = 0;  // pair rows the pair buffers hold
 };
 
 namespace {
@@ -207,6 +208,26 @@ int sg_fail(llama_sg *s, int code, const std::string &what, cudaError_t e = cuda
 
 }  // namespace
 
+namespace {
+
+constexpr size_t kReserveInv = 4096;  // invocations whose row padding is reserved at creation
+
+// Pair buffers for `rows` pair rows (h2, selection records and costs,
+// predictions, tile descriptors).
+cudaError_t reserve_rows(llama_sg *s, size_t rows) {
+    rows = std::max<size_t>(rows, kTileRows);
+    cudaError_t e = cudaSuccess;
+    const auto A = [&](Buf &b, size_t n) {
+        if (e == cudaSuccess) e = b.ensure(n);
+    };
+    A(s->h2, 2 * rows * kHid), A(s->pair_sel, 16 * rows), A(s->pair_cost, 8 * rows), A(s->lhat, 4 * rows);
+    A(s->chat, 8 * rows), A(s->tile_info, 8 * (rows / kTileRows + 1));
+    if (e == cudaSuccess) s->cap_rows = rows;
+    return e;
+}
+
+}  // namespace
+
 extern "C" int llama_sg_create(llama_sg **out, llama_ctx *ctx, llama_mlp *net, int64_t max_inv, int64_t max_pairs) {
     if (!out) return LLAMA_EINVAL;
     *out = nullptr;
@@ -218,6 +239,38 @@ extern "C" int llama_sg_create(llama_sg **out, llama_ctx *ctx, llama_mlp *net, i
     s->device = mlp_view(net).device;
     s->max_inv = max_inv;
     s->max_pairs = max_pairs;
+    // the scratch of every call, allocated here so that a call normally
+    // allocates nothing (an allocation inside a call synchronises the device
+    // and stalls every request queued behind it): the per-invocation arrays and
+    // the sort and scan scratch for max_inv invocations, and pair rows (whole
+    // tiles per invocation) for max_pairs pairs and the padding of up to
+    // kReserveInv invocations -- a call that needs more rows grows them
+    // geometrically (reserve_rows)
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != s->device) cudaSetDevice(s->device);
+    const size_t ni = (size_t)max_inv;
+    cudaError_t e = reserve_rows(s, (size_t)max_pairs + (size_t)(kTileRows - 1) * std::min<size_t>(ni, kReserveInv));
+    const auto A = [&](Buf &b, size_t n) {
+        if (e == cudaSuccess) e = b.ensure(n);
+    };
+    A(s->B, 4 * ni * kHid), A(s->slack, 4 * ni * LLAMA_MAX_HW), A(s->key, 4 * ni), A(s->key_sorted, 4 * ni);
+    A(s->idx, 4 * ni), A(s->idx_sorted, 4 * ni), A(s->npairs, 8 * (ni + 1)), A(s->nrows, 8 * (ni + 1));
+    A(s->row_off, 8 * (ni + 1)), A(s->inv_row, 8 * ni), A(s->best, 8 * ni), A(s->total, 8);
+    size_t t_sort = 0, t_scan = 0;  // for max_inv items and keys of up to 32 bits
+    if (e == cudaSuccess)
+        e = cub::DeviceRadixSort::SortPairs(nullptr, t_sort, s->key.as<int32_t>(), s->key_sorted.as<int32_t>(),
+                                            s->idx.as<int32_t>(), s->idx_sorted.as<int32_t>(), (int)max_inv, 0, 32);
+    if (e == cudaSuccess)
+        e = cub::DeviceScan::ExclusiveSum(nullptr, t_scan, s->nrows.as<int64_t>(), s->row_off.as<int64_t>(),
+                                          (int)(max_inv + 1));
+    A(s->scan_tmp, std::max(t_sort, t_scan));
+    if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        return e == cudaErrorMemoryAllocation ? LLAMA_ENOMEM : LLAMA_ECUDA;
+    }
     *out = s;
     return LLAMA_OK;
 }
@@ -244,8 +297,7 @@ extern "C" int llama_sg_schedule(llama_sg *s, const void *cfg_x, const void *inv
     if (prev != v.device) cudaSetDevice(v.device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int H = v.n_hw;
-    int64_t n_cfg = 0;
-    SG_CUDA(s, cudaMemcpy(&n_cfg, v.P.cfg_off + v.n_ops, sizeof(int64_t), cudaMemcpyDeviceToHost));
+    const int64_t n_cfg = v.P.n_cfg;  // the context's configuration count (host)
     const size_t ni = (size_t)s->max_inv;
     SG_CUDA(s, s->A.ensure(2 * (size_t)n_cfg * kHid));
     SG_CUDA(s, s->lam.ensure((size_t)n_cfg));
@@ -300,13 +352,7 @@ extern "C" int llama_sg_schedule(llama_sg *s, const void *cfg_x, const void *inv
     if (pairs > s->max_pairs) return sg_fail(s, LLAMA_EINVAL, "schedule: more (invocation, configuration) pairs than max_pairs");
     s->last_pairs = pairs;
     s->last_n_inv = n_inv;
-    const size_t cap = (size_t)std::max<int64_t>(rows, kTileRows);
-    SG_CUDA(s, s->h2.ensure(2 * cap * kHid));
-    SG_CUDA(s, s->pair_sel.ensure(16 * cap));
-    SG_CUDA(s, s->pair_cost.ensure(8 * cap));
-    SG_CUDA(s, s->lhat.ensure(4 * cap));
-    SG_CUDA(s, s->chat.ensure(8 * cap));
-    SG_CUDA(s, s->tile_info.ensure(8 * (cap / kTileRows)));
+    if ((size_t)rows > s->cap_rows) SG_CUDA(s, reserve_rows(s, std::max<size_t>((size_t)rows, 2 * s->cap_rows)));
     // first layer, split: A = configurations . W1^T (BF16), B = contents . W1^T + b1
     if (!a_cached) {
         SG_RC(s, gemm(cfg_x, nv.w16[0], nullptr, s->A.p, nullptr, n_cfg, kHid, kIn, 0, st), "layer 1 (configurations)");

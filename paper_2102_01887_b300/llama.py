@@ -48,7 +48,7 @@ EXPORTS = ("llama_create", "llama_destroy", "llama_set_dags", "llama_set_profile
            "llama_static_status", "llama_set_wait_limit", "llama_alu_peak", "llama_count_rate", "llama_stragglers", "llama_set_stats_file",
            "llama_check_build", "llama_check_word",
            "llama_loop_create", "llama_loop_destroy", "llama_loop_submit", "llama_loop_tick", "llama_loop_poll",
-           "llama_loop_run_arrivals",
+           "llama_loop_run_arrivals", "llama_sg_run_arrivals",
            "llama_loop_sync", "llama_loop_state_get", "llama_loop_refresh", "llama_loop_ticks_done",
            "llama_loop_start", "llama_loop_stop")
 TRACE_EVENTS = 3
@@ -175,6 +175,7 @@ def load(path: str = None) -> ctypes.CDLL:
             "llama_loop_tick": ([vp, i64, vp], ctypes.c_int),
             "llama_loop_poll": ([vp, vp, i64, ctypes.POINTER(i64)], ctypes.c_int),
             "llama_loop_run_arrivals": ([vp, vp, vp, i64, i64, i64, vp, vp], ctypes.c_int),
+            "llama_sg_run_arrivals": ([vp, vp, vp, vp, vp, vp, i64, vp, i64, i64, vp, vp, vp, vp], ctypes.c_int),
             "llama_loop_sync": ([vp], ctypes.c_int),
             "llama_loop_state_get": ([vp, ctypes.POINTER(llama_loop_state)], ctypes.c_int),
             "llama_loop_refresh": ([vp], ctypes.c_int),

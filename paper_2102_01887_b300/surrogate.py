@@ -113,6 +113,24 @@ class SurrogateScheduler:
         self._check(L.load().llama_sg_schedule(self.h, v(cfg_x), v(inv_x), dag.shape[0], v(dag), v(op_local),
                                                v(start), int(now_us), v(out), L._stream_ptr(stream)))
 
+    def run_arrivals(self, cfg_x, inv_x, dag, op_local, start, arrive_ns, now_us: int, max_batch: int = 4096,
+                     stream=None):
+        """Continuous batching on a native host thread: each call takes every
+        request that arrived while the previous one ran (at most max_batch);
+        returns when each request's decision was back on the host (ns after the
+        start).  inv_x, dag, op_local, start: device tensors, one row per request."""
+        import torch
+        v = lambda t: ctypes.c_void_p(t.data_ptr())
+        n = dag.shape[0]
+        t = np.ascontiguousarray(arrive_ns, np.int64)
+        out = torch.zeros(max_batch * 24, dtype=torch.uint8, device=dag.device)
+        host = torch.zeros(max_batch * 24, dtype=torch.uint8).pin_memory()
+        done = np.full(max(n, 1), -1, np.int64)
+        self._check(L.load().llama_sg_run_arrivals(self.h, v(cfg_x), v(inv_x), v(dag), v(op_local), v(start), n,
+                                                   t.ctypes.data, int(now_us), int(max_batch), v(out), v(host),
+                                                   L._stream_ptr(stream), done.ctypes.data))
+        return done[:n]
+
     def schedule(self, cfg_x, inv, content):
         """Decisions (numpy, DECISION_DTYPE) for invocations with their content."""
         import torch

@@ -302,3 +302,32 @@ def test_trained_surrogate_against_the_table_path(L, world):
     # on varied content it must gain: far fewer missed targets than the content-blind table
     assert con["surrogate"]["violations"] < 0.5 * con["table"]["violations"]
     assert hist[-1] < hist[0]
+
+
+def test_native_arrival_process_batches_what_arrived(L, world):
+    """llama_sg_run_arrivals: every request's decision comes back after it
+    arrived, in calls of at most max_batch requests that each took only
+    requests already arrived; decreasing arrival times are refused."""
+    import torch
+    from paper_2102_01887_b300 import surrogate as S
+    p, inv, cw = world
+    n = 3000
+    rng = np.random.default_rng(8)
+    idx = rng.integers(0, inv.n, n)
+    arrive = np.cumsum(rng.exponential(1e9 / 2e5, n)).astype(np.int64)  # 2e5 per second
+    content = S.content_inputs(W.invocation_content(6, n))
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    with L.Scheduler(p) as s, L.MLP(max_batch=1024) as net:
+        net.set_params(M.pack(perturbed_params(41)).astype(np.float32))
+        cfg_x = S.config_inputs(p, cw)
+        with S.SurrogateScheduler(s, net, max_inv=256, max_pairs=1 << 20) as sg:
+            done = sg.run_arrivals(cfg_x, content, dev(inv.dag[idx]), dev(inv.op_local[idx]),
+                                   dev(inv.start_us[idx]), arrive, inv.now_us, max_batch=256)
+            with pytest.raises(L.LlamaError):
+                sg.run_arrivals(cfg_x, content, dev(inv.dag[idx]), dev(inv.op_local[idx]), dev(inv.start_us[idx]),
+                                arrive[::-1].copy(), inv.now_us, max_batch=256)
+    assert (done >= arrive).all()
+    # a call's requests share its completion time: consecutive runs, each at most 256 long
+    ends = np.flatnonzero(np.diff(done) != 0)
+    sizes = np.diff(np.concatenate([[-1], ends, [n - 1]]))
+    assert (np.diff(done) >= 0).all() and sizes.max() <= 256 and sizes.sum() == n
