@@ -29,7 +29,7 @@ int gemm(const void *a, const void *b, const float *bias, void *c16, float *c32,
 // then one pass sums the partials in a fixed order, so the result does not
 // depend on scheduling.  For products with few output tiles and a long K
 // (weight gradients: K = the batch).
-constexpr int kMinSplitBlocks = 4;  // K blocks of 64 per split at least
+constexpr int kMinSplitBlocks = 8;  // K blocks of 64 per split at least
 int splits_for(int64_t m, int n, int k, int sms);
 int gemm_split_k(const void *a, const void *b, float *c32, int64_t m, int n, int k, int splits, float *part,
                  size_t part_bytes, cudaStream_t s);

@@ -41,24 +41,46 @@ def training_inputs(x: np.ndarray, t: np.ndarray, device="cuda"):
     return _bf16(x, 0, device), torch.from_numpy(np.ascontiguousarray(t, np.float32)).to(device)
 
 
-def train(net, x, t, epochs: int, batch: int = 8192, lr: float = 1e-3, w_fan: float = 0.5, seed: int = 0,
-          stream=None) -> list:
-    """Adam over shuffled mini-batches of the device tensors x (BF16 [n, 64]) and
-    t (FP32 [n, 2]); the mean batch loss of every epoch."""
+def _run_epochs(net, x, t, batch: int, w_fan: float, plan, stream=None) -> list:
+    """Adam epochs over the device tensors x (BF16 [n, 64]) and t (FP32 [n, 2]):
+    plan yields (permutation of the rows, CPU tensor; learning rate) per epoch,
+    lazily, so that the next epoch's order is drawn on the host and copied while
+    the current epoch runs.  The epochs' mean batch losses."""
     import torch
-    n = x.shape[0] // batch * batch
-    g = torch.Generator(device="cpu").manual_seed(seed)
+    nb = x.shape[0] // batch
     acc = torch.zeros(1, dtype=torch.float32, device=x.device)
     history = []
-    for _ in range(epochs):
-        # the permutation, the loss sum and the epoch on one stream
-        with torch.cuda.stream(stream) if stream is not None else contextlib.nullcontext():
-            perm = torch.randperm(x.shape[0], generator=g)[:n].to(device=x.device, dtype=torch.int32)
+
+    def upload(item):
+        if item is None:
+            return None
+        perm, lr = item
+        host = perm[:nb * batch].to(torch.int32).pin_memory()
+        return host, host.to(x.device, non_blocking=True), lr
+
+    plan = iter(plan)
+    # the permutation, the loss sum and the epochs on one stream
+    with torch.cuda.stream(stream) if stream is not None else contextlib.nullcontext():
+        nxt = upload(next(plan, None))
+        while nxt is not None:
+            _, perm, lr = nxt
             acc.zero_()
             # every batch of the epoch in one library call: gathered on the device
             net.train_epoch(x, t, perm, batch, w_fan, lr, acc, stream)
-            history.append(float(acc.item()) / (n // batch))
+            nxt = upload(next(plan, None))  # drawn and copied while this epoch runs
+            history.append(float(acc.item()) / nb)
     return history
+
+
+def train(net, x, t, epochs: int, batch: int = 8192, lr: float = 1e-3, w_fan: float = 0.5, seed: int = 0,
+          stream=None) -> list:
+    """Adam over shuffled mini-batches of the device tensors x (BF16 [n, 64]) and
+    t (FP32 [n, 2]), one seeded generator for every epoch's order; the mean
+    batch loss of every epoch."""
+    import torch
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    plan = ((torch.randperm(x.shape[0], generator=g), lr) for _ in range(epochs))
+    return _run_epochs(net, x, t, batch, w_fan, plan, stream)
 
 
 def held_out_rmse(net, x, t, batch: int = 8192) -> float:
@@ -79,11 +101,15 @@ def margin_from_rmse(rmse: float, noise_sigma: float) -> float:
 
 def train_schedule(net, x, t, epochs: int = 12, lr: float = 2e-3, halve_every: int = 3, w_fan: float = 0.1,
                    seed: int = 0) -> list:
-    """Adam with the learning rate halved every few epochs; the epochs' mean losses."""
-    hist = []
-    for e in range(epochs):
-        hist += train(net, x, t, epochs=1, lr=lr * 0.5 ** (e // halve_every), w_fan=w_fan, seed=seed + e)
-    return hist
+    """Adam with the learning rate halved every few epochs (epoch e's order from a
+    generator seeded seed + e); the epochs' mean losses."""
+    import torch
+
+    def order(e):
+        return torch.randperm(x.shape[0], generator=torch.Generator(device="cpu").manual_seed(seed + e))
+
+    plan = ((order(e), lr * 0.5 ** (e // halve_every)) for e in range(epochs))
+    return _run_epochs(net, x, t, 8192, w_fan, plan)
 
 
 class SurrogateScheduler:
