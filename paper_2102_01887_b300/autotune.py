@@ -24,8 +24,12 @@ DEFAULT_CTAS_PER_SM = (0, 4, 3)  # 0: as many as fit
 DEFAULT_DLAT_STAGE = (4096, 8192)  # the first is the library default
 
 
-def time_call(ctx, dag, op_local, start, now: int, out, stream, flush, reps: int = 5) -> float:
-    """Median device time (ms) of one scheduling call, L2 flushed before each."""
+def time_call(ctx, dag, op_local, start, now: int, out, stream, flush, reps: int = 10) -> float:
+    """Device time (ms) of one scheduling call, the L2 flushed before each: the
+    mean of reps calls without the fastest and the slowest.  Event timestamps
+    advance in steps of about 2 us, so a single call's time, and a median of
+    them, only tells schedules apart by whole steps; a mean of readings taken at
+    different phases of those steps resolves finer differences."""
     import torch
     times = []
     for r in range(reps + 1):
@@ -40,14 +44,15 @@ def time_call(ctx, dag, op_local, start, now: int, out, stream, flush, reps: int
         if r:  # the first call of a setting (re)captures its graph
             times.append(e0.elapsed_time(e1))
     times.sort()
-    return times[len(times) // 2]
+    kept = times[1:-1] if len(times) > 2 else times
+    return sum(kept) / len(kept)
 
 
 def autotune(ctx, dag, op_local, start, now: int, out, stream=None, flush=None,
              lanes: Iterable[int] = DEFAULT_LANES_MIN_VECTORS,
              ipts: Iterable[int] = DEFAULT_INV_PER_THREAD, chunks: Iterable[int] = (0,),
              stages: Iterable[int] = DEFAULT_STAGES, ctas_per_sm: Iterable[int] = DEFAULT_CTAS_PER_SM,
-             dlat_stage: Iterable[int] = DEFAULT_DLAT_STAGE, reps: int = 5) -> dict:
+             dlat_stage: Iterable[int] = DEFAULT_DLAT_STAGE, reps: int = 10) -> dict:
     """Sweep the candidates, apply the fastest, return {"best": ..., "trials": [...]}.
 
     ``chunks``: staging chunk sizes in configurations (0 = the library default);
