@@ -371,6 +371,21 @@ int llama_set_count_pass(llama_ctx *ctx, int32_t mode);
 #define LLAMA_METHOD_STAIRCASE 1
 int llama_set_method(llama_ctx *ctx, int32_t method);
 
+/* Small calls of the SCAN method (no counterpart in the paper; changes speed,
+ * never results): a call of at most n_inv invocations (default
+ * LLAMA_DIRECT_DEFAULT) skips the bucketing by operation.  Two kernels instead
+ * of the bucketing and scoring kernels: the critical paths of every DAG
+ * (Algorithm 1's longest remaining path), then a warp per invocation that
+ * computes its slack per backend and scans its operation's rank-encoded table
+ * straight from L2 (Eq. 1), with the same decisions.  Such a call has no
+ * bounded wait, so it never times out.  With few invocations per operation no
+ * table copy is shared, and two short kernels replace a cooperative launch and
+ * its grid barrier.  0: every call is bucketed.  Errors: EINVAL (n_inv outside
+ * 0..LLAMA_DIRECT_LIMIT). */
+#define LLAMA_DIRECT_DEFAULT 1024
+#define LLAMA_DIRECT_LIMIT (1 << 20)
+int llama_set_direct_max(llama_ctx *ctx, int64_t n_inv);
+
 /* Bounded device waits (no counterpart in the paper).  The bucketing kernel's
  * grid barriers poll at most `tries` times before they give up: the call then
  * decides nothing (every valid invocation is flagged LLAMA_FLAG_TIMEOUT with

@@ -1722,6 +1722,154 @@ __global__ void __launch_bounds__(256) k_stair(DevProblem P, int64_t n_inv, cons
     finish_call(S, out, false);
 }
 
+// ---------------------------------------------------------------------------
+// Small calls of the scan method: no bucketing
+// ---------------------------------------------------------------------------
+
+// A warp per invocation (warp-uniform loop).  The decision is the one the
+// bucketed scan reaches: the slack of each backend (Algorithm 1 from the
+// critical paths of the previous kernel) becomes the count of the op's
+// distinct latencies below it; every lane scans its share of the op's
+// rank-encoded table, each vector against the count of its backend segment
+// (Eq. 1's feasibility and objective in rank form, read from L2, where a call
+// of few invocations leaves no table to share); a warp minimum of the packed
+// keys; lane 0 decodes the least key.
+//
+// The counts: the searches of all backends advance together (their loads in
+// flight at once).  While more than 32 candidates are left, each lane probes
+// the last value of one of 32 equal blocks of them: the blocks whose last
+// value is below the slack (a prefix, the values ascending) are wholly below
+// it, and the first other block holds the boundary; then one probe per
+// remaining candidate.  At most four rounds of loads for 32^3 distinct
+// latencies.  The scan: four vectors per lane in flight.
+template <int MODE>
+__device__ __forceinline__ void direct_body(const DevProblem &P, int64_t n_inv, const int32_t *dag,
+                                            const int32_t *op_local, const int64_t *start, int64_t now,
+                                            const BucketScratch &S, llama_decision *out) {
+    constexpr int kWarps = 256 / 32, kUnroll = 4;
+    __shared__ TileConst tc;
+    __shared__ uint32_t w_c2[kWarps][LLAMA_MAX_HW];  // per warp: count of each segment, both halves
+    __shared__ int32_t w_end[kWarps][LLAMA_MAX_HW];  // per warp: end of each segment (vectors)
+    const int H = P.n_hw, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    // the critical paths (previous kernel) and the queueing times are visible after this
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    if ((int)threadIdx.x < H) tc.q[threadIdx.x] = P.q[threadIdx.x];
+    __syncthreads();
+    const int64_t n_warps = (int64_t)gridDim.x * kWarps;
+    for (int64_t i = blockIdx.x * (int64_t)kWarps + wid; i < n_inv; i += n_warps) {
+        int32_t g;
+        int64_t rbase;
+        if (!invocation_op(P, dag[i], op_local[i], start[i], now, g, rbase)) {
+            if (lane == 0) {
+                llama_decision bad;
+                bad.cfg = -1;
+                bad.lat = 0;
+                bad.cost = 0;
+                bad.slack = 0;
+                bad.flags = LLAMA_FLAG_INVALID;
+                out[i] = bad;
+                atomicAdd(&S.ctrl[kCtrlInvalid], 1ull);
+            }
+            continue;
+        }
+        // the remaining time before queueing, as a bucket entry holds it
+        const int64_t rem = max(rbase, (int64_t)0);
+        const int64_t ref = P.ref[g], cp = P.cp[g];
+        const uint64_t mg = P.cp_magic[g];
+        const int64_t p0 = P.pad_off[g];
+        const int32_t dn = P.dlat_n[g];
+        const int32_t *sp = P.seg_pad + (int64_t)g * (H + 1);
+        const int32_t npad = __ldg(sp + H), beg = __ldg(sp) / kVec;
+        if (!LLAMA_IN_BOUNDS(P, p0 >= 0 && p0 + npad <= P.n_pad && dn <= npad, LLAMA_CHECK_TILE)) continue;
+        const int32_t *dl = P.dlat + p0;
+        int32_t sl[LLAMA_MAX_HW], lo[LLAMA_MAX_HW], hi[LLAMA_MAX_HW];
+#pragma unroll
+        for (int h = 0; h < LLAMA_MAX_HW; ++h) {
+            sl[h] = h < H ? slack_of(ref, cp, mg, rem - tc.q[h]) : 0;
+            lo[h] = 0;
+            hi[h] = h < H ? dn : 0;
+        }
+        for (;;) {  // each round leaves fewer than 1/32 of the candidates
+            bool any = false, below[LLAMA_MAX_HW];
+            int32_t step[LLAMA_MAX_HW];
+#pragma unroll
+            for (int h = 0; h < LLAMA_MAX_HW; ++h) {
+                const bool act = hi[h] - lo[h] > 32;
+                any |= act;
+                step[h] = act ? (hi[h] - lo[h] + 31) / 32 : 0;
+                const int32_t p = lo[h] + (lane + 1) * step[h] - 1;
+                below[h] = act && p < hi[h] && __ldg(dl + p) < sl[h];
+            }
+            if (!any) break;
+#pragma unroll
+            for (int h = 0; h < LLAMA_MAX_HW; ++h) {
+                if (step[h] == 0) continue;
+                lo[h] += __popc(__ballot_sync(0xffffffffu, below[h])) * step[h];
+                hi[h] = min(hi[h], lo[h] + step[h] - 1);  // the first block not below ends at a value >= s
+            }
+        }
+        {
+            bool below[LLAMA_MAX_HW];
+#pragma unroll
+            for (int h = 0; h < LLAMA_MAX_HW; ++h) below[h] = lo[h] + lane < hi[h] && __ldg(dl + lo[h] + lane) < sl[h];
+#pragma unroll
+            for (int h = 0; h < LLAMA_MAX_HW; ++h) {
+                const int32_t c = lo[h] + __popc(__ballot_sync(0xffffffffu, below[h]));
+                if (lane == h && h < H) {
+                    w_c2[wid][h] = (uint32_t)c * 0x00010001u;
+                    w_end[wid][h] = __ldg(sp + h + 1) / kVec;
+                }
+            }
+        }
+        __syncwarp();
+        const uint4 *lr4 = reinterpret_cast<const uint4 *>(P.lrb + p0);
+        const uint4 *rf4 = reinterpret_cast<const uint4 *>(P.rf + p0);
+        const uint4 *df4 = reinterpret_cast<const uint4 *>(P.df + p0);
+        const int nv = npad / kVec;
+        uint32_t best = 0xFFFFFFFFu;
+        int h = 0;  // the segment of this lane's vector (non-decreasing along the loop)
+        for (int q0 = beg + lane; q0 < nv; q0 += 32 * kUnroll) {
+            uint4 lk[kUnroll], rk[kUnroll], dk[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const int q = q0 + 32 * u;
+                if (q < nv) {
+                    lk[u] = __ldg(lr4 + q);
+                    rk[u] = __ldg(rf4 + q);
+                    if (MODE == LLAMA_MODE_ALPHA) dk[u] = __ldg(df4 + q);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const int q = q0 + 32 * u;
+                if (q >= nv) break;
+                while (q >= w_end[wid][h]) ++h;  // the last segment ends at nv
+                if (MODE == LLAMA_MODE_ALPHA) best = scan8_alpha(best, w_c2[wid][h], lk[u], rk[u], dk[u]);
+                else best = scan8_cost_first(best, w_c2[wid][h], lk[u], rk[u]);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) best = vmin_u16x2(best, __shfl_xor_sync(0xffffffffu, best, o));
+        if (lane == 0)
+            decode_into<MODE>(P, g, (int32_t)P.cfg_off[g], min(best & 0xFFFFu, best >> 16), ref, cp, mg, rem, tc,
+                              out + i);
+        __syncwarp();  // the warp's segment words are read before the next invocation writes them
+    }
+    finish_call(S, out, false);
+}
+
+__global__ void __launch_bounds__(256) k_direct_cf(DevProblem P, int64_t n_inv, const int32_t *dag,
+                                                   const int32_t *op_local, const int64_t *start, int64_t now,
+                                                   BucketScratch S, llama_decision *out) {
+    direct_body<LLAMA_MODE_COST_FIRST>(P, n_inv, dag, op_local, start, now, S, out);
+}
+
+__global__ void __launch_bounds__(256) k_direct_al(DevProblem P, int64_t n_inv, const int32_t *dag,
+                                                   const int32_t *op_local, const int64_t *start, int64_t now,
+                                                   BucketScratch S, llama_decision *out) {
+    direct_body<LLAMA_MODE_ALPHA>(P, n_inv, dag, op_local, start, now, S, out);
+}
+
 // Inclusive minimum scan of a[0..n) in shared memory by the whole block, from
 // the front (reverse = false) or from the back; part[] holds 32 words.
 template <typename T>
@@ -1867,8 +2015,8 @@ cudaError_t enqueue_encode_objmin(const ContextView &v, int64_t *objmin, cudaStr
 
 int64_t max_tiles(int64_t n_inv, int32_t n_ops) { return n_inv + n_ops; }
 
-int schedule_launches(const ContextView &v, const BucketScratch &S) {
-    if (v.method == LLAMA_METHOD_STAIRCASE) return 2;
+int schedule_launches(const ContextView &v, const BucketScratch &S, int64_t n_inv) {
+    if (v.method == LLAMA_METHOD_STAIRCASE || n_inv <= v.direct_max) return 2;
     return S.b_cnt && v.need_counts ? 3 : 2;
 }
 
@@ -1926,6 +2074,30 @@ static cudaError_t enqueue_schedule_impl(const ContextView &v, const BucketScrat
         BucketScratch Sc = S;
         void *args[] = {&P, &n_inv, &dag, &op_local, &start, &now, &Sc, &out};
         e = cudaLaunchKernelExC(&cfg, (const void *)k_stair, args);
+        if (e != cudaSuccess) return e;
+        mark(2);
+        return cudaGetLastError();
+    }
+    if (n_inv <= v.direct_max) {
+        // a small call: critical paths, then a warp per invocation
+        k_critical_paths<<<std::max(1, (v.n_dags + 7) / 8), 256, 0, s>>>(v.P, v.topo, v.lvl_off, v.dag_lvl);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        launched = true;
+        mark(1);
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3((unsigned)std::max<int64_t>(1, (n_inv + 7) / 8));
+        cfg.blockDim = dim3(256);
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = trace ? 0 : 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        DevProblem P = v.P;
+        BucketScratch Sc = S;
+        void *args[] = {&P, &n_inv, &dag, &op_local, &start, &now, &Sc, &out};
+        e = cudaLaunchKernelExC(&cfg, v.mode == LLAMA_MODE_ALPHA ? (const void *)k_direct_al : (const void *)k_direct_cf,
+                                args);
         if (e != cudaSuccess) return e;
         mark(2);
         return cudaGetLastError();

@@ -138,6 +138,7 @@ struct llama_ctx {
     int32_t n_cta_ops = 0;  // ops (bucket order) scored by whole CTAs; the rest by warp tiles
     int32_t count_pass = LLAMA_COUNT_PASS_AUTO;
     int32_t wait_tries = kMaxWaitTries;  // polls of a bucketing grid barrier (llama_set_wait_limit)
+    int64_t direct_max = LLAMA_DIRECT_DEFAULT;  // small calls without bucketing (llama_set_direct_max)
     cudaEvent_t trace[LLAMA_TRACE_EVENTS] = {};
     bool tracing = false;
 
@@ -312,6 +313,7 @@ ContextView view_of(const llama_ctx *c) {
     v.score_smem = c->score_smem;
     v.max_ncfg = c->max_ncfg;
     v.warp_tiles = c->n_cta_ops < c->n_ops;
+    v.direct_max = c->method == LLAMA_METHOD_SCAN ? c->direct_max : 0;
     // the count pass: where some op may have more distinct latencies than the
     // scoring kernel stages, if asked for, or by default when such ops are at
     // least half of them (few invocations per table: the scoring kernel's own
@@ -565,7 +567,7 @@ int capture_graph(llama_ctx *c, int64_t n_inv, const int32_t *dag, const int32_t
     const BucketScratch S = make_scratch(c->ws);
     LL_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
     const cudaError_t e = enqueue_schedule(v, S, n_inv, dag, op_local, start, now, out, c->cap_stream, nullptr);
-    c->g_launches = schedule_launches(v, S);
+    c->g_launches = schedule_launches(v, S, n_inv);
     cudaGraph_t g = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
     if (e != cudaSuccess) {
@@ -585,9 +587,10 @@ int capture_graph(llama_ctx *c, int64_t n_inv, const int32_t *dag, const int32_t
         if (t == cudaGraphNodeTypeKernel) {
             cudaKernelNodeParams p{};
             LL_CUDA(c, cudaGraphKernelNodeGetParams(node, &p));
-            // `now` is argument 5 of both k_bucket (14 arguments) and k_stair (8)
+            // `now` is argument 5 of k_bucket (14 arguments), k_stair and k_direct_* (8)
             if (p.func == (void *)k_bucket) c->g_bucket = node, c->g_now_nargs = 14;
-            if (p.func == (void *)k_stair) c->g_bucket = node, c->g_now_nargs = 8;
+            if (p.func == (void *)k_stair || p.func == (void *)k_direct_cf || p.func == (void *)k_direct_al)
+                c->g_bucket = node, c->g_now_nargs = 8;
         }
     }
     if (!c->g_bucket) return c->fail(LLAMA_ECUDA, "graph capture: kernel node not found");
@@ -607,7 +610,7 @@ int launch_schedule(llama_ctx *c, int64_t n_inv, const int32_t *dag, const int32
         const BucketScratch S = make_scratch(c->ws);
         LL_CUDA(c, enqueue_schedule(v, S, n_inv, dag, op_local, start, now, out, s,
                                     c->tracing ? c->trace : nullptr));
-        c->last_launches = schedule_launches(v, S);
+        c->last_launches = schedule_launches(v, S, n_inv);
         return LLAMA_OK;
     }
     const bool same = c->gexec && c->g_n_inv == n_inv && c->g_args[0] == dag &&
@@ -1155,6 +1158,18 @@ extern "C" int llama_set_wait_limit(llama_ctx *c, int32_t tries) {
         DeviceGuard g(c->opts.device);
         c->drop_graph();  // the limit is a kernel argument of the captured launches
         c->wait_tries = tries;
+    }
+    return LLAMA_OK;
+}
+
+extern "C" int llama_set_direct_max(llama_ctx *c, int64_t n_inv) {
+    if (!c) return LLAMA_EINVAL;
+    if (n_inv < 0 || n_inv > LLAMA_DIRECT_LIMIT)
+        return c->fail(LLAMA_EINVAL, "set_direct_max: n_inv must be in 0..LLAMA_DIRECT_LIMIT");
+    if (n_inv != c->direct_max) {
+        DeviceGuard g(c->opts.device);
+        c->drop_graph();  // the captured launch sequence changes
+        c->direct_max = n_inv;
     }
     return LLAMA_OK;
 }

@@ -234,6 +234,7 @@ struct ContextView {
     bool need_counts;     // some op may have more distinct latencies than dlat_cap
     int32_t max_ncfg;     // configurations of the largest op
     bool warp_tiles;      // some op is scored by warp tiles (the scoring kernel with the warp phase)
+    int64_t direct_max;   // scan-method calls of at most this many invocations skip the bucketing
 };
 int context_view(llama_ctx *c, ContextView *v);  // LLAMA_OK or the readiness error
 int context_fail(llama_ctx *c, int code, const char *msg);
@@ -290,7 +291,7 @@ template <int MAXH>
 __global__ void k_counts(DevProblem P, BucketScratch S, int32_t dl_cap);
 // Kernel launches of one scheduling call (scan method): bucketing, the count
 // pass when it runs, scoring.
-int schedule_launches(const ContextView &v, const BucketScratch &S);
+int schedule_launches(const ContextView &v, const BucketScratch &S, int64_t n_inv);
 // Eq. 2: per-backend sums of L(x_i) R(x_i) over decided invocations, then the
 // queueing time floor(sum / R_total(lambda)) of every backend.
 __global__ void k_queue_sum(DevProblem P, int64_t n, const int32_t *dag, const int32_t *op_local,
@@ -321,6 +322,13 @@ __global__ void k_critical_paths(DevProblem P, const int32_t *topo, const int32_
                                  const int32_t *dag_lvl);
 __global__ void k_stair(DevProblem P, int64_t n_inv, const int32_t *dag, const int32_t *op_local,
                         const int64_t *start, int64_t now, BucketScratch S, llama_decision *out);
+// Small calls of the scan method (at most the context's direct limit of
+// invocations): critical paths, then a warp per invocation scanning its op's
+// table straight from L2, no bucketing (cost-first and alpha objectives).
+__global__ void k_direct_cf(DevProblem P, int64_t n_inv, const int32_t *dag, const int32_t *op_local,
+                            const int64_t *start, int64_t now, BucketScratch S, llama_decision *out);
+__global__ void k_direct_al(DevProblem P, int64_t n_inv, const int32_t *dag, const int32_t *op_local,
+                            const int64_t *start, int64_t now, BucketScratch S, llama_decision *out);
 __global__ void k_encode_rank(DevProblem P, int32_t sort_n, uint16_t *rf, uint16_t *df,
                               uint16_t *inv);
 

@@ -138,7 +138,7 @@ extern "C" int llama_schedule_static(llama_ctx *c, int64_t n_inv, const int32_t 
     e = enqueue_schedule(v, S, n_inv, dag, op_local, start_us, now_us, out,
                          static_cast<cudaStream_t>(stream), nullptr);
     if (e != cudaSuccess) return cuda_error(c, e, "enqueue");
-    context_set_launches(c, schedule_launches(v, S));
+    context_set_launches(c, schedule_launches(v, S, n_inv));
     return LLAMA_OK;
 }
 

@@ -26,6 +26,7 @@ MODE_COST_FIRST, MODE_ALPHA = 0, 1
 METHOD_SCAN, METHOD_STAIRCASE = 0, 1
 FLAG_FEASIBLE, FLAG_INVALID, FLAG_TIMEOUT = 1, 2, 4
 WAIT_LIMIT_DEFAULT = 1 << 20
+DIRECT_DEFAULT, DIRECT_LIMIT = 1024, 1 << 20
 MAX_HW, MAX_CFG = 8, 8192
 
 DECISION_DTYPE = np.dtype([("cfg", "<i4"), ("lat", "<i4"), ("cost", "<i8"),
@@ -45,7 +46,7 @@ EXPORTS = ("llama_create", "llama_destroy", "llama_set_dags", "llama_set_profile
            "llama_server_create", "llama_server_destroy", "llama_server_submit", "llama_server_poll",
            "llama_server_drain", "llama_server_stats_get", "llama_queue_time", "llama_feedback",
            "llama_get_profiles", "llama_backend_objectives", "llama_commit_order",
-           "llama_static_status", "llama_set_wait_limit", "llama_alu_peak", "llama_count_rate", "llama_stragglers", "llama_set_stats_file",
+           "llama_static_status", "llama_set_wait_limit", "llama_set_direct_max", "llama_alu_peak", "llama_count_rate", "llama_stragglers", "llama_set_stats_file",
            "llama_check_build", "llama_check_word",
            "llama_loop_create", "llama_loop_destroy", "llama_loop_submit", "llama_loop_tick", "llama_loop_poll",
            "llama_loop_run_arrivals", "llama_sg_run_arrivals",
@@ -162,6 +163,7 @@ def load(path: str = None) -> ctypes.CDLL:
             "llama_commit_order": ([vp, i64, vp, vp, vp, vp, vp, vp, vp], ctypes.c_int),
             "llama_static_status": ([vp, vp, vp, vp], ctypes.c_int),
             "llama_set_wait_limit": ([vp, i32], ctypes.c_int),
+            "llama_set_direct_max": ([vp, i64], ctypes.c_int),
             "llama_alu_peak": ([i32, i32, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
             "llama_count_rate": ([i32, i64, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
                                  ctypes.c_int),
@@ -548,6 +550,11 @@ def llama_set_wait_limit(ctx, tries: int) -> None:
     _check(ctx, load().llama_set_wait_limit(ctx, int(tries)))
 
 
+def llama_set_direct_max(ctx, n_inv: int) -> None:
+    """Scan-method calls of at most n_inv invocations skip the bucketing (DIRECT_DEFAULT; 0: never)."""
+    _check(ctx, load().llama_set_direct_max(ctx, int(n_inv)))
+
+
 def llama_stragglers(dec: np.ndarray, obs_us, failed, now_us: int, timeout=(3, 2), tick_us: int = 1) -> tuple:
     """(indices, hand-back times) of the invocations that get a duplicate: an
     error before the time-out or still running at it (timeout = num/den times
@@ -708,15 +715,22 @@ class Loop:
 
 
 class Scheduler:
-    """A context loaded with one Problem (see ``workloads``)."""
+    """A context loaded with one Problem (see ``workloads``).  direct_max: the
+    small-call limit (llama_set_direct_max; None keeps the class attribute,
+    whose None keeps the library's DIRECT_DEFAULT)."""
+
+    direct_max = None
 
     def __init__(self, problem, mode: int = MODE_COST_FIRST, alpha=(1, 1), device: int = 0,
-                 use_graph: bool = False, method: int = METHOD_SCAN):
+                 use_graph: bool = False, method: int = METHOD_SCAN, direct_max=None):
         self.problem = problem
         self.mode = mode
         self.ctx = llama_create(mode, problem.n_hw, alpha, device, use_graph)
         if method != METHOD_SCAN:
             llama_set_method(self.ctx, method)
+        direct_max = self.direct_max if direct_max is None else direct_max
+        if direct_max is not None:
+            llama_set_direct_max(self.ctx, direct_max)
         p = problem
         llama_set_dags(self.ctx, p.dag_op_off, p.row_ptr, p.col, p.slo_us)
         alpha_mode = mode == MODE_ALPHA

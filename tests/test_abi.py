@@ -71,7 +71,8 @@ def test_constants_match_header():
                       ("LLAMA_FLAG_FEASIBLE", L.FLAG_FEASIBLE), ("LLAMA_FLAG_INVALID", L.FLAG_INVALID),
                       ("LLAMA_FLAG_TIMEOUT", L.FLAG_TIMEOUT), ("LLAMA_WAIT_LIMIT_DEFAULT", L.WAIT_LIMIT_DEFAULT),
                       ("LLAMA_MAX_HW", L.MAX_HW), ("LLAMA_MAX_CFG", L.MAX_CFG),
-                      ("LLAMA_METHOD_STAIRCASE", L.METHOD_STAIRCASE), ("LLAMA_GEMM_RELU", L.GEMM_RELU)]:
+                      ("LLAMA_METHOD_STAIRCASE", L.METHOD_STAIRCASE), ("LLAMA_GEMM_RELU", L.GEMM_RELU),
+                      ("LLAMA_DIRECT_DEFAULT", L.DIRECT_DEFAULT), ("LLAMA_DIRECT_LIMIT", L.DIRECT_LIMIT)]:
         m = re.search(rf"#define {name} \(?(-?\d+)( << (\d+))?\)?", text)
         assert m and int(m.group(1)) << int(m.group(3) or 0) == val, name
 

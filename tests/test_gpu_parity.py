@@ -4,6 +4,8 @@ Integer work, so the bar is bit-exact on every field of every decision
 (chosen configuration, its latency, cost, slack and flags), on the critical
 path and on the slack of every backend.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -31,10 +33,15 @@ def assert_same(got, exp, what=""):
                               f"got {got[bad[:5]]} expected {exp[bad[:5]]}"
 
 
-@pytest.fixture(params=[0, 1], ids=["scan", "staircase"])
-def method(request):
-    """Selection method: the scan of every configuration, or the staircase."""
-    return request.param
+@pytest.fixture(params=[(0, 0), (0, 1), (1, None)], ids=["scan", "scan_direct", "staircase"])
+def method(request, L, monkeypatch):
+    """Selection method: the scan of every configuration, bucketed by op (every
+    call) or without bucketing (every call up to DIRECT_LIMIT invocations), or
+    the staircase."""
+    m, direct = request.param
+    if direct is not None:
+        monkeypatch.setattr(L.Scheduler, "direct_max", L.DIRECT_LIMIT if direct else 0)
+    return m
 
 
 def run_both(L, p, inv, mode=0, alpha=(1, 1), method=0):
@@ -628,3 +635,58 @@ def test_batched_large_full(L, batched_large, mode, alpha, method):
     p, inv = batched_large
     got, exp = run_both(L, p, inv, mode=mode, alpha=alpha, method=method)
     assert_same(got, exp)
+
+
+# ------------------------------------------------------------- small calls ---
+
+def test_small_calls_skip_the_bucketing(L):
+    # A call of at most the limit's invocations has no bounded wait (critical
+    # paths, then a warp per invocation): with a wait limit of 0 it still
+    # decides, one invocation above the limit is bucketed and gives up.  Both
+    # sides of the limit, the limit off and at its maximum, and the static
+    # entry point with invalid invocations, against the oracle.
+    import torch
+    lib = L.load()
+    p, inv = W.medium(n_inv=4096)
+    assert L.Scheduler.direct_max is None  # the library default applies
+    with L.Scheduler(p) as s:
+        assert lib.llama_set_direct_max(s.ctx, -1) == L.EINVAL
+        assert lib.llama_set_direct_max(s.ctx, L.DIRECT_LIMIT + 1) == L.EINVAL
+        L.llama_set_wait_limit(s.ctx, 0)
+        # (a bucketed call gives up only with two counting blocks or more: over 256 invocations)
+        for limit, n, decided in ((None, L.DIRECT_DEFAULT, True), (None, L.DIRECT_DEFAULT + 1, False),
+                                  (0, 300, False), (300, 300, True), (L.DIRECT_LIMIT, inv.n, True),
+                                  (None, 1, True)):
+            if limit is not None:
+                L.llama_set_direct_max(s.ctx, limit)
+            sub = inv.subset(np.arange(n))
+            out = np.full(n, -7, L.DECISION_DTYPE)
+            rc = lib.llama_schedule(s.ctx, n, sub.dag.ctypes.data, sub.op_local.ctypes.data,
+                                    sub.start_us.ctypes.data, sub.now_us, out.ctypes.data)
+            if decided:
+                assert rc == L.OK, L.llama_last_error(s.ctx)
+                assert L.llama_last_launch_count(s.ctx) == 2
+                exp, _ = oracle.schedule(p, sub)
+                assert_same(out, exp, f"{n} invocations, limit {limit}")
+            else:
+                assert rc == L.ETIMEOUT, (n, limit)
+        L.llama_set_wait_limit(s.ctx, L.WAIT_LIMIT_DEFAULT)
+        L.llama_set_direct_max(s.ctx, L.DIRECT_DEFAULT)
+        # the static entry point, a fifth of the invocations invalid
+        sub = inv.subset(np.arange(L.DIRECT_DEFAULT))
+        sub.dag[::5] = -1
+        exp, rc_o = oracle.schedule(p, sub)
+        assert rc_o == oracle.EINVAL
+        dev = torch.device("cuda", 0)
+        stream = torch.cuda.Stream(device=dev)
+        d = [torch.from_numpy(a).to(dev) for a in (sub.dag, sub.op_local, sub.start_us)]
+        o = torch.full((sub.n * 24,), 0xA5, dtype=torch.uint8, device=dev)
+        sp = ctypes.c_void_p(stream.cuda_stream)
+        assert lib.llama_schedule_static(s.ctx, sub.n, d[0].data_ptr(), d[1].data_ptr(), d[2].data_ptr(),
+                                         sub.now_us, o.data_ptr(), sp) == L.OK
+        n_bad, tmo = ctypes.c_int64(-1), ctypes.c_int32(-1)
+        assert lib.llama_static_status(s.ctx, sp, ctypes.byref(n_bad), ctypes.byref(tmo)) == L.OK
+        stream.synchronize()
+        assert (n_bad.value, tmo.value) == (int((sub.dag < 0).sum()), 0)
+        assert L.llama_last_launch_count(s.ctx) == 2
+        assert_same(o.cpu().numpy().view(L.DECISION_DTYPE), exp, "static entry point")
