@@ -393,8 +393,9 @@ int llama_set_direct_max(llama_ctx *ctx, int64_t n_inv);
  * llama_ws_status / llama_static_status.  The default,
  * LLAMA_WAIT_LIMIT_DEFAULT, is never reached by a launch whose blocks are all
  * resident; a lower value (0: give up at once) exercises the give-up path.
- * Table staging waits keep their own fixed bound.  Errors: EINVAL (tries
- * outside 0..LLAMA_WAIT_LIMIT_DEFAULT). */
+ * Table staging waits keep their own fixed bound.  Calls small enough for
+ * the path without bucketing (llama_set_direct_max) have no wait to give up.
+ * Errors: EINVAL (tries outside 0..LLAMA_WAIT_LIMIT_DEFAULT). */
 #define LLAMA_WAIT_LIMIT_DEFAULT (1 << 20)
 int llama_set_wait_limit(llama_ctx *ctx, int32_t tries);
 
